@@ -1,0 +1,498 @@
+/*
+ * glbm_oracle.c -- plain FP64 CPU oracle for the Gaussian lattice Boltzmann
+ * method of O. Ilyin, "Gaussian Lattice Boltzmann method and its applications
+ * to rarefied flows" (arXiv:1905.04597).
+ *
+ * TEST INFRASTRUCTURE. Only the test suite, the smoke check and the
+ * benchmark's CPU-baseline leg load this library. It shares no code, header,
+ * table or helper with the CUDA path:
+ *   - the equilibrium is evaluated at every node from the factorial sum of
+ *     Sec. 2 (Eq. maineq03 with Eqs. maineq04-05), never from a polynomial
+ *     coefficient table;
+ *   - streaming is written in push form (each population is moved from its
+ *     source node); the CUDA path pulls.
+ *
+ * Units. Lattice units per axis: node spacing c(N)*dt = 1 and dt = 1, so the
+ * discrete velocities of level N are the integers n = -N..N and the lattice
+ * temperature is theta = c_s^2 = N/3 (Eq. maineq05 with c = 1).
+ *
+ * Time stepping. The state X_t is the array of post-collision populations.
+ * One step is X_{t+1} = C(S(X_t)) with S the streaming (including boundary
+ * rules) and C the BGK collision of Eq. maineq01 with frequency
+ * 1/(tau + 1/2). The macroscopic fields "at time t" are the moments of the
+ * streamed populations S(X_t).
+ *
+ * Layout. Populations f[q][y][x], x fastest, q = (ny+NY)*(2NX+1) + (nx+NX)
+ * for the 2D tensor-product lattice (Sec. 4) and q = n+N in 1D.
+ *
+ * Boundary readings (the paper cites its wall condition but states no
+ * formula; Sec. 5.3-5.4):
+ *   - walls sit halfway between nodes, at y = -1/2 and y = Ly - 1/2;
+ *   - diffuse (kinetic) reflection: every population that streams into a wall
+ *     is absorbed and its mass is attributed to the column x it would have
+ *     reached; the wall re-emits, into every (node, velocity) whose source lies
+ *     inside the wall, rho_w(x) * E^x_{nx}(u_w) * E^y_{ny}(0), with rho_w(x)
+ *     chosen so that the emitted mass equals the absorbed mass of column x;
+ *   - 1D ends use halfway bounce-back;
+ *   - the body force is F_i = W_i * xi_{x,i} * g / theta_x added after the
+ *     relaxation (the linearised force of Sec. 5.4 written for the lattice
+ *     used along the flow).
+ */
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORC_MAX_N 16
+
+enum { ORC_BC_WALLS = 0, ORC_BC_BOUNCEBACK = 1, ORC_BC_PERIODIC = 2 };
+
+/* Configuration of one lattice; mirrored by a ctypes.Structure in oracle.py. */
+typedef struct {
+    int dims;  /* 1 or 2 */
+    int NX;    /* level N along x (velocities -NX..NX) */
+    int NY;    /* level N along y (2D only) */
+    int Lx;    /* nodes along x */
+    int Ly;    /* nodes along y (1 in 1D) */
+    int bc;    /* ORC_BC_* */
+    double tau;   /* relaxation time; omega = 1/(tau + 1/2) */
+    double uw_lo; /* x-velocity of the wall at y = -1/2 (lattice units) */
+    double uw_hi; /* x-velocity of the wall at y = Ly - 1/2 */
+    double g;     /* body force along x (lattice units), 2D only */
+} orc_cfg;
+
+static double orc_factorial(int n)
+{
+    double r = 1.0;
+    for (int i = 2; i <= n; ++i) r *= (double)i;
+    return r;
+}
+
+/*
+ * Sub-probabilities of one three-outcome variable at level N, Eqs. maineq04
+ * and the line after it: P_{N,+-} = (c_s^2 +- c*u + u^2/N) / (2 c^2 N) and
+ * P_{N,0} = 1 - P_{N,+} - P_{N,-}.
+ */
+static void orc_subprob(int N, double c, double cs2, double u,
+                        double *Pp, double *Pm, double *P0)
+{
+    *Pp = (cs2 + c * u + u * u / N) / (2.0 * c * c * N);
+    *Pm = (cs2 - c * u + u * u / N) / (2.0 * c * c * N);
+    *P0 = 1.0 - *Pp - *Pm;
+}
+
+/*
+ * Prob(sum_{j=1}^N X_j = n c), Eq. maineq03: for n >= 0,
+ *   sum_{m=0}^{floor((N-n)/2)} N!/((n+m)! m! (N-n-2m)!) P+^{n+m} P-^m P0^{N-n-2m};
+ * for n < 0 the same with |n| and P+ and P- exchanged (end of Sec. 2).
+ */
+static double orc_trinomial(int N, int n, double Pp, double Pm, double P0)
+{
+    if (n < 0) {
+        double t = Pp;
+        Pp = Pm;
+        Pm = t;
+        n = -n;
+    }
+    double s = 0.0;
+    for (int m = 0; m <= (N - n) / 2; ++m) {
+        double ways = orc_factorial(N) /
+                      (orc_factorial(n + m) * orc_factorial(m) * orc_factorial(N - n - 2 * m));
+        s += ways * pow(Pp, n + m) * pow(Pm, m) * pow(P0, N - n - 2 * m);
+    }
+    return s;
+}
+
+/*
+ * Equilibrium probabilities of level N in physical units (Eqs. maineq02-05):
+ * out[n+N] = Prob(sum = n c) for n = -N..N, lattice speed c and temperature
+ * cs2 = c_s^2 given independently so the worked example of App. A (unit
+ * temperature, c = sqrt(3/2)) can be evaluated. Returns 1 when a
+ * sub-probability is negative (outside the positivity domain of Sec. 3),
+ * else 0.
+ */
+int orc_prob(int N, double c, double cs2, double u, double *out)
+{
+    double Pp, Pm, P0;
+    if (N < 1 || N > ORC_MAX_N) return -1;
+    orc_subprob(N, c, cs2, u, &Pp, &Pm, &P0);
+    for (int n = -N; n <= N; ++n) out[n + N] = orc_trinomial(N, n, Pp, Pm, P0);
+    return (Pp < 0.0 || Pm < 0.0 || P0 < 0.0) ? 1 : 0;
+}
+
+/* Lattice-unit equilibrium f^eq_n / rho at level N: c = 1, c_s^2 = N/3. */
+static void orc_eq_lattice(int N, double u, double *out)
+{
+    double Pp, Pm, P0;
+    orc_subprob(N, 1.0, N / 3.0, u, &Pp, &Pm, &P0);
+    for (int n = -N; n <= N; ++n) out[n + N] = orc_trinomial(N, n, Pp, Pm, P0);
+}
+
+/* Public wrapper of orc_eq_lattice (density 1). */
+void orc_eq1d(int N, double u, double *out)
+{
+    orc_eq_lattice(N, u, out);
+}
+
+/* Rest weights W_n = f^eq_{n;N}(rho = 1, u = 0) (Sec. 5.4, App. A). */
+void orc_weights(int N, double *out)
+{
+    orc_eq_lattice(N, 0.0, out);
+}
+
+/*
+ * Knudsen number to relaxation time, Eq. (kn): Kn = sqrt(2/theta) nu / H with
+ * nu = theta * tau (Sec. 5.2), in lattice units theta = N/3.
+ */
+double orc_tau_from_kn(int N, double H, double kn)
+{
+    double theta = N / 3.0;
+    return kn * H / sqrt(2.0 * theta);
+}
+
+static int orc_check(const orc_cfg *c)
+{
+    if (c->dims == 1) {
+        if (c->NX < 1 || c->NX > ORC_MAX_N || c->Lx < 1 || c->Ly != 1) return -1;
+        if (c->bc == ORC_BC_BOUNCEBACK && c->Lx < c->NX) return -1;
+        if (c->bc != ORC_BC_BOUNCEBACK && c->bc != ORC_BC_PERIODIC) return -1;
+    } else if (c->dims == 2) {
+        if (c->NX < 1 || c->NX > ORC_MAX_N || c->NY < 1 || c->NY > ORC_MAX_N) return -1;
+        if (c->Lx < 1 || c->Ly < 1) return -1;
+        if (c->bc == ORC_BC_WALLS && c->Ly < c->NY) return -1;
+        if (c->bc != ORC_BC_WALLS && c->bc != ORC_BC_PERIODIC) return -1;
+    } else {
+        return -1;
+    }
+    return c->tau > 0.0 ? 0 : -1;
+}
+
+static int orc_nq(const orc_cfg *c)
+{
+    return c->dims == 1 ? 2 * c->NX + 1 : (2 * c->NX + 1) * (2 * c->NY + 1);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Streaming (push form)                                                     */
+/* ------------------------------------------------------------------------ */
+
+static int orc_wrap(int i, int L)
+{
+    i %= L;
+    return i < 0 ? i + L : i;
+}
+
+/*
+ * 1D streaming: f_n(x + n) <- X_n(x). Periodic, or halfway bounce-back at
+ * x = -1/2 and x = L - 1/2 (a population leaving through an end comes back
+ * with the opposite velocity, having travelled the same distance).
+ */
+static void orc_stream1d(const orc_cfg *c, const double *X, double *F)
+{
+    int N = c->NX, L = c->Lx;
+    for (int n = -N; n <= N; ++n) {
+        for (int x = 0; x < L; ++x) {
+            double v = X[(n + N) * L + x];
+            int xd = x + n;
+            if (c->bc == ORC_BC_PERIODIC) {
+                F[(n + N) * L + orc_wrap(xd, L)] = v;
+            } else if (xd < 0) {
+                F[(-n + N) * L + (-1 - xd)] = v;
+            } else if (xd >= L) {
+                F[(-n + N) * L + (2 * L - 1 - xd)] = v;
+            } else {
+                F[(n + N) * L + xd] = v;
+            }
+        }
+    }
+}
+
+/*
+ * 2D streaming: f_i(x + xi_x, y + xi_y) <- X_i(x, y), periodic in x. With
+ * walls, populations crossing y = -1/2 or y = Ly - 1/2 are absorbed into the
+ * wall of that side, booked under the column they would have reached; then
+ * each wall re-emits its absorbed mass of column x as
+ * rho_w(x) E^x(u_w) W^y into the rows whose source lies inside the wall.
+ */
+static void orc_stream2d(const orc_cfg *c, const double *X, double *F)
+{
+    int NX = c->NX, NY = c->NY, Lx = c->Lx, Ly = c->Ly;
+    int Q1x = 2 * NX + 1;
+    size_t plane = (size_t)Lx * Ly;
+    double *Dlo = (double *)calloc((size_t)Lx, sizeof(double));
+    double *Dhi = (double *)calloc((size_t)Lx, sizeof(double));
+
+    for (int ny = -NY; ny <= NY; ++ny) {
+        for (int nx = -NX; nx <= NX; ++nx) {
+            int q = (ny + NY) * Q1x + (nx + NX);
+            for (int y = 0; y < Ly; ++y) {
+                for (int x = 0; x < Lx; ++x) {
+                    double v = X[q * plane + (size_t)y * Lx + x];
+                    int xd = orc_wrap(x + nx, Lx);
+                    int yd = y + ny;
+                    if (c->bc == ORC_BC_PERIODIC) {
+                        F[q * plane + (size_t)orc_wrap(yd, Ly) * Lx + xd] = v;
+                    } else if (yd < 0) {
+                        Dlo[xd] += v;
+                    } else if (yd >= Ly) {
+                        Dhi[xd] += v;
+                    } else {
+                        F[q * plane + (size_t)yd * Lx + xd] = v;
+                    }
+                }
+            }
+        }
+    }
+
+    if (c->bc == ORC_BC_WALLS) {
+        double Wy[2 * ORC_MAX_N + 1], Elo[2 * ORC_MAX_N + 1], Ehi[2 * ORC_MAX_N + 1];
+        orc_eq_lattice(NY, 0.0, Wy);
+        orc_eq_lattice(NX, c->uw_lo, Elo);
+        orc_eq_lattice(NX, c->uw_hi, Ehi);
+        /* emitted mass per unit rho_w: sum over velocities leaving the wall of
+           |xi_y| * E^x * W^y, i.e. one population per row it fills */
+        double den = 0.0;
+        for (int ny = 1; ny <= NY; ++ny) {
+            for (int nx = -NX; nx <= NX; ++nx) den += ny * Elo[nx + NX] * Wy[ny + NY];
+        }
+        double den_hi = 0.0;
+        for (int ny = 1; ny <= NY; ++ny) {
+            for (int nx = -NX; nx <= NX; ++nx) den_hi += ny * Ehi[nx + NX] * Wy[-ny + NY];
+        }
+        for (int x = 0; x < Lx; ++x) {
+            double rlo = Dlo[x] / den;
+            double rhi = Dhi[x] / den_hi;
+            for (int ny = 1; ny <= NY; ++ny) {
+                for (int nx = -NX; nx <= NX; ++nx) {
+                    int qup = (ny + NY) * Q1x + (nx + NX);   /* leaves the lower wall */
+                    int qdn = (-ny + NY) * Q1x + (nx + NX);  /* leaves the upper wall */
+                    for (int k = 0; k < ny; ++k) {
+                        F[qup * plane + (size_t)k * Lx + x] = rlo * Elo[nx + NX] * Wy[ny + NY];
+                        F[qdn * plane + (size_t)(Ly - 1 - k) * Lx + x] =
+                            rhi * Ehi[nx + NX] * Wy[-ny + NY];
+                    }
+                }
+            }
+        }
+    }
+    free(Dlo);
+    free(Dhi);
+}
+
+int orc_stream(const orc_cfg *c, const double *X, double *F)
+{
+    if (orc_check(c)) return -1;
+    if (c->dims == 1)
+        orc_stream1d(c, X, F);
+    else
+        orc_stream2d(c, X, F);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Collision (Eq. maineq01 right-hand side)                                  */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * BGK relaxation at every node: f* = f + omega (f^eq - f) + F_i with
+ * omega = 1/(tau + 1/2), f^eq = rho E^x(u_x) E^y(u_y) (product form, Sec. 4)
+ * and rho, rho u the zeroth and first moments of f. Returns the number of
+ * nodes whose equilibrium left the positivity domain (Sec. 3) or whose
+ * density is not positive.
+ */
+int orc_collide(const orc_cfg *c, const double *F, double *X)
+{
+    if (orc_check(c)) return -1;
+    double omega = 1.0 / (c->tau + 0.5);
+    int bad = 0;
+    if (c->dims == 1) {
+        int N = c->NX, L = c->Lx;
+        double E[2 * ORC_MAX_N + 1];
+        for (int x = 0; x < L; ++x) {
+            double rho = 0.0, j = 0.0;
+            for (int n = -N; n <= N; ++n) {
+                rho += F[(n + N) * L + x];
+                j += n * F[(n + N) * L + x];
+            }
+            double u = j / rho;
+            if (!(rho > 0.0) || fabs(u) > sqrt(2.0 / 3.0) * N) ++bad;
+            orc_eq_lattice(N, u, E);
+            for (int n = -N; n <= N; ++n) {
+                double f = F[(n + N) * L + x];
+                X[(n + N) * L + x] = f + omega * (rho * E[n + N] - f);
+            }
+        }
+        return bad;
+    }
+
+    int NX = c->NX, NY = c->NY, Lx = c->Lx, Ly = c->Ly;
+    int Q1x = 2 * NX + 1;
+    size_t plane = (size_t)Lx * Ly;
+    double Wx[2 * ORC_MAX_N + 1], Wy[2 * ORC_MAX_N + 1];
+    double Ex[2 * ORC_MAX_N + 1], Ey[2 * ORC_MAX_N + 1];
+    orc_eq_lattice(NX, 0.0, Wx);
+    orc_eq_lattice(NY, 0.0, Wy);
+    double theta_x = NX / 3.0;
+    for (int y = 0; y < Ly; ++y) {
+        for (int x = 0; x < Lx; ++x) {
+            size_t node = (size_t)y * Lx + x;
+            double rho = 0.0, jx = 0.0, jy = 0.0;
+            for (int ny = -NY; ny <= NY; ++ny) {
+                for (int nx = -NX; nx <= NX; ++nx) {
+                    double f = F[((ny + NY) * Q1x + (nx + NX)) * plane + node];
+                    rho += f;
+                    jx += nx * f;
+                    jy += ny * f;
+                }
+            }
+            double ux = jx / rho, uy = jy / rho;
+            if (!(rho > 0.0) || fabs(ux) > sqrt(2.0 / 3.0) * NX ||
+                fabs(uy) > sqrt(2.0 / 3.0) * NY)
+                ++bad;
+            orc_eq_lattice(NX, ux, Ex);
+            orc_eq_lattice(NY, uy, Ey);
+            for (int ny = -NY; ny <= NY; ++ny) {
+                for (int nx = -NX; nx <= NX; ++nx) {
+                    size_t idx = ((ny + NY) * Q1x + (nx + NX)) * plane + node;
+                    double f = F[idx];
+                    double feq = rho * Ex[nx + NX] * Ey[ny + NY];
+                    double force = Wx[nx + NX] * Wy[ny + NY] * nx * c->g / theta_x;
+                    X[idx] = f + omega * (feq - f) + force;
+                }
+            }
+        }
+    }
+    return bad;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Macroscopic fields                                                        */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * Moments of populations F at every node (Sec. 2 for rho, rho u; the
+ * temperature, heat flux and shear stress are the usual central moments):
+ * 2D out[7][Ly][Lx] = rho, u_x, u_y, T = sum |xi-u|^2 f / (2 rho),
+ *   q_x, q_y = (1/2) sum (xi-u)_a |xi-u|^2 f, sigma_xy = sum (xi-u)_x (xi-u)_y f;
+ * 1D out[4][L] = rho, u, T = sum (xi-u)^2 f / rho, q = (1/2) sum (xi-u)^3 f.
+ */
+int orc_macro(const orc_cfg *c, const double *F, double *out)
+{
+    if (orc_check(c)) return -1;
+    if (c->dims == 1) {
+        int N = c->NX, L = c->Lx;
+        for (int x = 0; x < L; ++x) {
+            double rho = 0.0, j = 0.0;
+            for (int n = -N; n <= N; ++n) {
+                rho += F[(n + N) * L + x];
+                j += n * F[(n + N) * L + x];
+            }
+            double u = j / rho, e2 = 0.0, e3 = 0.0;
+            for (int n = -N; n <= N; ++n) {
+                double d = n - u, f = F[(n + N) * L + x];
+                e2 += d * d * f;
+                e3 += d * d * d * f;
+            }
+            out[0 * L + x] = rho;
+            out[1 * L + x] = u;
+            out[2 * L + x] = e2 / rho;
+            out[3 * L + x] = 0.5 * e3;
+        }
+        return 0;
+    }
+    int NX = c->NX, NY = c->NY, Lx = c->Lx, Ly = c->Ly;
+    int Q1x = 2 * NX + 1;
+    size_t plane = (size_t)Lx * Ly;
+    for (size_t node = 0; node < plane; ++node) {
+        double rho = 0.0, jx = 0.0, jy = 0.0;
+        for (int ny = -NY; ny <= NY; ++ny) {
+            for (int nx = -NX; nx <= NX; ++nx) {
+                double f = F[((ny + NY) * Q1x + (nx + NX)) * plane + node];
+                rho += f;
+                jx += nx * f;
+                jy += ny * f;
+            }
+        }
+        double ux = jx / rho, uy = jy / rho;
+        double e2 = 0.0, qx = 0.0, qy = 0.0, sxy = 0.0;
+        for (int ny = -NY; ny <= NY; ++ny) {
+            for (int nx = -NX; nx <= NX; ++nx) {
+                double f = F[((ny + NY) * Q1x + (nx + NX)) * plane + node];
+                double dx = nx - ux, dy = ny - uy, d2 = dx * dx + dy * dy;
+                e2 += d2 * f;
+                qx += dx * d2 * f;
+                qy += dy * d2 * f;
+                sxy += dx * dy * f;
+            }
+        }
+        out[0 * plane + node] = rho;
+        out[1 * plane + node] = ux;
+        out[2 * plane + node] = uy;
+        out[3 * plane + node] = e2 / (2.0 * rho);
+        out[4 * plane + node] = 0.5 * qx;
+        out[5 * plane + node] = 0.5 * qy;
+        out[6 * plane + node] = sxy;
+    }
+    return 0;
+}
+
+/*
+ * Local equilibrium initial state X_0 = rho E^x(u_x) E^y(u_y) at every node
+ * (rho, ux, uy given per node; uy ignored in 1D).
+ */
+int orc_equilibrium(const orc_cfg *c, const double *rho, const double *ux, const double *uy,
+                    double *X)
+{
+    if (orc_check(c)) return -1;
+    if (c->dims == 1) {
+        int N = c->NX, L = c->Lx;
+        double E[2 * ORC_MAX_N + 1];
+        for (int x = 0; x < L; ++x) {
+            orc_eq_lattice(N, ux[x], E);
+            for (int n = -N; n <= N; ++n) X[(n + N) * L + x] = rho[x] * E[n + N];
+        }
+        return 0;
+    }
+    int NX = c->NX, NY = c->NY;
+    int Q1x = 2 * NX + 1;
+    size_t plane = (size_t)c->Lx * c->Ly;
+    double Ex[2 * ORC_MAX_N + 1], Ey[2 * ORC_MAX_N + 1];
+    for (size_t node = 0; node < plane; ++node) {
+        orc_eq_lattice(NX, ux[node], Ex);
+        orc_eq_lattice(NY, uy[node], Ey);
+        for (int ny = -NY; ny <= NY; ++ny)
+            for (int nx = -NX; nx <= NX; ++nx)
+                X[((ny + NY) * Q1x + (nx + NX)) * plane + node] =
+                    rho[node] * Ex[nx + NX] * Ey[ny + NY];
+    }
+    return 0;
+}
+
+/*
+ * Advance X in place by `steps` steps X <- C(S(X)). Returns the number of
+ * collisions that left the positivity domain, or -1 on a bad configuration.
+ */
+long orc_run(const orc_cfg *c, double *X, long steps)
+{
+    if (orc_check(c)) return -1;
+    size_t n = (size_t)orc_nq(c) * c->Lx * c->Ly;
+    double *F = (double *)malloc(n * sizeof(double));
+    long bad = 0;
+    for (long t = 0; t < steps; ++t) {
+        orc_stream(c, X, F);
+        bad += orc_collide(c, F, X);
+    }
+    free(F);
+    return bad;
+}
+
+/* Moments at the current time: moments of S(X). */
+int orc_observe(const orc_cfg *c, const double *X, double *out)
+{
+    if (orc_check(c)) return -1;
+    size_t n = (size_t)orc_nq(c) * c->Lx * c->Ly;
+    double *F = (double *)malloc(n * sizeof(double));
+    orc_stream(c, X, F);
+    orc_macro(c, F, out);
+    free(F);
+    return 0;
+}

@@ -1,0 +1,162 @@
+"""ctypes binding of the FP64 CPU oracle (``glbm_oracle.c``).
+
+TEST INFRASTRUCTURE: only the tests, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` may import this module. It never touches
+the CUDA library and the CUDA path never imports it.
+
+Every function follows O. Ilyin, "Gaussian Lattice Boltzmann method and its
+applications to rarefied flows" (arXiv:1905.04597); the C source cites the
+section and equation behind each step.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+SRC = os.path.join(HERE, "glbm_oracle.c")
+LIB = os.path.join(HERE, "liboracle.so")
+
+BC_WALLS, BC_BOUNCEBACK, BC_PERIODIC = 0, 1, 2
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (plain -O2, no FMA contraction).
+
+    ``GLBM_ORACLE_LIB`` names a prebuilt copy to load instead; the mutation
+    tests use it to run the pins against an oracle with a planted mistake."""
+    override = os.environ.get("GLBM_ORACLE_LIB")
+    if override:
+        return override
+    if force or not os.path.exists(LIB) or os.path.getmtime(LIB) < os.path.getmtime(SRC):
+        tmp = LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(
+            ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared",
+             "-o", tmp, SRC, "-lm"])
+        os.replace(tmp, LIB)
+    return LIB
+
+
+class Cfg(ctypes.Structure):
+    _fields_ = [("dims", ctypes.c_int), ("NX", ctypes.c_int), ("NY", ctypes.c_int),
+                ("Lx", ctypes.c_int), ("Ly", ctypes.c_int), ("bc", ctypes.c_int),
+                ("tau", ctypes.c_double), ("uw_lo", ctypes.c_double),
+                ("uw_hi", ctypes.c_double), ("g", ctypes.c_double)]
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        _lib = ctypes.CDLL(build())
+        dp = ctypes.POINTER(ctypes.c_double)
+        cp = ctypes.POINTER(Cfg)
+        _lib.orc_prob.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                  ctypes.c_double, dp]
+        _lib.orc_prob.restype = ctypes.c_int
+        _lib.orc_eq1d.argtypes = [ctypes.c_int, ctypes.c_double, dp]
+        _lib.orc_weights.argtypes = [ctypes.c_int, dp]
+        _lib.orc_tau_from_kn.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double]
+        _lib.orc_tau_from_kn.restype = ctypes.c_double
+        for name in ("orc_stream", "orc_collide", "orc_macro", "orc_observe"):
+            getattr(_lib, name).argtypes = [cp, dp, dp]
+            getattr(_lib, name).restype = ctypes.c_int
+        _lib.orc_equilibrium.argtypes = [cp, dp, dp, dp, dp]
+        _lib.orc_equilibrium.restype = ctypes.c_int
+        _lib.orc_run.argtypes = [cp, dp, ctypes.c_long]
+        _lib.orc_run.restype = ctypes.c_long
+    return _lib
+
+
+def _dp(a: np.ndarray):
+    assert a.dtype == np.float64 and a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+class Lattice:
+    """One lattice for the oracle: level N per axis (N = k + 1), node counts,
+    boundary kind, relaxation time, wall speeds and body force, all in lattice
+    units (velocities are the integers -N..N)."""
+
+    def __init__(self, dims, NX, NY, Lx, Ly, bc, tau, uw_lo=0.0, uw_hi=0.0, g=0.0):
+        self.cfg = Cfg(dims, NX, NY if dims == 2 else 0, Lx, Ly if dims == 2 else 1, bc,
+                       tau, uw_lo, uw_hi, g)
+        self.dims = dims
+        self.Q = (2 * NX + 1) * ((2 * NY + 1) if dims == 2 else 1)
+        self.shape = (self.Q, self.cfg.Ly, Lx) if dims == 2 else (self.Q, Lx)
+        self.nfields = 7 if dims == 2 else 4
+
+    def _chk(self, rc):
+        if rc < 0:
+            raise ValueError("oracle rejected the configuration")
+        return rc
+
+    def equilibrium(self, rho, ux, uy=None):
+        rho = np.ascontiguousarray(rho, dtype=np.float64)
+        ux = np.ascontiguousarray(ux, dtype=np.float64)
+        uy = np.zeros_like(ux) if uy is None else np.ascontiguousarray(uy, dtype=np.float64)
+        X = np.empty(self.shape)
+        self._chk(lib().orc_equilibrium(ctypes.byref(self.cfg), _dp(rho), _dp(ux), _dp(uy),
+                                        _dp(X)))
+        return X
+
+    def stream(self, X):
+        X = np.ascontiguousarray(X, dtype=np.float64)
+        F = np.empty(self.shape)
+        self._chk(lib().orc_stream(ctypes.byref(self.cfg), _dp(X), _dp(F)))
+        return F
+
+    def collide(self, F):
+        F = np.ascontiguousarray(F, dtype=np.float64)
+        X = np.empty(self.shape)
+        bad = self._chk(lib().orc_collide(ctypes.byref(self.cfg), _dp(F), _dp(X)))
+        return X, bad
+
+    def macro(self, F):
+        F = np.ascontiguousarray(F, dtype=np.float64)
+        out = np.empty((self.nfields,) + self.shape[1:])
+        self._chk(lib().orc_macro(ctypes.byref(self.cfg), _dp(F), _dp(out)))
+        return out
+
+    def observe(self, X):
+        """Moments at the current time: moments of the streamed state S(X)."""
+        X = np.ascontiguousarray(X, dtype=np.float64)
+        out = np.empty((self.nfields,) + self.shape[1:])
+        self._chk(lib().orc_observe(ctypes.byref(self.cfg), _dp(X), _dp(out)))
+        return out
+
+    def run(self, X, steps):
+        """Advance a copy of X by `steps` steps; returns (X, unstable_count)."""
+        X = np.array(X, dtype=np.float64, order="C", copy=True)
+        bad = self._chk(lib().orc_run(ctypes.byref(self.cfg), _dp(X), int(steps)))
+        return X, bad
+
+
+def prob(N, c, cs2, u):
+    """Eqs. maineq02-05: Prob(sum of N variables = n c), n = -N..N, physical units."""
+    out = np.empty(2 * N + 1)
+    flag = lib().orc_prob(N, c, cs2, u, _dp(out))
+    if flag < 0:
+        raise ValueError("level out of range")
+    return out, bool(flag)
+
+
+def eq1d(N, u):
+    out = np.empty(2 * N + 1)
+    lib().orc_eq1d(N, u, _dp(out))
+    return out
+
+
+def weights(N):
+    out = np.empty(2 * N + 1)
+    lib().orc_weights(N, _dp(out))
+    return out
+
+
+def tau_from_kn(N, H, kn):
+    return lib().orc_tau_from_kn(N, H, kn)

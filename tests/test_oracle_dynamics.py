@@ -1,0 +1,232 @@
+"""Pins of the oracle's stream, collide and boundary steps.
+
+Checks against invariants and closed forms: conservation of mass and momentum
+by the BGK collision (Sec. 2: the equilibrium reproduces rho and rho u at every
+level), equilibrium as a fixed point, periodic streaming as an exact shift
+(numpy.roll), mass conservation of the diffuse walls and bounce-back ends,
+the rest state as a fixed point of the wall rule, linear Couette and parabolic
+Poiseuille profiles at small Knudsen number (Secs. 5.3-5.4, viscosity
+nu = theta tau), growth of the wall slip with Kn, the D2Q9 weights of the
+N = 1 tensor product (Sec. 4), and x-uniform flows staying x-uniform.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import oracle as orc
+from paper_1905_04597_gb300 import inputs
+
+
+def _lat2(NX, NY, Lx, Ly, bc=orc.BC_WALLS, tau=0.8, uw_lo=0.0, uw_hi=0.0, g=0.0):
+    return orc.Lattice(2, NX, NY, Lx, Ly, bc, tau, uw_lo, uw_hi, g)
+
+
+def _vel2(NX, NY):
+    nx = np.tile(np.arange(-NX, NX + 1), 2 * NY + 1).astype(float)
+    ny = np.repeat(np.arange(-NY, NY + 1), 2 * NX + 1).astype(float)
+    return nx, ny
+
+
+@pytest.mark.parametrize("N", [1, 2, 4])
+def test_collision_conserves_mass_and_momentum(N):
+    lat = _lat2(N, N, 7, 5, tau=0.63)
+    F = inputs.random_populations(1, lat.Q, 5, 7)
+    X, bad = lat.collide(F)
+    assert bad == 0
+    nx, ny = _vel2(N, N)
+    for w in (np.ones_like(nx), nx, ny):
+        a = np.tensordot(w, F, axes=1)
+        b = np.tensordot(w, X, axes=1)
+        np.testing.assert_allclose(b, a, rtol=0, atol=1e-15)
+
+
+def test_force_injects_exact_momentum():
+    """Sum_i F_i = 0 and sum_i xi_x F_i = g per node (Sec. 5.4 linearised force)."""
+    g = 3.7e-4
+    lat0 = _lat2(3, 3, 6, 4, tau=1.1)
+    latg = _lat2(3, 3, 6, 4, tau=1.1, g=g)
+    F = inputs.random_populations(2, lat0.Q, 4, 6)
+    X0, _ = lat0.collide(F)
+    Xg, _ = latg.collide(F)
+    nx, ny = _vel2(3, 3)
+    np.testing.assert_allclose(np.tensordot(np.ones_like(nx), Xg - X0, axes=1), 0, atol=1e-16)
+    np.testing.assert_allclose(np.tensordot(nx, Xg - X0, axes=1), g, rtol=1e-12)
+    np.testing.assert_allclose(np.tensordot(ny, Xg - X0, axes=1), 0, atol=1e-16)
+
+
+@pytest.mark.parametrize("N", [1, 3])
+def test_equilibrium_is_fixed_point_of_collision(N):
+    rho, ux, uy = inputs.random_macro(3, 8, 6)
+    lat = _lat2(N, N, 8, 6, tau=0.9)
+    Feq = lat.equilibrium(rho, ux, uy)
+    X, _ = lat.collide(Feq)
+    np.testing.assert_allclose(X, Feq, rtol=1e-14, atol=1e-17)
+    M = lat.macro(Feq)
+    np.testing.assert_allclose(M[0], rho, rtol=1e-14)
+    np.testing.assert_allclose(M[1], ux, atol=1e-15)
+    np.testing.assert_allclose(M[2], uy, atol=1e-15)
+    # temperature of the local equilibrium is the lattice temperature N/3
+    np.testing.assert_allclose(M[3], N / 3.0, rtol=1e-13)
+
+
+@pytest.mark.parametrize("N", [1, 2])
+def test_periodic_streaming_is_roll(N):
+    Lx, Ly = 9, 7
+    lat = _lat2(N, N, Lx, Ly, bc=orc.BC_PERIODIC)
+    X = inputs.random_populations(4, lat.Q, Ly, Lx)
+    F = lat.stream(X)
+    nx, ny = _vel2(N, N)
+    for q in range(lat.Q):
+        expect = np.roll(X[q], shift=(int(ny[q]), int(nx[q])), axis=(0, 1))
+        np.testing.assert_array_equal(F[q], expect)
+
+
+@pytest.mark.parametrize("N", [1, 2, 4])
+def test_wall_streaming_conserves_mass(N):
+    Lx, Ly = 6, max(N, 5)
+    lat = _lat2(N, N, Lx, Ly, uw_lo=-0.07, uw_hi=0.04)
+    X = inputs.random_populations(5, lat.Q, Ly, Lx)
+    F = lat.stream(X)
+    assert F.sum() == pytest.approx(X.sum(), rel=1e-14)
+    # per column: absorbed mass booked at column x is re-emitted into column x,
+    # and interior pushes conserve the column-summed totals overall
+    assert (F > 0).all()
+
+
+def test_rest_state_is_fixed_point_of_walls():
+    """The rest equilibrium rho = 1, u = 0 between stationary diffuse walls is steady."""
+    for N in (1, 3):
+        lat = _lat2(N, N, 4, 9, tau=0.7)
+        X = lat.equilibrium(np.ones((9, 4)), np.zeros((9, 4)), np.zeros((9, 4)))
+        Y, bad = lat.run(X, 5)
+        assert bad == 0
+        np.testing.assert_allclose(Y, X, rtol=1e-14)
+
+
+def test_wall_emits_wall_equilibrium_shape():
+    """Populations re-emitted by a wall have the shape E^x(u_w) W^y (diffuse reflection)."""
+    N, Lx, Ly, uw = 2, 3, 6, 0.08
+    lat = _lat2(N, N, Lx, Ly, uw_lo=uw)
+    X = inputs.random_populations(6, lat.Q, Ly, Lx)
+    F = lat.stream(X)
+    Ex = orc.eq1d(N, uw)
+    Wy = orc.weights(N)
+    Q1 = 2 * N + 1
+    for x in range(Lx):
+        ratios = []
+        for ny in range(1, N + 1):
+            for nxi in range(-N, N + 1):
+                q = (ny + N) * Q1 + nxi + N
+                for y in range(ny):
+                    ratios.append(F[q, y, x] / (Ex[nxi + N] * Wy[ny + N]))
+        np.testing.assert_allclose(ratios, ratios[0], rtol=1e-13)
+
+
+def test_bounceback_conserves_mass_1d():
+    N, L = 3, 11
+    lat = orc.Lattice(1, N, 0, L, 1, orc.BC_BOUNCEBACK, tau=0.6)
+    X = np.random.default_rng(7).uniform(0.5, 1.5, size=(2 * N + 1, L))
+    F = lat.stream(X)
+    assert F.sum() == pytest.approx(X.sum(), rel=1e-15)
+    # streaming is a permutation: same multiset of values
+    np.testing.assert_array_equal(np.sort(F.ravel()), np.sort(X.ravel()))
+    rho = inputs.sod_density(40)
+    lat = orc.Lattice(1, 2, 0, 40, 1, orc.BC_BOUNCEBACK, tau=0.55)
+    X0 = lat.equilibrium(rho, np.zeros(40))
+    X1, bad = lat.run(X0, 300)
+    assert bad == 0
+    assert X1.sum() == pytest.approx(X0.sum(), rel=1e-13)
+
+
+def test_d2q9_weights():
+    """Sec. 4: the N = 1 tensor product is D2Q9 with weights 1/36, 1/9, 4/9."""
+    lat = _lat2(1, 1, 1, 1, bc=orc.BC_PERIODIC)
+    W = lat.equilibrium(np.ones((1, 1)), np.zeros((1, 1)), np.zeros((1, 1))).ravel()
+    expect = np.array([1 / 36, 1 / 9, 1 / 36, 1 / 9, 4 / 9, 1 / 9, 1 / 36, 1 / 9, 1 / 36])
+    np.testing.assert_allclose(W, expect, rtol=1e-15)
+
+
+def _steady(lat, X, chunk=500, tol=1e-11, max_steps=40000):
+    prev = lat.observe(X)[1]
+    steps = 0
+    while steps < max_steps:
+        X, bad = lat.run(X, chunk)
+        assert bad == 0
+        steps += chunk
+        cur = lat.observe(X)[1]
+        if np.abs(cur - prev).max() < tol * max(np.abs(cur).max(), 1e-30):
+            return X
+        prev = cur
+    raise AssertionError("no steady state")
+
+
+def test_couette_linear_profile_and_slip():
+    N, Ly, uw = 2, 16, 0.01
+    slips = []
+    for kn in (0.02, 0.2):
+        tau = orc.tau_from_kn(N, Ly, kn)
+        lat = _lat2(N, N, 1, Ly, tau=tau, uw_lo=-uw, uw_hi=uw)
+        X = lat.equilibrium(np.ones((Ly, 1)), np.zeros((Ly, 1)), np.zeros((Ly, 1)))
+        X = _steady(lat, X)
+        u = lat.observe(X)[1][:, 0]
+        # antisymmetry of the Couette solution
+        np.testing.assert_allclose(u, -u[::-1], atol=1e-14)
+        y = np.arange(Ly)
+        if kn == 0.02:
+            # linear outside the Knudsen layers (two nodes at each wall), and
+            # within 1 % of the wall speed everywhere
+            bulk = slice(2, Ly - 2)
+            p = np.polyfit(y[bulk], u[bulk], 1)
+            assert np.abs(np.polyval(p, y[bulk]) - u[bulk]).max() < 1e-3 * uw
+            assert np.abs(np.polyval(p, y) - u).max() < 1e-2 * uw
+        # slip = wall speed minus the extrapolated fluid speed at the wall
+        p = np.polyfit(y[Ly // 4: 3 * Ly // 4], u[Ly // 4: 3 * Ly // 4], 1)
+        slips.append(uw - np.polyval(p, Ly - 0.5))
+    assert 0 < slips[0] < slips[1]
+
+
+def test_poiseuille_parabolic_profile():
+    N, Ly, g = 2, 24, 1e-5
+    theta = N / 3.0
+    tau = 0.75
+    nu = theta * tau
+    lat = _lat2(N, N, 1, Ly, tau=tau, g=g)
+    X = lat.equilibrium(np.ones((Ly, 1)), np.zeros((Ly, 1)), np.zeros((Ly, 1)))
+    X = _steady(lat, X, chunk=1000)
+    u = lat.observe(X)[1][:, 0]
+    np.testing.assert_allclose(u, u[::-1], rtol=1e-12)
+    y = np.arange(Ly) + 0.5 - Ly / 2.0
+    mid = slice(Ly // 4, 3 * Ly // 4)
+    a, b, c = np.polyfit(y[mid], u[mid], 2)
+    # Navier-Stokes: nu u'' = -g  =>  u = -g/(2 nu) y^2 + const
+    assert a == pytest.approx(-g / (2 * nu), rel=2e-2)
+    assert abs(b) < 1e-12
+    # wall slip lifts the centreline above the no-slip value U0 = g H^2 / (8 nu)
+    U0 = g * Ly ** 2 / (8 * nu)
+    assert U0 < u.max() < 1.3 * U0
+
+
+def test_x_uniform_flow_stays_uniform():
+    N, Ly = 2, 10
+    tau = 0.9
+    common = dict(tau=tau, uw_lo=-0.03, uw_hi=0.05, g=2e-5)
+    lat1 = _lat2(N, N, 1, Ly, **common)
+    lat4 = _lat2(N, N, 4, Ly, **common)
+    rho, ux, uy = inputs.random_macro(8, 1, Ly)
+    X1 = lat1.equilibrium(rho, ux, uy)
+    X4 = lat4.equilibrium(np.repeat(rho, 4, 1), np.repeat(ux, 4, 1), np.repeat(uy, 4, 1))
+    X1, _ = lat1.run(X1, 50)
+    X4, _ = lat4.run(X4, 50)
+    for x in range(4):
+        np.testing.assert_array_equal(X4[:, :, x], X1[:, :, 0])
+
+
+def test_mass_conserved_long_run_with_walls():
+    N, Lx, Ly = 3, 8, 12
+    lat = _lat2(N, N, Lx, Ly, tau=0.7, uw_lo=-0.05, uw_hi=0.05)
+    rho, ux, uy = inputs.random_macro(9, Lx, Ly)
+    X0 = lat.equilibrium(rho, ux, uy)
+    X1, bad = lat.run(X0, 200)
+    assert bad == 0
+    assert X1.sum() == pytest.approx(X0.sum(), rel=1e-13)

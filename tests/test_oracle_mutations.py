@@ -1,0 +1,49 @@
+"""Plant plausible mistakes in a copy of the oracle and check the pins catch each.
+
+Every mutation below edits one expression of ``oracle/glbm_oracle.c`` (a sign,
+a dropped term, a wrong index or factor), compiles the copy, and runs the oracle
+pin tests against it in a subprocess; the run must fail.
+"""
+import os
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SRC = os.path.join(ROOT, "oracle", "glbm_oracle.c")
+
+MUTATIONS = {
+    "P+ sign of c*u": ("*Pp = (cs2 + c * u + u * u / N)", "*Pp = (cs2 - c * u + u * u / N)"),
+    "dropped u^2/N": ("*Pm = (cs2 - c * u + u * u / N)", "*Pm = (cs2 - c * u)"),
+    "factorial index": ("orc_factorial(n + m) * orc_factorial(m)",
+                        "orc_factorial(n) * orc_factorial(m)"),
+    "mirror not swapped": ("        Pp = Pm;\n        Pm = t;\n", "        (void)t;\n"),
+    "omega without 1/2": ("double omega = 1.0 / (c->tau + 0.5);", "double omega = 1.0 / c->tau;"),
+    "force sign": ("* nx * c->g / theta_x", "* (-nx) * c->g / theta_x"),
+    "force theta": ("* nx * c->g / theta_x", "* nx * c->g"),
+    "stream x sign": ("int xd = orc_wrap(x + nx, Lx);", "int xd = orc_wrap(x - nx, Lx);"),
+    "wall speeds swapped": ("orc_eq_lattice(NX, c->uw_lo, Elo);", "orc_eq_lattice(NX, c->uw_hi, Elo);"),
+    "emission rows": ("for (int k = 0; k < ny; ++k) {", "for (int k = 0; k < ny - 1; ++k) {"),
+    "bounce-back offset": ("F[(-n + N) * L + (-1 - xd)] = v;", "F[(-n + N) * L + (-xd)] = v;"),
+    "temperature dims": ("out[3 * plane + node] = e2 / (2.0 * rho);",
+                         "out[3 * plane + node] = e2 / rho;"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(MUTATIONS))
+def test_pins_catch_planted_mistake(name, tmp_path):
+    old, new = MUTATIONS[name]
+    src = open(SRC).read()
+    assert src.count(old) >= 1, f"mutation anchor missing: {old!r}"
+    mutated = tmp_path / "mut.c"
+    mutated.write_text(src.replace(old, new, 1))
+    lib = tmp_path / "libmut.so"
+    subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared",
+                           "-o", str(lib), str(mutated), "-lm"])
+    env = dict(os.environ, GLBM_ORACLE_LIB=str(lib))
+    r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q",
+                        os.path.join(ROOT, "tests", "test_oracle_equilibrium.py"),
+                        os.path.join(ROOT, "tests", "test_oracle_dynamics.py")],
+                       cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+    assert r.returncode != 0, f"pins did not catch mutation {name!r}"
