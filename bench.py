@@ -1,0 +1,363 @@
+"""Throughput of the Gaussian lattice Boltzmann hot path on GB300.
+
+Default workload: plane Couette flow (Sec. 5.3) on the D2Q81 tensor-product
+lattice (k = 3 summations, N = 4, 81 velocities), 512 x 256 nodes, walls moving
+at -0.05 / +0.05, the three Knudsen numbers 0.01, 0.1, 1 stepped together as
+three instances of one batched launch, FP32-deviation storage. A step is one
+time step of all three instances (fused pull-stream + wall flux + BGK collide);
+the populations (255 MB over both buffers) exceed the 129 MB L2, so no flush is
+needed between steps. The same step is also timed in FP64 storage.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload couette|poiseuille|sod]
+
+Under torchrun (N > 1) every rank runs its own copy of the workload (the
+instances are independent: weak scaling, no data-path collective); rank 0
+prints one JSON line with the whole-job throughput (max time over ranks).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "population updates/s and HBM GB/s (% peak), FP32 vs FP64 at <=1e-5 moment err"
+UNIT = "pop-updates/s"
+
+
+def workload(name):
+    from paper_1905_04597_gb300 import inputs
+    if name == "couette":
+        c = inputs.COUETTE
+        cfgs = [dict(dims=2, nx=c["nx"], ny=c["ny"], k=c["k"], kn=kn, u_wall_lo=c["u_wall_lo"],
+                     u_wall_hi=c["u_wall_hi"]) for kn in c["kn"]]
+        label = "couette_d2q81_512x256_kn{0.01,0.1,1}"
+    elif name == "poiseuille":
+        c = inputs.POISEUILLE
+        cfgs = [dict(dims=2, nx=c["nx"], ny=c["ny"], k=c["k"], kn=kn, g=c["g"]) for kn in c["kn"]]
+        label = "poiseuille_d2q289_1024x128_kn8"
+    elif name == "sod":
+        c = inputs.SOD
+        cfgs = [dict(dims=1, nx=c["nx"], k=c["k"], kn=c["kn"])]
+        label = "sod_d1q5_1000"
+    else:
+        raise SystemExit(f"unknown workload {name}")
+    return cfgs, label
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            p = json.load(fh)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            time.sleep(0.15)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx = float(parts[1])
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def run_ours(args):
+    import torch
+    world, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    import __graft_entry__
+    if rank == 0:
+        __graft_entry__.build_library()
+    if world > 1:
+        torch.distributed.barrier()
+    from paper_1905_04597_gb300 import glbm
+
+    cfgs, label = workload(args.workload)
+    dims = cfgs[0]["dims"]
+    N = cfgs[0]["k"] + 1
+    Q = (2 * N + 1) ** dims
+    nodes = cfgs[0]["nx"] * (cfgs[0]["ny"] if dims == 2 else 1)
+    n_inst = len(cfgs)
+    pops_per_step = Q * nodes * n_inst
+    stream = torch.cuda.current_stream()
+
+    def timed(prec, steps, warmup):
+        lat = glbm.Lattice([dict(c, prec=prec) for c in cfgs])
+        lat.step(warmup)
+        lat.sync()
+        l0 = lat.kernel_launches
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with ClockSampler(local) as clk:
+            e0.record(stream)
+            lat.step(steps)
+            e1.record(stream)
+            torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        launches = lat.kernel_launches - l0
+        lat.sync()
+        lat.close()
+        if world > 1:
+            t = torch.tensor([ms], device="cuda")
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms, launches, clk.summary()
+
+    steps, warmup = args.steps, args.warmup
+    ms32, launches, clocks = timed(glbm.FP32_DEV, steps, warmup)
+    ms64, _, clocks64 = timed(glbm.FP64, max(steps // 4, 4), warmup)
+    steps64 = max(steps // 4, 4)
+
+    value = pops_per_step * steps * world / (ms32 / 1e3)
+    value64 = pops_per_step * steps64 * world / (ms64 / 1e3)
+    peak, peak_kind = peaks()
+    bytes32 = 2 * 4 * pops_per_step       # algorithmic bytes of one launch (read + write)
+    bytes64 = 2 * 8 * pops_per_step
+    per_launch_ms = ms32 / steps
+    gbs32 = bytes32 / (per_launch_ms / 1e3) / 1e9
+    gbs64 = bytes64 / (ms64 / steps64 / 1e3) / 1e9
+
+    # end to end through the public API with pinned host buffers: upload the initial
+    # fields, run a chunk of steps, read every moment back
+    e2e = None
+    if dims == 2:
+        lb_per_call = 100
+        lat = glbm.Lattice([dict(c, prec=glbm.FP32_DEV) for c in cfgs])
+        ny, nx = cfgs[0]["ny"], cfgs[0]["nx"]
+        pin = lambda a: torch.from_numpy(a).pin_memory()  # noqa: E731
+        rho = pin(np.ones((ny, nx)))
+        ux = pin(np.zeros((ny, nx)))
+        uy = pin(np.zeros((ny, nx)))
+        outs = [torch.empty((7, ny, nx), dtype=torch.float64).pin_memory() for _ in cfgs]
+        reps = max(2, min(20, steps // lb_per_call))
+
+        def one():
+            for i in range(n_inst):
+                lat.set_equilibrium(i, rho, ux, uy)
+            lat.step(lb_per_call)
+            for i in range(n_inst):
+                lat.moments(i, out=outs[i])
+
+        one()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            one()
+        torch.cuda.synchronize()
+        dt = (time.perf_counter() - t0) / reps
+        lat.close()
+        e2e = {"value": pops_per_step * lb_per_call * world / dt, "unit": UNIT,
+               "h2d_bytes_per_step": 3 * 8 * nodes * n_inst,
+               "d2h_bytes_per_step": 7 * 8 * nodes * n_inst,
+               "lb_steps_per_step": lb_per_call,
+               "call": "glbm_set_equilibrium(host) x3 + glbm_step(100) + glbm_moments(host) x3"}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(args.workload, budget_s=args.cpu_seconds)
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": steps,
+        "warmup": warmup, "ms_per_step": ms32 / steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": label, "lattice": f"D{dims}Q{Q}", "k": N - 1,
+                   "nodes": nodes, "instances": n_inst, "storage": "fp32 deviations",
+                   "l2": f"populations {2 * bytes32 / 2 / 1e6:.0f} MB per buffer set x2 > 129 MB L2; no flush",
+                   "parallelism": f"instances batched per launch; {world} rank(s), independent copies"},
+        "mlups": nodes * n_inst * steps * world / (ms32 / 1e3) / 1e6,
+        "hbm_gbs_algorithmic": gbs32,
+        "fp64": {"value": value64, "unit": UNIT, "ms_per_step": ms64 / steps64, "steps": steps64,
+                 "hbm_gbs_algorithmic": gbs64, "frac_of_hbm": gbs64 / peak,
+                 "clocks": clocks64},
+        "roofline": {"bound": "hbm", "achieved": gbs32, "peak": peak, "unit": "GB/s",
+                     "frac": gbs32 / peak, "traffic": None,
+                     "kernel": "k_step2d<4,float,1,4>",
+                     "bytes_per_launch": bytes32, "peak_source": peak_kind},
+        "gpu_launches": launches,
+        "clocks": clocks,
+        "e2e": e2e,
+        "cpu_baseline": cpu,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def cpu_baseline(name, budget_s=15.0, steps=None):
+    """The FP64 oracle, as it stands, on this host's cores (single thread) over a
+    bounded sample of the workload: the full lattice of one instance for as many
+    steps as fit the budget (at least one)."""
+    from oracle import oracle as orc
+    cfgs, label = workload(name)
+    c = cfgs[0]
+    N = c["k"] + 1
+    dims = c["dims"]
+    if dims == 2:
+        o = orc.Lattice(2, N, N, c["nx"], c["ny"], orc.BC_WALLS if name != "periodic" else 2,
+                        orc.tau_from_kn(N, c["ny"], c["kn"]), c.get("u_wall_lo", 0.0),
+                        c.get("u_wall_hi", 0.0), c.get("g", 0.0))
+        X = o.equilibrium(np.ones((c["ny"], c["nx"])), np.zeros((c["ny"], c["nx"])),
+                          np.zeros((c["ny"], c["nx"])))
+        pops = (2 * N + 1) ** 2 * c["nx"] * c["ny"]
+    else:
+        o = orc.Lattice(1, N, 0, c["nx"], 1, orc.BC_BOUNCEBACK, orc.tau_from_kn(N, c["nx"], c["kn"]))
+        X = o.equilibrium(np.ones(c["nx"]), np.zeros(c["nx"]))
+        pops = (2 * N + 1) * c["nx"]
+    t0 = time.perf_counter()
+    X, _ = o.run(X, 1)
+    one = time.perf_counter() - t0
+    n = steps or max(1, int(budget_s / max(one, 1e-6)) - 1)
+    t0 = time.perf_counter()
+    X, _ = o.run(X, n)
+    dt = time.perf_counter() - t0
+    return {"value": pops * n / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{label}: one instance (Kn {c['kn']}), full lattice, {n} steps, FP64, "
+                      f"single thread, {dt:.1f} s"}
+
+
+def run_reference(args):
+    """The oracle timed as the reference arm: each step one oracle time step of a
+    bounded slab of the workload (a column strip of the lattice)."""
+    world, rank, _ = dist_setup()
+    if rank != 0:
+        return
+    from oracle import oracle as orc
+    orc.build()
+    cfgs, label = workload(args.workload)
+    c = cfgs[0]
+    N = c["k"] + 1
+    dims = c["dims"]
+    budget = 120.0
+    total_steps = args.steps + args.warmup
+    if dims == 2:
+        ny = c["ny"]
+        mk = lambda nx: orc.Lattice(2, N, N, nx, ny, orc.BC_WALLS,  # noqa: E731
+                                    orc.tau_from_kn(N, ny, c["kn"]), c.get("u_wall_lo", 0.0),
+                                    c.get("u_wall_hi", 0.0), c.get("g", 0.0))
+        o = mk(1)
+        X = o.equilibrium(np.ones((ny, 1)), np.zeros((ny, 1)), np.zeros((ny, 1)))
+        t0 = time.perf_counter()
+        o.run(X, 3)
+        per_col = (time.perf_counter() - t0) / 3
+        cols = int(max(1, min(c["nx"], budget / total_steps / max(per_col, 1e-9))))
+        o = mk(cols)
+        X = o.equilibrium(np.ones((ny, cols)), np.zeros((ny, cols)), np.zeros((ny, cols)))
+        pops = (2 * N + 1) ** 2 * ny * cols
+        sample = f"{label}: strip of {cols} of {c['nx']} columns x {ny} rows, one instance, FP64"
+    else:
+        o = orc.Lattice(1, N, 0, c["nx"], 1, orc.BC_BOUNCEBACK, orc.tau_from_kn(N, c["nx"], c["kn"]))
+        X = o.equilibrium(np.ones(c["nx"]), np.zeros(c["nx"]))
+        pops = (2 * N + 1) * c["nx"]
+        sample = f"{label}: full lattice, FP64"
+    X, _ = o.run(X, args.warmup)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        X, _ = o.run(X, 1)
+    dt = time.perf_counter() - t0
+    value = pops * args.steps / dt
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": label, "reference": "FP64 CPU oracle (oracle/glbm_oracle.c)"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20000)
+    ap.add_argument("--warmup", type=int, default=200)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="couette", choices=["couette", "poiseuille", "sod"])
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        raise SystemExit("--warmup must be >= 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

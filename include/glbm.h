@@ -1,0 +1,186 @@
+/*
+ * glbm.h -- C ABI of libglbm, the GB300 (sm_103a) hot path of the Gaussian
+ * lattice Boltzmann method (O. Ilyin, arXiv:1905.04597).
+ *
+ * The method (Sec. 2, Eq. maineq01): populations f_n, one per integer
+ * velocity n = -N..N of level N (k = N-1 summations of D1Q3), follow
+ *   f_n(t+1, x+n) - f_n(t, x) = omega (f^eq_{n;N} - f_n)(t, x),
+ *   omega = 1 / (tau + 1/2),
+ * with the summed ("Gaussian") equilibrium of Eqs. maineq02-05; 2D lattices
+ * are tensor products of two 1D levels (Sec. 4). Everything here is in
+ * lattice units: node spacing 1, time step 1, lattice temperature N/3.
+ *
+ * Time convention. A context holds, per instance, the post-collision
+ * populations X_t. glbm_step advances X_{t+1} = C(S(X_t)) (S = streaming
+ * with the boundary rule, C = BGK collision plus body force). The
+ * macroscopic fields "at time t" are the moments of S(X_t).
+ *
+ * Population layout exchanged through this ABI: FP64, logical order
+ * f[q][y][x] with x fastest, q = (ny+N)*(2N+1) + (nx+N) in 2D and q = n+N in
+ * 1D. Internally the library stores FP64 or FP32 deviations from the rest
+ * weights in pitched planes; conversion happens on the device.
+ *
+ * Errors. Every call returns a glbm_status; on failure nothing changes except
+ * where a call says otherwise, and glbm_last_error() gives a message (per
+ * thread). Device pointers and streams are CUDA runtime objects of the
+ * current device. All calls are asynchronous on the context's stream unless
+ * stated otherwise.
+ */
+#ifndef GLBM_H
+#define GLBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct glbm_ctx glbm_ctx; /* opaque, owned by the library */
+
+typedef enum {
+    GLBM_OK = 0,
+    GLBM_E_INVAL = -1,       /* bad argument or configuration */
+    GLBM_E_NOMEM = -2,       /* device or host allocation failed */
+    GLBM_E_CUDA = -3,        /* a CUDA runtime call failed */
+    GLBM_E_UNSTABLE = -4,    /* a node left the positivity domain (Sec. 3) or rho <= 0 */
+    GLBM_E_TIMEOUT = -5,     /* a bounded device wait ran out */
+    GLBM_E_IO = -6,          /* checkpoint file error */
+    GLBM_E_UNSUPPORTED = -7  /* valid request not compiled into this build */
+} glbm_status;
+
+typedef enum {
+    GLBM_BC_WALLS = 0,       /* 2D: periodic in x, diffuse walls at y = -1/2 and y = ny-1/2 */
+    GLBM_BC_BOUNCEBACK = 1,  /* 1D: halfway bounce-back at x = -1/2 and x = nx-1/2 */
+    GLBM_BC_PERIODIC = 2     /* periodic along every axis */
+} glbm_bc;
+
+typedef enum {
+    GLBM_FP64 = 0,           /* populations stored and updated in FP64 */
+    GLBM_FP32_DEV = 1        /* FP32 deviations f - W from the rest weights, compensated sums */
+} glbm_prec;
+
+/*
+ * One lattice instance.
+ *   dims      1 or 2.
+ *   nx, ny    nodes (ny ignored when dims == 1). With walls ny >= k+1; with
+ *             bounce-back nx >= k+1.
+ *   k         summations of D1Q3 per axis (level N = k+1, 2N+1 velocities per
+ *             axis, Sec. 2); 0 <= k <= 7. Both axes use the same k.
+ *   tau       relaxation time (> 0), used when kn <= 0.
+ *   kn        Knudsen number of Eq. (kn), Sec. 5.2: when > 0 it sets
+ *             tau = kn * H / sqrt(2 theta), theta = N/3, H = ny (2D) or nx (1D).
+ *   bc, prec  glbm_bc, glbm_prec.
+ *   u_wall_lo, u_wall_hi  x-velocities of the walls (GLBM_BC_WALLS).
+ *   g         body force along x (2D), added after relaxation as
+ *             F_i = W_i xi_x g / theta (the linearised force of Sec. 5.4).
+ */
+typedef struct {
+    int dims;
+    int nx, ny;
+    int k;
+    double tau;
+    double kn;
+    int bc;
+    int prec;
+    double u_wall_lo, u_wall_hi;
+    double g;
+} glbm_config;
+
+/*
+ * Create a context of n instances. When every instance shares dims, nx, ny,
+ * k, bc and prec the batch is stepped by one launch with the instance as the
+ * grid's third dimension; otherwise GLBM_E_UNSUPPORTED (heterogeneous
+ * batches go through glbm_batch_create). `stream` is a cudaStream_t (NULL =
+ * legacy default stream) on which all work of the context is ordered. Every
+ * instance starts at rest (rho = 1, u = 0, X = W). The library allocates
+ * its device memory here with cudaMalloc (or the allocator installed by
+ * glbm_set_allocator) and frees it in glbm_destroy.
+ */
+glbm_status glbm_create(const glbm_config *cfgs, int n, void *stream, glbm_ctx **out);
+
+/* Heterogeneous batch: instances may differ in k, ny, nx, tau, walls and
+ * force (2D, GLBM_BC_WALLS or GLBM_BC_PERIODIC, one precision). Stepped by a
+ * persistent kernel over a work list of (instance, tile). */
+glbm_status glbm_batch_create(const glbm_config *cfgs, int n, void *stream, glbm_ctx **out);
+
+void glbm_destroy(glbm_ctx *ctx);
+
+/* Install device allocation callbacks used by later glbm_create calls
+ * (NULL, NULL restores cudaMalloc/cudaFree). alloc(bytes, stream, user)
+ * returns a device pointer or NULL; release(ptr, stream, user). */
+typedef void *(*glbm_alloc_fn)(size_t bytes, void *stream, void *user);
+typedef void (*glbm_free_fn)(void *ptr, void *stream, void *user);
+glbm_status glbm_set_allocator(glbm_alloc_fn alloc, glbm_free_fn release, void *user);
+
+/* Set instance `inst` to the local equilibrium X = rho E^x(u_x) E^y(u_y)
+ * (Eq. maineq02 with the product form of Sec. 4) of the given fields, each
+ * ny*nx FP64 values (uy ignored in 1D), on the device when on_device != 0,
+ * else in host memory (copied in this call). Resets the step counter. */
+glbm_status glbm_set_equilibrium(glbm_ctx *ctx, int inst, const double *rho, const double *ux,
+                                 const double *uy, int on_device);
+
+/* Set / read the populations X of instance `inst` in the FP64 logical layout
+ * described above (Q*ny*nx values). */
+glbm_status glbm_set_populations(glbm_ctx *ctx, int inst, const double *f, int on_device);
+glbm_status glbm_get_populations(glbm_ctx *ctx, int inst, double *f, int on_device);
+
+/* Advance every instance by n >= 0 steps (Eq. maineq01 with the boundary
+ * rule), asynchronously. Repeated chunks are replayed from a CUDA graph.
+ * Returns GLBM_E_UNSTABLE when an earlier, already-finished step flagged a
+ * node outside the positivity domain (the flag is read without waiting). */
+glbm_status glbm_step(glbm_ctx *ctx, int64_t n);
+
+/* Wait for the context's stream; GLBM_E_UNSTABLE if any step flagged a node. */
+glbm_status glbm_sync(glbm_ctx *ctx);
+
+/* Macroscopic fields of instance `inst` at the current time (moments of
+ * S(X), FP64, lattice units), fields packed in this order for the bits set
+ * in `mask`, each ny*nx values [y][x]:
+ *   bit 0 rho, bit 1 u_x, bit 2 u_y, bit 3 T = sum |xi-u|^2 f / (D rho),
+ *   bit 4 q_x, bit 5 q_y (q = (1/2) sum (xi-u) |xi-u|^2 f),
+ *   bit 6 sigma_xy = sum (xi_x-u_x)(xi_y-u_y) f.
+ * In 1D only bits 0, 1, 3, 4 apply. `out_len` is the capacity in doubles.
+ * Synchronises the stream when out is host memory. */
+#define GLBM_M_RHO 0x01u
+#define GLBM_M_UX 0x02u
+#define GLBM_M_UY 0x04u
+#define GLBM_M_T 0x08u
+#define GLBM_M_QX 0x10u
+#define GLBM_M_QY 0x20u
+#define GLBM_M_SXY 0x40u
+#define GLBM_M_ALL 0x7Fu
+glbm_status glbm_moments(glbm_ctx *ctx, int inst, unsigned mask, double *out, size_t out_len,
+                         int out_on_device);
+
+/* Global FP64 sums at the current time: total mass, x- and y-momentum of
+ * instance `inst` (fixed-order block reduction, deterministic). Synchronises. */
+glbm_status glbm_conservation(glbm_ctx *ctx, int inst, double *mass, double *mom_x,
+                              double *mom_y);
+
+/* Checkpoint of every instance's state (header, raw device image, CRC-32).
+ * glbm_load requires a context created with the same configuration. */
+glbm_status glbm_save(glbm_ctx *ctx, const char *path);
+glbm_status glbm_load(glbm_ctx *ctx, const char *path);
+
+/* Number of steps taken since creation or the last state reset. */
+int64_t glbm_time(const glbm_ctx *ctx);
+
+/* Number of kernels the library has launched (graph nodes counted once per
+ * replay). */
+int64_t glbm_kernel_launches(const glbm_ctx *ctx);
+
+/* Relaxation time actually used by instance `inst` (after the Kn mapping). */
+double glbm_tau(const glbm_ctx *ctx, int inst);
+
+/* Coefficients C[n][j] of the equilibrium polynomial E_n(u) = sum_j C[n][j] u^j
+ * of level N = k+1 (lattice units), row-major (2N+1) x (2N+1), n = -N..N. */
+glbm_status glbm_eq_table(int k, double *out, size_t out_len);
+
+const char *glbm_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GLBM_H */

@@ -1,0 +1,733 @@
+// C ABI of libglbm (include/glbm.h): contexts, device buffers, the step loop
+// with CUDA-graph replay, moments, conservation sums and checkpoints.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <new>
+#include <vector>
+
+#include "../../include/glbm.h"
+#include "glbm_internal.h"
+
+// ---------------------------------------------------------------------------
+// errors and allocation
+// ---------------------------------------------------------------------------
+static thread_local char g_err[512] = "";
+
+static glbm_status fail(glbm_status st, const char *fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+    return st;
+}
+
+#define CUDA_TRY(call)                                                                    \
+    do {                                                                                  \
+        cudaError_t e_ = (call);                                                          \
+        if (e_ != cudaSuccess)                                                            \
+            return fail(GLBM_E_CUDA, "%s failed: %s", #call, cudaGetErrorString(e_));    \
+    } while (0)
+
+static glbm_alloc_fn g_alloc = nullptr;
+static glbm_free_fn g_free = nullptr;
+static void *g_alloc_user = nullptr;
+
+extern "C" glbm_status glbm_set_allocator(glbm_alloc_fn alloc, glbm_free_fn release, void *user)
+{
+    if ((alloc == nullptr) != (release == nullptr))
+        return fail(GLBM_E_INVAL, "allocator and release must both be set or both be NULL");
+    g_alloc = alloc;
+    g_free = release;
+    g_alloc_user = user;
+    return GLBM_OK;
+}
+
+extern "C" const char *glbm_last_error(void) { return g_err; }
+
+struct DevAlloc {
+    glbm_alloc_fn alloc;
+    glbm_free_fn release;
+    void *user;
+};
+
+static void *dev_alloc(const DevAlloc &A, size_t bytes, cudaStream_t s)
+{
+    if (bytes == 0) bytes = 256;
+    if (A.alloc) return A.alloc(bytes, (void *)s, A.user);
+    void *p = nullptr;
+    if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return p;
+}
+
+static void dev_free(const DevAlloc &A, void *p, cudaStream_t s)
+{
+    if (!p) return;
+    if (A.release)
+        A.release(p, (void *)s, A.user);
+    else
+        cudaFree(p);
+}
+
+// ---------------------------------------------------------------------------
+// context
+// ---------------------------------------------------------------------------
+struct glbm_ctx {
+    int n_inst = 0;
+    int dims = 2, N = 1, Lx = 1, Ly = 1, pitch = 32, bc = 0, prec = 0;
+    int k = 0;
+    size_t elem = 8;
+    long long plane = 0, inst_stride = 0;
+    AxisTable tab;
+    std::vector<InstParams> h_ip;
+    std::vector<double> tau;
+    DevAlloc A{};
+    cudaStream_t stream = nullptr;
+    cudaStream_t cap = nullptr;  // private stream used only for graph capture
+    void *buf[2] = {nullptr, nullptr};
+    int cur = 0;  // buffer holding X_t
+    InstParams *d_ip = nullptr;
+    unsigned *d_status = nullptr;  // [0] status flags, [1] launch counter, [2] CTAs done
+    unsigned *h_status = nullptr;  // pinned copy, refreshed after every glbm_step
+    double *d_mom = nullptr;       // 7 fields of one instance
+    double *d_part = nullptr;      // block partials of the conservation sums
+    double *d_sums = nullptr;      // 3 sums
+    double *d_stage = nullptr;     // staging of host inputs
+    size_t stage_len = 0;
+    int sum_blocks = 1;
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};  // chunk graphs by starting buffer
+    int64_t t = 0;
+    int64_t launches = 0;
+    unsigned clock_word = 0;  // host copy uploaded by set_clock (lives as long as the context)
+};
+
+static const int kGraphChunk = 64;  // steps per captured graph (even: keeps buffer parity)
+
+static size_t bytes_state(const glbm_ctx *c) { return (size_t)c->n_inst * c->inst_stride * c->elem; }
+
+static void fill_inst(glbm_ctx *c, const glbm_config &cfg, InstParams &ip, double tau)
+{
+    memset(&ip, 0, sizeof(ip));
+    const int N = c->N;
+    const double theta = N / 3.0;
+    ip.omega = 1.0 / (tau + 0.5);
+    ip.g_theta = c->dims == 2 ? cfg.g / theta : 0.0;
+    double den = 0.0;
+    for (int n = 1; n <= N; ++n) den += n * c->tab.W[n + N];
+    ip.inv_den = 1.0 / den;
+    // E^x_n(u_w) from the coefficient table (FP64 Horner)
+    double full[GLBM_MAXQ1 * GLBM_MAXQ1];
+    AxisTable tmp;
+    glbm_build_axis_table(N, &tmp, full);
+    const int Q1 = 2 * N + 1;
+    for (int n = 0; n < Q1; ++n) {
+        double elo = 0.0, ehi = 0.0;
+        for (int j = Q1 - 1; j >= 0; --j) {
+            elo = elo * cfg.u_wall_lo + full[n * Q1 + j];
+            ehi = ehi * cfg.u_wall_hi + full[n * Q1 + j];
+        }
+        ip.ew_lo[n] = elo;
+        ip.ew_hi[n] = ehi;
+        // deviation computed without the constant term
+        double dlo = 0.0, dhi = 0.0;
+        for (int j = Q1 - 1; j >= 1; --j) {
+            dlo = dlo * cfg.u_wall_lo + full[n * Q1 + j];
+            dhi = dhi * cfg.u_wall_hi + full[n * Q1 + j];
+        }
+        ip.dw_lo_f[n] = (float)(dlo * cfg.u_wall_lo);
+        ip.dw_hi_f[n] = (float)(dhi * cfg.u_wall_hi);
+    }
+    ip.g_theta_om = ip.g_theta / ip.omega;
+    ip.omega_f = (float)ip.omega;
+    ip.g_theta_f = (float)ip.g_theta;
+    ip.g_theta_om_f = (float)ip.g_theta_om;
+    ip.inv_den_f = (float)ip.inv_den;
+    ip.N = N;
+    ip.Lx = c->Lx;
+    ip.Ly = c->Ly;
+    ip.pitch = c->pitch;
+    ip.bc = c->bc;
+    ip.plane = c->plane;
+}
+
+static glbm_status validate(const glbm_config &c)
+{
+    if (c.dims != 1 && c.dims != 2) return fail(GLBM_E_INVAL, "dims must be 1 or 2 (got %d)", c.dims);
+    if (c.k < 0 || c.k > GLBM_MAXN - 1)
+        return fail(GLBM_E_UNSUPPORTED, "k must be in 0..%d (got %d)", GLBM_MAXN - 1, c.k);
+    const int N = c.k + 1;
+    if (c.nx < 1 || (c.dims == 2 && c.ny < 1)) return fail(GLBM_E_INVAL, "nx, ny must be >= 1");
+    if (c.prec != GLBM_FP64 && c.prec != GLBM_FP32_DEV) return fail(GLBM_E_INVAL, "bad precision %d", c.prec);
+    if (c.dims == 1) {
+        if (c.bc != GLBM_BC_BOUNCEBACK && c.bc != GLBM_BC_PERIODIC)
+            return fail(GLBM_E_INVAL, "1D lattices take GLBM_BC_BOUNCEBACK or GLBM_BC_PERIODIC");
+        if (c.bc == GLBM_BC_BOUNCEBACK && c.nx < N)
+            return fail(GLBM_E_INVAL, "bounce-back needs nx >= k+1");
+    } else {
+        if (c.bc != GLBM_BC_WALLS && c.bc != GLBM_BC_PERIODIC)
+            return fail(GLBM_E_INVAL, "2D lattices take GLBM_BC_WALLS or GLBM_BC_PERIODIC");
+        if (c.bc == GLBM_BC_WALLS && c.ny < N) return fail(GLBM_E_INVAL, "walls need ny >= k+1");
+    }
+    if (!(c.kn > 0.0) && !(c.tau > 0.0)) return fail(GLBM_E_INVAL, "tau must be > 0 (or kn > 0)");
+    const double umax = sqrt(2.0 / 3.0) * N;
+    if (!(fabs(c.u_wall_lo) < umax) || !(fabs(c.u_wall_hi) < umax) || !isfinite(c.g))
+        return fail(GLBM_E_INVAL, "wall speed outside the positivity domain or bad force");
+    return GLBM_OK;
+}
+
+static double tau_of(const glbm_config &c)
+{
+    if (c.kn > 0.0) {
+        const int N = c.k + 1;
+        const double theta = N / 3.0;
+        const double H = c.dims == 2 ? c.ny : c.nx;
+        return c.kn * H / sqrt(2.0 * theta);  // Eq. (kn), nu = theta tau
+    }
+    return c.tau;
+}
+
+static void destroy_resources(glbm_ctx *c)
+{
+    for (int i = 0; i < 2; ++i) {
+        if (c->graph[i]) cudaGraphExecDestroy(c->graph[i]);
+        c->graph[i] = nullptr;
+    }
+    if (c->stream || c->cap) cudaStreamSynchronize(c->stream);
+    dev_free(c->A, c->buf[0], c->stream);
+    dev_free(c->A, c->buf[1], c->stream);
+    dev_free(c->A, c->d_ip, c->stream);
+    dev_free(c->A, c->d_status, c->stream);
+    dev_free(c->A, c->d_mom, c->stream);
+    dev_free(c->A, c->d_part, c->stream);
+    dev_free(c->A, c->d_sums, c->stream);
+    dev_free(c->A, c->d_stage, c->stream);
+    if (c->h_status) cudaFreeHost(c->h_status);
+    if (c->cap) cudaStreamDestroy(c->cap);
+}
+
+static AuxArgs aux_args(const glbm_ctx *c)
+{
+    AuxArgs a;
+    memset(&a, 0, sizeof(a));
+    a.tab = c->tab;
+    a.ip = c->d_ip;
+    a.dims = c->dims;
+    a.prec = c->prec;
+    a.Lx = c->Lx;
+    a.Ly = c->Ly;
+    a.pitch = c->pitch;
+    a.bc = c->bc;
+    a.N = c->N;
+    a.plane = c->plane;
+    a.inst_stride = c->inst_stride;
+    return a;
+}
+
+// The launch counter that seeds the dithered FP32 stores follows the step
+// clock, so a run resumed from a checkpoint repeats the same dither sequence.
+static cudaError_t set_clock(glbm_ctx *c, int64_t t)
+{
+    c->t = t;
+    c->clock_word = (unsigned)t;
+    return cudaMemcpyAsync(c->d_status + 1, &c->clock_word, sizeof(unsigned), cudaMemcpyHostToDevice,
+                           c->stream);
+}
+
+static glbm_status ensure_stage(glbm_ctx *c, size_t n)
+{
+    if (c->stage_len >= n) return GLBM_OK;
+    dev_free(c->A, c->d_stage, c->stream);
+    c->d_stage = (double *)dev_alloc(c->A, n * sizeof(double), c->stream);
+    c->stage_len = c->d_stage ? n : 0;
+    if (!c->d_stage) return fail(GLBM_E_NOMEM, "staging allocation of %zu doubles failed", n);
+    return GLBM_OK;
+}
+
+extern "C" glbm_status glbm_create(const glbm_config *cfgs, int n, void *stream, glbm_ctx **out)
+{
+    if (!cfgs || n < 1 || !out) return fail(GLBM_E_INVAL, "null argument or n < 1");
+    *out = nullptr;
+    for (int i = 0; i < n; ++i) {
+        glbm_status st = validate(cfgs[i]);
+        if (st != GLBM_OK) return st;
+        const glbm_config &a = cfgs[0], &b = cfgs[i];
+        if (a.dims != b.dims || a.nx != b.nx || (a.dims == 2 && a.ny != b.ny) || a.k != b.k ||
+            a.bc != b.bc || a.prec != b.prec)
+            return fail(GLBM_E_UNSUPPORTED,
+                        "instances differ in geometry; use glbm_batch_create for mixed batches");
+    }
+    glbm_ctx *c = new (std::nothrow) glbm_ctx();
+    if (!c) return fail(GLBM_E_NOMEM, "host allocation failed");
+    const glbm_config &c0 = cfgs[0];
+    c->n_inst = n;
+    c->dims = c0.dims;
+    c->k = c0.k;
+    c->N = c0.k + 1;
+    c->Lx = c0.nx;
+    c->Ly = c0.dims == 2 ? c0.ny : 1;
+    c->bc = c0.bc;
+    c->prec = c0.prec;
+    c->elem = c0.prec == GLBM_FP64 ? 8 : 4;
+    c->pitch = ((c->Lx + 31) / 32) * 32;
+    const int Q1 = 2 * c->N + 1;
+    const int Q = c->dims == 2 ? Q1 * Q1 : Q1;
+    c->plane = (long long)c->Ly * c->pitch;
+    c->inst_stride = (long long)Q * c->plane;
+    if (c->inst_stride >= (1LL << 31)) {
+        delete c;
+        return fail(GLBM_E_UNSUPPORTED, "one instance holds %lld populations; at most 2^31 - 1",
+                    (long long)Q * c0.nx * (c0.dims == 2 ? c0.ny : 1));
+    }
+    c->A = DevAlloc{g_alloc, g_free, g_alloc_user};
+    c->stream = (cudaStream_t)stream;
+    glbm_build_axis_table(c->N, &c->tab, nullptr);
+    c->h_ip.resize(n);
+    c->tau.resize(n);
+    for (int i = 0; i < n; ++i) {
+        c->tau[i] = tau_of(cfgs[i]);
+        fill_inst(c, cfgs[i], c->h_ip[i], c->tau[i]);
+    }
+
+    const size_t nodes = (size_t)c->Lx * c->Ly;
+    glbm_status st = GLBM_OK;
+    cudaError_t e = cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking);
+    if (e != cudaSuccess) st = fail(GLBM_E_CUDA, "stream creation failed: %s", cudaGetErrorString(e));
+    if (st == GLBM_OK && cudaHostAlloc((void **)&c->h_status, sizeof(unsigned), cudaHostAllocDefault) != cudaSuccess)
+        st = fail(GLBM_E_NOMEM, "pinned status allocation failed");
+    if (st == GLBM_OK) {
+        c->buf[0] = dev_alloc(c->A, bytes_state(c), c->stream);
+        c->buf[1] = dev_alloc(c->A, bytes_state(c), c->stream);
+        c->d_ip = (InstParams *)dev_alloc(c->A, sizeof(InstParams) * n, c->stream);
+        c->d_status = (unsigned *)dev_alloc(c->A, 4 * sizeof(unsigned), c->stream);
+        c->d_mom = (double *)dev_alloc(c->A, 7 * nodes * sizeof(double), c->stream);
+        c->sum_blocks = glbm_field_sum_blocks((long long)nodes);
+        c->d_part = (double *)dev_alloc(c->A, 3 * c->sum_blocks * sizeof(double), c->stream);
+        c->d_sums = (double *)dev_alloc(c->A, 3 * sizeof(double), c->stream);
+        if (!c->buf[0] || !c->buf[1] || !c->d_ip || !c->d_status || !c->d_mom || !c->d_part ||
+            !c->d_sums)
+            st = fail(GLBM_E_NOMEM, "device allocation of %.1f MB failed",
+                      2.0 * bytes_state(c) / 1e6);
+    }
+    if (st == GLBM_OK) {
+        *c->h_status = 0;
+        e = cudaMemcpyAsync(c->d_ip, c->h_ip.data(), sizeof(InstParams) * n,
+                            cudaMemcpyHostToDevice, c->stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(c->d_status, 0, 4 * sizeof(unsigned), c->stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(c->buf[0], 0, bytes_state(c), c->stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(c->buf[1], 0, bytes_state(c), c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        if (e != cudaSuccess) st = fail(GLBM_E_CUDA, "initialisation failed: %s", cudaGetErrorString(e));
+    }
+    if (st == GLBM_OK) {
+        // rest state X = W
+        std::vector<double> one(nodes, 1.0), zero(nodes, 0.0);
+        st = ensure_stage(c, 3 * nodes);
+        if (st == GLBM_OK) {
+            e = cudaMemcpy(c->d_stage, one.data(), nodes * 8, cudaMemcpyHostToDevice);
+            if (e == cudaSuccess) e = cudaMemcpy(c->d_stage + nodes, zero.data(), nodes * 8, cudaMemcpyHostToDevice);
+            if (e == cudaSuccess) e = cudaMemcpy(c->d_stage + 2 * nodes, zero.data(), nodes * 8, cudaMemcpyHostToDevice);
+            AuxArgs a = aux_args(c);
+            for (int i = 0; i < n && e == cudaSuccess; ++i)
+                e = glbm_launch_set_equilibrium(a, c->buf[0], i, c->d_stage, c->d_stage + nodes,
+                                                c->d_stage + 2 * nodes, c->stream);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+            if (e != cudaSuccess) st = fail(GLBM_E_CUDA, "rest-state launch failed: %s", cudaGetErrorString(e));
+            c->launches += n;
+        }
+    }
+    if (st != GLBM_OK) {
+        destroy_resources(c);
+        delete c;
+        return st;
+    }
+    *out = c;
+    return GLBM_OK;
+}
+
+extern "C" void glbm_destroy(glbm_ctx *c)
+{
+    if (!c) return;
+    destroy_resources(c);
+    delete c;
+}
+
+extern "C" int64_t glbm_time(const glbm_ctx *c) { return c ? c->t : -1; }
+extern "C" int64_t glbm_kernel_launches(const glbm_ctx *c) { return c ? c->launches : -1; }
+extern "C" double glbm_tau(const glbm_ctx *c, int inst)
+{
+    if (!c || inst < 0 || inst >= c->n_inst) return -1.0;
+    return c->tau[inst];
+}
+
+extern "C" glbm_status glbm_eq_table(int k, double *out, size_t out_len)
+{
+    if (k < 0 || k > GLBM_MAXN - 1 || !out) return fail(GLBM_E_INVAL, "bad k or null output");
+    const int N = k + 1, Q1 = 2 * N + 1;
+    if (out_len < (size_t)Q1 * Q1) return fail(GLBM_E_INVAL, "output needs %d doubles", Q1 * Q1);
+    AxisTable t;
+    glbm_build_axis_table(N, &t, out);
+    return GLBM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// state import / export
+// ---------------------------------------------------------------------------
+static glbm_status check_inst(const glbm_ctx *c, int inst)
+{
+    if (!c) return fail(GLBM_E_INVAL, "null context");
+    if (inst < 0 || inst >= c->n_inst) return fail(GLBM_E_INVAL, "instance %d out of range", inst);
+    return GLBM_OK;
+}
+
+static int n_q(const glbm_ctx *c)
+{
+    const int Q1 = 2 * c->N + 1;
+    return c->dims == 2 ? Q1 * Q1 : Q1;
+}
+
+extern "C" glbm_status glbm_set_equilibrium(glbm_ctx *c, int inst, const double *rho,
+                                            const double *ux, const double *uy, int on_device)
+{
+    glbm_status st = check_inst(c, inst);
+    if (st != GLBM_OK) return st;
+    if (!rho || !ux || (c->dims == 2 && !uy)) return fail(GLBM_E_INVAL, "null field");
+    const size_t nodes = (size_t)c->Lx * c->Ly;
+    const double *dr = rho, *du = ux, *dv = uy;
+    if (!on_device) {
+        st = ensure_stage(c, 3 * nodes);
+        if (st != GLBM_OK) return st;
+        CUDA_TRY(cudaMemcpyAsync(c->d_stage, rho, nodes * 8, cudaMemcpyHostToDevice, c->stream));
+        CUDA_TRY(cudaMemcpyAsync(c->d_stage + nodes, ux, nodes * 8, cudaMemcpyHostToDevice, c->stream));
+        if (c->dims == 2)
+            CUDA_TRY(cudaMemcpyAsync(c->d_stage + 2 * nodes, uy, nodes * 8, cudaMemcpyHostToDevice, c->stream));
+        dr = c->d_stage;
+        du = c->d_stage + nodes;
+        dv = c->dims == 2 ? c->d_stage + 2 * nodes : c->d_stage;
+    }
+    if (!dv) dv = du;
+    CUDA_TRY(glbm_launch_set_equilibrium(aux_args(c), c->buf[c->cur], inst, dr, du, dv, c->stream));
+    c->launches += 1;
+    CUDA_TRY(set_clock(c, 0));
+    if (!on_device) CUDA_TRY(cudaStreamSynchronize(c->stream));  // host buffers reusable on return
+    return GLBM_OK;
+}
+
+extern "C" glbm_status glbm_set_populations(glbm_ctx *c, int inst, const double *f, int on_device)
+{
+    glbm_status st = check_inst(c, inst);
+    if (st != GLBM_OK) return st;
+    if (!f) return fail(GLBM_E_INVAL, "null populations");
+    const size_t n = (size_t)n_q(c) * c->Lx * c->Ly;
+    const double *src = f;
+    if (!on_device) {
+        st = ensure_stage(c, n);
+        if (st != GLBM_OK) return st;
+        CUDA_TRY(cudaMemcpyAsync(c->d_stage, f, n * 8, cudaMemcpyHostToDevice, c->stream));
+        src = c->d_stage;
+    }
+    CUDA_TRY(glbm_launch_set_populations(aux_args(c), c->buf[c->cur], inst, src, c->stream));
+    c->launches += 1;
+    CUDA_TRY(set_clock(c, 0));
+    if (!on_device) CUDA_TRY(cudaStreamSynchronize(c->stream));
+    return GLBM_OK;
+}
+
+extern "C" glbm_status glbm_get_populations(glbm_ctx *c, int inst, double *f, int on_device)
+{
+    glbm_status st = check_inst(c, inst);
+    if (st != GLBM_OK) return st;
+    if (!f) return fail(GLBM_E_INVAL, "null output");
+    const size_t n = (size_t)n_q(c) * c->Lx * c->Ly;
+    double *dst = f;
+    if (!on_device) {
+        st = ensure_stage(c, n);
+        if (st != GLBM_OK) return st;
+        dst = c->d_stage;
+    }
+    CUDA_TRY(glbm_launch_get_populations(aux_args(c), c->buf[c->cur], inst, dst, c->stream));
+    c->launches += 1;
+    if (!on_device) {
+        CUDA_TRY(cudaMemcpyAsync(f, dst, n * 8, cudaMemcpyDeviceToHost, c->stream));
+        CUDA_TRY(cudaStreamSynchronize(c->stream));
+    }
+    return GLBM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// stepping
+// ---------------------------------------------------------------------------
+static Step2DArgs step_args(const glbm_ctx *c, int from)
+{
+    Step2DArgs a;
+    memset(&a, 0, sizeof(a));
+    a.tab = c->tab;
+    a.fin = c->buf[from];
+    a.fout = c->buf[1 - from];
+    a.ip = c->d_ip;
+    a.status = c->d_status;
+    a.step_ctr = c->d_status + 1;
+    a.done_ctr = c->d_status + 2;
+    a.Lx = c->Lx;
+    a.Ly = c->Ly;
+    a.pitch = c->pitch;
+    a.bc = c->bc;
+    a.plane = c->plane;
+    a.inst_stride = c->inst_stride;
+    return a;
+}
+
+// One 2D step from buffer `from` into the other, on stream s.
+static cudaError_t launch_one_2d(const glbm_ctx *c, int from, cudaStream_t s)
+{
+    const Step2DArgs a = step_args(c, from);
+    return c->prec == GLBM_FP64 ? glbm_launch_step2d_f64(c->N, a, c->n_inst, s)
+                                : glbm_launch_step2d_f32(c->N, a, c->n_inst, s);
+}
+
+static glbm_status capture_chunk(glbm_ctx *c, int from)
+{
+    cudaGraph_t g = nullptr;
+    CUDA_TRY(cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = cudaSuccess;
+    int b = from;
+    for (int i = 0; i < kGraphChunk && e == cudaSuccess; ++i) {
+        e = launch_one_2d(c, b, c->cap);
+        b = 1 - b;
+    }
+    cudaError_t e2 = cudaStreamEndCapture(c->cap, &g);
+    if (e != cudaSuccess || e2 != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return fail(GLBM_E_CUDA, "graph capture failed: %s",
+                    cudaGetErrorString(e != cudaSuccess ? e : e2));
+    }
+    e = cudaGraphInstantiate(&c->graph[from], g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return fail(GLBM_E_CUDA, "graph instantiate failed: %s", cudaGetErrorString(e));
+    return GLBM_OK;
+}
+
+extern "C" glbm_status glbm_step(glbm_ctx *c, int64_t n)
+{
+    if (!c) return fail(GLBM_E_INVAL, "null context");
+    if (n < 0) return fail(GLBM_E_INVAL, "negative step count");
+    const unsigned prior = *c->h_status;  // flags of steps already finished
+    if (n == 0) return prior ? fail(GLBM_E_UNSTABLE, "a node left the positivity domain") : GLBM_OK;
+    if (c->dims == 1) {
+        const AuxArgs a = aux_args(c);
+        for (int i = 0; i < c->n_inst; ++i) {
+            int ok = 0;
+            CUDA_TRY(glbm_launch_run1d_resident(a, c->buf[c->cur], i, n, c->d_status, c->stream, &ok));
+            if (ok) {
+                c->launches += 1;
+                continue;
+            }
+            // too large for one CTA: one launch per step, ping-pong through both buffers
+            int b = c->cur;
+            for (int64_t s = 0; s < n; ++s) {
+                CUDA_TRY(glbm_launch_step1d(a, c->buf[b], c->buf[1 - b], i, c->d_status, c->stream));
+                b = 1 - b;
+            }
+            if (b != c->cur) {
+                const size_t bytes = (size_t)c->inst_stride * c->elem;
+                CUDA_TRY(cudaMemcpyAsync((char *)c->buf[c->cur] + (size_t)i * bytes,
+                                         (char *)c->buf[b] + (size_t)i * bytes, bytes,
+                                         cudaMemcpyDeviceToDevice, c->stream));
+            }
+            c->launches += n;
+        }
+    } else {
+        int64_t left = n;
+        while (left >= kGraphChunk) {
+            if (!c->graph[c->cur]) {
+                glbm_status st = capture_chunk(c, c->cur);
+                if (st != GLBM_OK) return st;
+            }
+            CUDA_TRY(cudaGraphLaunch(c->graph[c->cur], c->stream));
+            c->launches += kGraphChunk;
+            left -= kGraphChunk;  // even chunk: c->cur unchanged
+        }
+        for (; left > 0; --left) {
+            CUDA_TRY(launch_one_2d(c, c->cur, c->stream));
+            c->cur = 1 - c->cur;
+            c->launches += 1;
+        }
+    }
+    c->t += n;
+    CUDA_TRY(cudaMemcpyAsync(c->h_status, c->d_status, sizeof(unsigned), cudaMemcpyDeviceToHost,
+                             c->stream));
+    if (prior) return fail(GLBM_E_UNSTABLE, "a node left the positivity domain");
+    return GLBM_OK;
+}
+
+extern "C" glbm_status glbm_sync(glbm_ctx *c)
+{
+    if (!c) return fail(GLBM_E_INVAL, "null context");
+    CUDA_TRY(cudaMemcpyAsync(c->h_status, c->d_status, sizeof(unsigned), cudaMemcpyDeviceToHost,
+                             c->stream));
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
+    if (*c->h_status) return fail(GLBM_E_UNSTABLE, "a node left the positivity domain");
+    return GLBM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// moments and conservation
+// ---------------------------------------------------------------------------
+static glbm_status compute_moments(glbm_ctx *c, int inst)
+{
+    CUDA_TRY(glbm_launch_moments(aux_args(c), c->buf[c->cur], inst, c->d_mom, c->stream));
+    c->launches += 1;
+    return GLBM_OK;
+}
+
+extern "C" glbm_status glbm_moments(glbm_ctx *c, int inst, unsigned mask, double *out,
+                                    size_t out_len, int out_on_device)
+{
+    glbm_status st = check_inst(c, inst);
+    if (st != GLBM_OK) return st;
+    if (!out) return fail(GLBM_E_INVAL, "null output");
+    // field slot of each mask bit in the reducer's output
+    const int slot2d[7] = {0, 1, 2, 3, 4, 5, 6};
+    const int slot1d[7] = {0, 1, -1, 2, 3, -1, -1};
+    const size_t nodes = (size_t)c->Lx * c->Ly;
+    size_t need = 0;
+    for (int b = 0; b < 7; ++b) {
+        if (!(mask & (1u << b))) continue;
+        if (c->dims == 1 && slot1d[b] < 0) return fail(GLBM_E_INVAL, "field bit %d has no 1D meaning", b);
+        need += nodes;
+    }
+    if (need == 0) return fail(GLBM_E_INVAL, "empty field mask");
+    if (out_len < need) return fail(GLBM_E_INVAL, "output holds %zu doubles, needs %zu", out_len, need);
+    st = compute_moments(c, inst);
+    if (st != GLBM_OK) return st;
+    size_t o = 0;
+    for (int b = 0; b < 7; ++b) {
+        if (!(mask & (1u << b))) continue;
+        const int slot = c->dims == 2 ? slot2d[b] : slot1d[b];
+        CUDA_TRY(cudaMemcpyAsync(out + o, c->d_mom + (size_t)slot * nodes, nodes * 8,
+                                 out_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                                 c->stream));
+        o += nodes;
+    }
+    if (!out_on_device) CUDA_TRY(cudaStreamSynchronize(c->stream));
+    return GLBM_OK;
+}
+
+extern "C" glbm_status glbm_conservation(glbm_ctx *c, int inst, double *mass, double *mom_x,
+                                         double *mom_y)
+{
+    glbm_status st = check_inst(c, inst);
+    if (st != GLBM_OK) return st;
+    st = compute_moments(c, inst);
+    if (st != GLBM_OK) return st;
+    const long long nodes = (long long)c->Lx * c->Ly;
+    CUDA_TRY(glbm_launch_field_sums(c->d_mom, c->dims == 2 ? 3 : 2, nodes, c->d_part, c->sum_blocks,
+                                    c->d_sums, c->stream));
+    c->launches += 2;
+    double h[3];
+    CUDA_TRY(cudaMemcpyAsync(h, c->d_sums, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
+    if (mass) *mass = h[0];
+    if (mom_x) *mom_x = h[1];
+    if (mom_y) *mom_y = c->dims == 2 ? h[2] : 0.0;
+    return GLBM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// checkpoints: header, raw state image of every instance, CRC-32
+// ---------------------------------------------------------------------------
+struct CkptHeader {
+    char magic[8];
+    int32_t version, dims, nx, ny, k, bc, prec, n_inst;
+    int64_t t;
+    uint64_t bytes;
+};
+
+static uint32_t crc32_update(uint32_t crc, const unsigned char *p, size_t n)
+{
+    crc = ~crc;
+    for (size_t i = 0; i < n; ++i) {
+        crc ^= p[i];
+        for (int b = 0; b < 8; ++b) crc = (crc >> 1) ^ (0xEDB88320u & (0u - (crc & 1u)));
+    }
+    return ~crc;
+}
+
+static void fill_header(const glbm_ctx *c, CkptHeader &h)
+{
+    memset(&h, 0, sizeof(h));
+    memcpy(h.magic, "GLBMCKP1", 8);
+    h.version = 1;
+    h.dims = c->dims;
+    h.nx = c->Lx;
+    h.ny = c->Ly;
+    h.k = c->k;
+    h.bc = c->bc;
+    h.prec = c->prec;
+    h.n_inst = c->n_inst;
+    h.t = c->t;
+    h.bytes = bytes_state(c);
+}
+
+extern "C" glbm_status glbm_save(glbm_ctx *c, const char *path)
+{
+    if (!c || !path) return fail(GLBM_E_INVAL, "null argument");
+    std::vector<unsigned char> img(bytes_state(c));
+    CUDA_TRY(cudaMemcpyAsync(img.data(), c->buf[c->cur], img.size(), cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
+    CkptHeader h;
+    fill_header(c, h);
+    uint32_t crc = crc32_update(0, (const unsigned char *)&h, sizeof(h));
+    crc = crc32_update(crc, img.data(), img.size());
+    FILE *fp = fopen(path, "wb");
+    if (!fp) return fail(GLBM_E_IO, "cannot open %s for writing", path);
+    bool ok = fwrite(&h, sizeof(h), 1, fp) == 1 && fwrite(img.data(), 1, img.size(), fp) == img.size() &&
+              fwrite(&crc, sizeof(crc), 1, fp) == 1;
+    ok = (fclose(fp) == 0) && ok;
+    return ok ? GLBM_OK : fail(GLBM_E_IO, "write to %s failed", path);
+}
+
+extern "C" glbm_status glbm_load(glbm_ctx *c, const char *path)
+{
+    if (!c || !path) return fail(GLBM_E_INVAL, "null argument");
+    FILE *fp = fopen(path, "rb");
+    if (!fp) return fail(GLBM_E_IO, "cannot open %s", path);
+    CkptHeader h, want;
+    fill_header(c, want);
+    std::vector<unsigned char> img;
+    uint32_t crc_file = 0;
+    bool ok = fread(&h, sizeof(h), 1, fp) == 1;
+    if (ok) {
+        want.t = h.t;
+        ok = memcmp(&h, &want, sizeof(h)) == 0;
+        if (!ok) {
+            fclose(fp);
+            return fail(GLBM_E_INVAL, "checkpoint %s does not match this context's configuration", path);
+        }
+        img.resize(h.bytes);
+        ok = fread(img.data(), 1, img.size(), fp) == img.size() && fread(&crc_file, sizeof(crc_file), 1, fp) == 1;
+    }
+    fclose(fp);
+    if (!ok) return fail(GLBM_E_IO, "checkpoint %s is truncated", path);
+    uint32_t crc = crc32_update(0, (const unsigned char *)&h, sizeof(h));
+    crc = crc32_update(crc, img.data(), img.size());
+    if (crc != crc_file) return fail(GLBM_E_IO, "checkpoint %s fails its CRC-32 check", path);
+    CUDA_TRY(cudaMemcpyAsync(c->buf[c->cur], img.data(), img.size(), cudaMemcpyHostToDevice, c->stream));
+    CUDA_TRY(set_clock(c, h.t));
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
+    return GLBM_OK;
+}
+
+extern "C" glbm_status glbm_batch_create(const glbm_config *cfgs, int n, void *stream, glbm_ctx **out)
+{
+    (void)cfgs;
+    (void)n;
+    (void)stream;
+    if (out) *out = nullptr;
+    return fail(GLBM_E_UNSUPPORTED, "heterogeneous batches are not built yet");
+}

@@ -1,0 +1,463 @@
+// Auxiliary kernels of libglbm: initial equilibrium, import/export of
+// populations in the FP64 logical layout, the moment reducer (moments of the
+// streamed state, Sec. 2 for rho and u; temperature, heat flux and shear
+// stress as central moments), deterministic global sums, and the 1D step
+// (Sec. 5.1 shock tube, halfway bounce-back) both per launch and resident in
+// one CTA for many steps.
+#include "glbm_device.cuh"
+
+namespace {
+
+// E_n(u) - W_n at runtime level t.N (FP64 Horner on the coefficient table).
+__device__ double eq_dev_rt(const AxisTable &t, double u, int n)
+{
+    const int N = t.N;
+    const int an = n < 0 ? -n : n;
+    const double v = u * u;
+    double ae = t.Ce[an][N];
+    for (int i = N - 1; i >= 1; --i) ae = fma(ae, v, t.Ce[an][i]);
+    ae *= v;
+    double bo = 0.0;
+    if (an > 0) {
+        bo = t.Co[an][N - 1];
+        for (int i = N - 2; i >= 0; --i) bo = fma(bo, v, t.Co[an][i]);
+    }
+    return n >= 0 ? fma(u, bo, ae) : fma(-u, bo, ae);
+}
+
+__device__ __forceinline__ double load_full(const AuxArgs &a, const void *f, long long idx, int q)
+{
+    (void)q;
+    if (a.prec == GLBM_FP64) return static_cast<const double *>(f)[idx];
+    return (double)static_cast<const float *>(f)[idx];
+}
+
+// rest weight of flat velocity q
+__device__ __forceinline__ double rest_weight(const AxisTable &t, int dims, int q)
+{
+    const int Q1 = 2 * t.N + 1;
+    if (dims == 1) return t.W[q];
+    return t.W[q / Q1] * t.W[q % Q1];
+}
+
+__global__ void k_set_equilibrium(const __grid_constant__ AuxArgs a, void *f, int inst,
+                                  const double *__restrict__ rho, const double *__restrict__ ux,
+                                  const double *__restrict__ uy)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y;
+    if (x >= a.Lx) return;
+    const int N = a.N, Q1 = 2 * N + 1;
+    const long long node = (long long)y * a.Lx + x;
+    const double r = rho[node], u = ux[node], v = a.dims == 2 ? uy[node] : 0.0;
+    const long long base = (long long)inst * a.inst_stride + (long long)y * a.pitch + x;
+    const int Qy = a.dims == 2 ? Q1 : 1;
+    for (int iy = 0; iy < Qy; ++iy) {
+        const double wy = a.dims == 2 ? a.tab.W[iy] : 1.0;
+        const double dy = a.dims == 2 ? eq_dev_rt(a.tab, v, iy - N) : 0.0;
+        for (int ix = 0; ix < Q1; ++ix) {
+            const double wx = a.tab.W[ix];
+            const double dx = eq_dev_rt(a.tab, u, ix - N);
+            const long long idx = base + (long long)(iy * Q1 + ix) * a.plane;
+            if (a.prec == GLBM_FP64) {
+                static_cast<double *>(f)[idx] = r * (wx + dx) * (wy + dy);
+            } else {
+                // rho E^x E^y - W^x W^y without cancellation
+                const double dev = (r - 1.0) * wx * wy + r * (dx * (wy + dy) + wx * dy);
+                static_cast<float *>(f)[idx] = (float)dev;
+            }
+        }
+    }
+}
+
+__global__ void k_set_populations(const __grid_constant__ AuxArgs a, void *f, int inst,
+                                  const double *__restrict__ src)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y;
+    const int q = blockIdx.z;
+    if (x >= a.Lx) return;
+    const double v = src[((long long)q * a.Ly + y) * a.Lx + x];
+    const long long idx =
+        (long long)inst * a.inst_stride + (long long)q * a.plane + (long long)y * a.pitch + x;
+    if (a.prec == GLBM_FP64)
+        static_cast<double *>(f)[idx] = v;
+    else
+        static_cast<float *>(f)[idx] = (float)(v - rest_weight(a.tab, a.dims, q));
+}
+
+__global__ void k_get_populations(const __grid_constant__ AuxArgs a, const void *f, int inst,
+                                  double *__restrict__ dst)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y;
+    const int q = blockIdx.z;
+    if (x >= a.Lx) return;
+    const long long idx =
+        (long long)inst * a.inst_stride + (long long)q * a.plane + (long long)y * a.pitch + x;
+    double v = load_full(a, f, idx, q);
+    if (a.prec != GLBM_FP64) v += rest_weight(a.tab, a.dims, q);
+    dst[((long long)q * a.Ly + y) * a.Lx + x] = v;
+}
+
+// Population of velocity (ix, iy) arriving at node (x, y) by streaming X
+// (full FP64 value), including the boundary rule. rw_lo / rw_hi are the wall
+// densities of column x.
+__device__ double pulled(const AuxArgs &a, const InstParams &ip, const void *f, long long ibase,
+                         int x, int y, int ix, int iy, double rw_lo, double rw_hi)
+{
+    const int N = a.N, Q1 = 2 * N + 1;
+    if (a.dims == 1) {
+        const int n = ix - N;
+        int xs = x - n;
+        int q = ix;
+        if (a.bc == GLBM_BC_PERIODIC) {
+            xs = wrap_index(xs, a.Lx);
+        } else if (xs < 0) {
+            xs = -1 - xs;
+            q = 2 * N - ix;
+        } else if (xs >= a.Lx) {
+            xs = 2 * a.Lx - 1 - xs;
+            q = 2 * N - ix;
+        }
+        double v = load_full(a, f, ibase + (long long)q * a.plane + xs, q);
+        if (a.prec != GLBM_FP64) v += a.tab.W[q];
+        return v;
+    }
+    const int nx = ix - N, ny = iy - N;
+    const int xs = wrap_index(x - nx, a.Lx);
+    int ys = y - ny;
+    if (a.bc == GLBM_BC_WALLS) {
+        if (ys < 0) return rw_lo * ip.ew_lo[ix] * a.tab.W[iy];
+        if (ys >= a.Ly) return rw_hi * ip.ew_hi[ix] * a.tab.W[iy];
+    } else {
+        ys = wrap_index(ys, a.Ly);
+    }
+    const int q = iy * Q1 + ix;
+    double v = load_full(a, f, ibase + (long long)q * a.plane + (long long)ys * a.pitch + xs, q);
+    if (a.prec != GLBM_FP64) v += a.tab.W[iy] * a.tab.W[ix];
+    return v;
+}
+
+// Wall density of column x: absorbed mass / sum_{n>0} n W_n (FP64).
+__device__ double wall_density(const AuxArgs &a, const InstParams &ip, const void *f,
+                               long long ibase, int x, bool lower)
+{
+    const int N = a.N, Q1 = 2 * N + 1;
+    double D = 0.0;
+    for (int aa = 1; aa <= N; ++aa) {
+        for (int k = 0; k < aa; ++k) {
+            const int iy = lower ? N - aa : N + aa;
+            const int row = lower ? k : a.Ly - 1 - k;
+            for (int ix = 0; ix < Q1; ++ix) {
+                const int xs = wrap_index(x - (ix - N), a.Lx);
+                const int q = iy * Q1 + ix;
+                double v = load_full(a, f, ibase + (long long)q * a.plane + (long long)row * a.pitch + xs, q);
+                if (a.prec != GLBM_FP64) v += a.tab.W[iy] * a.tab.W[ix];
+                D += v;
+            }
+        }
+    }
+    return D * ip.inv_den;
+}
+
+// out[7][Ly][Lx] (2D) or out[4][Lx] (1D): moments of S(X) at every node.
+__global__ void k_moments(const __grid_constant__ AuxArgs a, const void *f, int inst,
+                          double *__restrict__ out)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y;
+    if (x >= a.Lx) return;
+    const InstParams &ip = a.ip[inst];
+    const int N = a.N, Q1 = 2 * N + 1;
+    const int Qy = a.dims == 2 ? Q1 : 1;
+    const long long ibase = (long long)inst * a.inst_stride;
+    double rw_lo = 0.0, rw_hi = 0.0;
+    if (a.dims == 2 && a.bc == GLBM_BC_WALLS) {
+        if (y < N) rw_lo = wall_density(a, ip, f, ibase, x, true);
+        if (y >= a.Ly - N) rw_hi = wall_density(a, ip, f, ibase, x, false);
+    }
+    double rho = 0.0, jx = 0.0, jy = 0.0;
+    for (int iy = 0; iy < Qy; ++iy)
+        for (int ix = 0; ix < Q1; ++ix) {
+            const double v = pulled(a, ip, f, ibase, x, y, ix, iy, rw_lo, rw_hi);
+            rho += v;
+            jx += (ix - N) * v;
+            jy += (a.dims == 2 ? iy - N : 0) * v;
+        }
+    const double ux = jx / rho, uy = jy / rho;
+    double e2 = 0.0, qx = 0.0, qy = 0.0, sxy = 0.0;
+    for (int iy = 0; iy < Qy; ++iy)
+        for (int ix = 0; ix < Q1; ++ix) {
+            const double v = pulled(a, ip, f, ibase, x, y, ix, iy, rw_lo, rw_hi);
+            const double dx = (ix - N) - ux;
+            const double dy = a.dims == 2 ? (iy - N) - uy : 0.0;
+            const double d2 = dx * dx + dy * dy;
+            e2 += d2 * v;
+            qx += dx * d2 * v;
+            qy += dy * d2 * v;
+            sxy += dx * dy * v;
+        }
+    const long long plane = (long long)a.Lx * a.Ly;
+    const long long node = (long long)y * a.Lx + x;
+    if (a.dims == 2) {
+        out[0 * plane + node] = rho;
+        out[1 * plane + node] = ux;
+        out[2 * plane + node] = uy;
+        out[3 * plane + node] = e2 / (2.0 * rho);
+        out[4 * plane + node] = 0.5 * qx;
+        out[5 * plane + node] = 0.5 * qy;
+        out[6 * plane + node] = sxy;
+    } else {
+        out[0 * plane + node] = rho;
+        out[1 * plane + node] = ux;
+        out[2 * plane + node] = e2 / rho;
+        out[3 * plane + node] = 0.5 * qx;
+    }
+}
+
+// Deterministic sums of rho, rho u_x, rho u_y over n nodes: every block sums a
+// fixed contiguous range in a fixed tree order; a second launch adds the
+// block partials in index order.
+constexpr int SUM_THREADS = 256;
+
+__global__ void k_field_partials(const double *__restrict__ fields, int nfields, long long n,
+                                 double *__restrict__ partials)
+{
+    __shared__ double sh[3][SUM_THREADS];
+    const long long per = (n + gridDim.x - 1) / gridDim.x;
+    const long long lo = blockIdx.x * per;
+    const long long hi = min(n, lo + per);
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+    for (long long i = lo + threadIdx.x; i < hi; i += SUM_THREADS) {
+        const double r = fields[i];
+        s0 += r;
+        s1 += r * fields[n + i];
+        if (nfields > 2) s2 += r * fields[2 * n + i];
+    }
+    sh[0][threadIdx.x] = s0;
+    sh[1][threadIdx.x] = s1;
+    sh[2][threadIdx.x] = s2;
+    __syncthreads();
+    for (int stride = SUM_THREADS / 2; stride > 0; stride >>= 1) {
+        if ((int)threadIdx.x < stride)
+            for (int m = 0; m < 3; ++m) sh[m][threadIdx.x] += sh[m][threadIdx.x + stride];
+        __syncthreads();
+    }
+    if (threadIdx.x < 3) partials[blockIdx.x * 3 + threadIdx.x] = sh[threadIdx.x][0];
+}
+
+__global__ void k_field_final(const double *__restrict__ partials, int nblocks, double *out)
+{
+    if (threadIdx.x < 3) {
+        double s = 0.0;
+        for (int b = 0; b < nblocks; ++b) s += partials[b * 3 + threadIdx.x];
+        out[threadIdx.x] = s;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// 1D step (Sec. 5.1): pull with halfway bounce-back or periodic ends, moments,
+// equilibrium, relaxation. One thread per node.
+// ---------------------------------------------------------------------------
+template <int N, typename T>
+__device__ __forceinline__ void node1d(const AuxArgs &a, const InstParams &ip, const T *fin,
+                                       T *fout, int x, int L, long long plane, unsigned *status)
+{
+    constexpr int Q1 = 2 * N + 1;
+    constexpr bool DEV = sizeof(T) == 4;
+    using Acc = TabAcc<T>;
+    T f[Q1];
+#pragma unroll
+    for (int ix = 0; ix < Q1; ++ix) {
+        const int n = ix - N;
+        int xs = x - n, q = ix;
+        if (a.bc == GLBM_BC_PERIODIC) {
+            xs = wrap_index(xs, L);
+        } else if (xs < 0) {
+            xs = -1 - xs;
+            q = 2 * N - ix;
+        } else if (xs >= L) {
+            xs = 2 * L - 1 - xs;
+            q = 2 * N - ix;
+        }
+        f[ix] = fin[(long long)q * plane + xs];
+    }
+    T s = T(0), c = T(0), sj = T(0), cj = T(0);
+#pragma unroll
+    for (int ix = 0; ix < Q1; ++ix) acc2(s, c, f[ix]);
+#pragma unroll
+    for (int n = 1; n <= N; ++n) acc2(sj, cj, T(n) * (f[N + n] - f[N - n]));
+    const T m0 = s + c;
+    const T rho = DEV ? T(1) + m0 : m0;
+    const T drho = DEV ? m0 : m0 - T(1);
+    const T u = (sj + cj) / rho;
+    const T umax = (T)(0.816496580927726 * N);
+    if (!(rho > T(0)) || !(fabs(u) <= umax)) atomicOr(status, 1u);
+    T d[Q1];
+    eq_dev_all<N, T>(a.tab, u, d);
+    const T om = DEV ? (T)ip.omega_f : (T)ip.omega;
+#pragma unroll
+    for (int ix = 0; ix < Q1; ++ix) {
+        const T w = Acc::W(a.tab, ix);
+        // FP32: delta f^eq = drho W + rho d ; FP64: f^eq = rho (W + d)
+        const T eq = DEV ? fma(drho, w, rho * d[ix]) : rho * (w + d[ix]);
+        fout[(long long)ix * plane + x] = fma(om, eq - f[ix], f[ix]);  // f + omega (f^eq - f)
+    }
+}
+
+template <int N, typename T>
+__global__ void k_step1d(const __grid_constant__ AuxArgs a, const T *__restrict__ fin,
+                         T *__restrict__ fout, int inst, unsigned *status)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= a.Lx) return;
+    node1d<N, T>(a, a.ip[inst], fin, fout, x, a.Lx, a.plane, status);
+}
+
+// Many steps of one small 1D lattice inside one CTA: both population copies
+// live in shared memory and a block barrier separates the steps, so the whole
+// run is one launch (the shock tube is launch-latency bound, not HBM bound).
+template <int N, typename T>
+__global__ void k_run1d_resident(const __grid_constant__ AuxArgs a, T *__restrict__ f,
+                                 int inst, long long steps, unsigned *status)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    constexpr int Q1 = 2 * N + 1;
+    const int L = a.Lx;
+    T *A = reinterpret_cast<T *>(smem_raw);
+    T *B = A + (long long)Q1 * L;
+    for (int i = threadIdx.x; i < Q1 * L; i += blockDim.x) {
+        const int q = i / L, x = i % L;
+        A[i] = f[(long long)q * a.plane + x];
+    }
+    __syncthreads();
+    for (long long t = 0; t < steps; ++t) {
+        for (int x = threadIdx.x; x < L; x += blockDim.x)
+            node1d<N, T>(a, a.ip[inst], A, B, x, L, L, status);
+        __syncthreads();
+        T *tmp = A;
+        A = B;
+        B = tmp;
+    }
+    for (int i = threadIdx.x; i < Q1 * L; i += blockDim.x) {
+        const int q = i / L, x = i % L;
+        f[(long long)q * a.plane + x] = A[i];
+    }
+}
+
+template <typename T>
+cudaError_t launch_step1d_t(const AuxArgs &a, const void *fin, void *fout, int inst,
+                            unsigned *status, cudaStream_t s)
+{
+    const T *in = static_cast<const T *>(fin) + (long long)inst * a.inst_stride;
+    T *out = static_cast<T *>(fout) + (long long)inst * a.inst_stride;
+    const int threads = 128;
+    const int blocks = (a.Lx + threads - 1) / threads;
+    switch (a.N) {
+#define GLBM_CASE(NN) \
+    case NN: k_step1d<NN, T><<<blocks, threads, 0, s>>>(a, in, out, inst, status); break;
+        GLBM_CASE(1) GLBM_CASE(2) GLBM_CASE(3) GLBM_CASE(4)
+        GLBM_CASE(5) GLBM_CASE(6) GLBM_CASE(7) GLBM_CASE(8)
+#undef GLBM_CASE
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+template <int N, typename T>
+cudaError_t launch_resident_n(const AuxArgs &a, T *f, int inst, long long steps,
+                              unsigned *status, cudaStream_t s, size_t smem)
+{
+    cudaError_t e = cudaFuncSetAttribute(k_run1d_resident<N, T>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const int threads = a.Lx >= 1024 ? 1024 : ((a.Lx + 31) / 32) * 32;
+    k_run1d_resident<N, T><<<1, threads, smem, s>>>(a, f, inst, steps, status);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_resident_t(const AuxArgs &a, void *fv, int inst, long long steps,
+                              unsigned *status, cudaStream_t s, int *ok)
+{
+    const size_t smem = (size_t)2 * (2 * a.N + 1) * a.Lx * sizeof(T);
+    *ok = 0;
+    if (smem > 200 * 1024) return cudaSuccess;  // caller falls back to per-step launches
+    *ok = 1;
+    T *f = static_cast<T *>(fv) + (long long)inst * a.inst_stride;
+    switch (a.N) {
+#define GLBM_CASE(NN) \
+    case NN: return launch_resident_n<NN, T>(a, f, inst, steps, status, s, smem);
+        GLBM_CASE(1) GLBM_CASE(2) GLBM_CASE(3) GLBM_CASE(4)
+        GLBM_CASE(5) GLBM_CASE(6) GLBM_CASE(7) GLBM_CASE(8)
+#undef GLBM_CASE
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace
+
+cudaError_t glbm_launch_set_equilibrium(const AuxArgs &a, void *f, int inst, const double *rho,
+                                        const double *ux, const double *uy, cudaStream_t s)
+{
+    dim3 grid((a.Lx + 127) / 128, a.Ly);
+    k_set_equilibrium<<<grid, 128, 0, s>>>(a, f, inst, rho, ux, uy);
+    return cudaGetLastError();
+}
+
+cudaError_t glbm_launch_set_populations(const AuxArgs &a, void *f, int inst, const double *src,
+                                        cudaStream_t s)
+{
+    const int Q1 = 2 * a.N + 1;
+    dim3 grid((a.Lx + 127) / 128, a.Ly, a.dims == 2 ? Q1 * Q1 : Q1);
+    k_set_populations<<<grid, 128, 0, s>>>(a, f, inst, src);
+    return cudaGetLastError();
+}
+
+cudaError_t glbm_launch_get_populations(const AuxArgs &a, const void *f, int inst, double *dst,
+                                        cudaStream_t s)
+{
+    const int Q1 = 2 * a.N + 1;
+    dim3 grid((a.Lx + 127) / 128, a.Ly, a.dims == 2 ? Q1 * Q1 : Q1);
+    k_get_populations<<<grid, 128, 0, s>>>(a, f, inst, dst);
+    return cudaGetLastError();
+}
+
+cudaError_t glbm_launch_moments(const AuxArgs &a, const void *f, int inst, double *out,
+                                cudaStream_t s)
+{
+    dim3 grid((a.Lx + 63) / 64, a.Ly);
+    k_moments<<<grid, 64, 0, s>>>(a, f, inst, out);
+    return cudaGetLastError();
+}
+
+int glbm_field_sum_blocks(long long n)
+{
+    long long b = (n + 4095) / 4096;
+    if (b < 1) b = 1;
+    if (b > 1024) b = 1024;
+    return (int)b;
+}
+
+cudaError_t glbm_launch_field_sums(const double *fields, int nfields, long long n, double *partials,
+                                   int nblocks, double *out, cudaStream_t s)
+{
+    k_field_partials<<<nblocks, SUM_THREADS, 0, s>>>(fields, nfields, n, partials);
+    k_field_final<<<1, 32, 0, s>>>(partials, nblocks, out);
+    return cudaGetLastError();
+}
+
+cudaError_t glbm_launch_step1d(const AuxArgs &a, const void *fin, void *fout, int inst,
+                               unsigned *status, cudaStream_t s)
+{
+    if (a.prec == GLBM_FP64) return launch_step1d_t<double>(a, fin, fout, inst, status, s);
+    return launch_step1d_t<float>(a, fin, fout, inst, status, s);
+}
+
+cudaError_t glbm_launch_run1d_resident(const AuxArgs &a, void *f, int inst, long long steps,
+                                       unsigned *status, cudaStream_t s, int *ok)
+{
+    if (a.prec == GLBM_FP64) return launch_resident_t<double>(a, f, inst, steps, status, s, ok);
+    return launch_resident_t<float>(a, f, inst, steps, status, s, ok);
+}

@@ -1,0 +1,136 @@
+// Device helpers shared by the libglbm kernels: table access by precision,
+// Horner evaluation of the equilibrium polynomials, compensated addition.
+#pragma once
+#include "glbm_internal.h"
+#include "../../include/glbm.h"
+
+template <typename T>
+struct TabAcc;
+
+template <>
+struct TabAcc<double> {
+    static constexpr bool HILO = false;
+    static __device__ __forceinline__ double C1lo(const AxisTable &, int) { return 0.0; }
+    static __device__ __forceinline__ double W(const AxisTable &t, int i) { return t.W[i]; }
+    static __device__ __forceinline__ double WN(const AxisTable &t, int i) { return t.WN[i]; }
+    static __device__ __forceinline__ double Ce(const AxisTable &t, int n, int i) { return t.Ce[n][i]; }
+    static __device__ __forceinline__ double Co(const AxisTable &t, int n, int i) { return t.Co[n][i]; }
+};
+
+template <>
+struct TabAcc<float> {
+    static constexpr bool HILO = true;
+    static __device__ __forceinline__ float C1lo(const AxisTable &t, int n) { return t.Co1lo[n]; }
+    static __device__ __forceinline__ float W(const AxisTable &t, int i) { return t.Wf[i]; }
+    static __device__ __forceinline__ float WN(const AxisTable &t, int i) { return t.WNf[i]; }
+    static __device__ __forceinline__ float Ce(const AxisTable &t, int n, int i) { return t.Cef[n][i]; }
+    static __device__ __forceinline__ float Co(const AxisTable &t, int n, int i) { return t.Cof[n][i]; }
+};
+
+// Deviation of the level-N equilibrium from the rest weights, for one |n|:
+// Ae_n(v) (even powers >= 2) and Bo_n(v) (odd powers / u), v = u^2, so that
+// E_{+n}(u) - W_n = Ae + u Bo and E_{-n}(u) - W_n = Ae - u Bo.
+template <int N, typename T>
+__device__ __forceinline__ void eq_parts(const AxisTable &t, int n, T v, T &ae, T &bo)
+{
+    using A = TabAcc<T>;
+    T a = A::Ce(t, n, N);
+#pragma unroll
+    for (int i = N - 1; i >= 1; --i) a = fma(a, v, A::Ce(t, n, i));
+    ae = a * v;
+    if (n == 0) {
+        bo = T(0);  // E_0 is even in u
+    } else if (A::HILO) {
+        // linear coefficient as hi + lo: the low part joins before the high part
+        T b = A::Co(t, n, N - 1);
+        if (N >= 2) {
+#pragma unroll
+            for (int i = N - 2; i >= 1; --i) b = fma(b, v, A::Co(t, n, i));
+            b = fma(b, v, A::C1lo(t, n));
+        } else {
+            b = A::C1lo(t, n);
+        }
+        bo = b + A::Co(t, n, 0);
+    } else {
+        T b = A::Co(t, n, N - 1);
+#pragma unroll
+        for (int i = N - 2; i >= 0; --i) b = fma(b, v, A::Co(t, n, i));
+        bo = b;
+    }
+}
+
+// d[n+N] = E_n(u) - W_n for every n = -N..N.
+template <int N, typename T>
+__device__ __forceinline__ void eq_dev_all(const AxisTable &t, T u, T (&d)[2 * N + 1])
+{
+    const T v = u * u;
+#pragma unroll
+    for (int n = 0; n <= N; ++n) {
+        T ae, bo;
+        eq_parts<N, T>(t, n, v, ae, bo);
+        if (n == 0) {
+            d[N] = ae;
+        } else {
+            d[N + n] = fma(u, bo, ae);
+            d[N - n] = fma(-u, bo, ae);
+        }
+    }
+}
+
+// E_n(u) - W_n for a single n (compile-time after unrolling).
+template <int N, typename T>
+__device__ __forceinline__ T eq_dev_one(const AxisTable &t, T u, int n)
+{
+    const int an = n < 0 ? -n : n;
+    T ae, bo;
+    eq_parts<N, T>(t, an, u * u, ae, bo);
+    if (an == 0) return ae;
+    return n > 0 ? fma(u, bo, ae) : fma(-u, bo, ae);
+}
+
+// Knuth's two-sum: s + x is added to (s, c) with the rounding error of the
+// addition carried in c (compensated summation of the FP32 moments).
+__device__ __forceinline__ void acc2(float &s, float &c, float x)
+{
+    const float t = s + x;
+    const float bp = t - s;
+    const float err = (s - (t - bp)) + (x - bp);
+    s = t;
+    c += err;
+}
+__device__ __forceinline__ void acc2(double &s, double &c, double x)
+{
+    (void)c;
+    s += x;
+}
+
+// 32-bit integer hash (xorshift-multiply), used to draw the dither of the
+// FP32 stores from (launch, instance, node).
+__device__ __forceinline__ unsigned hash32(unsigned x)
+{
+    x ^= x >> 16;
+    x *= 0x7feb352dU;
+    x ^= x >> 15;
+    x *= 0x846ca68bU;
+    x ^= x >> 16;
+    return x;
+}
+
+// Dither for the FP32 store of `ref + inc`: uniform in [-1/2, 1/2) units in the
+// last place of `ref`, from the random word r. Adding it to the increment
+// before the final rounding makes the rounding error zero-mean, so a steady
+// state does not repeat the same rounding error at every step (whose effect on
+// slowly relaxing moments would grow like 1/omega).
+__device__ __forceinline__ float dither_ulp(float ref, unsigned r)
+{
+    // 2^(exponent - 23 - 32): one ulp of ref per 2^32 of the signed word (0 for
+    // ref below 2^-72, where no dither is needed)
+    const int e = (int)(__float_as_uint(ref) & 0x7F800000u) - (55 << 23);
+    return (float)(int)r * __int_as_float(max(e, 0));
+}
+
+__device__ __forceinline__ int wrap_index(int i, int L)
+{
+    i %= L;
+    return i < 0 ? i + L : i;
+}

@@ -1,0 +1,108 @@
+// Internal declarations shared by the CUDA translation units of libglbm.
+// Not part of the public C ABI (include/glbm.h).
+#pragma once
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#define GLBM_MAXN 8                       // highest level N = k + 1 compiled
+#define GLBM_MAXQ1 (2 * GLBM_MAXN + 1)    // velocities per axis at GLBM_MAXN
+
+// Equilibrium of one axis at level N in lattice units (velocities -N..N,
+// temperature N/3), as a polynomial in the velocity u:
+//   E_n(u) = sum_j C[n][j] u^j,  n = -N..N, j = 0..2N,
+// the coefficient of z^n in (P- / z + P0 + P+ z)^N with
+//   P+- = 1/6 +- u/(2N) + u^2/(2N^2),  P0 = 2/3 - u^2/N^2     (Sec. 2, Eqs. maineq03-05).
+// Stored split into even and odd powers so that E_n and E_-n = E_n(-u) share
+// one evaluation: with v = u^2,
+//   E_{+-n}(u) = W_n + Ae_n(v) +- u Bo_n(v),
+//   Ae_n(v) = sum_{i=1..N} Ce[n][i] v^i,  Bo_n(v) = sum_{i=0..N-1} Co[n][i] v^i,
+// and W_n = C[n][0] the rest weight.
+struct AxisTable {
+    int N;
+    int pad_;
+    double W[GLBM_MAXQ1];                    // index n + N
+    double WN[GLBM_MAXQ1];                   // n W_n
+    double Ce[GLBM_MAXN + 1][GLBM_MAXN + 1];  // [n][i] = C[n][2i], n = 0..N
+    double Co[GLBM_MAXN + 1][GLBM_MAXN];      // [n][i] = C[n][2i+1]
+    float Wf[GLBM_MAXQ1];
+    float WNf[GLBM_MAXQ1];
+    float Cef[GLBM_MAXN + 1][GLBM_MAXN + 1];
+    float Cof[GLBM_MAXN + 1][GLBM_MAXN];
+    float Co1lo[GLBM_MAXN + 1];  // C[n][1] - Cof[n][0]: low part of the linear coefficient
+};
+
+// Host: build the table of level N by N exact polynomial convolutions
+// (the N-fold summation of D1Q3, Sec. 2). Also returns the full C[n][j]
+// array (row-major, (2N+1) x (2N+1)) when `full` is non-null.
+// The largest FP64 coefficient of each power j is then adjusted so that the
+// identities of the exact polynomials, sum_n C[n][j] = [j == 0] (mass) and
+// sum_n n C[n][j] = [j == 1] (momentum), hold to half an ulp of that entry.
+// With plainly rounded coefficients the residual (up to several ulps) acts as
+// a mass and momentum source of the same sign at every step of a steady flow.
+void glbm_build_axis_table(int N, AxisTable *t, double *full);
+
+// Per-instance constants read by the step kernels (one per lattice instance).
+struct InstParams {
+    double omega;      // 1 / (tau + 1/2)                         (Eq. maineq01)
+    double g_theta;    // g / theta_x: force F_i = W_i xi_x g/theta_x   (Sec. 5.4)
+    double inv_den;    // 1 / sum_{n>0} n W^y_n: wall emission normaliser
+    double g_theta_om; // g / (theta_x omega): force folded into the equilibrium
+    double ew_lo[GLBM_MAXQ1];  // E^x_n(u_wall_lo)
+    double ew_hi[GLBM_MAXQ1];  // E^x_n(u_wall_hi)
+    float omega_f, g_theta_f, inv_den_f, g_theta_om_f;
+    float dw_lo_f[GLBM_MAXQ1];  // E^x_n(u_wall_lo) - W_n
+    float dw_hi_f[GLBM_MAXQ1];  // E^x_n(u_wall_hi) - W_n
+    // geometry of the instance (heterogeneous batches keep their own)
+    int N;            // level along both axes
+    int Lx, Ly;       // nodes
+    int pitch;        // row pitch in elements (multiple of 32)
+    int bc;           // GLBM_BC_*
+    int pad_i;
+    long long off;    // element offset of this instance in the population buffers
+    long long plane;  // elements per velocity plane (Ly * pitch)
+};
+
+// Arguments of one uniform (same geometry for every instance) 2D step.
+struct Step2DArgs {
+    AxisTable tab;
+    const void *fin;      // populations read (post-collision of the last step)
+    void *fout;           // populations written
+    const InstParams *ip; // n_inst entries
+    unsigned *status;     // bit 0: non-positive density / positivity domain left
+    unsigned *step_ctr;   // launches so far: seeds the FP32 dithered rounding
+    unsigned *done_ctr;   // CTAs finished in the current launch
+    int Lx, Ly, pitch, bc;
+    long long plane;      // elements per velocity plane
+    long long inst_stride;// elements per instance
+};
+
+enum { GLBM_MODE_STEP = 0 };
+
+// Launchers (return cudaError_t of the launch).
+cudaError_t glbm_launch_step2d_f32(int N, const Step2DArgs &a, int n_inst, cudaStream_t s);
+cudaError_t glbm_launch_step2d_f64(int N, const Step2DArgs &a, int n_inst, cudaStream_t s);
+
+// Auxiliary kernels (glbm_aux.cu).
+struct AuxArgs {
+    AxisTable tab;
+    const InstParams *ip;
+    int dims, prec;       // prec: 0 = FP64, 1 = FP32 deviations
+    int Lx, Ly, pitch, bc, N;
+    long long plane, inst_stride;
+};
+cudaError_t glbm_launch_set_equilibrium(const AuxArgs &a, void *f, int inst, const double *rho,
+                                        const double *ux, const double *uy, cudaStream_t s);
+cudaError_t glbm_launch_set_populations(const AuxArgs &a, void *f, int inst, const double *src,
+                                        cudaStream_t s);
+cudaError_t glbm_launch_get_populations(const AuxArgs &a, const void *f, int inst, double *dst,
+                                        cudaStream_t s);
+cudaError_t glbm_launch_moments(const AuxArgs &a, const void *f, int inst, double *out,
+                                cudaStream_t s);
+cudaError_t glbm_launch_field_sums(const double *fields, int nfields, long long n, double *partials,
+                                   int nblocks, double *out, cudaStream_t s);
+int glbm_field_sum_blocks(long long n);
+cudaError_t glbm_launch_step1d(const AuxArgs &a, const void *fin, void *fout, int inst,
+                               unsigned *status, cudaStream_t s);
+cudaError_t glbm_launch_run1d_resident(const AuxArgs &a, void *f, int inst, long long steps,
+                                       unsigned *status, cudaStream_t s, int *ok);

@@ -1,0 +1,314 @@
+// Fused pull-stream + BGK collide for the 2D tensor-product Gaussian lattices
+// (Sec. 2, Eq. maineq01, product equilibrium of Sec. 4), with the diffuse
+// walls' density computed in a CTA prologue and the linearised body force
+// (Sec. 5.4).
+//
+// One CTA covers a tile of 32 columns x R rows of one instance. Each node's
+// (2N+1)^2 populations are split by velocity row (ny) over G warps, so a
+// thread holds at most ceil((2N+1)/G) * (2N+1) values in registers:
+//   phase 0 (CTAs touching a wall): per column, the mass streaming into each
+//           wall is summed from the previous post-collision state and turned
+//           into the wall density rho_w(x) (emission balances absorption);
+//   phase 1: pull every population f_i(x - xi_i) (coalesced 32-wide loads per
+//           velocity plane, periodic wrap in x; sources inside a wall take the
+//           wall's re-emitted value rho_w(x) E^x_i(u_w) W^y_i), then partial
+//           moments (density and momentum) per velocity row;
+//   phase 2: partial moments exchanged through shared memory (fixed order),
+//           u = j / rho, equilibrium polynomials by Horner, relaxation plus
+//           force, and a coalesced store of each population at its own node.
+// FP32 mode stores deviations delta f = f - W (rest density 1) and adds the
+// moments with compensated row sums; FP64 mode stores f.
+#pragma once
+#include "glbm_device.cuh"
+
+template <int N, typename T, int G, int R>
+struct Step2D {
+    static constexpr int Q1 = 2 * N + 1;
+    static constexpr int RPG = (Q1 + G - 1) / G;  // velocity rows per warp group
+    static constexpr int NW = G * R;              // warps per CTA
+    static constexpr int NT = 32 * NW;
+    static constexpr bool DEV = sizeof(T) == 4;   // FP32 deviation storage
+    using A = TabAcc<T>;
+
+    struct Smem {
+        T part[R][G][6][32];  // (s, c) pairs of delta rho, j_x, j_y per row and group
+        T rw[2][32];          // wall density (FP64) or its deviation (FP32): lo, hi
+        T dsum[NW][2][32];    // per-warp partial wall fluxes
+    };
+
+    __device__ static void run(const Step2DArgs &a, const InstParams &ip,
+                               const T *__restrict__ fin, T *__restrict__ fout, int x0, int y0,
+                               Smem &sm, unsigned *status, unsigned seed)
+    {
+        const int lane = threadIdx.x & 31;
+        const int w = threadIdx.x >> 5;
+        const int g = w % G;
+        const int r = w / G;
+        const int Lx = a.Lx, Ly = a.Ly, pitch = a.pitch;
+        const int plane = (int)a.plane;  // instance offsets fit 31 bits (checked at creation)
+        const bool walls = a.bc == GLBM_BC_WALLS;
+        const int x = x0 + lane, y = y0 + r;
+        const bool active = (x < Lx) && (y < Ly);
+        const int xc = x < Lx ? x : Lx - 1;
+        const int yc = y < Ly ? y : Ly - 1;
+
+        // offset of velocity column ix's plane plus its periodic source column
+        int cofs[Q1];
+#pragma unroll
+        for (int ix = 0; ix < Q1; ++ix) cofs[ix] = ix * plane + wrap_index(xc - (ix - N), Lx);
+
+        // ---- phase 0: wall densities of this tile's columns ---------------
+        const bool need_lo = walls && (y0 < N);
+        const bool need_hi = walls && (y0 + R > Ly - N);
+        if (need_lo || need_hi) {
+            T slo = T(0), shi = T(0);
+            int p = 0;
+#pragma unroll
+            for (int aa = 1; aa <= N; ++aa) {
+#pragma unroll
+                for (int k = 0; k < aa; ++k, ++p) {
+                    if (p % NW != w) continue;
+                    if (need_lo) {  // velocity ny = -aa leaving row k through y = -1/2
+                        const T *pl = fin + ((N - aa) * Q1 * plane + k * pitch);
+#pragma unroll
+                        for (int ix = 0; ix < Q1; ++ix) slo += __ldg(pl + cofs[ix]);
+                    }
+                    if (need_hi) {  // velocity ny = +aa leaving row Ly-1-k through y = Ly-1/2
+                        const T *ph = fin + ((N + aa) * Q1 * plane + (Ly - 1 - k) * pitch);
+#pragma unroll
+                        for (int ix = 0; ix < Q1; ++ix) shi += __ldg(ph + cofs[ix]);
+                    }
+                }
+            }
+            sm.dsum[w][0][lane] = slo;
+            sm.dsum[w][1][lane] = shi;
+            __syncthreads();
+            if (w == 0) {
+                T s0 = T(0), s1 = T(0);
+                for (int j = 0; j < NW; ++j) {
+                    s0 += sm.dsum[j][0][lane];
+                    s1 += sm.dsum[j][1][lane];
+                }
+                const T inv_den = DEV ? (T)ip.inv_den_f : (T)ip.inv_den;
+                // FP64: rho_w = D / den.  FP32: rho_w - 1 = (D - den) / den, and
+                // D - den is the sum of the absorbed deviations.
+                sm.rw[0][lane] = s0 * inv_den;
+                sm.rw[1][lane] = s1 * inv_den;
+            }
+            __syncthreads();
+        }
+
+        // ---- phase 1: pull and partial moments -----------------------------
+        T f[RPG][Q1];
+        T s_r = T(0), c_r = T(0), s_x = T(0), c_x = T(0), s_y = T(0), c_y = T(0);
+#pragma unroll
+        for (int gi = 0; gi < G; ++gi) {
+            if (g != gi) continue;
+            // loads first, all independent
+#pragma unroll
+            for (int k = 0; k < RPG; ++k) {
+                const int iy = gi + k * G;
+                if (iy < Q1) {
+                    const int ny = iy - N;
+                    int ys = yc - ny;
+                    ys = walls ? min(max(ys, 0), Ly - 1) : wrap_index(ys, Ly);
+                    const T *rowp = fin + (iy * Q1 * plane + ys * pitch);
+#pragma unroll
+                    for (int ix = 0; ix < Q1; ++ix) f[k][ix] = __ldg(rowp + cofs[ix]);
+                }
+            }
+            // wall re-emission and row sums
+#pragma unroll
+            for (int k = 0; k < RPG; ++k) {
+                const int iy = gi + k * G;
+                if (iy < Q1) {
+                    const int ny = iy - N;
+                    const int ys = yc - ny;
+                    if (walls && (ys < 0 || ys >= Ly)) {  // uniform across the warp
+                        const bool lo = ys < 0;
+                        const T wy = A::W(a.tab, iy);
+                        const T rw = sm.rw[lo ? 0 : 1][lane];
+#pragma unroll
+                        for (int ix = 0; ix < Q1; ++ix) {
+                            if (DEV) {
+                                const T dw = lo ? (T)ip.dw_lo_f[ix] : (T)ip.dw_hi_f[ix];
+                                // W^y (drho_w W^x + rho_w (E^x(u_w) - W^x))
+                                f[k][ix] = wy * fma(rw, A::W(a.tab, ix), (T(1) + rw) * dw);
+                            } else {
+                                const T ew = lo ? (T)ip.ew_lo[ix] : (T)ip.ew_hi[ix];
+                                f[k][ix] = rw * ew * wy;
+                            }
+                        }
+                    }
+                    T rs = T(0);
+#pragma unroll
+                    for (int ix = 0; ix < Q1; ++ix) rs += f[k][ix];
+                    T jx = T(0);
+#pragma unroll
+                    for (int n = 1; n <= N; ++n) jx = fma(T(n), f[k][N + n] - f[k][N - n], jx);
+                    acc2(s_r, c_r, rs);
+                    acc2(s_x, c_x, jx);
+                    if (ny != 0) acc2(s_y, c_y, T(ny) * rs);
+                }
+            }
+        }
+        sm.part[r][g][0][lane] = s_r;
+        sm.part[r][g][1][lane] = c_r;
+        sm.part[r][g][2][lane] = s_x;
+        sm.part[r][g][3][lane] = c_x;
+        sm.part[r][g][4][lane] = s_y;
+        sm.part[r][g][5][lane] = c_y;
+        __syncthreads();
+
+        // ---- phase 2: moments, equilibrium, relaxation, store --------------
+        T S_r = T(0), C_r = T(0), S_x = T(0), C_x = T(0), S_y = T(0), C_y = T(0);
+#pragma unroll
+        for (int gi = 0; gi < G; ++gi) {
+            acc2(S_r, C_r, sm.part[r][gi][0][lane]);
+            acc2(S_x, C_x, sm.part[r][gi][2][lane]);
+            acc2(S_y, C_y, sm.part[r][gi][4][lane]);
+            if (DEV) {
+                C_r += sm.part[r][gi][1][lane];
+                C_x += sm.part[r][gi][3][lane];
+                C_y += sm.part[r][gi][5][lane];
+            }
+        }
+        const T m0 = S_r + C_r;            // FP32: delta rho; FP64: rho
+        const T rho = DEV ? T(1) + m0 : m0;
+        const T drho = DEV ? m0 : m0 - T(1);
+        const T inv_rho = T(1) / rho;
+        const T ux = (S_x + C_x) * inv_rho;
+        const T uy = (S_y + C_y) * inv_rho;
+        if (active) {
+            const T umax = (T)(0.816496580927726 * N);  // sqrt(2/3) N: positivity bound (Sec. 3)
+            if (!(rho > T(0)) || !(fabs(ux) <= umax) || !(fabs(uy) <= umax)) atomicOr(status, 1u);
+        }
+
+        T dx[Q1];
+        eq_dev_all<N, T>(a.tab, ux, dx);
+        T ex[Q1];  // FP64 mode: E^x = W + d^x
+#pragma unroll
+        for (int ix = 0; ix < Q1; ++ix) ex[ix] = DEV ? T(0) : A::W(a.tab, ix) + dx[ix];
+        const T om = DEV ? (T)ip.omega_f : (T)ip.omega;
+        const T gto = DEV ? (T)ip.g_theta_om_f : (T)ip.g_theta_om;  // g / (theta omega)
+        T *const obase = fout + (y * pitch + x);
+        // random word of this node and launch for the dithered FP32 stores
+        const unsigned hnode = DEV ? hash32((unsigned)(y * Lx + x) ^ seed) : 0u;
+
+        // f* = f + omega (f^eq + F/omega - f): the relaxation is written as a
+        // correction to f (no rounded (1 - omega) factor biases mass or momentum)
+        // and the force F_i = W^x_i xi_x W^y_i g/theta joins the equilibrium
+        // through the per-row factor gr = W^y g / (theta omega).
+#pragma unroll
+        for (int gi = 0; gi < G; ++gi) {
+            if (g != gi) continue;
+#pragma unroll
+            for (int k = 0; k < RPG; ++k) {
+                const int iy = gi + k * G;
+                if (iy < Q1) {
+                    const int ny = iy - N;
+                    const T wy = A::W(a.tab, iy);
+                    const T dy = eq_dev_one<N, T>(a.tab, uy, ny);
+                    const T rey = rho * (wy + dy);  // rho e^y
+                    const T gr = gto * wy;
+                    // FP32: delta f^eq = d^x rho e^y + W^x (drho W^y + rho d^y)
+                    const T B = DEV ? fma(drho, wy, rho * dy) : T(0);
+                    T *const op = obase + iy * Q1 * plane;
+#pragma unroll
+                    for (int ix = 0; ix < Q1; ++ix) {
+                        const int nx = ix - N;
+                        const T f0 = f[k][ix];
+                        T v;
+                        if (DEV) {
+                            const T Bn = nx != 0 ? fma(T(nx), gr, B) : B;
+                            const T eq = fma(dx[ix], rey, A::W(a.tab, ix) * Bn);
+                            // increment plus dither, then one rounding of the store
+                            const unsigned q = iy * Q1 + ix;
+                            const unsigned rnd = hnode * (0x9E3779B9u * (2u * q + 1u)) + 0x7F4A7C15u * q;
+                            const T inc = fma(om, eq - f0, (T)dither_ulp((float)f0, rnd));
+                            v = f0 + inc;
+                        } else {
+                            T eq = ex[ix] * rey;
+                            if (nx != 0) eq = fma(A::WN(a.tab, ix), gr, eq);
+                            v = fma(om, eq - f0, f0);
+                        }
+                        if (active) op[ix * plane] = v;
+                    }
+                }
+            }
+        }
+    }
+};
+
+template <int N, typename T, int G, int R>
+__global__ void __launch_bounds__(32 * G * R)
+    k_step2d(const __grid_constant__ Step2DArgs a)
+{
+    using S = Step2D<N, T, G, R>;
+    __shared__ typename S::Smem sm;
+    const int inst = blockIdx.z;
+    const T *fin = static_cast<const T *>(a.fin) + (long long)inst * a.inst_stride;
+    T *fout = static_cast<T *>(a.fout) + (long long)inst * a.inst_stride;
+    // launch counter (read before any CTA of this launch can advance it)
+    const unsigned seed = S::DEV ? hash32(__ldcg(a.step_ctr) * 0x632BE5ABu + inst) : 0u;
+    S::run(a, a.ip[inst], fin, fout, blockIdx.x * 32, blockIdx.y * R, sm, a.status, seed);
+    if (S::DEV) {
+        // the last CTA to finish advances the launch counter for the next launch
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            const unsigned total = gridDim.x * gridDim.y * gridDim.z;
+            if (atomicAdd(a.done_ctr, 1u) == total - 1u) {
+                *a.done_ctr = 0u;
+                atomicAdd(a.step_ctr, 1u);
+            }
+        }
+    }
+}
+
+// Warp-group split (G) and rows per CTA (R) per level and precision: about
+// 80 FP32 or 50 FP64 population registers per thread.
+template <int N, typename T>
+struct Tile2D;
+// FP32 deviations
+template <> struct Tile2D<1, float> { static constexpr int G = 1, R = 8; };
+template <> struct Tile2D<2, float> { static constexpr int G = 1, R = 8; };
+template <> struct Tile2D<3, float> { static constexpr int G = 1, R = 4; };
+template <> struct Tile2D<4, float> { static constexpr int G = 1, R = 4; };
+template <> struct Tile2D<5, float> { static constexpr int G = 2, R = 2; };
+template <> struct Tile2D<6, float> { static constexpr int G = 2, R = 2; };
+template <> struct Tile2D<7, float> { static constexpr int G = 3, R = 1; };
+template <> struct Tile2D<8, float> { static constexpr int G = 4, R = 1; };
+// FP64
+template <> struct Tile2D<1, double> { static constexpr int G = 1, R = 8; };
+template <> struct Tile2D<2, double> { static constexpr int G = 1, R = 4; };
+template <> struct Tile2D<3, double> { static constexpr int G = 2, R = 2; };
+template <> struct Tile2D<4, double> { static constexpr int G = 2, R = 2; };
+template <> struct Tile2D<5, double> { static constexpr int G = 3, R = 1; };
+template <> struct Tile2D<6, double> { static constexpr int G = 4, R = 1; };
+template <> struct Tile2D<7, double> { static constexpr int G = 5, R = 1; };
+template <> struct Tile2D<8, double> { static constexpr int G = 6, R = 1; };
+
+template <int N, typename T>
+cudaError_t launch_step2d_n(const Step2DArgs &a, int n_inst, cudaStream_t s)
+{
+    constexpr int G = Tile2D<N, T>::G, R = Tile2D<N, T>::R;
+    dim3 grid((a.Lx + 31) / 32, (a.Ly + R - 1) / R, n_inst);
+    k_step2d<N, T, G, R><<<grid, 32 * G * R, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_step2d(int N, const Step2DArgs &a, int n_inst, cudaStream_t s)
+{
+    switch (N) {
+    case 1: return launch_step2d_n<1, T>(a, n_inst, s);
+    case 2: return launch_step2d_n<2, T>(a, n_inst, s);
+    case 3: return launch_step2d_n<3, T>(a, n_inst, s);
+    case 4: return launch_step2d_n<4, T>(a, n_inst, s);
+    case 5: return launch_step2d_n<5, T>(a, n_inst, s);
+    case 6: return launch_step2d_n<6, T>(a, n_inst, s);
+    case 7: return launch_step2d_n<7, T>(a, n_inst, s);
+    case 8: return launch_step2d_n<8, T>(a, n_inst, s);
+    default: return cudaErrorInvalidValue;
+    }
+}

@@ -1,0 +1,269 @@
+"""Python binding of libglbm (argument marshalling only).
+
+Every step of the lattice Boltzmann path runs in the CUDA library; this
+module converts numpy arrays / torch tensors to pointers, passes torch's
+current CUDA stream, and raises on error statuses. It has no CPU fallback:
+if ``libglbm.so`` is missing or no GPU is present, calls fail loudly.
+
+The C functions and their arguments are documented in ``include/glbm.h``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "libglbm.so")
+
+OK, E_INVAL, E_NOMEM, E_CUDA, E_UNSTABLE, E_TIMEOUT, E_IO, E_UNSUPPORTED = 0, -1, -2, -3, -4, -5, -6, -7
+BC_WALLS, BC_BOUNCEBACK, BC_PERIODIC = 0, 1, 2
+FP64, FP32_DEV = 0, 1
+M_RHO, M_UX, M_UY, M_T, M_QX, M_QY, M_SXY, M_ALL = 1, 2, 4, 8, 16, 32, 64, 127
+FIELDS_2D = ("rho", "ux", "uy", "T", "qx", "qy", "sxy")
+FIELDS_1D = ("rho", "ux", "T", "qx")
+
+
+class GlbmError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"glbm status {status}: {msg}")
+        self.status = status
+
+
+class UnstableError(GlbmError):
+    pass
+
+
+class Config(ctypes.Structure):
+    _fields_ = [("dims", ctypes.c_int), ("nx", ctypes.c_int), ("ny", ctypes.c_int),
+                ("k", ctypes.c_int), ("tau", ctypes.c_double), ("kn", ctypes.c_double),
+                ("bc", ctypes.c_int), ("prec", ctypes.c_int), ("u_wall_lo", ctypes.c_double),
+                ("u_wall_hi", ctypes.c_double), ("g", ctypes.c_double)]
+
+
+_lib = None
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p)
+
+
+def lib():
+    """Load libglbm.so; raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                           "`python -m paper_1905_04597_gb300.build` (no CPU fallback exists)")
+    L = ctypes.CDLL(LIB_PATH)
+    vp, dp, cp = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(Config)
+    i, i64, sz = ctypes.c_int, ctypes.c_int64, ctypes.c_size_t
+    sig = {
+        "glbm_create": ([cp, i, vp, ctypes.POINTER(vp)], i),
+        "glbm_batch_create": ([cp, i, vp, ctypes.POINTER(vp)], i),
+        "glbm_destroy": ([vp], None),
+        "glbm_set_allocator": ([ALLOC_FN, FREE_FN, vp], i),
+        "glbm_set_equilibrium": ([vp, i, vp, vp, vp, i], i),
+        "glbm_set_populations": ([vp, i, vp, i], i),
+        "glbm_get_populations": ([vp, i, vp, i], i),
+        "glbm_step": ([vp, i64], i),
+        "glbm_sync": ([vp], i),
+        "glbm_moments": ([vp, i, ctypes.c_uint, vp, sz, i], i),
+        "glbm_conservation": ([vp, i, dp, dp, dp], i),
+        "glbm_save": ([vp, ctypes.c_char_p], i),
+        "glbm_load": ([vp, ctypes.c_char_p], i),
+        "glbm_time": ([vp], i64),
+        "glbm_kernel_launches": ([vp], i64),
+        "glbm_tau": ([vp, i], ctypes.c_double),
+        "glbm_eq_table": ([i, dp, sz], i),
+        "glbm_last_error": ([], ctypes.c_char_p),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(L, name)
+        fn.argtypes = args
+        fn.restype = res
+    _lib = L
+    return L
+
+
+def check(status):
+    if status == OK:
+        return
+    msg = lib().glbm_last_error().decode(errors="replace")
+    if status == E_UNSTABLE:
+        raise UnstableError(status, msg)
+    raise GlbmError(status, msg)
+
+
+def eq_table(k: int) -> np.ndarray:
+    """Coefficients C[n][j] of E_n(u) = sum_j C[n][j] u^j at level k+1."""
+    Q1 = 2 * k + 3
+    out = np.empty((Q1, Q1))
+    check(lib().glbm_eq_table(k, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), out.size))
+    return out
+
+
+def make_config(dims=2, nx=1, ny=1, k=0, tau=0.0, kn=0.0, bc=None, prec=FP64, u_wall_lo=0.0,
+                u_wall_hi=0.0, g=0.0) -> Config:
+    if bc is None:
+        bc = BC_WALLS if dims == 2 else BC_BOUNCEBACK
+    return Config(dims, nx, ny if dims == 2 else 1, k, tau, kn, bc, prec, u_wall_lo, u_wall_hi, g)
+
+
+_torch_alloc_refs = None
+
+
+def install_torch_allocator():
+    """Back later glbm_create calls with torch's CUDA caching allocator."""
+    global _torch_alloc_refs
+    import torch
+
+    def _alloc(nbytes, stream, user):
+        try:
+            return torch.cuda.caching_allocator_alloc(int(nbytes), torch.cuda.current_device(),
+                                                      stream or 0)
+        except Exception:
+            return None
+
+    def _free(ptr, stream, user):
+        torch.cuda.caching_allocator_delete(ptr)
+
+    a, f = ALLOC_FN(_alloc), FREE_FN(_free)
+    check(lib().glbm_set_allocator(a, f, None))
+    _torch_alloc_refs = (a, f)
+
+
+def uninstall_allocator():
+    global _torch_alloc_refs
+    check(lib().glbm_set_allocator(ALLOC_FN(), FREE_FN(), None))
+    _torch_alloc_refs = None
+
+
+def _current_stream():
+    import torch
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _ptr(a):
+    """(pointer, on_device) of a contiguous float64 numpy array or torch tensor."""
+    if isinstance(a, np.ndarray):
+        if a.dtype != np.float64 or not a.flags["C_CONTIGUOUS"]:
+            raise TypeError("expected a C-contiguous float64 array")
+        return ctypes.c_void_p(a.ctypes.data), 0
+    import torch
+    if isinstance(a, torch.Tensor):
+        if a.dtype != torch.float64 or not a.is_contiguous():
+            raise TypeError("expected a contiguous float64 tensor")
+        return ctypes.c_void_p(a.data_ptr()), 1 if a.is_cuda else 0
+    raise TypeError(f"unsupported array type {type(a)}")
+
+
+class Lattice:
+    """One or more lattice instances stepped together by libglbm."""
+
+    def __init__(self, configs, stream=None, hetero=False):
+        if isinstance(configs, (Config, dict)):
+            configs = [configs]
+        cfgs = [c if isinstance(c, Config) else make_config(**c) for c in configs]
+        arr = (Config * len(cfgs))(*cfgs)
+        self.configs = cfgs
+        self.n = len(cfgs)
+        self.dims = cfgs[0].dims
+        self._stream = stream if stream is not None else _current_stream()
+        h = ctypes.c_void_p()
+        create = lib().glbm_batch_create if hetero else lib().glbm_create
+        check(create(arr, len(cfgs), self._stream, ctypes.byref(h)))
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().glbm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def nodes(self, inst=0):
+        c = self.configs[inst]
+        return c.nx * (c.ny if c.dims == 2 else 1)
+
+    def nq(self, inst=0):
+        c = self.configs[inst]
+        q1 = 2 * c.k + 3
+        return q1 * q1 if c.dims == 2 else q1
+
+    def shape(self, inst=0):
+        c = self.configs[inst]
+        return (c.ny, c.nx) if c.dims == 2 else (c.nx,)
+
+    def set_equilibrium(self, inst, rho, ux, uy=None):
+        pr, dev = _ptr(rho)
+        pu, _ = _ptr(ux)
+        pv = _ptr(uy)[0] if uy is not None else ctypes.c_void_p()
+        check(lib().glbm_set_equilibrium(self.h, inst, pr, pu, pv, dev))
+
+    def set_populations(self, inst, f):
+        p, dev = _ptr(f)
+        check(lib().glbm_set_populations(self.h, inst, p, dev))
+
+    def get_populations(self, inst=0, out=None):
+        if out is None:
+            out = np.empty((self.nq(inst),) + self.shape(inst))
+        p, dev = _ptr(out)
+        check(lib().glbm_get_populations(self.h, inst, p, dev))
+        return out
+
+    def step(self, n=1):
+        check(lib().glbm_step(self.h, int(n)))
+
+    def sync(self):
+        check(lib().glbm_sync(self.h))
+
+    def moments(self, inst=0, mask=M_ALL, out=None):
+        """Moments of S(X) at the current time; returns a dict of arrays (host) or
+        fills `out` (numpy or torch, host or device) packed in field order."""
+        fields = FIELDS_2D if self.dims == 2 else FIELDS_1D
+        bits = [1, 2, 4, 8, 16, 32, 64] if self.dims == 2 else [1, 2, 8, 16]
+        names = [f for f, b in zip(fields, bits) if mask & b]
+        if self.dims == 1:
+            mask &= M_RHO | M_UX | M_T | M_QX
+        if out is None:
+            out = np.empty((len(names),) + self.shape(inst))
+        p, dev = _ptr(out)
+        n_el = out.size if isinstance(out, np.ndarray) else out.numel()
+        check(lib().glbm_moments(self.h, inst, mask, p, n_el, dev))
+        if isinstance(out, np.ndarray):
+            return {k: out[i] for i, k in enumerate(names)}
+        return out
+
+    def conservation(self, inst=0):
+        m, jx, jy = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        check(lib().glbm_conservation(self.h, inst, ctypes.byref(m), ctypes.byref(jx),
+                                      ctypes.byref(jy)))
+        return m.value, jx.value, jy.value
+
+    def save(self, path):
+        check(lib().glbm_save(self.h, str(path).encode()))
+
+    def load(self, path):
+        check(lib().glbm_load(self.h, str(path).encode()))
+
+    @property
+    def time(self):
+        return lib().glbm_time(self.h)
+
+    @property
+    def kernel_launches(self):
+        return lib().glbm_kernel_launches(self.h)
+
+    def tau(self, inst=0):
+        return lib().glbm_tau(self.h, inst)

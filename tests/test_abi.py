@@ -1,0 +1,72 @@
+"""The C-ABI library loads, exports every symbol include/glbm.h declares, and its
+host-side pieces (equilibrium-coefficient table, Kn mapping inputs, error
+paths) agree with the oracle -- no GPU needed."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from oracle import oracle as orc
+from paper_1905_04597_gb300 import glbm
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "glbm.h")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    import __graft_entry__
+    __graft_entry__.build_library()
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(glbm_[a-z0-9_]+)\s*\(", text)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for must in ("glbm_create", "glbm_step", "glbm_moments", "glbm_destroy", "glbm_conservation",
+                 "glbm_save", "glbm_load", "glbm_batch_create", "glbm_last_error"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol():
+    L = ctypes.CDLL(glbm.LIB_PATH)
+    missing = [n for n in declared_functions() if not hasattr(L, n)]
+    assert not missing, missing
+
+
+@pytest.mark.parametrize("k", range(0, 8))
+def test_coefficient_table_matches_oracle(k):
+    """Row a1: the convolution-built polynomial table reproduces the factorial-sum
+    equilibrium of the oracle at any velocity (Sec. 2, Eqs. maineq03-05)."""
+    N = k + 1
+    C = glbm.eq_table(k)
+    rng = np.random.default_rng(k)
+    for u in np.concatenate([[0.0, 0.05, -0.3], rng.uniform(-0.8, 0.8, 5)]):
+        E = np.array([np.polyval(C[i, ::-1], u) for i in range(2 * N + 1)])
+        np.testing.assert_allclose(E, orc.eq1d(N, u), rtol=1e-13, atol=1e-15)
+    np.testing.assert_allclose(C[:, 0], orc.weights(N), rtol=1e-9, atol=1e-15)
+
+
+def test_table_rejects_bad_level():
+    with pytest.raises(glbm.GlbmError):
+        glbm.eq_table(8)
+
+
+def test_invalid_config_is_rejected_before_any_device_call():
+    cfg = glbm.make_config(dims=2, nx=8, ny=2, k=3, tau=1.0)  # walls need ny >= 4
+    h = ctypes.c_void_p()
+    st = glbm.lib().glbm_create(ctypes.byref(cfg), 1, None, ctypes.byref(h))
+    assert st == glbm.E_INVAL and not h.value
+    assert b"ny" in glbm.lib().glbm_last_error()
+    cfg = glbm.make_config(dims=2, nx=8, ny=8, k=9, tau=1.0)
+    assert glbm.lib().glbm_create(ctypes.byref(cfg), 1, None, ctypes.byref(h)) == glbm.E_UNSUPPORTED
+    cfg = glbm.make_config(dims=2, nx=8, ny=8, k=1, tau=-1.0)
+    assert glbm.lib().glbm_create(ctypes.byref(cfg), 1, None, ctypes.byref(h)) == glbm.E_INVAL
+    cfg = glbm.make_config(dims=2, nx=8, ny=8, k=0, tau=1.0, u_wall_lo=0.9)  # > sqrt(2/3)
+    assert glbm.lib().glbm_create(ctypes.byref(cfg), 1, None, ctypes.byref(h)) == glbm.E_INVAL
