@@ -158,6 +158,38 @@ glbm_status glbm_moments(glbm_ctx *ctx, int inst, unsigned mask, double *out, si
 glbm_status glbm_conservation(glbm_ctx *ctx, int inst, double *mass, double *mom_x,
                               double *mom_y);
 
+/*
+ * Conservation sums without allocation. The paper has no counterpart: this is
+ * a runtime convenience. It computes the same deterministic sums as
+ * glbm_conservation (total mass, x- and y-momentum: sum rho, sum rho u_x,
+ * sum rho u_y), but it owns no context and allocates nothing. The block
+ * partials go to a static 24 KiB array in the library's device memory.
+ *
+ * It is for callers that may not call cudaMalloc: code running while a
+ * stream is captured into a CUDA graph (allocation is not a stream operation
+ * and would break the capture), real-time loops that cannot take the
+ * allocator's device-wide synchronisation, and applications whose memory pool
+ * owns all device memory.
+ *
+ *   fields  device pointer to the moment fields as glbm_moments writes them
+ *           with mask GLBM_M_RHO | GLBM_M_UX | GLBM_M_UY: rho, u_x, u_y (2D,
+ *           dims = 2) or rho, u_x (1D, dims = 1), each `nodes` doubles.
+ *   nodes   1 .. GLBM_NOALLOC_MAX_NODES; larger counts return GLBM_E_INVAL.
+ *   sums    device pointer to 3 doubles: mass, x-momentum, y-momentum
+ *           (0 in 1D).
+ *   stream  cudaStream_t; the call is asynchronous on it.
+ *
+ * The first call on a device looks up the scratch's device address, and it
+ * should come before any stream capture. Every call shares the one scratch
+ * array, which keeps the last call's contents. Nothing in it needs clearing,
+ * because each call overwrites every partial it reads. Calls that overlap on
+ * the GPU (different streams, or the same graph launched concurrently) race
+ * on the scratch and must be serialised by the caller.
+ */
+#define GLBM_NOALLOC_MAX_NODES (4096LL * 1024LL)
+glbm_status glbm_conservation_noalloc(const double *fields, int dims, int64_t nodes, double *sums,
+                                      void *stream);
+
 /* Checkpoint of every instance's state (header, raw device image, CRC-32).
  * glbm_load requires a context created with the same configuration. */
 glbm_status glbm_save(glbm_ctx *ctx, const char *path);

@@ -25,6 +25,15 @@ static glbm_status fail(glbm_status st, const char *fmt, ...)
     return st;
 }
 
+glbm_status glbm_set_error(glbm_status st, const char *fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+    return st;
+}
+
 #define CUDA_TRY(call)                                                                    \
     do {                                                                                  \
         cudaError_t e_ = (call);                                                          \

@@ -4,6 +4,8 @@
 // stress as central moments), deterministic global sums, and the 1D step
 // (Sec. 5.1 shock tube, halfway bounce-back) both per launch and resident in
 // one CTA for many steps.
+#include <mutex>
+
 #include "glbm_device.cuh"
 
 namespace {
@@ -460,4 +462,57 @@ cudaError_t glbm_launch_run1d_resident(const AuxArgs &a, void *f, int inst, long
 {
     if (a.prec == GLBM_FP64) return launch_resident_t<double>(a, f, inst, steps, status, s, ok);
     return launch_resident_t<float>(a, f, inst, steps, status, s, ok);
+}
+
+// ---------------------------------------------------------------------------
+// Conservation sums without allocation (glbm_conservation_noalloc).
+//
+// The block partials of the deterministic sum live in this file-scope device
+// array instead of context memory, for callers that may not allocate device
+// memory. Every GPU that loads the library holds it (24 KiB) until the process
+// exits, and every call shares it.
+// ---------------------------------------------------------------------------
+#define GLBM_NOALLOC_MAX_BLOCKS 1024
+static __device__ __align__(256) double g_noalloc_partials[3 * GLBM_NOALLOC_MAX_BLOCKS];
+
+static std::mutex g_noalloc_mu;
+static void *g_noalloc_ptr[64];  // device address of g_noalloc_partials, per device
+
+extern "C" glbm_status glbm_conservation_noalloc(const double *fields, int dims, int64_t nodes,
+                                                 double *sums, void *stream)
+{
+    if (!fields || !sums) return glbm_set_error(GLBM_E_INVAL, "null fields or sums");
+    if (dims != 1 && dims != 2) return glbm_set_error(GLBM_E_INVAL, "dims must be 1 or 2");
+    if (nodes < 1 || nodes > GLBM_NOALLOC_MAX_NODES)
+        return glbm_set_error(GLBM_E_INVAL,
+                              "glbm_conservation_noalloc takes 1 to %lld nodes (got %lld): its "
+                              "static scratch holds %d block partials of 4096 nodes",
+                              (long long)GLBM_NOALLOC_MAX_NODES, (long long)nodes,
+                              GLBM_NOALLOC_MAX_BLOCKS);
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return glbm_set_error(GLBM_E_CUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
+    if (dev < 0 || dev >= 64) return glbm_set_error(GLBM_E_UNSUPPORTED, "device index %d >= 64", dev);
+    void *scratch = nullptr;
+    {
+        // set-up once per device, with that device current: in host code the
+        // array's name is only a stand-in, its device address comes from here
+        std::lock_guard<std::mutex> lock(g_noalloc_mu);
+        if (!g_noalloc_ptr[dev]) {
+            e = cudaGetSymbolAddress(&g_noalloc_ptr[dev], g_noalloc_partials);
+            if (e != cudaSuccess) {
+                g_noalloc_ptr[dev] = nullptr;
+                return glbm_set_error(GLBM_E_CUDA, "cudaGetSymbolAddress of the scratch: %s",
+                                      cudaGetErrorString(e));
+            }
+        }
+        scratch = g_noalloc_ptr[dev];
+    }
+    // every block writes all three of its partials before the final pass reads
+    // them, so nothing has to be cleared between calls
+    const int nblocks = glbm_field_sum_blocks(nodes);
+    e = glbm_launch_field_sums(fields, dims == 2 ? 3 : 2, nodes, static_cast<double *>(scratch),
+                               nblocks, sums, static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return glbm_set_error(GLBM_E_CUDA, "launch: %s", cudaGetErrorString(e));
+    return GLBM_OK;
 }

@@ -5,6 +5,11 @@
 #include <stddef.h>
 #include <stdint.h>
 
+#include "../../include/glbm.h"
+
+// Record the thread's error message (glbm_last_error) and return `st`.
+glbm_status glbm_set_error(glbm_status st, const char *fmt, ...);
+
 #define GLBM_MAXN 8                       // highest level N = k + 1 compiled
 #define GLBM_MAXQ1 (2 * GLBM_MAXN + 1)    // velocities per axis at GLBM_MAXN
 

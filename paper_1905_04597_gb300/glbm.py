@@ -76,6 +76,7 @@ def lib():
         "glbm_kernel_launches": ([vp], i64),
         "glbm_tau": ([vp, i], ctypes.c_double),
         "glbm_eq_table": ([i, dp, sz], i),
+        "glbm_conservation_noalloc": ([vp, i, i64, vp, vp], i),
         "glbm_last_error": ([], ctypes.c_char_p),
     }
     for name, (args, res) in sig.items():
