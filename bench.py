@@ -46,6 +46,9 @@ def workload(name):
         c = inputs.POISEUILLE
         cfgs = [dict(dims=2, nx=c["nx"], ny=c["ny"], k=c["k"], kn=kn, g=c["g"]) for kn in c["kn"]]
         label = "poiseuille_d2q289_1024x128_kn8"
+    elif name == "batched":
+        cfgs = [dict(dims=2, **r) for r in inputs.batched_instances(seed=0)]
+        label = "batched_256_channels_k1-7_ny32-512_nx64"
     elif name == "sod":
         c = inputs.SOD
         cfgs = [dict(dims=1, nx=c["nx"], k=c["k"], kn=c["kn"])]
@@ -144,6 +147,19 @@ def run_ours(args):
         torch.distributed.barrier()
     from paper_1905_04597_gb300 import glbm
 
+    if args.workload == "batched":
+        res = measure_batched(steps32=args.steps, steps64=max(args.steps // 8, 8),
+                              warmup=args.warmup)
+        if rank == 0:
+            b = res["fp32_batched"]
+            print(json.dumps({"metric": METRIC, "value": b["pop_updates_per_s"], "unit": UNIT,
+                              "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+                              "ms_per_step": b["ms_per_step"], "higher_is_better": True,
+                              "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                              "data": "synthetic",
+                              "config": {"workload": "batched_256_channels_k1-7_ny32-512_nx64"},
+                              "batched": res, "gpu_launches": int(args.steps)}), flush=True)
+        return
     cfgs, label = workload(args.workload)
     dims = cfgs[0]["dims"]
     N = cfgs[0]["k"] + 1
@@ -226,6 +242,8 @@ def run_ours(args):
                "lb_steps_per_step": lb_per_call,
                "call": "glbm_set_equilibrium(host) x3 + glbm_step(100) + glbm_moments(host) x3"}
 
+    batched = measure_batched() if (args.workload == "couette" and not args.no_batched) else None
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         cpu = cpu_baseline(args.workload, budget_s=args.cpu_seconds)
@@ -250,12 +268,64 @@ def run_ours(args):
         "gpu_launches": launches,
         "clocks": clocks,
         "e2e": e2e,
+        "batched": batched,
         "cpu_baseline": cpu,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+STEPS_PER_SOLVE = 2000  # a channel solve of the batched workload
+
+
+def measure_batched(steps32=256, steps64=64, warmup=8):
+    """Solves/s of the 256-instance heterogeneous batch in FP32 (one persistent
+    launch per step) against the same instances in FP64, one context (and one
+    launch per step) per instance."""
+    import torch
+    from paper_1905_04597_gb300 import glbm, inputs
+    recipe = inputs.batched_instances(seed=0)
+    pops = sum((2 * r["k"] + 3) ** 2 * r["nx"] * r["ny"] for r in recipe)
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    lat = glbm.Lattice([dict(dims=2, prec=glbm.FP32_DEV, **r) for r in recipe], hetero=True)
+    lat.step(warmup)
+    lat.sync()
+    l0 = lat.kernel_launches
+    torch.cuda.synchronize()
+    e0.record(stream)
+    lat.step(steps32)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms32 = e0.elapsed_time(e1)
+    launches32 = lat.kernel_launches - l0
+    lat.close()
+    singles = [glbm.Lattice(dict(dims=2, prec=glbm.FP64, **r)) for r in recipe]
+    for x in singles:
+        x.step(2)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for x in singles:
+        x.step(steps64)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms64 = e0.elapsed_time(e1)
+    for x in singles:
+        x.close()
+    sps32 = steps32 / (ms32 / 1e3)          # steps/s of all 256 instances
+    sps64 = steps64 / (ms64 / 1e3)
+    n = len(recipe)
+    return {"instances": n, "pop_updates_per_step": pops,
+            "fp32_batched": {"solves_per_s": n * sps32 / STEPS_PER_SOLVE,
+                             "pop_updates_per_s": pops * sps32, "ms_per_step": ms32 / steps32,
+                             "launches_per_step": launches32 / steps32},
+            "fp64_one_instance_per_launch": {"solves_per_s": n * sps64 / STEPS_PER_SOLVE,
+                                             "pop_updates_per_s": pops * sps64,
+                                             "ms_per_step": ms64 / steps64,
+                                             "launches_per_step": n},
+            "speedup": sps32 / sps64, "steps_per_solve": STEPS_PER_SOLVE}
 
 
 def cpu_baseline(name, budget_s=15.0, steps=None):
@@ -347,9 +417,11 @@ def main():
     ap.add_argument("--steps", type=int, default=20000)
     ap.add_argument("--warmup", type=int, default=200)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="couette", choices=["couette", "poiseuille", "sod"])
+    ap.add_argument("--workload", default="couette",
+                    choices=["couette", "poiseuille", "sod", "batched"])
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")

@@ -1,10 +1,18 @@
 // C ABI of libglbm (include/glbm.h): contexts, device buffers, the step loop
 // with CUDA-graph replay, moments, conservation sums and checkpoints.
+//
+// A context holds n lattice instances in one pool of device memory (two
+// copies: ping-pong). Every instance has its own geometry record (level,
+// nodes, pitch, offset into the pool). A uniform context (every instance
+// alike) is stepped by one launch of the tile kernel with the instance as the
+// grid's third dimension; a heterogeneous one by a persistent kernel over a
+// work list of (instance, tile) items.
 #include <math.h>
 #include <stdarg.h>
 #include <stdio.h>
 #include <string.h>
 
+#include <algorithm>
 #include <new>
 #include <vector>
 
@@ -16,15 +24,6 @@
 // ---------------------------------------------------------------------------
 static thread_local char g_err[512] = "";
 
-static glbm_status fail(glbm_status st, const char *fmt, ...)
-{
-    va_list ap;
-    va_start(ap, fmt);
-    vsnprintf(g_err, sizeof(g_err), fmt, ap);
-    va_end(ap);
-    return st;
-}
-
 glbm_status glbm_set_error(glbm_status st, const char *fmt, ...)
 {
     va_list ap;
@@ -33,6 +32,7 @@ glbm_status glbm_set_error(glbm_status st, const char *fmt, ...)
     va_end(ap);
     return st;
 }
+#define fail glbm_set_error
 
 #define CUDA_TRY(call)                                                                    \
     do {                                                                                  \
@@ -87,20 +87,29 @@ static void dev_free(const DevAlloc &A, void *p, cudaStream_t s)
 // ---------------------------------------------------------------------------
 // context
 // ---------------------------------------------------------------------------
+struct Geo {
+    int N, Lx, Ly, pitch, Q;
+    long long plane;  // elements per velocity plane
+    long long off;    // element offset of the instance in the pool
+    long long nodes() const { return (long long)Lx * Ly; }
+};
+
 struct glbm_ctx {
     int n_inst = 0;
-    int dims = 2, N = 1, Lx = 1, Ly = 1, pitch = 32, bc = 0, prec = 0;
-    int k = 0;
+    int dims = 2, prec = 0;
+    bool hetero = false;
     size_t elem = 8;
-    long long plane = 0, inst_stride = 0;
-    AxisTable tab;
+    std::vector<Geo> geo;
+    std::vector<glbm_config> cfg;
+    std::vector<AxisTable> tabs;  // index N (1..GLBM_MAXN)
     std::vector<InstParams> h_ip;
     std::vector<double> tau;
     DevAlloc A{};
     cudaStream_t stream = nullptr;
     cudaStream_t cap = nullptr;  // private stream used only for graph capture
+    long long pool_elems = 0;    // elements per buffer
     void *buf[2] = {nullptr, nullptr};
-    int cur = 0;  // buffer holding X_t
+    int cur = 0;                 // buffer holding X_t
     InstParams *d_ip = nullptr;
     unsigned *d_status = nullptr;  // [0] status flags, [1] launch counter, [2] CTAs done
     unsigned *h_status = nullptr;  // pinned copy, refreshed after every glbm_step
@@ -109,7 +118,9 @@ struct glbm_ctx {
     double *d_sums = nullptr;      // 3 sums
     double *d_stage = nullptr;     // staging of host inputs
     size_t stage_len = 0;
-    int sum_blocks = 1;
+    int4 *d_items = nullptr;       // heterogeneous work list, sorted by level
+    int n_items = 0;
+    int group[GLBM_MAXN + 2] = {0};  // first item of each level
     cudaGraphExec_t graph[2] = {nullptr, nullptr};  // chunk graphs by starting buffer
     int64_t t = 0;
     int64_t launches = 0;
@@ -118,17 +129,19 @@ struct glbm_ctx {
 
 static const int kGraphChunk = 64;  // steps per captured graph (even: keeps buffer parity)
 
-static size_t bytes_state(const glbm_ctx *c) { return (size_t)c->n_inst * c->inst_stride * c->elem; }
+static size_t bytes_state(const glbm_ctx *c) { return (size_t)c->pool_elems * c->elem; }
 
-static void fill_inst(glbm_ctx *c, const glbm_config &cfg, InstParams &ip, double tau)
+static void fill_inst(const glbm_ctx *c, const glbm_config &cfg, const Geo &g, InstParams &ip,
+                      double tau)
 {
     memset(&ip, 0, sizeof(ip));
-    const int N = c->N;
+    const int N = g.N;
+    const AxisTable &tab = c->tabs[N];
     const double theta = N / 3.0;
     ip.omega = 1.0 / (tau + 0.5);
     ip.g_theta = c->dims == 2 ? cfg.g / theta : 0.0;
     double den = 0.0;
-    for (int n = 1; n <= N; ++n) den += n * c->tab.W[n + N];
+    for (int n = 1; n <= N; ++n) den += n * tab.W[n + N];
     ip.inv_den = 1.0 / den;
     // E^x_n(u_w) from the coefficient table (FP64 Horner)
     double full[GLBM_MAXQ1 * GLBM_MAXQ1];
@@ -158,11 +171,12 @@ static void fill_inst(glbm_ctx *c, const glbm_config &cfg, InstParams &ip, doubl
     ip.g_theta_om_f = (float)ip.g_theta_om;
     ip.inv_den_f = (float)ip.inv_den;
     ip.N = N;
-    ip.Lx = c->Lx;
-    ip.Ly = c->Ly;
-    ip.pitch = c->pitch;
-    ip.bc = c->bc;
-    ip.plane = c->plane;
+    ip.Lx = g.Lx;
+    ip.Ly = g.Ly;
+    ip.pitch = g.pitch;
+    ip.bc = cfg.bc;
+    ip.off = g.off;
+    ip.plane = g.plane;
 }
 
 static glbm_status validate(const glbm_config &c)
@@ -201,13 +215,27 @@ static double tau_of(const glbm_config &c)
     return c.tau;
 }
 
+static Geo make_geo(const glbm_config &c)
+{
+    Geo g;
+    g.N = c.k + 1;
+    g.Lx = c.nx;
+    g.Ly = c.dims == 2 ? c.ny : 1;
+    g.pitch = ((g.Lx + 31) / 32) * 32;
+    const int Q1 = 2 * g.N + 1;
+    g.Q = c.dims == 2 ? Q1 * Q1 : Q1;
+    g.plane = (long long)g.Ly * g.pitch;
+    g.off = 0;
+    return g;
+}
+
 static void destroy_resources(glbm_ctx *c)
 {
     for (int i = 0; i < 2; ++i) {
         if (c->graph[i]) cudaGraphExecDestroy(c->graph[i]);
         c->graph[i] = nullptr;
     }
-    if (c->stream || c->cap) cudaStreamSynchronize(c->stream);
+    cudaStreamSynchronize(c->stream);
     dev_free(c->A, c->buf[0], c->stream);
     dev_free(c->A, c->buf[1], c->stream);
     dev_free(c->A, c->d_ip, c->stream);
@@ -216,26 +244,35 @@ static void destroy_resources(glbm_ctx *c)
     dev_free(c->A, c->d_part, c->stream);
     dev_free(c->A, c->d_sums, c->stream);
     dev_free(c->A, c->d_stage, c->stream);
+    dev_free(c->A, c->d_items, c->stream);
     if (c->h_status) cudaFreeHost(c->h_status);
     if (c->cap) cudaStreamDestroy(c->cap);
 }
 
-static AuxArgs aux_args(const glbm_ctx *c)
+// Arguments of the auxiliary kernels for one instance: the pool pointer is
+// advanced to the instance and the kernels are called with instance 0.
+static AuxArgs aux_args(const glbm_ctx *c, int inst)
 {
+    const Geo &g = c->geo[inst];
     AuxArgs a;
     memset(&a, 0, sizeof(a));
-    a.tab = c->tab;
-    a.ip = c->d_ip;
+    a.tab = c->tabs[g.N];
+    a.ip = c->d_ip + inst;
     a.dims = c->dims;
     a.prec = c->prec;
-    a.Lx = c->Lx;
-    a.Ly = c->Ly;
-    a.pitch = c->pitch;
-    a.bc = c->bc;
-    a.N = c->N;
-    a.plane = c->plane;
-    a.inst_stride = c->inst_stride;
+    a.Lx = g.Lx;
+    a.Ly = g.Ly;
+    a.pitch = g.pitch;
+    a.bc = c->cfg[inst].bc;
+    a.N = g.N;
+    a.plane = g.plane;
+    a.inst_stride = 0;
     return a;
+}
+
+static void *inst_ptr(const glbm_ctx *c, int b, int inst)
+{
+    return (char *)c->buf[b] + (size_t)c->geo[inst].off * c->elem;
 }
 
 // The launch counter that seeds the dithered FP32 stores follows the step
@@ -258,6 +295,78 @@ static glbm_status ensure_stage(glbm_ctx *c, size_t n)
     return GLBM_OK;
 }
 
+// Allocation and initial state shared by both kinds of context.
+static glbm_status finish_create(glbm_ctx *c, const glbm_config *cfgs, int n, void *stream)
+{
+    c->n_inst = n;
+    c->dims = cfgs[0].dims;
+    c->prec = cfgs[0].prec;
+    c->elem = c->prec == GLBM_FP64 ? 8 : 4;
+    c->A = DevAlloc{g_alloc, g_free, g_alloc_user};
+    c->stream = (cudaStream_t)stream;
+    c->cfg.assign(cfgs, cfgs + n);
+    c->tabs.resize(GLBM_MAXN + 1);
+    for (int N = 1; N <= GLBM_MAXN; ++N) glbm_build_axis_table(N, &c->tabs[N], nullptr);
+    // pool layout: instances back to back, each starting on a 256-byte boundary
+    c->geo.resize(n);
+    long long off = 0;
+    long long max_nodes = 1;
+    const long long align = 256 / (long long)c->elem;
+    for (int i = 0; i < n; ++i) {
+        Geo g = make_geo(cfgs[i]);
+        if ((long long)g.Q * g.plane >= (1LL << 31))
+            return fail(GLBM_E_UNSUPPORTED, "instance %d holds %lld populations; at most 2^31 - 1", i,
+                        (long long)g.Q * g.plane);
+        g.off = off;
+        off += ((g.Q * g.plane + align - 1) / align) * align;
+        max_nodes = std::max(max_nodes, g.nodes());
+        c->geo[i] = g;
+    }
+    c->pool_elems = off;
+    c->h_ip.resize(n);
+    c->tau.resize(n);
+    for (int i = 0; i < n; ++i) {
+        c->tau[i] = tau_of(cfgs[i]);
+        fill_inst(c, cfgs[i], c->geo[i], c->h_ip[i], c->tau[i]);
+    }
+
+    cudaError_t e = cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return fail(GLBM_E_CUDA, "stream creation failed: %s", cudaGetErrorString(e));
+    if (cudaHostAlloc((void **)&c->h_status, sizeof(unsigned), cudaHostAllocDefault) != cudaSuccess)
+        return fail(GLBM_E_NOMEM, "pinned status allocation failed");
+    *c->h_status = 0;
+    const int blocks = glbm_field_sum_blocks(max_nodes);
+    c->buf[0] = dev_alloc(c->A, bytes_state(c), c->stream);
+    c->buf[1] = dev_alloc(c->A, bytes_state(c), c->stream);
+    c->d_ip = (InstParams *)dev_alloc(c->A, sizeof(InstParams) * n, c->stream);
+    c->d_status = (unsigned *)dev_alloc(c->A, 4 * sizeof(unsigned), c->stream);
+    c->d_mom = (double *)dev_alloc(c->A, 7 * (size_t)max_nodes * sizeof(double), c->stream);
+    c->d_part = (double *)dev_alloc(c->A, 3 * (size_t)blocks * sizeof(double), c->stream);
+    c->d_sums = (double *)dev_alloc(c->A, 3 * sizeof(double), c->stream);
+    if (!c->buf[0] || !c->buf[1] || !c->d_ip || !c->d_status || !c->d_mom || !c->d_part || !c->d_sums)
+        return fail(GLBM_E_NOMEM, "device allocation of %.1f MB failed", 2.0 * bytes_state(c) / 1e6);
+    CUDA_TRY(cudaMemcpyAsync(c->d_ip, c->h_ip.data(), sizeof(InstParams) * n, cudaMemcpyHostToDevice,
+                             c->stream));
+    CUDA_TRY(cudaMemsetAsync(c->d_status, 0, 4 * sizeof(unsigned), c->stream));
+    CUDA_TRY(cudaMemsetAsync(c->buf[0], 0, bytes_state(c), c->stream));
+    CUDA_TRY(cudaMemsetAsync(c->buf[1], 0, bytes_state(c), c->stream));
+    // rest state X = W everywhere
+    glbm_status st = ensure_stage(c, 3 * (size_t)max_nodes);
+    if (st != GLBM_OK) return st;
+    std::vector<double> one(max_nodes, 1.0), zero(max_nodes, 0.0);
+    CUDA_TRY(cudaMemcpy(c->d_stage, one.data(), max_nodes * 8, cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(c->d_stage + max_nodes, zero.data(), max_nodes * 8, cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(c->d_stage + 2 * max_nodes, zero.data(), max_nodes * 8, cudaMemcpyHostToDevice));
+    for (int i = 0; i < n; ++i) {
+        CUDA_TRY(glbm_launch_set_equilibrium(aux_args(c, i), inst_ptr(c, 0, i), 0, c->d_stage,
+                                             c->d_stage + max_nodes, c->d_stage + 2 * max_nodes,
+                                             c->stream));
+        c->launches += 1;
+    }
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
+    return GLBM_OK;
+}
+
 extern "C" glbm_status glbm_create(const glbm_config *cfgs, int n, void *stream, glbm_ctx **out)
 {
     if (!cfgs || n < 1 || !out) return fail(GLBM_E_INVAL, "null argument or n < 1");
@@ -273,81 +382,56 @@ extern "C" glbm_status glbm_create(const glbm_config *cfgs, int n, void *stream,
     }
     glbm_ctx *c = new (std::nothrow) glbm_ctx();
     if (!c) return fail(GLBM_E_NOMEM, "host allocation failed");
-    const glbm_config &c0 = cfgs[0];
-    c->n_inst = n;
-    c->dims = c0.dims;
-    c->k = c0.k;
-    c->N = c0.k + 1;
-    c->Lx = c0.nx;
-    c->Ly = c0.dims == 2 ? c0.ny : 1;
-    c->bc = c0.bc;
-    c->prec = c0.prec;
-    c->elem = c0.prec == GLBM_FP64 ? 8 : 4;
-    c->pitch = ((c->Lx + 31) / 32) * 32;
-    const int Q1 = 2 * c->N + 1;
-    const int Q = c->dims == 2 ? Q1 * Q1 : Q1;
-    c->plane = (long long)c->Ly * c->pitch;
-    c->inst_stride = (long long)Q * c->plane;
-    if (c->inst_stride >= (1LL << 31)) {
+    glbm_status st = finish_create(c, cfgs, n, stream);
+    if (st != GLBM_OK) {
+        destroy_resources(c);
         delete c;
-        return fail(GLBM_E_UNSUPPORTED, "one instance holds %lld populations; at most 2^31 - 1",
-                    (long long)Q * c0.nx * (c0.dims == 2 ? c0.ny : 1));
+        return st;
     }
-    c->A = DevAlloc{g_alloc, g_free, g_alloc_user};
-    c->stream = (cudaStream_t)stream;
-    glbm_build_axis_table(c->N, &c->tab, nullptr);
-    c->h_ip.resize(n);
-    c->tau.resize(n);
-    for (int i = 0; i < n; ++i) {
-        c->tau[i] = tau_of(cfgs[i]);
-        fill_inst(c, cfgs[i], c->h_ip[i], c->tau[i]);
-    }
+    *out = c;
+    return GLBM_OK;
+}
 
-    const size_t nodes = (size_t)c->Lx * c->Ly;
-    glbm_status st = GLBM_OK;
-    cudaError_t e = cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking);
-    if (e != cudaSuccess) st = fail(GLBM_E_CUDA, "stream creation failed: %s", cudaGetErrorString(e));
-    if (st == GLBM_OK && cudaHostAlloc((void **)&c->h_status, sizeof(unsigned), cudaHostAllocDefault) != cudaSuccess)
-        st = fail(GLBM_E_NOMEM, "pinned status allocation failed");
-    if (st == GLBM_OK) {
-        c->buf[0] = dev_alloc(c->A, bytes_state(c), c->stream);
-        c->buf[1] = dev_alloc(c->A, bytes_state(c), c->stream);
-        c->d_ip = (InstParams *)dev_alloc(c->A, sizeof(InstParams) * n, c->stream);
-        c->d_status = (unsigned *)dev_alloc(c->A, 4 * sizeof(unsigned), c->stream);
-        c->d_mom = (double *)dev_alloc(c->A, 7 * nodes * sizeof(double), c->stream);
-        c->sum_blocks = glbm_field_sum_blocks((long long)nodes);
-        c->d_part = (double *)dev_alloc(c->A, 3 * c->sum_blocks * sizeof(double), c->stream);
-        c->d_sums = (double *)dev_alloc(c->A, 3 * sizeof(double), c->stream);
-        if (!c->buf[0] || !c->buf[1] || !c->d_ip || !c->d_status || !c->d_mom || !c->d_part ||
-            !c->d_sums)
-            st = fail(GLBM_E_NOMEM, "device allocation of %.1f MB failed",
-                      2.0 * bytes_state(c) / 1e6);
+extern "C" glbm_status glbm_batch_create(const glbm_config *cfgs, int n, void *stream, glbm_ctx **out)
+{
+    if (!cfgs || n < 1 || !out) return fail(GLBM_E_INVAL, "null argument or n < 1");
+    *out = nullptr;
+    for (int i = 0; i < n; ++i) {
+        glbm_status st = validate(cfgs[i]);
+        if (st != GLBM_OK) return st;
+        if (cfgs[i].dims != 2) return fail(GLBM_E_UNSUPPORTED, "heterogeneous batches are 2D");
+        if (cfgs[i].prec != GLBM_FP32_DEV)
+            return fail(GLBM_E_UNSUPPORTED,
+                        "heterogeneous batches store FP32 deviations (FP64 instances go through "
+                        "glbm_create)");
     }
+    glbm_ctx *c = new (std::nothrow) glbm_ctx();
+    if (!c) return fail(GLBM_E_NOMEM, "host allocation failed");
+    c->hetero = true;
+    glbm_status st = finish_create(c, cfgs, n, stream);
     if (st == GLBM_OK) {
-        *c->h_status = 0;
-        e = cudaMemcpyAsync(c->d_ip, c->h_ip.data(), sizeof(InstParams) * n,
-                            cudaMemcpyHostToDevice, c->stream);
-        if (e == cudaSuccess) e = cudaMemsetAsync(c->d_status, 0, 4 * sizeof(unsigned), c->stream);
-        if (e == cudaSuccess) e = cudaMemsetAsync(c->buf[0], 0, bytes_state(c), c->stream);
-        if (e == cudaSuccess) e = cudaMemsetAsync(c->buf[1], 0, bytes_state(c), c->stream);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
-        if (e != cudaSuccess) st = fail(GLBM_E_CUDA, "initialisation failed: %s", cudaGetErrorString(e));
-    }
-    if (st == GLBM_OK) {
-        // rest state X = W
-        std::vector<double> one(nodes, 1.0), zero(nodes, 0.0);
-        st = ensure_stage(c, 3 * nodes);
+        // work list: every (instance, tile), grouped by level
+        std::vector<int4> items;
+        for (int i = 0; i < n; ++i) {
+            const Geo &g = c->geo[i];
+            const int R = glbm_batched_rows(g.N);
+            for (int y0 = 0; y0 < g.Ly; y0 += R)
+                for (int x0 = 0; x0 < g.Lx; x0 += 32) items.push_back(make_int4(i, x0, y0, g.N));
+        }
+        std::stable_sort(items.begin(), items.end(),
+                         [](const int4 &a, const int4 &b) { return a.w < b.w; });
+        for (int N = 0; N <= GLBM_MAXN + 1; ++N) {  // first item of level >= N
+            int k = 0;
+            while (k < (int)items.size() && items[k].w < N) ++k;
+            c->group[N] = k;
+        }
+        c->n_items = (int)items.size();
+        c->d_items = (int4 *)dev_alloc(c->A, sizeof(int4) * items.size(), c->stream);
+        if (!c->d_items) st = fail(GLBM_E_NOMEM, "work list allocation failed");
         if (st == GLBM_OK) {
-            e = cudaMemcpy(c->d_stage, one.data(), nodes * 8, cudaMemcpyHostToDevice);
-            if (e == cudaSuccess) e = cudaMemcpy(c->d_stage + nodes, zero.data(), nodes * 8, cudaMemcpyHostToDevice);
-            if (e == cudaSuccess) e = cudaMemcpy(c->d_stage + 2 * nodes, zero.data(), nodes * 8, cudaMemcpyHostToDevice);
-            AuxArgs a = aux_args(c);
-            for (int i = 0; i < n && e == cudaSuccess; ++i)
-                e = glbm_launch_set_equilibrium(a, c->buf[0], i, c->d_stage, c->d_stage + nodes,
-                                                c->d_stage + 2 * nodes, c->stream);
-            if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
-            if (e != cudaSuccess) st = fail(GLBM_E_CUDA, "rest-state launch failed: %s", cudaGetErrorString(e));
-            c->launches += n;
+            cudaError_t e = cudaMemcpy(c->d_items, items.data(), sizeof(int4) * items.size(),
+                                       cudaMemcpyHostToDevice);
+            if (e != cudaSuccess) st = fail(GLBM_E_CUDA, "work list upload: %s", cudaGetErrorString(e));
         }
     }
     if (st != GLBM_OK) {
@@ -394,19 +478,13 @@ static glbm_status check_inst(const glbm_ctx *c, int inst)
     return GLBM_OK;
 }
 
-static int n_q(const glbm_ctx *c)
-{
-    const int Q1 = 2 * c->N + 1;
-    return c->dims == 2 ? Q1 * Q1 : Q1;
-}
-
 extern "C" glbm_status glbm_set_equilibrium(glbm_ctx *c, int inst, const double *rho,
                                             const double *ux, const double *uy, int on_device)
 {
     glbm_status st = check_inst(c, inst);
     if (st != GLBM_OK) return st;
     if (!rho || !ux || (c->dims == 2 && !uy)) return fail(GLBM_E_INVAL, "null field");
-    const size_t nodes = (size_t)c->Lx * c->Ly;
+    const size_t nodes = (size_t)c->geo[inst].nodes();
     const double *dr = rho, *du = ux, *dv = uy;
     if (!on_device) {
         st = ensure_stage(c, 3 * nodes);
@@ -420,7 +498,8 @@ extern "C" glbm_status glbm_set_equilibrium(glbm_ctx *c, int inst, const double 
         dv = c->dims == 2 ? c->d_stage + 2 * nodes : c->d_stage;
     }
     if (!dv) dv = du;
-    CUDA_TRY(glbm_launch_set_equilibrium(aux_args(c), c->buf[c->cur], inst, dr, du, dv, c->stream));
+    CUDA_TRY(glbm_launch_set_equilibrium(aux_args(c, inst), inst_ptr(c, c->cur, inst), 0, dr, du, dv,
+                                         c->stream));
     c->launches += 1;
     CUDA_TRY(set_clock(c, 0));
     if (!on_device) CUDA_TRY(cudaStreamSynchronize(c->stream));  // host buffers reusable on return
@@ -432,7 +511,7 @@ extern "C" glbm_status glbm_set_populations(glbm_ctx *c, int inst, const double 
     glbm_status st = check_inst(c, inst);
     if (st != GLBM_OK) return st;
     if (!f) return fail(GLBM_E_INVAL, "null populations");
-    const size_t n = (size_t)n_q(c) * c->Lx * c->Ly;
+    const size_t n = (size_t)c->geo[inst].Q * c->geo[inst].nodes();
     const double *src = f;
     if (!on_device) {
         st = ensure_stage(c, n);
@@ -440,7 +519,8 @@ extern "C" glbm_status glbm_set_populations(glbm_ctx *c, int inst, const double 
         CUDA_TRY(cudaMemcpyAsync(c->d_stage, f, n * 8, cudaMemcpyHostToDevice, c->stream));
         src = c->d_stage;
     }
-    CUDA_TRY(glbm_launch_set_populations(aux_args(c), c->buf[c->cur], inst, src, c->stream));
+    CUDA_TRY(glbm_launch_set_populations(aux_args(c, inst), inst_ptr(c, c->cur, inst), 0, src,
+                                         c->stream));
     c->launches += 1;
     CUDA_TRY(set_clock(c, 0));
     if (!on_device) CUDA_TRY(cudaStreamSynchronize(c->stream));
@@ -452,14 +532,15 @@ extern "C" glbm_status glbm_get_populations(glbm_ctx *c, int inst, double *f, in
     glbm_status st = check_inst(c, inst);
     if (st != GLBM_OK) return st;
     if (!f) return fail(GLBM_E_INVAL, "null output");
-    const size_t n = (size_t)n_q(c) * c->Lx * c->Ly;
+    const size_t n = (size_t)c->geo[inst].Q * c->geo[inst].nodes();
     double *dst = f;
     if (!on_device) {
         st = ensure_stage(c, n);
         if (st != GLBM_OK) return st;
         dst = c->d_stage;
     }
-    CUDA_TRY(glbm_launch_get_populations(aux_args(c), c->buf[c->cur], inst, dst, c->stream));
+    CUDA_TRY(glbm_launch_get_populations(aux_args(c, inst), inst_ptr(c, c->cur, inst), 0, dst,
+                                         c->stream));
     c->launches += 1;
     if (!on_device) {
         CUDA_TRY(cudaMemcpyAsync(f, dst, n * 8, cudaMemcpyDeviceToHost, c->stream));
@@ -473,30 +554,55 @@ extern "C" glbm_status glbm_get_populations(glbm_ctx *c, int inst, double *f, in
 // ---------------------------------------------------------------------------
 static Step2DArgs step_args(const glbm_ctx *c, int from)
 {
+    const Geo &g = c->geo[0];
     Step2DArgs a;
     memset(&a, 0, sizeof(a));
-    a.tab = c->tab;
+    a.tab = c->tabs[g.N];
     a.fin = c->buf[from];
     a.fout = c->buf[1 - from];
     a.ip = c->d_ip;
     a.status = c->d_status;
     a.step_ctr = c->d_status + 1;
     a.done_ctr = c->d_status + 2;
-    a.Lx = c->Lx;
-    a.Ly = c->Ly;
-    a.pitch = c->pitch;
-    a.bc = c->bc;
-    a.plane = c->plane;
-    a.inst_stride = c->inst_stride;
+    a.Lx = g.Lx;
+    a.Ly = g.Ly;
+    a.pitch = g.pitch;
+    a.bc = c->cfg[0].bc;
+    a.plane = g.plane;
+    a.inst_stride = c->n_inst > 1 ? c->geo[1].off : 0;
     return a;
 }
 
-// One 2D step from buffer `from` into the other, on stream s.
+static BatchArgs batch_args(const glbm_ctx *c, int from)
+{
+    BatchArgs b;
+    memset(&b, 0, sizeof(b));
+    for (int N = 1; N <= GLBM_MAXN; ++N) b.tab[N - 1] = c->tabs[N];
+    b.fin = c->buf[from];
+    b.fout = c->buf[1 - from];
+    b.ip = c->d_ip;
+    b.items = c->d_items;
+    b.n_items = c->n_items;
+    for (int N = 0; N <= GLBM_MAXN + 1; ++N) b.group[N] = c->group[N];
+    b.status = c->d_status;
+    b.step_ctr = c->d_status + 1;
+    b.done_ctr = c->d_status + 2;
+    return b;
+}
+
+// Kernel launches of one 2D step.
+static int launches_per_step(const glbm_ctx *c)
+{
+    return c->hetero ? glbm_batched_launches(batch_args(c, 0)) : 1;
+}
+
+// One 2D step of every instance from buffer `from` into the other, on stream s.
 static cudaError_t launch_one_2d(const glbm_ctx *c, int from, cudaStream_t s)
 {
+    if (c->hetero) return glbm_launch_batched_f32(batch_args(c, from), s);
     const Step2DArgs a = step_args(c, from);
-    return c->prec == GLBM_FP64 ? glbm_launch_step2d_f64(c->N, a, c->n_inst, s)
-                                : glbm_launch_step2d_f32(c->N, a, c->n_inst, s);
+    return c->prec == GLBM_FP64 ? glbm_launch_step2d_f64(c->geo[0].N, a, c->n_inst, s)
+                                : glbm_launch_step2d_f32(c->geo[0].N, a, c->n_inst, s);
 }
 
 static glbm_status capture_chunk(glbm_ctx *c, int from)
@@ -528,10 +634,11 @@ extern "C" glbm_status glbm_step(glbm_ctx *c, int64_t n)
     const unsigned prior = *c->h_status;  // flags of steps already finished
     if (n == 0) return prior ? fail(GLBM_E_UNSTABLE, "a node left the positivity domain") : GLBM_OK;
     if (c->dims == 1) {
-        const AuxArgs a = aux_args(c);
         for (int i = 0; i < c->n_inst; ++i) {
+            const AuxArgs a = aux_args(c, i);
             int ok = 0;
-            CUDA_TRY(glbm_launch_run1d_resident(a, c->buf[c->cur], i, n, c->d_status, c->stream, &ok));
+            CUDA_TRY(glbm_launch_run1d_resident(a, inst_ptr(c, c->cur, i), 0, n, c->d_status,
+                                                c->stream, &ok));
             if (ok) {
                 c->launches += 1;
                 continue;
@@ -539,13 +646,13 @@ extern "C" glbm_status glbm_step(glbm_ctx *c, int64_t n)
             // too large for one CTA: one launch per step, ping-pong through both buffers
             int b = c->cur;
             for (int64_t s = 0; s < n; ++s) {
-                CUDA_TRY(glbm_launch_step1d(a, c->buf[b], c->buf[1 - b], i, c->d_status, c->stream));
+                CUDA_TRY(glbm_launch_step1d(a, inst_ptr(c, b, i), inst_ptr(c, 1 - b, i), 0,
+                                            c->d_status, c->stream));
                 b = 1 - b;
             }
             if (b != c->cur) {
-                const size_t bytes = (size_t)c->inst_stride * c->elem;
-                CUDA_TRY(cudaMemcpyAsync((char *)c->buf[c->cur] + (size_t)i * bytes,
-                                         (char *)c->buf[b] + (size_t)i * bytes, bytes,
+                const size_t bytes = (size_t)c->geo[i].Q * c->geo[i].plane * c->elem;
+                CUDA_TRY(cudaMemcpyAsync(inst_ptr(c, c->cur, i), inst_ptr(c, b, i), bytes,
                                          cudaMemcpyDeviceToDevice, c->stream));
             }
             c->launches += n;
@@ -558,13 +665,13 @@ extern "C" glbm_status glbm_step(glbm_ctx *c, int64_t n)
                 if (st != GLBM_OK) return st;
             }
             CUDA_TRY(cudaGraphLaunch(c->graph[c->cur], c->stream));
-            c->launches += kGraphChunk;
+            c->launches += kGraphChunk * launches_per_step(c);
             left -= kGraphChunk;  // even chunk: c->cur unchanged
         }
         for (; left > 0; --left) {
             CUDA_TRY(launch_one_2d(c, c->cur, c->stream));
             c->cur = 1 - c->cur;
-            c->launches += 1;
+            c->launches += launches_per_step(c);
         }
     }
     c->t += n;
@@ -589,7 +696,7 @@ extern "C" glbm_status glbm_sync(glbm_ctx *c)
 // ---------------------------------------------------------------------------
 static glbm_status compute_moments(glbm_ctx *c, int inst)
 {
-    CUDA_TRY(glbm_launch_moments(aux_args(c), c->buf[c->cur], inst, c->d_mom, c->stream));
+    CUDA_TRY(glbm_launch_moments(aux_args(c, inst), inst_ptr(c, c->cur, inst), 0, c->d_mom, c->stream));
     c->launches += 1;
     return GLBM_OK;
 }
@@ -603,7 +710,7 @@ extern "C" glbm_status glbm_moments(glbm_ctx *c, int inst, unsigned mask, double
     // field slot of each mask bit in the reducer's output
     const int slot2d[7] = {0, 1, 2, 3, 4, 5, 6};
     const int slot1d[7] = {0, 1, -1, 2, 3, -1, -1};
-    const size_t nodes = (size_t)c->Lx * c->Ly;
+    const size_t nodes = (size_t)c->geo[inst].nodes();
     size_t need = 0;
     for (int b = 0; b < 7; ++b) {
         if (!(mask & (1u << b))) continue;
@@ -634,9 +741,9 @@ extern "C" glbm_status glbm_conservation(glbm_ctx *c, int inst, double *mass, do
     if (st != GLBM_OK) return st;
     st = compute_moments(c, inst);
     if (st != GLBM_OK) return st;
-    const long long nodes = (long long)c->Lx * c->Ly;
-    CUDA_TRY(glbm_launch_field_sums(c->d_mom, c->dims == 2 ? 3 : 2, nodes, c->d_part, c->sum_blocks,
-                                    c->d_sums, c->stream));
+    const long long nodes = c->geo[inst].nodes();
+    CUDA_TRY(glbm_launch_field_sums(c->d_mom, c->dims == 2 ? 3 : 2, nodes, c->d_part,
+                                    glbm_field_sum_blocks(nodes), c->d_sums, c->stream));
     c->launches += 2;
     double h[3];
     CUDA_TRY(cudaMemcpyAsync(h, c->d_sums, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
@@ -648,13 +755,14 @@ extern "C" glbm_status glbm_conservation(glbm_ctx *c, int inst, double *mass, do
 }
 
 // ---------------------------------------------------------------------------
-// checkpoints: header, raw state image of every instance, CRC-32
+// checkpoints: header, raw pool image of every instance, CRC-32
 // ---------------------------------------------------------------------------
 struct CkptHeader {
     char magic[8];
-    int32_t version, dims, nx, ny, k, bc, prec, n_inst;
+    int32_t version, dims, prec, n_inst, hetero, pad;
     int64_t t;
     uint64_t bytes;
+    uint64_t config_crc;  // CRC-32 of every instance's geometry, level and boundary
 };
 
 static uint32_t crc32_update(uint32_t crc, const unsigned char *p, size_t n)
@@ -670,17 +778,20 @@ static uint32_t crc32_update(uint32_t crc, const unsigned char *p, size_t n)
 static void fill_header(const glbm_ctx *c, CkptHeader &h)
 {
     memset(&h, 0, sizeof(h));
-    memcpy(h.magic, "GLBMCKP1", 8);
-    h.version = 1;
+    memcpy(h.magic, "GLBMCKP2", 8);
+    h.version = 2;
     h.dims = c->dims;
-    h.nx = c->Lx;
-    h.ny = c->Ly;
-    h.k = c->k;
-    h.bc = c->bc;
     h.prec = c->prec;
     h.n_inst = c->n_inst;
+    h.hetero = c->hetero ? 1 : 0;
     h.t = c->t;
     h.bytes = bytes_state(c);
+    uint32_t crc = 0;
+    for (const glbm_config &g : c->cfg) {
+        const int geo[6] = {g.dims, g.nx, g.ny, g.k, g.bc, g.prec};
+        crc = crc32_update(crc, (const unsigned char *)geo, sizeof(geo));
+    }
+    h.config_crc = crc;
 }
 
 extern "C" glbm_status glbm_save(glbm_ctx *c, const char *path)
@@ -713,13 +824,13 @@ extern "C" glbm_status glbm_load(glbm_ctx *c, const char *path)
     bool ok = fread(&h, sizeof(h), 1, fp) == 1;
     if (ok) {
         want.t = h.t;
-        ok = memcmp(&h, &want, sizeof(h)) == 0;
-        if (!ok) {
+        if (memcmp(&h, &want, sizeof(h)) != 0) {
             fclose(fp);
             return fail(GLBM_E_INVAL, "checkpoint %s does not match this context's configuration", path);
         }
         img.resize(h.bytes);
-        ok = fread(img.data(), 1, img.size(), fp) == img.size() && fread(&crc_file, sizeof(crc_file), 1, fp) == 1;
+        ok = fread(img.data(), 1, img.size(), fp) == img.size() &&
+             fread(&crc_file, sizeof(crc_file), 1, fp) == 1;
     }
     fclose(fp);
     if (!ok) return fail(GLBM_E_IO, "checkpoint %s is truncated", path);
@@ -730,13 +841,4 @@ extern "C" glbm_status glbm_load(glbm_ctx *c, const char *path)
     CUDA_TRY(set_clock(c, h.t));
     CUDA_TRY(cudaStreamSynchronize(c->stream));
     return GLBM_OK;
-}
-
-extern "C" glbm_status glbm_batch_create(const glbm_config *cfgs, int n, void *stream, glbm_ctx **out)
-{
-    (void)cfgs;
-    (void)n;
-    (void)stream;
-    if (out) *out = nullptr;
-    return fail(GLBM_E_UNSUPPORTED, "heterogeneous batches are not built yet");
 }

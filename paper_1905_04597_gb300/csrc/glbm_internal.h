@@ -82,7 +82,21 @@ struct Step2DArgs {
     long long inst_stride;// elements per instance
 };
 
-enum { GLBM_MODE_STEP = 0 };
+// Arguments of one step of a heterogeneous batch: one launch per level over
+// that level's slice of a work list of (instance, x0, y0, N) tiles.
+struct BatchArgs {
+    AxisTable tab[GLBM_MAXN];  // tab[N - 1]
+    const void *fin;           // pool read
+    void *fout;                // pool written
+    const InstParams *ip;      // per instance (offset, geometry, constants)
+    const int4 *items;         // work list, sorted by level
+    int n_items;
+    int group[GLBM_MAXN + 2];  // items of level N: [group[N], group[N + 1]) (group[0] unused)
+    unsigned *status, *step_ctr, *done_ctr;
+};
+int glbm_batched_rows(int N);                   // node rows per tile of level N
+int glbm_batched_launches(const BatchArgs &a);  // launches per step (levels present)
+cudaError_t glbm_launch_batched_f32(const BatchArgs &a, cudaStream_t s);
 
 // Launchers (return cudaError_t of the launch).
 cudaError_t glbm_launch_step2d_f32(int N, const Step2DArgs &a, int n_inst, cudaStream_t s);

@@ -36,17 +36,19 @@ struct Step2D {
         T dsum[NW][2][32];    // per-warp partial wall fluxes
     };
 
-    __device__ static void run(const Step2DArgs &a, const InstParams &ip,
-                               const T *__restrict__ fin, T *__restrict__ fout, int x0, int y0,
-                               Smem &sm, unsigned *status, unsigned seed)
+    // One tile: columns x0..x0+31, rows y0..y0+R-1 of one instance whose
+    // populations start at fin / fout. Every thread of the CTA calls it.
+    __device__ static void run(const AxisTable &tab, const InstParams &ip, int Lx, int Ly,
+                               int pitch, int plane, int bc, const T *__restrict__ fin,
+                               T *__restrict__ fout, int x0, int y0, Smem &sm, unsigned *status,
+                               unsigned seed)
     {
         const int lane = threadIdx.x & 31;
         const int w = threadIdx.x >> 5;
         const int g = w % G;
         const int r = w / G;
-        const int Lx = a.Lx, Ly = a.Ly, pitch = a.pitch;
-        const int plane = (int)a.plane;  // instance offsets fit 31 bits (checked at creation)
-        const bool walls = a.bc == GLBM_BC_WALLS;
+        // plane < 2^31 / Q: instance offsets fit 31 bits (checked at creation)
+        const bool walls = bc == GLBM_BC_WALLS;
         const int x = x0 + lane, y = y0 + r;
         const bool active = (x < Lx) && (y < Ly);
         const int xc = x < Lx ? x : Lx - 1;
@@ -126,14 +128,14 @@ struct Step2D {
                     const int ys = yc - ny;
                     if (walls && (ys < 0 || ys >= Ly)) {  // uniform across the warp
                         const bool lo = ys < 0;
-                        const T wy = A::W(a.tab, iy);
+                        const T wy = A::W(tab, iy);
                         const T rw = sm.rw[lo ? 0 : 1][lane];
 #pragma unroll
                         for (int ix = 0; ix < Q1; ++ix) {
                             if (DEV) {
                                 const T dw = lo ? (T)ip.dw_lo_f[ix] : (T)ip.dw_hi_f[ix];
                                 // W^y (drho_w W^x + rho_w (E^x(u_w) - W^x))
-                                f[k][ix] = wy * fma(rw, A::W(a.tab, ix), (T(1) + rw) * dw);
+                                f[k][ix] = wy * fma(rw, A::W(tab, ix), (T(1) + rw) * dw);
                             } else {
                                 const T ew = lo ? (T)ip.ew_lo[ix] : (T)ip.ew_hi[ix];
                                 f[k][ix] = rw * ew * wy;
@@ -185,10 +187,10 @@ struct Step2D {
         }
 
         T dx[Q1];
-        eq_dev_all<N, T>(a.tab, ux, dx);
+        eq_dev_all<N, T>(tab, ux, dx);
         T ex[Q1];  // FP64 mode: E^x = W + d^x
 #pragma unroll
-        for (int ix = 0; ix < Q1; ++ix) ex[ix] = DEV ? T(0) : A::W(a.tab, ix) + dx[ix];
+        for (int ix = 0; ix < Q1; ++ix) ex[ix] = DEV ? T(0) : A::W(tab, ix) + dx[ix];
         const T om = DEV ? (T)ip.omega_f : (T)ip.omega;
         const T gto = DEV ? (T)ip.g_theta_om_f : (T)ip.g_theta_om;  // g / (theta omega)
         T *const obase = fout + (y * pitch + x);
@@ -207,8 +209,8 @@ struct Step2D {
                 const int iy = gi + k * G;
                 if (iy < Q1) {
                     const int ny = iy - N;
-                    const T wy = A::W(a.tab, iy);
-                    const T dy = eq_dev_one<N, T>(a.tab, uy, ny);
+                    const T wy = A::W(tab, iy);
+                    const T dy = eq_dev_one<N, T>(tab, uy, ny);
                     const T rey = rho * (wy + dy);  // rho e^y
                     const T gr = gto * wy;
                     // FP32: delta f^eq = d^x rho e^y + W^x (drho W^y + rho d^y)
@@ -221,7 +223,7 @@ struct Step2D {
                         T v;
                         if (DEV) {
                             const T Bn = nx != 0 ? fma(T(nx), gr, B) : B;
-                            const T eq = fma(dx[ix], rey, A::W(a.tab, ix) * Bn);
+                            const T eq = fma(dx[ix], rey, A::W(tab, ix) * Bn);
                             // increment plus dither, then one rounding of the store
                             const unsigned q = iy * Q1 + ix;
                             const unsigned rnd = hnode * (0x9E3779B9u * (2u * q + 1u)) + 0x7F4A7C15u * q;
@@ -229,7 +231,7 @@ struct Step2D {
                             v = f0 + inc;
                         } else {
                             T eq = ex[ix] * rey;
-                            if (nx != 0) eq = fma(A::WN(a.tab, ix), gr, eq);
+                            if (nx != 0) eq = fma(A::WN(tab, ix), gr, eq);
                             v = fma(om, eq - f0, f0);
                         }
                         if (active) op[ix * plane] = v;
@@ -239,6 +241,20 @@ struct Step2D {
         }
     }
 };
+
+// The last CTA of a launch to finish advances the launch counter that seeds the
+// dithered stores of the next launch (every CTA read it before finishing).
+__device__ __forceinline__ void advance_launch_counter(unsigned *step_ctr, unsigned *done_ctr)
+{
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const unsigned total = gridDim.x * gridDim.y * gridDim.z;
+        if (atomicAdd(done_ctr, 1u) == total - 1u) {
+            *done_ctr = 0u;
+            atomicAdd(step_ctr, 1u);
+        }
+    }
+}
 
 template <int N, typename T, int G, int R>
 __global__ void __launch_bounds__(32 * G * R)
@@ -251,18 +267,9 @@ __global__ void __launch_bounds__(32 * G * R)
     T *fout = static_cast<T *>(a.fout) + (long long)inst * a.inst_stride;
     // launch counter (read before any CTA of this launch can advance it)
     const unsigned seed = S::DEV ? hash32(__ldcg(a.step_ctr) * 0x632BE5ABu + inst) : 0u;
-    S::run(a, a.ip[inst], fin, fout, blockIdx.x * 32, blockIdx.y * R, sm, a.status, seed);
-    if (S::DEV) {
-        // the last CTA to finish advances the launch counter for the next launch
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            const unsigned total = gridDim.x * gridDim.y * gridDim.z;
-            if (atomicAdd(a.done_ctr, 1u) == total - 1u) {
-                *a.done_ctr = 0u;
-                atomicAdd(a.step_ctr, 1u);
-            }
-        }
-    }
+    S::run(a.tab, a.ip[inst], a.Lx, a.Ly, a.pitch, (int)a.plane, a.bc, fin, fout, blockIdx.x * 32,
+           blockIdx.y * R, sm, a.status, seed);
+    if (S::DEV) advance_launch_counter(a.step_ctr, a.done_ctr);
 }
 
 // Warp-group split (G) and rows per CTA (R) per level and precision: about
