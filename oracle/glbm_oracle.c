@@ -496,3 +496,143 @@ int orc_observe(const orc_cfg *c, const double *X, double *out)
     free(F);
     return 0;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Forward-mode gradient of the flow rate (dual numbers)                     */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * Equilibrium and its derivative in u at level N (lattice units): E[n+N] as in
+ * orc_eq_lattice and dE[n+N] = dE_n/du, by differentiating every term of the
+ * factorial sum of Eq. maineq03 with P+- = (N/3 +- u + u^2/N)/(2N) and
+ * P0 = 1 - P+ - P-:  dP+-/du = (+-1 + 2u/N)/(2N),  dP0/du = -2u/N^2.
+ */
+static void orc_eq_lattice_du(int N, double u, double *E, double *dE)
+{
+    const double Pp = (N / 3.0 + u + u * u / N) / (2.0 * N);
+    const double Pm = (N / 3.0 - u + u * u / N) / (2.0 * N);
+    const double P0 = 1.0 - Pp - Pm;
+    const double dPp = (1.0 + 2.0 * u / N) / (2.0 * N);
+    const double dPm = (-1.0 + 2.0 * u / N) / (2.0 * N);
+    const double dP0 = -dPp - dPm;
+    for (int n = -N; n <= N; ++n) {
+        double pp = Pp, pm = Pm, dpp = dPp, dpm = dPm;
+        int an = n;
+        if (n < 0) { /* mirror: exchange P+ and P- */
+            pp = Pm; pm = Pp; dpp = dPm; dpm = dPp; an = -n;
+        }
+        double s = 0.0, ds = 0.0;
+        for (int m = 0; m <= (N - an) / 2; ++m) {
+            const int a = an + m, b = m, c = N - an - 2 * m;
+            const double ways = orc_factorial(N) /
+                                (orc_factorial(a) * orc_factorial(b) * orc_factorial(c));
+            const double t = pow(pp, a) * pow(pm, b) * pow(P0, c);
+            s += ways * t;
+            /* product rule over the three powers */
+            double dt = 0.0;
+            if (a > 0) dt += a * pow(pp, a - 1) * dpp * pow(pm, b) * pow(P0, c);
+            if (b > 0) dt += b * pow(pp, a) * pow(pm, b - 1) * dpm * pow(P0, c);
+            if (c > 0) dt += c * pow(pp, a) * pow(pm, b) * pow(P0, c - 1) * dP0;
+            ds += ways * dt;
+        }
+        E[n + N] = s;
+        dE[n + N] = ds;
+    }
+}
+
+/*
+ * Collision of a dual state: X = C(F) for the values and, for each of the two
+ * parameters p in (tau, g), dX/dp = dC/dF . dF/dp + dC/dp, with
+ *   f* = f + omega (f^eq - f) + F_i,  omega = 1/(tau + 1/2),
+ *   d omega / d tau = -omega^2,  dF_i/dg = W_i xi_x / theta_x,
+ *   d f^eq_i = E_i d rho + rho (dE^x_i/du_x du_x E^y_i + E^x_i dE^y_i/du_y du_y),
+ *   du = (dj - u d rho) / rho.
+ * F, dF arrays hold [value | d/dtau | d/dg] each of n populations.
+ */
+static void orc_collide_dual(const orc_cfg *c, const double *F, double *X)
+{
+    const int NX = c->NX, NY = c->NY, Lx = c->Lx, Ly = c->Ly;
+    const int Q1x = 2 * NX + 1;
+    const size_t plane = (size_t)Lx * Ly;
+    const size_t n = (size_t)orc_nq(c) * plane;
+    const double omega = 1.0 / (c->tau + 0.5);
+    const double domega = -omega * omega;
+    const double theta_x = NX / 3.0;
+    double Wx[2 * ORC_MAX_N + 1], Wy[2 * ORC_MAX_N + 1];
+    double Ex[2 * ORC_MAX_N + 1], Ey[2 * ORC_MAX_N + 1], dEx[2 * ORC_MAX_N + 1], dEy[2 * ORC_MAX_N + 1];
+    orc_eq_lattice(NX, 0.0, Wx);
+    orc_eq_lattice(NY, 0.0, Wy);
+    for (size_t node = 0; node < plane; ++node) {
+        double rho[3] = {0, 0, 0}, jx[3] = {0, 0, 0}, jy[3] = {0, 0, 0};
+        for (int ny = -NY; ny <= NY; ++ny)
+            for (int nx = -NX; nx <= NX; ++nx) {
+                const size_t idx = ((ny + NY) * Q1x + (nx + NX)) * plane + node;
+                for (int d = 0; d < 3; ++d) {
+                    const double f = F[d * n + idx];
+                    rho[d] += f;
+                    jx[d] += nx * f;
+                    jy[d] += ny * f;
+                }
+            }
+        const double ux = jx[0] / rho[0], uy = jy[0] / rho[0];
+        double dux[3], duy[3];
+        for (int d = 1; d < 3; ++d) {
+            dux[d] = (jx[d] - ux * rho[d]) / rho[0];
+            duy[d] = (jy[d] - uy * rho[d]) / rho[0];
+        }
+        orc_eq_lattice_du(NX, ux, Ex, dEx);
+        orc_eq_lattice_du(NY, uy, Ey, dEy);
+        for (int ny = -NY; ny <= NY; ++ny)
+            for (int nx = -NX; nx <= NX; ++nx) {
+                const size_t idx = ((ny + NY) * Q1x + (nx + NX)) * plane + node;
+                const double f = F[idx];
+                const double feq = rho[0] * Ex[nx + NX] * Ey[ny + NY];
+                const double wxg = Wx[nx + NX] * Wy[ny + NY] * nx / theta_x;
+                X[idx] = f + omega * (feq - f) + wxg * c->g;
+                for (int d = 1; d < 3; ++d) {
+                    const double df = F[d * n + idx];
+                    const double dfeq = rho[d] * Ex[nx + NX] * Ey[ny + NY] +
+                                        rho[0] * (dEx[nx + NX] * dux[d] * Ey[ny + NY] +
+                                                  Ex[nx + NX] * dEy[ny + NY] * duy[d]);
+                    double v = df + omega * (dfeq - df);
+                    if (d == 1) v += domega * (feq - f); /* d/dtau */
+                    if (d == 2) v += wxg;                /* d/dg */
+                    X[d * n + idx] = v;
+                }
+            }
+    }
+}
+
+/*
+ * Flow rate J = (1/Lx) sum over nodes of the x-momentum of S(X_T) after `steps`
+ * steps from X (2D), and dJ/dtau, dJ/dg by forward-mode differentiation of every
+ * step (streaming is linear, so the tangents stream like the values).
+ * X holds the initial populations (independent of tau and g); out = {J, dJ/dtau,
+ * dJ/dg}. Returns -1 on a bad configuration.
+ */
+int orc_flowrate_grad(const orc_cfg *c, const double *X0, long steps, double *out)
+{
+    if (orc_check(c) || c->dims != 2) return -1;
+    const size_t plane = (size_t)c->Lx * c->Ly;
+    const size_t n = (size_t)orc_nq(c) * plane;
+    double *X = (double *)calloc(3 * n, sizeof(double));
+    double *F = (double *)malloc(3 * n * sizeof(double));
+    memcpy(X, X0, n * sizeof(double));
+    for (long t = 0; t < steps; ++t) {
+        for (int d = 0; d < 3; ++d) orc_stream2d(c, X + d * n, F + d * n);
+        orc_collide_dual(c, F, X);
+    }
+    for (int d = 0; d < 3; ++d) orc_stream2d(c, X + d * n, F + d * n);
+    const int NX = c->NX, NY = c->NY, Q1x = 2 * NX + 1;
+    for (int d = 0; d < 3; ++d) {
+        double s = 0.0;
+        for (int ny = -NY; ny <= NY; ++ny)
+            for (int nx = -NX; nx <= NX; ++nx)
+                for (size_t node = 0; node < plane; ++node)
+                    s += nx * F[d * n + ((ny + NY) * Q1x + (nx + NX)) * plane + node];
+        out[d] = s / c->Lx;
+    }
+    free(X);
+    free(F);
+    return 0;
+}

@@ -70,6 +70,8 @@ def lib():
         _lib.orc_equilibrium.restype = ctypes.c_int
         _lib.orc_run.argtypes = [cp, dp, ctypes.c_long]
         _lib.orc_run.restype = ctypes.c_long
+        _lib.orc_flowrate_grad.argtypes = [cp, dp, ctypes.c_long, dp]
+        _lib.orc_flowrate_grad.restype = ctypes.c_int
     return _lib
 
 
@@ -129,6 +131,21 @@ class Lattice:
         out = np.empty((self.nfields,) + self.shape[1:])
         self._chk(lib().orc_observe(ctypes.byref(self.cfg), _dp(X), _dp(out)))
         return out
+
+    def flowrate_grad(self, X, steps):
+        """J = x-momentum of S(X_T) per column after `steps` steps from X, and
+        (dJ/dtau, dJ/dg) by forward-mode dual numbers."""
+        X = np.ascontiguousarray(X, dtype=np.float64)
+        out = np.empty(3)
+        self._chk(lib().orc_flowrate_grad(ctypes.byref(self.cfg), _dp(X), int(steps), _dp(out)))
+        return out[0], out[1], out[2]
+
+    def flowrate(self, X, steps):
+        """J alone from a plain run (no tangents)."""
+        Y, _ = self.run(X, steps)
+        F = self.stream(Y)
+        nx = np.tile(np.arange(-self.cfg.NX, self.cfg.NX + 1), 2 * self.cfg.NY + 1)
+        return float(np.tensordot(nx.astype(float), F, axes=1).sum() / self.cfg.Lx)
 
     def run(self, X, steps):
         """Advance a copy of X by `steps` steps; returns (X, unstable_count)."""

@@ -28,6 +28,8 @@ MUTATIONS = {
     "bounce-back offset": ("F[(-n + N) * L + (-1 - xd)] = v;", "F[(-n + N) * L + (-xd)] = v;"),
     "temperature dims": ("out[3 * plane + node] = e2 / (2.0 * rho);",
                          "out[3 * plane + node] = e2 / rho;"),
+    "tangent of omega": ("if (d == 1) v += domega * (feq - f);", "if (d == 1) v += omega * (feq - f);"),
+    "tangent of P0": ("const double dP0 = -dPp - dPm;", "const double dP0 = dPp + dPm;"),
 }
 
 
@@ -44,6 +46,7 @@ def test_pins_catch_planted_mistake(name, tmp_path):
     env = dict(os.environ, GLBM_ORACLE_LIB=str(lib))
     r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q",
                         os.path.join(ROOT, "tests", "test_oracle_equilibrium.py"),
-                        os.path.join(ROOT, "tests", "test_oracle_dynamics.py")],
+                        os.path.join(ROOT, "tests", "test_oracle_dynamics.py"),
+                        os.path.join(ROOT, "tests", "test_oracle_gradient.py")],
                        cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
     assert r.returncode != 0, f"pins did not catch mutation {name!r}"
