@@ -190,6 +190,26 @@ glbm_status glbm_conservation(glbm_ctx *ctx, int inst, double *mass, double *mom
 glbm_status glbm_conservation_noalloc(const double *fields, int dims, int64_t nodes, double *sums,
                                       void *stream);
 
+/*
+ * Gradient of the flow rate by the discrete adjoint. From the current state
+ * X_t0 the context advances `steps` steps (the state afterwards is X_t0+steps,
+ * as after glbm_step) keeping a checkpoint every `ckpt_every` steps. It then
+ * sweeps backwards: it recomputes each segment from its checkpoint and
+ * applies the hand-written adjoint stream-collide step (reverse streaming,
+ * transposed diffuse-wall rule, rank-3 transposed BGK Jacobian). Per instance
+ * it returns
+ *   J        = (1/nx) sum over nodes of the x-momentum of S(X_T) (the
+ *              volumetric flow rate per unit width, Sec. 5.4),
+ *   dJ_dtau  = dJ/dtau  (omega = 1/(tau + 1/2)),
+ *   dJ_dg    = dJ/dg    (body force along x).
+ * Each output is an array of n_inst doubles in host memory. 2D uniform
+ * contexts only. The adjoint state and the gradient sums are FP64. The call
+ * allocates steps/ckpt_every + ckpt_every state copies for the duration of
+ * the call. Synchronises.
+ */
+glbm_status glbm_adjoint_flowrate(glbm_ctx *ctx, int64_t steps, int64_t ckpt_every, double *J,
+                                  double *dJ_dtau, double *dJ_dg);
+
 /* Checkpoint of every instance's state (header, raw device image, CRC-32).
  * glbm_load requires a context created with the same configuration. */
 glbm_status glbm_save(glbm_ctx *ctx, const char *path);

@@ -842,3 +842,124 @@ extern "C" glbm_status glbm_load(glbm_ctx *c, const char *path)
     CUDA_TRY(cudaStreamSynchronize(c->stream));
     return GLBM_OK;
 }
+
+// ---------------------------------------------------------------------------
+// adjoint gradient of the flow rate
+// ---------------------------------------------------------------------------
+// One uniform 2D step from an arbitrary pool image `fin` into `fout`.
+static cudaError_t launch_2d_between(const glbm_ctx *c, const void *fin, void *fout, cudaStream_t s)
+{
+    Step2DArgs a = step_args(c, 0);
+    a.fin = fin;
+    a.fout = fout;
+    return c->prec == GLBM_FP64 ? glbm_launch_step2d_f64(c->geo[0].N, a, c->n_inst, s)
+                                : glbm_launch_step2d_f32(c->geo[0].N, a, c->n_inst, s);
+}
+
+struct Scratch {
+    const DevAlloc &A;
+    cudaStream_t s;
+    std::vector<void *> ptrs;
+    Scratch(const DevAlloc &a, cudaStream_t st) : A(a), s(st) {}
+    void *get(size_t bytes)
+    {
+        void *p = dev_alloc(A, bytes, s);
+        if (p) ptrs.push_back(p);
+        return p;
+    }
+    ~Scratch()
+    {
+        cudaStreamSynchronize(s);
+        for (void *p : ptrs) dev_free(A, p, s);
+    }
+};
+
+extern "C" glbm_status glbm_adjoint_flowrate(glbm_ctx *c, int64_t steps, int64_t ckpt_every,
+                                             double *J, double *dJ_dtau, double *dJ_dg)
+{
+    if (!c || !J || !dJ_dtau || !dJ_dg) return fail(GLBM_E_INVAL, "null argument");
+    if (c->dims != 2 || c->hetero)
+        return fail(GLBM_E_UNSUPPORTED, "the adjoint takes 2D uniform contexts");
+    if (steps < 1 || ckpt_every < 1) return fail(GLBM_E_INVAL, "steps and ckpt_every must be >= 1");
+    const int64_t K = ckpt_every < steps ? ckpt_every : steps;
+    const int64_t nseg = (steps + K - 1) / K;
+    const size_t pool = bytes_state(c);
+    const Geo &g = c->geo[0];
+    const size_t mu_bytes = (size_t)g.Q * g.plane * sizeof(double);
+    const long long nblk = glbm_adj_blocks(g.Lx, g.Ly);
+    Scratch S(c->A, c->stream);
+    char *ck = (char *)S.get(pool * nseg);
+    char *seg = (char *)S.get(pool * K);
+    double *mu0 = (double *)S.get(mu_bytes), *mu1 = (double *)S.get(mu_bytes);
+    double *G = (double *)S.get(2 * (size_t)g.Lx * sizeof(double));
+    double *gpart = (double *)S.get(2 * (size_t)nblk * sizeof(double));
+    double *gsum = (double *)S.get(2 * sizeof(double));
+    if (!ck || !seg || !mu0 || !mu1 || !G || !gpart || !gsum)
+        return fail(GLBM_E_NOMEM, "adjoint scratch of %.1f MB failed",
+                    (pool * (nseg + K) + 2.0 * mu_bytes) / 1e6);
+    const int64_t t_start = c->t;
+
+    // forward with checkpoints
+    for (int64_t s = 0; s < nseg; ++s) {
+        CUDA_TRY(cudaMemcpyAsync(ck + pool * s, c->buf[c->cur], pool, cudaMemcpyDeviceToDevice, c->stream));
+        const int64_t len = std::min<int64_t>(K, steps - s * K);
+        glbm_status st = glbm_step(c, len);
+        if (st != GLBM_OK) return st;
+    }
+    for (int i = 0; i < c->n_inst; ++i) {
+        double mass, jx, jy;
+        glbm_status st = glbm_conservation(c, i, &mass, &jx, &jy);
+        if (st != GLBM_OK) return st;
+        J[i] = jx / c->geo[i].Lx;
+    }
+    const int64_t t_end = c->t;
+
+    // backward, one instance at a time
+    for (int i = 0; i < c->n_inst; ++i) {
+        AdjArgs a;
+        memset(&a, 0, sizeof(a));
+        a.tab = c->tabs[g.N];
+        a.ip = c->d_ip + i;
+        a.G = G;
+        a.Gw = G;
+        a.gpart = gpart;
+        a.Lx = g.Lx;
+        a.Ly = g.Ly;
+        a.pitch = g.pitch;
+        a.bc = c->cfg[i].bc;
+        a.N = g.N;
+        a.prec = c->prec;
+        a.plane = g.plane;
+        double *mu_cur = mu0, *mu_nxt = mu1;
+        a.mu_out = mu_cur;
+        CUDA_TRY(glbm_launch_adj_seed(a, c->stream));
+        CUDA_TRY(cudaMemsetAsync(gpart, 0, 2 * (size_t)nblk * sizeof(double), c->stream));
+        for (int64_t s = nseg - 1; s >= 0; --s) {
+            const int64_t t0 = s * K, len = std::min<int64_t>(K, steps - t0);
+            // recompute X_t0 .. X_t0+len-1 with the dither counter of the forward pass
+            CUDA_TRY(cudaMemcpyAsync(seg, ck + pool * s, pool, cudaMemcpyDeviceToDevice, c->stream));
+            CUDA_TRY(set_clock(c, t_start + t0));
+            for (int64_t r = 0; r + 1 < len; ++r) {
+                CUDA_TRY(launch_2d_between(c, seg + pool * r, seg + pool * (r + 1), c->stream));
+                c->launches += 1;
+            }
+            for (int64_t r = len - 1; r >= 0; --r) {
+                a.X = seg + pool * r + (size_t)c->geo[i].off * c->elem;
+                a.mu_in = mu_cur;
+                a.mu_out = mu_nxt;
+                CUDA_TRY(glbm_launch_adj_step(a, c->stream));
+                c->launches += 2;
+                std::swap(mu_cur, mu_nxt);
+            }
+        }
+        CUDA_TRY(glbm_launch_adj_sum(gpart, nblk, gsum, c->stream));
+        double h[2];
+        CUDA_TRY(cudaMemcpyAsync(h, gsum, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
+        CUDA_TRY(cudaStreamSynchronize(c->stream));
+        dJ_dtau[i] = h[0];
+        dJ_dg[i] = h[1];
+    }
+    CUDA_TRY(set_clock(c, t_end));
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
+    return GLBM_OK;
+}

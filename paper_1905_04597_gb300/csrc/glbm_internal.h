@@ -125,3 +125,21 @@ cudaError_t glbm_launch_step1d(const AuxArgs &a, const void *fin, void *fout, in
                                unsigned *status, cudaStream_t s);
 cudaError_t glbm_launch_run1d_resident(const AuxArgs &a, void *f, int inst, long long steps,
                                        unsigned *status, cudaStream_t s, int *ok);
+
+// Adjoint step of one instance (glbm_adjoint.cu).
+struct AdjArgs {
+    AxisTable tab;
+    const InstParams *ip;  // this instance
+    const void *X;         // forward state X_t of the instance (FP64, or FP32 deviations)
+    const double *mu_in;   // mu_{t+1} = dJ/dF_{t+1}, pitched like the populations
+    double *mu_out;        // mu_t
+    const double *G;       // [2][Lx] wall sums of mu_in (lower, upper)
+    double *Gw;            // the same array, written by the wall kernel
+    double *gpart;         // [blocks][2] partials of dJ/dtau, dJ/dg, summed over steps
+    int Lx, Ly, pitch, bc, N, prec;
+    long long plane;
+};
+long long glbm_adj_blocks(int Lx, int Ly);
+cudaError_t glbm_launch_adj_seed(const AdjArgs &a, cudaStream_t s);
+cudaError_t glbm_launch_adj_step(const AdjArgs &a, cudaStream_t s);
+cudaError_t glbm_launch_adj_sum(const double *gpart, long long nblocks, double *out, cudaStream_t s);

@@ -77,6 +77,7 @@ def lib():
         "glbm_tau": ([vp, i], ctypes.c_double),
         "glbm_eq_table": ([i, dp, sz], i),
         "glbm_conservation_noalloc": ([vp, i, i64, vp, vp], i),
+        "glbm_adjoint_flowrate": ([vp, i64, i64, dp, dp, dp], i),
         "glbm_last_error": ([], ctypes.c_char_p),
     }
     for name, (args, res) in sig.items():
@@ -258,6 +259,14 @@ class Lattice:
     def load(self, path):
         check(lib().glbm_load(self.h, str(path).encode()))
 
+    def adjoint_flowrate(self, steps, ckpt_every=100):
+        """Advance `steps` steps and return per instance (J, dJ/dtau, dJ/dg) of the flow
+        rate J = (1/nx) sum of the x-momentum of S(X_T), by the discrete adjoint."""
+        n = self.n
+        J, dt, dg = (ctypes.c_double * n)(), (ctypes.c_double * n)(), (ctypes.c_double * n)()
+        check(lib().glbm_adjoint_flowrate(self.h, int(steps), int(ckpt_every), J, dt, dg))
+        return np.array(J[:]), np.array(dt[:]), np.array(dg[:])
+
     @property
     def time(self):
         return lib().glbm_time(self.h)
@@ -268,3 +277,35 @@ class Lattice:
 
     def tau(self, inst=0):
         return lib().glbm_tau(self.h, inst)
+
+
+def _flowrate_autograd():
+    import torch
+
+    class FlowRate(torch.autograd.Function):
+        """J(tau, g): flow rate of a force-driven (or wall-driven) channel after
+        `steps` steps from rest, with gradients from the hand-written adjoint.
+
+        config: glbm lattice configuration without tau/g (dims, nx, ny, k, bc,
+        prec, u_wall_lo, u_wall_hi); tau and g are 0-d float64 tensors."""
+
+        @staticmethod
+        def forward(ctx, tau, g, config, steps, ckpt_every=100):
+            cfg = dict(config, tau=float(tau), kn=0.0, g=float(g))
+            with Lattice(cfg) as lat:
+                J, dtau, dg = lat.adjoint_flowrate(steps, ckpt_every)
+            ctx.save_for_backward(torch.tensor(dtau[0], dtype=torch.float64),
+                                  torch.tensor(dg[0], dtype=torch.float64))
+            return torch.tensor(J[0], dtype=torch.float64)
+
+        @staticmethod
+        def backward(ctx, grad):
+            dtau, dg = ctx.saved_tensors
+            return grad * dtau, grad * dg, None, None, None
+
+    return FlowRate
+
+
+def flow_rate(tau, g, config, steps, ckpt_every=100):
+    """Differentiable flow rate (torch.autograd) through libglbm's adjoint."""
+    return _flowrate_autograd().apply(tau, g, config, steps, ckpt_every)

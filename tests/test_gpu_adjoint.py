@@ -1,0 +1,105 @@
+"""Gradient of the flow rate by the hand-written adjoint (glbm_adjoint_flowrate)
+against the oracle's forward-mode dual numbers and against central finite
+differences of GPU forward runs."""
+import numpy as np
+import pytest
+
+from oracle import oracle as orc
+from paper_1905_04597_gb300 import glbm, inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+def _compare(cfg, steps, ckpt, fields, rtol):
+    N = cfg["k"] + 1
+    lat = glbm.Lattice(cfg)
+    lat.set_equilibrium(0, *fields)
+    J, dtau, dg = lat.adjoint_flowrate(steps, ckpt)
+    assert lat.time == steps
+    lat.close()
+    o = orc.Lattice(2, N, N, cfg["nx"], cfg["ny"], cfg.get("bc", orc.BC_WALLS), cfg["tau"],
+                    cfg.get("u_wall_lo", 0.0), cfg.get("u_wall_hi", 0.0), cfg.get("g", 0.0))
+    oJ, otau, og = o.flowrate_grad(o.equilibrium(*fields), steps)
+    assert J[0] == pytest.approx(oJ, rel=rtol, abs=1e-300)
+    assert dtau[0] == pytest.approx(otau, rel=rtol)
+    assert dg[0] == pytest.approx(og, rel=rtol)
+    return J[0], dtau[0], dg[0]
+
+
+@pytest.mark.parametrize("k", [0, 2, 4])
+def test_adjoint_fp64_matches_dual_numbers(k):
+    """Random initial fields, force and moving walls; 61 steps with checkpoints every
+    16 (a short last segment)."""
+    nx, ny = 20, 3 * (k + 1) + 5
+    cfg = dict(dims=2, nx=nx, ny=ny, k=k, tau=0.8, prec=glbm.FP64, u_wall_lo=-0.02,
+               u_wall_hi=0.04, g=3e-5)
+    _compare(cfg, 61, 16, inputs.random_macro(70 + k, nx, ny), 1e-9)
+
+
+def test_adjoint_periodic_fp64():
+    nx, ny, k = 16, 10, 1
+    cfg = dict(dims=2, nx=nx, ny=ny, k=k, tau=1.3, prec=glbm.FP64, bc=glbm.BC_PERIODIC, g=1e-5)
+    _compare(cfg, 40, 7, inputs.random_macro(81, nx, ny), 1e-9)
+
+
+def test_adjoint_fp32_forward_matches_dual_numbers():
+    nx, ny, k = 24, 16, 3
+    cfg = dict(dims=2, nx=nx, ny=ny, k=k, tau=0.9, prec=glbm.FP32_DEV, u_wall_lo=-0.03,
+               u_wall_hi=0.03, g=2e-5)
+    _compare(cfg, 80, 20, inputs.random_macro(90, nx, ny), 1e-4)
+
+
+def test_adjoint_config_poiseuille_d2q121():
+    """The adjoint workload: D2Q121 (k = 4), 256 x 128, Kn = 0.1, g = 1e-6, 4000 FP32
+    steps with checkpoints every 100. The flow stays x-uniform, so the oracle's
+    dual-number gradient runs on one column. Also checked against central finite
+    differences (h = 1e-4 relative) of FP64 GPU forward runs."""
+    c = inputs.ADJOINT
+    N = c["k"] + 1
+    tau = orc.tau_from_kn(N, c["ny"], c["kn"])
+    cfg = dict(dims=2, nx=c["nx"], ny=c["ny"], k=c["k"], tau=tau, prec=glbm.FP32_DEV, g=c["g"])
+    lat = glbm.Lattice(cfg)
+    J, dtau, dg = lat.adjoint_flowrate(c["steps"], c["ckpt_every"])
+    lat.close()
+    o = orc.Lattice(2, N, N, 1, c["ny"], orc.BC_WALLS, tau, 0.0, 0.0, c["g"])
+    X0 = o.equilibrium(np.ones((c["ny"], 1)), np.zeros((c["ny"], 1)), np.zeros((c["ny"], 1)))
+    oJ, otau, og = o.flowrate_grad(X0, c["steps"])
+    assert J[0] == pytest.approx(oJ, rel=1e-4)
+    assert dtau[0] == pytest.approx(otau, rel=1e-4)
+    assert dg[0] == pytest.approx(og, rel=1e-4)
+
+    def J64(t, g):
+        with glbm.Lattice(dict(cfg, prec=glbm.FP64, tau=t, g=g)) as L:
+            L.step(c["steps"])
+            return L.conservation(0)[1] / c["nx"]
+    h = 1e-4
+    fd_tau = (J64(tau * (1 + h), c["g"]) - J64(tau * (1 - h), c["g"])) / (2 * h * tau)
+    fd_g = (J64(tau, c["g"] * (1 + h)) - J64(tau, c["g"] * (1 - h))) / (2 * h * c["g"])
+    assert dtau[0] == pytest.approx(fd_tau, rel=1e-4)
+    assert dg[0] == pytest.approx(fd_g, rel=1e-4)
+
+
+def test_autograd_function():
+    import torch
+    nx, ny, k = 16, 12, 1
+    config = dict(dims=2, nx=nx, ny=ny, k=k, prec=glbm.FP64)
+    tau = torch.tensor(0.9, dtype=torch.float64, requires_grad=True)
+    g = torch.tensor(2e-5, dtype=torch.float64, requires_grad=True)
+    J = glbm.flow_rate(tau, g, config, steps=50, ckpt_every=10)
+    (3.0 * J).backward()
+    N = k + 1
+    o = orc.Lattice(2, N, N, nx, ny, orc.BC_WALLS, 0.9, 0.0, 0.0, 2e-5)
+    X0 = o.equilibrium(np.ones((ny, nx)), np.zeros((ny, nx)), np.zeros((ny, nx)))
+    oJ, otau, og = o.flowrate_grad(X0, 50)
+    assert J.item() == pytest.approx(oJ, rel=1e-10)
+    assert tau.grad.item() == pytest.approx(3 * otau, rel=1e-9)
+    assert g.grad.item() == pytest.approx(3 * og, rel=1e-9)
