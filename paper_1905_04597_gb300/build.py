@@ -64,11 +64,17 @@ def build(verbose: bool = False, jobs: int | None = None) -> str:
     if todo:
         with ThreadPoolExecutor(max_workers=jobs or min(len(todo), os.cpu_count() or 4)) as ex:
             list(ex.map(run, todo))
-    if todo or not os.path.exists(LIB):
+    # relink when an object changed or the source list did (a removed source
+    # must leave the library too)
+    manifest = os.path.join(OBJ, "objects.txt")
+    listed = open(manifest).read() if os.path.exists(manifest) else ""
+    if todo or not os.path.exists(LIB) or listed != "\n".join(objs):
         tmp = LIB + f".tmp{os.getpid()}"
         run([nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart_static", "-lrt", "-ldl",
              "-lpthread"])
         os.replace(tmp, LIB)
+        with open(manifest, "w") as fh:
+            fh.write("\n".join(objs))
     return LIB
 
 

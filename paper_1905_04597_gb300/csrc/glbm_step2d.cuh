@@ -64,22 +64,25 @@ struct Step2D {
         const bool need_hi = walls && (y0 + R > Ly - N);
         if (need_lo || need_hi) {
             T slo = T(0), shi = T(0);
-            int p = 0;
+            // pairs (|ny|, row) = (aa, k), k < aa, enumerated p = aa(aa-1)/2 + k,
+            // dealt to the warps round robin; the loop stays rolled (the wall
+            // prologue runs on few tiles and must not grow the code)
+#pragma unroll 1
+            for (int p = w; p < N * (N + 1) / 2; p += NW) {
+                int aa = 1, k = p;
+                while (k >= aa) {
+                    k -= aa;
+                    ++aa;
+                }
+                if (need_lo) {  // velocity ny = -aa leaving row k through y = -1/2
+                    const T *pl = fin + ((N - aa) * Q1 * plane + k * pitch);
 #pragma unroll
-            for (int aa = 1; aa <= N; ++aa) {
+                    for (int ix = 0; ix < Q1; ++ix) slo += __ldg(pl + cofs[ix]);
+                }
+                if (need_hi) {  // velocity ny = +aa leaving row Ly-1-k through y = Ly-1/2
+                    const T *ph = fin + ((N + aa) * Q1 * plane + (Ly - 1 - k) * pitch);
 #pragma unroll
-                for (int k = 0; k < aa; ++k, ++p) {
-                    if (p % NW != w) continue;
-                    if (need_lo) {  // velocity ny = -aa leaving row k through y = -1/2
-                        const T *pl = fin + ((N - aa) * Q1 * plane + k * pitch);
-#pragma unroll
-                        for (int ix = 0; ix < Q1; ++ix) slo += __ldg(pl + cofs[ix]);
-                    }
-                    if (need_hi) {  // velocity ny = +aa leaving row Ly-1-k through y = Ly-1/2
-                        const T *ph = fin + ((N + aa) * Q1 * plane + (Ly - 1 - k) * pitch);
-#pragma unroll
-                        for (int ix = 0; ix < Q1; ++ix) shi += __ldg(ph + cofs[ix]);
-                    }
+                    for (int ix = 0; ix < Q1; ++ix) shi += __ldg(ph + cofs[ix]);
                 }
             }
             sm.dsum[w][0][lane] = slo;
@@ -101,57 +104,56 @@ struct Step2D {
         }
 
         // ---- phase 1: pull and partial moments -----------------------------
+        // This warp's velocity rows are iy = g + k G (k = 0..RPG-1): the row is a
+        // run-time value while the register array f[k][ix] keeps compile-time
+        // indices, so all G warp groups share one copy of the unrolled code.
         T f[RPG][Q1];
         T s_r = T(0), c_r = T(0), s_x = T(0), c_x = T(0), s_y = T(0), c_y = T(0);
+        // loads first, all independent
 #pragma unroll
-        for (int gi = 0; gi < G; ++gi) {
-            if (g != gi) continue;
-            // loads first, all independent
+        for (int k = 0; k < RPG; ++k) {
+            const int iy = g + k * G;
+            if (iy < Q1) {
+                const int ny = iy - N;
+                int ys = yc - ny;
+                ys = walls ? min(max(ys, 0), Ly - 1) : wrap_index(ys, Ly);
+                const T *rowp = fin + (iy * Q1 * plane + ys * pitch);
 #pragma unroll
-            for (int k = 0; k < RPG; ++k) {
-                const int iy = gi + k * G;
-                if (iy < Q1) {
-                    const int ny = iy - N;
-                    int ys = yc - ny;
-                    ys = walls ? min(max(ys, 0), Ly - 1) : wrap_index(ys, Ly);
-                    const T *rowp = fin + (iy * Q1 * plane + ys * pitch);
-#pragma unroll
-                    for (int ix = 0; ix < Q1; ++ix) f[k][ix] = __ldg(rowp + cofs[ix]);
-                }
+                for (int ix = 0; ix < Q1; ++ix) f[k][ix] = __ldg(rowp + cofs[ix]);
             }
-            // wall re-emission and row sums
+        }
+        // wall re-emission and row sums
 #pragma unroll
-            for (int k = 0; k < RPG; ++k) {
-                const int iy = gi + k * G;
-                if (iy < Q1) {
-                    const int ny = iy - N;
-                    const int ys = yc - ny;
-                    if (walls && (ys < 0 || ys >= Ly)) {  // uniform across the warp
-                        const bool lo = ys < 0;
-                        const T wy = A::W(tab, iy);
-                        const T rw = sm.rw[lo ? 0 : 1][lane];
+        for (int k = 0; k < RPG; ++k) {
+            const int iy = g + k * G;
+            if (iy < Q1) {
+                const int ny = iy - N;
+                const int ys = yc - ny;
+                if (walls && (ys < 0 || ys >= Ly)) {  // uniform across the warp
+                    const bool lo = ys < 0;
+                    const T wy = A::W(tab, iy);
+                    const T rw = sm.rw[lo ? 0 : 1][lane];
 #pragma unroll
-                        for (int ix = 0; ix < Q1; ++ix) {
-                            if (DEV) {
-                                const T dw = lo ? (T)ip.dw_lo_f[ix] : (T)ip.dw_hi_f[ix];
-                                // W^y (drho_w W^x + rho_w (E^x(u_w) - W^x))
-                                f[k][ix] = wy * fma(rw, A::W(tab, ix), (T(1) + rw) * dw);
-                            } else {
-                                const T ew = lo ? (T)ip.ew_lo[ix] : (T)ip.ew_hi[ix];
-                                f[k][ix] = rw * ew * wy;
-                            }
+                    for (int ix = 0; ix < Q1; ++ix) {
+                        if (DEV) {
+                            const T dw = lo ? (T)ip.dw_lo_f[ix] : (T)ip.dw_hi_f[ix];
+                            // W^y (drho_w W^x + rho_w (E^x(u_w) - W^x))
+                            f[k][ix] = wy * fma(rw, A::W(tab, ix), (T(1) + rw) * dw);
+                        } else {
+                            const T ew = lo ? (T)ip.ew_lo[ix] : (T)ip.ew_hi[ix];
+                            f[k][ix] = rw * ew * wy;
                         }
                     }
-                    T rs = T(0);
-#pragma unroll
-                    for (int ix = 0; ix < Q1; ++ix) rs += f[k][ix];
-                    T jx = T(0);
-#pragma unroll
-                    for (int n = 1; n <= N; ++n) jx = fma(T(n), f[k][N + n] - f[k][N - n], jx);
-                    acc2(s_r, c_r, rs);
-                    acc2(s_x, c_x, jx);
-                    if (ny != 0) acc2(s_y, c_y, T(ny) * rs);
                 }
+                T rs = T(0);
+#pragma unroll
+                for (int ix = 0; ix < Q1; ++ix) rs += f[k][ix];
+                T jx = T(0);
+#pragma unroll
+                for (int n = 1; n <= N; ++n) jx = fma(T(n), f[k][N + n] - f[k][N - n], jx);
+                acc2(s_r, c_r, rs);
+                acc2(s_x, c_x, jx);
+                if (ny != 0) acc2(s_y, c_y, T(ny) * rs);
             }
         }
         sm.part[r][g][0][lane] = s_r;
@@ -202,40 +204,37 @@ struct Step2D {
         // and the force F_i = W^x_i xi_x W^y_i g/theta joins the equilibrium
         // through the per-row factor gr = W^y g / (theta omega).
 #pragma unroll
-        for (int gi = 0; gi < G; ++gi) {
-            if (g != gi) continue;
+        for (int k = 0; k < RPG; ++k) {
+            const int iy = g + k * G;
+            if (iy < Q1) {
+                const int ny = iy - N;
+                const T wy = A::W(tab, iy);
+                const T dy = G == 1 ? eq_dev_one<N, T>(tab, uy, ny) : eq_dev_one_run<N, T>(tab, uy, ny);
+                const T rey = rho * (wy + dy);  // rho e^y
+                const T gr = gto * wy;
+                // FP32: delta f^eq = d^x rho e^y + W^x (drho W^y + rho d^y)
+                const T B = DEV ? fma(drho, wy, rho * dy) : T(0);
+                T *const op = obase + iy * Q1 * plane;
+                const unsigned q0 = (unsigned)(iy * Q1);
 #pragma unroll
-            for (int k = 0; k < RPG; ++k) {
-                const int iy = gi + k * G;
-                if (iy < Q1) {
-                    const int ny = iy - N;
-                    const T wy = A::W(tab, iy);
-                    const T dy = eq_dev_one<N, T>(tab, uy, ny);
-                    const T rey = rho * (wy + dy);  // rho e^y
-                    const T gr = gto * wy;
-                    // FP32: delta f^eq = d^x rho e^y + W^x (drho W^y + rho d^y)
-                    const T B = DEV ? fma(drho, wy, rho * dy) : T(0);
-                    T *const op = obase + iy * Q1 * plane;
-#pragma unroll
-                    for (int ix = 0; ix < Q1; ++ix) {
-                        const int nx = ix - N;
-                        const T f0 = f[k][ix];
-                        T v;
-                        if (DEV) {
-                            const T Bn = nx != 0 ? fma(T(nx), gr, B) : B;
-                            const T eq = fma(dx[ix], rey, A::W(tab, ix) * Bn);
-                            // increment plus dither, then one rounding of the store
-                            const unsigned q = iy * Q1 + ix;
-                            const unsigned rnd = hnode * (0x9E3779B9u * (2u * q + 1u)) + 0x7F4A7C15u * q;
-                            const T inc = fma(om, eq - f0, (T)dither_ulp((float)f0, rnd));
-                            v = f0 + inc;
-                        } else {
-                            T eq = ex[ix] * rey;
-                            if (nx != 0) eq = fma(A::WN(tab, ix), gr, eq);
-                            v = fma(om, eq - f0, f0);
-                        }
-                        if (active) op[ix * plane] = v;
+                for (int ix = 0; ix < Q1; ++ix) {
+                    const int nx = ix - N;
+                    const T f0 = f[k][ix];
+                    T v;
+                    if (DEV) {
+                        const T Bn = nx != 0 ? fma(T(nx), gr, B) : B;
+                        const T eq = fma(dx[ix], rey, A::W(tab, ix) * Bn);
+                        // increment plus dither, then one rounding of the store
+                        const unsigned q = q0 + ix;
+                        const unsigned rnd = hnode * (0x9E3779B9u * (2u * q + 1u)) + 0x7F4A7C15u * q;
+                        const T inc = fma(om, eq - f0, (T)dither_ulp((float)f0, rnd));
+                        v = f0 + inc;
+                    } else {
+                        T eq = ex[ix] * rey;
+                        if (nx != 0) eq = fma(A::WN(tab, ix), gr, eq);
+                        v = fma(om, eq - f0, f0);
                     }
+                    if (active) op[ix * plane] = v;
                 }
             }
         }

@@ -375,3 +375,54 @@ def test_device_pointers_and_torch_allocator():
         lat.close()
     finally:
         glbm.uninstall_allocator()
+
+
+# --------------------------------------------------------------------------
+# high levels: narrow and ragged widths, several instances in one launch
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("bc", [glbm.BC_WALLS, glbm.BC_PERIODIC])
+@pytest.mark.parametrize("nx", [64, 100, 36, 4])
+@pytest.mark.parametrize("k", [3, 4, 5, 6, 7])
+def test_high_level_one_step(k, nx, bc):
+    """Pulls that wrap the periodic x edge once (nx = 36, 100) or several times
+    (nx = 4 < the largest shift), walls and periodic rows, one step."""
+    N = k + 1
+    ny = 2 * N + 3
+    tau, uw_lo, uw_hi, g = 0.77, 0.03, -0.05, 2e-4
+    f0 = inputs.random_populations(500 + k + nx, (2 * N + 1) ** 2, ny, nx)
+    lat = glbm.Lattice(dict(dims=2, nx=nx, ny=ny, k=k, tau=tau, bc=bc, prec=glbm.FP32_DEV,
+                            u_wall_lo=uw_lo, u_wall_hi=uw_hi, g=g))
+    lat.set_populations(0, f0)
+    lat.step(1)
+    lat.sync()
+    got = lat.get_populations(0)
+    o = oracle_lattice(2, k, nx, ny, bc, tau, uw_lo, uw_hi, g)
+    want, _ = o.run(f0, 1)
+    err = np.abs(got - want).max() / np.abs(want).max()
+    assert err < POP_TOL[glbm.FP32_DEV], err
+    lat.close()
+
+
+@pytest.mark.parametrize("k", [3, 7])
+def test_high_level_many_steps_batch(k):
+    """Three instances in one launch, 50 steps, moments against the oracle."""
+    N = k + 1
+    nx, ny, steps = 68, 3 * N + 4, 50
+    cfgs, fields = [], []
+    for i, kn in enumerate((0.05, 0.3, 2.0)):
+        cfgs.append(dict(dims=2, nx=nx, ny=ny, k=k, kn=kn, prec=glbm.FP32_DEV,
+                         u_wall_lo=-0.04 * i, u_wall_hi=0.03, g=1e-5 * i))
+        fields.append(inputs.random_macro(600 + 10 * k + i, nx, ny))
+    lat = glbm.Lattice(cfgs)
+    for i, f in enumerate(fields):
+        lat.set_equilibrium(i, *f)
+    lat.step(steps)
+    lat.sync()
+    for i, c in enumerate(cfgs):
+        o = oracle_lattice(2, k, nx, ny, orc.BC_WALLS, orc.tau_from_kn(N, ny, c["kn"]),
+                           c["u_wall_lo"], c["u_wall_hi"], c["g"])
+        X, _ = o.run(o.equilibrium(*fields[i]), steps)
+        want, F = oracle_moments(o, X)
+        errs = rel_errors(lat.moments(i), want, F=F)
+        assert max(errs.values()) < TOL[glbm.FP32_DEV], (i, errs)
+    lat.close()
