@@ -210,6 +210,37 @@ glbm_status glbm_conservation_noalloc(const double *fields, int dims, int64_t no
 glbm_status glbm_adjoint_flowrate(glbm_ctx *ctx, int64_t steps, int64_t ckpt_every, double *J,
                                   double *dJ_dtau, double *dJ_dg);
 
+/*
+ * Tile shapes of the fused 2D step (an engineering choice; the paper has no
+ * counterpart). A CTA of the stream-collide kernel covers 32 columns x R node
+ * rows, and each node's 2k+3 velocity rows are dealt to G warps. Every level
+ * k (0..GLBM_LEVELS-1) and precision has up to GLBM_MAX_TILES candidate
+ * shapes; entry 0 is the default of a new context.
+ *
+ * glbm_tile_count returns the number of candidates of level k in precision
+ * prec (0 for an invalid pair); glbm_tile_shape returns candidate idx.
+ * glbm_get_tiles writes the index in use for every level (array of
+ * GLBM_LEVELS ints, entry k for level k); glbm_set_tiles sets them (-1 keeps
+ * a level's index; GLBM_E_INVAL and no change if an index is out of range).
+ *
+ * glbm_autotune times every candidate of every level the context steps: reps
+ * launches each (1..1000) from the current state into the spare buffer, with
+ * CUDA events on the context's stream, and keeps the fastest. The state, the
+ * step clock and the dither sequence are unchanged. If us is non-NULL it
+ * receives the microseconds per launch, us[k * GLBM_MAX_TILES + idx], -1 for
+ * pairs not timed (GLBM_LEVELS * GLBM_MAX_TILES doubles, host memory). R
+ * changes only which CTA a node belongs to; G also groups the partial
+ * moments before their compensated sum, so shapes of different G may differ
+ * in the last bits of FP32 results. 2D contexts only. Synchronises.
+ */
+#define GLBM_LEVELS 8
+#define GLBM_MAX_TILES 6
+int glbm_tile_count(int k, glbm_prec prec);
+glbm_status glbm_tile_shape(int k, glbm_prec prec, int idx, int *G, int *R);
+glbm_status glbm_get_tiles(const glbm_ctx *ctx, int *tiles);
+glbm_status glbm_set_tiles(glbm_ctx *ctx, const int *tiles);
+glbm_status glbm_autotune(glbm_ctx *ctx, int reps, double *us);
+
 /* Checkpoint of every instance's state (header, raw device image, CRC-32).
  * glbm_load requires a context created with the same configuration. */
 glbm_status glbm_save(glbm_ctx *ctx, const char *path);

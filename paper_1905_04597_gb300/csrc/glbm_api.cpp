@@ -121,6 +121,7 @@ struct glbm_ctx {
     int4 *d_items = nullptr;       // heterogeneous work list, sorted by level
     int n_items = 0;
     int group[GLBM_MAXN + 2] = {0};  // first item of each level
+    int tile[GLBM_MAXN + 1] = {0};   // tile shape index per level (glbm_tiles.h)
     cudaGraphExec_t graph[2] = {nullptr, nullptr};  // chunk graphs by starting buffer
     int64_t t = 0;
     int64_t launches = 0;
@@ -392,6 +393,43 @@ extern "C" glbm_status glbm_create(const glbm_config *cfgs, int n, void *stream,
     return GLBM_OK;
 }
 
+// Shape of the tiles of level N in this context.
+static TileShape tile_of(const glbm_ctx *c, int N)
+{
+    TileShape sh[GLBM_MAX_TILES];
+    const int n = glbm_tile_shapes(N, c->prec, sh);
+    return n > 0 ? sh[c->tile[N] < n ? c->tile[N] : 0] : TileShape{1, 1};
+}
+
+// Work list of a heterogeneous batch: every (instance, tile) with the rows of
+// its level's tile shape, grouped by level (instance order within a level).
+static glbm_status build_items(glbm_ctx *c)
+{
+    std::vector<int4> items;
+    for (int i = 0; i < c->n_inst; ++i) {
+        const Geo &g = c->geo[i];
+        const int R = tile_of(c, g.N).R;
+        for (int y0 = 0; y0 < g.Ly; y0 += R)
+            for (int x0 = 0; x0 < g.Lx; x0 += 32) items.push_back(make_int4(i, x0, y0, g.N));
+    }
+    std::stable_sort(items.begin(), items.end(),
+                     [](const int4 &a, const int4 &b) { return a.w < b.w; });
+    for (int N = 0; N <= GLBM_MAXN + 1; ++N) {  // first item of level >= N
+        int k = 0;
+        while (k < (int)items.size() && items[k].w < N) ++k;
+        c->group[N] = k;
+    }
+    CUDA_TRY(cudaStreamSynchronize(c->stream));  // no launch still reads the old list
+    dev_free(c->A, c->d_items, c->stream);
+    c->n_items = (int)items.size();
+    c->d_items = (int4 *)dev_alloc(c->A, sizeof(int4) * items.size(), c->stream);
+    if (!c->d_items) return fail(GLBM_E_NOMEM, "work list allocation failed");
+    CUDA_TRY(cudaMemcpyAsync(c->d_items, items.data(), sizeof(int4) * items.size(),
+                             cudaMemcpyHostToDevice, c->stream));
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
+    return GLBM_OK;
+}
+
 extern "C" glbm_status glbm_batch_create(const glbm_config *cfgs, int n, void *stream, glbm_ctx **out)
 {
     if (!cfgs || n < 1 || !out) return fail(GLBM_E_INVAL, "null argument or n < 1");
@@ -409,31 +447,7 @@ extern "C" glbm_status glbm_batch_create(const glbm_config *cfgs, int n, void *s
     if (!c) return fail(GLBM_E_NOMEM, "host allocation failed");
     c->hetero = true;
     glbm_status st = finish_create(c, cfgs, n, stream);
-    if (st == GLBM_OK) {
-        // work list: every (instance, tile), grouped by level
-        std::vector<int4> items;
-        for (int i = 0; i < n; ++i) {
-            const Geo &g = c->geo[i];
-            const int R = glbm_batched_rows(g.N);
-            for (int y0 = 0; y0 < g.Ly; y0 += R)
-                for (int x0 = 0; x0 < g.Lx; x0 += 32) items.push_back(make_int4(i, x0, y0, g.N));
-        }
-        std::stable_sort(items.begin(), items.end(),
-                         [](const int4 &a, const int4 &b) { return a.w < b.w; });
-        for (int N = 0; N <= GLBM_MAXN + 1; ++N) {  // first item of level >= N
-            int k = 0;
-            while (k < (int)items.size() && items[k].w < N) ++k;
-            c->group[N] = k;
-        }
-        c->n_items = (int)items.size();
-        c->d_items = (int4 *)dev_alloc(c->A, sizeof(int4) * items.size(), c->stream);
-        if (!c->d_items) st = fail(GLBM_E_NOMEM, "work list allocation failed");
-        if (st == GLBM_OK) {
-            cudaError_t e = cudaMemcpy(c->d_items, items.data(), sizeof(int4) * items.size(),
-                                       cudaMemcpyHostToDevice);
-            if (e != cudaSuccess) st = fail(GLBM_E_CUDA, "work list upload: %s", cudaGetErrorString(e));
-        }
-    }
+    if (st == GLBM_OK) st = build_items(c);
     if (st != GLBM_OK) {
         destroy_resources(c);
         delete c;
@@ -584,6 +598,7 @@ static BatchArgs batch_args(const glbm_ctx *c, int from)
     b.items = c->d_items;
     b.n_items = c->n_items;
     for (int N = 0; N <= GLBM_MAXN + 1; ++N) b.group[N] = c->group[N];
+    for (int N = 0; N <= GLBM_MAXN; ++N) b.shape[N] = c->tile[N];
     b.status = c->d_status;
     b.step_ctr = c->d_status + 1;
     b.done_ctr = c->d_status + 2;
@@ -601,8 +616,9 @@ static cudaError_t launch_one_2d(const glbm_ctx *c, int from, cudaStream_t s)
 {
     if (c->hetero) return glbm_launch_batched_f32(batch_args(c, from), s);
     const Step2DArgs a = step_args(c, from);
-    return c->prec == GLBM_FP64 ? glbm_launch_step2d_f64(c->geo[0].N, a, c->n_inst, s)
-                                : glbm_launch_step2d_f32(c->geo[0].N, a, c->n_inst, s);
+    const int N = c->geo[0].N;
+    return c->prec == GLBM_FP64 ? glbm_launch_step2d_f64(N, c->tile[N], a, c->n_inst, s)
+                                : glbm_launch_step2d_f32(N, c->tile[N], a, c->n_inst, s);
 }
 
 static glbm_status capture_chunk(glbm_ctx *c, int from)
@@ -852,8 +868,9 @@ static cudaError_t launch_2d_between(const glbm_ctx *c, const void *fin, void *f
     Step2DArgs a = step_args(c, 0);
     a.fin = fin;
     a.fout = fout;
-    return c->prec == GLBM_FP64 ? glbm_launch_step2d_f64(c->geo[0].N, a, c->n_inst, s)
-                                : glbm_launch_step2d_f32(c->geo[0].N, a, c->n_inst, s);
+    const int N = c->geo[0].N;
+    return c->prec == GLBM_FP64 ? glbm_launch_step2d_f64(N, c->tile[N], a, c->n_inst, s)
+                                : glbm_launch_step2d_f32(N, c->tile[N], a, c->n_inst, s);
 }
 
 struct Scratch {
@@ -960,6 +977,120 @@ extern "C" glbm_status glbm_adjoint_flowrate(glbm_ctx *c, int64_t steps, int64_t
         dJ_dg[i] = h[1];
     }
     CUDA_TRY(set_clock(c, t_end));
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
+    return GLBM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// tile shapes and the autotuner
+
+extern "C" int glbm_tile_count(int k, glbm_prec prec)
+{
+    TileShape sh[GLBM_MAX_TILES];
+    if (k < 0 || k >= GLBM_LEVELS || (prec != GLBM_FP64 && prec != GLBM_FP32_DEV)) return 0;
+    return glbm_tile_shapes(k + 1, prec, sh);
+}
+
+extern "C" glbm_status glbm_tile_shape(int k, glbm_prec prec, int idx, int *G, int *R)
+{
+    TileShape sh[GLBM_MAX_TILES];
+    const int n = glbm_tile_count(k, prec);
+    if (!G || !R) return fail(GLBM_E_INVAL, "null argument");
+    if (idx < 0 || idx >= n) return fail(GLBM_E_INVAL, "no tile shape %d for k=%d", idx, k);
+    glbm_tile_shapes(k + 1, prec, sh);
+    *G = sh[idx].G;
+    *R = sh[idx].R;
+    return GLBM_OK;
+}
+
+extern "C" glbm_status glbm_get_tiles(const glbm_ctx *c, int *tiles)
+{
+    if (!c || !tiles) return fail(GLBM_E_INVAL, "null argument");
+    for (int k = 0; k < GLBM_LEVELS; ++k) tiles[k] = c->tile[k + 1];
+    return GLBM_OK;
+}
+
+// Graphs and (in batches) the work list follow the tile shapes.
+static glbm_status tiles_changed(glbm_ctx *c)
+{
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
+    for (int i = 0; i < 2; ++i) {
+        if (c->graph[i]) cudaGraphExecDestroy(c->graph[i]);
+        c->graph[i] = nullptr;
+    }
+    return c->hetero ? build_items(c) : GLBM_OK;
+}
+
+extern "C" glbm_status glbm_set_tiles(glbm_ctx *c, const int *tiles)
+{
+    if (!c || !tiles) return fail(GLBM_E_INVAL, "null argument");
+    for (int k = 0; k < GLBM_LEVELS; ++k)
+        if (tiles[k] < -1 || tiles[k] >= glbm_tile_count(k, (glbm_prec)c->prec))
+            return fail(GLBM_E_INVAL, "tile index %d out of range for k=%d", tiles[k], k);
+    for (int k = 0; k < GLBM_LEVELS; ++k)
+        if (tiles[k] >= 0) c->tile[k + 1] = tiles[k];
+    return tiles_changed(c);
+}
+
+// Whether the context steps instances of level N.
+static bool level_present(const glbm_ctx *c, int N)
+{
+    if (c->hetero) return c->group[N + 1] > c->group[N];
+    return c->geo[0].N == N;
+}
+
+// One launch of level N's instances from the current buffer into the spare one.
+static cudaError_t launch_level_once(const glbm_ctx *c, int N)
+{
+    if (c->hetero) return glbm_launch_batched_level(N, batch_args(c, c->cur), false, c->stream);
+    return launch_one_2d(c, c->cur, c->stream);
+}
+
+extern "C" glbm_status glbm_autotune(glbm_ctx *c, int reps, double *us)
+{
+    if (!c) return fail(GLBM_E_INVAL, "null context");
+    if (c->dims != 2) return fail(GLBM_E_UNSUPPORTED, "tile shapes apply to 2D lattices");
+    if (reps < 1 || reps > 1000) return fail(GLBM_E_INVAL, "reps must be in 1..1000");
+    if (us)
+        for (int i = 0; i < GLBM_LEVELS * GLBM_MAX_TILES; ++i) us[i] = -1.0;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    CUDA_TRY(cudaEventCreate(&e0));
+    cudaError_t ce = cudaEventCreate(&e1);
+    glbm_status st = ce == cudaSuccess ? GLBM_OK : fail(GLBM_E_CUDA, "event: %s", cudaGetErrorString(ce));
+    for (int N = 1; N <= GLBM_MAXN && st == GLBM_OK; ++N) {
+        if (!level_present(c, N)) continue;
+        const int n = glbm_tile_count(N - 1, (glbm_prec)c->prec);
+        int best = c->tile[N];
+        float best_ms = 0.f;
+        for (int idx = 0; idx < n && st == GLBM_OK; ++idx) {
+            c->tile[N] = idx;
+            if (c->hetero && (st = build_items(c)) != GLBM_OK) break;
+            cudaError_t e = launch_level_once(c, N);  // warm-up
+            if (e == cudaSuccess) e = cudaEventRecord(e0, c->stream);
+            for (int r = 0; r < reps && e == cudaSuccess; ++r) e = launch_level_once(c, N);
+            if (e == cudaSuccess) e = cudaEventRecord(e1, c->stream);
+            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            float ms = 0.f;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+            if (e != cudaSuccess) {
+                st = fail(GLBM_E_CUDA, "autotune launch: %s", cudaGetErrorString(e));
+                break;
+            }
+            if (us) us[(N - 1) * GLBM_MAX_TILES + idx] = 1e3 * ms / reps;
+            if (idx == 0 || ms < best_ms) {
+                best_ms = ms;
+                best = idx;
+            }
+        }
+        c->tile[N] = best;
+    }
+    if (e1) cudaEventDestroy(e1);
+    cudaEventDestroy(e0);
+    if (st != GLBM_OK) return st;
+    st = tiles_changed(c);
+    if (st != GLBM_OK) return st;
+    // the uniform FP32 launches advanced the dither counter: put it back
+    CUDA_TRY(set_clock(c, c->t));
     CUDA_TRY(cudaStreamSynchronize(c->stream));
     return GLBM_OK;
 }

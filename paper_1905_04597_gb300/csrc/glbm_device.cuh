@@ -153,10 +153,10 @@ __device__ __forceinline__ unsigned hash32(unsigned x)
 // slowly relaxing moments would grow like 1/omega).
 __device__ __forceinline__ float dither_ulp(float ref, unsigned r)
 {
-    // 2^(exponent - 23 - 32): one ulp of ref per 2^32 of the signed word (0 for
-    // ref below 2^-72, where no dither is needed)
-    const int e = (int)(__float_as_uint(ref) & 0x7F800000u) - (55 << 23);
-    return (float)(int)r * __int_as_float(max(e, 0));
+    // the signed word times 2^-55 lies in [-2^-24, 2^-24); times the power of
+    // two of ref's exponent (0 for zero and subnormal ref) that is half an ulp
+    const float p2 = __int_as_float(__float_as_int(ref) & 0x7F800000);
+    return ((float)(int)r * 0x1p-55f) * p2;
 }
 
 __device__ __forceinline__ int wrap_index(int i, int L)

@@ -82,6 +82,15 @@ struct Step2DArgs {
     long long inst_stride;// elements per instance
 };
 
+// Tile shape of the fused 2D step: G warps share a node's velocity rows, R node
+// rows per CTA (the candidates per level are listed in glbm_tiles.h).
+struct TileShape {
+    int G, R;
+};
+// Candidate shapes of level N (1..GLBM_MAXN) in precision prec (0 FP64, 1 FP32
+// deviations): fills out[0..count) and returns count (0 for an invalid level).
+int glbm_tile_shapes(int N, int prec, TileShape *out);
+
 // Arguments of one step of a heterogeneous batch: one launch per level over
 // that level's slice of a work list of (instance, x0, y0, N) tiles.
 struct BatchArgs {
@@ -92,15 +101,24 @@ struct BatchArgs {
     const int4 *items;         // work list, sorted by level
     int n_items;
     int group[GLBM_MAXN + 2];  // items of level N: [group[N], group[N + 1]) (group[0] unused)
+    int shape[GLBM_MAXN + 1];  // FP32 tile shape index of each level
     unsigned *status, *step_ctr, *done_ctr;
 };
-int glbm_batched_rows(int N);                   // node rows per tile of level N
 int glbm_batched_launches(const BatchArgs &a);  // launches per step (levels present)
 cudaError_t glbm_launch_batched_f32(const BatchArgs &a, cudaStream_t s);
+cudaError_t glbm_launch_batched_level(int N, const BatchArgs &a, bool advance, cudaStream_t s);
+// One level's launch of a batch step; `advance` moves the launch counter on.
+template <int N>
+cudaError_t glbm_batched_level(const BatchArgs &a, bool advance, cudaStream_t s);
 
-// Launchers (return cudaError_t of the launch).
-cudaError_t glbm_launch_step2d_f32(int N, const Step2DArgs &a, int n_inst, cudaStream_t s);
-cudaError_t glbm_launch_step2d_f64(int N, const Step2DArgs &a, int n_inst, cudaStream_t s);
+// Launchers of the uniform step with tile shape index `shape` (return the
+// cudaError_t of the launch; cudaErrorInvalidValue for an unknown level/shape).
+cudaError_t glbm_launch_step2d_f32(int N, int shape, const Step2DArgs &a, int n_inst,
+                                   cudaStream_t s);
+cudaError_t glbm_launch_step2d_f64(int N, int shape, const Step2DArgs &a, int n_inst,
+                                   cudaStream_t s);
+template <int N, typename T>
+cudaError_t glbm_step2d_level(int shape, const Step2DArgs &a, int n_inst, cudaStream_t s);
 
 // Auxiliary kernels (glbm_aux.cu).
 struct AuxArgs {

@@ -20,6 +20,7 @@
 // moments with compensated row sums; FP64 mode stores f.
 #pragma once
 #include "glbm_device.cuh"
+#include "glbm_tiles.h"
 
 template <int N, typename T, int G, int R>
 struct Step2D {
@@ -190,6 +191,8 @@ struct Step2D {
 
         T dx[Q1];
         eq_dev_all<N, T>(tab, ux, dx);
+        T dyall[G == 1 ? Q1 : 1];  // one warp group: E^y - W for every row at once
+        if constexpr (G == 1) eq_dev_all<N, T>(tab, uy, dyall);
         T ex[Q1];  // FP64 mode: E^x = W + d^x
 #pragma unroll
         for (int ix = 0; ix < Q1; ++ix) ex[ix] = DEV ? T(0) : A::W(tab, ix) + dx[ix];
@@ -209,7 +212,11 @@ struct Step2D {
             if (iy < Q1) {
                 const int ny = iy - N;
                 const T wy = A::W(tab, iy);
-                const T dy = G == 1 ? eq_dev_one<N, T>(tab, uy, ny) : eq_dev_one_run<N, T>(tab, uy, ny);
+                T dy;
+                if constexpr (G == 1)
+                    dy = dyall[k];
+                else
+                    dy = eq_dev_one_run<N, T>(tab, uy, ny);
                 const T rey = rho * (wy + dy);  // rho e^y
                 const T gr = gto * wy;
                 // FP32: delta f^eq = d^x rho e^y + W^x (drho W^y + rho d^y)
@@ -271,50 +278,25 @@ __global__ void __launch_bounds__(32 * G * R)
     if (S::DEV) advance_launch_counter(a.step_ctr, a.done_ctr);
 }
 
-// Warp-group split (G) and rows per CTA (R) per level and precision: about
-// 80 FP32 or 50 FP64 population registers per thread.
-template <int N, typename T>
-struct Tile2D;
-// FP32 deviations
-template <> struct Tile2D<1, float> { static constexpr int G = 1, R = 8; };
-template <> struct Tile2D<2, float> { static constexpr int G = 1, R = 8; };
-template <> struct Tile2D<3, float> { static constexpr int G = 1, R = 4; };
-template <> struct Tile2D<4, float> { static constexpr int G = 1, R = 4; };
-template <> struct Tile2D<5, float> { static constexpr int G = 2, R = 2; };
-template <> struct Tile2D<6, float> { static constexpr int G = 2, R = 2; };
-template <> struct Tile2D<7, float> { static constexpr int G = 3, R = 1; };
-template <> struct Tile2D<8, float> { static constexpr int G = 4, R = 1; };
-// FP64
-template <> struct Tile2D<1, double> { static constexpr int G = 1, R = 8; };
-template <> struct Tile2D<2, double> { static constexpr int G = 1, R = 4; };
-template <> struct Tile2D<3, double> { static constexpr int G = 2, R = 2; };
-template <> struct Tile2D<4, double> { static constexpr int G = 2, R = 2; };
-template <> struct Tile2D<5, double> { static constexpr int G = 3, R = 1; };
-template <> struct Tile2D<6, double> { static constexpr int G = 4, R = 1; };
-template <> struct Tile2D<7, double> { static constexpr int G = 5, R = 1; };
-template <> struct Tile2D<8, double> { static constexpr int G = 6, R = 1; };
-
-template <int N, typename T>
-cudaError_t launch_step2d_n(const Step2DArgs &a, int n_inst, cudaStream_t s)
+// Launch of tile shape number I of level N (shapes from glbm_tiles.h).
+template <int N, typename T, int I = 0>
+cudaError_t launch_step2d_shape(int shape, const Step2DArgs &a, int n_inst, cudaStream_t s)
 {
-    constexpr int G = Tile2D<N, T>::G, R = Tile2D<N, T>::R;
-    dim3 grid((a.Lx + 31) / 32, (a.Ly + R - 1) / R, n_inst);
-    k_step2d<N, T, G, R><<<grid, 32 * G * R, 0, s>>>(a);
-    return cudaGetLastError();
+    if constexpr (I < Tiles<N, T>::count) {
+        if (shape == I) {
+            constexpr int G = Tiles<N, T>::shape[I].G, R = Tiles<N, T>::shape[I].R;
+            const dim3 grid((a.Lx + 31) / 32, (a.Ly + R - 1) / R, n_inst);
+            k_step2d<N, T, G, R><<<grid, 32 * G * R, 0, s>>>(a);
+            return cudaGetLastError();
+        }
+        return launch_step2d_shape<N, T, I + 1>(shape, a, n_inst, s);
+    } else {
+        return cudaErrorInvalidValue;
+    }
 }
 
-template <typename T>
-cudaError_t launch_step2d(int N, const Step2DArgs &a, int n_inst, cudaStream_t s)
+template <int N, typename T>
+cudaError_t glbm_step2d_level(int shape, const Step2DArgs &a, int n_inst, cudaStream_t s)
 {
-    switch (N) {
-    case 1: return launch_step2d_n<1, T>(a, n_inst, s);
-    case 2: return launch_step2d_n<2, T>(a, n_inst, s);
-    case 3: return launch_step2d_n<3, T>(a, n_inst, s);
-    case 4: return launch_step2d_n<4, T>(a, n_inst, s);
-    case 5: return launch_step2d_n<5, T>(a, n_inst, s);
-    case 6: return launch_step2d_n<6, T>(a, n_inst, s);
-    case 7: return launch_step2d_n<7, T>(a, n_inst, s);
-    case 8: return launch_step2d_n<8, T>(a, n_inst, s);
-    default: return cudaErrorInvalidValue;
-    }
+    return launch_step2d_shape<N, T>(shape, a, n_inst, s);
 }

@@ -78,6 +78,11 @@ def lib():
         "glbm_eq_table": ([i, dp, sz], i),
         "glbm_conservation_noalloc": ([vp, i, i64, vp, vp], i),
         "glbm_adjoint_flowrate": ([vp, i64, i64, dp, dp, dp], i),
+        "glbm_tile_count": ([i, i], i),
+        "glbm_tile_shape": ([i, i, i, ctypes.POINTER(i), ctypes.POINTER(i)], i),
+        "glbm_get_tiles": ([vp, ctypes.POINTER(i)], i),
+        "glbm_set_tiles": ([vp, ctypes.POINTER(i)], i),
+        "glbm_autotune": ([vp, i, dp], i),
         "glbm_last_error": ([], ctypes.c_char_p),
     }
     for name, (args, res) in sig.items():
@@ -95,6 +100,21 @@ def check(status):
     if status == E_UNSTABLE:
         raise UnstableError(status, msg)
     raise GlbmError(status, msg)
+
+
+LEVELS = 8      # levels k = 0..7
+MAX_TILES = 6   # candidate tile shapes per level and precision
+
+
+def tile_shapes(k: int, prec: int) -> list:
+    """Candidate (G, R) tile shapes of level k in precision prec; entry 0 is the default."""
+    L = lib()
+    out = []
+    for idx in range(L.glbm_tile_count(k, prec)):
+        G, R = ctypes.c_int(), ctypes.c_int()
+        check(L.glbm_tile_shape(k, prec, idx, ctypes.byref(G), ctypes.byref(R)))
+        out.append((G.value, R.value))
+    return out
 
 
 def eq_table(k: int) -> np.ndarray:
@@ -266,6 +286,29 @@ class Lattice:
         J, dt, dg = (ctypes.c_double * n)(), (ctypes.c_double * n)(), (ctypes.c_double * n)()
         check(lib().glbm_adjoint_flowrate(self.h, int(steps), int(ckpt_every), J, dt, dg))
         return np.array(J[:]), np.array(dt[:]), np.array(dg[:])
+
+    def tiles(self):
+        """Tile shape index in use for every level k = 0..7."""
+        t = (ctypes.c_int * LEVELS)()
+        check(lib().glbm_get_tiles(self.h, t))
+        return list(t)
+
+    def set_tiles(self, tiles):
+        """Set the tile shape index per level (-1 keeps a level's index)."""
+        t = (ctypes.c_int * LEVELS)(*[int(v) for v in tiles])
+        check(lib().glbm_set_tiles(self.h, t))
+
+    def autotune(self, reps=20):
+        """Time every candidate tile shape of the levels this context steps and
+        keep the fastest. Returns {k: [us per launch of each candidate]}."""
+        us = (ctypes.c_double * (LEVELS * MAX_TILES))()
+        check(lib().glbm_autotune(self.h, int(reps), us))
+        out = {}
+        for k in range(LEVELS):
+            row = [us[k * MAX_TILES + j] for j in range(MAX_TILES)]
+            if any(v >= 0 for v in row):
+                out[k] = [v for v in row if v >= 0]
+        return out
 
     @property
     def time(self):
