@@ -212,10 +212,11 @@ glbm_status glbm_adjoint_flowrate(glbm_ctx *ctx, int64_t steps, int64_t ckpt_eve
 
 /*
  * Tile shapes of the fused 2D step (an engineering choice; the paper has no
- * counterpart). A CTA of the stream-collide kernel covers 32 columns x R node
- * rows, and each node's 2k+3 velocity rows are dealt to G warps. Every level
- * k (0..GLBM_LEVELS-1) and precision has up to GLBM_MAX_TILES candidate
- * shapes; entry 0 is the default of a new context.
+ * counterpart). A CTA of the stream-collide kernel covers 32 V columns x R
+ * node rows: each thread updates V x-adjacent nodes (V = 2: FP32 pairs with
+ * packed two-lane arithmetic), and each node's 2k+3 velocity rows are dealt
+ * to G warps. Every level k (0..GLBM_LEVELS-1) and precision has up to
+ * GLBM_MAX_TILES candidate shapes; entry 0 is the default of a new context.
  *
  * glbm_tile_count returns the number of candidates of level k in precision
  * prec (0 for an invalid pair); glbm_tile_shape returns candidate idx.
@@ -228,15 +229,15 @@ glbm_status glbm_adjoint_flowrate(glbm_ctx *ctx, int64_t steps, int64_t ckpt_eve
  * CUDA events on the context's stream, and keeps the fastest. The state, the
  * step clock and the dither sequence are unchanged. If us is non-NULL it
  * receives the microseconds per launch, us[k * GLBM_MAX_TILES + idx], -1 for
- * pairs not timed (GLBM_LEVELS * GLBM_MAX_TILES doubles, host memory). R
- * changes only which CTA a node belongs to; G also groups the partial
- * moments before their compensated sum, so shapes of different G may differ
- * in the last bits of FP32 results. 2D contexts only. Synchronises.
+ * pairs not timed (GLBM_LEVELS * GLBM_MAX_TILES doubles, host memory). R and
+ * V change only which CTA and thread update a node; G also groups the
+ * partial moments before their compensated sum, so shapes of different G may
+ * differ in the last bits of FP32 results. 2D contexts only. Synchronises.
  */
 #define GLBM_LEVELS 8
-#define GLBM_MAX_TILES 6
+#define GLBM_MAX_TILES 8
 int glbm_tile_count(int k, glbm_prec prec);
-glbm_status glbm_tile_shape(int k, glbm_prec prec, int idx, int *G, int *R);
+glbm_status glbm_tile_shape(int k, glbm_prec prec, int idx, int *G, int *R, int *V);
 glbm_status glbm_get_tiles(const glbm_ctx *ctx, int *tiles);
 glbm_status glbm_set_tiles(glbm_ctx *ctx, const int *tiles);
 glbm_status glbm_autotune(glbm_ctx *ctx, int reps, double *us);

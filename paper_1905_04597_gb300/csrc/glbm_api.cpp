@@ -398,7 +398,7 @@ static TileShape tile_of(const glbm_ctx *c, int N)
 {
     TileShape sh[GLBM_MAX_TILES];
     const int n = glbm_tile_shapes(N, c->prec, sh);
-    return n > 0 ? sh[c->tile[N] < n ? c->tile[N] : 0] : TileShape{1, 1};
+    return n > 0 ? sh[c->tile[N] < n ? c->tile[N] : 0] : TileShape{1, 1, 1};
 }
 
 // Work list of a heterogeneous batch: every (instance, tile) with the rows of
@@ -408,9 +408,9 @@ static glbm_status build_items(glbm_ctx *c)
     std::vector<int4> items;
     for (int i = 0; i < c->n_inst; ++i) {
         const Geo &g = c->geo[i];
-        const int R = tile_of(c, g.N).R;
-        for (int y0 = 0; y0 < g.Ly; y0 += R)
-            for (int x0 = 0; x0 < g.Lx; x0 += 32) items.push_back(make_int4(i, x0, y0, g.N));
+        const TileShape t = tile_of(c, g.N);
+        for (int y0 = 0; y0 < g.Ly; y0 += t.R)
+            for (int x0 = 0; x0 < g.Lx; x0 += 32 * t.V) items.push_back(make_int4(i, x0, y0, g.N));
     }
     std::stable_sort(items.begin(), items.end(),
                      [](const int4 &a, const int4 &b) { return a.w < b.w; });
@@ -991,15 +991,16 @@ extern "C" int glbm_tile_count(int k, glbm_prec prec)
     return glbm_tile_shapes(k + 1, prec, sh);
 }
 
-extern "C" glbm_status glbm_tile_shape(int k, glbm_prec prec, int idx, int *G, int *R)
+extern "C" glbm_status glbm_tile_shape(int k, glbm_prec prec, int idx, int *G, int *R, int *V)
 {
     TileShape sh[GLBM_MAX_TILES];
     const int n = glbm_tile_count(k, prec);
-    if (!G || !R) return fail(GLBM_E_INVAL, "null argument");
+    if (!G || !R || !V) return fail(GLBM_E_INVAL, "null argument");
     if (idx < 0 || idx >= n) return fail(GLBM_E_INVAL, "no tile shape %d for k=%d", idx, k);
     glbm_tile_shapes(k + 1, prec, sh);
     *G = sh[idx].G;
     *R = sh[idx].R;
+    *V = sh[idx].V;
     return GLBM_OK;
 }
 

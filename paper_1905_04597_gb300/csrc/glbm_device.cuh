@@ -27,6 +27,11 @@ struct TabAcc<float> {
     static __device__ __forceinline__ float Co(const AxisTable &t, int n, int i) { return t.Cof[n][i]; }
 };
 
+// Product rounded on its own (never contracted into a following addition), so
+// that the one-node and the packed pair tiles round alike.
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+
 // Deviation of the level-N equilibrium from the rest weights, for one |n|:
 // Ae_n(v) (even powers >= 2) and Bo_n(v) (odd powers / u), v = u^2, so that
 // E_{+n}(u) - W_n = Ae + u Bo and E_{-n}(u) - W_n = Ae - u Bo.
@@ -37,7 +42,7 @@ __device__ __forceinline__ void eq_parts(const AxisTable &t, int n, T v, T &ae, 
     T a = A::Ce(t, n, N);
 #pragma unroll
     for (int i = N - 1; i >= 1; --i) a = fma(a, v, A::Ce(t, n, i));
-    ae = a * v;
+    ae = mul_rn(a, v);
     if (n == 0) {
         bo = T(0);  // E_0 is even in u
     } else if (A::HILO) {
@@ -115,7 +120,7 @@ __device__ __forceinline__ T eq_dev_one_run(const AxisTable &t, T u, int n)
     T a = A::Ce(t, an, N);
 #pragma unroll
     for (int i = N - 1; i >= 1; --i) a = fma(a, v, A::Ce(t, an, i));
-    const T ae = a * v;
+    const T ae = mul_rn(a, v);
     if (an == 0) return ae;
     T b = A::Co(t, an, N - 1);
     if (A::HILO) {
@@ -163,4 +168,14 @@ __device__ __forceinline__ int wrap_index(int i, int L)
 {
     i %= L;
     return i < 0 ? i + L : i;
+}
+
+// i mod L for a column or row index shifted by at most one period (-L <= i <
+// 2L): two selects instead of a division. `one_wrap` (L larger than the
+// largest shift, uniform across the launch) selects it; otherwise the
+// remainder is taken.
+__device__ __forceinline__ int wrap_shift(int i, int L, bool one_wrap)
+{
+    if (one_wrap) return i < 0 ? i + L : (i >= L ? i - L : i);
+    return wrap_index(i, L);
 }

@@ -83,9 +83,10 @@ struct Step2DArgs {
 };
 
 // Tile shape of the fused 2D step: G warps share a node's velocity rows, R node
-// rows per CTA (the candidates per level are listed in glbm_tiles.h).
+// rows per CTA, V x-adjacent nodes per thread (the candidates per level are
+// listed in glbm_tiles.h).
 struct TileShape {
-    int G, R;
+    int G, R, V;
 };
 // Candidate shapes of level N (1..GLBM_MAXN) in precision prec (0 FP64, 1 FP32
 // deviations): fills out[0..count) and returns count (0 for an invalid level).

@@ -20,7 +20,6 @@
 // moments with compensated row sums; FP64 mode stores f.
 #pragma once
 #include "glbm_device.cuh"
-#include "glbm_tiles.h"
 
 template <int N, typename T, int G, int R>
 struct Step2D {
@@ -28,13 +27,14 @@ struct Step2D {
     static constexpr int RPG = (Q1 + G - 1) / G;  // velocity rows per warp group
     static constexpr int NW = G * R;              // warps per CTA
     static constexpr int NT = 32 * NW;
+    static constexpr int NV = 4;                  // wall-flux accumulators
     static constexpr bool DEV = sizeof(T) == 4;   // FP32 deviation storage
     using A = TabAcc<T>;
 
     struct Smem {
         T part[R][G][6][32];  // (s, c) pairs of delta rho, j_x, j_y per row and group
         T rw[2][32];          // wall density (FP64) or its deviation (FP32): lo, hi
-        T dsum[NW][2][32];    // per-warp partial wall fluxes
+        T dsum[NV][2][32];    // partial wall fluxes of the NV accumulators
     };
 
     // One tile: columns x0..x0+31, rows y0..y0+R-1 of one instance whose
@@ -58,40 +58,46 @@ struct Step2D {
         // offset of velocity column ix's plane plus its periodic source column
         int cofs[Q1];
 #pragma unroll
-        for (int ix = 0; ix < Q1; ++ix) cofs[ix] = ix * plane + wrap_index(xc - (ix - N), Lx);
+        for (int ix = 0; ix < Q1; ++ix) cofs[ix] = ix * plane + wrap_shift(xc - (ix - N), Lx, Lx > N);
 
         // ---- phase 0: wall densities of this tile's columns ---------------
         const bool need_lo = walls && (y0 < N);
         const bool need_hi = walls && (y0 + R > Ly - N);
         if (need_lo || need_hi) {
-            T slo = T(0), shi = T(0);
             // pairs (|ny|, row) = (aa, k), k < aa, enumerated p = aa(aa-1)/2 + k,
-            // dealt to the warps round robin; the loop stays rolled (the wall
-            // prologue runs on few tiles and must not grow the code)
+            // summed by NV fixed accumulators (p mod NV) that the warps share
+            // round robin, so the order of the additions does not depend on the
+            // tile shape; the loops stay rolled (the wall prologue runs on few
+            // tiles and must not grow the code)
 #pragma unroll 1
-            for (int p = w; p < N * (N + 1) / 2; p += NW) {
-                int aa = 1, k = p;
-                while (k >= aa) {
-                    k -= aa;
-                    ++aa;
-                }
-                if (need_lo) {  // velocity ny = -aa leaving row k through y = -1/2
-                    const T *pl = fin + ((N - aa) * Q1 * plane + k * pitch);
+            for (int v = w; v < NV; v += NW) {
+                T slo = T(0), shi = T(0);
+#pragma unroll 1
+                for (int p = v; p < N * (N + 1) / 2; p += NV) {
+                    int aa = 1, k = p;
+                    while (k >= aa) {
+                        k -= aa;
+                        ++aa;
+                    }
+                    if (need_lo) {  // velocity ny = -aa leaving row k through y = -1/2
+                        const T *pl = fin + ((N - aa) * Q1 * plane + k * pitch);
 #pragma unroll
-                    for (int ix = 0; ix < Q1; ++ix) slo += __ldg(pl + cofs[ix]);
-                }
-                if (need_hi) {  // velocity ny = +aa leaving row Ly-1-k through y = Ly-1/2
-                    const T *ph = fin + ((N + aa) * Q1 * plane + (Ly - 1 - k) * pitch);
+                        for (int ix = 0; ix < Q1; ++ix) slo += __ldg(pl + cofs[ix]);
+                    }
+                    if (need_hi) {  // velocity ny = +aa leaving row Ly-1-k through y = Ly-1/2
+                        const T *ph = fin + ((N + aa) * Q1 * plane + (Ly - 1 - k) * pitch);
 #pragma unroll
-                    for (int ix = 0; ix < Q1; ++ix) shi += __ldg(ph + cofs[ix]);
+                        for (int ix = 0; ix < Q1; ++ix) shi += __ldg(ph + cofs[ix]);
+                    }
                 }
+                sm.dsum[v][0][lane] = slo;
+                sm.dsum[v][1][lane] = shi;
             }
-            sm.dsum[w][0][lane] = slo;
-            sm.dsum[w][1][lane] = shi;
             __syncthreads();
             if (w == 0) {
                 T s0 = T(0), s1 = T(0);
-                for (int j = 0; j < NW; ++j) {
+#pragma unroll
+                for (int j = 0; j < NV; ++j) {
                     s0 += sm.dsum[j][0][lane];
                     s1 += sm.dsum[j][1][lane];
                 }
@@ -117,7 +123,7 @@ struct Step2D {
             if (iy < Q1) {
                 const int ny = iy - N;
                 int ys = yc - ny;
-                ys = walls ? min(max(ys, 0), Ly - 1) : wrap_index(ys, Ly);
+                ys = walls ? min(max(ys, 0), Ly - 1) : wrap_shift(ys, Ly, Ly > N);
                 const T *rowp = fin + (iy * Q1 * plane + ys * pitch);
 #pragma unroll
                 for (int ix = 0; ix < Q1; ++ix) f[k][ix] = __ldg(rowp + cofs[ix]);
@@ -139,10 +145,10 @@ struct Step2D {
                         if (DEV) {
                             const T dw = lo ? (T)ip.dw_lo_f[ix] : (T)ip.dw_hi_f[ix];
                             // W^y (drho_w W^x + rho_w (E^x(u_w) - W^x))
-                            f[k][ix] = wy * fma(rw, A::W(tab, ix), (T(1) + rw) * dw);
+                            f[k][ix] = mul_rn(wy, fma(rw, A::W(tab, ix), (T(1) + rw) * dw));
                         } else {
                             const T ew = lo ? (T)ip.ew_lo[ix] : (T)ip.ew_hi[ix];
-                            f[k][ix] = rw * ew * wy;
+                            f[k][ix] = mul_rn(rw * ew, wy);
                         }
                     }
                 }
@@ -154,7 +160,7 @@ struct Step2D {
                 for (int n = 1; n <= N; ++n) jx = fma(T(n), f[k][N + n] - f[k][N - n], jx);
                 acc2(s_r, c_r, rs);
                 acc2(s_x, c_x, jx);
-                if (ny != 0) acc2(s_y, c_y, T(ny) * rs);
+                if (ny != 0) acc2(s_y, c_y, mul_rn(T(ny), rs));
             }
         }
         sm.part[r][g][0][lane] = s_r;
@@ -218,7 +224,7 @@ struct Step2D {
                 else
                     dy = eq_dev_one_run<N, T>(tab, uy, ny);
                 const T rey = rho * (wy + dy);  // rho e^y
-                const T gr = gto * wy;
+                const T gr = mul_rn(gto, wy);
                 // FP32: delta f^eq = d^x rho e^y + W^x (drho W^y + rho d^y)
                 const T B = DEV ? fma(drho, wy, rho * dy) : T(0);
                 T *const op = obase + iy * Q1 * plane;
@@ -276,27 +282,4 @@ __global__ void __launch_bounds__(32 * G * R)
     S::run(a.tab, a.ip[inst], a.Lx, a.Ly, a.pitch, (int)a.plane, a.bc, fin, fout, blockIdx.x * 32,
            blockIdx.y * R, sm, a.status, seed);
     if (S::DEV) advance_launch_counter(a.step_ctr, a.done_ctr);
-}
-
-// Launch of tile shape number I of level N (shapes from glbm_tiles.h).
-template <int N, typename T, int I = 0>
-cudaError_t launch_step2d_shape(int shape, const Step2DArgs &a, int n_inst, cudaStream_t s)
-{
-    if constexpr (I < Tiles<N, T>::count) {
-        if (shape == I) {
-            constexpr int G = Tiles<N, T>::shape[I].G, R = Tiles<N, T>::shape[I].R;
-            const dim3 grid((a.Lx + 31) / 32, (a.Ly + R - 1) / R, n_inst);
-            k_step2d<N, T, G, R><<<grid, 32 * G * R, 0, s>>>(a);
-            return cudaGetLastError();
-        }
-        return launch_step2d_shape<N, T, I + 1>(shape, a, n_inst, s);
-    } else {
-        return cudaErrorInvalidValue;
-    }
-}
-
-template <int N, typename T>
-cudaError_t glbm_step2d_level(int shape, const Step2DArgs &a, int n_inst, cudaStream_t s)
-{
-    return launch_step2d_shape<N, T>(shape, a, n_inst, s);
 }

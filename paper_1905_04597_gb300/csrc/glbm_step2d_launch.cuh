@@ -1,0 +1,50 @@
+// Launch of the uniform fused 2D step by tile shape (glbm_tiles.h): one-node
+// tiles for both precisions, packed pair tiles for FP32 deviations.
+#pragma once
+#include "glbm_step2d_pair.cuh"
+#include "glbm_tiles.h"
+
+template <int N, int G, int R>
+__global__ void __launch_bounds__(32 * G * R)
+    k_step2d_pair(const __grid_constant__ Step2DArgs a)
+{
+    using S = Step2DPair<N, G, R>;
+    __shared__ __align__(16) typename S::Smem sm;
+    const int inst = blockIdx.z;
+    const float *fin = static_cast<const float *>(a.fin) + (long long)inst * a.inst_stride;
+    float *fout = static_cast<float *>(a.fout) + (long long)inst * a.inst_stride;
+    // launch counter (read before any CTA of this launch can advance it)
+    const unsigned seed = hash32(__ldcg(a.step_ctr) * 0x632BE5ABu + inst);
+    S::run(a.tab, a.ip[inst], a.Lx, a.Ly, a.pitch, (int)a.plane, a.bc, fin, fout,
+           blockIdx.x * S::TW, blockIdx.y * R, sm, a.status, seed);
+    advance_launch_counter(a.step_ctr, a.done_ctr);
+}
+
+// Launch of tile shape number I of level N.
+template <int N, typename T, int I = 0>
+cudaError_t launch_step2d_shape(int shape, const Step2DArgs &a, int n_inst, cudaStream_t s)
+{
+    if constexpr (I < Tiles<N, T>::count) {
+        if (shape == I) {
+            constexpr TileShape t = Tiles<N, T>::shape[I];
+            constexpr int G = t.G, R = t.R, TW = 32 * t.V;
+            const dim3 grid((a.Lx + TW - 1) / TW, (a.Ly + R - 1) / R, n_inst);
+            if constexpr (t.V == 2) {
+                static_assert(sizeof(T) == 4, "pair tiles store FP32 deviations");
+                k_step2d_pair<N, G, R><<<grid, 32 * G * R, 0, s>>>(a);
+            } else {
+                k_step2d<N, T, G, R><<<grid, 32 * G * R, 0, s>>>(a);
+            }
+            return cudaGetLastError();
+        }
+        return launch_step2d_shape<N, T, I + 1>(shape, a, n_inst, s);
+    } else {
+        return cudaErrorInvalidValue;
+    }
+}
+
+template <int N, typename T>
+cudaError_t glbm_step2d_level(int shape, const Step2DArgs &a, int n_inst, cudaStream_t s)
+{
+    return launch_step2d_shape<N, T>(shape, a, n_inst, s);
+}

@@ -1,0 +1,357 @@
+// FP32-deviation form of the fused pull-stream + BGK collide tile (Sec. 2,
+// Eq. maineq01, product equilibrium of Sec. 4, diffuse walls, linearised
+// force of Sec. 5.4) working on PAIRS of x-adjacent nodes with the packed
+// two-lane FP32 instructions of sm_100 and later (add/sub/mul/fma .f32x2).
+//
+// A thread owns nodes (x, y) and (x + 1, y), x even, and keeps each
+// population of the two nodes in one 64-bit register pair (low word: node x).
+// Every lane of a packed instruction is rounded exactly like the scalar
+// instruction of the one-node tile (glbm_step2d.cuh), and the operations are
+// done in the same order, so a pair tile and a one-node tile of the same G
+// give bit-identical results. What the pairing saves is instructions: one
+// packed op updates two populations, a pull whose velocity has even n_x is one
+// 8-byte load, and the store of both nodes is one 8-byte store.
+//
+// A CTA covers 64 columns x R rows with G warps per node row (32 G R
+// threads); phases as in the one-node tile:
+//   phase 0 (CTAs touching a wall): wall densities of the tile's columns;
+//   phase 1: pull every population of both nodes (periodic wrap in x; sources
+//            inside a wall take the wall's re-emitted value), partial moments
+//            per velocity row with compensated sums;
+//   phase 2: moments, equilibrium, relaxation plus force, dithered store.
+#pragma once
+#include "glbm_step2d.cuh"
+
+typedef unsigned long long f32x2;  // two FP32 lanes, low word = node x
+
+__device__ __forceinline__ f32x2 pk2(float a, float b)
+{
+    f32x2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ float lo2(f32x2 v)
+{
+    float a;
+    asm("{ .reg .f32 t; mov.b64 {%0, t}, %1; }" : "=f"(a) : "l"(v));
+    return a;
+}
+__device__ __forceinline__ float hi2(f32x2 v)
+{
+    float b;
+    asm("{ .reg .f32 t; mov.b64 {t, %0}, %1; }" : "=f"(b) : "l"(v));
+    return b;
+}
+__device__ __forceinline__ f32x2 add2(f32x2 a, f32x2 b)
+{
+    f32x2 d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f32x2 sub2(f32x2 a, f32x2 b)
+{
+    f32x2 d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f32x2 mul2(f32x2 a, f32x2 b)
+{
+    f32x2 d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f32x2 fma2(f32x2 a, f32x2 b, f32x2 c)
+{
+    f32x2 d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+
+// Knuth's two-sum on both lanes (the packed form of acc2).
+__device__ __forceinline__ void acc2x2(f32x2 &s, f32x2 &c, f32x2 x)
+{
+    const f32x2 t = add2(s, x);
+    const f32x2 bp = sub2(t, s);
+    const f32x2 err = add2(sub2(s, sub2(t, bp)), sub2(x, bp));
+    s = t;
+    c = add2(c, err);
+}
+
+template <int N, int G, int R>
+struct Step2DPair {
+    static constexpr int Q1 = 2 * N + 1;
+    static constexpr int RPG = (Q1 + G - 1) / G;  // velocity rows per warp group
+    static constexpr int NW = G * R;              // warps per CTA
+    static constexpr int TW = 64;                 // tile width (columns)
+    static constexpr int NWIN = 2 * N + 2;        // source columns of a node pair
+    static constexpr int NV = Step2D<N, float, G, R>::NV;  // wall-flux accumulators
+    using A = TabAcc<float>;
+
+    struct Smem {
+        float part[R][G][6][TW];  // (s, c) of delta rho, j_x, j_y per row, group, column
+        float rw[2][TW];          // wall density deviations: lo, hi
+        float dsum[NV][2][TW];    // partial wall fluxes of the NV accumulators
+    };
+
+    // One tile: columns x0..x0+63 (x0 a multiple of 64), rows y0..y0+R-1 of one
+    // instance whose populations start at fin / fout (8-byte aligned planes).
+    __device__ static void run(const AxisTable &tab, const InstParams &ip, int Lx, int Ly,
+                               int pitch, int plane, int bc, const float *__restrict__ fin,
+                               float *__restrict__ fout, int x0, int y0, Smem &sm,
+                               unsigned *status, unsigned seed)
+    {
+        const int lane = threadIdx.x & 31;
+        const int w = threadIdx.x >> 5;
+        const int g = w % G;
+        const int r = w / G;
+        const bool walls = bc == GLBM_BC_WALLS;
+        const int x = x0 + 2 * lane, y = y0 + r;
+        const bool yin = y < Ly;
+        const bool act0 = yin && x < Lx, act1 = yin && x + 1 < Lx;
+        const int xc = x < Lx ? x : Lx - 1;
+        const int yc = yin ? y : Ly - 1;
+        // the tile pulls from columns x0-N .. x0+63+N without wrapping
+        const bool inner = x0 >= N && x0 + TW + N <= Lx;
+
+        // source columns of the pair: node x pulls velocity n_x from column
+        // win[N - n_x], node x + 1 from win[N - n_x + 1]
+        int win[NWIN];
+        const bool one_wrap = Lx > N + 1;
+#pragma unroll
+        for (int j = 0; j < NWIN; ++j) win[j] = wrap_shift(xc - N + j, Lx, one_wrap);
+
+        // ---- phase 0: wall densities of this tile's columns ---------------
+        const bool need_lo = walls && (y0 < N);
+        const bool need_hi = walls && (y0 + R > Ly - N);
+        if (need_lo || need_hi) {
+            // the wall-flux sums in the order of the one-node tile: NV fixed
+            // accumulators (pair p mod NV), whatever the tile shape
+#pragma unroll 1
+            for (int v = w; v < NV; v += NW) {
+                float slo0 = 0.f, slo1 = 0.f, shi0 = 0.f, shi1 = 0.f;
+#pragma unroll 1
+                for (int p = v; p < N * (N + 1) / 2; p += NV) {
+                    int aa = 1, k = p;
+                    while (k >= aa) {
+                        k -= aa;
+                        ++aa;
+                    }
+                    if (need_lo) {  // velocity ny = -aa leaving row k through y = -1/2
+                        const float *pl = fin + ((N - aa) * Q1 * plane + k * pitch);
+#pragma unroll
+                        for (int ix = 0; ix < Q1; ++ix) {
+                            slo0 += __ldg(pl + (ix * plane + win[2 * N - ix]));
+                            slo1 += __ldg(pl + (ix * plane + win[2 * N - ix + 1]));
+                        }
+                    }
+                    if (need_hi) {  // velocity ny = +aa leaving row Ly-1-k through y = Ly-1/2
+                        const float *ph = fin + ((N + aa) * Q1 * plane + (Ly - 1 - k) * pitch);
+#pragma unroll
+                        for (int ix = 0; ix < Q1; ++ix) {
+                            shi0 += __ldg(ph + (ix * plane + win[2 * N - ix]));
+                            shi1 += __ldg(ph + (ix * plane + win[2 * N - ix + 1]));
+                        }
+                    }
+                }
+                sm.dsum[v][0][2 * lane] = slo0;
+                sm.dsum[v][0][2 * lane + 1] = slo1;
+                sm.dsum[v][1][2 * lane] = shi0;
+                sm.dsum[v][1][2 * lane + 1] = shi1;
+            }
+            __syncthreads();
+            if (w == 0) {
+                const float inv_den = ip.inv_den_f;
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int col = 2 * lane + h;
+                    float s0 = 0.f, s1 = 0.f;
+#pragma unroll
+                    for (int j = 0; j < NV; ++j) {
+                        s0 += sm.dsum[j][0][col];
+                        s1 += sm.dsum[j][1][col];
+                    }
+                    // rho_w - 1 = (D - den) / den: D - den is the absorbed deviation
+                    sm.rw[0][col] = s0 * inv_den;
+                    sm.rw[1][col] = s1 * inv_den;
+                }
+            }
+            __syncthreads();
+        }
+
+        // ---- phase 1: pull and partial moments -----------------------------
+        // rows iy = g + k G of this warp group; f[k][ix] holds both nodes
+        f32x2 f[RPG][Q1];
+        f32x2 s_r = 0ull, c_r = 0ull, s_x = 0ull, c_x = 0ull, s_y = 0ull, c_y = 0ull;
+#pragma unroll
+        for (int k = 0; k < RPG; ++k) {
+            const int iy = g + k * G;
+            if (iy < Q1) {
+                const int ny = iy - N;
+                int ys = yc - ny;
+                ys = walls ? min(max(ys, 0), Ly - 1) : wrap_shift(ys, Ly, Ly > N);
+                const float *rowp = fin + (iy * Q1 * plane + ys * pitch);
+                if (inner) {
+#pragma unroll
+                    for (int ix = 0; ix < Q1; ++ix) {
+                        const int nx = ix - N;
+                        const float *p = rowp + (ix * plane + (x - nx));
+                        if ((nx & 1) == 0)  // (x - nx) even: one aligned 8-byte load
+                            f[k][ix] = __ldg(reinterpret_cast<const f32x2 *>(p));
+                        else
+                            f[k][ix] = pk2(__ldg(p), __ldg(p + 1));
+                    }
+                } else {
+#pragma unroll
+                    for (int ix = 0; ix < Q1; ++ix) {
+                        const float *p = rowp + ix * plane;
+                        f[k][ix] = pk2(__ldg(p + win[2 * N - ix]), __ldg(p + win[2 * N - ix + 1]));
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < RPG; ++k) {
+            const int iy = g + k * G;
+            if (iy < Q1) {
+                const int ny = iy - N;
+                const int ys = yc - ny;
+                if (walls && (ys < 0 || ys >= Ly)) {  // uniform across the warp
+                    const bool lo = ys < 0;
+                    const float wy = A::W(tab, iy);
+                    const float rw0 = sm.rw[lo ? 0 : 1][2 * lane];
+                    const float rw1 = sm.rw[lo ? 0 : 1][2 * lane + 1];
+#pragma unroll
+                    for (int ix = 0; ix < Q1; ++ix) {
+                        const float dw = lo ? ip.dw_lo_f[ix] : ip.dw_hi_f[ix];
+                        const float wx = A::W(tab, ix);
+                        // W^y (drho_w W^x + rho_w (E^x(u_w) - W^x))
+                        f[k][ix] = pk2(wy * fmaf(rw0, wx, (1.f + rw0) * dw),
+                                       wy * fmaf(rw1, wx, (1.f + rw1) * dw));
+                    }
+                }
+                f32x2 rs = 0ull;
+#pragma unroll
+                for (int ix = 0; ix < Q1; ++ix) rs = add2(rs, f[k][ix]);
+                f32x2 jx = 0ull;
+#pragma unroll
+                for (int n = 1; n <= N; ++n)
+                    jx = fma2(pk2((float)n, (float)n), sub2(f[k][N + n], f[k][N - n]), jx);
+                acc2x2(s_r, c_r, rs);
+                acc2x2(s_x, c_x, jx);
+                if (ny != 0)  // products rounded per lane, as in the one-node tile
+                    acc2x2(s_y, c_y, pk2(mul_rn((float)ny, lo2(rs)), mul_rn((float)ny, hi2(rs))));
+            }
+        }
+        {
+            f32x2 *pp = reinterpret_cast<f32x2 *>(&sm.part[r][g][0][2 * lane]);
+            constexpr int st = TW / 2;  // f32x2 stride between the six rows
+            pp[0 * st] = s_r;
+            pp[1 * st] = c_r;
+            pp[2 * st] = s_x;
+            pp[3 * st] = c_x;
+            pp[4 * st] = s_y;
+            pp[5 * st] = c_y;
+        }
+        __syncthreads();
+
+        // ---- phase 2: moments, equilibrium, relaxation, store --------------
+        f32x2 S_r = 0ull, C_r = 0ull, S_x = 0ull, C_x = 0ull, S_y = 0ull, C_y = 0ull;
+#pragma unroll
+        for (int gi = 0; gi < G; ++gi) {
+            const f32x2 *pp = reinterpret_cast<const f32x2 *>(&sm.part[r][gi][0][2 * lane]);
+            constexpr int st = TW / 2;
+            acc2x2(S_r, C_r, pp[0 * st]);
+            acc2x2(S_x, C_x, pp[2 * st]);
+            acc2x2(S_y, C_y, pp[4 * st]);
+            C_r = add2(C_r, pp[1 * st]);
+            C_x = add2(C_x, pp[3 * st]);
+            C_y = add2(C_y, pp[5 * st]);
+        }
+        const f32x2 drho = add2(S_r, C_r);  // delta rho of both nodes
+        const f32x2 rho = add2(pk2(1.f, 1.f), drho);
+        const f32x2 inv_rho = pk2(1.f / lo2(rho), 1.f / hi2(rho));
+        const f32x2 ux = mul2(add2(S_x, C_x), inv_rho);
+        const f32x2 uy = mul2(add2(S_y, C_y), inv_rho);
+        {
+            const float umax = (float)(0.816496580927726 * N);  // sqrt(2/3) N (Sec. 3)
+            const bool bad0 = act0 && (!(lo2(rho) > 0.f) || !(fabsf(lo2(ux)) <= umax) ||
+                                       !(fabsf(lo2(uy)) <= umax));
+            const bool bad1 = act1 && (!(hi2(rho) > 0.f) || !(fabsf(hi2(ux)) <= umax) ||
+                                       !(fabsf(hi2(uy)) <= umax));
+            if (bad0 || bad1) atomicOr(status, 1u);
+        }
+
+        // E^x - W for both nodes
+        f32x2 dx[Q1];
+        {
+            float d0[Q1], d1[Q1];
+            eq_dev_all<N, float>(tab, lo2(ux), d0);
+            eq_dev_all<N, float>(tab, hi2(ux), d1);
+#pragma unroll
+            for (int ix = 0; ix < Q1; ++ix) dx[ix] = pk2(d0[ix], d1[ix]);
+        }
+        float dy0all[G == 1 ? Q1 : 1], dy1all[G == 1 ? Q1 : 1];
+        if constexpr (G == 1) {
+            eq_dev_all<N, float>(tab, lo2(uy), dy0all);
+            eq_dev_all<N, float>(tab, hi2(uy), dy1all);
+        }
+        const f32x2 om = pk2(ip.omega_f, ip.omega_f);
+        const float gto = ip.g_theta_om_f;  // g / (theta omega)
+        float *const obase = fout + (y * pitch + x);
+        // random words of the two nodes and this launch (dithered stores)
+        const unsigned h0 = hash32((unsigned)(y * Lx + x) ^ seed);
+        const unsigned h1 = hash32((unsigned)(y * Lx + x + 1) ^ seed);
+        const f32x2 two55 = pk2(0x1p-55f, 0x1p-55f);
+
+#pragma unroll
+        for (int k = 0; k < RPG; ++k) {
+            const int iy = g + k * G;
+            if (iy < Q1) {
+                const int ny = iy - N;
+                const float wy = A::W(tab, iy);
+                float dy0, dy1;
+                if constexpr (G == 1) {
+                    dy0 = dy0all[k];
+                    dy1 = dy1all[k];
+                } else {
+                    dy0 = eq_dev_one_run<N, float>(tab, lo2(uy), ny);
+                    dy1 = eq_dev_one_run<N, float>(tab, hi2(uy), ny);
+                }
+                const f32x2 dy = pk2(dy0, dy1);
+                const f32x2 wy2 = pk2(wy, wy);
+                const f32x2 rey = mul2(rho, add2(wy2, dy));  // rho e^y
+                const float grs = mul_rn(gto, wy);
+                const f32x2 gr = pk2(grs, grs);
+                // delta f^eq = d^x rho e^y + W^x (drho W^y + rho d^y) + force
+                const f32x2 B = fma2(drho, wy2, mul2(rho, dy));
+                float *const op = obase + iy * Q1 * plane;
+                const unsigned q0 = (unsigned)(iy * Q1);
+#pragma unroll
+                for (int ix = 0; ix < Q1; ++ix) {
+                    const int nx = ix - N;
+                    const f32x2 f0 = f[k][ix];
+                    const f32x2 Bn = nx != 0 ? fma2(pk2((float)nx, (float)nx), gr, B) : B;
+                    const float wx = A::W(tab, ix);
+                    const f32x2 eq = fma2(dx[ix], rey, mul2(pk2(wx, wx), Bn));
+                    // increment plus dither, then one rounding of the store
+                    const unsigned q = q0 + ix;
+                    const unsigned a = 0x9E3779B9u * (2u * q + 1u), b = 0x7F4A7C15u * q;
+                    const unsigned r0 = h0 * a + b, r1 = h1 * a + b;
+                    const float p0 = __int_as_float(__float_as_int(lo2(f0)) & 0x7F800000);
+                    const float p1 = __int_as_float(__float_as_int(hi2(f0)) & 0x7F800000);
+                    const f32x2 dith =
+                        mul2(mul2(pk2((float)(int)r0, (float)(int)r1), two55), pk2(p0, p1));
+                    const f32x2 inc = fma2(om, sub2(eq, f0), dith);
+                    const f32x2 v = add2(f0, inc);
+                    float *const o = op + ix * plane;
+                    if (act0 && act1) {
+                        *reinterpret_cast<f32x2 *>(o) = v;
+                    } else {
+                        if (act0) o[0] = lo2(v);
+                        if (act1) o[1] = hi2(v);
+                    }
+                }
+            }
+        }
+    }
+};

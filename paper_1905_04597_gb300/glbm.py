@@ -79,7 +79,7 @@ def lib():
         "glbm_conservation_noalloc": ([vp, i, i64, vp, vp], i),
         "glbm_adjoint_flowrate": ([vp, i64, i64, dp, dp, dp], i),
         "glbm_tile_count": ([i, i], i),
-        "glbm_tile_shape": ([i, i, i, ctypes.POINTER(i), ctypes.POINTER(i)], i),
+        "glbm_tile_shape": ([i, i, i, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i)], i),
         "glbm_get_tiles": ([vp, ctypes.POINTER(i)], i),
         "glbm_set_tiles": ([vp, ctypes.POINTER(i)], i),
         "glbm_autotune": ([vp, i, dp], i),
@@ -103,17 +103,18 @@ def check(status):
 
 
 LEVELS = 8      # levels k = 0..7
-MAX_TILES = 6   # candidate tile shapes per level and precision
+MAX_TILES = 8   # candidate tile shapes per level and precision
 
 
 def tile_shapes(k: int, prec: int) -> list:
-    """Candidate (G, R) tile shapes of level k in precision prec; entry 0 is the default."""
+    """Candidate (G, R, V) tile shapes of level k in precision prec (G warps per
+    node row, R node rows per CTA, V nodes per thread); entry 0 is the default."""
     L = lib()
     out = []
     for idx in range(L.glbm_tile_count(k, prec)):
-        G, R = ctypes.c_int(), ctypes.c_int()
-        check(L.glbm_tile_shape(k, prec, idx, ctypes.byref(G), ctypes.byref(R)))
-        out.append((G.value, R.value))
+        G, R, V = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        check(L.glbm_tile_shape(k, prec, idx, ctypes.byref(G), ctypes.byref(R), ctypes.byref(V)))
+        out.append((G.value, R.value, V.value))
     return out
 
 

@@ -74,15 +74,16 @@ def test_invalid_config_is_rejected_before_any_device_call():
 
 def test_tile_shape_candidates():
     """Every level has 1..MAX_TILES candidate shapes in each precision, each
-    with 1 <= G <= 2k+3 warp groups and at most 512 threads per CTA; invalid
-    levels have none."""
+    with 1 <= G <= 2k+3 warp groups, at most 512 threads per CTA and one or
+    two nodes per thread (pairs in FP32 only); invalid levels have none."""
     for prec in (glbm.FP64, glbm.FP32_DEV):
         for k in range(glbm.LEVELS):
             shapes = glbm.tile_shapes(k, prec)
             assert 1 <= len(shapes) <= glbm.MAX_TILES
             assert len(set(shapes)) == len(shapes)
-            for G, R in shapes:
+            for G, R, V in shapes:
                 assert 1 <= G <= 2 * k + 3 and R >= 1 and 32 * G * R <= 512
+                assert V == 1 or (V == 2 and prec == glbm.FP32_DEV)
         assert glbm.tile_shapes(8, prec) == [] and glbm.tile_shapes(-1, prec) == []
     with pytest.raises(glbm.GlbmError):
-        glbm.check(glbm.lib().glbm_tile_shape(0, glbm.FP64, 99, None, None))
+        glbm.check(glbm.lib().glbm_tile_shape(0, glbm.FP64, 99, None, None, None))

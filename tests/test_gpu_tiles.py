@@ -36,7 +36,7 @@ def test_every_tile_shape_one_step(k, prec):
     want, _ = o.run(f0, 1)
     shapes = glbm.tile_shapes(k, prec)
     assert shapes
-    for idx, (G, R) in enumerate(shapes):
+    for idx, (G, R, V) in enumerate(shapes):
         lat = glbm.Lattice(dict(dims=2, nx=nx, ny=ny, k=k, tau=tau, prec=prec, u_wall_lo=uw_lo,
                                 u_wall_hi=uw_hi, g=g))
         tiles = [-1] * glbm.LEVELS
@@ -48,7 +48,7 @@ def test_every_tile_shape_one_step(k, prec):
         lat.sync()
         got = lat.get_populations(0)
         err = np.abs(got - want).max() / np.abs(want).max()
-        assert err < POP_TOL[prec], (idx, G, R, err)
+        assert err < POP_TOL[prec], (idx, G, R, V, err)
         lat.close()
 
 
@@ -119,3 +119,33 @@ def test_set_tiles_rejects_out_of_range_index():
         lat.set_tiles(bad)
     assert lat.tiles() == before
     lat.close()
+
+
+@pytest.mark.parametrize("k", range(8))
+def test_pair_tiles_bitwise_equal_one_node_tiles_of_same_split(k):
+    """A packed pair tile rounds every lane like the one-node tile: with the same
+    warp-group split G they give bit-identical populations (walls, force, a
+    ragged width that is not a multiple of the 64-column pair tile)."""
+    shapes = glbm.tile_shapes(k, glbm.FP32_DEV)
+    pairs = [(i, j) for i, a in enumerate(shapes) for j, b in enumerate(shapes)
+             if a[2] == 1 and b[2] == 2 and a[0] == b[0]]
+    if not pairs:
+        pytest.skip("no pair tile with a one-node tile of the same G at this level")
+    N = k + 1
+    nx, ny = 100, 3 * N + 4
+    cfg = dict(dims=2, nx=nx, ny=ny, k=k, kn=0.2, prec=glbm.FP32_DEV, u_wall_lo=-0.03,
+               u_wall_hi=0.05, g=2e-5)
+    fields = inputs.random_macro(40 + k, nx, ny)
+    for i, j in pairs[:2]:
+        out = []
+        for idx in (i, j):
+            lat = glbm.Lattice(cfg)
+            tiles = [-1] * glbm.LEVELS
+            tiles[k] = idx
+            lat.set_tiles(tiles)
+            lat.set_equilibrium(0, *fields)
+            lat.step(9)
+            lat.sync()
+            out.append(lat.get_populations(0))
+            lat.close()
+        np.testing.assert_array_equal(out[0], out[1])
