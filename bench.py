@@ -149,7 +149,7 @@ def run_ours(args):
 
     if args.workload == "batched":
         res = measure_batched(steps32=args.steps, steps64=max(args.steps // 8, 8),
-                              warmup=args.warmup)
+                              warmup=args.warmup, autotune=args.tiles == "autotune")
         if rank == 0:
             b = res["fp32_batched"]
             print(json.dumps({"metric": METRIC, "value": b["pop_updates_per_s"], "unit": UNIT,
@@ -169,8 +169,21 @@ def run_ours(args):
     pops_per_step = Q * nodes * n_inst
     stream = torch.cuda.current_stream()
 
+    tiles_used = {}
+
+    def kernel_name(prec, lat):
+        k = N - 1
+        G, R, V = glbm.tile_shapes(k, prec)[lat.tiles()[k]]
+        if V == 2:
+            return f"k_step2d_pair<{N},{G},{R}>"
+        return f"k_step2d<{N},{'float' if prec == glbm.FP32_DEV else 'double'},{G},{R}>"
+
     def timed(prec, steps, warmup):
         lat = glbm.Lattice([dict(c, prec=prec) for c in cfgs])
+        if dims == 2:
+            if args.tiles == "autotune":
+                lat.autotune(reps=10)
+            tiles_used[prec] = kernel_name(prec, lat)
         lat.step(warmup)
         lat.sync()
         l0 = lat.kernel_launches
@@ -213,6 +226,8 @@ def run_ours(args):
     if dims == 2:
         lb_per_call = 100
         lat = glbm.Lattice([dict(c, prec=glbm.FP32_DEV) for c in cfgs])
+        if args.tiles == "autotune":
+            lat.autotune(reps=10)
         ny, nx = cfgs[0]["ny"], cfgs[0]["nx"]
         pin = lambda a: torch.from_numpy(a).pin_memory()  # noqa: E731
         rho = pin(np.ones((ny, nx)))
@@ -242,7 +257,8 @@ def run_ours(args):
                "lb_steps_per_step": lb_per_call,
                "call": "glbm_set_equilibrium(host) x3 + glbm_step(100) + glbm_moments(host) x3"}
 
-    batched = measure_batched() if (args.workload == "couette" and not args.no_batched) else None
+    batched = (measure_batched(autotune=args.tiles == "autotune")
+               if (args.workload == "couette" and not args.no_batched) else None)
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -255,15 +271,17 @@ def run_ours(args):
         "config": {"workload": label, "lattice": f"D{dims}Q{Q}", "k": N - 1,
                    "nodes": nodes, "instances": n_inst, "storage": "fp32 deviations",
                    "l2": f"populations {2 * bytes32 / 2 / 1e6:.0f} MB per buffer set x2 > 129 MB L2; no flush",
-                   "parallelism": f"instances batched per launch; {world} rank(s), independent copies"},
+                   "parallelism": f"instances batched per launch; {world} rank(s), independent copies",
+                   "tiles": args.tiles},
         "mlups": nodes * n_inst * steps * world / (ms32 / 1e3) / 1e6,
         "hbm_gbs_algorithmic": gbs32,
         "fp64": {"value": value64, "unit": UNIT, "ms_per_step": ms64 / steps64, "steps": steps64,
+                 "kernel": tiles_used.get(glbm.FP64, "k_step1d"),
                  "hbm_gbs_algorithmic": gbs64, "frac_of_hbm": gbs64 / peak,
                  "clocks": clocks64},
         "roofline": {"bound": "hbm", "achieved": gbs32, "peak": peak, "unit": "GB/s",
                      "frac": gbs32 / peak, "traffic": None,
-                     "kernel": "k_step2d<4,float,1,4>",
+                     "kernel": tiles_used.get(glbm.FP32_DEV, "k_step1d"),
                      "bytes_per_launch": bytes32, "peak_source": peak_kind},
         "gpu_launches": launches,
         "clocks": clocks,
@@ -280,7 +298,7 @@ def run_ours(args):
 STEPS_PER_SOLVE = 2000  # a channel solve of the batched workload
 
 
-def measure_batched(steps32=256, steps64=64, warmup=8):
+def measure_batched(steps32=256, steps64=64, warmup=8, autotune=True):
     """Solves/s of the 256-instance heterogeneous batch in FP32 (one persistent
     launch per step) against the same instances in FP64, one context (and one
     launch per step) per instance."""
@@ -291,6 +309,9 @@ def measure_batched(steps32=256, steps64=64, warmup=8):
     stream = torch.cuda.current_stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     lat = glbm.Lattice([dict(dims=2, prec=glbm.FP32_DEV, **r) for r in recipe], hetero=True)
+    if autotune:
+        lat.autotune(reps=5)
+    tiles = lat.tiles()
     lat.step(warmup)
     lat.sync()
     l0 = lat.kernel_launches
@@ -318,7 +339,7 @@ def measure_batched(steps32=256, steps64=64, warmup=8):
     sps64 = steps64 / (ms64 / 1e3)
     n = len(recipe)
     return {"instances": n, "pop_updates_per_step": pops,
-            "fp32_batched": {"solves_per_s": n * sps32 / STEPS_PER_SOLVE,
+            "fp32_batched": {"solves_per_s": n * sps32 / STEPS_PER_SOLVE, "tiles": tiles,
                              "pop_updates_per_s": pops * sps32, "ms_per_step": ms32 / steps32,
                              "launches_per_step": launches32 / steps32},
             "fp64_one_instance_per_launch": {"solves_per_s": n * sps64 / STEPS_PER_SOLVE,
@@ -422,6 +443,8 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--tiles", default="autotune", choices=["autotune", "default"],
+                    help="time every tile shape on the context first, or keep the defaults")
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")

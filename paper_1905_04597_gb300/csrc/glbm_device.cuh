@@ -109,36 +109,6 @@ __device__ __forceinline__ void acc2(double &s, double &c, double x)
     s += x;
 }
 
-// E_n(u) - W_n for a single run-time n, either precision (table read with a
-// run-time row index).
-template <int N, typename T>
-__device__ __forceinline__ T eq_dev_one_run(const AxisTable &t, T u, int n)
-{
-    using A = TabAcc<T>;
-    const int an = n < 0 ? -n : n;
-    const T v = u * u;
-    T a = A::Ce(t, an, N);
-#pragma unroll
-    for (int i = N - 1; i >= 1; --i) a = fma(a, v, A::Ce(t, an, i));
-    const T ae = mul_rn(a, v);
-    if (an == 0) return ae;
-    T b = A::Co(t, an, N - 1);
-    if (A::HILO) {
-        if (N >= 2) {
-#pragma unroll
-            for (int i = N - 2; i >= 1; --i) b = fma(b, v, A::Co(t, an, i));
-            b = fma(b, v, A::C1lo(t, an));
-        } else {
-            b = A::C1lo(t, an);
-        }
-        b = b + A::Co(t, an, 0);
-    } else {
-#pragma unroll
-        for (int i = N - 2; i >= 0; --i) b = fma(b, v, A::Co(t, an, i));
-    }
-    return n > 0 ? fma(u, b, ae) : fma(-u, b, ae);
-}
-
 // 32-bit integer hash (xorshift-multiply), used to draw the dither of the
 // FP32 stores from (launch, instance, node).
 __device__ __forceinline__ unsigned hash32(unsigned x)

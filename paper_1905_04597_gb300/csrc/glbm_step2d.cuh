@@ -35,6 +35,9 @@ struct Step2D {
         T part[R][G][6][32];  // (s, c) pairs of delta rho, j_x, j_y per row and group
         T rw[2][32];          // wall density (FP64) or its deviation (FP32): lo, hi
         T dsum[NV][2][32];    // partial wall fluxes of the NV accumulators
+        // E^x - W and E^y - W of the tile's nodes, shared by the warp groups
+        T eqx[G > 1 ? R : 1][G > 1 ? Q1 : 1][32];
+        T eqy[G > 1 ? R : 1][G > 1 ? Q1 : 1][32];
     };
 
     // One tile: columns x0..x0+31, rows y0..y0+R-1 of one instance whose
@@ -196,9 +199,30 @@ struct Step2D {
         }
 
         T dx[Q1];
-        eq_dev_all<N, T>(tab, ux, dx);
         T dyall[G == 1 ? Q1 : 1];  // one warp group: E^y - W for every row at once
-        if constexpr (G == 1) eq_dev_all<N, T>(tab, uy, dyall);
+        if constexpr (G == 1) {
+            eq_dev_all<N, T>(tab, ux, dx);
+            eq_dev_all<N, T>(tab, uy, dyall);
+        } else {
+            // the G warp groups of a node row share the polynomial work: group g
+            // evaluates E^x - W and E^y - W for |n| = g, g + G, ..., and the
+            // values meet in shared memory
+            const T vx = ux * ux, vy = uy * uy;
+#pragma unroll
+            for (int n = 0; n <= N; ++n) {
+                if (n % G != g) continue;
+                T ae, bo;
+                eq_parts<N, T>(tab, n, vx, ae, bo);
+                sm.eqx[r][N + n][lane] = n == 0 ? ae : fma(ux, bo, ae);
+                if (n != 0) sm.eqx[r][N - n][lane] = fma(-ux, bo, ae);
+                eq_parts<N, T>(tab, n, vy, ae, bo);
+                sm.eqy[r][N + n][lane] = n == 0 ? ae : fma(uy, bo, ae);
+                if (n != 0) sm.eqy[r][N - n][lane] = fma(-uy, bo, ae);
+            }
+            __syncthreads();
+#pragma unroll
+            for (int ix = 0; ix < Q1; ++ix) dx[ix] = sm.eqx[r][ix][lane];
+        }
         T ex[Q1];  // FP64 mode: E^x = W + d^x
 #pragma unroll
         for (int ix = 0; ix < Q1; ++ix) ex[ix] = DEV ? T(0) : A::W(tab, ix) + dx[ix];
@@ -222,13 +246,14 @@ struct Step2D {
                 if constexpr (G == 1)
                     dy = dyall[k];
                 else
-                    dy = eq_dev_one_run<N, T>(tab, uy, ny);
+                    dy = sm.eqy[r][iy][lane];
                 const T rey = rho * (wy + dy);  // rho e^y
                 const T gr = mul_rn(gto, wy);
                 // FP32: delta f^eq = d^x rho e^y + W^x (drho W^y + rho d^y)
                 const T B = DEV ? fma(drho, wy, rho * dy) : T(0);
                 T *const op = obase + iy * Q1 * plane;
-                const unsigned q0 = (unsigned)(iy * Q1);
+                // random word of this row: node word plus a multiple of the row
+                const unsigned hrow = hnode + (unsigned)iy * 0x85EBCA6Bu;
 #pragma unroll
                 for (int ix = 0; ix < Q1; ++ix) {
                     const int nx = ix - N;
@@ -238,8 +263,7 @@ struct Step2D {
                         const T Bn = nx != 0 ? fma(T(nx), gr, B) : B;
                         const T eq = fma(dx[ix], rey, A::W(tab, ix) * Bn);
                         // increment plus dither, then one rounding of the store
-                        const unsigned q = q0 + ix;
-                        const unsigned rnd = hnode * (0x9E3779B9u * (2u * q + 1u)) + 0x7F4A7C15u * q;
+                        const unsigned rnd = hrow * (0x9E3779B9u * (2u * ix + 1u)) + 0x7F4A7C15u * ix;
                         const T inc = fma(om, eq - f0, (T)dither_ulp((float)f0, rnd));
                         v = f0 + inc;
                     } else {

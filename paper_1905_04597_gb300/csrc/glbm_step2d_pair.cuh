@@ -91,6 +91,9 @@ struct Step2DPair {
         float part[R][G][6][TW];  // (s, c) of delta rho, j_x, j_y per row, group, column
         float rw[2][TW];          // wall density deviations: lo, hi
         float dsum[NV][2][TW];    // partial wall fluxes of the NV accumulators
+        // E^x - W and E^y - W of the tile's nodes, shared by the warp groups
+        float eqx[G > 1 ? R : 1][G > 1 ? Q1 : 1][TW];
+        float eqy[G > 1 ? R : 1][G > 1 ? Q1 : 1][TW];
     };
 
     // One tile: columns x0..x0+63 (x0 a multiple of 64), rows y0..y0+R-1 of one
@@ -281,19 +284,44 @@ struct Step2DPair {
             if (bad0 || bad1) atomicOr(status, 1u);
         }
 
-        // E^x - W for both nodes
+        // E^x - W and E^y - W for both nodes
         f32x2 dx[Q1];
-        {
+        float dy0all[G == 1 ? Q1 : 1], dy1all[G == 1 ? Q1 : 1];
+        if constexpr (G == 1) {
             float d0[Q1], d1[Q1];
             eq_dev_all<N, float>(tab, lo2(ux), d0);
             eq_dev_all<N, float>(tab, hi2(ux), d1);
 #pragma unroll
             for (int ix = 0; ix < Q1; ++ix) dx[ix] = pk2(d0[ix], d1[ix]);
-        }
-        float dy0all[G == 1 ? Q1 : 1], dy1all[G == 1 ? Q1 : 1];
-        if constexpr (G == 1) {
             eq_dev_all<N, float>(tab, lo2(uy), dy0all);
             eq_dev_all<N, float>(tab, hi2(uy), dy1all);
+        } else {
+            // the G warp groups share the polynomial work: group g evaluates
+            // |n| = g, g + G, ... for both nodes and both axes, and the values
+            // meet in shared memory
+            const float u[4] = {lo2(ux), hi2(ux), lo2(uy), hi2(uy)};
+#pragma unroll
+            for (int n = 0; n <= N; ++n) {
+                if (n % G != g) continue;
+                float plus[4], minus[4];
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    float ae, bo;
+                    eq_parts<N, float>(tab, n, u[c] * u[c], ae, bo);
+                    plus[c] = n == 0 ? ae : fmaf(u[c], bo, ae);
+                    minus[c] = n == 0 ? ae : fmaf(-u[c], bo, ae);
+                }
+                *reinterpret_cast<f32x2 *>(&sm.eqx[r][N + n][2 * lane]) = pk2(plus[0], plus[1]);
+                *reinterpret_cast<f32x2 *>(&sm.eqy[r][N + n][2 * lane]) = pk2(plus[2], plus[3]);
+                if (n != 0) {
+                    *reinterpret_cast<f32x2 *>(&sm.eqx[r][N - n][2 * lane]) = pk2(minus[0], minus[1]);
+                    *reinterpret_cast<f32x2 *>(&sm.eqy[r][N - n][2 * lane]) = pk2(minus[2], minus[3]);
+                }
+            }
+            __syncthreads();
+#pragma unroll
+            for (int ix = 0; ix < Q1; ++ix)
+                dx[ix] = *reinterpret_cast<const f32x2 *>(&sm.eqx[r][ix][2 * lane]);
         }
         const f32x2 om = pk2(ip.omega_f, ip.omega_f);
         const float gto = ip.g_theta_om_f;  // g / (theta omega)
@@ -309,15 +337,11 @@ struct Step2DPair {
             if (iy < Q1) {
                 const int ny = iy - N;
                 const float wy = A::W(tab, iy);
-                float dy0, dy1;
-                if constexpr (G == 1) {
-                    dy0 = dy0all[k];
-                    dy1 = dy1all[k];
-                } else {
-                    dy0 = eq_dev_one_run<N, float>(tab, lo2(uy), ny);
-                    dy1 = eq_dev_one_run<N, float>(tab, hi2(uy), ny);
-                }
-                const f32x2 dy = pk2(dy0, dy1);
+                f32x2 dy;
+                if constexpr (G == 1)
+                    dy = pk2(dy0all[k], dy1all[k]);
+                else
+                    dy = *reinterpret_cast<const f32x2 *>(&sm.eqy[r][iy][2 * lane]);
                 const f32x2 wy2 = pk2(wy, wy);
                 const f32x2 rey = mul2(rho, add2(wy2, dy));  // rho e^y
                 const float grs = mul_rn(gto, wy);
@@ -325,7 +349,8 @@ struct Step2DPair {
                 // delta f^eq = d^x rho e^y + W^x (drho W^y + rho d^y) + force
                 const f32x2 B = fma2(drho, wy2, mul2(rho, dy));
                 float *const op = obase + iy * Q1 * plane;
-                const unsigned q0 = (unsigned)(iy * Q1);
+                const unsigned hr0 = h0 + (unsigned)iy * 0x85EBCA6Bu;  // row words
+                const unsigned hr1 = h1 + (unsigned)iy * 0x85EBCA6Bu;
 #pragma unroll
                 for (int ix = 0; ix < Q1; ++ix) {
                     const int nx = ix - N;
@@ -334,9 +359,8 @@ struct Step2DPair {
                     const float wx = A::W(tab, ix);
                     const f32x2 eq = fma2(dx[ix], rey, mul2(pk2(wx, wx), Bn));
                     // increment plus dither, then one rounding of the store
-                    const unsigned q = q0 + ix;
-                    const unsigned a = 0x9E3779B9u * (2u * q + 1u), b = 0x7F4A7C15u * q;
-                    const unsigned r0 = h0 * a + b, r1 = h1 * a + b;
+                    const unsigned a = 0x9E3779B9u * (2u * ix + 1u), b = 0x7F4A7C15u * ix;
+                    const unsigned r0 = hr0 * a + b, r1 = hr1 * a + b;
                     const float p0 = __int_as_float(__float_as_int(lo2(f0)) & 0x7F800000);
                     const float p1 = __int_as_float(__float_as_int(hi2(f0)) & 0x7F800000);
                     const f32x2 dith =
