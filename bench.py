@@ -58,6 +58,36 @@ def workload(name):
     return cfgs, label
 
 
+KERNEL_SOURCES = ("glbm_device.cuh", "glbm_step2d.cuh", "glbm_step2d_pair.cuh",
+                  "glbm_step2d_launch.cuh", "glbm_tiles.h", "glbm_internal.h")
+
+
+def kernel_source_hash():
+    """SHA-256 (first 16 hex digits) of the sources of the fused 2D step."""
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_1905_04597_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(kernel, workload):
+    """DRAM bytes per launch of `kernel` on `workload` from the committed ncu
+    capture (profiles/traffic.json), or None when there is none for the kernel
+    sources as they are now."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as fh:
+        rec = json.load(fh)
+    for r in rec.get("captures", []):
+        if (r.get("kernel") == kernel and r.get("workload") == workload
+                and r.get("source_hash") == kernel_source_hash()):
+            return r["dram_bytes_per_launch"]
+    return None
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -257,6 +287,7 @@ def run_ours(args):
                "lb_steps_per_step": lb_per_call,
                "call": "glbm_set_equilibrium(host) x3 + glbm_step(100) + glbm_moments(host) x3"}
 
+    precision = precision_check(cfgs[0], min(steps, 2000)) if dims == 2 else None
     batched = (measure_batched(autotune=args.tiles == "autotune")
                if (args.workload == "couette" and not args.no_batched) else None)
 
@@ -280,12 +311,14 @@ def run_ours(args):
                  "hbm_gbs_algorithmic": gbs64, "frac_of_hbm": gbs64 / peak,
                  "clocks": clocks64},
         "roofline": {"bound": "hbm", "achieved": gbs32, "peak": peak, "unit": "GB/s",
-                     "frac": gbs32 / peak, "traffic": None,
+                     "frac": gbs32 / peak,
+                     "traffic": measured_traffic(tiles_used.get(glbm.FP32_DEV), label),
                      "kernel": tiles_used.get(glbm.FP32_DEV, "k_step1d"),
                      "bytes_per_launch": bytes32, "peak_source": peak_kind},
         "gpu_launches": launches,
         "clocks": clocks,
         "e2e": e2e,
+        "precision": precision,
         "batched": batched,
         "cpu_baseline": cpu,
     }
@@ -296,6 +329,27 @@ def run_ours(args):
 
 
 STEPS_PER_SOLVE = 2000  # a channel solve of the batched workload
+
+
+def precision_check(cfg, steps):
+    """FP32-deviation against FP64 storage on the GPU for one instance of the
+    workload from the same initial state: max relative error of every moment
+    after `steps` steps (the FP64 path itself matches the CPU oracle to 1e-12 in
+    the parity tests)."""
+    from paper_1905_04597_gb300 import glbm, metrics
+    runs = {}
+    for prec in (glbm.FP32_DEV, glbm.FP64):
+        lat = glbm.Lattice(dict(cfg, prec=prec))
+        lat.step(steps)
+        lat.sync()
+        runs[prec] = (lat.moments(0), lat.get_populations(0) if prec == glbm.FP64 else None)
+        lat.close()
+    dims = cfg["dims"]
+    names = metrics.FIELDS_2D if dims == 2 else metrics.FIELDS_1D
+    want = np.stack([runs[glbm.FP64][0][n] for n in names])
+    errs = metrics.rel_errors(runs[glbm.FP32_DEV][0], want, dims=dims, F=runs[glbm.FP64][1])
+    return {"steps": steps, "instance": {k: cfg[k] for k in ("k", "nx", "ny", "kn") if k in cfg},
+            "fp32_vs_fp64_max_rel_err": errs, "max": max(errs.values())}
 
 
 def measure_batched(steps32=256, steps64=64, warmup=8, autotune=True):

@@ -1,58 +1,10 @@
-"""Error metric of the GPU parity tests (moment comparison against the oracle).
-
-A field's error is max |got - want| divided by max(max |want|, 1e-3 * S), where
-S is the largest per-node sum of the absolute terms of that moment: a moment
-that cancels to below a thousandth of its own terms cannot be reproduced to a
-fixed fraction of its value by sums taken in another order, so it is judged
-against that floor. The two velocity and the two heat-flux components are
-normalised jointly.
-"""
-import numpy as np
-
-from paper_1905_04597_gb300 import glbm
-
-
-def term_scales(F, want, dims=2):
-    """Largest per-node sum of absolute terms of each moment of populations F."""
-    Q = F.shape[0]
-    if dims == 2:
-        Q1 = int(round(np.sqrt(Q)))
-        N = (Q1 - 1) // 2
-        cx = np.tile(np.arange(-N, N + 1), Q1).astype(float)[:, None, None]
-        cy = np.repeat(np.arange(-N, N + 1), Q1).astype(float)[:, None, None]
-        rho, ux, uy = want[0], want[1], want[2]
-        dx, dy = cx - ux, cy - uy
-        d2 = dx * dx + dy * dy
-        su = max((np.abs(cx) * F).sum(0).max(), (np.abs(cy) * F).sum(0).max()) / rho.min()
-        sq = 0.5 * (np.sqrt(d2) ** 3 * F).sum(0).max()
-        return {"rho": F.sum(0).max(), "ux": su, "uy": su, "T": (d2 * F).sum(0).max() / 2 / rho.min(),
-                "qx": sq, "qy": sq, "sxy": (np.abs(dx * dy) * F).sum(0).max()}
-    N = (Q - 1) // 2
-    c = np.arange(-N, N + 1).astype(float)[:, None]
-    rho, ux = want[0], want[1]
-    d = c - ux
-    return {"rho": F.sum(0).max(), "ux": (np.abs(c) * F).sum(0).max() / rho.min(),
-            "T": (d * d * F).sum(0).max() / rho.min(), "qx": 0.5 * (np.abs(d) ** 3 * F).sum(0).max()}
-
-
-def rel_errors(got, want, dims=2, F=None):
-    """Per-field max |got - want| / max(max |want|, 1e-3 S); velocity and heat-flux
-    pairs joint. F (the oracle's streamed populations) gives the term scales S."""
-    names = glbm.FIELDS_2D if dims == 2 else glbm.FIELDS_1D
-    w = {n: want[i] for i, n in enumerate(names)}
-    groups = {"ux": ("ux", "uy"), "uy": ("ux", "uy"), "qx": ("qx", "qy"), "qy": ("qx", "qy")}
-    S = term_scales(F, want, dims) if F is not None else {}
-    out = {}
-    for n in names:
-        scale = max(np.abs(w[m]).max() for m in groups.get(n, (n,)) if m in w)
-        scale = max(scale, 1e-3 * S.get(n, 0.0))
-        out[n] = np.abs(got[n] - w[n]).max() / max(scale, 1e-300)
-    return out
+"""Helpers of the GPU parity tests: the moment error metric (the package's
+metrics module, also used by the benchmark's FP32-vs-FP64 check) and the
+oracle's moments of a state."""
+from paper_1905_04597_gb300.metrics import rel_errors, term_scales  # noqa: F401
 
 
 def oracle_moments(o, X):
     """(moments, streamed populations) of the oracle state X."""
     F = o.stream(X)
     return o.macro(F), F
-
-
