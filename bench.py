@@ -88,6 +88,26 @@ def measured_traffic(kernel, workload):
     return None
 
 
+def fp64_pipe_record(kernel, workload):
+    """FP64 instructions per launch of `kernel` on `workload` from the committed
+    ncu counters (profiles/traffic.json), or None if they do not describe the
+    current kernel sources."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as fh:
+        rec = json.load(fh)
+    for r in rec.get("fp64", []):
+        if (r.get("kernel") == kernel and r.get("workload") == workload
+                and r.get("source_hash") == kernel_source_hash()):
+            return r
+    return None
+
+
+FP64_INST_PER_SM_CLK = 2  # FP64 pipe issue rate of a GB300 SM (ncu peak_sustained of DFMA)
+N_SM = 152
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -157,10 +177,30 @@ class ClockSampler:
 
 
 def dist_setup():
+    """(world size, rank, local rank) from the torchrun environment (1, 0, 0 alone)."""
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return world, rank, local
+
+
+def max_over_ranks(x):
+    """The largest x over the ranks of the initialised process group (x alone
+    without one): the job's time is that of its slowest rank."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(units_per_rank, world, ms_max):
+    """Whole-job throughput: the units every rank processed over the slowest
+    rank's time (weak scaling: each rank runs its own copy of the workload)."""
+    return units_per_rank * world / (ms_max / 1e3)
 
 
 def run_ours(args):
@@ -230,10 +270,7 @@ def run_ours(args):
         launches = lat.kernel_launches - l0
         lat.sync()
         lat.close()
-        if world > 1:
-            t = torch.tensor([ms], device="cuda")
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            ms = float(t.item())
+        ms = max_over_ranks(ms)
         return ms, launches, clk.summary()
 
     steps, warmup = args.steps, args.warmup
@@ -241,8 +278,8 @@ def run_ours(args):
     ms64, _, clocks64 = timed(glbm.FP64, max(steps // 4, 4), warmup)
     steps64 = max(steps // 4, 4)
 
-    value = pops_per_step * steps * world / (ms32 / 1e3)
-    value64 = pops_per_step * steps64 * world / (ms64 / 1e3)
+    value = job_throughput(pops_per_step * steps, world, ms32)
+    value64 = job_throughput(pops_per_step * steps64, world, ms64)
     peak, peak_kind = peaks()
     bytes32 = 2 * 4 * pops_per_step       # algorithmic bytes of one launch (read + write)
     bytes64 = 2 * 8 * pops_per_step
@@ -288,6 +325,16 @@ def run_ours(args):
                "call": "glbm_set_equilibrium(host) x3 + glbm_step(100) + glbm_moments(host) x3"}
 
     precision = precision_check(cfgs[0], min(steps, 2000)) if dims == 2 else None
+    # FP64 is bound by the FP64 pipe: its instructions per launch come from the
+    # committed ncu counters, the peak from the pipe's issue rate and the clock
+    fp64_roof = None
+    rec = fp64_pipe_record(tiles_used.get(glbm.FP64), label)
+    if rec is not None and clocks64.get("sm_max_mhz"):
+        ach = rec["dp_inst_per_launch"] / (ms64 / steps64 / 1e3) / 1e9
+        pk = FP64_INST_PER_SM_CLK * N_SM * clocks64["sm_max_mhz"] / 1e3
+        fp64_roof = {"bound": "alu", "achieved": ach, "peak": pk, "unit": "G FP64 inst/s",
+                     "frac": ach / pk, "hbm_frac": gbs64 / peak,
+                     "dp_flops_per_pop": rec["dp_flops_per_launch"] / pops_per_step}
     batched = (measure_batched(autotune=args.tiles == "autotune")
                if (args.workload == "couette" and not args.no_batched) else None)
 
@@ -307,7 +354,7 @@ def run_ours(args):
         "mlups": nodes * n_inst * steps * world / (ms32 / 1e3) / 1e6,
         "hbm_gbs_algorithmic": gbs32,
         "fp64": {"value": value64, "unit": UNIT, "ms_per_step": ms64 / steps64, "steps": steps64,
-                 "kernel": tiles_used.get(glbm.FP64, "k_step1d"),
+                 "kernel": tiles_used.get(glbm.FP64, "k_step1d"), "roofline": fp64_roof,
                  "hbm_gbs_algorithmic": gbs64, "frac_of_hbm": gbs64 / peak,
                  "clocks": clocks64},
         "roofline": {"bound": "hbm", "achieved": gbs32, "peak": peak, "unit": "GB/s",
