@@ -28,6 +28,7 @@ struct Step2D {
     static constexpr int NW = G * R;              // warps per CTA
     static constexpr int NT = 32 * NW;
     static constexpr int NV = 4;                  // wall-flux accumulators
+    static constexpr bool DX_SHARED = G > 1 && sizeof(T) == 4;  // E^x - W read from smem
     static constexpr bool DEV = sizeof(T) == 4;   // FP32 deviation storage
     using A = TabAcc<T>;
 
@@ -220,8 +221,10 @@ struct Step2D {
                 if (n != 0) sm.eqy[r][N - n][lane] = fma(-uy, bo, ae);
             }
             __syncthreads();
+            if constexpr (!DX_SHARED) {
 #pragma unroll
-            for (int ix = 0; ix < Q1; ++ix) dx[ix] = sm.eqx[r][ix][lane];
+                for (int ix = 0; ix < Q1; ++ix) dx[ix] = sm.eqx[r][ix][lane];
+            }
         }
         T ex[Q1];  // FP64 mode: E^x = W + d^x
 #pragma unroll
@@ -261,7 +264,9 @@ struct Step2D {
                     T v;
                     if (DEV) {
                         const T Bn = nx != 0 ? fma(T(nx), gr, B) : B;
-                        const T eq = fma(dx[ix], rey, A::W(tab, ix) * Bn);
+                        // split FP32 tiles read E^x - W where it is used (fewer registers)
+                        const T dxv = DX_SHARED ? sm.eqx[r][ix][lane] : dx[ix];
+                        const T eq = fma(dxv, rey, A::W(tab, ix) * Bn);
                         // increment plus dither, then one rounding of the store
                         const unsigned rnd = hrow * (0x9E3779B9u * (2u * ix + 1u)) + 0x7F4A7C15u * ix;
                         const T inc = fma(om, eq - f0, (T)dither_ulp((float)f0, rnd));

@@ -318,10 +318,7 @@ struct Step2DPair {
                     *reinterpret_cast<f32x2 *>(&sm.eqy[r][N - n][2 * lane]) = pk2(minus[2], minus[3]);
                 }
             }
-            __syncthreads();
-#pragma unroll
-            for (int ix = 0; ix < Q1; ++ix)
-                dx[ix] = *reinterpret_cast<const f32x2 *>(&sm.eqx[r][ix][2 * lane]);
+            __syncthreads();  // E^x - W is read from shared memory where it is used
         }
         const f32x2 om = pk2(ip.omega_f, ip.omega_f);
         const float gto = ip.g_theta_om_f;  // g / (theta omega)
@@ -357,7 +354,9 @@ struct Step2DPair {
                     const f32x2 f0 = f[k][ix];
                     const f32x2 Bn = nx != 0 ? fma2(pk2((float)nx, (float)nx), gr, B) : B;
                     const float wx = A::W(tab, ix);
-                    const f32x2 eq = fma2(dx[ix], rey, mul2(pk2(wx, wx), Bn));
+                    const f32x2 dxv = G == 1 ? dx[ix]
+                                             : *reinterpret_cast<const f32x2 *>(&sm.eqx[r][ix][2 * lane]);
+                    const f32x2 eq = fma2(dxv, rey, mul2(pk2(wx, wx), Bn));
                     // increment plus dither, then one rounding of the store
                     const unsigned a = 0x9E3779B9u * (2u * ix + 1u), b = 0x7F4A7C15u * ix;
                     const unsigned r0 = hr0 * a + b, r1 = hr1 * a + b;

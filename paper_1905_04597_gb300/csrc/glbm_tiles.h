@@ -26,16 +26,16 @@ struct Tiles;
 // given context).
 GLBM_TILES(1, float, {1, 16, 2}, {1, 8, 2}, {1, 16, 1}, {1, 8, 1}, {1, 4, 1})
 GLBM_TILES(2, float, {1, 4, 2}, {1, 8, 2}, {1, 8, 1}, {1, 4, 1}, {1, 16, 1})
-GLBM_TILES(3, float, {1, 4, 1}, {1, 2, 1}, {1, 8, 1}, {2, 4, 1}, {1, 2, 2}, {2, 2, 2}, {2, 4, 2})
+GLBM_TILES(3, float, {2, 2, 2}, {1, 4, 1}, {1, 2, 1}, {1, 8, 1}, {2, 4, 1}, {1, 2, 2}, {2, 4, 2})
 GLBM_TILES(4, float, {3, 1, 2}, {2, 2, 2}, {3, 2, 2}, {1, 4, 1}, {1, 2, 1}, {2, 2, 1}, {2, 4, 1},
            {3, 2, 1})
 GLBM_TILES(5, float, {4, 1, 2}, {3, 1, 2}, {4, 2, 2}, {3, 2, 1}, {2, 2, 1}, {2, 1, 1}, {2, 4, 1},
            {4, 2, 1})
-GLBM_TILES(6, float, {2, 2, 1}, {4, 1, 2}, {5, 1, 2}, {7, 1, 2}, {2, 1, 1}, {3, 1, 1}, {3, 2, 1},
-           {4, 2, 1})
-GLBM_TILES(7, float, {5, 1, 1}, {4, 1, 1}, {3, 1, 1}, {3, 2, 1}, {2, 2, 1}, {4, 2, 1}, {5, 1, 2},
+GLBM_TILES(6, float, {4, 2, 1}, {2, 2, 1}, {4, 1, 2}, {5, 1, 2}, {7, 1, 2}, {2, 1, 1}, {3, 1, 1},
+           {3, 2, 1})
+GLBM_TILES(7, float, {5, 1, 2}, {5, 1, 1}, {4, 1, 1}, {3, 1, 1}, {3, 2, 1}, {2, 2, 1}, {4, 2, 1},
            {4, 1, 2})
-GLBM_TILES(8, float, {4, 1, 1}, {4, 2, 1}, {3, 1, 1}, {3, 2, 1}, {5, 1, 1}, {6, 1, 1}, {6, 1, 2},
+GLBM_TILES(8, float, {6, 1, 1}, {4, 1, 1}, {4, 2, 1}, {3, 1, 1}, {3, 2, 1}, {5, 1, 1}, {6, 1, 2},
            {9, 1, 2})
 // FP64 (one-node tiles)
 GLBM_TILES(1, double, {1, 8, 1}, {1, 4, 1})
