@@ -77,6 +77,163 @@ __device__ __forceinline__ void acc2x2(f32x2 &s, f32x2 &c, f32x2 x)
     c = add2(c, err);
 }
 
+// Wall densities of a pair tile's 64 columns (row a2 of the fused step): the
+// mass streaming into each wall, summed through NV fixed accumulators (pair
+// p mod NV of the (|n_y|, row) pairs) in the order of the one-node tile,
+// whatever the tile shape; the NW warps of the CTA share the accumulators.
+// Leaves rho_w - 1 of both walls in rw[2][64]. Every thread calls it.
+template <int N, int NV>
+__device__ __forceinline__ void pair_wall_densities(const InstParams &ip, const float *__restrict__ fin,
+                                                    int Ly, int pitch, int plane, const int *win,
+                                                    bool need_lo, bool need_hi, int w, int NW,
+                                                    int lane, float (*dsum)[2][64], float (*rw)[64])
+{
+    constexpr int Q1 = 2 * N + 1;
+#pragma unroll 1
+    for (int v = w; v < NV; v += NW) {
+        float slo0 = 0.f, slo1 = 0.f, shi0 = 0.f, shi1 = 0.f;
+#pragma unroll 1
+        for (int p = v; p < N * (N + 1) / 2; p += NV) {
+            int aa = 1, k = p;
+            while (k >= aa) {
+                k -= aa;
+                ++aa;
+            }
+            if (need_lo) {  // velocity ny = -aa leaving row k through y = -1/2
+                const float *pl = fin + ((N - aa) * Q1 * plane + k * pitch);
+#pragma unroll
+                for (int ix = 0; ix < Q1; ++ix) {
+                    slo0 += __ldg(pl + (ix * plane + win[2 * N - ix]));
+                    slo1 += __ldg(pl + (ix * plane + win[2 * N - ix + 1]));
+                }
+            }
+            if (need_hi) {  // velocity ny = +aa leaving row Ly-1-k through y = Ly-1/2
+                const float *ph = fin + ((N + aa) * Q1 * plane + (Ly - 1 - k) * pitch);
+#pragma unroll
+                for (int ix = 0; ix < Q1; ++ix) {
+                    shi0 += __ldg(ph + (ix * plane + win[2 * N - ix]));
+                    shi1 += __ldg(ph + (ix * plane + win[2 * N - ix + 1]));
+                }
+            }
+        }
+        dsum[v][0][2 * lane] = slo0;
+        dsum[v][0][2 * lane + 1] = slo1;
+        dsum[v][1][2 * lane] = shi0;
+        dsum[v][1][2 * lane + 1] = shi1;
+    }
+    __syncthreads();
+    if (w == 0) {
+        const float inv_den = ip.inv_den_f;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int col = 2 * lane + h;
+            float s0 = 0.f, s1 = 0.f;
+#pragma unroll
+            for (int j = 0; j < NV; ++j) {
+                s0 += dsum[j][0][col];
+                s1 += dsum[j][1][col];
+            }
+            // rho_w - 1 = (D - den) / den: D - den is the absorbed deviation
+            rw[0][col] = s0 * inv_den;
+            rw[1][col] = s1 * inv_den;
+        }
+    }
+    __syncthreads();
+}
+
+// Pull of one velocity row iy (source row ys) for a node pair: f[ix] holds
+// both nodes' populations of velocity (ix - N, iy - N).
+template <int N>
+__device__ __forceinline__ void pair_load_row(const float *__restrict__ fin, int iy, int ys,
+                                              int pitch, int plane, int x, bool inner,
+                                              const int *win, f32x2 (&f)[2 * N + 1])
+{
+    constexpr int Q1 = 2 * N + 1;
+    const float *rowp = fin + (iy * Q1 * plane + ys * pitch);
+    if (inner) {
+#pragma unroll
+        for (int ix = 0; ix < Q1; ++ix) {
+            const int nx = ix - N;
+            const float *p = rowp + (ix * plane + (x - nx));
+            if ((nx & 1) == 0)  // (x - nx) even: one aligned 8-byte load
+                f[ix] = __ldg(reinterpret_cast<const f32x2 *>(p));
+            else
+                f[ix] = pk2(__ldg(p), __ldg(p + 1));
+        }
+    } else {
+#pragma unroll
+        for (int ix = 0; ix < Q1; ++ix) {
+            const float *p = rowp + ix * plane;
+            f[ix] = pk2(__ldg(p + win[2 * N - ix]), __ldg(p + win[2 * N - ix + 1]));
+        }
+    }
+}
+
+// The populations a wall re-emits into velocity row iy of a node pair
+// (sources inside the wall): W^y (drho_w W^x + rho_w (E^x(u_w) - W^x)).
+template <int N>
+__device__ __forceinline__ void pair_wall_row(const AxisTable &tab, const InstParams &ip, int iy,
+                                              bool lo, float rw0, float rw1, f32x2 (&f)[2 * N + 1])
+{
+    using A = TabAcc<float>;
+    const float wy = A::W(tab, iy);
+#pragma unroll
+    for (int ix = 0; ix < 2 * N + 1; ++ix) {
+        const float dw = lo ? ip.dw_lo_f[ix] : ip.dw_hi_f[ix];
+        const float wx = A::W(tab, ix);
+        f[ix] = pk2(wy * fmaf(rw0, wx, (1.f + rw0) * dw), wy * fmaf(rw1, wx, (1.f + rw1) * dw));
+    }
+}
+
+// Relaxation plus force and the dithered FP32 store of velocity row iy of a
+// node pair: f* = f + omega (f^eq + F/omega - f) with
+// delta f^eq = d^x rho e^y + W^x (drho W^y + rho d^y), the force through the
+// row factor gr = W^y g / (theta omega), and a dither of half an ulp drawn from
+// the nodes' words h0, h1, the row and the column. E^x - W comes from the
+// registers dxr, or from shared memory at dxs (stride 32 pairs) when DXS.
+template <int N, bool DXS>
+__device__ __forceinline__ void pair_collide_row(const AxisTable &tab, int iy, float wy, f32x2 dy,
+                                                 f32x2 rho, f32x2 drho, f32x2 om, float gto,
+                                                 const f32x2 (&f)[2 * N + 1],
+                                                 const f32x2 (&dxr)[2 * N + 1], const f32x2 *dxs,
+                                                 float *op, int plane, unsigned h0, unsigned h1,
+                                                 bool act0, bool act1)
+{
+    using A = TabAcc<float>;
+    const f32x2 wy2 = pk2(wy, wy);
+    const f32x2 rey = mul2(rho, add2(wy2, dy));  // rho e^y
+    const float grs = mul_rn(gto, wy);
+    const f32x2 gr = pk2(grs, grs);
+    const f32x2 B = fma2(drho, wy2, mul2(rho, dy));
+    const unsigned hr0 = h0 + (unsigned)iy * 0x85EBCA6Bu;  // row words
+    const unsigned hr1 = h1 + (unsigned)iy * 0x85EBCA6Bu;
+    const f32x2 two55 = pk2(0x1p-55f, 0x1p-55f);
+#pragma unroll
+    for (int ix = 0; ix < 2 * N + 1; ++ix) {
+        const int nx = ix - N;
+        const f32x2 f0 = f[ix];
+        const f32x2 Bn = nx != 0 ? fma2(pk2((float)nx, (float)nx), gr, B) : B;
+        const float wx = A::W(tab, ix);
+        const f32x2 dxv = DXS ? dxs[ix * 32] : dxr[ix];
+        const f32x2 eq = fma2(dxv, rey, mul2(pk2(wx, wx), Bn));
+        // increment plus dither, then one rounding of the store
+        const unsigned a = 0x9E3779B9u * (2u * ix + 1u), b = 0x7F4A7C15u * ix;
+        const unsigned r0 = hr0 * a + b, r1 = hr1 * a + b;
+        const float p0 = __int_as_float(__float_as_int(lo2(f0)) & 0x7F800000);
+        const float p1 = __int_as_float(__float_as_int(hi2(f0)) & 0x7F800000);
+        const f32x2 dith = mul2(mul2(pk2((float)(int)r0, (float)(int)r1), two55), pk2(p0, p1));
+        const f32x2 inc = fma2(om, sub2(eq, f0), dith);
+        const f32x2 v = add2(f0, inc);
+        float *const o = op + ix * plane;
+        if (act0 && act1) {
+            *reinterpret_cast<f32x2 *>(o) = v;
+        } else {
+            if (act0) o[0] = lo2(v);
+            if (act1) o[1] = hi2(v);
+        }
+    }
+}
+
 template <int N, int G, int R>
 struct Step2DPair {
     static constexpr int Q1 = 2 * N + 1;
@@ -126,60 +283,9 @@ struct Step2DPair {
         // ---- phase 0: wall densities of this tile's columns ---------------
         const bool need_lo = walls && (y0 < N);
         const bool need_hi = walls && (y0 + R > Ly - N);
-        if (need_lo || need_hi) {
-            // the wall-flux sums in the order of the one-node tile: NV fixed
-            // accumulators (pair p mod NV), whatever the tile shape
-#pragma unroll 1
-            for (int v = w; v < NV; v += NW) {
-                float slo0 = 0.f, slo1 = 0.f, shi0 = 0.f, shi1 = 0.f;
-#pragma unroll 1
-                for (int p = v; p < N * (N + 1) / 2; p += NV) {
-                    int aa = 1, k = p;
-                    while (k >= aa) {
-                        k -= aa;
-                        ++aa;
-                    }
-                    if (need_lo) {  // velocity ny = -aa leaving row k through y = -1/2
-                        const float *pl = fin + ((N - aa) * Q1 * plane + k * pitch);
-#pragma unroll
-                        for (int ix = 0; ix < Q1; ++ix) {
-                            slo0 += __ldg(pl + (ix * plane + win[2 * N - ix]));
-                            slo1 += __ldg(pl + (ix * plane + win[2 * N - ix + 1]));
-                        }
-                    }
-                    if (need_hi) {  // velocity ny = +aa leaving row Ly-1-k through y = Ly-1/2
-                        const float *ph = fin + ((N + aa) * Q1 * plane + (Ly - 1 - k) * pitch);
-#pragma unroll
-                        for (int ix = 0; ix < Q1; ++ix) {
-                            shi0 += __ldg(ph + (ix * plane + win[2 * N - ix]));
-                            shi1 += __ldg(ph + (ix * plane + win[2 * N - ix + 1]));
-                        }
-                    }
-                }
-                sm.dsum[v][0][2 * lane] = slo0;
-                sm.dsum[v][0][2 * lane + 1] = slo1;
-                sm.dsum[v][1][2 * lane] = shi0;
-                sm.dsum[v][1][2 * lane + 1] = shi1;
-            }
-            __syncthreads();
-            if (w == 0) {
-                const float inv_den = ip.inv_den_f;
-#pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const int col = 2 * lane + h;
-                    float s0 = 0.f, s1 = 0.f;
-#pragma unroll
-                    for (int j = 0; j < NV; ++j) {
-                        s0 += sm.dsum[j][0][col];
-                        s1 += sm.dsum[j][1][col];
-                    }
-                    // rho_w - 1 = (D - den) / den: D - den is the absorbed deviation
-                    sm.rw[0][col] = s0 * inv_den;
-                    sm.rw[1][col] = s1 * inv_den;
-                }
-            }
-            __syncthreads();
-        }
+        if (need_lo || need_hi)
+            pair_wall_densities<N, NV>(ip, fin, Ly, pitch, plane, win, need_lo, need_hi, w, NW, lane,
+                                       sm.dsum, sm.rw);
 
         // ---- phase 1: pull and partial moments -----------------------------
         // rows iy = g + k G of this warp group; f[k][ix] holds both nodes
@@ -192,24 +298,7 @@ struct Step2DPair {
                 const int ny = iy - N;
                 int ys = yc - ny;
                 ys = walls ? min(max(ys, 0), Ly - 1) : wrap_shift(ys, Ly, Ly > N);
-                const float *rowp = fin + (iy * Q1 * plane + ys * pitch);
-                if (inner) {
-#pragma unroll
-                    for (int ix = 0; ix < Q1; ++ix) {
-                        const int nx = ix - N;
-                        const float *p = rowp + (ix * plane + (x - nx));
-                        if ((nx & 1) == 0)  // (x - nx) even: one aligned 8-byte load
-                            f[k][ix] = __ldg(reinterpret_cast<const f32x2 *>(p));
-                        else
-                            f[k][ix] = pk2(__ldg(p), __ldg(p + 1));
-                    }
-                } else {
-#pragma unroll
-                    for (int ix = 0; ix < Q1; ++ix) {
-                        const float *p = rowp + ix * plane;
-                        f[k][ix] = pk2(__ldg(p + win[2 * N - ix]), __ldg(p + win[2 * N - ix + 1]));
-                    }
-                }
+                pair_load_row<N>(fin, iy, ys, pitch, plane, x, inner, win, f[k]);
             }
         }
 #pragma unroll
@@ -220,17 +309,8 @@ struct Step2DPair {
                 const int ys = yc - ny;
                 if (walls && (ys < 0 || ys >= Ly)) {  // uniform across the warp
                     const bool lo = ys < 0;
-                    const float wy = A::W(tab, iy);
-                    const float rw0 = sm.rw[lo ? 0 : 1][2 * lane];
-                    const float rw1 = sm.rw[lo ? 0 : 1][2 * lane + 1];
-#pragma unroll
-                    for (int ix = 0; ix < Q1; ++ix) {
-                        const float dw = lo ? ip.dw_lo_f[ix] : ip.dw_hi_f[ix];
-                        const float wx = A::W(tab, ix);
-                        // W^y (drho_w W^x + rho_w (E^x(u_w) - W^x))
-                        f[k][ix] = pk2(wy * fmaf(rw0, wx, (1.f + rw0) * dw),
-                                       wy * fmaf(rw1, wx, (1.f + rw1) * dw));
-                    }
+                    pair_wall_row<N>(tab, ip, iy, lo, sm.rw[lo ? 0 : 1][2 * lane],
+                                     sm.rw[lo ? 0 : 1][2 * lane + 1], f[k]);
                 }
                 f32x2 rs = 0ull;
 #pragma unroll
@@ -326,55 +406,22 @@ struct Step2DPair {
         // random words of the two nodes and this launch (dithered stores)
         const unsigned h0 = hash32((unsigned)(y * Lx + x) ^ seed);
         const unsigned h1 = hash32((unsigned)(y * Lx + x + 1) ^ seed);
-        const f32x2 two55 = pk2(0x1p-55f, 0x1p-55f);
 
 #pragma unroll
         for (int k = 0; k < RPG; ++k) {
             const int iy = g + k * G;
             if (iy < Q1) {
-                const int ny = iy - N;
                 const float wy = A::W(tab, iy);
                 f32x2 dy;
                 if constexpr (G == 1)
                     dy = pk2(dy0all[k], dy1all[k]);
                 else
                     dy = *reinterpret_cast<const f32x2 *>(&sm.eqy[r][iy][2 * lane]);
-                const f32x2 wy2 = pk2(wy, wy);
-                const f32x2 rey = mul2(rho, add2(wy2, dy));  // rho e^y
-                const float grs = mul_rn(gto, wy);
-                const f32x2 gr = pk2(grs, grs);
-                // delta f^eq = d^x rho e^y + W^x (drho W^y + rho d^y) + force
-                const f32x2 B = fma2(drho, wy2, mul2(rho, dy));
-                float *const op = obase + iy * Q1 * plane;
-                const unsigned hr0 = h0 + (unsigned)iy * 0x85EBCA6Bu;  // row words
-                const unsigned hr1 = h1 + (unsigned)iy * 0x85EBCA6Bu;
-#pragma unroll
-                for (int ix = 0; ix < Q1; ++ix) {
-                    const int nx = ix - N;
-                    const f32x2 f0 = f[k][ix];
-                    const f32x2 Bn = nx != 0 ? fma2(pk2((float)nx, (float)nx), gr, B) : B;
-                    const float wx = A::W(tab, ix);
-                    const f32x2 dxv = G == 1 ? dx[ix]
-                                             : *reinterpret_cast<const f32x2 *>(&sm.eqx[r][ix][2 * lane]);
-                    const f32x2 eq = fma2(dxv, rey, mul2(pk2(wx, wx), Bn));
-                    // increment plus dither, then one rounding of the store
-                    const unsigned a = 0x9E3779B9u * (2u * ix + 1u), b = 0x7F4A7C15u * ix;
-                    const unsigned r0 = hr0 * a + b, r1 = hr1 * a + b;
-                    const float p0 = __int_as_float(__float_as_int(lo2(f0)) & 0x7F800000);
-                    const float p1 = __int_as_float(__float_as_int(hi2(f0)) & 0x7F800000);
-                    const f32x2 dith =
-                        mul2(mul2(pk2((float)(int)r0, (float)(int)r1), two55), pk2(p0, p1));
-                    const f32x2 inc = fma2(om, sub2(eq, f0), dith);
-                    const f32x2 v = add2(f0, inc);
-                    float *const o = op + ix * plane;
-                    if (act0 && act1) {
-                        *reinterpret_cast<f32x2 *>(o) = v;
-                    } else {
-                        if (act0) o[0] = lo2(v);
-                        if (act1) o[1] = hi2(v);
-                    }
-                }
+                const f32x2 *dxs = reinterpret_cast<const f32x2 *>(&sm.eqx[G > 1 ? r : 0][0][2 * lane]);
+                pair_collide_row<N, (G > 1)>(tab, iy, wy, dy, rho, drho, om, gto, f[k], dx, dxs,
+                                             obase + iy * Q1 * plane, plane, h0, h1, act0, act1);
             }
         }
     }
 };
+
