@@ -66,19 +66,28 @@ typedef enum {
  *   nx, ny    nodes (ny ignored when dims == 1). With walls ny >= k+1; with
  *             bounce-back nx >= k+1.
  *   k         summations of D1Q3 per axis (level N = k+1, 2N+1 velocities per
- *             axis, Sec. 2); 0 <= k <= 7. Both axes use the same k.
+ *             axis, Sec. 2); 0 <= k <= 7.
+ *   x_level   level along x of a 2D lattice: 0 (or k+1) takes the level of k
+ *             on both axes; 1 makes the anisotropic product D1Q3 (x) times
+ *             the level-(k+1) lattice (y), the tensor product of Sec. 4 with
+ *             3 (2k+3) velocities that the paper uses for channel flows. The
+ *             x axis then has its own lattice units (theta_x = 1/3): the force
+ *             and the wall speeds are x quantities. Velocity q of the layout is
+ *             (ny + N) (2 N_x + 1) + (nx + N_x). Not for 1D lattices,
+ *             heterogeneous batches or the adjoint.
  *   tau       relaxation time (> 0), used when kn <= 0.
  *   kn        Knudsen number of Eq. (kn), Sec. 5.2: when > 0 it sets
  *             tau = kn * H / sqrt(2 theta), theta = N/3, H = ny (2D) or nx (1D).
  *   bc, prec  glbm_bc, glbm_prec.
  *   u_wall_lo, u_wall_hi  x-velocities of the walls (GLBM_BC_WALLS).
  *   g         body force along x (2D), added after relaxation as
- *             F_i = W_i xi_x g / theta (the linearised force of Sec. 5.4).
+ *             F_i = W_i xi_x g / theta_x (the linearised force of Sec. 5.4).
  */
 typedef struct {
     int dims;
     int nx, ny;
     int k;
+    int x_level;
     double tau;
     double kn;
     int bc;

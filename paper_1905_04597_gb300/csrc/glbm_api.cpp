@@ -88,7 +88,7 @@ static void dev_free(const DevAlloc &A, void *p, cudaStream_t s)
 // context
 // ---------------------------------------------------------------------------
 struct Geo {
-    int N, Lx, Ly, pitch, Q;
+    int N, NX, Lx, Ly, pitch, Q;  // N: level along y (and x), NX: level along x
     long long plane;  // elements per velocity plane
     long long off;    // element offset of the instance in the pool
     long long nodes() const { return (long long)Lx * Ly; }
@@ -136,19 +136,19 @@ static void fill_inst(const glbm_ctx *c, const glbm_config &cfg, const Geo &g, I
                       double tau)
 {
     memset(&ip, 0, sizeof(ip));
-    const int N = g.N;
-    const AxisTable &tab = c->tabs[N];
-    const double theta = N / 3.0;
+    const int N = g.N, NX = g.NX;
+    const AxisTable &tab = c->tabs[N];  // y axis
+    const double theta_x = NX / 3.0;
     ip.omega = 1.0 / (tau + 0.5);
-    ip.g_theta = c->dims == 2 ? cfg.g / theta : 0.0;
-    double den = 0.0;
+    ip.g_theta = c->dims == 2 ? cfg.g / theta_x : 0.0;
+    double den = 0.0;  // the wall's normaliser runs over the y velocities
     for (int n = 1; n <= N; ++n) den += n * tab.W[n + N];
     ip.inv_den = 1.0 / den;
-    // E^x_n(u_w) from the coefficient table (FP64 Horner)
+    // E^x_n(u_w) of the x axis from its coefficient table (FP64 Horner)
     double full[GLBM_MAXQ1 * GLBM_MAXQ1];
     AxisTable tmp;
-    glbm_build_axis_table(N, &tmp, full);
-    const int Q1 = 2 * N + 1;
+    glbm_build_axis_table(NX, &tmp, full);
+    const int Q1 = 2 * NX + 1;
     for (int n = 0; n < Q1; ++n) {
         double elo = 0.0, ehi = 0.0;
         for (int j = Q1 - 1; j >= 0; --j) {
@@ -172,6 +172,7 @@ static void fill_inst(const glbm_ctx *c, const glbm_config &cfg, const Geo &g, I
     ip.g_theta_om_f = (float)ip.g_theta_om;
     ip.inv_den_f = (float)ip.inv_den;
     ip.N = N;
+    ip.NX = NX;
     ip.Lx = g.Lx;
     ip.Ly = g.Ly;
     ip.pitch = g.pitch;
@@ -186,6 +187,13 @@ static glbm_status validate(const glbm_config &c)
     if (c.k < 0 || c.k > GLBM_MAXN - 1)
         return fail(GLBM_E_UNSUPPORTED, "k must be in 0..%d (got %d)", GLBM_MAXN - 1, c.k);
     const int N = c.k + 1;
+    if (c.x_level < 0 || c.x_level > GLBM_MAXN)
+        return fail(GLBM_E_INVAL, "x_level must be in 0..%d (got %d)", GLBM_MAXN, c.x_level);
+    if (c.x_level != 0 && c.x_level != 1 && c.x_level != N)
+        return fail(GLBM_E_UNSUPPORTED,
+                    "anisotropic lattices take D1Q3 along x (x_level 1) or the level of k");
+    if (c.x_level != 0 && c.dims != 2) return fail(GLBM_E_INVAL, "x_level applies to 2D lattices");
+    const int NX = c.x_level > 0 ? c.x_level : N;
     if (c.nx < 1 || (c.dims == 2 && c.ny < 1)) return fail(GLBM_E_INVAL, "nx, ny must be >= 1");
     if (c.prec != GLBM_FP64 && c.prec != GLBM_FP32_DEV) return fail(GLBM_E_INVAL, "bad precision %d", c.prec);
     if (c.dims == 1) {
@@ -199,7 +207,7 @@ static glbm_status validate(const glbm_config &c)
         if (c.bc == GLBM_BC_WALLS && c.ny < N) return fail(GLBM_E_INVAL, "walls need ny >= k+1");
     }
     if (!(c.kn > 0.0) && !(c.tau > 0.0)) return fail(GLBM_E_INVAL, "tau must be > 0 (or kn > 0)");
-    const double umax = sqrt(2.0 / 3.0) * N;
+    const double umax = sqrt(2.0 / 3.0) * NX;  // the wall speeds are x velocities
     if (!(fabs(c.u_wall_lo) < umax) || !(fabs(c.u_wall_hi) < umax) || !isfinite(c.g))
         return fail(GLBM_E_INVAL, "wall speed outside the positivity domain or bad force");
     return GLBM_OK;
@@ -220,11 +228,12 @@ static Geo make_geo(const glbm_config &c)
 {
     Geo g;
     g.N = c.k + 1;
+    g.NX = c.dims == 2 && c.x_level > 0 ? c.x_level : g.N;
     g.Lx = c.nx;
     g.Ly = c.dims == 2 ? c.ny : 1;
     g.pitch = ((g.Lx + 31) / 32) * 32;
     const int Q1 = 2 * g.N + 1;
-    g.Q = c.dims == 2 ? Q1 * Q1 : Q1;
+    g.Q = c.dims == 2 ? Q1 * (2 * g.NX + 1) : Q1;
     g.plane = (long long)g.Ly * g.pitch;
     g.off = 0;
     return g;
@@ -258,6 +267,7 @@ static AuxArgs aux_args(const glbm_ctx *c, int inst)
     AuxArgs a;
     memset(&a, 0, sizeof(a));
     a.tab = c->tabs[g.N];
+    a.tabx = c->tabs[g.NX];
     a.ip = c->d_ip + inst;
     a.dims = c->dims;
     a.prec = c->prec;
@@ -266,6 +276,7 @@ static AuxArgs aux_args(const glbm_ctx *c, int inst)
     a.pitch = g.pitch;
     a.bc = c->cfg[inst].bc;
     a.N = g.N;
+    a.NX = g.NX;
     a.plane = g.plane;
     a.inst_stride = 0;
     return a;
@@ -377,7 +388,7 @@ extern "C" glbm_status glbm_create(const glbm_config *cfgs, int n, void *stream,
         if (st != GLBM_OK) return st;
         const glbm_config &a = cfgs[0], &b = cfgs[i];
         if (a.dims != b.dims || a.nx != b.nx || (a.dims == 2 && a.ny != b.ny) || a.k != b.k ||
-            a.bc != b.bc || a.prec != b.prec)
+            a.bc != b.bc || a.prec != b.prec || make_geo(a).NX != make_geo(b).NX)
             return fail(GLBM_E_UNSUPPORTED,
                         "instances differ in geometry; use glbm_batch_create for mixed batches");
     }
@@ -394,10 +405,19 @@ extern "C" glbm_status glbm_create(const glbm_config *cfgs, int n, void *stream,
 }
 
 // Shape of the tiles of level N in this context.
+// Whether the context steps an anisotropic product (D1Q3 along x).
+static bool is_x1(const glbm_ctx *c) { return c->dims == 2 && c->geo[0].NX != c->geo[0].N; }
+
+// Candidate tile shapes of level N for this context's lattices.
+static int ctx_tile_shapes(const glbm_ctx *c, int N, TileShape *out)
+{
+    return is_x1(c) ? glbm_tile_shapes_x1(N, c->prec, out) : glbm_tile_shapes(N, c->prec, out);
+}
+
 static TileShape tile_of(const glbm_ctx *c, int N)
 {
     TileShape sh[GLBM_MAX_TILES];
-    const int n = glbm_tile_shapes(N, c->prec, sh);
+    const int n = ctx_tile_shapes(c, N, sh);
     return n > 0 ? sh[c->tile[N] < n ? c->tile[N] : 0] : TileShape{1, 1, 1};
 }
 
@@ -438,6 +458,8 @@ extern "C" glbm_status glbm_batch_create(const glbm_config *cfgs, int n, void *s
         glbm_status st = validate(cfgs[i]);
         if (st != GLBM_OK) return st;
         if (cfgs[i].dims != 2) return fail(GLBM_E_UNSUPPORTED, "heterogeneous batches are 2D");
+        if (make_geo(cfgs[i]).NX != cfgs[i].k + 1)
+            return fail(GLBM_E_UNSUPPORTED, "heterogeneous batches take isotropic lattices");
         if (cfgs[i].prec != GLBM_FP32_DEV)
             return fail(GLBM_E_UNSUPPORTED,
                         "heterogeneous batches store FP32 deviations (FP64 instances go through "
@@ -572,6 +594,7 @@ static Step2DArgs step_args(const glbm_ctx *c, int from)
     Step2DArgs a;
     memset(&a, 0, sizeof(a));
     a.tab = c->tabs[g.N];
+    a.tabx = c->tabs[g.NX];
     a.fin = c->buf[from];
     a.fout = c->buf[1 - from];
     a.ip = c->d_ip;
@@ -617,6 +640,7 @@ static cudaError_t launch_one_2d(const glbm_ctx *c, int from, cudaStream_t s)
     if (c->hetero) return glbm_launch_batched_f32(batch_args(c, from), s);
     const Step2DArgs a = step_args(c, from);
     const int N = c->geo[0].N;
+    if (is_x1(c)) return glbm_launch_step2d_x1(N, c->prec, c->tile[N], a, c->n_inst, s);
     return c->prec == GLBM_FP64 ? glbm_launch_step2d_f64(N, c->tile[N], a, c->n_inst, s)
                                 : glbm_launch_step2d_f32(N, c->tile[N], a, c->n_inst, s);
 }
@@ -806,6 +830,8 @@ static void fill_header(const glbm_ctx *c, CkptHeader &h)
     for (const glbm_config &g : c->cfg) {
         const int geo[6] = {g.dims, g.nx, g.ny, g.k, g.bc, g.prec};
         crc = crc32_update(crc, (const unsigned char *)geo, sizeof(geo));
+        const int nx_level = make_geo(g).NX;  // anisotropic lattices add their x level
+        if (nx_level != g.k + 1) crc = crc32_update(crc, (const unsigned char *)&nx_level, sizeof(int));
     }
     h.config_crc = crc;
 }
@@ -869,6 +895,7 @@ static cudaError_t launch_2d_between(const glbm_ctx *c, const void *fin, void *f
     a.fin = fin;
     a.fout = fout;
     const int N = c->geo[0].N;
+    if (is_x1(c)) return glbm_launch_step2d_x1(N, c->prec, c->tile[N], a, c->n_inst, s);
     return c->prec == GLBM_FP64 ? glbm_launch_step2d_f64(N, c->tile[N], a, c->n_inst, s)
                                 : glbm_launch_step2d_f32(N, c->tile[N], a, c->n_inst, s);
 }
@@ -897,6 +924,7 @@ extern "C" glbm_status glbm_adjoint_flowrate(glbm_ctx *c, int64_t steps, int64_t
     if (!c || !J || !dJ_dtau || !dJ_dg) return fail(GLBM_E_INVAL, "null argument");
     if (c->dims != 2 || c->hetero)
         return fail(GLBM_E_UNSUPPORTED, "the adjoint takes 2D uniform contexts");
+    if (is_x1(c)) return fail(GLBM_E_UNSUPPORTED, "the adjoint takes isotropic lattices");
     if (steps < 1 || ckpt_every < 1) return fail(GLBM_E_INVAL, "steps and ckpt_every must be >= 1");
     const int64_t K = ckpt_every < steps ? ckpt_every : steps;
     const int64_t nseg = (steps + K - 1) / K;
@@ -1025,8 +1053,10 @@ static glbm_status tiles_changed(glbm_ctx *c)
 extern "C" glbm_status glbm_set_tiles(glbm_ctx *c, const int *tiles)
 {
     if (!c || !tiles) return fail(GLBM_E_INVAL, "null argument");
+    TileShape sh[GLBM_MAX_TILES];
     for (int k = 0; k < GLBM_LEVELS; ++k)
-        if (tiles[k] < -1 || tiles[k] >= glbm_tile_count(k, (glbm_prec)c->prec))
+        if (tiles[k] < -1 || tiles[k] >= (is_x1(c) ? glbm_tile_shapes_x1(k + 1, c->prec, sh)
+                                                    : glbm_tile_count(k, (glbm_prec)c->prec)))
             return fail(GLBM_E_INVAL, "tile index %d out of range for k=%d", tiles[k], k);
     for (int k = 0; k < GLBM_LEVELS; ++k)
         if (tiles[k] >= 0) c->tile[k + 1] = tiles[k];
@@ -1060,7 +1090,8 @@ extern "C" glbm_status glbm_autotune(glbm_ctx *c, int reps, double *us)
     glbm_status st = ce == cudaSuccess ? GLBM_OK : fail(GLBM_E_CUDA, "event: %s", cudaGetErrorString(ce));
     for (int N = 1; N <= GLBM_MAXN && st == GLBM_OK; ++N) {
         if (!level_present(c, N)) continue;
-        const int n = glbm_tile_count(N - 1, (glbm_prec)c->prec);
+        TileShape sh[GLBM_MAX_TILES];
+        const int n = ctx_tile_shapes(c, N, sh);
         int best = c->tile[N];
         float best_ms = 0.f;
         for (int idx = 0; idx < n && st == GLBM_OK; ++idx) {

@@ -34,12 +34,12 @@ __device__ __forceinline__ double load_full(const AuxArgs &a, const void *f, lon
     return (double)static_cast<const float *>(f)[idx];
 }
 
-// rest weight of flat velocity q
-__device__ __forceinline__ double rest_weight(const AxisTable &t, int dims, int q)
+// rest weight of flat velocity q (q = iy (2NX+1) + ix in 2D)
+__device__ __forceinline__ double rest_weight(const AuxArgs &a, int q)
 {
-    const int Q1 = 2 * t.N + 1;
-    if (dims == 1) return t.W[q];
-    return t.W[q / Q1] * t.W[q % Q1];
+    if (a.dims == 1) return a.tab.W[q];
+    const int Q1x = 2 * a.NX + 1;
+    return a.tab.W[q / Q1x] * a.tabx.W[q % Q1x];
 }
 
 __global__ void k_set_equilibrium(const __grid_constant__ AuxArgs a, void *f, int inst,
@@ -49,18 +49,21 @@ __global__ void k_set_equilibrium(const __grid_constant__ AuxArgs a, void *f, in
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y;
     if (x >= a.Lx) return;
-    const int N = a.N, Q1 = 2 * N + 1;
+    // 1D: the only axis is x, with table tab and level N
+    const int N = a.N, NX = a.dims == 2 ? a.NX : a.N;
+    const AxisTable &tx = a.dims == 2 ? a.tabx : a.tab;
+    const int Q1x = 2 * NX + 1;
     const long long node = (long long)y * a.Lx + x;
     const double r = rho[node], u = ux[node], v = a.dims == 2 ? uy[node] : 0.0;
     const long long base = (long long)inst * a.inst_stride + (long long)y * a.pitch + x;
-    const int Qy = a.dims == 2 ? Q1 : 1;
+    const int Qy = a.dims == 2 ? 2 * N + 1 : 1;
     for (int iy = 0; iy < Qy; ++iy) {
         const double wy = a.dims == 2 ? a.tab.W[iy] : 1.0;
         const double dy = a.dims == 2 ? eq_dev_rt(a.tab, v, iy - N) : 0.0;
-        for (int ix = 0; ix < Q1; ++ix) {
-            const double wx = a.tab.W[ix];
-            const double dx = eq_dev_rt(a.tab, u, ix - N);
-            const long long idx = base + (long long)(iy * Q1 + ix) * a.plane;
+        for (int ix = 0; ix < Q1x; ++ix) {
+            const double wx = tx.W[ix];
+            const double dx = eq_dev_rt(tx, u, ix - NX);
+            const long long idx = base + (long long)(iy * Q1x + ix) * a.plane;
             if (a.prec == GLBM_FP64) {
                 static_cast<double *>(f)[idx] = r * (wx + dx) * (wy + dy);
             } else {
@@ -85,7 +88,7 @@ __global__ void k_set_populations(const __grid_constant__ AuxArgs a, void *f, in
     if (a.prec == GLBM_FP64)
         static_cast<double *>(f)[idx] = v;
     else
-        static_cast<float *>(f)[idx] = (float)(v - rest_weight(a.tab, a.dims, q));
+        static_cast<float *>(f)[idx] = (float)(v - rest_weight(a, q));
 }
 
 __global__ void k_get_populations(const __grid_constant__ AuxArgs a, const void *f, int inst,
@@ -98,7 +101,7 @@ __global__ void k_get_populations(const __grid_constant__ AuxArgs a, const void 
     const long long idx =
         (long long)inst * a.inst_stride + (long long)q * a.plane + (long long)y * a.pitch + x;
     double v = load_full(a, f, idx, q);
-    if (a.prec != GLBM_FP64) v += rest_weight(a.tab, a.dims, q);
+    if (a.prec != GLBM_FP64) v += rest_weight(a, q);
     dst[((long long)q * a.Ly + y) * a.Lx + x] = v;
 }
 
@@ -126,7 +129,7 @@ __device__ double pulled(const AuxArgs &a, const InstParams &ip, const void *f, 
         if (a.prec != GLBM_FP64) v += a.tab.W[q];
         return v;
     }
-    const int nx = ix - N, ny = iy - N;
+    const int nx = ix - a.NX, ny = iy - N;
     const int xs = wrap_index(x - nx, a.Lx);
     int ys = y - ny;
     if (a.bc == GLBM_BC_WALLS) {
@@ -135,9 +138,9 @@ __device__ double pulled(const AuxArgs &a, const InstParams &ip, const void *f, 
     } else {
         ys = wrap_index(ys, a.Ly);
     }
-    const int q = iy * Q1 + ix;
+    const int q = iy * (2 * a.NX + 1) + ix;
     double v = load_full(a, f, ibase + (long long)q * a.plane + (long long)ys * a.pitch + xs, q);
-    if (a.prec != GLBM_FP64) v += a.tab.W[iy] * a.tab.W[ix];
+    if (a.prec != GLBM_FP64) v += a.tab.W[iy] * a.tabx.W[ix];
     return v;
 }
 
@@ -145,17 +148,17 @@ __device__ double pulled(const AuxArgs &a, const InstParams &ip, const void *f, 
 __device__ double wall_density(const AuxArgs &a, const InstParams &ip, const void *f,
                                long long ibase, int x, bool lower)
 {
-    const int N = a.N, Q1 = 2 * N + 1;
+    const int N = a.N, Q1x = 2 * a.NX + 1;
     double D = 0.0;
     for (int aa = 1; aa <= N; ++aa) {
         for (int k = 0; k < aa; ++k) {
             const int iy = lower ? N - aa : N + aa;
             const int row = lower ? k : a.Ly - 1 - k;
-            for (int ix = 0; ix < Q1; ++ix) {
-                const int xs = wrap_index(x - (ix - N), a.Lx);
-                const int q = iy * Q1 + ix;
+            for (int ix = 0; ix < Q1x; ++ix) {
+                const int xs = wrap_index(x - (ix - a.NX), a.Lx);
+                const int q = iy * Q1x + ix;
                 double v = load_full(a, f, ibase + (long long)q * a.plane + (long long)row * a.pitch + xs, q);
-                if (a.prec != GLBM_FP64) v += a.tab.W[iy] * a.tab.W[ix];
+                if (a.prec != GLBM_FP64) v += a.tab.W[iy] * a.tabx.W[ix];
                 D += v;
             }
         }
@@ -171,8 +174,9 @@ __global__ void k_moments(const __grid_constant__ AuxArgs a, const void *f, int 
     const int y = blockIdx.y;
     if (x >= a.Lx) return;
     const InstParams &ip = a.ip[inst];
-    const int N = a.N, Q1 = 2 * N + 1;
-    const int Qy = a.dims == 2 ? Q1 : 1;
+    const int N = a.N, NX = a.dims == 2 ? a.NX : a.N;
+    const int Q1x = 2 * NX + 1;
+    const int Qy = a.dims == 2 ? 2 * N + 1 : 1;
     const long long ibase = (long long)inst * a.inst_stride;
     double rw_lo = 0.0, rw_hi = 0.0;
     if (a.dims == 2 && a.bc == GLBM_BC_WALLS) {
@@ -181,18 +185,18 @@ __global__ void k_moments(const __grid_constant__ AuxArgs a, const void *f, int 
     }
     double rho = 0.0, jx = 0.0, jy = 0.0;
     for (int iy = 0; iy < Qy; ++iy)
-        for (int ix = 0; ix < Q1; ++ix) {
+        for (int ix = 0; ix < Q1x; ++ix) {
             const double v = pulled(a, ip, f, ibase, x, y, ix, iy, rw_lo, rw_hi);
             rho += v;
-            jx += (ix - N) * v;
+            jx += (ix - NX) * v;
             jy += (a.dims == 2 ? iy - N : 0) * v;
         }
     const double ux = jx / rho, uy = jy / rho;
     double e2 = 0.0, qx = 0.0, qy = 0.0, sxy = 0.0;
     for (int iy = 0; iy < Qy; ++iy)
-        for (int ix = 0; ix < Q1; ++ix) {
+        for (int ix = 0; ix < Q1x; ++ix) {
             const double v = pulled(a, ip, f, ibase, x, y, ix, iy, rw_lo, rw_hi);
-            const double dx = (ix - N) - ux;
+            const double dx = (ix - NX) - ux;
             const double dy = a.dims == 2 ? (iy - N) - uy : 0.0;
             const double d2 = dx * dx + dy * dy;
             e2 += d2 * v;
@@ -412,7 +416,7 @@ cudaError_t glbm_launch_set_populations(const AuxArgs &a, void *f, int inst, con
                                         cudaStream_t s)
 {
     const int Q1 = 2 * a.N + 1;
-    dim3 grid((a.Lx + 127) / 128, a.Ly, a.dims == 2 ? Q1 * Q1 : Q1);
+    dim3 grid((a.Lx + 127) / 128, a.Ly, a.dims == 2 ? Q1 * (2 * a.NX + 1) : Q1);
     k_set_populations<<<grid, 128, 0, s>>>(a, f, inst, src);
     return cudaGetLastError();
 }
@@ -421,7 +425,7 @@ cudaError_t glbm_launch_get_populations(const AuxArgs &a, const void *f, int ins
                                         cudaStream_t s)
 {
     const int Q1 = 2 * a.N + 1;
-    dim3 grid((a.Lx + 127) / 128, a.Ly, a.dims == 2 ? Q1 * Q1 : Q1);
+    dim3 grid((a.Lx + 127) / 128, a.Ly, a.dims == 2 ? Q1 * (2 * a.NX + 1) : Q1);
     k_get_populations<<<grid, 128, 0, s>>>(a, f, inst, dst);
     return cudaGetLastError();
 }

@@ -59,18 +59,19 @@ struct InstParams {
     float dw_lo_f[GLBM_MAXQ1];  // E^x_n(u_wall_lo) - W_n
     float dw_hi_f[GLBM_MAXQ1];  // E^x_n(u_wall_hi) - W_n
     // geometry of the instance (heterogeneous batches keep their own)
-    int N;            // level along both axes
+    int N;            // level along y (along both axes unless NX differs)
     int Lx, Ly;       // nodes
     int pitch;        // row pitch in elements (multiple of 32)
     int bc;           // GLBM_BC_*
-    int pad_i;
+    int NX;           // level along x
     long long off;    // element offset of this instance in the population buffers
     long long plane;  // elements per velocity plane (Ly * pitch)
 };
 
 // Arguments of one uniform (same geometry for every instance) 2D step.
 struct Step2DArgs {
-    AxisTable tab;
+    AxisTable tab;        // level along y (and x for isotropic lattices)
+    AxisTable tabx;       // level along x of anisotropic products (else unused)
     const void *fin;      // populations read (post-collision of the last step)
     void *fout;           // populations written
     const InstParams *ip; // n_inst entries
@@ -120,13 +121,19 @@ cudaError_t glbm_launch_step2d_f64(int N, int shape, const Step2DArgs &a, int n_
                                    cudaStream_t s);
 template <int N, typename T>
 cudaError_t glbm_step2d_level(int shape, const Step2DArgs &a, int n_inst, cudaStream_t s);
+// Anisotropic products with D1Q3 along x (level 1) and level N along y: the
+// step with tile shape `shape` of the list glbm_tile_shapes_x1 gives.
+cudaError_t glbm_launch_step2d_x1(int N, int prec, int shape, const Step2DArgs &a, int n_inst,
+                                  cudaStream_t s);
+int glbm_tile_shapes_x1(int N, int prec, TileShape *out);
 
 // Auxiliary kernels (glbm_aux.cu).
 struct AuxArgs {
-    AxisTable tab;
+    AxisTable tab;        // level N along y (the only axis in 1D)
+    AxisTable tabx;       // level NX along x (2D; equal to tab for isotropic lattices)
     const InstParams *ip;
     int dims, prec;       // prec: 0 = FP64, 1 = FP32 deviations
-    int Lx, Ly, pitch, bc, N;
+    int Lx, Ly, pitch, bc, N, NX;
     long long plane, inst_stride;
 };
 cudaError_t glbm_launch_set_equilibrium(const AuxArgs &a, void *f, int inst, const double *rho,

@@ -21,9 +21,10 @@
 #pragma once
 #include "glbm_device.cuh"
 
-template <int N, typename T, int G, int R>
+template <int N, typename T, int G, int R, int NXL = N>
 struct Step2D {
-    static constexpr int Q1 = 2 * N + 1;
+    static constexpr int Q1 = 2 * N + 1;          // velocity rows (level N along y)
+    static constexpr int QX = 2 * NXL + 1;        // velocity columns (level NXL along x)
     static constexpr int RPG = (Q1 + G - 1) / G;  // velocity rows per warp group
     static constexpr int NW = G * R;              // warps per CTA
     static constexpr int NT = 32 * NW;
@@ -37,13 +38,15 @@ struct Step2D {
         T rw[2][32];          // wall density (FP64) or its deviation (FP32): lo, hi
         T dsum[NV][2][32];    // partial wall fluxes of the NV accumulators
         // E^x - W and E^y - W of the tile's nodes, shared by the warp groups
-        T eqx[G > 1 ? R : 1][G > 1 ? Q1 : 1][32];
+        T eqx[G > 1 ? R : 1][G > 1 ? QX : 1][32];
         T eqy[G > 1 ? R : 1][G > 1 ? Q1 : 1][32];
     };
 
     // One tile: columns x0..x0+31, rows y0..y0+R-1 of one instance whose
-    // populations start at fin / fout. Every thread of the CTA calls it.
-    __device__ static void run(const AxisTable &tab, const InstParams &ip, int Lx, int Ly,
+    // populations start at fin / fout; tab is the y axis's table, tabx the x
+    // axis's (the same table for isotropic lattices). Every thread calls it.
+    __device__ static void run(const AxisTable &tab, const AxisTable &tabx, const InstParams &ip,
+                               int Lx, int Ly,
                                int pitch, int plane, int bc, const T *__restrict__ fin,
                                T *__restrict__ fout, int x0, int y0, Smem &sm, unsigned *status,
                                unsigned seed)
@@ -60,9 +63,10 @@ struct Step2D {
         const int yc = y < Ly ? y : Ly - 1;
 
         // offset of velocity column ix's plane plus its periodic source column
-        int cofs[Q1];
+        int cofs[QX];
 #pragma unroll
-        for (int ix = 0; ix < Q1; ++ix) cofs[ix] = ix * plane + wrap_shift(xc - (ix - N), Lx, Lx > N);
+        for (int ix = 0; ix < QX; ++ix)
+            cofs[ix] = ix * plane + wrap_shift(xc - (ix - NXL), Lx, Lx > NXL);
 
         // ---- phase 0: wall densities of this tile's columns ---------------
         const bool need_lo = walls && (y0 < N);
@@ -84,14 +88,14 @@ struct Step2D {
                         ++aa;
                     }
                     if (need_lo) {  // velocity ny = -aa leaving row k through y = -1/2
-                        const T *pl = fin + ((N - aa) * Q1 * plane + k * pitch);
+                        const T *pl = fin + ((N - aa) * QX * plane + k * pitch);
 #pragma unroll
-                        for (int ix = 0; ix < Q1; ++ix) slo += __ldg(pl + cofs[ix]);
+                        for (int ix = 0; ix < QX; ++ix) slo += __ldg(pl + cofs[ix]);
                     }
                     if (need_hi) {  // velocity ny = +aa leaving row Ly-1-k through y = Ly-1/2
-                        const T *ph = fin + ((N + aa) * Q1 * plane + (Ly - 1 - k) * pitch);
+                        const T *ph = fin + ((N + aa) * QX * plane + (Ly - 1 - k) * pitch);
 #pragma unroll
-                        for (int ix = 0; ix < Q1; ++ix) shi += __ldg(ph + cofs[ix]);
+                        for (int ix = 0; ix < QX; ++ix) shi += __ldg(ph + cofs[ix]);
                     }
                 }
                 sm.dsum[v][0][lane] = slo;
@@ -118,7 +122,7 @@ struct Step2D {
         // This warp's velocity rows are iy = g + k G (k = 0..RPG-1): the row is a
         // run-time value while the register array f[k][ix] keeps compile-time
         // indices, so all G warp groups share one copy of the unrolled code.
-        T f[RPG][Q1];
+        T f[RPG][QX];
         T s_r = T(0), c_r = T(0), s_x = T(0), c_x = T(0), s_y = T(0), c_y = T(0);
         // loads first, all independent
 #pragma unroll
@@ -128,9 +132,9 @@ struct Step2D {
                 const int ny = iy - N;
                 int ys = yc - ny;
                 ys = walls ? min(max(ys, 0), Ly - 1) : wrap_shift(ys, Ly, Ly > N);
-                const T *rowp = fin + (iy * Q1 * plane + ys * pitch);
+                const T *rowp = fin + (iy * QX * plane + ys * pitch);
 #pragma unroll
-                for (int ix = 0; ix < Q1; ++ix) f[k][ix] = __ldg(rowp + cofs[ix]);
+                for (int ix = 0; ix < QX; ++ix) f[k][ix] = __ldg(rowp + cofs[ix]);
             }
         }
         // wall re-emission and row sums
@@ -145,11 +149,11 @@ struct Step2D {
                     const T wy = A::W(tab, iy);
                     const T rw = sm.rw[lo ? 0 : 1][lane];
 #pragma unroll
-                    for (int ix = 0; ix < Q1; ++ix) {
+                    for (int ix = 0; ix < QX; ++ix) {
                         if (DEV) {
                             const T dw = lo ? (T)ip.dw_lo_f[ix] : (T)ip.dw_hi_f[ix];
                             // W^y (drho_w W^x + rho_w (E^x(u_w) - W^x))
-                            f[k][ix] = mul_rn(wy, fma(rw, A::W(tab, ix), (T(1) + rw) * dw));
+                            f[k][ix] = mul_rn(wy, fma(rw, A::W(tabx, ix), (T(1) + rw) * dw));
                         } else {
                             const T ew = lo ? (T)ip.ew_lo[ix] : (T)ip.ew_hi[ix];
                             f[k][ix] = mul_rn(rw * ew, wy);
@@ -158,10 +162,10 @@ struct Step2D {
                 }
                 T rs = T(0);
 #pragma unroll
-                for (int ix = 0; ix < Q1; ++ix) rs += f[k][ix];
+                for (int ix = 0; ix < QX; ++ix) rs += f[k][ix];
                 T jx = T(0);
 #pragma unroll
-                for (int n = 1; n <= N; ++n) jx = fma(T(n), f[k][N + n] - f[k][N - n], jx);
+                for (int n = 1; n <= NXL; ++n) jx = fma(T(n), f[k][NXL + n] - f[k][NXL - n], jx);
                 acc2(s_r, c_r, rs);
                 acc2(s_x, c_x, jx);
                 if (ny != 0) acc2(s_y, c_y, mul_rn(T(ny), rs));
@@ -195,14 +199,15 @@ struct Step2D {
         const T ux = (S_x + C_x) * inv_rho;
         const T uy = (S_y + C_y) * inv_rho;
         if (active) {
-            const T umax = (T)(0.816496580927726 * N);  // sqrt(2/3) N: positivity bound (Sec. 3)
-            if (!(rho > T(0)) || !(fabs(ux) <= umax) || !(fabs(uy) <= umax)) atomicOr(status, 1u);
+            // sqrt(2/3) N per axis: positivity bound (Sec. 3)
+            const T umax = (T)(0.816496580927726 * N), umaxx = (T)(0.816496580927726 * NXL);
+            if (!(rho > T(0)) || !(fabs(ux) <= umaxx) || !(fabs(uy) <= umax)) atomicOr(status, 1u);
         }
 
-        T dx[Q1];
+        T dx[QX];
         T dyall[G == 1 ? Q1 : 1];  // one warp group: E^y - W for every row at once
         if constexpr (G == 1) {
-            eq_dev_all<N, T>(tab, ux, dx);
+            eq_dev_all<NXL, T>(tabx, ux, dx);
             eq_dev_all<N, T>(tab, uy, dyall);
         } else {
             // the G warp groups of a node row share the polynomial work: group g
@@ -210,25 +215,29 @@ struct Step2D {
             // values meet in shared memory
             const T vx = ux * ux, vy = uy * uy;
 #pragma unroll
-            for (int n = 0; n <= N; ++n) {
+            for (int n = 0; n <= (N > NXL ? N : NXL); ++n) {
                 if (n % G != g) continue;
                 T ae, bo;
-                eq_parts<N, T>(tab, n, vx, ae, bo);
-                sm.eqx[r][N + n][lane] = n == 0 ? ae : fma(ux, bo, ae);
-                if (n != 0) sm.eqx[r][N - n][lane] = fma(-ux, bo, ae);
-                eq_parts<N, T>(tab, n, vy, ae, bo);
-                sm.eqy[r][N + n][lane] = n == 0 ? ae : fma(uy, bo, ae);
-                if (n != 0) sm.eqy[r][N - n][lane] = fma(-uy, bo, ae);
+                if (n <= NXL) {
+                    eq_parts<NXL, T>(tabx, n, vx, ae, bo);
+                    sm.eqx[r][NXL + n][lane] = n == 0 ? ae : fma(ux, bo, ae);
+                    if (n != 0) sm.eqx[r][NXL - n][lane] = fma(-ux, bo, ae);
+                }
+                if (n <= N) {
+                    eq_parts<N, T>(tab, n, vy, ae, bo);
+                    sm.eqy[r][N + n][lane] = n == 0 ? ae : fma(uy, bo, ae);
+                    if (n != 0) sm.eqy[r][N - n][lane] = fma(-uy, bo, ae);
+                }
             }
             __syncthreads();
             if constexpr (!DX_SHARED) {
 #pragma unroll
-                for (int ix = 0; ix < Q1; ++ix) dx[ix] = sm.eqx[r][ix][lane];
+                for (int ix = 0; ix < QX; ++ix) dx[ix] = sm.eqx[r][ix][lane];
             }
         }
-        T ex[Q1];  // FP64 mode: E^x = W + d^x
+        T ex[QX];  // FP64 mode: E^x = W + d^x
 #pragma unroll
-        for (int ix = 0; ix < Q1; ++ix) ex[ix] = DEV ? T(0) : A::W(tab, ix) + dx[ix];
+        for (int ix = 0; ix < QX; ++ix) ex[ix] = DEV ? T(0) : A::W(tabx, ix) + dx[ix];
         const T om = DEV ? (T)ip.omega_f : (T)ip.omega;
         const T gto = DEV ? (T)ip.g_theta_om_f : (T)ip.g_theta_om;  // g / (theta omega)
         T *const obase = fout + (y * pitch + x);
@@ -254,26 +263,26 @@ struct Step2D {
                 const T gr = mul_rn(gto, wy);
                 // FP32: delta f^eq = d^x rho e^y + W^x (drho W^y + rho d^y)
                 const T B = DEV ? fma(drho, wy, rho * dy) : T(0);
-                T *const op = obase + iy * Q1 * plane;
+                T *const op = obase + iy * QX * plane;
                 // random word of this row: node word plus a multiple of the row
                 const unsigned hrow = hnode + (unsigned)iy * 0x85EBCA6Bu;
 #pragma unroll
-                for (int ix = 0; ix < Q1; ++ix) {
-                    const int nx = ix - N;
+                for (int ix = 0; ix < QX; ++ix) {
+                    const int nx = ix - NXL;
                     const T f0 = f[k][ix];
                     T v;
                     if (DEV) {
                         const T Bn = nx != 0 ? fma(T(nx), gr, B) : B;
                         // split FP32 tiles read E^x - W where it is used (fewer registers)
                         const T dxv = DX_SHARED ? sm.eqx[r][ix][lane] : dx[ix];
-                        const T eq = fma(dxv, rey, A::W(tab, ix) * Bn);
+                        const T eq = fma(dxv, rey, A::W(tabx, ix) * Bn);
                         // increment plus dither, then one rounding of the store
                         const unsigned rnd = hrow * (0x9E3779B9u * (2u * ix + 1u)) + 0x7F4A7C15u * ix;
                         const T inc = fma(om, eq - f0, (T)dither_ulp((float)f0, rnd));
                         v = f0 + inc;
                     } else {
                         T eq = ex[ix] * rey;
-                        if (nx != 0) eq = fma(A::WN(tab, ix), gr, eq);
+                        if (nx != 0) eq = fma(A::WN(tabx, ix), gr, eq);
                         v = fma(om, eq - f0, f0);
                     }
                     if (active) op[ix * plane] = v;
@@ -297,18 +306,18 @@ __device__ __forceinline__ void advance_launch_counter(unsigned *step_ctr, unsig
     }
 }
 
-template <int N, typename T, int G, int R>
+template <int N, typename T, int G, int R, int NXL = N>
 __global__ void __launch_bounds__(32 * G * R)
     k_step2d(const __grid_constant__ Step2DArgs a)
 {
-    using S = Step2D<N, T, G, R>;
+    using S = Step2D<N, T, G, R, NXL>;
     __shared__ typename S::Smem sm;
     const int inst = blockIdx.z;
     const T *fin = static_cast<const T *>(a.fin) + (long long)inst * a.inst_stride;
     T *fout = static_cast<T *>(a.fout) + (long long)inst * a.inst_stride;
     // launch counter (read before any CTA of this launch can advance it)
     const unsigned seed = S::DEV ? hash32(__ldcg(a.step_ctr) * 0x632BE5ABu + inst) : 0u;
-    S::run(a.tab, a.ip[inst], a.Lx, a.Ly, a.pitch, (int)a.plane, a.bc, fin, fout, blockIdx.x * 32,
-           blockIdx.y * R, sm, a.status, seed);
+    S::run(a.tab, NXL == N ? a.tab : a.tabx, a.ip[inst], a.Lx, a.Ly, a.pitch, (int)a.plane, a.bc,
+           fin, fout, blockIdx.x * 32, blockIdx.y * R, sm, a.status, seed);
     if (S::DEV) advance_launch_counter(a.step_ctr, a.done_ctr);
 }

@@ -1,0 +1,100 @@
+// Anisotropic tensor products (Sec. 4 builds a 2D lattice as the product of any
+// two 1D levels): D1Q3 along x (level 1) times the level-N Gaussian lattice
+// along y, the form the paper uses for its channel flows. One-node tiles,
+// both precisions; the candidate shapes of each level follow.
+#include "glbm_step2d.cuh"
+
+template <int N, typename T>
+struct TilesX1;
+
+#define GLBM_TILES_X1(N_, T_, ...)                                     \
+    template <>                                                        \
+    struct TilesX1<N_, T_> {                                           \
+        static constexpr TileShape shape[] = {__VA_ARGS__};            \
+        static constexpr int count = sizeof(shape) / sizeof(shape[0]); \
+    };
+// {G, R, V}: 3 (2N+1) populations per node, a few rows per CTA
+GLBM_TILES_X1(1, float, {1, 8, 1}, {1, 4, 1}, {1, 16, 1})
+GLBM_TILES_X1(2, float, {1, 8, 1}, {1, 4, 1}, {1, 16, 1})
+GLBM_TILES_X1(3, float, {1, 8, 1}, {1, 4, 1}, {1, 16, 1})
+GLBM_TILES_X1(4, float, {1, 8, 1}, {1, 4, 1}, {1, 2, 1})
+GLBM_TILES_X1(5, float, {1, 4, 1}, {1, 8, 1}, {1, 2, 1})
+GLBM_TILES_X1(6, float, {1, 4, 1}, {1, 8, 1}, {1, 2, 1})
+GLBM_TILES_X1(7, float, {1, 4, 1}, {1, 2, 1}, {2, 4, 1})
+GLBM_TILES_X1(8, float, {1, 4, 1}, {1, 2, 1}, {2, 4, 1})
+GLBM_TILES_X1(1, double, {1, 8, 1}, {1, 4, 1})
+GLBM_TILES_X1(2, double, {1, 8, 1}, {1, 4, 1})
+GLBM_TILES_X1(3, double, {1, 4, 1}, {1, 8, 1})
+GLBM_TILES_X1(4, double, {1, 4, 1}, {1, 2, 1})
+GLBM_TILES_X1(5, double, {1, 4, 1}, {1, 2, 1})
+GLBM_TILES_X1(6, double, {1, 4, 1}, {2, 2, 1})
+GLBM_TILES_X1(7, double, {1, 4, 1}, {2, 2, 1})
+GLBM_TILES_X1(8, double, {1, 2, 1}, {2, 2, 1})
+#undef GLBM_TILES_X1
+
+template <int N, typename T, int I = 0>
+static cudaError_t launch_x1_shape(int shape, const Step2DArgs &a, int n_inst, cudaStream_t s)
+{
+    if constexpr (I < TilesX1<N, T>::count) {
+        if (shape == I) {
+            constexpr TileShape t = TilesX1<N, T>::shape[I];
+            const dim3 grid((a.Lx + 31) / 32, (a.Ly + t.R - 1) / t.R, n_inst);
+            k_step2d<N, T, t.G, t.R, 1><<<grid, 32 * t.G * t.R, 0, s>>>(a);
+            return cudaGetLastError();
+        }
+        return launch_x1_shape<N, T, I + 1>(shape, a, n_inst, s);
+    } else {
+        return cudaErrorInvalidValue;
+    }
+}
+
+template <typename T>
+static cudaError_t launch_x1(int N, int shape, const Step2DArgs &a, int n_inst, cudaStream_t s)
+{
+    switch (N) {
+    case 1: return launch_x1_shape<1, T>(shape, a, n_inst, s);
+    case 2: return launch_x1_shape<2, T>(shape, a, n_inst, s);
+    case 3: return launch_x1_shape<3, T>(shape, a, n_inst, s);
+    case 4: return launch_x1_shape<4, T>(shape, a, n_inst, s);
+    case 5: return launch_x1_shape<5, T>(shape, a, n_inst, s);
+    case 6: return launch_x1_shape<6, T>(shape, a, n_inst, s);
+    case 7: return launch_x1_shape<7, T>(shape, a, n_inst, s);
+    case 8: return launch_x1_shape<8, T>(shape, a, n_inst, s);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t glbm_launch_step2d_x1(int N, int prec, int shape, const Step2DArgs &a, int n_inst,
+                                  cudaStream_t s)
+{
+    return prec == GLBM_FP64 ? launch_x1<double>(N, shape, a, n_inst, s)
+                             : launch_x1<float>(N, shape, a, n_inst, s);
+}
+
+template <int N, typename T>
+static int copy_x1(TileShape *out)
+{
+    for (int i = 0; i < TilesX1<N, T>::count; ++i) out[i] = TilesX1<N, T>::shape[i];
+    return TilesX1<N, T>::count;
+}
+
+template <typename T>
+static int shapes_x1(int N, TileShape *out)
+{
+    switch (N) {
+    case 1: return copy_x1<1, T>(out);
+    case 2: return copy_x1<2, T>(out);
+    case 3: return copy_x1<3, T>(out);
+    case 4: return copy_x1<4, T>(out);
+    case 5: return copy_x1<5, T>(out);
+    case 6: return copy_x1<6, T>(out);
+    case 7: return copy_x1<7, T>(out);
+    case 8: return copy_x1<8, T>(out);
+    default: return 0;
+    }
+}
+
+int glbm_tile_shapes_x1(int N, int prec, TileShape *out)
+{
+    return prec == GLBM_FP64 ? shapes_x1<double>(N, out) : shapes_x1<float>(N, out);
+}

@@ -37,7 +37,8 @@ class UnstableError(GlbmError):
 
 class Config(ctypes.Structure):
     _fields_ = [("dims", ctypes.c_int), ("nx", ctypes.c_int), ("ny", ctypes.c_int),
-                ("k", ctypes.c_int), ("tau", ctypes.c_double), ("kn", ctypes.c_double),
+                ("k", ctypes.c_int), ("x_level", ctypes.c_int), ("tau", ctypes.c_double),
+                ("kn", ctypes.c_double),
                 ("bc", ctypes.c_int), ("prec", ctypes.c_int), ("u_wall_lo", ctypes.c_double),
                 ("u_wall_hi", ctypes.c_double), ("g", ctypes.c_double)]
 
@@ -127,10 +128,13 @@ def eq_table(k: int) -> np.ndarray:
 
 
 def make_config(dims=2, nx=1, ny=1, k=0, tau=0.0, kn=0.0, bc=None, prec=FP64, u_wall_lo=0.0,
-                u_wall_hi=0.0, g=0.0) -> Config:
+                u_wall_hi=0.0, g=0.0, x_level=0) -> Config:
+    """One instance; x_level=1 makes the anisotropic product D1Q3 (x) times the
+    level-(k+1) lattice (y); 0 keeps level k+1 on both axes."""
     if bc is None:
         bc = BC_WALLS if dims == 2 else BC_BOUNCEBACK
-    return Config(dims, nx, ny if dims == 2 else 1, k, tau, kn, bc, prec, u_wall_lo, u_wall_hi, g)
+    return Config(dims, nx, ny if dims == 2 else 1, k, x_level, tau, kn, bc, prec, u_wall_lo,
+                  u_wall_hi, g)
 
 
 _torch_alloc_refs = None
@@ -222,7 +226,8 @@ class Lattice:
     def nq(self, inst=0):
         c = self.configs[inst]
         q1 = 2 * c.k + 3
-        return q1 * q1 if c.dims == 2 else q1
+        q1x = 2 * c.x_level + 1 if c.x_level > 0 else q1
+        return q1 * q1x if c.dims == 2 else q1
 
     def shape(self, inst=0):
         c = self.configs[inst]

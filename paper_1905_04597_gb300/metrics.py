@@ -14,16 +14,18 @@ FIELDS_2D = ("rho", "ux", "uy", "T", "qx", "qy", "sxy")
 FIELDS_1D = ("rho", "ux", "T", "qx")
 
 
-def term_scales(F, want, dims=2):
+def term_scales(F, want, dims=2, q1x=None):
     """Largest per-node sum of absolute terms of each moment of populations F
     (velocity-major array [Q, ny, nx] in 2D, [Q, nx] in 1D); want holds the
-    moments in the order of FIELDS_2D / FIELDS_1D."""
+    moments in the order of FIELDS_2D / FIELDS_1D. q1x is the number of x
+    velocities of an anisotropic product (default: the square lattice)."""
     Q = F.shape[0]
     if dims == 2:
-        Q1 = int(round(np.sqrt(Q)))
-        N = (Q1 - 1) // 2
-        cx = np.tile(np.arange(-N, N + 1), Q1).astype(float)[:, None, None]
-        cy = np.repeat(np.arange(-N, N + 1), Q1).astype(float)[:, None, None]
+        Q1x = q1x or int(round(np.sqrt(Q)))
+        Q1y = Q // Q1x
+        NX, NY = (Q1x - 1) // 2, (Q1y - 1) // 2
+        cx = np.tile(np.arange(-NX, NX + 1), Q1y).astype(float)[:, None, None]
+        cy = np.repeat(np.arange(-NY, NY + 1), Q1x).astype(float)[:, None, None]
         rho, ux, uy = want[0], want[1], want[2]
         dx, dy = cx - ux, cy - uy
         d2 = dx * dx + dy * dy
@@ -39,14 +41,14 @@ def term_scales(F, want, dims=2):
             "T": (d * d * F).sum(0).max() / rho.min(), "qx": 0.5 * (np.abs(d) ** 3 * F).sum(0).max()}
 
 
-def rel_errors(got, want, dims=2, F=None):
+def rel_errors(got, want, dims=2, F=None, q1x=None):
     """Per-field max |got - want| / max(max |want|, 1e-3 S); got maps field names
     to arrays, want is the stacked reference moments. F (populations of the
-    reference) gives the term scales S."""
+    reference) gives the term scales S; q1x as in term_scales."""
     names = FIELDS_2D if dims == 2 else FIELDS_1D
     w = {n: want[i] for i, n in enumerate(names)}
     groups = {"ux": ("ux", "uy"), "uy": ("ux", "uy"), "qx": ("qx", "qy"), "qy": ("qx", "qy")}
-    S = term_scales(F, want, dims) if F is not None else {}
+    S = term_scales(F, want, dims, q1x) if F is not None else {}
     out = {}
     for n in names:
         scale = max(np.abs(w[m]).max() for m in groups.get(n, (n,)) if m in w)

@@ -72,6 +72,30 @@ def test_invalid_config_is_rejected_before_any_device_call():
     assert glbm.lib().glbm_create(ctypes.byref(cfg), 1, None, ctypes.byref(h)) == glbm.E_INVAL
 
 
+def test_anisotropic_configs_are_checked_before_any_device_call():
+    """x_level: 0 or the level of k (isotropic) or 1 (D1Q3 along x); not in 1D,
+    not in heterogeneous batches; the wall speeds are bounded by the x level."""
+    h = ctypes.c_void_p()
+    create = glbm.lib().glbm_create
+    cfg = glbm.make_config(dims=2, nx=8, ny=8, k=5, tau=1.0, x_level=3)
+    assert create(ctypes.byref(cfg), 1, None, ctypes.byref(h)) == glbm.E_UNSUPPORTED
+    cfg = glbm.make_config(dims=2, nx=8, ny=8, k=5, tau=1.0, x_level=9)
+    assert create(ctypes.byref(cfg), 1, None, ctypes.byref(h)) == glbm.E_INVAL
+    cfg = glbm.make_config(dims=1, nx=8, k=2, tau=1.0, x_level=1)
+    assert create(ctypes.byref(cfg), 1, None, ctypes.byref(h)) == glbm.E_INVAL
+    # |u_w| < sqrt(2/3) along the D1Q3 axis even at a high y level
+    cfg = glbm.make_config(dims=2, nx=8, ny=8, k=5, tau=1.0, x_level=1, u_wall_hi=0.9)
+    assert create(ctypes.byref(cfg), 1, None, ctypes.byref(h)) == glbm.E_INVAL
+    cfg = glbm.make_config(dims=2, nx=8, ny=8, k=5, tau=1.0, x_level=1, prec=glbm.FP32_DEV)
+    st = glbm.lib().glbm_batch_create(ctypes.byref(cfg), 1, None, ctypes.byref(h))
+    assert st == glbm.E_UNSUPPORTED and not h.value
+    assert b"isotropic" in glbm.lib().glbm_last_error()
+    # a context mixing isotropic and anisotropic instances is not uniform
+    two = (glbm.Config * 2)(glbm.make_config(dims=2, nx=8, ny=8, k=5, tau=1.0),
+                            glbm.make_config(dims=2, nx=8, ny=8, k=5, tau=1.0, x_level=1))
+    assert create(two, 2, None, ctypes.byref(h)) == glbm.E_UNSUPPORTED
+
+
 def test_tile_shape_candidates():
     """Every level has 1..MAX_TILES candidate shapes in each precision, each
     with 1 <= G <= 2k+3 warp groups, at most 512 threads per CTA and one or
