@@ -42,6 +42,11 @@ def workload(name):
         cfgs = [dict(dims=2, nx=c["nx"], ny=c["ny"], k=c["k"], kn=kn, u_wall_lo=c["u_wall_lo"],
                      u_wall_hi=c["u_wall_hi"]) for kn in c["kn"]]
         label = "couette_d2q81_512x256_kn{0.01,0.1,1}"
+    elif name == "couette_aniso":
+        c = inputs.COUETTE_ANISO
+        cfgs = [dict(dims=2, nx=c["nx"], ny=c["ny"], k=c["k"], x_level=c["x_level"], kn=kn,
+                     u_wall_lo=c["u_wall_lo"], u_wall_hi=c["u_wall_hi"]) for kn in c["kn"]]
+        label = "couette_d1q3xd1q17_1024x200_kn{0.01,0.1,1}"
     elif name == "poiseuille":
         c = inputs.POISEUILLE
         cfgs = [dict(dims=2, nx=c["nx"], ny=c["ny"], k=c["k"], kn=kn, g=c["g"]) for kn in c["kn"]]
@@ -233,7 +238,8 @@ def run_ours(args):
     cfgs, label = workload(args.workload)
     dims = cfgs[0]["dims"]
     N = cfgs[0]["k"] + 1
-    Q = (2 * N + 1) ** dims
+    NX = cfgs[0].get("x_level") or N
+    Q = (2 * N + 1) * (2 * NX + 1) if dims == 2 else 2 * N + 1
     nodes = cfgs[0]["nx"] * (cfgs[0]["ny"] if dims == 2 else 1)
     n_inst = len(cfgs)
     pops_per_step = Q * nodes * n_inst
@@ -242,11 +248,11 @@ def run_ours(args):
     tiles_used = {}
 
     def kernel_name(prec, lat):
-        k = N - 1
-        G, R, V = glbm.tile_shapes(k, prec)[lat.tiles()[k]]
+        G, R, V = lat.tile_shape(N - 1)
         if V == 2:
             return f"k_step2d_pair<{N},{G},{R}>"
-        return f"k_step2d<{N},{'float' if prec == glbm.FP32_DEV else 'double'},{G},{R}>"
+        t = "float" if prec == glbm.FP32_DEV else "double"
+        return f"k_step2d<{N},{t},{G},{R}{',1' if NX != N else ''}>"
 
     def timed(prec, steps, warmup):
         lat = glbm.Lattice([dict(c, prec=prec) for c in cfgs])
@@ -394,8 +400,11 @@ def precision_check(cfg, steps):
     dims = cfg["dims"]
     names = metrics.FIELDS_2D if dims == 2 else metrics.FIELDS_1D
     want = np.stack([runs[glbm.FP64][0][n] for n in names])
-    errs = metrics.rel_errors(runs[glbm.FP32_DEV][0], want, dims=dims, F=runs[glbm.FP64][1])
-    return {"steps": steps, "instance": {k: cfg[k] for k in ("k", "nx", "ny", "kn") if k in cfg},
+    q1x = 2 * cfg["x_level"] + 1 if cfg.get("x_level") else None
+    errs = metrics.rel_errors(runs[glbm.FP32_DEV][0], want, dims=dims, F=runs[glbm.FP64][1],
+                              q1x=q1x)
+    return {"steps": steps,
+            "instance": {k: cfg[k] for k in ("k", "x_level", "nx", "ny", "kn") if k in cfg},
             "fp32_vs_fp64_max_rel_err": errs, "max": max(errs.values())}
 
 
@@ -460,12 +469,13 @@ def cpu_baseline(name, budget_s=15.0, steps=None):
     N = c["k"] + 1
     dims = c["dims"]
     if dims == 2:
-        o = orc.Lattice(2, N, N, c["nx"], c["ny"], orc.BC_WALLS if name != "periodic" else 2,
+        NX = c.get("x_level") or N
+        o = orc.Lattice(2, NX, N, c["nx"], c["ny"], orc.BC_WALLS if name != "periodic" else 2,
                         orc.tau_from_kn(N, c["ny"], c["kn"]), c.get("u_wall_lo", 0.0),
                         c.get("u_wall_hi", 0.0), c.get("g", 0.0))
         X = o.equilibrium(np.ones((c["ny"], c["nx"])), np.zeros((c["ny"], c["nx"])),
                           np.zeros((c["ny"], c["nx"])))
-        pops = (2 * N + 1) ** 2 * c["nx"] * c["ny"]
+        pops = (2 * N + 1) * (2 * NX + 1) * c["nx"] * c["ny"]
     else:
         o = orc.Lattice(1, N, 0, c["nx"], 1, orc.BC_BOUNCEBACK, orc.tau_from_kn(N, c["nx"], c["kn"]))
         X = o.equilibrium(np.ones(c["nx"]), np.zeros(c["nx"]))
@@ -498,7 +508,8 @@ def run_reference(args):
     total_steps = args.steps + args.warmup
     if dims == 2:
         ny = c["ny"]
-        mk = lambda nx: orc.Lattice(2, N, N, nx, ny, orc.BC_WALLS,  # noqa: E731
+        NX = c.get("x_level") or N
+        mk = lambda nx: orc.Lattice(2, NX, N, nx, ny, orc.BC_WALLS,  # noqa: E731
                                     orc.tau_from_kn(N, ny, c["kn"]), c.get("u_wall_lo", 0.0),
                                     c.get("u_wall_hi", 0.0), c.get("g", 0.0))
         o = mk(1)
@@ -509,7 +520,7 @@ def run_reference(args):
         cols = int(max(1, min(c["nx"], budget / total_steps / max(per_col, 1e-9))))
         o = mk(cols)
         X = o.equilibrium(np.ones((ny, cols)), np.zeros((ny, cols)), np.zeros((ny, cols)))
-        pops = (2 * N + 1) ** 2 * ny * cols
+        pops = (2 * N + 1) * (2 * NX + 1) * ny * cols
         sample = f"{label}: strip of {cols} of {c['nx']} columns x {ny} rows, one instance, FP64"
     else:
         o = orc.Lattice(1, N, 0, c["nx"], 1, orc.BC_BOUNCEBACK, orc.tau_from_kn(N, c["nx"], c["kn"]))
@@ -540,7 +551,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=200)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="couette",
-                    choices=["couette", "poiseuille", "sod", "batched"])
+                    choices=["couette", "couette_aniso", "poiseuille", "sod", "batched"])
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")

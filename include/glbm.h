@@ -228,7 +228,9 @@ glbm_status glbm_adjoint_flowrate(glbm_ctx *ctx, int64_t steps, int64_t ckpt_eve
  * GLBM_MAX_TILES candidate shapes; entry 0 is the default of a new context.
  *
  * glbm_tile_count returns the number of candidates of level k in precision
- * prec (0 for an invalid pair); glbm_tile_shape returns candidate idx.
+ * prec (0 for an invalid pair); glbm_tile_shape returns candidate idx. Both
+ * describe isotropic lattices; anisotropic contexts (x_level 1) have their own
+ * lists, which glbm_autotune, glbm_set_tiles and glbm_get_tile_shape use.
  * glbm_get_tiles writes the index in use for every level (array of
  * GLBM_LEVELS ints, entry k for level k); glbm_set_tiles sets them (-1 keeps
  * a level's index; GLBM_E_INVAL and no change if an index is out of range).
@@ -248,6 +250,9 @@ glbm_status glbm_adjoint_flowrate(glbm_ctx *ctx, int64_t steps, int64_t ckpt_eve
 int glbm_tile_count(int k, glbm_prec prec);
 glbm_status glbm_tile_shape(int k, glbm_prec prec, int idx, int *G, int *R, int *V);
 glbm_status glbm_get_tiles(const glbm_ctx *ctx, int *tiles);
+/* The (G, R, V) shape the context uses for level k (for an anisotropic
+ * context, from its own candidate list). */
+glbm_status glbm_get_tile_shape(const glbm_ctx *ctx, int k, int *G, int *R, int *V);
 glbm_status glbm_set_tiles(glbm_ctx *ctx, const int *tiles);
 glbm_status glbm_autotune(glbm_ctx *ctx, int reps, double *us);
 

@@ -1039,6 +1039,17 @@ extern "C" glbm_status glbm_get_tiles(const glbm_ctx *c, int *tiles)
     return GLBM_OK;
 }
 
+extern "C" glbm_status glbm_get_tile_shape(const glbm_ctx *c, int k, int *G, int *R, int *V)
+{
+    if (!c || !G || !R || !V) return fail(GLBM_E_INVAL, "null argument");
+    if (k < 0 || k >= GLBM_LEVELS) return fail(GLBM_E_INVAL, "no level k=%d", k);
+    const TileShape t = tile_of(c, k + 1);
+    *G = t.G;
+    *R = t.R;
+    *V = t.V;
+    return GLBM_OK;
+}
+
 // Graphs and (in batches) the work list follow the tile shapes.
 static glbm_status tiles_changed(glbm_ctx *c)
 {

@@ -83,6 +83,7 @@ def lib():
         "glbm_tile_shape": ([i, i, i, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i)], i),
         "glbm_get_tiles": ([vp, ctypes.POINTER(i)], i),
         "glbm_set_tiles": ([vp, ctypes.POINTER(i)], i),
+        "glbm_get_tile_shape": ([vp, i] + [ctypes.POINTER(i)] * 3, i),
         "glbm_autotune": ([vp, i, dp], i),
         "glbm_last_error": ([], ctypes.c_char_p),
     }
@@ -298,6 +299,12 @@ class Lattice:
         t = (ctypes.c_int * LEVELS)()
         check(lib().glbm_get_tiles(self.h, t))
         return list(t)
+
+    def tile_shape(self, k):
+        """(G, R, V) of the tile this context uses for level k."""
+        v = [ctypes.c_int() for _ in range(3)]
+        check(lib().glbm_get_tile_shape(self.h, int(k), *[ctypes.byref(x) for x in v]))
+        return tuple(x.value for x in v)
 
     def set_tiles(self, tiles):
         """Set the tile shape index per level (-1 keeps a level's index)."""

@@ -68,6 +68,12 @@ def sod_density(nx: int = 1000, left: float = 1.0, right: float = 0.125) -> np.n
     return rho
 
 
+# Couette channel on the anisotropic product D1Q3 (x) x D1Q17 (y), the form of
+# the paper's channel models (Sec. 5.3) at its Ny = 200
+COUETTE_ANISO = dict(nx=1024, ny=200, k=7, x_level=1, kn=(0.01, 0.1, 1.0), u_wall_lo=-0.05,
+                     u_wall_hi=0.05)
+
+
 def batched_instances(seed: int = 0, n: int = 256, nx: int = 64):
     """Per-instance recipe of the batched channel workload, drawn in a fixed order."""
     rng = np.random.default_rng(seed)

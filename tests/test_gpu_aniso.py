@@ -85,6 +85,8 @@ def test_every_tile_shape_one_step(prec):
         base = glbm.Lattice(_cfg(k, nx, ny, prec, tau=0.9, u_wall_lo=0.03, u_wall_hi=-0.02, g=1e-4))
         times = base.autotune(reps=2)
         assert set(times) == {k} and len(times[k]) >= 2
+        G, R, V = base.tile_shape(k)
+        assert G >= 1 and R >= 1 and V == 1
         n_shapes = len(times[k])
         base.close()
         for idx in range(n_shapes):
