@@ -250,7 +250,7 @@ def run_ours(args):
     def kernel_name(prec, lat):
         G, R, V = lat.tile_shape(N - 1)
         if V == 2:
-            return f"k_step2d_pair<{N},{G},{R}>"
+            return f"k_step2d_pair<{N},{G},{R}{',1' if NX != N else ''}>"
         t = "float" if prec == glbm.FP32_DEV else "double"
         return f"k_step2d<{N},{t},{G},{R}{',1' if NX != N else ''}>"
 

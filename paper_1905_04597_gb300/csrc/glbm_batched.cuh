@@ -36,8 +36,8 @@ __global__ void __launch_bounds__(32 * G * R)
     const float *fin = static_cast<const float *>(a.fin) + ip.off;
     float *fout = static_cast<float *>(a.fout) + ip.off;
     const unsigned seed = hash32(__ldcg(a.step_ctr) * 0x632BE5ABu + (unsigned)it.x);
-    S::run(a.tab[N - 1], ip, ip.Lx, ip.Ly, ip.pitch, (int)ip.plane, ip.bc, fin, fout, it.y, it.z, sm,
-           a.status, seed);
+    S::run(a.tab[N - 1], a.tab[N - 1], ip, ip.Lx, ip.Ly, ip.pitch, (int)ip.plane, ip.bc, fin, fout,
+           it.y, it.z, sm, a.status, seed);
     if (advance) advance_launch_counter(a.step_ctr, a.done_ctr);
 }
 

@@ -1,8 +1,9 @@
 // Anisotropic tensor products (Sec. 4 builds a 2D lattice as the product of any
 // two 1D levels): D1Q3 along x (level 1) times the level-N Gaussian lattice
 // along y, the form the paper uses for its channel flows. One-node tiles,
-// both precisions; the candidate shapes of each level follow.
-#include "glbm_step2d.cuh"
+// both precisions, and packed pair tiles in FP32; the candidate shapes of each
+// level follow.
+#include "glbm_step2d_launch.cuh"
 
 template <int N, typename T>
 struct TilesX1;
@@ -13,15 +14,16 @@ struct TilesX1;
         static constexpr TileShape shape[] = {__VA_ARGS__};            \
         static constexpr int count = sizeof(shape) / sizeof(shape[0]); \
     };
-// {G, R, V}: 3 (2N+1) populations per node, a few rows per CTA
-GLBM_TILES_X1(1, float, {1, 8, 1}, {1, 4, 1}, {1, 16, 1})
-GLBM_TILES_X1(2, float, {1, 8, 1}, {1, 4, 1}, {1, 16, 1})
-GLBM_TILES_X1(3, float, {1, 8, 1}, {1, 4, 1}, {1, 16, 1})
-GLBM_TILES_X1(4, float, {1, 8, 1}, {1, 4, 1}, {1, 2, 1})
-GLBM_TILES_X1(5, float, {1, 4, 1}, {1, 8, 1}, {1, 2, 1})
-GLBM_TILES_X1(6, float, {1, 4, 1}, {1, 8, 1}, {1, 2, 1})
-GLBM_TILES_X1(7, float, {1, 4, 1}, {1, 2, 1}, {2, 4, 1})
-GLBM_TILES_X1(8, float, {1, 4, 1}, {1, 2, 1}, {2, 4, 1})
+// {G, R, V}: 3 (2N+1) populations per node, a few rows per CTA; V = 2 pairs.
+// Entry 0 of each level is the fastest measured on GB300 (1024 x 200, walls).
+GLBM_TILES_X1(1, float, {1, 8, 2}, {1, 4, 2}, {1, 8, 1}, {1, 4, 1}, {1, 16, 1})
+GLBM_TILES_X1(2, float, {1, 8, 2}, {1, 4, 2}, {1, 8, 1}, {1, 4, 1}, {1, 16, 1})
+GLBM_TILES_X1(3, float, {1, 4, 2}, {1, 2, 2}, {1, 8, 1}, {1, 4, 1}, {1, 16, 1})
+GLBM_TILES_X1(4, float, {1, 4, 2}, {1, 2, 2}, {2, 2, 2}, {1, 8, 1}, {1, 4, 1}, {1, 2, 1})
+GLBM_TILES_X1(5, float, {2, 2, 2}, {1, 2, 2}, {2, 1, 2}, {1, 4, 1}, {1, 8, 1}, {1, 2, 1})
+GLBM_TILES_X1(6, float, {2, 2, 2}, {1, 2, 2}, {2, 1, 2}, {1, 4, 1}, {1, 8, 1}, {1, 2, 1})
+GLBM_TILES_X1(7, float, {2, 2, 2}, {2, 1, 2}, {3, 1, 2}, {1, 4, 1}, {1, 2, 1}, {2, 4, 1})
+GLBM_TILES_X1(8, float, {2, 2, 2}, {2, 1, 2}, {3, 1, 2}, {1, 4, 1}, {1, 2, 1}, {2, 4, 1})
 GLBM_TILES_X1(1, double, {1, 8, 1}, {1, 4, 1})
 GLBM_TILES_X1(2, double, {1, 8, 1}, {1, 4, 1})
 GLBM_TILES_X1(3, double, {1, 4, 1}, {1, 8, 1})
@@ -38,8 +40,13 @@ static cudaError_t launch_x1_shape(int shape, const Step2DArgs &a, int n_inst, c
     if constexpr (I < TilesX1<N, T>::count) {
         if (shape == I) {
             constexpr TileShape t = TilesX1<N, T>::shape[I];
-            const dim3 grid((a.Lx + 31) / 32, (a.Ly + t.R - 1) / t.R, n_inst);
-            k_step2d<N, T, t.G, t.R, 1><<<grid, 32 * t.G * t.R, 0, s>>>(a);
+            const dim3 grid((a.Lx + 32 * t.V - 1) / (32 * t.V), (a.Ly + t.R - 1) / t.R, n_inst);
+            if constexpr (t.V == 2) {
+                static_assert(sizeof(T) == 4, "pair tiles store FP32 deviations");
+                k_step2d_pair<N, t.G, t.R, 1><<<grid, 32 * t.G * t.R, 0, s>>>(a);
+            } else {
+                k_step2d<N, T, t.G, t.R, 1><<<grid, 32 * t.G * t.R, 0, s>>>(a);
+            }
             return cudaGetLastError();
         }
         return launch_x1_shape<N, T, I + 1>(shape, a, n_inst, s);

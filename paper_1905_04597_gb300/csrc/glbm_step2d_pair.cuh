@@ -82,13 +82,13 @@ __device__ __forceinline__ void acc2x2(f32x2 &s, f32x2 &c, f32x2 x)
 // p mod NV of the (|n_y|, row) pairs) in the order of the one-node tile,
 // whatever the tile shape; the NW warps of the CTA share the accumulators.
 // Leaves rho_w - 1 of both walls in rw[2][64]. Every thread calls it.
-template <int N, int NV>
+template <int N, int NX, int NV>
 __device__ __forceinline__ void pair_wall_densities(const InstParams &ip, const float *__restrict__ fin,
                                                     int Ly, int pitch, int plane, const int *win,
                                                     bool need_lo, bool need_hi, int w, int NW,
                                                     int lane, float (*dsum)[2][64], float (*rw)[64])
 {
-    constexpr int Q1 = 2 * N + 1;
+    constexpr int Q1 = 2 * NX + 1;  // velocity columns (N: level along y)
 #pragma unroll 1
     for (int v = w; v < NV; v += NW) {
         float slo0 = 0.f, slo1 = 0.f, shi0 = 0.f, shi1 = 0.f;
@@ -103,16 +103,16 @@ __device__ __forceinline__ void pair_wall_densities(const InstParams &ip, const 
                 const float *pl = fin + ((N - aa) * Q1 * plane + k * pitch);
 #pragma unroll
                 for (int ix = 0; ix < Q1; ++ix) {
-                    slo0 += __ldg(pl + (ix * plane + win[2 * N - ix]));
-                    slo1 += __ldg(pl + (ix * plane + win[2 * N - ix + 1]));
+                    slo0 += __ldg(pl + (ix * plane + win[2 * NX - ix]));
+                    slo1 += __ldg(pl + (ix * plane + win[2 * NX - ix + 1]));
                 }
             }
             if (need_hi) {  // velocity ny = +aa leaving row Ly-1-k through y = Ly-1/2
                 const float *ph = fin + ((N + aa) * Q1 * plane + (Ly - 1 - k) * pitch);
 #pragma unroll
                 for (int ix = 0; ix < Q1; ++ix) {
-                    shi0 += __ldg(ph + (ix * plane + win[2 * N - ix]));
-                    shi1 += __ldg(ph + (ix * plane + win[2 * N - ix + 1]));
+                    shi0 += __ldg(ph + (ix * plane + win[2 * NX - ix]));
+                    shi1 += __ldg(ph + (ix * plane + win[2 * NX - ix + 1]));
                 }
             }
         }
@@ -142,7 +142,7 @@ __device__ __forceinline__ void pair_wall_densities(const InstParams &ip, const 
 }
 
 // Pull of one velocity row iy (source row ys) for a node pair: f[ix] holds
-// both nodes' populations of velocity (ix - N, iy - N).
+// both nodes' populations of velocity (ix - N, iy - N_y); N is the x level.
 template <int N>
 __device__ __forceinline__ void pair_load_row(const float *__restrict__ fin, int iy, int ys,
                                               int pitch, int plane, int x, bool inner,
@@ -172,15 +172,16 @@ __device__ __forceinline__ void pair_load_row(const float *__restrict__ fin, int
 // The populations a wall re-emits into velocity row iy of a node pair
 // (sources inside the wall): W^y (drho_w W^x + rho_w (E^x(u_w) - W^x)).
 template <int N>
-__device__ __forceinline__ void pair_wall_row(const AxisTable &tab, const InstParams &ip, int iy,
-                                              bool lo, float rw0, float rw1, f32x2 (&f)[2 * N + 1])
+__device__ __forceinline__ void pair_wall_row(const AxisTable &tab, const AxisTable &tabx,
+                                              const InstParams &ip, int iy, bool lo, float rw0,
+                                              float rw1, f32x2 (&f)[2 * N + 1])
 {
     using A = TabAcc<float>;
-    const float wy = A::W(tab, iy);
+    const float wy = A::W(tab, iy);  // tab: y axis; tabx and N: x axis
 #pragma unroll
     for (int ix = 0; ix < 2 * N + 1; ++ix) {
         const float dw = lo ? ip.dw_lo_f[ix] : ip.dw_hi_f[ix];
-        const float wx = A::W(tab, ix);
+        const float wx = A::W(tabx, ix);
         f[ix] = pk2(wy * fmaf(rw0, wx, (1.f + rw0) * dw), wy * fmaf(rw1, wx, (1.f + rw1) * dw));
     }
 }
@@ -191,8 +192,9 @@ __device__ __forceinline__ void pair_wall_row(const AxisTable &tab, const InstPa
 // row factor gr = W^y g / (theta omega), and a dither of half an ulp drawn from
 // the nodes' words h0, h1, the row and the column. E^x - W comes from the
 // registers dxr, or from shared memory at dxs (stride 32 pairs) when DXS.
+// N and tabx: the x axis.
 template <int N, bool DXS>
-__device__ __forceinline__ void pair_collide_row(const AxisTable &tab, int iy, float wy, f32x2 dy,
+__device__ __forceinline__ void pair_collide_row(const AxisTable &tabx, int iy, float wy, f32x2 dy,
                                                  f32x2 rho, f32x2 drho, f32x2 om, float gto,
                                                  const f32x2 (&f)[2 * N + 1],
                                                  const f32x2 (&dxr)[2 * N + 1], const f32x2 *dxs,
@@ -213,7 +215,7 @@ __device__ __forceinline__ void pair_collide_row(const AxisTable &tab, int iy, f
         const int nx = ix - N;
         const f32x2 f0 = f[ix];
         const f32x2 Bn = nx != 0 ? fma2(pk2((float)nx, (float)nx), gr, B) : B;
-        const float wx = A::W(tab, ix);
+        const float wx = A::W(tabx, ix);
         const f32x2 dxv = DXS ? dxs[ix * 32] : dxr[ix];
         const f32x2 eq = fma2(dxv, rey, mul2(pk2(wx, wx), Bn));
         // increment plus dither, then one rounding of the store
@@ -234,13 +236,14 @@ __device__ __forceinline__ void pair_collide_row(const AxisTable &tab, int iy, f
     }
 }
 
-template <int N, int G, int R>
+template <int N, int G, int R, int NXL = N>
 struct Step2DPair {
-    static constexpr int Q1 = 2 * N + 1;
+    static constexpr int Q1 = 2 * N + 1;          // velocity rows (level N along y)
+    static constexpr int QX = 2 * NXL + 1;        // velocity columns (level NXL along x)
     static constexpr int RPG = (Q1 + G - 1) / G;  // velocity rows per warp group
     static constexpr int NW = G * R;              // warps per CTA
     static constexpr int TW = 64;                 // tile width (columns)
-    static constexpr int NWIN = 2 * N + 2;        // source columns of a node pair
+    static constexpr int NWIN = 2 * NXL + 2;      // source columns of a node pair
     static constexpr int NV = Step2D<N, float, G, R>::NV;  // wall-flux accumulators
     using A = TabAcc<float>;
 
@@ -249,13 +252,15 @@ struct Step2DPair {
         float rw[2][TW];          // wall density deviations: lo, hi
         float dsum[NV][2][TW];    // partial wall fluxes of the NV accumulators
         // E^x - W and E^y - W of the tile's nodes, shared by the warp groups
-        float eqx[G > 1 ? R : 1][G > 1 ? Q1 : 1][TW];
+        float eqx[G > 1 ? R : 1][G > 1 ? QX : 1][TW];
         float eqy[G > 1 ? R : 1][G > 1 ? Q1 : 1][TW];
     };
 
     // One tile: columns x0..x0+63 (x0 a multiple of 64), rows y0..y0+R-1 of one
-    // instance whose populations start at fin / fout (8-byte aligned planes).
-    __device__ static void run(const AxisTable &tab, const InstParams &ip, int Lx, int Ly,
+    // instance whose populations start at fin / fout (8-byte aligned planes);
+    // tab is the y axis's table, tabx the x axis's (the same when isotropic).
+    __device__ static void run(const AxisTable &tab, const AxisTable &tabx, const InstParams &ip,
+                               int Lx, int Ly,
                                int pitch, int plane, int bc, const float *__restrict__ fin,
                                float *__restrict__ fout, int x0, int y0, Smem &sm,
                                unsigned *status, unsigned seed)
@@ -270,26 +275,26 @@ struct Step2DPair {
         const bool act0 = yin && x < Lx, act1 = yin && x + 1 < Lx;
         const int xc = x < Lx ? x : Lx - 1;
         const int yc = yin ? y : Ly - 1;
-        // the tile pulls from columns x0-N .. x0+63+N without wrapping
-        const bool inner = x0 >= N && x0 + TW + N <= Lx;
+        // the tile pulls from columns x0-NXL .. x0+63+NXL without wrapping
+        const bool inner = x0 >= NXL && x0 + TW + NXL <= Lx;
 
         // source columns of the pair: node x pulls velocity n_x from column
         // win[N - n_x], node x + 1 from win[N - n_x + 1]
         int win[NWIN];
-        const bool one_wrap = Lx > N + 1;
+        const bool one_wrap = Lx > NXL + 1;
 #pragma unroll
-        for (int j = 0; j < NWIN; ++j) win[j] = wrap_shift(xc - N + j, Lx, one_wrap);
+        for (int j = 0; j < NWIN; ++j) win[j] = wrap_shift(xc - NXL + j, Lx, one_wrap);
 
         // ---- phase 0: wall densities of this tile's columns ---------------
         const bool need_lo = walls && (y0 < N);
         const bool need_hi = walls && (y0 + R > Ly - N);
         if (need_lo || need_hi)
-            pair_wall_densities<N, NV>(ip, fin, Ly, pitch, plane, win, need_lo, need_hi, w, NW, lane,
+            pair_wall_densities<N, NXL, NV>(ip, fin, Ly, pitch, plane, win, need_lo, need_hi, w, NW, lane,
                                        sm.dsum, sm.rw);
 
         // ---- phase 1: pull and partial moments -----------------------------
         // rows iy = g + k G of this warp group; f[k][ix] holds both nodes
-        f32x2 f[RPG][Q1];
+        f32x2 f[RPG][QX];
         f32x2 s_r = 0ull, c_r = 0ull, s_x = 0ull, c_x = 0ull, s_y = 0ull, c_y = 0ull;
 #pragma unroll
         for (int k = 0; k < RPG; ++k) {
@@ -298,7 +303,7 @@ struct Step2DPair {
                 const int ny = iy - N;
                 int ys = yc - ny;
                 ys = walls ? min(max(ys, 0), Ly - 1) : wrap_shift(ys, Ly, Ly > N);
-                pair_load_row<N>(fin, iy, ys, pitch, plane, x, inner, win, f[k]);
+                pair_load_row<NXL>(fin, iy, ys, pitch, plane, x, inner, win, f[k]);
             }
         }
 #pragma unroll
@@ -309,16 +314,16 @@ struct Step2DPair {
                 const int ys = yc - ny;
                 if (walls && (ys < 0 || ys >= Ly)) {  // uniform across the warp
                     const bool lo = ys < 0;
-                    pair_wall_row<N>(tab, ip, iy, lo, sm.rw[lo ? 0 : 1][2 * lane],
+                    pair_wall_row<NXL>(tab, tabx, ip, iy, lo, sm.rw[lo ? 0 : 1][2 * lane],
                                      sm.rw[lo ? 0 : 1][2 * lane + 1], f[k]);
                 }
                 f32x2 rs = 0ull;
 #pragma unroll
-                for (int ix = 0; ix < Q1; ++ix) rs = add2(rs, f[k][ix]);
+                for (int ix = 0; ix < QX; ++ix) rs = add2(rs, f[k][ix]);
                 f32x2 jx = 0ull;
 #pragma unroll
-                for (int n = 1; n <= N; ++n)
-                    jx = fma2(pk2((float)n, (float)n), sub2(f[k][N + n], f[k][N - n]), jx);
+                for (int n = 1; n <= NXL; ++n)
+                    jx = fma2(pk2((float)n, (float)n), sub2(f[k][NXL + n], f[k][NXL - n]), jx);
                 acc2x2(s_r, c_r, rs);
                 acc2x2(s_x, c_x, jx);
                 if (ny != 0)  // products rounded per lane, as in the one-node tile
@@ -356,23 +361,24 @@ struct Step2DPair {
         const f32x2 ux = mul2(add2(S_x, C_x), inv_rho);
         const f32x2 uy = mul2(add2(S_y, C_y), inv_rho);
         {
-            const float umax = (float)(0.816496580927726 * N);  // sqrt(2/3) N (Sec. 3)
-            const bool bad0 = act0 && (!(lo2(rho) > 0.f) || !(fabsf(lo2(ux)) <= umax) ||
+            // sqrt(2/3) N per axis (Sec. 3)
+            const float umax = (float)(0.816496580927726 * N), umaxx = (float)(0.816496580927726 * NXL);
+            const bool bad0 = act0 && (!(lo2(rho) > 0.f) || !(fabsf(lo2(ux)) <= umaxx) ||
                                        !(fabsf(lo2(uy)) <= umax));
-            const bool bad1 = act1 && (!(hi2(rho) > 0.f) || !(fabsf(hi2(ux)) <= umax) ||
+            const bool bad1 = act1 && (!(hi2(rho) > 0.f) || !(fabsf(hi2(ux)) <= umaxx) ||
                                        !(fabsf(hi2(uy)) <= umax));
             if (bad0 || bad1) atomicOr(status, 1u);
         }
 
         // E^x - W and E^y - W for both nodes
-        f32x2 dx[Q1];
+        f32x2 dx[QX];
         float dy0all[G == 1 ? Q1 : 1], dy1all[G == 1 ? Q1 : 1];
         if constexpr (G == 1) {
-            float d0[Q1], d1[Q1];
-            eq_dev_all<N, float>(tab, lo2(ux), d0);
-            eq_dev_all<N, float>(tab, hi2(ux), d1);
+            float d0[QX], d1[QX];
+            eq_dev_all<NXL, float>(tabx, lo2(ux), d0);
+            eq_dev_all<NXL, float>(tabx, hi2(ux), d1);
 #pragma unroll
-            for (int ix = 0; ix < Q1; ++ix) dx[ix] = pk2(d0[ix], d1[ix]);
+            for (int ix = 0; ix < QX; ++ix) dx[ix] = pk2(d0[ix], d1[ix]);
             eq_dev_all<N, float>(tab, lo2(uy), dy0all);
             eq_dev_all<N, float>(tab, hi2(uy), dy1all);
         } else {
@@ -381,21 +387,31 @@ struct Step2DPair {
             // meet in shared memory
             const float u[4] = {lo2(ux), hi2(ux), lo2(uy), hi2(uy)};
 #pragma unroll
-            for (int n = 0; n <= N; ++n) {
+            for (int n = 0; n <= (N > NXL ? N : NXL); ++n) {
                 if (n % G != g) continue;
                 float plus[4], minus[4];
 #pragma unroll
                 for (int c = 0; c < 4; ++c) {
+                    if (c < 2 ? n > NXL : n > N) continue;  // x nodes: level NXL; y: N
                     float ae, bo;
-                    eq_parts<N, float>(tab, n, u[c] * u[c], ae, bo);
+                    if (c < 2)
+                        eq_parts<NXL, float>(tabx, n, u[c] * u[c], ae, bo);
+                    else
+                        eq_parts<N, float>(tab, n, u[c] * u[c], ae, bo);
                     plus[c] = n == 0 ? ae : fmaf(u[c], bo, ae);
                     minus[c] = n == 0 ? ae : fmaf(-u[c], bo, ae);
                 }
-                *reinterpret_cast<f32x2 *>(&sm.eqx[r][N + n][2 * lane]) = pk2(plus[0], plus[1]);
-                *reinterpret_cast<f32x2 *>(&sm.eqy[r][N + n][2 * lane]) = pk2(plus[2], plus[3]);
-                if (n != 0) {
-                    *reinterpret_cast<f32x2 *>(&sm.eqx[r][N - n][2 * lane]) = pk2(minus[0], minus[1]);
-                    *reinterpret_cast<f32x2 *>(&sm.eqy[r][N - n][2 * lane]) = pk2(minus[2], minus[3]);
+                if (n <= NXL) {
+                    *reinterpret_cast<f32x2 *>(&sm.eqx[r][NXL + n][2 * lane]) = pk2(plus[0], plus[1]);
+                    if (n != 0)
+                        *reinterpret_cast<f32x2 *>(&sm.eqx[r][NXL - n][2 * lane]) =
+                            pk2(minus[0], minus[1]);
+                }
+                if (n <= N) {
+                    *reinterpret_cast<f32x2 *>(&sm.eqy[r][N + n][2 * lane]) = pk2(plus[2], plus[3]);
+                    if (n != 0)
+                        *reinterpret_cast<f32x2 *>(&sm.eqy[r][N - n][2 * lane]) =
+                            pk2(minus[2], minus[3]);
                 }
             }
             __syncthreads();  // E^x - W is read from shared memory where it is used
@@ -418,8 +434,8 @@ struct Step2DPair {
                 else
                     dy = *reinterpret_cast<const f32x2 *>(&sm.eqy[r][iy][2 * lane]);
                 const f32x2 *dxs = reinterpret_cast<const f32x2 *>(&sm.eqx[G > 1 ? r : 0][0][2 * lane]);
-                pair_collide_row<N, (G > 1)>(tab, iy, wy, dy, rho, drho, om, gto, f[k], dx, dxs,
-                                             obase + iy * Q1 * plane, plane, h0, h1, act0, act1);
+                pair_collide_row<NXL, (G > 1)>(tabx, iy, wy, dy, rho, drho, om, gto, f[k], dx, dxs,
+                                               obase + iy * QX * plane, plane, h0, h1, act0, act1);
             }
         }
     }
