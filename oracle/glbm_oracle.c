@@ -23,7 +23,18 @@
  * streamed populations S(X_t).
  *
  * Layout. Populations f[q][y][x], x fastest, q = (ny+NY)*(2NX+1) + (nx+NX)
- * for the 2D tensor-product lattice (Sec. 4) and q = n+N in 1D.
+ * for the 2D tensor-product lattice (Sec. 4) and q = n+N in 1D; on the 2N+2
+ * lattices below, q = iy*Qx + ix with the velocity indices of each axis.
+ *
+ * The 2N+2 hierarchy (Sec. 4, "zero velocity is removed"): the velocities
+ * (n + 1/2) c, n = 0..N, and (n - 1/2) c, n = -N..0, with the equilibrium of
+ * each taken as the mean of the 2N+1 hierarchy's equilibria at the two
+ * neighbouring velocities (Eqs. maineq01_noball - maineq04_noball). Written on
+ * a lattice of spacing c/2, its velocities are the odd integers -(2N+1) ..
+ * 2N+1, the 2N+1 equilibria are evaluated at u/c = u/2, and the lattice
+ * temperature is (4N+3)/3 (Eq. temp_2N2 with c = 2). 2D lattices only, per
+ * axis (orc_cfg.zv): the paper's channel models G-D1Q6 x D1Q3 and
+ * G-D1Q8 x D1Q3 take it along the wall normal y only, G-D2Q784 along both.
  *
  * Boundary readings (the paper cites its wall condition but states no
  * formula; Sec. 5.3-5.4):
@@ -45,6 +56,7 @@
 #define ORC_MAX_N 16
 
 enum { ORC_BC_WALLS = 0, ORC_BC_BOUNCEBACK = 1, ORC_BC_PERIODIC = 2 };
+enum { ORC_ZV_X = 1, ORC_ZV_Y = 2 };
 
 /* Configuration of one lattice; mirrored by a ctypes.Structure in oracle.py. */
 typedef struct {
@@ -58,6 +70,8 @@ typedef struct {
     double uw_lo; /* x-velocity of the wall at y = -1/2 (lattice units) */
     double uw_hi; /* x-velocity of the wall at y = Ly - 1/2 */
     double g;     /* body force along x (lattice units), 2D only */
+    int zv;       /* 2D axes that take the 2N+2 hierarchy without zero velocity:
+                     bit 0 (ORC_ZV_X) x, bit 1 (ORC_ZV_Y) y; 0 = none */
 } orc_cfg;
 
 static double orc_factorial(int n)
@@ -139,6 +153,73 @@ void orc_weights(int N, double *out)
     orc_eq_lattice(N, 0.0, out);
 }
 
+/* One axis of a 2D lattice: level N, hierarchy (zv = 0: 2N+1 velocities
+ * -N..N; zv = 1: 2N+2 velocities, the odd integers -(2N+1)..2N+1). */
+typedef struct {
+    int N, zv, Q;
+    int v[2 * ORC_MAX_N + 2];
+} orc_axis;
+
+static void orc_axis_make(int N, int zv, orc_axis *a)
+{
+    a->N = N;
+    a->zv = zv;
+    a->Q = zv ? 2 * N + 2 : 2 * N + 1;
+    for (int j = 0; j < a->Q; ++j) a->v[j] = zv ? 2 * j - (2 * N + 1) : j - N;
+}
+
+/*
+ * f^eq_j / rho of the axis at velocity u (its lattice units). On the 2N+2
+ * hierarchy the velocity v = 2n +- 1 (that is (n +- 1/2) c) takes the mean
+ * of the 2N+1 equilibria at its neighbours n and n +- 1 (c units, u / c =
+ * u / 2), an equilibrium beyond -N..N counting zero (Eqs. maineq01_noball -
+ * maineq04_noball).
+ */
+static void orc_axis_eq(const orc_axis *a, double u, double *E)
+{
+    if (!a->zv) {
+        orc_eq_lattice(a->N, u, E);
+        return;
+    }
+    const int N = a->N;
+    double En[2 * ORC_MAX_N + 1];
+    orc_eq_lattice(N, 0.5 * u, En);
+    for (int j = 0; j < a->Q; ++j) {
+        const int lo = (a->v[j] - 1) / 2, hi = (a->v[j] + 1) / 2;
+        const double elo = (lo >= -N && lo <= N) ? En[lo + N] : 0.0;
+        const double ehi = (hi >= -N && hi <= N) ? En[hi + N] : 0.0;
+        E[j] = 0.5 * (elo + ehi);
+    }
+}
+
+/* Lattice temperature of the axis: N/3, or (4N+3)/3 on the 2N+2 hierarchy. */
+static double orc_axis_theta(const orc_axis *a)
+{
+    return a->zv ? (4.0 * a->N + 3.0) / 3.0 : a->N / 3.0;
+}
+
+/* Positivity bound on |u| (Sec. 3: |u/c| <= sqrt(2/3) N). */
+static double orc_axis_umax(const orc_axis *a)
+{
+    return (a->zv ? 2.0 : 1.0) * sqrt(2.0 / 3.0) * a->N;
+}
+
+/* Public: f^eq / rho of one axis (Q values), hierarchy zv. */
+void orc_eq_axis(int N, int zv, double u, double *out)
+{
+    orc_axis a;
+    orc_axis_make(N, zv, &a);
+    orc_axis_eq(&a, u, out);
+}
+
+/* Public: Eq. (kn) with the lattice temperature of the hierarchy. */
+double orc_tau_from_kn_axis(int N, int zv, double H, double kn)
+{
+    orc_axis a;
+    orc_axis_make(N, zv, &a);
+    return kn * H / sqrt(2.0 * orc_axis_theta(&a));
+}
+
 /*
  * Knudsen number to relaxation time, Eq. (kn): Kn = sqrt(2/theta) nu / H with
  * nu = theta * tau (Sec. 5.2), in lattice units theta = N/3.
@@ -149,8 +230,12 @@ double orc_tau_from_kn(int N, double H, double kn)
     return kn * H / sqrt(2.0 * theta);
 }
 
+#define ORC_ZVX(c) (((c)->zv & ORC_ZV_X) != 0)
+#define ORC_ZVY(c) (((c)->zv & ORC_ZV_Y) != 0)
+
 static int orc_check(const orc_cfg *c)
 {
+    if (c->zv < 0 || c->zv > 3 || (c->zv && c->dims != 2)) return -1;
     if (c->dims == 1) {
         if (c->NX < 1 || c->NX > ORC_MAX_N || c->Lx < 1 || c->Ly != 1) return -1;
         if (c->bc == ORC_BC_BOUNCEBACK && c->Lx < c->NX) return -1;
@@ -158,7 +243,7 @@ static int orc_check(const orc_cfg *c)
     } else if (c->dims == 2) {
         if (c->NX < 1 || c->NX > ORC_MAX_N || c->NY < 1 || c->NY > ORC_MAX_N) return -1;
         if (c->Lx < 1 || c->Ly < 1) return -1;
-        if (c->bc == ORC_BC_WALLS && c->Ly < c->NY) return -1;
+        if (c->bc == ORC_BC_WALLS && c->Ly < (ORC_ZVY(c) ? 2 * c->NY + 1 : c->NY)) return -1;
         if (c->bc != ORC_BC_WALLS && c->bc != ORC_BC_PERIODIC) return -1;
     } else {
         return -1;
@@ -168,7 +253,7 @@ static int orc_check(const orc_cfg *c)
 
 static int orc_nq(const orc_cfg *c)
 {
-    return c->dims == 1 ? 2 * c->NX + 1 : (2 * c->NX + 1) * (2 * c->NY + 1);
+    return c->dims == 1 ? 2 * c->NX + 1 : (2 * c->NX + 1 + ORC_ZVX(c)) * (2 * c->NY + 1 + ORC_ZVY(c));
 }
 
 /* ------------------------------------------------------------------------ */
@@ -215,15 +300,17 @@ static void orc_stream1d(const orc_cfg *c, const double *X, double *F)
  */
 static void orc_stream2d(const orc_cfg *c, const double *X, double *F)
 {
-    int NX = c->NX, NY = c->NY, Lx = c->Lx, Ly = c->Ly;
-    int Q1x = 2 * NX + 1;
+    orc_axis ax, ay;
+    orc_axis_make(c->NX, ORC_ZVX(c), &ax);
+    orc_axis_make(c->NY, ORC_ZVY(c), &ay);
+    int Lx = c->Lx, Ly = c->Ly;
     size_t plane = (size_t)Lx * Ly;
     double *Dlo = (double *)calloc((size_t)Lx, sizeof(double));
     double *Dhi = (double *)calloc((size_t)Lx, sizeof(double));
 
-    for (int ny = -NY; ny <= NY; ++ny) {
-        for (int nx = -NX; nx <= NX; ++nx) {
-            int q = (ny + NY) * Q1x + (nx + NX);
+    for (int iy = 0; iy < ay.Q; ++iy) {
+        for (int ix = 0; ix < ax.Q; ++ix) {
+            int q = iy * ax.Q + ix, nx = ax.v[ix], ny = ay.v[iy];
             for (int y = 0; y < Ly; ++y) {
                 for (int x = 0; x < Lx; ++x) {
                     double v = X[q * plane + (size_t)y * Lx + x];
@@ -244,31 +331,33 @@ static void orc_stream2d(const orc_cfg *c, const double *X, double *F)
     }
 
     if (c->bc == ORC_BC_WALLS) {
-        double Wy[2 * ORC_MAX_N + 1], Elo[2 * ORC_MAX_N + 1], Ehi[2 * ORC_MAX_N + 1];
-        orc_eq_lattice(NY, 0.0, Wy);
-        orc_eq_lattice(NX, c->uw_lo, Elo);
-        orc_eq_lattice(NX, c->uw_hi, Ehi);
+        double Wy[2 * ORC_MAX_N + 2], Elo[2 * ORC_MAX_N + 2], Ehi[2 * ORC_MAX_N + 2];
+        orc_axis_eq(&ay, 0.0, Wy);
+        orc_axis_eq(&ax, c->uw_lo, Elo);
+        orc_axis_eq(&ax, c->uw_hi, Ehi);
         /* emitted mass per unit rho_w: sum over velocities leaving the wall of
            |xi_y| * E^x * W^y, i.e. one population per row it fills */
-        double den = 0.0;
-        for (int ny = 1; ny <= NY; ++ny) {
-            for (int nx = -NX; nx <= NX; ++nx) den += ny * Elo[nx + NX] * Wy[ny + NY];
-        }
-        double den_hi = 0.0;
-        for (int ny = 1; ny <= NY; ++ny) {
-            for (int nx = -NX; nx <= NX; ++nx) den_hi += ny * Ehi[nx + NX] * Wy[-ny + NY];
+        double den = 0.0, den_hi = 0.0;
+        for (int iy = 0; iy < ay.Q; ++iy) {
+            for (int ix = 0; ix < ax.Q; ++ix) {
+                if (ay.v[iy] > 0) den += ay.v[iy] * Elo[ix] * Wy[iy];
+                if (ay.v[iy] < 0) den_hi += -ay.v[iy] * Ehi[ix] * Wy[iy];
+            }
         }
         for (int x = 0; x < Lx; ++x) {
             double rlo = Dlo[x] / den;
             double rhi = Dhi[x] / den_hi;
-            for (int ny = 1; ny <= NY; ++ny) {
-                for (int nx = -NX; nx <= NX; ++nx) {
-                    int qup = (ny + NY) * Q1x + (nx + NX);   /* leaves the lower wall */
-                    int qdn = (-ny + NY) * Q1x + (nx + NX);  /* leaves the upper wall */
-                    for (int k = 0; k < ny; ++k) {
-                        F[qup * plane + (size_t)k * Lx + x] = rlo * Elo[nx + NX] * Wy[ny + NY];
-                        F[qdn * plane + (size_t)(Ly - 1 - k) * Lx + x] =
-                            rhi * Ehi[nx + NX] * Wy[-ny + NY];
+            for (int iy = 0; iy < ay.Q; ++iy) {
+                int ny = ay.v[iy];
+                for (int ix = 0; ix < ax.Q; ++ix) {
+                    int q = iy * ax.Q + ix;
+                    /* ny > 0 leaves the lower wall into rows 0..ny-1, ny < 0 the
+                       upper wall into rows Ly-1 .. Ly+ny */
+                    for (int k = 0; k < (ny > 0 ? ny : -ny); ++k) {
+                        if (ny > 0)
+                            F[q * plane + (size_t)k * Lx + x] = rlo * Elo[ix] * Wy[iy];
+                        else
+                            F[q * plane + (size_t)(Ly - 1 - k) * Lx + x] = rhi * Ehi[ix] * Wy[iy];
                     }
                 }
             }
@@ -324,38 +413,39 @@ int orc_collide(const orc_cfg *c, const double *F, double *X)
         return bad;
     }
 
-    int NX = c->NX, NY = c->NY, Lx = c->Lx, Ly = c->Ly;
-    int Q1x = 2 * NX + 1;
+    orc_axis ax, ay;
+    orc_axis_make(c->NX, ORC_ZVX(c), &ax);
+    orc_axis_make(c->NY, ORC_ZVY(c), &ay);
+    int Lx = c->Lx, Ly = c->Ly;
     size_t plane = (size_t)Lx * Ly;
-    double Wx[2 * ORC_MAX_N + 1], Wy[2 * ORC_MAX_N + 1];
-    double Ex[2 * ORC_MAX_N + 1], Ey[2 * ORC_MAX_N + 1];
-    orc_eq_lattice(NX, 0.0, Wx);
-    orc_eq_lattice(NY, 0.0, Wy);
-    double theta_x = NX / 3.0;
+    double Wx[2 * ORC_MAX_N + 2], Wy[2 * ORC_MAX_N + 2];
+    double Ex[2 * ORC_MAX_N + 2], Ey[2 * ORC_MAX_N + 2];
+    orc_axis_eq(&ax, 0.0, Wx);
+    orc_axis_eq(&ay, 0.0, Wy);
+    double theta_x = orc_axis_theta(&ax);
     for (int y = 0; y < Ly; ++y) {
         for (int x = 0; x < Lx; ++x) {
             size_t node = (size_t)y * Lx + x;
             double rho = 0.0, jx = 0.0, jy = 0.0;
-            for (int ny = -NY; ny <= NY; ++ny) {
-                for (int nx = -NX; nx <= NX; ++nx) {
-                    double f = F[((ny + NY) * Q1x + (nx + NX)) * plane + node];
+            for (int iy = 0; iy < ay.Q; ++iy) {
+                for (int ix = 0; ix < ax.Q; ++ix) {
+                    double f = F[(iy * ax.Q + ix) * plane + node];
                     rho += f;
-                    jx += nx * f;
-                    jy += ny * f;
+                    jx += ax.v[ix] * f;
+                    jy += ay.v[iy] * f;
                 }
             }
             double ux = jx / rho, uy = jy / rho;
-            if (!(rho > 0.0) || fabs(ux) > sqrt(2.0 / 3.0) * NX ||
-                fabs(uy) > sqrt(2.0 / 3.0) * NY)
+            if (!(rho > 0.0) || fabs(ux) > orc_axis_umax(&ax) || fabs(uy) > orc_axis_umax(&ay))
                 ++bad;
-            orc_eq_lattice(NX, ux, Ex);
-            orc_eq_lattice(NY, uy, Ey);
-            for (int ny = -NY; ny <= NY; ++ny) {
-                for (int nx = -NX; nx <= NX; ++nx) {
-                    size_t idx = ((ny + NY) * Q1x + (nx + NX)) * plane + node;
+            orc_axis_eq(&ax, ux, Ex);
+            orc_axis_eq(&ay, uy, Ey);
+            for (int iy = 0; iy < ay.Q; ++iy) {
+                for (int ix = 0; ix < ax.Q; ++ix) {
+                    size_t idx = (iy * ax.Q + ix) * plane + node;
                     double f = F[idx];
-                    double feq = rho * Ex[nx + NX] * Ey[ny + NY];
-                    double force = Wx[nx + NX] * Wy[ny + NY] * nx * c->g / theta_x;
+                    double feq = rho * Ex[ix] * Ey[iy];
+                    double force = Wx[ix] * Wy[iy] * ax.v[ix] * c->g / theta_x;
                     X[idx] = f + omega * (feq - f) + force;
                 }
             }
@@ -399,25 +489,26 @@ int orc_macro(const orc_cfg *c, const double *F, double *out)
         }
         return 0;
     }
-    int NX = c->NX, NY = c->NY, Lx = c->Lx, Ly = c->Ly;
-    int Q1x = 2 * NX + 1;
-    size_t plane = (size_t)Lx * Ly;
+    orc_axis ax, ay;
+    orc_axis_make(c->NX, ORC_ZVX(c), &ax);
+    orc_axis_make(c->NY, ORC_ZVY(c), &ay);
+    size_t plane = (size_t)c->Lx * c->Ly;
     for (size_t node = 0; node < plane; ++node) {
         double rho = 0.0, jx = 0.0, jy = 0.0;
-        for (int ny = -NY; ny <= NY; ++ny) {
-            for (int nx = -NX; nx <= NX; ++nx) {
-                double f = F[((ny + NY) * Q1x + (nx + NX)) * plane + node];
+        for (int iy = 0; iy < ay.Q; ++iy) {
+            for (int ix = 0; ix < ax.Q; ++ix) {
+                double f = F[(iy * ax.Q + ix) * plane + node];
                 rho += f;
-                jx += nx * f;
-                jy += ny * f;
+                jx += ax.v[ix] * f;
+                jy += ay.v[iy] * f;
             }
         }
         double ux = jx / rho, uy = jy / rho;
         double e2 = 0.0, qx = 0.0, qy = 0.0, sxy = 0.0;
-        for (int ny = -NY; ny <= NY; ++ny) {
-            for (int nx = -NX; nx <= NX; ++nx) {
-                double f = F[((ny + NY) * Q1x + (nx + NX)) * plane + node];
-                double dx = nx - ux, dy = ny - uy, d2 = dx * dx + dy * dy;
+        for (int iy = 0; iy < ay.Q; ++iy) {
+            for (int ix = 0; ix < ax.Q; ++ix) {
+                double f = F[(iy * ax.Q + ix) * plane + node];
+                double dx = ax.v[ix] - ux, dy = ay.v[iy] - uy, d2 = dx * dx + dy * dy;
                 e2 += d2 * f;
                 qx += dx * d2 * f;
                 qy += dy * d2 * f;
@@ -452,17 +543,17 @@ int orc_equilibrium(const orc_cfg *c, const double *rho, const double *ux, const
         }
         return 0;
     }
-    int NX = c->NX, NY = c->NY;
-    int Q1x = 2 * NX + 1;
+    orc_axis ax, ay;
+    orc_axis_make(c->NX, ORC_ZVX(c), &ax);
+    orc_axis_make(c->NY, ORC_ZVY(c), &ay);
     size_t plane = (size_t)c->Lx * c->Ly;
-    double Ex[2 * ORC_MAX_N + 1], Ey[2 * ORC_MAX_N + 1];
+    double Ex[2 * ORC_MAX_N + 2], Ey[2 * ORC_MAX_N + 2];
     for (size_t node = 0; node < plane; ++node) {
-        orc_eq_lattice(NX, ux[node], Ex);
-        orc_eq_lattice(NY, uy[node], Ey);
-        for (int ny = -NY; ny <= NY; ++ny)
-            for (int nx = -NX; nx <= NX; ++nx)
-                X[((ny + NY) * Q1x + (nx + NX)) * plane + node] =
-                    rho[node] * Ex[nx + NX] * Ey[ny + NY];
+        orc_axis_eq(&ax, ux[node], Ex);
+        orc_axis_eq(&ay, uy[node], Ey);
+        for (int iy = 0; iy < ay.Q; ++iy)
+            for (int ix = 0; ix < ax.Q; ++ix)
+                X[(iy * ax.Q + ix) * plane + node] = rho[node] * Ex[ix] * Ey[iy];
     }
     return 0;
 }
@@ -612,7 +703,7 @@ static void orc_collide_dual(const orc_cfg *c, const double *F, double *X)
  */
 int orc_flowrate_grad(const orc_cfg *c, const double *X0, long steps, double *out)
 {
-    if (orc_check(c) || c->dims != 2) return -1;
+    if (orc_check(c) || c->dims != 2 || c->zv) return -1;  /* the 2N+1 hierarchy only */
     const size_t plane = (size_t)c->Lx * c->Ly;
     const size_t n = (size_t)orc_nq(c) * plane;
     double *X = (double *)calloc(3 * n, sizeof(double));

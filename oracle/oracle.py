@@ -21,6 +21,7 @@ SRC = os.path.join(HERE, "glbm_oracle.c")
 LIB = os.path.join(HERE, "liboracle.so")
 
 BC_WALLS, BC_BOUNCEBACK, BC_PERIODIC = 0, 1, 2
+ZV_X, ZV_Y = 1, 2  # axes on the 2N+2 hierarchy (Lattice zv mask)
 
 
 def build(force: bool = False) -> str:
@@ -44,7 +45,7 @@ class Cfg(ctypes.Structure):
     _fields_ = [("dims", ctypes.c_int), ("NX", ctypes.c_int), ("NY", ctypes.c_int),
                 ("Lx", ctypes.c_int), ("Ly", ctypes.c_int), ("bc", ctypes.c_int),
                 ("tau", ctypes.c_double), ("uw_lo", ctypes.c_double),
-                ("uw_hi", ctypes.c_double), ("g", ctypes.c_double)]
+                ("uw_hi", ctypes.c_double), ("g", ctypes.c_double), ("zv", ctypes.c_int)]
 
 
 _lib = None
@@ -63,6 +64,10 @@ def lib():
         _lib.orc_weights.argtypes = [ctypes.c_int, dp]
         _lib.orc_tau_from_kn.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double]
         _lib.orc_tau_from_kn.restype = ctypes.c_double
+        _lib.orc_eq_axis.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, dp]
+        _lib.orc_tau_from_kn_axis.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                              ctypes.c_double]
+        _lib.orc_tau_from_kn_axis.restype = ctypes.c_double
         for name in ("orc_stream", "orc_collide", "orc_macro", "orc_observe"):
             getattr(_lib, name).argtypes = [cp, dp, dp]
             getattr(_lib, name).restype = ctypes.c_int
@@ -83,13 +88,17 @@ def _dp(a: np.ndarray):
 class Lattice:
     """One lattice for the oracle: level N per axis (N = k + 1), node counts,
     boundary kind, relaxation time, wall speeds and body force, all in lattice
-    units (velocities are the integers -N..N)."""
+    units (velocities are the integers -N..N; on an axis that zv selects,
+    ZV_X = 1 and/or ZV_Y = 2, the 2N+2 hierarchy's odd integers
+    -(2N+1)..2N+1, 2D only)."""
 
-    def __init__(self, dims, NX, NY, Lx, Ly, bc, tau, uw_lo=0.0, uw_hi=0.0, g=0.0):
+    def __init__(self, dims, NX, NY, Lx, Ly, bc, tau, uw_lo=0.0, uw_hi=0.0, g=0.0, zv=0):
         self.cfg = Cfg(dims, NX, NY if dims == 2 else 0, Lx, Ly if dims == 2 else 1, bc,
-                       tau, uw_lo, uw_hi, g)
+                       tau, uw_lo, uw_hi, g, zv)
         self.dims = dims
-        self.Q = (2 * NX + 1) * ((2 * NY + 1) if dims == 2 else 1)
+        qx = 2 * NX + (2 if zv & ZV_X else 1)
+        qy = 2 * NY + (2 if zv & ZV_Y else 1)
+        self.Q = qx * (qy if dims == 2 else 1)
         self.shape = (self.Q, self.cfg.Ly, Lx) if dims == 2 else (self.Q, Lx)
         self.nfields = 7 if dims == 2 else 4
 
@@ -175,5 +184,14 @@ def weights(N):
     return out
 
 
-def tau_from_kn(N, H, kn):
+def tau_from_kn(N, H, kn, zv=0):
+    if zv:
+        return lib().orc_tau_from_kn_axis(N, zv, H, kn)
     return lib().orc_tau_from_kn(N, H, kn)
+
+
+def eq_axis(N, zv, u):
+    """f^eq / rho of one axis: the 2N+1 hierarchy (zv=0) or the 2N+2 one."""
+    out = np.empty(2 * N + (2 if zv else 1))
+    lib().orc_eq_axis(N, zv, u, _dp(out))
+    return out

@@ -20,16 +20,24 @@ MUTATIONS = {
                         "orc_factorial(n) * orc_factorial(m)"),
     "mirror not swapped": ("        Pp = Pm;\n        Pm = t;\n", "        (void)t;\n"),
     "omega without 1/2": ("double omega = 1.0 / (c->tau + 0.5);", "double omega = 1.0 / c->tau;"),
-    "force sign": ("* nx * c->g / theta_x", "* (-nx) * c->g / theta_x"),
-    "force theta": ("* nx * c->g / theta_x", "* nx * c->g"),
+    "force sign": ("* ax.v[ix] * c->g / theta_x", "* (-ax.v[ix]) * c->g / theta_x"),
+    "force theta": ("* ax.v[ix] * c->g / theta_x", "* ax.v[ix] * c->g"),
     "stream x sign": ("int xd = orc_wrap(x + nx, Lx);", "int xd = orc_wrap(x - nx, Lx);"),
-    "wall speeds swapped": ("orc_eq_lattice(NX, c->uw_lo, Elo);", "orc_eq_lattice(NX, c->uw_hi, Elo);"),
-    "emission rows": ("for (int k = 0; k < ny; ++k) {", "for (int k = 0; k < ny - 1; ++k) {"),
+    "wall speeds swapped": ("orc_axis_eq(&ax, c->uw_lo, Elo);", "orc_axis_eq(&ax, c->uw_hi, Elo);"),
+    "emission rows": ("for (int k = 0; k < (ny > 0 ? ny : -ny); ++k) {",
+                      "for (int k = 0; k < (ny > 0 ? ny : -ny) - 1; ++k) {"),
     "bounce-back offset": ("F[(-n + N) * L + (-1 - xd)] = v;", "F[(-n + N) * L + (-xd)] = v;"),
     "temperature dims": ("out[3 * plane + node] = e2 / (2.0 * rho);",
                          "out[3 * plane + node] = e2 / rho;"),
     "tangent of omega": ("if (d == 1) v += domega * (feq - f);", "if (d == 1) v += omega * (feq - f);"),
     "tangent of P0": ("const double dP0 = -dPp - dPm;", "const double dP0 = dPp + dPm;"),
+    "2N+2 at full speed": ("orc_eq_lattice(N, 0.5 * u, En);", "orc_eq_lattice(N, u, En);"),
+    "2N+2 one neighbour": ("const int lo = (a->v[j] - 1) / 2, hi = (a->v[j] + 1) / 2;",
+                           "const int lo = (a->v[j] - 1) / 2, hi = lo;"),
+    "2N+2 theta without c^2/4": ("return a->zv ? (4.0 * a->N + 3.0) / 3.0 : a->N / 3.0;",
+                             "return a->N / (a->zv ? 0.75 : 3.0);"),
+    "2N+2 even velocities": ("a->v[j] = zv ? 2 * j - (2 * N + 1) : j - N;",
+                             "a->v[j] = zv ? 2 * j - 2 * N : j - N;"),
 }
 
 
@@ -47,6 +55,8 @@ def test_pins_catch_planted_mistake(name, tmp_path):
     r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q",
                         os.path.join(ROOT, "tests", "test_oracle_equilibrium.py"),
                         os.path.join(ROOT, "tests", "test_oracle_dynamics.py"),
-                        os.path.join(ROOT, "tests", "test_oracle_gradient.py")],
+                        os.path.join(ROOT, "tests", "test_oracle_gradient.py"),
+                        os.path.join(ROOT, "tests", "test_oracle_aniso.py"),
+                        os.path.join(ROOT, "tests", "test_oracle_zv.py")],
                        cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
     assert r.returncode != 0, f"pins did not catch mutation {name!r}"
