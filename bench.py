@@ -47,6 +47,12 @@ def workload(name):
         cfgs = [dict(dims=2, nx=c["nx"], ny=c["ny"], k=c["k"], x_level=c["x_level"], kn=kn,
                      u_wall_lo=c["u_wall_lo"], u_wall_hi=c["u_wall_hi"]) for kn in c["kn"]]
         label = "couette_d1q3xd1q17_1024x200_kn{0.01,0.1,1}"
+    elif name in ("couette_zv", "couette_zv_xy"):
+        c = inputs.COUETTE_ZV if name == "couette_zv" else inputs.COUETTE_ZV_XY
+        cfgs = [dict(dims=2, nx=c["nx"], ny=c["ny"], k=c["k"], x_level=c["x_level"],
+                     zv_axes=c["zv_axes"], kn=kn, u_wall_lo=c["u_wall_lo"],
+                     u_wall_hi=c["u_wall_hi"]) for kn in c["kn"]]
+        label = c["label"]
     elif name == "poiseuille":
         c = inputs.POISEUILLE
         cfgs = [dict(dims=2, nx=c["nx"], ny=c["ny"], k=c["k"], kn=kn, g=c["g"]) for kn in c["kn"]]
@@ -61,6 +67,15 @@ def workload(name):
     else:
         raise SystemExit(f"unknown workload {name}")
     return cfgs, label
+
+
+def lattice_axes(cfg):
+    """(N, NX, Q1y, Q1x, zv) of a 2D workload instance: levels along y and x,
+    velocities per axis and the mask of axes on the 2N+2 hierarchy."""
+    N = cfg["k"] + 1
+    NX = cfg.get("x_level") or N
+    zv = cfg.get("zv_axes", 0)
+    return N, NX, 2 * N + 1 + (1 if zv & 2 else 0), 2 * NX + 1 + (1 if zv & 1 else 0), zv
 
 
 KERNEL_SOURCES = ("glbm_device.cuh", "glbm_step2d.cuh", "glbm_step2d_pair.cuh",
@@ -237,9 +252,8 @@ def run_ours(args):
         return
     cfgs, label = workload(args.workload)
     dims = cfgs[0]["dims"]
-    N = cfgs[0]["k"] + 1
-    NX = cfgs[0].get("x_level") or N
-    Q = (2 * N + 1) * (2 * NX + 1) if dims == 2 else 2 * N + 1
+    N, NX, Q1y, Q1x, ZV = lattice_axes(cfgs[0])
+    Q = Q1y * Q1x if dims == 2 else 2 * N + 1
     nodes = cfgs[0]["nx"] * (cfgs[0]["ny"] if dims == 2 else 1)
     n_inst = len(cfgs)
     pops_per_step = Q * nodes * n_inst
@@ -252,7 +266,9 @@ def run_ours(args):
         if V == 2:
             return f"k_step2d_pair<{N},{G},{R}{',1' if NX != N else ''}>"
         t = "float" if prec == glbm.FP32_DEV else "double"
-        return f"k_step2d<{N},{t},{G},{R}{',1' if NX != N else ''}>"
+        tail = f",{NX},{1 if ZV & 2 else 0},{1 if ZV & 1 else 0}" if ZV else (
+            ",1" if NX != N else "")
+        return f"k_step2d<{N},{t},{G},{R}{tail}>"
 
     def timed(prec, steps, warmup):
         lat = glbm.Lattice([dict(c, prec=prec) for c in cfgs])
@@ -400,11 +416,12 @@ def precision_check(cfg, steps):
     dims = cfg["dims"]
     names = metrics.FIELDS_2D if dims == 2 else metrics.FIELDS_1D
     want = np.stack([runs[glbm.FP64][0][n] for n in names])
-    q1x = 2 * cfg["x_level"] + 1 if cfg.get("x_level") else None
+    q1x, zv = (lattice_axes(cfg)[3], cfg.get("zv_axes", 0)) if dims == 2 else (None, 0)
     errs = metrics.rel_errors(runs[glbm.FP32_DEV][0], want, dims=dims, F=runs[glbm.FP64][1],
-                              q1x=q1x)
+                              q1x=q1x, zv=zv)
     return {"steps": steps,
-            "instance": {k: cfg[k] for k in ("k", "x_level", "nx", "ny", "kn") if k in cfg},
+            "instance": {k: cfg[k] for k in ("k", "x_level", "zv_axes", "nx", "ny", "kn")
+                         if k in cfg},
             "fp32_vs_fp64_max_rel_err": errs, "max": max(errs.values())}
 
 
@@ -469,13 +486,13 @@ def cpu_baseline(name, budget_s=15.0, steps=None):
     N = c["k"] + 1
     dims = c["dims"]
     if dims == 2:
-        NX = c.get("x_level") or N
-        o = orc.Lattice(2, NX, N, c["nx"], c["ny"], orc.BC_WALLS if name != "periodic" else 2,
-                        orc.tau_from_kn(N, c["ny"], c["kn"]), c.get("u_wall_lo", 0.0),
-                        c.get("u_wall_hi", 0.0), c.get("g", 0.0))
+        _, NX, Q1y, Q1x, zv = lattice_axes(c)
+        o = orc.Lattice(2, NX, N, c["nx"], c["ny"], orc.BC_WALLS,
+                        orc.tau_from_kn(N, c["ny"], c["kn"], zv=zv & 2), c.get("u_wall_lo", 0.0),
+                        c.get("u_wall_hi", 0.0), c.get("g", 0.0), zv=zv)
         X = o.equilibrium(np.ones((c["ny"], c["nx"])), np.zeros((c["ny"], c["nx"])),
                           np.zeros((c["ny"], c["nx"])))
-        pops = (2 * N + 1) * (2 * NX + 1) * c["nx"] * c["ny"]
+        pops = Q1y * Q1x * c["nx"] * c["ny"]
     else:
         o = orc.Lattice(1, N, 0, c["nx"], 1, orc.BC_BOUNCEBACK, orc.tau_from_kn(N, c["nx"], c["kn"]))
         X = o.equilibrium(np.ones(c["nx"]), np.zeros(c["nx"]))
@@ -508,10 +525,11 @@ def run_reference(args):
     total_steps = args.steps + args.warmup
     if dims == 2:
         ny = c["ny"]
-        NX = c.get("x_level") or N
+        _, NX, Q1y, Q1x, zv = lattice_axes(c)
         mk = lambda nx: orc.Lattice(2, NX, N, nx, ny, orc.BC_WALLS,  # noqa: E731
-                                    orc.tau_from_kn(N, ny, c["kn"]), c.get("u_wall_lo", 0.0),
-                                    c.get("u_wall_hi", 0.0), c.get("g", 0.0))
+                                    orc.tau_from_kn(N, ny, c["kn"], zv=zv & 2),
+                                    c.get("u_wall_lo", 0.0), c.get("u_wall_hi", 0.0),
+                                    c.get("g", 0.0), zv=zv)
         o = mk(1)
         X = o.equilibrium(np.ones((ny, 1)), np.zeros((ny, 1)), np.zeros((ny, 1)))
         t0 = time.perf_counter()
@@ -520,7 +538,7 @@ def run_reference(args):
         cols = int(max(1, min(c["nx"], budget / total_steps / max(per_col, 1e-9))))
         o = mk(cols)
         X = o.equilibrium(np.ones((ny, cols)), np.zeros((ny, cols)), np.zeros((ny, cols)))
-        pops = (2 * N + 1) * (2 * NX + 1) * ny * cols
+        pops = Q1y * Q1x * ny * cols
         sample = f"{label}: strip of {cols} of {c['nx']} columns x {ny} rows, one instance, FP64"
     else:
         o = orc.Lattice(1, N, 0, c["nx"], 1, orc.BC_BOUNCEBACK, orc.tau_from_kn(N, c["nx"], c["kn"]))
@@ -551,7 +569,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=200)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="couette",
-                    choices=["couette", "couette_aniso", "poiseuille", "sod", "batched"])
+                    choices=["couette", "couette_aniso", "couette_zv", "couette_zv_xy",
+                             "poiseuille", "sod", "batched"])
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")

@@ -60,6 +60,11 @@ typedef enum {
     GLBM_FP32_DEV = 1        /* FP32 deviations f - W from the rest weights, compensated sums */
 } glbm_prec;
 
+typedef enum {
+    GLBM_ZV_X = 1,           /* x axis on the 2N+2 hierarchy (zero velocity removed, Sec. 4) */
+    GLBM_ZV_Y = 2            /* y axis on the 2N+2 hierarchy */
+} glbm_zv;
+
 /*
  * One lattice instance.
  *   dims      1 or 2.
@@ -77,11 +82,27 @@ typedef enum {
  *             heterogeneous batches or the adjoint.
  *   tau       relaxation time (> 0), used when kn <= 0.
  *   kn        Knudsen number of Eq. (kn), Sec. 5.2: when > 0 it sets
- *             tau = kn * H / sqrt(2 theta), theta = N/3, H = ny (2D) or nx (1D).
+ *             tau = kn * H / sqrt(2 theta), theta = N/3, H = ny (2D) or nx (1D);
+ *             theta = (4N+3)/3 when y is on the 2N+2 hierarchy.
  *   bc, prec  glbm_bc, glbm_prec.
  *   u_wall_lo, u_wall_hi  x-velocities of the walls (GLBM_BC_WALLS).
  *   g         body force along x (2D), added after relaxation as
  *             F_i = W_i xi_x g / theta_x (the linearised force of Sec. 5.4).
+ *   zv_axes   axes of a 2D lattice on the 2N+2 hierarchy of Sec. 4 (the zero
+ *             velocity removed, Eqs. maineq01_noball - maineq04_noball), a
+ *             mask of glbm_zv; 0 keeps the 2N+1 hierarchy. Such an axis has
+ *             the 2N+2 velocities (m + 1/2) c, m = -N-1..N, each with the mean
+ *             of the two neighbouring 2N+1 equilibria. It is written on a
+ *             lattice of half the spacing, so its velocities are the odd
+ *             integers v = 2i - (2N+1) of index i = 0..2N+1 and its lattice
+ *             temperature is (4N+3)/3 (Eq. temp_2N2); speeds along it (wall
+ *             speeds, u) are in those units. Compiled: GLBM_ZV_Y with
+ *             x_level 1 (D1Q3 x D1Q(2N+2), the channel models G-D1Q6 x D1Q3,
+ *             G-D1Q8 x D1Q3 of Sec. 5) and GLBM_ZV_X | GLBM_ZV_Y on an
+ *             isotropic lattice (D2Q(2N+2)^2); other masks return
+ *             GLBM_E_UNSUPPORTED. Walls then need ny >= 2N+1. Velocity q of
+ *             the layout is iy Q_x + ix with the velocity indices of the axes.
+ *             Not for heterogeneous batches or the adjoint.
  */
 typedef struct {
     int dims;
@@ -94,6 +115,7 @@ typedef struct {
     int prec;
     double u_wall_lo, u_wall_hi;
     double g;
+    int zv_axes;
 } glbm_config;
 
 /*

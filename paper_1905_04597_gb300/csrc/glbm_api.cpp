@@ -89,6 +89,7 @@ static void dev_free(const DevAlloc &A, void *p, cudaStream_t s)
 // ---------------------------------------------------------------------------
 struct Geo {
     int N, NX, Lx, Ly, pitch, Q;  // N: level along y (and x), NX: level along x
+    int zv;           // axes on the 2N+2 hierarchy (GLBM_ZV_X | GLBM_ZV_Y)
     long long plane;  // elements per velocity plane
     long long off;    // element offset of the instance in the pool
     long long nodes() const { return (long long)Lx * Ly; }
@@ -101,7 +102,8 @@ struct glbm_ctx {
     size_t elem = 8;
     std::vector<Geo> geo;
     std::vector<glbm_config> cfg;
-    std::vector<AxisTable> tabs;  // index N (1..GLBM_MAXN)
+    std::vector<AxisTable> tabs;     // index N (1..GLBM_MAXN)
+    std::vector<AxisTable> tabs_zv;  // the same levels on the 2N+2 hierarchy
     std::vector<InstParams> h_ip;
     std::vector<double> tau;
     DevAlloc A{};
@@ -132,23 +134,50 @@ static const int kGraphChunk = 64;  // steps per captured graph (even: keeps buf
 
 static size_t bytes_state(const glbm_ctx *c) { return (size_t)c->pool_elems * c->elem; }
 
+// Tables of the y axis (level N) and the x axis (level NX) of a geometry.
+static const AxisTable &tab_y(const glbm_ctx *c, const Geo &g)
+{
+    return (g.zv & GLBM_ZV_Y) ? c->tabs_zv[g.N] : c->tabs[g.N];
+}
+static const AxisTable &tab_x(const glbm_ctx *c, const Geo &g)
+{
+    return (g.zv & GLBM_ZV_X) ? c->tabs_zv[g.NX] : c->tabs[g.NX];
+}
+
+// Lattice temperature of one axis: N/3, or (4N+3)/3 on the 2N+2 hierarchy
+// (Eq. temp_2N2 in units of half the lattice spacing).
+static double axis_theta(int N, bool zv) { return zv ? (4.0 * N + 3.0) / 3.0 : N / 3.0; }
+
 static void fill_inst(const glbm_ctx *c, const glbm_config &cfg, const Geo &g, InstParams &ip,
                       double tau)
 {
     memset(&ip, 0, sizeof(ip));
     const int N = g.N, NX = g.NX;
-    const AxisTable &tab = c->tabs[N];  // y axis
-    const double theta_x = NX / 3.0;
+    const AxisTable &tab = tab_y(c, g);
+    const double theta_x = axis_theta(NX, (g.zv & GLBM_ZV_X) != 0);
     ip.omega = 1.0 / (tau + 0.5);
     ip.g_theta = c->dims == 2 ? cfg.g / theta_x : 0.0;
     double den = 0.0;  // the wall's normaliser runs over the y velocities
-    for (int n = 1; n <= N; ++n) den += n * tab.W[n + N];
+    for (int i = 0; i < ax_q(tab); ++i)
+        if (ax_vel(tab, i) > 0) den += ax_vel(tab, i) * tab.W[i];
     ip.inv_den = 1.0 / den;
-    // E^x_n(u_w) of the x axis from its coefficient table (FP64 Horner)
+    if (g.zv & GLBM_ZV_X) {
+        // E^x_i(u_w) of a 2N+2 x axis by Horner on its table
+        const AxisTable &tx = tab_x(c, g);
+        for (int i = 0; i < ax_q(tx); ++i) {
+            const double dlo = glbm_eq_dev_host(tx, cfg.u_wall_lo, i);
+            const double dhi = glbm_eq_dev_host(tx, cfg.u_wall_hi, i);
+            ip.ew_lo[i] = tx.W[i] + dlo;
+            ip.ew_hi[i] = tx.W[i] + dhi;
+            ip.dw_lo_f[i] = (float)dlo;
+            ip.dw_hi_f[i] = (float)dhi;
+        }
+    }
+    // E^x_n(u_w) of a 2N+1 x axis from its coefficient table (FP64 Horner)
     double full[GLBM_MAXQ1 * GLBM_MAXQ1];
     AxisTable tmp;
     glbm_build_axis_table(NX, &tmp, full);
-    const int Q1 = 2 * NX + 1;
+    const int Q1 = (g.zv & GLBM_ZV_X) ? 0 : 2 * NX + 1;
     for (int n = 0; n < Q1; ++n) {
         double elo = 0.0, ehi = 0.0;
         for (int j = Q1 - 1; j >= 0; --j) {
@@ -194,6 +223,15 @@ static glbm_status validate(const glbm_config &c)
                     "anisotropic lattices take D1Q3 along x (x_level 1) or the level of k");
     if (c.x_level != 0 && c.dims != 2) return fail(GLBM_E_INVAL, "x_level applies to 2D lattices");
     const int NX = c.x_level > 0 ? c.x_level : N;
+    const int zv = c.zv_axes;
+    if (zv < 0 || zv > (GLBM_ZV_X | GLBM_ZV_Y))
+        return fail(GLBM_E_INVAL, "zv_axes must be a mask of GLBM_ZV_X and GLBM_ZV_Y (got %d)", zv);
+    if (zv != 0 && c.dims != 2) return fail(GLBM_E_INVAL, "the 2N+2 hierarchy applies to 2D lattices");
+    if (zv != 0 && !(zv == GLBM_ZV_Y && NX == 1) &&
+        !(zv == (GLBM_ZV_X | GLBM_ZV_Y) && NX == N))
+        return fail(GLBM_E_UNSUPPORTED,
+                    "the 2N+2 hierarchy is compiled along y with D1Q3 along x (x_level 1) "
+                    "or along both axes of an isotropic lattice");
     if (c.nx < 1 || (c.dims == 2 && c.ny < 1)) return fail(GLBM_E_INVAL, "nx, ny must be >= 1");
     if (c.prec != GLBM_FP64 && c.prec != GLBM_FP32_DEV) return fail(GLBM_E_INVAL, "bad precision %d", c.prec);
     if (c.dims == 1) {
@@ -204,10 +242,13 @@ static glbm_status validate(const glbm_config &c)
     } else {
         if (c.bc != GLBM_BC_WALLS && c.bc != GLBM_BC_PERIODIC)
             return fail(GLBM_E_INVAL, "2D lattices take GLBM_BC_WALLS or GLBM_BC_PERIODIC");
-        if (c.bc == GLBM_BC_WALLS && c.ny < N) return fail(GLBM_E_INVAL, "walls need ny >= k+1");
+        const int vmax = (zv & GLBM_ZV_Y) ? 2 * N + 1 : N;  // fastest y velocity
+        if (c.bc == GLBM_BC_WALLS && c.ny < vmax)
+            return fail(GLBM_E_INVAL, "walls need ny >= %d (the fastest y velocity)", vmax);
     }
     if (!(c.kn > 0.0) && !(c.tau > 0.0)) return fail(GLBM_E_INVAL, "tau must be > 0 (or kn > 0)");
-    const double umax = sqrt(2.0 / 3.0) * NX;  // the wall speeds are x velocities
+    // the wall speeds are x velocities (half-spacing units on a 2N+2 x axis)
+    const double umax = sqrt(2.0 / 3.0) * NX * ((zv & GLBM_ZV_X) ? 2.0 : 1.0);
     if (!(fabs(c.u_wall_lo) < umax) || !(fabs(c.u_wall_hi) < umax) || !isfinite(c.g))
         return fail(GLBM_E_INVAL, "wall speed outside the positivity domain or bad force");
     return GLBM_OK;
@@ -217,7 +258,7 @@ static double tau_of(const glbm_config &c)
 {
     if (c.kn > 0.0) {
         const int N = c.k + 1;
-        const double theta = N / 3.0;
+        const double theta = axis_theta(N, c.dims == 2 && (c.zv_axes & GLBM_ZV_Y));
         const double H = c.dims == 2 ? c.ny : c.nx;
         return c.kn * H / sqrt(2.0 * theta);  // Eq. (kn), nu = theta tau
     }
@@ -232,8 +273,9 @@ static Geo make_geo(const glbm_config &c)
     g.Lx = c.nx;
     g.Ly = c.dims == 2 ? c.ny : 1;
     g.pitch = ((g.Lx + 31) / 32) * 32;
-    const int Q1 = 2 * g.N + 1;
-    g.Q = c.dims == 2 ? Q1 * (2 * g.NX + 1) : Q1;
+    g.zv = c.dims == 2 ? c.zv_axes : 0;
+    const int Q1 = 2 * g.N + 1 + ((g.zv & GLBM_ZV_Y) ? 1 : 0);
+    g.Q = c.dims == 2 ? Q1 * (2 * g.NX + 1 + ((g.zv & GLBM_ZV_X) ? 1 : 0)) : Q1;
     g.plane = (long long)g.Ly * g.pitch;
     g.off = 0;
     return g;
@@ -266,8 +308,8 @@ static AuxArgs aux_args(const glbm_ctx *c, int inst)
     const Geo &g = c->geo[inst];
     AuxArgs a;
     memset(&a, 0, sizeof(a));
-    a.tab = c->tabs[g.N];
-    a.tabx = c->tabs[g.NX];
+    a.tab = tab_y(c, g);
+    a.tabx = tab_x(c, g);
     a.ip = c->d_ip + inst;
     a.dims = c->dims;
     a.prec = c->prec;
@@ -318,7 +360,11 @@ static glbm_status finish_create(glbm_ctx *c, const glbm_config *cfgs, int n, vo
     c->stream = (cudaStream_t)stream;
     c->cfg.assign(cfgs, cfgs + n);
     c->tabs.resize(GLBM_MAXN + 1);
-    for (int N = 1; N <= GLBM_MAXN; ++N) glbm_build_axis_table(N, &c->tabs[N], nullptr);
+    c->tabs_zv.resize(GLBM_MAXN + 1);
+    for (int N = 1; N <= GLBM_MAXN; ++N) {
+        glbm_build_axis_table(N, &c->tabs[N], nullptr);
+        glbm_build_axis_table_zv(N, &c->tabs_zv[N]);
+    }
     // pool layout: instances back to back, each starting on a 256-byte boundary
     c->geo.resize(n);
     long long off = 0;
@@ -388,7 +434,8 @@ extern "C" glbm_status glbm_create(const glbm_config *cfgs, int n, void *stream,
         if (st != GLBM_OK) return st;
         const glbm_config &a = cfgs[0], &b = cfgs[i];
         if (a.dims != b.dims || a.nx != b.nx || (a.dims == 2 && a.ny != b.ny) || a.k != b.k ||
-            a.bc != b.bc || a.prec != b.prec || make_geo(a).NX != make_geo(b).NX)
+            a.bc != b.bc || a.prec != b.prec || make_geo(a).NX != make_geo(b).NX ||
+            make_geo(a).zv != make_geo(b).zv)
             return fail(GLBM_E_UNSUPPORTED,
                         "instances differ in geometry; use glbm_batch_create for mixed batches");
     }
@@ -404,13 +451,19 @@ extern "C" glbm_status glbm_create(const glbm_config *cfgs, int n, void *stream,
     return GLBM_OK;
 }
 
-// Shape of the tiles of level N in this context.
 // Whether the context steps an anisotropic product (D1Q3 along x).
 static bool is_x1(const glbm_ctx *c) { return c->dims == 2 && c->geo[0].NX != c->geo[0].N; }
+// Whether it steps a lattice with an axis on the 2N+2 hierarchy, and which kind.
+static bool is_zv(const glbm_ctx *c) { return c->dims == 2 && c->geo[0].zv != 0; }
+static int zv_kind(const glbm_ctx *c)
+{
+    return c->geo[0].zv == GLBM_ZV_Y ? GLBM_ZVK_X1 : GLBM_ZVK_XY;
+}
 
 // Candidate tile shapes of level N for this context's lattices.
 static int ctx_tile_shapes(const glbm_ctx *c, int N, TileShape *out)
 {
+    if (is_zv(c)) return glbm_tile_shapes_zv(N, zv_kind(c), c->prec, out);
     return is_x1(c) ? glbm_tile_shapes_x1(N, c->prec, out) : glbm_tile_shapes(N, c->prec, out);
 }
 
@@ -458,8 +511,9 @@ extern "C" glbm_status glbm_batch_create(const glbm_config *cfgs, int n, void *s
         glbm_status st = validate(cfgs[i]);
         if (st != GLBM_OK) return st;
         if (cfgs[i].dims != 2) return fail(GLBM_E_UNSUPPORTED, "heterogeneous batches are 2D");
-        if (make_geo(cfgs[i]).NX != cfgs[i].k + 1)
-            return fail(GLBM_E_UNSUPPORTED, "heterogeneous batches take isotropic lattices");
+        if (make_geo(cfgs[i]).NX != cfgs[i].k + 1 || cfgs[i].zv_axes != 0)
+            return fail(GLBM_E_UNSUPPORTED,
+                        "heterogeneous batches take isotropic lattices of the 2N+1 hierarchy");
         if (cfgs[i].prec != GLBM_FP32_DEV)
             return fail(GLBM_E_UNSUPPORTED,
                         "heterogeneous batches store FP32 deviations (FP64 instances go through "
@@ -593,8 +647,8 @@ static Step2DArgs step_args(const glbm_ctx *c, int from)
     const Geo &g = c->geo[0];
     Step2DArgs a;
     memset(&a, 0, sizeof(a));
-    a.tab = c->tabs[g.N];
-    a.tabx = c->tabs[g.NX];
+    a.tab = tab_y(c, g);
+    a.tabx = tab_x(c, g);
     a.fin = c->buf[from];
     a.fout = c->buf[1 - from];
     a.ip = c->d_ip;
@@ -640,6 +694,7 @@ static cudaError_t launch_one_2d(const glbm_ctx *c, int from, cudaStream_t s)
     if (c->hetero) return glbm_launch_batched_f32(batch_args(c, from), s);
     const Step2DArgs a = step_args(c, from);
     const int N = c->geo[0].N;
+    if (is_zv(c)) return glbm_launch_step2d_zv(N, zv_kind(c), c->prec, c->tile[N], a, c->n_inst, s);
     if (is_x1(c)) return glbm_launch_step2d_x1(N, c->prec, c->tile[N], a, c->n_inst, s);
     return c->prec == GLBM_FP64 ? glbm_launch_step2d_f64(N, c->tile[N], a, c->n_inst, s)
                                 : glbm_launch_step2d_f32(N, c->tile[N], a, c->n_inst, s);
@@ -832,6 +887,8 @@ static void fill_header(const glbm_ctx *c, CkptHeader &h)
         crc = crc32_update(crc, (const unsigned char *)geo, sizeof(geo));
         const int nx_level = make_geo(g).NX;  // anisotropic lattices add their x level
         if (nx_level != g.k + 1) crc = crc32_update(crc, (const unsigned char *)&nx_level, sizeof(int));
+        const int zv = make_geo(g).zv;  // and 2N+2 lattices their axes
+        if (zv != 0) crc = crc32_update(crc, (const unsigned char *)&zv, sizeof(int));
     }
     h.config_crc = crc;
 }
@@ -895,6 +952,7 @@ static cudaError_t launch_2d_between(const glbm_ctx *c, const void *fin, void *f
     a.fin = fin;
     a.fout = fout;
     const int N = c->geo[0].N;
+    if (is_zv(c)) return glbm_launch_step2d_zv(N, zv_kind(c), c->prec, c->tile[N], a, c->n_inst, s);
     if (is_x1(c)) return glbm_launch_step2d_x1(N, c->prec, c->tile[N], a, c->n_inst, s);
     return c->prec == GLBM_FP64 ? glbm_launch_step2d_f64(N, c->tile[N], a, c->n_inst, s)
                                 : glbm_launch_step2d_f32(N, c->tile[N], a, c->n_inst, s);
@@ -924,7 +982,8 @@ extern "C" glbm_status glbm_adjoint_flowrate(glbm_ctx *c, int64_t steps, int64_t
     if (!c || !J || !dJ_dtau || !dJ_dg) return fail(GLBM_E_INVAL, "null argument");
     if (c->dims != 2 || c->hetero)
         return fail(GLBM_E_UNSUPPORTED, "the adjoint takes 2D uniform contexts");
-    if (is_x1(c)) return fail(GLBM_E_UNSUPPORTED, "the adjoint takes isotropic lattices");
+    if (is_x1(c) || is_zv(c))
+        return fail(GLBM_E_UNSUPPORTED, "the adjoint takes isotropic lattices of the 2N+1 hierarchy");
     if (steps < 1 || ckpt_every < 1) return fail(GLBM_E_INVAL, "steps and ckpt_every must be >= 1");
     const int64_t K = ckpt_every < steps ? ckpt_every : steps;
     const int64_t nseg = (steps + K - 1) / K;
@@ -1066,8 +1125,7 @@ extern "C" glbm_status glbm_set_tiles(glbm_ctx *c, const int *tiles)
     if (!c || !tiles) return fail(GLBM_E_INVAL, "null argument");
     TileShape sh[GLBM_MAX_TILES];
     for (int k = 0; k < GLBM_LEVELS; ++k)
-        if (tiles[k] < -1 || tiles[k] >= (is_x1(c) ? glbm_tile_shapes_x1(k + 1, c->prec, sh)
-                                                    : glbm_tile_count(k, (glbm_prec)c->prec)))
+        if (tiles[k] < -1 || tiles[k] >= ctx_tile_shapes(c, k + 1, sh))
             return fail(GLBM_E_INVAL, "tile index %d out of range for k=%d", tiles[k], k);
     for (int k = 0; k < GLBM_LEVELS; ++k)
         if (tiles[k] >= 0) c->tile[k + 1] = tiles[k];

@@ -10,19 +10,22 @@
 
 namespace {
 
-// E_n(u) - W_n at runtime level t.N (FP64 Horner on the coefficient table).
-__device__ double eq_dev_rt(const AxisTable &t, double u, int n)
+// E_i(u) - W_i of velocity index i at runtime level t.N (FP64 Horner on the
+// coefficient table; on the 2N+2 hierarchy the velocity is +-(2m+1)).
+__device__ double eq_dev_rt(const AxisTable &t, double u, int i)
 {
     const int N = t.N;
+    const int n = ax_vel(t, i);
     const int an = n < 0 ? -n : n;
+    const int m = t.zv ? (an - 1) / 2 : an;
     const double v = u * u;
-    double ae = t.Ce[an][N];
-    for (int i = N - 1; i >= 1; --i) ae = fma(ae, v, t.Ce[an][i]);
+    double ae = t.Ce[m][N];
+    for (int k = N - 1; k >= 1; --k) ae = fma(ae, v, t.Ce[m][k]);
     ae *= v;
     double bo = 0.0;
     if (an > 0) {
-        bo = t.Co[an][N - 1];
-        for (int i = N - 2; i >= 0; --i) bo = fma(bo, v, t.Co[an][i]);
+        bo = t.Co[m][N - 1];
+        for (int k = N - 2; k >= 0; --k) bo = fma(bo, v, t.Co[m][k]);
     }
     return n >= 0 ? fma(u, bo, ae) : fma(-u, bo, ae);
 }
@@ -34,12 +37,12 @@ __device__ __forceinline__ double load_full(const AuxArgs &a, const void *f, lon
     return (double)static_cast<const float *>(f)[idx];
 }
 
-// rest weight of flat velocity q (q = iy (2NX+1) + ix in 2D)
+// rest weight of flat velocity q (q = iy Qx + ix in 2D)
 __device__ __forceinline__ double rest_weight(const AuxArgs &a, int q)
 {
     if (a.dims == 1) return a.tab.W[q];
-    const int Q1x = 2 * a.NX + 1;
-    return a.tab.W[q / Q1x] * a.tabx.W[q % Q1x];
+    const int Qx = ax_q(a.tabx);
+    return a.tab.W[q / Qx] * a.tabx.W[q % Qx];
 }
 
 __global__ void k_set_equilibrium(const __grid_constant__ AuxArgs a, void *f, int inst,
@@ -50,19 +53,18 @@ __global__ void k_set_equilibrium(const __grid_constant__ AuxArgs a, void *f, in
     const int y = blockIdx.y;
     if (x >= a.Lx) return;
     // 1D: the only axis is x, with table tab and level N
-    const int N = a.N, NX = a.dims == 2 ? a.NX : a.N;
     const AxisTable &tx = a.dims == 2 ? a.tabx : a.tab;
-    const int Q1x = 2 * NX + 1;
+    const int Q1x = ax_q(tx);
     const long long node = (long long)y * a.Lx + x;
     const double r = rho[node], u = ux[node], v = a.dims == 2 ? uy[node] : 0.0;
     const long long base = (long long)inst * a.inst_stride + (long long)y * a.pitch + x;
-    const int Qy = a.dims == 2 ? 2 * N + 1 : 1;
+    const int Qy = a.dims == 2 ? ax_q(a.tab) : 1;
     for (int iy = 0; iy < Qy; ++iy) {
         const double wy = a.dims == 2 ? a.tab.W[iy] : 1.0;
-        const double dy = a.dims == 2 ? eq_dev_rt(a.tab, v, iy - N) : 0.0;
+        const double dy = a.dims == 2 ? eq_dev_rt(a.tab, v, iy) : 0.0;
         for (int ix = 0; ix < Q1x; ++ix) {
             const double wx = tx.W[ix];
-            const double dx = eq_dev_rt(tx, u, ix - NX);
+            const double dx = eq_dev_rt(tx, u, ix);
             const long long idx = base + (long long)(iy * Q1x + ix) * a.plane;
             if (a.prec == GLBM_FP64) {
                 static_cast<double *>(f)[idx] = r * (wx + dx) * (wy + dy);
@@ -129,7 +131,7 @@ __device__ double pulled(const AuxArgs &a, const InstParams &ip, const void *f, 
         if (a.prec != GLBM_FP64) v += a.tab.W[q];
         return v;
     }
-    const int nx = ix - a.NX, ny = iy - N;
+    const int nx = ax_vel(a.tabx, ix), ny = ax_vel(a.tab, iy);
     const int xs = wrap_index(x - nx, a.Lx);
     int ys = y - ny;
     if (a.bc == GLBM_BC_WALLS) {
@@ -138,24 +140,26 @@ __device__ double pulled(const AuxArgs &a, const InstParams &ip, const void *f, 
     } else {
         ys = wrap_index(ys, a.Ly);
     }
-    const int q = iy * (2 * a.NX + 1) + ix;
+    const int q = iy * ax_q(a.tabx) + ix;
     double v = load_full(a, f, ibase + (long long)q * a.plane + (long long)ys * a.pitch + xs, q);
     if (a.prec != GLBM_FP64) v += a.tab.W[iy] * a.tabx.W[ix];
     return v;
 }
 
-// Wall density of column x: absorbed mass / sum_{n>0} n W_n (FP64).
+// Wall density of column x: absorbed mass / sum_{v>0} v W_v (FP64).
 __device__ double wall_density(const AuxArgs &a, const InstParams &ip, const void *f,
                                long long ibase, int x, bool lower)
 {
-    const int N = a.N, Q1x = 2 * a.NX + 1;
+    const int N = a.N, Q1x = ax_q(a.tabx), zv = a.tab.zv;
     double D = 0.0;
-    for (int aa = 1; aa <= N; ++aa) {
+    // velocity magnitudes |v| = m (2N+1) or 2m+1 (2N+2) in increasing order
+    for (int m = zv ? 0 : 1; m <= N; ++m) {
+        const int aa = zv ? 2 * m + 1 : m;
         for (int k = 0; k < aa; ++k) {
-            const int iy = lower ? N - aa : N + aa;
+            const int iy = lower ? N - m : (zv ? N + 1 + m : N + m);
             const int row = lower ? k : a.Ly - 1 - k;
             for (int ix = 0; ix < Q1x; ++ix) {
-                const int xs = wrap_index(x - (ix - a.NX), a.Lx);
+                const int xs = wrap_index(x - ax_vel(a.tabx, ix), a.Lx);
                 const int q = iy * Q1x + ix;
                 double v = load_full(a, f, ibase + (long long)q * a.plane + (long long)row * a.pitch + xs, q);
                 if (a.prec != GLBM_FP64) v += a.tab.W[iy] * a.tabx.W[ix];
@@ -174,30 +178,31 @@ __global__ void k_moments(const __grid_constant__ AuxArgs a, const void *f, int 
     const int y = blockIdx.y;
     if (x >= a.Lx) return;
     const InstParams &ip = a.ip[inst];
-    const int N = a.N, NX = a.dims == 2 ? a.NX : a.N;
-    const int Q1x = 2 * NX + 1;
-    const int Qy = a.dims == 2 ? 2 * N + 1 : 1;
+    const AxisTable &tx = a.dims == 2 ? a.tabx : a.tab;
+    const int Q1x = ax_q(tx);
+    const int Qy = a.dims == 2 ? ax_q(a.tab) : 1;
+    const int vmax = a.tab.zv ? 2 * a.N + 1 : a.N;  // fastest y velocity
     const long long ibase = (long long)inst * a.inst_stride;
     double rw_lo = 0.0, rw_hi = 0.0;
     if (a.dims == 2 && a.bc == GLBM_BC_WALLS) {
-        if (y < N) rw_lo = wall_density(a, ip, f, ibase, x, true);
-        if (y >= a.Ly - N) rw_hi = wall_density(a, ip, f, ibase, x, false);
+        if (y < vmax) rw_lo = wall_density(a, ip, f, ibase, x, true);
+        if (y >= a.Ly - vmax) rw_hi = wall_density(a, ip, f, ibase, x, false);
     }
     double rho = 0.0, jx = 0.0, jy = 0.0;
     for (int iy = 0; iy < Qy; ++iy)
         for (int ix = 0; ix < Q1x; ++ix) {
             const double v = pulled(a, ip, f, ibase, x, y, ix, iy, rw_lo, rw_hi);
             rho += v;
-            jx += (ix - NX) * v;
-            jy += (a.dims == 2 ? iy - N : 0) * v;
+            jx += ax_vel(tx, ix) * v;
+            jy += (a.dims == 2 ? ax_vel(a.tab, iy) : 0) * v;
         }
     const double ux = jx / rho, uy = jy / rho;
     double e2 = 0.0, qx = 0.0, qy = 0.0, sxy = 0.0;
     for (int iy = 0; iy < Qy; ++iy)
         for (int ix = 0; ix < Q1x; ++ix) {
             const double v = pulled(a, ip, f, ibase, x, y, ix, iy, rw_lo, rw_hi);
-            const double dx = (ix - NX) - ux;
-            const double dy = a.dims == 2 ? (iy - N) - uy : 0.0;
+            const double dx = ax_vel(tx, ix) - ux;
+            const double dy = a.dims == 2 ? ax_vel(a.tab, iy) - uy : 0.0;
             const double d2 = dx * dx + dy * dy;
             e2 += d2 * v;
             qx += dx * d2 * v;
@@ -415,8 +420,7 @@ cudaError_t glbm_launch_set_equilibrium(const AuxArgs &a, void *f, int inst, con
 cudaError_t glbm_launch_set_populations(const AuxArgs &a, void *f, int inst, const double *src,
                                         cudaStream_t s)
 {
-    const int Q1 = 2 * a.N + 1;
-    dim3 grid((a.Lx + 127) / 128, a.Ly, a.dims == 2 ? Q1 * (2 * a.NX + 1) : Q1);
+    dim3 grid((a.Lx + 127) / 128, a.Ly, a.dims == 2 ? ax_q(a.tab) * ax_q(a.tabx) : ax_q(a.tab));
     k_set_populations<<<grid, 128, 0, s>>>(a, f, inst, src);
     return cudaGetLastError();
 }
@@ -424,8 +428,7 @@ cudaError_t glbm_launch_set_populations(const AuxArgs &a, void *f, int inst, con
 cudaError_t glbm_launch_get_populations(const AuxArgs &a, const void *f, int inst, double *dst,
                                         cudaStream_t s)
 {
-    const int Q1 = 2 * a.N + 1;
-    dim3 grid((a.Lx + 127) / 128, a.Ly, a.dims == 2 ? Q1 * (2 * a.NX + 1) : Q1);
+    dim3 grid((a.Lx + 127) / 128, a.Ly, a.dims == 2 ? ax_q(a.tab) * ax_q(a.tabx) : ax_q(a.tab));
     k_get_populations<<<grid, 128, 0, s>>>(a, f, inst, dst);
     return cudaGetLastError();
 }

@@ -34,8 +34,9 @@ __device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(
 
 // Deviation of the level-N equilibrium from the rest weights, for one |n|:
 // Ae_n(v) (even powers >= 2) and Bo_n(v) (odd powers / u), v = u^2, so that
-// E_{+n}(u) - W_n = Ae + u Bo and E_{-n}(u) - W_n = Ae - u Bo.
-template <int N, typename T>
+// E_{+n}(u) - W_n = Ae + u Bo and E_{-n}(u) - W_n = Ae - u Bo. On the 2N+2
+// hierarchy (Z = 1) n is the magnitude index m of the velocities +-(2m+1).
+template <int N, typename T, int Z = 0>
 __device__ __forceinline__ void eq_parts(const AxisTable &t, int n, T v, T &ae, T &bo)
 {
     using A = TabAcc<T>;
@@ -43,7 +44,7 @@ __device__ __forceinline__ void eq_parts(const AxisTable &t, int n, T v, T &ae, 
 #pragma unroll
     for (int i = N - 1; i >= 1; --i) a = fma(a, v, A::Ce(t, n, i));
     ae = mul_rn(a, v);
-    if (n == 0) {
+    if (n == 0 && !Z) {
         bo = T(0);  // E_0 is even in u
     } else if (A::HILO) {
         // linear coefficient as hi + lo: the low part joins before the high part
@@ -64,20 +65,22 @@ __device__ __forceinline__ void eq_parts(const AxisTable &t, int n, T v, T &ae, 
     }
 }
 
-// d[n+N] = E_n(u) - W_n for every n = -N..N.
-template <int N, typename T>
-__device__ __forceinline__ void eq_dev_all(const AxisTable &t, T u, T (&d)[2 * N + 1])
+// d[i] = E_i(u) - W_i for every velocity index i of the axis (i = n + N on
+// the 2N+1 hierarchy).
+template <int N, typename T, int Z = 0>
+__device__ __forceinline__ void eq_dev_all(const AxisTable &t, T u, T (&d)[2 * N + 1 + Z])
 {
+    using AV = AxisVel<N, Z>;
     const T v = u * u;
 #pragma unroll
     for (int n = 0; n <= N; ++n) {
         T ae, bo;
-        eq_parts<N, T>(t, n, v, ae, bo);
-        if (n == 0) {
+        eq_parts<N, T, Z>(t, n, v, ae, bo);
+        if (n == 0 && !Z) {
             d[N] = ae;
         } else {
-            d[N + n] = fma(u, bo, ae);
-            d[N - n] = fma(-u, bo, ae);
+            d[AV::ipos(n)] = fma(u, bo, ae);
+            d[AV::ineg(n)] = fma(-u, bo, ae);
         }
     }
 }

@@ -12,6 +12,7 @@ glbm_status glbm_set_error(glbm_status st, const char *fmt, ...);
 
 #define GLBM_MAXN 8                       // highest level N = k + 1 compiled
 #define GLBM_MAXQ1 (2 * GLBM_MAXN + 1)    // velocities per axis at GLBM_MAXN
+#define GLBM_MAXQA (2 * GLBM_MAXN + 2)    // the same on the 2N+2 hierarchy
 
 // Equilibrium of one axis at level N in lattice units (velocities -N..N,
 // temperature N/3), as a polynomial in the velocity u:
@@ -23,19 +24,52 @@ glbm_status glbm_set_error(glbm_status st, const char *fmt, ...);
 //   E_{+-n}(u) = W_n + Ae_n(v) +- u Bo_n(v),
 //   Ae_n(v) = sum_{i=1..N} Ce[n][i] v^i,  Bo_n(v) = sum_{i=0..N-1} Co[n][i] v^i,
 // and W_n = C[n][0] the rest weight.
+//
+// On the 2N+2 hierarchy (Sec. 4, zero velocity removed; zv = 1) the axis has
+// the 2N+2 velocities (m + 1/2) c, written as the odd integers v = +-(2m+1),
+// m = 0..N, on a lattice of spacing c/2, whose equilibria are the means of the
+// 2N+1 equilibria at the neighbouring velocities m c and (m+1) c
+// (Eqs. maineq01_noball - maineq04_noball). They are again polynomials of
+// degree 2N in u with E_{-v}(u) = E_v(-u), so the same split holds with the
+// magnitude index m in place of n (and no velocity without a mirror):
+//   E_{+-(2m+1)}(u) = W_m + Ae_m(v) +- u Bo_m(v).
+// Velocity index i of the axis: v = i - N (2N+1 velocities) or
+// v = 2i - (2N+1) (2N+2 velocities); W and WN are indexed by i.
 struct AxisTable {
     int N;
-    int pad_;
-    double W[GLBM_MAXQ1];                    // index n + N
-    double WN[GLBM_MAXQ1];                   // n W_n
+    int zv;                                  // 1: the 2N+2 hierarchy
+    double W[GLBM_MAXQA];                    // by velocity index i
+    double WN[GLBM_MAXQA];                   // v_i W_i
     double Ce[GLBM_MAXN + 1][GLBM_MAXN + 1];  // [n][i] = C[n][2i], n = 0..N
     double Co[GLBM_MAXN + 1][GLBM_MAXN];      // [n][i] = C[n][2i+1]
-    float Wf[GLBM_MAXQ1];
-    float WNf[GLBM_MAXQ1];
+    float Wf[GLBM_MAXQA];
+    float WNf[GLBM_MAXQA];
     float Cef[GLBM_MAXN + 1][GLBM_MAXN + 1];
     float Cof[GLBM_MAXN + 1][GLBM_MAXN];
     float Co1lo[GLBM_MAXN + 1];  // C[n][1] - Cof[n][0]: low part of the linear coefficient
 };
+
+// Velocities of one axis at compile time: level N, Z = 1 on the 2N+2 hierarchy.
+// m is the magnitude index of a +- pair (the zero velocity of the 2N+1
+// hierarchy is m = 0 with ipos(0) == ineg(0)).
+template <int N, int Z>
+struct AxisVel {
+    static constexpr int Q = 2 * N + 1 + Z;        // velocities
+    static constexpr int VMAX = Z ? 2 * N + 1 : N;  // largest |v|
+    static constexpr int M0 = Z ? 0 : 1;           // first m with a +- pair
+    static constexpr int NPAIR = Z ? (N + 1) * (N + 1) : N * (N + 1) / 2;  // sum of |v| over v > 0
+    __host__ __device__ static constexpr int vel(int i) { return Z ? 2 * i - (2 * N + 1) : i - N; }
+    __host__ __device__ static constexpr int vmag(int m) { return Z ? 2 * m + 1 : m; }
+    __host__ __device__ static constexpr int ipos(int m) { return Z ? N + 1 + m : N + m; }
+    __host__ __device__ static constexpr int ineg(int m) { return N - m; }
+};
+
+// The same at run time from a table.
+__host__ __device__ inline int ax_q(const AxisTable &t) { return 2 * t.N + 1 + t.zv; }
+__host__ __device__ inline int ax_vel(const AxisTable &t, int i)
+{
+    return t.zv ? 2 * i - (2 * t.N + 1) : i - t.N;
+}
 
 // Host: build the table of level N by N exact polynomial convolutions
 // (the N-fold summation of D1Q3, Sec. 2). Also returns the full C[n][j]
@@ -46,6 +80,13 @@ struct AxisTable {
 // With plainly rounded coefficients the residual (up to several ulps) acts as
 // a mass and momentum source of the same sign at every step of a steady flow.
 void glbm_build_axis_table(int N, AxisTable *t, double *full);
+// Host: the table of level N on the 2N+2 hierarchy (zv = 1), from the exact
+// 2N+1 coefficients: C'_v[j] = (C_m[j] + C_{m+1}[j]) / 2^{j+1} for v = 2m+1
+// (u in units of c/2), with the same half-ulp adjustment of the mass and
+// momentum identities.
+void glbm_build_axis_table_zv(int N, AxisTable *t);
+// Host: E_i(u) - W_i of velocity index i from a table (FP64 Horner).
+double glbm_eq_dev_host(const AxisTable &t, double u, int i);
 
 // Per-instance constants read by the step kernels (one per lattice instance).
 struct InstParams {
@@ -53,11 +94,11 @@ struct InstParams {
     double g_theta;    // g / theta_x: force F_i = W_i xi_x g/theta_x   (Sec. 5.4)
     double inv_den;    // 1 / sum_{n>0} n W^y_n: wall emission normaliser
     double g_theta_om; // g / (theta_x omega): force folded into the equilibrium
-    double ew_lo[GLBM_MAXQ1];  // E^x_n(u_wall_lo)
-    double ew_hi[GLBM_MAXQ1];  // E^x_n(u_wall_hi)
+    double ew_lo[GLBM_MAXQA];  // E^x_i(u_wall_lo) by x velocity index
+    double ew_hi[GLBM_MAXQA];  // E^x_i(u_wall_hi)
     float omega_f, g_theta_f, inv_den_f, g_theta_om_f;
-    float dw_lo_f[GLBM_MAXQ1];  // E^x_n(u_wall_lo) - W_n
-    float dw_hi_f[GLBM_MAXQ1];  // E^x_n(u_wall_hi) - W_n
+    float dw_lo_f[GLBM_MAXQA];  // E^x_i(u_wall_lo) - W_i
+    float dw_hi_f[GLBM_MAXQA];  // E^x_i(u_wall_hi) - W_i
     // geometry of the instance (heterogeneous batches keep their own)
     int N;            // level along y (along both axes unless NX differs)
     int Lx, Ly;       // nodes
@@ -126,6 +167,15 @@ cudaError_t glbm_step2d_level(int shape, const Step2DArgs &a, int n_inst, cudaSt
 cudaError_t glbm_launch_step2d_x1(int N, int prec, int shape, const Step2DArgs &a, int n_inst,
                                   cudaStream_t s);
 int glbm_tile_shapes_x1(int N, int prec, TileShape *out);
+// Lattices on the 2N+2 hierarchy: kind GLBM_ZVK_X1 is D1Q3 along x times the
+// level-N 2N+2 axis along y; GLBM_ZVK_XY has the level-N 2N+2 axis on both.
+enum { GLBM_ZVK_X1 = 0, GLBM_ZVK_XY = 1 };
+cudaError_t glbm_launch_step2d_zv(int N, int kind, int prec, int shape, const Step2DArgs &a,
+                                  int n_inst, cudaStream_t s);
+int glbm_tile_shapes_zv(int N, int kind, int prec, TileShape *out);
+template <int N, typename T>
+cudaError_t glbm_step2d_zv_level(int kind, int shape, const Step2DArgs &a, int n_inst,
+                                 cudaStream_t s);
 
 // Auxiliary kernels (glbm_aux.cu).
 struct AuxArgs {

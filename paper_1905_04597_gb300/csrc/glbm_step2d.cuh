@@ -18,13 +18,18 @@
 //           force, and a coalesced store of each population at its own node.
 // FP32 mode stores deviations delta f = f - W (rest density 1) and adds the
 // moments with compensated row sums; FP64 mode stores f.
+// ZY / ZX select the 2N+2 hierarchy (Sec. 4, zero velocity removed) along y /
+// x: that axis has 2N+2 velocity indices i with the odd velocities
+// v = 2i - (2N+1) on a lattice of half the spacing (AxisVel).
 #pragma once
 #include "glbm_device.cuh"
 
-template <int N, typename T, int G, int R, int NXL = N>
+template <int N, typename T, int G, int R, int NXL = N, int ZY = 0, int ZX = 0>
 struct Step2D {
-    static constexpr int Q1 = 2 * N + 1;          // velocity rows (level N along y)
-    static constexpr int QX = 2 * NXL + 1;        // velocity columns (level NXL along x)
+    using AY = AxisVel<N, ZY>;
+    using AX = AxisVel<NXL, ZX>;
+    static constexpr int Q1 = AY::Q;              // velocity rows (level N along y)
+    static constexpr int QX = AX::Q;              // velocity columns (level NXL along x)
     static constexpr int RPG = (Q1 + G - 1) / G;  // velocity rows per warp group
     static constexpr int NW = G * R;              // warps per CTA
     static constexpr int NT = 32 * NW;
@@ -66,13 +71,13 @@ struct Step2D {
         int cofs[QX];
 #pragma unroll
         for (int ix = 0; ix < QX; ++ix)
-            cofs[ix] = ix * plane + wrap_shift(xc - (ix - NXL), Lx, Lx > NXL);
+            cofs[ix] = ix * plane + wrap_shift(xc - AX::vel(ix), Lx, Lx > AX::VMAX);
 
         // ---- phase 0: wall densities of this tile's columns ---------------
-        const bool need_lo = walls && (y0 < N);
-        const bool need_hi = walls && (y0 + R > Ly - N);
+        const bool need_lo = walls && (y0 < AY::VMAX);
+        const bool need_hi = walls && (y0 + R > Ly - AY::VMAX);
         if (need_lo || need_hi) {
-            // pairs (|ny|, row) = (aa, k), k < aa, enumerated p = aa(aa-1)/2 + k,
+            // pairs (velocity, row) with row < |ny|, enumerated in order of |ny|,
             // summed by NV fixed accumulators (p mod NV) that the warps share
             // round robin, so the order of the additions does not depend on the
             // tile shape; the loops stay rolled (the wall prologue runs on few
@@ -81,19 +86,19 @@ struct Step2D {
             for (int v = w; v < NV; v += NW) {
                 T slo = T(0), shi = T(0);
 #pragma unroll 1
-                for (int p = v; p < N * (N + 1) / 2; p += NV) {
-                    int aa = 1, k = p;
-                    while (k >= aa) {
-                        k -= aa;
-                        ++aa;
+                for (int p = v; p < AY::NPAIR; p += NV) {
+                    int m = AY::M0, k = p;
+                    while (k >= AY::vmag(m)) {
+                        k -= AY::vmag(m);
+                        ++m;
                     }
-                    if (need_lo) {  // velocity ny = -aa leaving row k through y = -1/2
-                        const T *pl = fin + ((N - aa) * QX * plane + k * pitch);
+                    if (need_lo) {  // velocity ny = -|v_m| leaving row k through y = -1/2
+                        const T *pl = fin + (AY::ineg(m) * QX * plane + k * pitch);
 #pragma unroll
                         for (int ix = 0; ix < QX; ++ix) slo += __ldg(pl + cofs[ix]);
                     }
-                    if (need_hi) {  // velocity ny = +aa leaving row Ly-1-k through y = Ly-1/2
-                        const T *ph = fin + ((N + aa) * QX * plane + (Ly - 1 - k) * pitch);
+                    if (need_hi) {  // velocity ny = +|v_m| leaving row Ly-1-k through y = Ly-1/2
+                        const T *ph = fin + (AY::ipos(m) * QX * plane + (Ly - 1 - k) * pitch);
 #pragma unroll
                         for (int ix = 0; ix < QX; ++ix) shi += __ldg(ph + cofs[ix]);
                     }
@@ -129,9 +134,9 @@ struct Step2D {
         for (int k = 0; k < RPG; ++k) {
             const int iy = g + k * G;
             if (iy < Q1) {
-                const int ny = iy - N;
+                const int ny = AY::vel(iy);
                 int ys = yc - ny;
-                ys = walls ? min(max(ys, 0), Ly - 1) : wrap_shift(ys, Ly, Ly > N);
+                ys = walls ? min(max(ys, 0), Ly - 1) : wrap_shift(ys, Ly, Ly > AY::VMAX);
                 const T *rowp = fin + (iy * QX * plane + ys * pitch);
 #pragma unroll
                 for (int ix = 0; ix < QX; ++ix) f[k][ix] = __ldg(rowp + cofs[ix]);
@@ -142,7 +147,7 @@ struct Step2D {
         for (int k = 0; k < RPG; ++k) {
             const int iy = g + k * G;
             if (iy < Q1) {
-                const int ny = iy - N;
+                const int ny = AY::vel(iy);
                 const int ys = yc - ny;
                 if (walls && (ys < 0 || ys >= Ly)) {  // uniform across the warp
                     const bool lo = ys < 0;
@@ -165,7 +170,8 @@ struct Step2D {
                 for (int ix = 0; ix < QX; ++ix) rs += f[k][ix];
                 T jx = T(0);
 #pragma unroll
-                for (int n = 1; n <= NXL; ++n) jx = fma(T(n), f[k][NXL + n] - f[k][NXL - n], jx);
+                for (int m = AX::M0; m <= NXL; ++m)
+                    jx = fma(T(AX::vmag(m)), f[k][AX::ipos(m)] - f[k][AX::ineg(m)], jx);
                 acc2(s_r, c_r, rs);
                 acc2(s_x, c_x, jx);
                 if (ny != 0) acc2(s_y, c_y, mul_rn(T(ny), rs));
@@ -199,16 +205,18 @@ struct Step2D {
         const T ux = (S_x + C_x) * inv_rho;
         const T uy = (S_y + C_y) * inv_rho;
         if (active) {
-            // sqrt(2/3) N per axis: positivity bound (Sec. 3)
-            const T umax = (T)(0.816496580927726 * N), umaxx = (T)(0.816496580927726 * NXL);
+            // sqrt(2/3) N per axis: positivity bound (Sec. 3), twice that in
+            // the half-spacing units of a 2N+2 axis
+            const T umax = (T)(0.816496580927726 * (ZY ? 2 * N : N));
+            const T umaxx = (T)(0.816496580927726 * (ZX ? 2 * NXL : NXL));
             if (!(rho > T(0)) || !(fabs(ux) <= umaxx) || !(fabs(uy) <= umax)) atomicOr(status, 1u);
         }
 
         T dx[QX];
         T dyall[G == 1 ? Q1 : 1];  // one warp group: E^y - W for every row at once
         if constexpr (G == 1) {
-            eq_dev_all<NXL, T>(tabx, ux, dx);
-            eq_dev_all<N, T>(tab, uy, dyall);
+            eq_dev_all<NXL, T, ZX>(tabx, ux, dx);
+            eq_dev_all<N, T, ZY>(tab, uy, dyall);
         } else {
             // the G warp groups of a node row share the polynomial work: group g
             // evaluates E^x - W and E^y - W for |n| = g, g + G, ..., and the
@@ -219,14 +227,16 @@ struct Step2D {
                 if (n % G != g) continue;
                 T ae, bo;
                 if (n <= NXL) {
-                    eq_parts<NXL, T>(tabx, n, vx, ae, bo);
-                    sm.eqx[r][NXL + n][lane] = n == 0 ? ae : fma(ux, bo, ae);
-                    if (n != 0) sm.eqx[r][NXL - n][lane] = fma(-ux, bo, ae);
+                    eq_parts<NXL, T, ZX>(tabx, n, vx, ae, bo);
+                    const bool single = n == 0 && !ZX;  // the zero velocity
+                    sm.eqx[r][AX::ipos(n)][lane] = single ? ae : fma(ux, bo, ae);
+                    if (!single) sm.eqx[r][AX::ineg(n)][lane] = fma(-ux, bo, ae);
                 }
                 if (n <= N) {
-                    eq_parts<N, T>(tab, n, vy, ae, bo);
-                    sm.eqy[r][N + n][lane] = n == 0 ? ae : fma(uy, bo, ae);
-                    if (n != 0) sm.eqy[r][N - n][lane] = fma(-uy, bo, ae);
+                    eq_parts<N, T, ZY>(tab, n, vy, ae, bo);
+                    const bool single = n == 0 && !ZY;
+                    sm.eqy[r][AY::ipos(n)][lane] = single ? ae : fma(uy, bo, ae);
+                    if (!single) sm.eqy[r][AY::ineg(n)][lane] = fma(-uy, bo, ae);
                 }
             }
             __syncthreads();
@@ -252,7 +262,6 @@ struct Step2D {
         for (int k = 0; k < RPG; ++k) {
             const int iy = g + k * G;
             if (iy < Q1) {
-                const int ny = iy - N;
                 const T wy = A::W(tab, iy);
                 T dy;
                 if constexpr (G == 1)
@@ -268,7 +277,7 @@ struct Step2D {
                 const unsigned hrow = hnode + (unsigned)iy * 0x85EBCA6Bu;
 #pragma unroll
                 for (int ix = 0; ix < QX; ++ix) {
-                    const int nx = ix - NXL;
+                    const int nx = AX::vel(ix);
                     const T f0 = f[k][ix];
                     T v;
                     if (DEV) {
@@ -306,18 +315,18 @@ __device__ __forceinline__ void advance_launch_counter(unsigned *step_ctr, unsig
     }
 }
 
-template <int N, typename T, int G, int R, int NXL = N>
+template <int N, typename T, int G, int R, int NXL = N, int ZY = 0, int ZX = 0>
 __global__ void __launch_bounds__(32 * G * R)
     k_step2d(const __grid_constant__ Step2DArgs a)
 {
-    using S = Step2D<N, T, G, R, NXL>;
+    using S = Step2D<N, T, G, R, NXL, ZY, ZX>;
     __shared__ typename S::Smem sm;
     const int inst = blockIdx.z;
     const T *fin = static_cast<const T *>(a.fin) + (long long)inst * a.inst_stride;
     T *fout = static_cast<T *>(a.fout) + (long long)inst * a.inst_stride;
     // launch counter (read before any CTA of this launch can advance it)
     const unsigned seed = S::DEV ? hash32(__ldcg(a.step_ctr) * 0x632BE5ABu + inst) : 0u;
-    S::run(a.tab, NXL == N ? a.tab : a.tabx, a.ip[inst], a.Lx, a.Ly, a.pitch, (int)a.plane, a.bc,
-           fin, fout, blockIdx.x * 32, blockIdx.y * R, sm, a.status, seed);
+    S::run(a.tab, (NXL == N && ZX == ZY) ? a.tab : a.tabx, a.ip[inst], a.Lx, a.Ly, a.pitch,
+           (int)a.plane, a.bc, fin, fout, blockIdx.x * 32, blockIdx.y * R, sm, a.status, seed);
     if (S::DEV) advance_launch_counter(a.step_ctr, a.done_ctr);
 }

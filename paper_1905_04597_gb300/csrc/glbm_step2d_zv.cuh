@@ -1,0 +1,35 @@
+// Fused 2D step on the 2N+2 hierarchy (Sec. 4: the zero velocity removed,
+// Eqs. maineq01_noball - maineq04_noball): the one-node tile of
+// glbm_step2d.cuh with the 2N+2 axis along y (kind GLBM_ZVK_X1: D1Q3 along x,
+// the form of the paper's channel models G-D1Q6 x D1Q3 and G-D1Q8 x D1Q3) or
+// along both axes (kind GLBM_ZVK_XY, the fully symmetric lattices).
+#pragma once
+#include "glbm_step2d.cuh"
+#include "glbm_tiles_zv.h"
+
+template <int N, typename T, int KIND, int I = 0>
+cudaError_t launch_zv_shape(int shape, const Step2DArgs &a, int n_inst, cudaStream_t s)
+{
+    if constexpr (I < TilesZv<N, T, KIND>::count) {
+        if (shape == I) {
+            constexpr TileShape t = TilesZv<N, T, KIND>::shape[I];
+            static_assert(t.V == 1, "2N+2 lattices take one-node tiles");
+            constexpr int NXL = KIND == GLBM_ZVK_X1 ? 1 : N;
+            constexpr int ZX = KIND == GLBM_ZVK_X1 ? 0 : 1;
+            const dim3 grid((a.Lx + 31) / 32, (a.Ly + t.R - 1) / t.R, n_inst);
+            k_step2d<N, T, t.G, t.R, NXL, 1, ZX><<<grid, 32 * t.G * t.R, 0, s>>>(a);
+            return cudaGetLastError();
+        }
+        return launch_zv_shape<N, T, KIND, I + 1>(shape, a, n_inst, s);
+    } else {
+        return cudaErrorInvalidValue;
+    }
+}
+
+template <int N, typename T>
+cudaError_t glbm_step2d_zv_level(int kind, int shape, const Step2DArgs &a, int n_inst,
+                                 cudaStream_t s)
+{
+    return kind == GLBM_ZVK_X1 ? launch_zv_shape<N, T, GLBM_ZVK_X1>(shape, a, n_inst, s)
+                               : launch_zv_shape<N, T, GLBM_ZVK_XY>(shape, a, n_inst, s);
+}

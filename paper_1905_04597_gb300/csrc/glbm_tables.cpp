@@ -10,6 +10,7 @@
 // trinomial (the N-fold summation itself); the kernels evaluate E_n by Horner
 // and never touch factorials.
 #include <math.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include "glbm_internal.h"
@@ -22,7 +23,9 @@
 // the correctly rounded entries is computed exactly: every entry is an integer
 // multiple of the smallest entry's ulp, so the weighted sum is an exact
 // 128-bit integer. All other entries keep full relative precision.
-static void fix_identity(double *c, int N, int j)
+// On the 2N+2 hierarchy (zv) c[m] belongs to the velocities +-(2m+1): the
+// weights are 2 (mass) and 2 (2m+1) (momentum), and c[0] absorbs both.
+static void fix_identity(double *c, int N, int j, bool zv = false)
 {
     int emin = 0;
     bool any = false;
@@ -36,27 +39,29 @@ static void fix_identity(double *c, int N, int j)
     const double delta = (j == 0 || j == 1) ? 1.0 : 0.0;
     // largest magnitude of any term in units of 2^emin must fit the accumulator
     double big = fabs(delta);
-    for (int n = 0; n <= N; ++n) big = fmax(big, 2.0 * (n + 1) * fabs(c[n]));
+    for (int n = 0; n <= N; ++n) big = fmax(big, (zv ? 4.0 : 2.0) * (n + 1) * fabs(c[n]));
     if (ilogb(big) - emin > 120) return;  // span too wide for exact integers: keep as is
     __int128 S = 0;
     for (int n = 0; n <= N; ++n) {
         const __int128 I = (__int128)ldexp(c[n], -emin);  // exact integer
-        const int mult = (j % 2 == 0) ? (n == 0 ? 1 : 2) : 2 * n;
+        const int mult = zv ? ((j % 2 == 0) ? 2 : 2 * (2 * n + 1))
+                            : ((j % 2 == 0) ? (n == 0 ? 1 : 2) : 2 * n);
         S += (__int128)mult * I;
     }
     const __int128 T = (__int128)ldexp(delta, -emin);
     const double R = ldexp((double)(T - S), emin);  // residual (rounded once)
-    if (j % 2 == 0)
+    if (zv)
+        c[0] += 0.5 * R;
+    else if (j % 2 == 0)
         c[0] += R;
     else
         c[1] += 0.5 * R;
 }
 
-void glbm_build_axis_table(int N, AxisTable *t, double *full)
+// Exact N-fold convolution: cur[n + N][j] = coefficient of z^n u^j.
+static void convolve(int N, double (&cur)[GLBM_MAXQ1][GLBM_MAXQ1])
 {
     const int Q1 = 2 * N + 1;
-    // poly[n + N][j]: coefficient of z^n u^j; sized for the largest level
-    double cur[GLBM_MAXQ1][GLBM_MAXQ1];
     double nxt[GLBM_MAXQ1][GLBM_MAXQ1];
     memset(cur, 0, sizeof(cur));
     cur[N][0] = 1.0;
@@ -85,6 +90,31 @@ void glbm_build_axis_table(int N, AxisTable *t, double *full)
         }
         memcpy(cur, nxt, sizeof(cur));
     }
+}
+
+// FP32 copies and the hi + lo split of the linear coefficient.
+static void fill_f32(AxisTable *t, int Q)
+{
+    const int N = t->N;
+    for (int i = 0; i < Q; ++i) {
+        t->Wf[i] = (float)t->W[i];
+        t->WNf[i] = (float)t->WN[i];
+    }
+    for (int n = 0; n <= N; ++n) {
+        for (int i = 0; i <= N; ++i) t->Cef[n][i] = (float)t->Ce[n][i];
+        for (int i = 0; i < N; ++i) t->Cof[n][i] = (float)t->Co[n][i];
+        // FP32 keeps the linear coefficient as hi + lo so that the momentum
+        // identity is not broken by its rounding
+        t->Co1lo[n] = (float)(t->Co[n][0] - (double)t->Cof[n][0]);
+    }
+}
+
+void glbm_build_axis_table(int N, AxisTable *t, double *full)
+{
+    const int Q1 = 2 * N + 1;
+    // cur[n + N][j]: coefficient of z^n u^j; sized for the largest level
+    double cur[GLBM_MAXQ1][GLBM_MAXQ1];
+    convolve(N, cur);
 
     // conservation identities of the FP64 coefficients to half an ulp
     for (int j = 0; j < Q1; ++j) {
@@ -101,25 +131,65 @@ void glbm_build_axis_table(int N, AxisTable *t, double *full)
     t->N = N;
     for (int n = -N; n <= N; ++n) {
         t->W[n + N] = cur[n + N][0];
-        t->Wf[n + N] = (float)cur[n + N][0];
         t->WN[n + N] = n * cur[n + N][0];
-        t->WNf[n + N] = (float)(n * cur[n + N][0]);
     }
     for (int n = 0; n <= N; ++n) {
-        for (int i = 0; i <= N; ++i) {
-            t->Ce[n][i] = cur[n + N][2 * i];
-            t->Cef[n][i] = (float)cur[n + N][2 * i];
-        }
-        for (int i = 0; i < N; ++i) {
-            t->Co[n][i] = cur[n + N][2 * i + 1];
-            t->Cof[n][i] = (float)cur[n + N][2 * i + 1];
-        }
-        // FP32 keeps the linear coefficient as hi + lo so that the momentum
-        // identity sum_n n C[n][1] = 1 is not broken by its rounding
-        t->Co1lo[n] = (float)(cur[n + N][1] - (double)t->Cof[n][0]);
+        for (int i = 0; i <= N; ++i) t->Ce[n][i] = cur[n + N][2 * i];
+        for (int i = 0; i < N; ++i) t->Co[n][i] = cur[n + N][2 * i + 1];
     }
+    fill_f32(t, Q1);
     if (full) {
         for (int n = 0; n < Q1; ++n)
             for (int j = 0; j < Q1; ++j) full[n * Q1 + j] = cur[n][j];
     }
+}
+
+void glbm_build_axis_table_zv(int N, AxisTable *t)
+{
+    double cur[GLBM_MAXQ1][GLBM_MAXQ1];
+    convolve(N, cur);
+    // c[m][j]: coefficient of u^j of E_{2m+1}(u) = (E_m(u/2) + E_{m+1}(u/2)) / 2,
+    // u in units of c/2 (E_{N+1} = 0); halving and the powers of two are exact,
+    // the sum of the two neighbours is rounded once
+    double c[GLBM_MAXN + 1][GLBM_MAXQ1];
+    for (int m = 0; m <= N; ++m)
+        for (int j = 0; j <= 2 * N; ++j) {
+            const double hi = m + 1 <= N ? cur[m + 1 + N][j] : 0.0;
+            c[m][j] = ldexp(cur[m + N][j] + hi, -(j + 1));
+        }
+    for (int j = 0; j <= 2 * N; ++j) {
+        double col[GLBM_MAXN + 1];
+        for (int m = 0; m <= N; ++m) col[m] = c[m][j];
+        fix_identity(col, N, j, true);
+        for (int m = 0; m <= N; ++m) c[m][j] = col[m];
+    }
+    memset(t, 0, sizeof(*t));
+    t->N = N;
+    t->zv = 1;
+    for (int m = 0; m <= N; ++m) {
+        const int ip = N + 1 + m, in = N - m, v = 2 * m + 1;
+        t->W[ip] = t->W[in] = c[m][0];
+        t->WN[ip] = v * c[m][0];
+        t->WN[in] = -v * c[m][0];
+        for (int i = 0; i <= N; ++i) t->Ce[m][i] = c[m][2 * i];
+        for (int i = 0; i < N; ++i) t->Co[m][i] = c[m][2 * i + 1];
+    }
+    fill_f32(t, 2 * N + 2);
+}
+
+double glbm_eq_dev_host(const AxisTable &t, double u, int i)
+{
+    const int N = t.N;
+    const int v = ax_vel(t, i);
+    const int m = t.zv ? (abs(v) - 1) / 2 : abs(v);
+    const double w = u * u;
+    double ae = t.Ce[m][N];
+    for (int k = N - 1; k >= 1; --k) ae = fma(ae, w, t.Ce[m][k]);
+    ae *= w;
+    double bo = 0.0;
+    if (v != 0) {
+        bo = t.Co[m][N - 1];
+        for (int k = N - 2; k >= 0; --k) bo = fma(bo, w, t.Co[m][k]);
+    }
+    return v >= 0 ? fma(u, bo, ae) : fma(-u, bo, ae);
 }

@@ -20,6 +20,7 @@ LIB_PATH = os.path.join(PKG, "libglbm.so")
 OK, E_INVAL, E_NOMEM, E_CUDA, E_UNSTABLE, E_TIMEOUT, E_IO, E_UNSUPPORTED = 0, -1, -2, -3, -4, -5, -6, -7
 BC_WALLS, BC_BOUNCEBACK, BC_PERIODIC = 0, 1, 2
 FP64, FP32_DEV = 0, 1
+ZV_X, ZV_Y = 1, 2  # axes on the 2N+2 hierarchy (Config.zv_axes)
 M_RHO, M_UX, M_UY, M_T, M_QX, M_QY, M_SXY, M_ALL = 1, 2, 4, 8, 16, 32, 64, 127
 FIELDS_2D = ("rho", "ux", "uy", "T", "qx", "qy", "sxy")
 FIELDS_1D = ("rho", "ux", "T", "qx")
@@ -40,7 +41,8 @@ class Config(ctypes.Structure):
                 ("k", ctypes.c_int), ("x_level", ctypes.c_int), ("tau", ctypes.c_double),
                 ("kn", ctypes.c_double),
                 ("bc", ctypes.c_int), ("prec", ctypes.c_int), ("u_wall_lo", ctypes.c_double),
-                ("u_wall_hi", ctypes.c_double), ("g", ctypes.c_double)]
+                ("u_wall_hi", ctypes.c_double), ("g", ctypes.c_double),
+                ("zv_axes", ctypes.c_int)]
 
 
 _lib = None
@@ -129,13 +131,14 @@ def eq_table(k: int) -> np.ndarray:
 
 
 def make_config(dims=2, nx=1, ny=1, k=0, tau=0.0, kn=0.0, bc=None, prec=FP64, u_wall_lo=0.0,
-                u_wall_hi=0.0, g=0.0, x_level=0) -> Config:
+                u_wall_hi=0.0, g=0.0, x_level=0, zv_axes=0) -> Config:
     """One instance; x_level=1 makes the anisotropic product D1Q3 (x) times the
-    level-(k+1) lattice (y); 0 keeps level k+1 on both axes."""
+    level-(k+1) lattice (y); 0 keeps level k+1 on both axes. zv_axes (ZV_X,
+    ZV_Y) puts axes on the 2N+2 hierarchy (odd velocities, half spacing)."""
     if bc is None:
         bc = BC_WALLS if dims == 2 else BC_BOUNCEBACK
     return Config(dims, nx, ny if dims == 2 else 1, k, x_level, tau, kn, bc, prec, u_wall_lo,
-                  u_wall_hi, g)
+                  u_wall_hi, g, zv_axes)
 
 
 _torch_alloc_refs = None
@@ -226,9 +229,11 @@ class Lattice:
 
     def nq(self, inst=0):
         c = self.configs[inst]
-        q1 = 2 * c.k + 3
-        q1x = 2 * c.x_level + 1 if c.x_level > 0 else q1
-        return q1 * q1x if c.dims == 2 else q1
+        if c.dims != 2:
+            return 2 * c.k + 3
+        q1 = 2 * c.k + 3 + (1 if c.zv_axes & ZV_Y else 0)
+        q1x = 2 * (c.x_level if c.x_level > 0 else c.k + 1) + 1 + (1 if c.zv_axes & ZV_X else 0)
+        return q1 * q1x
 
     def shape(self, inst=0):
         c = self.configs[inst]

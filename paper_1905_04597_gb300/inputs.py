@@ -73,6 +73,17 @@ def sod_density(nx: int = 1000, left: float = 1.0, right: float = 0.125) -> np.n
 COUETTE_ANISO = dict(nx=1024, ny=200, k=7, x_level=1, kn=(0.01, 0.1, 1.0), u_wall_lo=-0.05,
                      u_wall_hi=0.05)
 
+# Couette channel on the 2N+2 hierarchy (Sec. 4, zero velocity removed): the
+# paper's G-D1Q8 x D1Q3 (D1Q3 along x, the 2N+2 axis with N = 3 along y) at
+# Ny = 200, long enough in x that the populations exceed the L2 cache
+COUETTE_ZV = dict(nx=4096, ny=200, k=2, x_level=1, zv_axes=2, kn=(0.01, 0.1, 1.0),
+                  u_wall_lo=-0.05, u_wall_hi=0.05,
+                  label="couette_zv_d1q3xd1q8_4096x200_kn{0.01,0.1,1}")
+# and the fully symmetric 2N+2 lattice of the same level, D2Q64 (8 x 8)
+COUETTE_ZV_XY = dict(nx=512, ny=256, k=2, x_level=0, zv_axes=3, kn=(0.01, 0.1, 1.0),
+                     u_wall_lo=-0.05, u_wall_hi=0.05,
+                     label="couette_zv_d2q64_512x256_kn{0.01,0.1,1}")
+
 
 def batched_instances(seed: int = 0, n: int = 256, nx: int = 64):
     """Per-instance recipe of the batched channel workload, drawn in a fixed order."""

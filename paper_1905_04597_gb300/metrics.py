@@ -14,18 +14,26 @@ FIELDS_2D = ("rho", "ux", "uy", "T", "qx", "qy", "sxy")
 FIELDS_1D = ("rho", "ux", "T", "qx")
 
 
-def term_scales(F, want, dims=2, q1x=None):
+def _axis_velocities(Q1, zv):
+    """Velocities of one axis with Q1 of them: -N..N, or on the 2N+2 hierarchy
+    (zv) the odd integers -(Q1-1)..Q1-1."""
+    if zv:
+        return np.arange(-(Q1 - 1), Q1, 2)
+    return np.arange(-((Q1 - 1) // 2), (Q1 - 1) // 2 + 1)
+
+
+def term_scales(F, want, dims=2, q1x=None, zv=0):
     """Largest per-node sum of absolute terms of each moment of populations F
     (velocity-major array [Q, ny, nx] in 2D, [Q, nx] in 1D); want holds the
     moments in the order of FIELDS_2D / FIELDS_1D. q1x is the number of x
-    velocities of an anisotropic product (default: the square lattice)."""
+    velocities of an anisotropic product (default: the square lattice); zv the
+    mask of axes on the 2N+2 hierarchy (1: x, 2: y)."""
     Q = F.shape[0]
     if dims == 2:
         Q1x = q1x or int(round(np.sqrt(Q)))
         Q1y = Q // Q1x
-        NX, NY = (Q1x - 1) // 2, (Q1y - 1) // 2
-        cx = np.tile(np.arange(-NX, NX + 1), Q1y).astype(float)[:, None, None]
-        cy = np.repeat(np.arange(-NY, NY + 1), Q1x).astype(float)[:, None, None]
+        cx = np.tile(_axis_velocities(Q1x, zv & 1), Q1y).astype(float)[:, None, None]
+        cy = np.repeat(_axis_velocities(Q1y, zv & 2), Q1x).astype(float)[:, None, None]
         rho, ux, uy = want[0], want[1], want[2]
         dx, dy = cx - ux, cy - uy
         d2 = dx * dx + dy * dy
@@ -41,14 +49,14 @@ def term_scales(F, want, dims=2, q1x=None):
             "T": (d * d * F).sum(0).max() / rho.min(), "qx": 0.5 * (np.abs(d) ** 3 * F).sum(0).max()}
 
 
-def rel_errors(got, want, dims=2, F=None, q1x=None):
+def rel_errors(got, want, dims=2, F=None, q1x=None, zv=0):
     """Per-field max |got - want| / max(max |want|, 1e-3 S); got maps field names
     to arrays, want is the stacked reference moments. F (populations of the
-    reference) gives the term scales S; q1x as in term_scales."""
+    reference) gives the term scales S; q1x and zv as in term_scales."""
     names = FIELDS_2D if dims == 2 else FIELDS_1D
     w = {n: want[i] for i, n in enumerate(names)}
     groups = {"ux": ("ux", "uy"), "uy": ("ux", "uy"), "qx": ("qx", "qy"), "qy": ("qx", "qy")}
-    S = term_scales(F, want, dims, q1x) if F is not None else {}
+    S = term_scales(F, want, dims, q1x, zv) if F is not None else {}
     out = {}
     for n in names:
         scale = max(np.abs(w[m]).max() for m in groups.get(n, (n,)) if m in w)

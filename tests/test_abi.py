@@ -96,6 +96,35 @@ def test_anisotropic_configs_are_checked_before_any_device_call():
     assert create(two, 2, None, ctypes.byref(h)) == glbm.E_UNSUPPORTED
 
 
+def test_2n2_configs_are_checked_before_any_device_call():
+    """zv_axes: the 2N+2 hierarchy along y with D1Q3 along x, or along both axes
+    of an isotropic lattice; 2D only; walls need ny >= 2N+1; the wall-speed
+    bound doubles in the half-spacing units of a 2N+2 x axis; no batches."""
+    h = ctypes.c_void_p()
+    create = glbm.lib().glbm_create
+    zy, zxy = glbm.ZV_Y, glbm.ZV_X | glbm.ZV_Y
+    for kw, st in [(dict(dims=1, nx=8, k=2, zv_axes=zy), glbm.E_INVAL),
+                   (dict(dims=2, nx=8, ny=16, k=2, zv_axes=4), glbm.E_INVAL),
+                   (dict(dims=2, nx=8, ny=16, k=2, zv_axes=glbm.ZV_X), glbm.E_UNSUPPORTED),
+                   (dict(dims=2, nx=8, ny=16, k=2, zv_axes=zy), glbm.E_UNSUPPORTED),
+                   (dict(dims=2, nx=8, ny=16, k=2, x_level=1, zv_axes=zxy), glbm.E_UNSUPPORTED),
+                   (dict(dims=2, nx=8, ny=6, k=2, x_level=1, zv_axes=zy), glbm.E_INVAL),
+                   (dict(dims=2, nx=8, ny=6, k=2, zv_axes=zxy), glbm.E_INVAL),
+                   (dict(dims=2, nx=8, ny=8, k=0, zv_axes=zxy, u_wall_lo=1.7), glbm.E_INVAL),
+                   (dict(dims=2, nx=8, ny=8, k=0, x_level=1, zv_axes=zy, u_wall_lo=0.9),
+                    glbm.E_INVAL)]:
+        cfg = glbm.make_config(tau=1.0, **kw)
+        assert create(ctypes.byref(cfg), 1, None, ctypes.byref(h)) == st, kw
+        assert not h.value
+    cfg = glbm.make_config(dims=2, nx=8, ny=16, k=2, tau=1.0, zv_axes=zxy, prec=glbm.FP32_DEV)
+    assert glbm.lib().glbm_batch_create(ctypes.byref(cfg), 1, None,
+                                        ctypes.byref(h)) == glbm.E_UNSUPPORTED
+    # instances on different hierarchies are not one uniform context
+    two = (glbm.Config * 2)(glbm.make_config(dims=2, nx=8, ny=16, k=2, tau=1.0),
+                            glbm.make_config(dims=2, nx=8, ny=16, k=2, tau=1.0, zv_axes=zxy))
+    assert create(two, 2, None, ctypes.byref(h)) == glbm.E_UNSUPPORTED
+
+
 def test_tile_shape_candidates():
     """Every level has 1..MAX_TILES candidate shapes in each precision, each
     with 1 <= G <= 2k+3 warp groups, at most 512 threads per CTA and one or

@@ -1,0 +1,186 @@
+"""The 2N+2 hierarchy (Sec. 4: the zero velocity removed) on the GPU against the
+oracle: D1Q3 along x times the 2N+2 axis along y (the channel models
+G-D1Q6 x D1Q3 and G-D1Q8 x D1Q3 of Sec. 5) and the fully symmetric lattices
+with the 2N+2 axis on both. Every population after one step at every level in
+both precisions, moments after many steps from smooth fields, every tile
+shape, Poiseuille channels, the lattice temperature of the equilibrium,
+checkpoints and the operations that take the 2N+1 hierarchy only."""
+import numpy as np
+import pytest
+
+from oracle import oracle as orc
+from paper_1905_04597_gb300 import glbm, inputs
+from parity_helpers import oracle_moments, rel_errors
+
+pytestmark = pytest.mark.gpu
+
+TOL = {glbm.FP64: 1e-12, glbm.FP32_DEV: 1e-5}
+POP_TOL = {glbm.FP64: 1e-13, glbm.FP32_DEV: 1e-6}
+KINDS = {"x1": glbm.ZV_Y, "xy": glbm.ZV_X | glbm.ZV_Y}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+def _nx_level(kind, k):
+    return 1 if kind == "x1" else k + 1
+
+
+def _q1x(kind, k):
+    return 3 if kind == "x1" else 2 * k + 4
+
+
+def _oracle(kind, k, nx, ny, bc, tau, uw_lo=0.0, uw_hi=0.0, g=0.0):
+    return orc.Lattice(2, _nx_level(kind, k), k + 1, nx, ny, bc, tau, uw_lo, uw_hi, g,
+                       zv=KINDS[kind])
+
+
+def _cfg(kind, k, nx, ny, prec, **kw):
+    return dict(dims=2, nx=nx, ny=ny, k=k, x_level=1 if kind == "x1" else 0,
+                zv_axes=KINDS[kind], prec=prec, **kw)
+
+
+@pytest.mark.parametrize("prec", [glbm.FP64, glbm.FP32_DEV])
+@pytest.mark.parametrize("bc", [glbm.BC_WALLS, glbm.BC_PERIODIC])
+@pytest.mark.parametrize("k", range(8))
+@pytest.mark.parametrize("kind", sorted(KINDS))
+def test_one_step_all_populations(kind, k, bc, prec):
+    N = k + 1
+    nx, ny = 37, 2 * N + 4
+    tau, uw_lo, uw_hi, g = 0.83, -0.05, 0.07, 2e-4
+    Q = _q1x(kind, k) * (2 * N + 2)
+    f0 = inputs.random_populations(900 + k, Q, ny, nx)
+    lat = glbm.Lattice(_cfg(kind, k, nx, ny, prec, tau=tau, bc=bc, u_wall_lo=uw_lo,
+                            u_wall_hi=uw_hi, g=g))
+    assert lat.nq() == Q
+    lat.set_populations(0, f0)
+    # FP32 stores f - W: the round trip is exact to half an ulp of the deviation
+    np.testing.assert_allclose(lat.get_populations(0), f0, rtol=0, atol=3e-8 if prec else 0)
+    lat.step(1)
+    lat.sync()
+    got = lat.get_populations(0)
+    want, _ = _oracle(kind, k, nx, ny, bc, tau, uw_lo, uw_hi, g).run(f0, 1)
+    err = np.abs(got - want).max() / np.abs(want).max()
+    assert err < POP_TOL[prec], err
+    lat.close()
+
+
+@pytest.mark.parametrize("prec", [glbm.FP64, glbm.FP32_DEV])
+@pytest.mark.parametrize("k", [1, 4, 7])
+@pytest.mark.parametrize("kind", sorted(KINDS))
+def test_moments_after_steps(kind, k, prec):
+    N = k + 1
+    nx, ny, steps = 48, 3 * N + 8, 60
+    kw = dict(kn=0.15, u_wall_lo=-0.05, u_wall_hi=0.05, g=1e-5)
+    fields = inputs.random_macro(920 + k, nx, ny)
+    lat = glbm.Lattice(_cfg(kind, k, nx, ny, prec, **kw))
+    lat.set_equilibrium(0, *fields)
+    lat.step(steps)
+    lat.sync()
+    tau = orc.tau_from_kn(N, ny, 0.15, zv=1)
+    assert lat.tau(0) == pytest.approx(tau, rel=1e-14)
+    o = _oracle(kind, k, nx, ny, orc.BC_WALLS, tau, -0.05, 0.05, 1e-5)
+    X, _ = o.run(o.equilibrium(*fields), steps)
+    want, F = oracle_moments(o, X)
+    errs = rel_errors(lat.moments(0), want, F=F, q1x=_q1x(kind, k), zv=KINDS[kind])
+    assert max(errs.values()) < TOL[prec], errs
+    lat.close()
+
+
+@pytest.mark.parametrize("kind", sorted(KINDS))
+def test_equilibrium_has_the_shifted_temperature(kind):
+    """Sec. 4: the 2N+2 equilibrium at rest has temperature (4N+3)/3 (lattice
+    units of the half spacing); the macro temperature averages the two axes."""
+    k, nx, ny = 2, 33, 12
+    N = k + 1
+    lat = glbm.Lattice(_cfg(kind, k, nx, ny, glbm.FP64, tau=0.9, bc=glbm.BC_PERIODIC))
+    rho, ux, uy = inputs.random_macro(930, nx, ny)
+    lat.set_equilibrium(0, rho, ux, uy)
+    m = lat.moments(0)
+    o = _oracle(kind, k, nx, ny, orc.BC_PERIODIC, 0.9)
+    want, _ = oracle_moments(o, o.equilibrium(rho, ux, uy))
+    np.testing.assert_allclose(m["T"], want[3], rtol=1e-13)
+    thx = (4 * N + 3) / 3.0 if kind == "xy" else 1 / 3.0
+    # the streamed equilibrium is not the local one; compare the mean
+    assert np.mean(m["T"]) == pytest.approx(0.5 * (thx + (4 * N + 3) / 3.0), rel=2e-2)
+    lat.close()
+
+
+@pytest.mark.parametrize("prec", [glbm.FP64, glbm.FP32_DEV])
+@pytest.mark.parametrize("kind", sorted(KINDS))
+def test_every_tile_shape_one_step(kind, prec):
+    for k in (2, 7):
+        N = k + 1
+        nx, ny = 45, 2 * N + 3
+        Q = _q1x(kind, k) * (2 * N + 2)
+        f0 = inputs.random_populations(940 + k, Q, ny, nx)
+        want, _ = _oracle(kind, k, nx, ny, orc.BC_WALLS, 0.9, 0.03, -0.02, 1e-4).run(f0, 1)
+        kw = dict(tau=0.9, u_wall_lo=0.03, u_wall_hi=-0.02, g=1e-4)
+        base = glbm.Lattice(_cfg(kind, k, nx, ny, prec, **kw))
+        times = base.autotune(reps=2)
+        assert set(times) == {k} and len(times[k]) >= 2
+        n_shapes = len(times[k])
+        base.close()
+        for idx in range(n_shapes):
+            lat = glbm.Lattice(_cfg(kind, k, nx, ny, prec, **kw))
+            t = [-1] * glbm.LEVELS
+            t[k] = idx
+            lat.set_tiles(t)
+            assert lat.tile_shape(k)[2] == 1
+            lat.set_populations(0, f0)
+            lat.step(1)
+            lat.sync()
+            err = np.abs(lat.get_populations(0) - want).max() / np.abs(want).max()
+            assert err < POP_TOL[prec], (k, idx, err)
+            lat.close()
+
+
+@pytest.mark.parametrize("k", [1, 2])
+def test_poiseuille_channel_fp32(k):
+    """G-D1Q6 x D1Q3 (k = 1) and G-D1Q8 x D1Q3 (k = 2): x-uniform Poiseuille flow
+    between diffuse walls, 2000 steps in FP32 deviations against the FP64 oracle."""
+    ny, steps, g = 40, 2000, 1e-5
+    N = k + 1
+    for kn in (0.05, 0.5):
+        lat = glbm.Lattice(_cfg("x1", k, 1, ny, glbm.FP32_DEV, kn=kn, g=g))
+        lat.step(steps)
+        lat.sync()
+        o = _oracle("x1", k, 1, ny, orc.BC_WALLS, orc.tau_from_kn(N, ny, kn, zv=1), g=g)
+        X, _ = o.run(o.equilibrium(np.ones((ny, 1)), np.zeros((ny, 1)), np.zeros((ny, 1))), steps)
+        want, F = oracle_moments(o, X)
+        errs = rel_errors(lat.moments(0), want, F=F, q1x=3, zv=glbm.ZV_Y)
+        assert max(errs.values()) < TOL[glbm.FP32_DEV], (kn, errs)
+        u = lat.moments(0)["ux"][:, 0]
+        assert u.max() > 0 and np.allclose(u, u[::-1], rtol=1e-4)
+        lat.close()
+
+
+def test_conservation_checkpoint_and_unsupported_operations(tmp_path):
+    k, nx, ny = 3, 40, 14
+    cfg = _cfg("x1", k, nx, ny, glbm.FP32_DEV, tau=0.7, u_wall_lo=-0.03, u_wall_hi=0.03)
+    a = glbm.Lattice(cfg)
+    a.set_equilibrium(0, *inputs.random_macro(950, nx, ny))
+    m0, _, _ = a.conservation(0)
+    a.step(30)
+    m1, _, _ = a.conservation(0)
+    assert m1 == pytest.approx(m0, rel=1e-6)
+    path = str(tmp_path / "zv.ckpt")
+    a.save(path)
+    b = glbm.Lattice(cfg)
+    b.load(path)
+    a.step(20)
+    b.step(20)
+    np.testing.assert_array_equal(a.get_populations(0), b.get_populations(0))
+    odd = glbm.Lattice(dict(cfg, zv_axes=0, ny=14))
+    with pytest.raises(glbm.GlbmError):
+        odd.load(path)  # the 2N+1 lattice of the same level: refused
+    with pytest.raises(glbm.GlbmError):
+        a.adjoint_flowrate(10, 5)
+    for x in (a, b, odd):
+        x.close()
