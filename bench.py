@@ -264,7 +264,8 @@ def run_ours(args):
     def kernel_name(prec, lat):
         G, R, V = lat.tile_shape(N - 1)
         if V == 2:
-            return f"k_step2d_pair<{N},{G},{R}{',1' if NX != N else ''}>"
+            tail = ",1,1" if ZV else (",1" if NX != N else "")
+            return f"k_step2d_pair<{N},{G},{R}{tail}>"
         t = "float" if prec == glbm.FP32_DEV else "double"
         tail = f",{NX},{1 if ZV & 2 else 0},{1 if ZV & 1 else 0}" if ZV else (
             ",1" if NX != N else "")

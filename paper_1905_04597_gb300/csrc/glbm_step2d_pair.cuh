@@ -19,6 +19,9 @@
 //            inside a wall take the wall's re-emitted value), partial moments
 //            per velocity row with compensated sums;
 //   phase 2: moments, equilibrium, relaxation plus force, dithered store.
+// ZY = 1 puts the y axis on the 2N+2 hierarchy (Sec. 4, zero velocity
+// removed: odd velocities on a half-spacing lattice); the x axis is always on
+// the 2N+1 hierarchy here.
 #pragma once
 #include "glbm_step2d.cuh"
 
@@ -82,33 +85,34 @@ __device__ __forceinline__ void acc2x2(f32x2 &s, f32x2 &c, f32x2 x)
 // p mod NV of the (|n_y|, row) pairs) in the order of the one-node tile,
 // whatever the tile shape; the NW warps of the CTA share the accumulators.
 // Leaves rho_w - 1 of both walls in rw[2][64]. Every thread calls it.
-template <int N, int NX, int NV>
+template <int N, int NX, int NV, int ZY = 0>
 __device__ __forceinline__ void pair_wall_densities(const InstParams &ip, const float *__restrict__ fin,
                                                     int Ly, int pitch, int plane, const int *win,
                                                     bool need_lo, bool need_hi, int w, int NW,
                                                     int lane, float (*dsum)[2][64], float (*rw)[64])
 {
+    using AY = AxisVel<N, ZY>;
     constexpr int Q1 = 2 * NX + 1;  // velocity columns (N: level along y)
 #pragma unroll 1
     for (int v = w; v < NV; v += NW) {
         float slo0 = 0.f, slo1 = 0.f, shi0 = 0.f, shi1 = 0.f;
 #pragma unroll 1
-        for (int p = v; p < N * (N + 1) / 2; p += NV) {
-            int aa = 1, k = p;
-            while (k >= aa) {
-                k -= aa;
-                ++aa;
+        for (int p = v; p < AY::NPAIR; p += NV) {
+            int m = AY::M0, k = p;
+            while (k >= AY::vmag(m)) {
+                k -= AY::vmag(m);
+                ++m;
             }
-            if (need_lo) {  // velocity ny = -aa leaving row k through y = -1/2
-                const float *pl = fin + ((N - aa) * Q1 * plane + k * pitch);
+            if (need_lo) {  // velocity ny = -|v_m| leaving row k through y = -1/2
+                const float *pl = fin + (AY::ineg(m) * Q1 * plane + k * pitch);
 #pragma unroll
                 for (int ix = 0; ix < Q1; ++ix) {
                     slo0 += __ldg(pl + (ix * plane + win[2 * NX - ix]));
                     slo1 += __ldg(pl + (ix * plane + win[2 * NX - ix + 1]));
                 }
             }
-            if (need_hi) {  // velocity ny = +aa leaving row Ly-1-k through y = Ly-1/2
-                const float *ph = fin + ((N + aa) * Q1 * plane + (Ly - 1 - k) * pitch);
+            if (need_hi) {  // velocity ny = +|v_m| leaving row Ly-1-k through y = Ly-1/2
+                const float *ph = fin + (AY::ipos(m) * Q1 * plane + (Ly - 1 - k) * pitch);
 #pragma unroll
                 for (int ix = 0; ix < Q1; ++ix) {
                     shi0 += __ldg(ph + (ix * plane + win[2 * NX - ix]));
@@ -236,9 +240,10 @@ __device__ __forceinline__ void pair_collide_row(const AxisTable &tabx, int iy, 
     }
 }
 
-template <int N, int G, int R, int NXL = N>
+template <int N, int G, int R, int NXL = N, int ZY = 0>
 struct Step2DPair {
-    static constexpr int Q1 = 2 * N + 1;          // velocity rows (level N along y)
+    using AY = AxisVel<N, ZY>;
+    static constexpr int Q1 = AY::Q;              // velocity rows (level N along y)
     static constexpr int QX = 2 * NXL + 1;        // velocity columns (level NXL along x)
     static constexpr int RPG = (Q1 + G - 1) / G;  // velocity rows per warp group
     static constexpr int NW = G * R;              // warps per CTA
@@ -286,11 +291,11 @@ struct Step2DPair {
         for (int j = 0; j < NWIN; ++j) win[j] = wrap_shift(xc - NXL + j, Lx, one_wrap);
 
         // ---- phase 0: wall densities of this tile's columns ---------------
-        const bool need_lo = walls && (y0 < N);
-        const bool need_hi = walls && (y0 + R > Ly - N);
+        const bool need_lo = walls && (y0 < AY::VMAX);
+        const bool need_hi = walls && (y0 + R > Ly - AY::VMAX);
         if (need_lo || need_hi)
-            pair_wall_densities<N, NXL, NV>(ip, fin, Ly, pitch, plane, win, need_lo, need_hi, w, NW, lane,
-                                       sm.dsum, sm.rw);
+            pair_wall_densities<N, NXL, NV, ZY>(ip, fin, Ly, pitch, plane, win, need_lo, need_hi, w,
+                                                NW, lane, sm.dsum, sm.rw);
 
         // ---- phase 1: pull and partial moments -----------------------------
         // rows iy = g + k G of this warp group; f[k][ix] holds both nodes
@@ -300,9 +305,9 @@ struct Step2DPair {
         for (int k = 0; k < RPG; ++k) {
             const int iy = g + k * G;
             if (iy < Q1) {
-                const int ny = iy - N;
+                const int ny = AY::vel(iy);
                 int ys = yc - ny;
-                ys = walls ? min(max(ys, 0), Ly - 1) : wrap_shift(ys, Ly, Ly > N);
+                ys = walls ? min(max(ys, 0), Ly - 1) : wrap_shift(ys, Ly, Ly > AY::VMAX);
                 pair_load_row<NXL>(fin, iy, ys, pitch, plane, x, inner, win, f[k]);
             }
         }
@@ -310,7 +315,7 @@ struct Step2DPair {
         for (int k = 0; k < RPG; ++k) {
             const int iy = g + k * G;
             if (iy < Q1) {
-                const int ny = iy - N;
+                const int ny = AY::vel(iy);
                 const int ys = yc - ny;
                 if (walls && (ys < 0 || ys >= Ly)) {  // uniform across the warp
                     const bool lo = ys < 0;
@@ -361,8 +366,9 @@ struct Step2DPair {
         const f32x2 ux = mul2(add2(S_x, C_x), inv_rho);
         const f32x2 uy = mul2(add2(S_y, C_y), inv_rho);
         {
-            // sqrt(2/3) N per axis (Sec. 3)
-            const float umax = (float)(0.816496580927726 * N), umaxx = (float)(0.816496580927726 * NXL);
+            // sqrt(2/3) N per axis (Sec. 3), twice that on a 2N+2 axis
+            const float umax = (float)(0.816496580927726 * (ZY ? 2 * N : N));
+            const float umaxx = (float)(0.816496580927726 * NXL);
             const bool bad0 = act0 && (!(lo2(rho) > 0.f) || !(fabsf(lo2(ux)) <= umaxx) ||
                                        !(fabsf(lo2(uy)) <= umax));
             const bool bad1 = act1 && (!(hi2(rho) > 0.f) || !(fabsf(hi2(ux)) <= umaxx) ||
@@ -379,8 +385,8 @@ struct Step2DPair {
             eq_dev_all<NXL, float>(tabx, hi2(ux), d1);
 #pragma unroll
             for (int ix = 0; ix < QX; ++ix) dx[ix] = pk2(d0[ix], d1[ix]);
-            eq_dev_all<N, float>(tab, lo2(uy), dy0all);
-            eq_dev_all<N, float>(tab, hi2(uy), dy1all);
+            eq_dev_all<N, float, ZY>(tab, lo2(uy), dy0all);
+            eq_dev_all<N, float, ZY>(tab, hi2(uy), dy1all);
         } else {
             // the G warp groups share the polynomial work: group g evaluates
             // |n| = g, g + G, ... for both nodes and both axes, and the values
@@ -397,9 +403,10 @@ struct Step2DPair {
                     if (c < 2)
                         eq_parts<NXL, float>(tabx, n, u[c] * u[c], ae, bo);
                     else
-                        eq_parts<N, float>(tab, n, u[c] * u[c], ae, bo);
-                    plus[c] = n == 0 ? ae : fmaf(u[c], bo, ae);
-                    minus[c] = n == 0 ? ae : fmaf(-u[c], bo, ae);
+                        eq_parts<N, float, ZY>(tab, n, u[c] * u[c], ae, bo);
+                    const bool single = n == 0 && (c < 2 || !ZY);  // the zero velocity
+                    plus[c] = single ? ae : fmaf(u[c], bo, ae);
+                    minus[c] = single ? ae : fmaf(-u[c], bo, ae);
                 }
                 if (n <= NXL) {
                     *reinterpret_cast<f32x2 *>(&sm.eqx[r][NXL + n][2 * lane]) = pk2(plus[0], plus[1]);
@@ -408,9 +415,10 @@ struct Step2DPair {
                             pk2(minus[0], minus[1]);
                 }
                 if (n <= N) {
-                    *reinterpret_cast<f32x2 *>(&sm.eqy[r][N + n][2 * lane]) = pk2(plus[2], plus[3]);
-                    if (n != 0)
-                        *reinterpret_cast<f32x2 *>(&sm.eqy[r][N - n][2 * lane]) =
+                    *reinterpret_cast<f32x2 *>(&sm.eqy[r][AY::ipos(n)][2 * lane]) =
+                        pk2(plus[2], plus[3]);
+                    if (n != 0 || ZY)
+                        *reinterpret_cast<f32x2 *>(&sm.eqy[r][AY::ineg(n)][2 * lane]) =
                             pk2(minus[2], minus[3]);
                 }
             }

@@ -1,7 +1,8 @@
 // Candidate tile shapes of the fused 2D step on the 2N+2 hierarchy (Sec. 4:
 // the zero velocity removed), per level N, precision and kind: GLBM_ZVK_X1
 // (D1Q3 along x times the level-N 2N+2 axis along y) or GLBM_ZVK_XY (the 2N+2
-// axis on both). Only one-node tiles (V = 1) are compiled for these lattices.
+// axis on both). X1 lattices in FP32 also have packed pair tiles (V = 2, the
+// x axis being D1Q3); the others take one-node tiles (V = 1).
 #pragma once
 #include "glbm_internal.h"
 
@@ -15,17 +16,17 @@ struct TilesZv;
         static constexpr int count = sizeof(shape) / sizeof(shape[0]); \
         static_assert(count <= GLBM_MAX_TILES, "too many shapes");     \
     };
-// {G, R, V}: one-node tiles (V = 1). The 2N+2 velocity rows divide evenly
-// among G warps where the list allows it. Entry 0 is the fastest measured on
+// {G, R, V}: the 2N+2 velocity rows divide evenly among G warps where the
+// list allows it. Entry 0 is the fastest measured on
 // GB300 (1024 x 200 channels for X1, 512 x 256 for XY, walls).
-GLBM_TILES_ZV(1, float, GLBM_ZVK_X1, {1, 16, 1}, {1, 8, 1}, {1, 4, 1})
-GLBM_TILES_ZV(2, float, GLBM_ZVK_X1, {1, 8, 1}, {1, 4, 1}, {1, 16, 1})
-GLBM_TILES_ZV(3, float, GLBM_ZVK_X1, {1, 8, 1}, {1, 4, 1}, {2, 4, 1})
-GLBM_TILES_ZV(4, float, GLBM_ZVK_X1, {1, 8, 1}, {1, 4, 1}, {2, 2, 1})
-GLBM_TILES_ZV(5, float, GLBM_ZVK_X1, {1, 4, 1}, {2, 2, 1}, {1, 2, 1})
-GLBM_TILES_ZV(6, float, GLBM_ZVK_X1, {1, 4, 1}, {2, 2, 1}, {1, 2, 1})
-GLBM_TILES_ZV(7, float, GLBM_ZVK_X1, {1, 4, 1}, {2, 2, 1}, {2, 4, 1})
-GLBM_TILES_ZV(8, float, GLBM_ZVK_X1, {2, 2, 1}, {1, 4, 1}, {3, 2, 1})
+GLBM_TILES_ZV(1, float, GLBM_ZVK_X1, {1, 8, 2}, {1, 4, 2}, {1, 16, 1}, {1, 8, 1}, {1, 4, 1})
+GLBM_TILES_ZV(2, float, GLBM_ZVK_X1, {1, 4, 2}, {1, 8, 2}, {1, 8, 1}, {1, 4, 1}, {1, 16, 1})
+GLBM_TILES_ZV(3, float, GLBM_ZVK_X1, {1, 4, 2}, {2, 4, 2}, {1, 8, 1}, {1, 4, 1}, {2, 4, 1})
+GLBM_TILES_ZV(4, float, GLBM_ZVK_X1, {2, 2, 2}, {1, 4, 2}, {1, 8, 1}, {1, 4, 1}, {2, 2, 1})
+GLBM_TILES_ZV(5, float, GLBM_ZVK_X1, {2, 2, 2}, {1, 2, 2}, {1, 4, 1}, {2, 2, 1}, {1, 2, 1})
+GLBM_TILES_ZV(6, float, GLBM_ZVK_X1, {2, 2, 2}, {1, 2, 2}, {1, 4, 1}, {2, 2, 1}, {1, 2, 1})
+GLBM_TILES_ZV(7, float, GLBM_ZVK_X1, {2, 2, 2}, {4, 1, 2}, {1, 4, 1}, {2, 2, 1}, {2, 4, 1})
+GLBM_TILES_ZV(8, float, GLBM_ZVK_X1, {2, 2, 2}, {3, 1, 2}, {2, 2, 1}, {1, 4, 1}, {3, 2, 1})
 GLBM_TILES_ZV(1, double, GLBM_ZVK_X1, {1, 4, 1}, {1, 8, 1})
 GLBM_TILES_ZV(2, double, GLBM_ZVK_X1, {1, 4, 1}, {1, 8, 1})
 GLBM_TILES_ZV(3, double, GLBM_ZVK_X1, {1, 4, 1}, {2, 2, 1})
