@@ -71,7 +71,9 @@ typedef enum {
  *   nx, ny    nodes (ny ignored when dims == 1). With walls ny >= k+1; with
  *             bounce-back nx >= k+1.
  *   k         summations of D1Q3 per axis (level N = k+1, 2N+1 velocities per
- *             axis, Sec. 2); 0 <= k <= 7.
+ *             axis, Sec. 2); 0 <= k <= 7, and up to 12 for the channel models
+ *             D1Q3 x D1Q(2k+4) of the 2N+2 hierarchy (zv_axes GLBM_ZV_Y with
+ *             x_level 1; the paper's G-D1Q22 x D1Q3 .. G-D1Q28 x D1Q3).
  *   x_level   level along x of a 2D lattice: 0 (or k+1) takes the level of k
  *             on both axes; 1 makes the anisotropic product D1Q3 (x) times
  *             the level-(k+1) lattice (y), the tensor product of Sec. 4 with
@@ -251,8 +253,9 @@ glbm_status glbm_adjoint_flowrate(glbm_ctx *ctx, int64_t steps, int64_t ckpt_eve
  *
  * glbm_tile_count returns the number of candidates of level k in precision
  * prec (0 for an invalid pair); glbm_tile_shape returns candidate idx. Both
- * describe isotropic lattices; anisotropic contexts (x_level 1) have their own
- * lists, which glbm_autotune, glbm_set_tiles and glbm_get_tile_shape use.
+ * describe isotropic lattices of the 2N+1 hierarchy (levels k <= 7);
+ * anisotropic contexts (x_level 1) and the 2N+2 lattices (zv_axes) have their
+ * own lists, which glbm_autotune, glbm_set_tiles and glbm_get_tile_shape use.
  * glbm_get_tiles writes the index in use for every level (array of
  * GLBM_LEVELS ints, entry k for level k); glbm_set_tiles sets them (-1 keeps
  * a level's index; GLBM_E_INVAL and no change if an index is out of range).
@@ -267,7 +270,7 @@ glbm_status glbm_adjoint_flowrate(glbm_ctx *ctx, int64_t steps, int64_t ckpt_eve
  * partial moments before their compensated sum, so shapes of different G may
  * differ in the last bits of FP32 results. 2D contexts only. Synchronises.
  */
-#define GLBM_LEVELS 8
+#define GLBM_LEVELS 13
 #define GLBM_MAX_TILES 8
 int glbm_tile_count(int k, glbm_prec prec);
 glbm_status glbm_tile_shape(int k, glbm_prec prec, int idx, int *G, int *R, int *V);

@@ -102,8 +102,8 @@ struct glbm_ctx {
     size_t elem = 8;
     std::vector<Geo> geo;
     std::vector<glbm_config> cfg;
-    std::vector<AxisTable> tabs;     // index N (1..GLBM_MAXN)
-    std::vector<AxisTable> tabs_zv;  // the same levels on the 2N+2 hierarchy
+    std::vector<AxisTableHi> tabs;     // index N (1..GLBM_MAXN)
+    std::vector<AxisTableHi> tabs_zv;  // the same levels on the 2N+2 hierarchy
     std::vector<InstParams> h_ip;
     std::vector<double> tau;
     DevAlloc A{};
@@ -135,11 +135,11 @@ static const int kGraphChunk = 64;  // steps per captured graph (even: keeps buf
 static size_t bytes_state(const glbm_ctx *c) { return (size_t)c->pool_elems * c->elem; }
 
 // Tables of the y axis (level N) and the x axis (level NX) of a geometry.
-static const AxisTable &tab_y(const glbm_ctx *c, const Geo &g)
+static const AxisTableHi &tab_y(const glbm_ctx *c, const Geo &g)
 {
     return (g.zv & GLBM_ZV_Y) ? c->tabs_zv[g.N] : c->tabs[g.N];
 }
-static const AxisTable &tab_x(const glbm_ctx *c, const Geo &g)
+static const AxisTableHi &tab_x(const glbm_ctx *c, const Geo &g)
 {
     return (g.zv & GLBM_ZV_X) ? c->tabs_zv[g.NX] : c->tabs[g.NX];
 }
@@ -153,7 +153,7 @@ static void fill_inst(const glbm_ctx *c, const glbm_config &cfg, const Geo &g, I
 {
     memset(&ip, 0, sizeof(ip));
     const int N = g.N, NX = g.NX;
-    const AxisTable &tab = tab_y(c, g);
+    const AxisTableHi &tab = tab_y(c, g);
     const double theta_x = axis_theta(NX, (g.zv & GLBM_ZV_X) != 0);
     ip.omega = 1.0 / (tau + 0.5);
     ip.g_theta = c->dims == 2 ? cfg.g / theta_x : 0.0;
@@ -163,7 +163,7 @@ static void fill_inst(const glbm_ctx *c, const glbm_config &cfg, const Geo &g, I
     ip.inv_den = 1.0 / den;
     if (g.zv & GLBM_ZV_X) {
         // E^x_i(u_w) of a 2N+2 x axis by Horner on its table
-        const AxisTable &tx = tab_x(c, g);
+        const AxisTableHi &tx = tab_x(c, g);
         for (int i = 0; i < ax_q(tx); ++i) {
             const double dlo = glbm_eq_dev_host(tx, cfg.u_wall_lo, i);
             const double dhi = glbm_eq_dev_host(tx, cfg.u_wall_hi, i);
@@ -175,7 +175,7 @@ static void fill_inst(const glbm_ctx *c, const glbm_config &cfg, const Geo &g, I
     }
     // E^x_n(u_w) of a 2N+1 x axis from its coefficient table (FP64 Horner)
     double full[GLBM_MAXQ1 * GLBM_MAXQ1];
-    AxisTable tmp;
+    AxisTableHi tmp;
     glbm_build_axis_table(NX, &tmp, full);
     const int Q1 = (g.zv & GLBM_ZV_X) ? 0 : 2 * NX + 1;
     for (int n = 0; n < Q1; ++n) {
@@ -216,6 +216,11 @@ static glbm_status validate(const glbm_config &c)
     if (c.k < 0 || c.k > GLBM_MAXN - 1)
         return fail(GLBM_E_UNSUPPORTED, "k must be in 0..%d (got %d)", GLBM_MAXN - 1, c.k);
     const int N = c.k + 1;
+    // levels above 8: only the channel models D1Q3 x D1Q(2N+2) (Sec. 5.4 uses N = 10..13)
+    if (N > GLBM_MAXN_2N1 && !(c.dims == 2 && c.zv_axes == GLBM_ZV_Y && c.x_level == 1))
+        return fail(GLBM_E_UNSUPPORTED,
+                    "k > %d is compiled for D1Q3 x D1Q(2k+4) (x_level 1, zv_axes GLBM_ZV_Y) only",
+                    GLBM_MAXN_2N1 - 1);
     if (c.x_level < 0 || c.x_level > GLBM_MAXN)
         return fail(GLBM_E_INVAL, "x_level must be in 0..%d (got %d)", GLBM_MAXN, c.x_level);
     if (c.x_level != 0 && c.x_level != 1 && c.x_level != N)
@@ -553,7 +558,7 @@ extern "C" glbm_status glbm_eq_table(int k, double *out, size_t out_len)
     if (k < 0 || k > GLBM_MAXN - 1 || !out) return fail(GLBM_E_INVAL, "bad k or null output");
     const int N = k + 1, Q1 = 2 * N + 1;
     if (out_len < (size_t)Q1 * Q1) return fail(GLBM_E_INVAL, "output needs %d doubles", Q1 * Q1);
-    AxisTable t;
+    AxisTableHi t;
     glbm_build_axis_table(N, &t, out);
     return GLBM_OK;
 }
@@ -642,13 +647,19 @@ extern "C" glbm_status glbm_get_populations(glbm_ctx *c, int inst, double *f, in
 // ---------------------------------------------------------------------------
 // stepping
 // ---------------------------------------------------------------------------
-static Step2DArgs step_args(const glbm_ctx *c, int from)
+// Arguments of the uniform step; TY is AxisTable for levels up to 8 and
+// AxisTableHi above.
+template <class TY>
+static Step2DArgsT<TY> step_args_t(const glbm_ctx *c, int from)
 {
     const Geo &g = c->geo[0];
-    Step2DArgs a;
+    Step2DArgsT<TY> a;
     memset(&a, 0, sizeof(a));
-    a.tab = tab_y(c, g);
-    a.tabx = tab_x(c, g);
+    if constexpr (std::is_same<TY, AxisTableHi>::value)
+        a.tab = tab_y(c, g);
+    else
+        a.tab = glbm_narrow_table(tab_y(c, g));
+    a.tabx = glbm_narrow_table(tab_x(c, g));
     a.fin = c->buf[from];
     a.fout = c->buf[1 - from];
     a.ip = c->d_ip;
@@ -663,12 +674,13 @@ static Step2DArgs step_args(const glbm_ctx *c, int from)
     a.inst_stride = c->n_inst > 1 ? c->geo[1].off : 0;
     return a;
 }
+static Step2DArgs step_args(const glbm_ctx *c, int from) { return step_args_t<AxisTable>(c, from); }
 
 static BatchArgs batch_args(const glbm_ctx *c, int from)
 {
     BatchArgs b;
     memset(&b, 0, sizeof(b));
-    for (int N = 1; N <= GLBM_MAXN; ++N) b.tab[N - 1] = c->tabs[N];
+    for (int N = 1; N <= GLBM_MAXN_2N1; ++N) b.tab[N - 1] = glbm_narrow_table(c->tabs[N]);
     b.fin = c->buf[from];
     b.fout = c->buf[1 - from];
     b.ip = c->d_ip;
@@ -692,8 +704,11 @@ static int launches_per_step(const glbm_ctx *c)
 static cudaError_t launch_one_2d(const glbm_ctx *c, int from, cudaStream_t s)
 {
     if (c->hetero) return glbm_launch_batched_f32(batch_args(c, from), s);
-    const Step2DArgs a = step_args(c, from);
     const int N = c->geo[0].N;
+    if (N > GLBM_MAXN_2N1)
+        return glbm_launch_step2d_zv_hi(N, c->prec, c->tile[N],
+                                        step_args_t<AxisTableHi>(c, from), c->n_inst, s);
+    const Step2DArgs a = step_args(c, from);
     if (is_zv(c)) return glbm_launch_step2d_zv(N, zv_kind(c), c->prec, c->tile[N], a, c->n_inst, s);
     if (is_x1(c)) return glbm_launch_step2d_x1(N, c->prec, c->tile[N], a, c->n_inst, s);
     return c->prec == GLBM_FP64 ? glbm_launch_step2d_f64(N, c->tile[N], a, c->n_inst, s)
@@ -948,10 +963,11 @@ extern "C" glbm_status glbm_load(glbm_ctx *c, const char *path)
 // One uniform 2D step from an arbitrary pool image `fin` into `fout`.
 static cudaError_t launch_2d_between(const glbm_ctx *c, const void *fin, void *fout, cudaStream_t s)
 {
+    const int N = c->geo[0].N;
+    if (N > GLBM_MAXN_2N1) return cudaErrorInvalidValue;  // the adjoint takes levels <= 8
     Step2DArgs a = step_args(c, 0);
     a.fin = fin;
     a.fout = fout;
-    const int N = c->geo[0].N;
     if (is_zv(c)) return glbm_launch_step2d_zv(N, zv_kind(c), c->prec, c->tile[N], a, c->n_inst, s);
     if (is_x1(c)) return glbm_launch_step2d_x1(N, c->prec, c->tile[N], a, c->n_inst, s);
     return c->prec == GLBM_FP64 ? glbm_launch_step2d_f64(N, c->tile[N], a, c->n_inst, s)
@@ -1022,7 +1038,7 @@ extern "C" glbm_status glbm_adjoint_flowrate(glbm_ctx *c, int64_t steps, int64_t
     for (int i = 0; i < c->n_inst; ++i) {
         AdjArgs a;
         memset(&a, 0, sizeof(a));
-        a.tab = c->tabs[g.N];
+        a.tab = glbm_narrow_table(c->tabs[g.N]);
         a.ip = c->d_ip + i;
         a.G = G;
         a.Gw = G;
@@ -1124,9 +1140,12 @@ extern "C" glbm_status glbm_set_tiles(glbm_ctx *c, const int *tiles)
 {
     if (!c || !tiles) return fail(GLBM_E_INVAL, "null argument");
     TileShape sh[GLBM_MAX_TILES];
-    for (int k = 0; k < GLBM_LEVELS; ++k)
-        if (tiles[k] < -1 || tiles[k] >= ctx_tile_shapes(c, k + 1, sh))
+    // a level without candidates in this context keeps index 0 (accepted as given)
+    for (int k = 0; k < GLBM_LEVELS; ++k) {
+        const int n = ctx_tile_shapes(c, k + 1, sh);
+        if (tiles[k] < -1 || tiles[k] >= (n > 0 ? n : 1))
             return fail(GLBM_E_INVAL, "tile index %d out of range for k=%d", tiles[k], k);
+    }
     for (int k = 0; k < GLBM_LEVELS; ++k)
         if (tiles[k] >= 0) c->tile[k + 1] = tiles[k];
     return tiles_changed(c);

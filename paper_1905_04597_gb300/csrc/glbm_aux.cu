@@ -12,7 +12,7 @@ namespace {
 
 // E_i(u) - W_i of velocity index i at runtime level t.N (FP64 Horner on the
 // coefficient table; on the 2N+2 hierarchy the velocity is +-(2m+1)).
-__device__ double eq_dev_rt(const AxisTable &t, double u, int i)
+__device__ double eq_dev_rt(const AxisTableHi &t, double u, int i)
 {
     const int N = t.N;
     const int n = ax_vel(t, i);
@@ -53,7 +53,7 @@ __global__ void k_set_equilibrium(const __grid_constant__ AuxArgs a, void *f, in
     const int y = blockIdx.y;
     if (x >= a.Lx) return;
     // 1D: the only axis is x, with table tab and level N
-    const AxisTable &tx = a.dims == 2 ? a.tabx : a.tab;
+    const AxisTableHi &tx = a.dims == 2 ? a.tabx : a.tab;
     const int Q1x = ax_q(tx);
     const long long node = (long long)y * a.Lx + x;
     const double r = rho[node], u = ux[node], v = a.dims == 2 ? uy[node] : 0.0;
@@ -178,7 +178,7 @@ __global__ void k_moments(const __grid_constant__ AuxArgs a, const void *f, int 
     const int y = blockIdx.y;
     if (x >= a.Lx) return;
     const InstParams &ip = a.ip[inst];
-    const AxisTable &tx = a.dims == 2 ? a.tabx : a.tab;
+    const AxisTableHi &tx = a.dims == 2 ? a.tabx : a.tab;
     const int Q1x = ax_q(tx);
     const int Qy = a.dims == 2 ? ax_q(a.tab) : 1;
     const int vmax = a.tab.zv ? 2 * a.N + 1 : a.N;  // fastest y velocity

@@ -10,21 +10,31 @@ struct TabAcc;
 template <>
 struct TabAcc<double> {
     static constexpr bool HILO = false;
-    static __device__ __forceinline__ double C1lo(const AxisTable &, int) { return 0.0; }
-    static __device__ __forceinline__ double W(const AxisTable &t, int i) { return t.W[i]; }
-    static __device__ __forceinline__ double WN(const AxisTable &t, int i) { return t.WN[i]; }
-    static __device__ __forceinline__ double Ce(const AxisTable &t, int n, int i) { return t.Ce[n][i]; }
-    static __device__ __forceinline__ double Co(const AxisTable &t, int n, int i) { return t.Co[n][i]; }
+    template <class Tab>
+    static __device__ __forceinline__ double C1lo(const Tab &, int) { return 0.0; }
+    template <class Tab>
+    static __device__ __forceinline__ double W(const Tab &t, int i) { return t.W[i]; }
+    template <class Tab>
+    static __device__ __forceinline__ double WN(const Tab &t, int i) { return t.WN[i]; }
+    template <class Tab>
+    static __device__ __forceinline__ double Ce(const Tab &t, int n, int i) { return t.Ce[n][i]; }
+    template <class Tab>
+    static __device__ __forceinline__ double Co(const Tab &t, int n, int i) { return t.Co[n][i]; }
 };
 
 template <>
 struct TabAcc<float> {
     static constexpr bool HILO = true;
-    static __device__ __forceinline__ float C1lo(const AxisTable &t, int n) { return t.Co1lo[n]; }
-    static __device__ __forceinline__ float W(const AxisTable &t, int i) { return t.Wf[i]; }
-    static __device__ __forceinline__ float WN(const AxisTable &t, int i) { return t.WNf[i]; }
-    static __device__ __forceinline__ float Ce(const AxisTable &t, int n, int i) { return t.Cef[n][i]; }
-    static __device__ __forceinline__ float Co(const AxisTable &t, int n, int i) { return t.Cof[n][i]; }
+    template <class Tab>
+    static __device__ __forceinline__ float C1lo(const Tab &t, int n) { return t.Co1lo[n]; }
+    template <class Tab>
+    static __device__ __forceinline__ float W(const Tab &t, int i) { return t.Wf[i]; }
+    template <class Tab>
+    static __device__ __forceinline__ float WN(const Tab &t, int i) { return t.WNf[i]; }
+    template <class Tab>
+    static __device__ __forceinline__ float Ce(const Tab &t, int n, int i) { return t.Cef[n][i]; }
+    template <class Tab>
+    static __device__ __forceinline__ float Co(const Tab &t, int n, int i) { return t.Cof[n][i]; }
 };
 
 // Product rounded on its own (never contracted into a following addition), so
@@ -36,8 +46,8 @@ __device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(
 // Ae_n(v) (even powers >= 2) and Bo_n(v) (odd powers / u), v = u^2, so that
 // E_{+n}(u) - W_n = Ae + u Bo and E_{-n}(u) - W_n = Ae - u Bo. On the 2N+2
 // hierarchy (Z = 1) n is the magnitude index m of the velocities +-(2m+1).
-template <int N, typename T, int Z = 0>
-__device__ __forceinline__ void eq_parts(const AxisTable &t, int n, T v, T &ae, T &bo)
+template <int N, typename T, int Z = 0, class Tab>
+__device__ __forceinline__ void eq_parts(const Tab &t, int n, T v, T &ae, T &bo)
 {
     using A = TabAcc<T>;
     T a = A::Ce(t, n, N);
@@ -67,8 +77,8 @@ __device__ __forceinline__ void eq_parts(const AxisTable &t, int n, T v, T &ae, 
 
 // d[i] = E_i(u) - W_i for every velocity index i of the axis (i = n + N on
 // the 2N+1 hierarchy).
-template <int N, typename T, int Z = 0>
-__device__ __forceinline__ void eq_dev_all(const AxisTable &t, T u, T (&d)[2 * N + 1 + Z])
+template <int N, typename T, int Z = 0, class Tab>
+__device__ __forceinline__ void eq_dev_all(const Tab &t, T u, T (&d)[2 * N + 1 + Z])
 {
     using AV = AxisVel<N, Z>;
     const T v = u * u;
@@ -86,8 +96,8 @@ __device__ __forceinline__ void eq_dev_all(const AxisTable &t, T u, T (&d)[2 * N
 }
 
 // E_n(u) - W_n for a single n (compile-time after unrolling).
-template <int N, typename T>
-__device__ __forceinline__ T eq_dev_one(const AxisTable &t, T u, int n)
+template <int N, typename T, class Tab>
+__device__ __forceinline__ T eq_dev_one(const Tab &t, T u, int n)
 {
     const int an = n < 0 ? -n : n;
     T ae, bo;

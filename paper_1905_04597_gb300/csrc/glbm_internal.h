@@ -10,9 +10,12 @@
 // Record the thread's error message (glbm_last_error) and return `st`.
 glbm_status glbm_set_error(glbm_status st, const char *fmt, ...);
 
-#define GLBM_MAXN 8                       // highest level N = k + 1 compiled
+#define GLBM_MAXN 13                      // highest level N = k + 1 of any lattice
+#define GLBM_MAXN_2N1 8                   // highest level of the 2N+1 hierarchy and of
+                                          // the 2N+2 axes of D2Q(2N+2)^2 lattices
 #define GLBM_MAXQ1 (2 * GLBM_MAXN + 1)    // velocities per axis at GLBM_MAXN
 #define GLBM_MAXQA (2 * GLBM_MAXN + 2)    // the same on the 2N+2 hierarchy
+#include <type_traits>
 
 // Equilibrium of one axis at level N in lattice units (velocities -N..N,
 // temperature N/3), as a polynomial in the velocity u:
@@ -35,19 +38,27 @@ glbm_status glbm_set_error(glbm_status st, const char *fmt, ...);
 //   E_{+-(2m+1)}(u) = W_m + Ae_m(v) +- u Bo_m(v).
 // Velocity index i of the axis: v = i - N (2N+1 velocities) or
 // v = 2i - (2N+1) (2N+2 velocities); W and WN are indexed by i.
-struct AxisTable {
+// M is the capacity (highest level the arrays hold): the step kernels of
+// levels up to 8 take AxisTable, whose small size keeps eight of them (the
+// batch kernels' parameters) within the kernel-parameter limit; the levels up
+// to 13 of the D1Q3 x D1Q(2N+2) channels and the auxiliary kernels take
+// AxisTableHi.
+template <int M>
+struct AxisTableT {
     int N;
-    int zv;                                  // 1: the 2N+2 hierarchy
-    double W[GLBM_MAXQA];                    // by velocity index i
-    double WN[GLBM_MAXQA];                   // v_i W_i
-    double Ce[GLBM_MAXN + 1][GLBM_MAXN + 1];  // [n][i] = C[n][2i], n = 0..N
-    double Co[GLBM_MAXN + 1][GLBM_MAXN];      // [n][i] = C[n][2i+1]
-    float Wf[GLBM_MAXQA];
-    float WNf[GLBM_MAXQA];
-    float Cef[GLBM_MAXN + 1][GLBM_MAXN + 1];
-    float Cof[GLBM_MAXN + 1][GLBM_MAXN];
-    float Co1lo[GLBM_MAXN + 1];  // C[n][1] - Cof[n][0]: low part of the linear coefficient
+    int zv;                          // 1: the 2N+2 hierarchy
+    double W[2 * M + 2];             // by velocity index i
+    double WN[2 * M + 2];            // v_i W_i
+    double Ce[M + 1][M + 1];         // [n][i] = C[n][2i], n = 0..N
+    double Co[M + 1][M];             // [n][i] = C[n][2i+1]
+    float Wf[2 * M + 2];
+    float WNf[2 * M + 2];
+    float Cef[M + 1][M + 1];
+    float Cof[M + 1][M];
+    float Co1lo[M + 1];  // C[n][1] - Cof[n][0]: low part of the linear coefficient
 };
+using AxisTable = AxisTableT<GLBM_MAXN_2N1>;
+using AxisTableHi = AxisTableT<GLBM_MAXN>;
 
 // Velocities of one axis at compile time: level N, Z = 1 on the 2N+2 hierarchy.
 // m is the magnitude index of a +- pair (the zero velocity of the 2N+1
@@ -65,8 +76,13 @@ struct AxisVel {
 };
 
 // The same at run time from a table.
-__host__ __device__ inline int ax_q(const AxisTable &t) { return 2 * t.N + 1 + t.zv; }
-__host__ __device__ inline int ax_vel(const AxisTable &t, int i)
+template <class Tab>
+__host__ __device__ inline int ax_q(const Tab &t)
+{
+    return 2 * t.N + 1 + t.zv;
+}
+template <class Tab>
+__host__ __device__ inline int ax_vel(const Tab &t, int i)
 {
     return t.zv ? 2 * i - (2 * t.N + 1) : i - t.N;
 }
@@ -79,14 +95,16 @@ __host__ __device__ inline int ax_vel(const AxisTable &t, int i)
 // sum_n n C[n][j] = [j == 1] (momentum), hold to half an ulp of that entry.
 // With plainly rounded coefficients the residual (up to several ulps) acts as
 // a mass and momentum source of the same sign at every step of a steady flow.
-void glbm_build_axis_table(int N, AxisTable *t, double *full);
+void glbm_build_axis_table(int N, AxisTableHi *t, double *full);
 // Host: the table of level N on the 2N+2 hierarchy (zv = 1), from the exact
 // 2N+1 coefficients: C'_v[j] = (C_m[j] + C_{m+1}[j]) / 2^{j+1} for v = 2m+1
 // (u in units of c/2), with the same half-ulp adjustment of the mass and
 // momentum identities.
-void glbm_build_axis_table_zv(int N, AxisTable *t);
+void glbm_build_axis_table_zv(int N, AxisTableHi *t);
 // Host: E_i(u) - W_i of velocity index i from a table (FP64 Horner).
-double glbm_eq_dev_host(const AxisTable &t, double u, int i);
+double glbm_eq_dev_host(const AxisTableHi &t, double u, int i);
+// Host: the same table in the small layout (level N <= 8).
+AxisTable glbm_narrow_table(const AxisTableHi &t);
 
 // Per-instance constants read by the step kernels (one per lattice instance).
 struct InstParams {
@@ -109,9 +127,11 @@ struct InstParams {
     long long plane;  // elements per velocity plane (Ly * pitch)
 };
 
-// Arguments of one uniform (same geometry for every instance) 2D step.
-struct Step2DArgs {
-    AxisTable tab;        // level along y (and x for isotropic lattices)
+// Arguments of one uniform (same geometry for every instance) 2D step; TY is
+// the table type of the y axis (AxisTableHi above level 8).
+template <class TY>
+struct Step2DArgsT {
+    TY tab;               // level along y (and x for isotropic lattices)
     AxisTable tabx;       // level along x of anisotropic products (else unused)
     const void *fin;      // populations read (post-collision of the last step)
     void *fout;           // populations written
@@ -123,6 +143,10 @@ struct Step2DArgs {
     long long plane;      // elements per velocity plane
     long long inst_stride;// elements per instance
 };
+using Step2DArgs = Step2DArgsT<AxisTable>;
+using Step2DArgsHi = Step2DArgsT<AxisTableHi>;
+template <int N>
+using Step2DArgsOf = std::conditional_t<(N > GLBM_MAXN_2N1), Step2DArgsHi, Step2DArgs>;
 
 // Tile shape of the fused 2D step: G warps share a node's velocity rows, R node
 // rows per CTA, V x-adjacent nodes per thread (the candidates per level are
@@ -137,7 +161,7 @@ int glbm_tile_shapes(int N, int prec, TileShape *out);
 // Arguments of one step of a heterogeneous batch: one launch per level over
 // that level's slice of a work list of (instance, x0, y0, N) tiles.
 struct BatchArgs {
-    AxisTable tab[GLBM_MAXN];  // tab[N - 1]
+    AxisTable tab[GLBM_MAXN_2N1];  // tab[N - 1] (batches take the 2N+1 levels 1..8)
     const void *fin;           // pool read
     void *fout;                // pool written
     const InstParams *ip;      // per instance (offset, geometry, constants)
@@ -172,15 +196,18 @@ int glbm_tile_shapes_x1(int N, int prec, TileShape *out);
 enum { GLBM_ZVK_X1 = 0, GLBM_ZVK_XY = 1 };
 cudaError_t glbm_launch_step2d_zv(int N, int kind, int prec, int shape, const Step2DArgs &a,
                                   int n_inst, cudaStream_t s);
+// Levels 9..13 (kind GLBM_ZVK_X1 only).
+cudaError_t glbm_launch_step2d_zv_hi(int N, int prec, int shape, const Step2DArgsHi &a,
+                                     int n_inst, cudaStream_t s);
 int glbm_tile_shapes_zv(int N, int kind, int prec, TileShape *out);
 template <int N, typename T>
-cudaError_t glbm_step2d_zv_level(int kind, int shape, const Step2DArgs &a, int n_inst,
+cudaError_t glbm_step2d_zv_level(int kind, int shape, const Step2DArgsOf<N> &a, int n_inst,
                                  cudaStream_t s);
 
 // Auxiliary kernels (glbm_aux.cu).
 struct AuxArgs {
-    AxisTable tab;        // level N along y (the only axis in 1D)
-    AxisTable tabx;       // level NX along x (2D; equal to tab for isotropic lattices)
+    AxisTableHi tab;      // level N along y (the only axis in 1D)
+    AxisTableHi tabx;     // level NX along x (2D; equal to tab for isotropic lattices)
     const InstParams *ip;
     int dims, prec;       // prec: 0 = FP64, 1 = FP32 deviations
     int Lx, Ly, pitch, bc, N, NX;

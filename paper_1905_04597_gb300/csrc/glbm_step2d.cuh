@@ -50,7 +50,8 @@ struct Step2D {
     // One tile: columns x0..x0+31, rows y0..y0+R-1 of one instance whose
     // populations start at fin / fout; tab is the y axis's table, tabx the x
     // axis's (the same table for isotropic lattices). Every thread calls it.
-    __device__ static void run(const AxisTable &tab, const AxisTable &tabx, const InstParams &ip,
+    template <class TY, class TX>
+    __device__ static void run(const TY &tab, const TX &tabx, const InstParams &ip,
                                int Lx, int Ly,
                                int pitch, int plane, int bc, const T *__restrict__ fin,
                                T *__restrict__ fout, int x0, int y0, Smem &sm, unsigned *status,
@@ -317,7 +318,7 @@ __device__ __forceinline__ void advance_launch_counter(unsigned *step_ctr, unsig
 
 template <int N, typename T, int G, int R, int NXL = N, int ZY = 0, int ZX = 0>
 __global__ void __launch_bounds__(32 * G * R)
-    k_step2d(const __grid_constant__ Step2DArgs a)
+    k_step2d(const __grid_constant__ Step2DArgsOf<N> a)
 {
     using S = Step2D<N, T, G, R, NXL, ZY, ZX>;
     __shared__ typename S::Smem sm;
@@ -326,7 +327,11 @@ __global__ void __launch_bounds__(32 * G * R)
     T *fout = static_cast<T *>(a.fout) + (long long)inst * a.inst_stride;
     // launch counter (read before any CTA of this launch can advance it)
     const unsigned seed = S::DEV ? hash32(__ldcg(a.step_ctr) * 0x632BE5ABu + inst) : 0u;
-    S::run(a.tab, (NXL == N && ZX == ZY) ? a.tab : a.tabx, a.ip[inst], a.Lx, a.Ly, a.pitch,
-           (int)a.plane, a.bc, fin, fout, blockIdx.x * 32, blockIdx.y * R, sm, a.status, seed);
+    if constexpr (NXL == N && ZX == ZY)
+        S::run(a.tab, a.tab, a.ip[inst], a.Lx, a.Ly, a.pitch, (int)a.plane, a.bc, fin, fout,
+               blockIdx.x * 32, blockIdx.y * R, sm, a.status, seed);
+    else
+        S::run(a.tab, a.tabx, a.ip[inst], a.Lx, a.Ly, a.pitch, (int)a.plane, a.bc, fin, fout,
+               blockIdx.x * 32, blockIdx.y * R, sm, a.status, seed);
     if (S::DEV) advance_launch_counter(a.step_ctr, a.done_ctr);
 }

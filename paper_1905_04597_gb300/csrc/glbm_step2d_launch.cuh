@@ -6,7 +6,7 @@
 
 template <int N, int G, int R, int NXL = N, int ZY = 0>
 __global__ void __launch_bounds__(32 * G * R)
-    k_step2d_pair(const __grid_constant__ Step2DArgs a)
+    k_step2d_pair(const __grid_constant__ Step2DArgsOf<N> a)
 {
     using S = Step2DPair<N, G, R, NXL, ZY>;
     __shared__ __align__(16) typename S::Smem sm;
@@ -15,8 +15,12 @@ __global__ void __launch_bounds__(32 * G * R)
     float *fout = static_cast<float *>(a.fout) + (long long)inst * a.inst_stride;
     // launch counter (read before any CTA of this launch can advance it)
     const unsigned seed = hash32(__ldcg(a.step_ctr) * 0x632BE5ABu + inst);
-    S::run(a.tab, (NXL == N && !ZY) ? a.tab : a.tabx, a.ip[inst], a.Lx, a.Ly, a.pitch, (int)a.plane, a.bc,
-           fin, fout, blockIdx.x * S::TW, blockIdx.y * R, sm, a.status, seed);
+    if constexpr (NXL == N && !ZY)
+        S::run(a.tab, a.tab, a.ip[inst], a.Lx, a.Ly, a.pitch, (int)a.plane, a.bc, fin, fout,
+               blockIdx.x * S::TW, blockIdx.y * R, sm, a.status, seed);
+    else
+        S::run(a.tab, a.tabx, a.ip[inst], a.Lx, a.Ly, a.pitch, (int)a.plane, a.bc, fin, fout,
+               blockIdx.x * S::TW, blockIdx.y * R, sm, a.status, seed);
     advance_launch_counter(a.step_ctr, a.done_ctr);
 }
 

@@ -175,8 +175,8 @@ __device__ __forceinline__ void pair_load_row(const float *__restrict__ fin, int
 
 // The populations a wall re-emits into velocity row iy of a node pair
 // (sources inside the wall): W^y (drho_w W^x + rho_w (E^x(u_w) - W^x)).
-template <int N>
-__device__ __forceinline__ void pair_wall_row(const AxisTable &tab, const AxisTable &tabx,
+template <int N, class TY, class TX>
+__device__ __forceinline__ void pair_wall_row(const TY &tab, const TX &tabx,
                                               const InstParams &ip, int iy, bool lo, float rw0,
                                               float rw1, f32x2 (&f)[2 * N + 1])
 {
@@ -197,8 +197,8 @@ __device__ __forceinline__ void pair_wall_row(const AxisTable &tab, const AxisTa
 // the nodes' words h0, h1, the row and the column. E^x - W comes from the
 // registers dxr, or from shared memory at dxs (stride 32 pairs) when DXS.
 // N and tabx: the x axis.
-template <int N, bool DXS>
-__device__ __forceinline__ void pair_collide_row(const AxisTable &tabx, int iy, float wy, f32x2 dy,
+template <int N, bool DXS, class TX>
+__device__ __forceinline__ void pair_collide_row(const TX &tabx, int iy, float wy, f32x2 dy,
                                                  f32x2 rho, f32x2 drho, f32x2 om, float gto,
                                                  const f32x2 (&f)[2 * N + 1],
                                                  const f32x2 (&dxr)[2 * N + 1], const f32x2 *dxs,
@@ -264,7 +264,8 @@ struct Step2DPair {
     // One tile: columns x0..x0+63 (x0 a multiple of 64), rows y0..y0+R-1 of one
     // instance whose populations start at fin / fout (8-byte aligned planes);
     // tab is the y axis's table, tabx the x axis's (the same when isotropic).
-    __device__ static void run(const AxisTable &tab, const AxisTable &tabx, const InstParams &ip,
+    template <class TY, class TX>
+    __device__ static void run(const TY &tab, const TX &tabx, const InstParams &ip,
                                int Lx, int Ly,
                                int pitch, int plane, int bc, const float *__restrict__ fin,
                                float *__restrict__ fout, int x0, int y0, Smem &sm,

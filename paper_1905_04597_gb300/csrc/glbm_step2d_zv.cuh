@@ -9,7 +9,7 @@
 #include "glbm_tiles_zv.h"
 
 template <int N, typename T, int KIND, int I = 0>
-cudaError_t launch_zv_shape(int shape, const Step2DArgs &a, int n_inst, cudaStream_t s)
+cudaError_t launch_zv_shape(int shape, const Step2DArgsOf<N> &a, int n_inst, cudaStream_t s)
 {
     if constexpr (I < TilesZv<N, T, KIND>::count) {
         if (shape == I) {
@@ -33,7 +33,7 @@ cudaError_t launch_zv_shape(int shape, const Step2DArgs &a, int n_inst, cudaStre
 }
 
 template <int N, typename T>
-cudaError_t glbm_step2d_zv_level(int kind, int shape, const Step2DArgs &a, int n_inst,
+cudaError_t glbm_step2d_zv_level(int kind, int shape, const Step2DArgsOf<N> &a, int n_inst,
                                  cudaStream_t s)
 {
     return kind == GLBM_ZVK_X1 ? launch_zv_shape<N, T, GLBM_ZVK_X1>(shape, a, n_inst, s)

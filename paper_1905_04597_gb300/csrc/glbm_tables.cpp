@@ -92,14 +92,59 @@ static void convolve(int N, double (&cur)[GLBM_MAXQ1][GLBM_MAXQ1])
     }
 }
 
+// Exact value of a float in units of 2^-80 (the weights lie in (2^-40, 1)).
+static __int128 float_units(float f) { return (__int128)ldexp((double)f, 80); }
+
+// FP32 rest weights whose exact sum is 1 as closely as the floats allow. The
+// weight sum of one axis multiplies the other axis's momentum in the FP32
+// deviation equilibrium (delta f^eq = d^x rho e^y + W^x (...)), so a sum of
+// 1 + eps would scale the momentum by 1 + eps at every collision (nearest
+// rounding gives eps up to 4e-8; D1Q3: 1/6 + 2/3 + 1/6 = 1 + 3e-8). Starting
+// from the nearest floats, the weight whose one-ulp move (a velocity and its
+// mirror move together) brings the exact sum closest to 1 is moved, until no
+// move helps; no weight moves more than 8 ulps.
+static void balance_weights_f32(AxisTableHi *t, int Q)
+{
+    const int nd = (Q + 1) / 2;  // distinct weights: index i < nd and its mirror Q-1-i
+    float w[GLBM_MAXN + 1];
+    int mult[GLBM_MAXN + 1], moved[GLBM_MAXN + 1];
+    __int128 R = -((__int128)1 << 80);  // sum - 1
+    for (int j = 0; j < nd; ++j) {
+        w[j] = (float)t->W[j];
+        mult[j] = (j == Q - 1 - j) ? 1 : 2;
+        moved[j] = 0;
+        R += mult[j] * float_units(w[j]);
+    }
+    for (int it = 0; it < 16 * nd; ++it) {
+        int bj = -1, bd = 0;
+        __int128 bR = R;
+        for (int j = 0; j < nd; ++j) {
+            for (int d = -1; d <= 1; d += 2) {
+                if (moved[j] + d > 8 || moved[j] + d < -8) continue;
+                const float g = nextafterf(w[j], d > 0 ? 2.0f : 0.0f);
+                const __int128 R2 = R + mult[j] * (float_units(g) - float_units(w[j]));
+                const __int128 a2 = R2 < 0 ? -R2 : R2, ab = bR < 0 ? -bR : bR;
+                if (a2 < ab) {
+                    bj = j;
+                    bd = d;
+                    bR = R2;
+                }
+            }
+        }
+        if (bj < 0) break;
+        w[bj] = nextafterf(w[bj], bd > 0 ? 2.0f : 0.0f);
+        moved[bj] += bd;
+        R = bR;
+    }
+    for (int j = 0; j < nd; ++j) t->Wf[j] = t->Wf[Q - 1 - j] = w[j];
+}
+
 // FP32 copies and the hi + lo split of the linear coefficient.
-static void fill_f32(AxisTable *t, int Q)
+static void fill_f32(AxisTableHi *t, int Q)
 {
     const int N = t->N;
-    for (int i = 0; i < Q; ++i) {
-        t->Wf[i] = (float)t->W[i];
-        t->WNf[i] = (float)t->WN[i];
-    }
+    for (int i = 0; i < Q; ++i) t->WNf[i] = (float)t->WN[i];
+    balance_weights_f32(t, Q);
     for (int n = 0; n <= N; ++n) {
         for (int i = 0; i <= N; ++i) t->Cef[n][i] = (float)t->Ce[n][i];
         for (int i = 0; i < N; ++i) t->Cof[n][i] = (float)t->Co[n][i];
@@ -109,7 +154,7 @@ static void fill_f32(AxisTable *t, int Q)
     }
 }
 
-void glbm_build_axis_table(int N, AxisTable *t, double *full)
+void glbm_build_axis_table(int N, AxisTableHi *t, double *full)
 {
     const int Q1 = 2 * N + 1;
     // cur[n + N][j]: coefficient of z^n u^j; sized for the largest level
@@ -144,7 +189,7 @@ void glbm_build_axis_table(int N, AxisTable *t, double *full)
     }
 }
 
-void glbm_build_axis_table_zv(int N, AxisTable *t)
+void glbm_build_axis_table_zv(int N, AxisTableHi *t)
 {
     double cur[GLBM_MAXQ1][GLBM_MAXQ1];
     convolve(N, cur);
@@ -177,7 +222,7 @@ void glbm_build_axis_table_zv(int N, AxisTable *t)
     fill_f32(t, 2 * N + 2);
 }
 
-double glbm_eq_dev_host(const AxisTable &t, double u, int i)
+double glbm_eq_dev_host(const AxisTableHi &t, double u, int i)
 {
     const int N = t.N;
     const int v = ax_vel(t, i);
@@ -192,4 +237,31 @@ double glbm_eq_dev_host(const AxisTable &t, double u, int i)
         for (int k = N - 2; k >= 0; --k) bo = fma(bo, w, t.Co[m][k]);
     }
     return v >= 0 ? fma(u, bo, ae) : fma(-u, bo, ae);
+}
+
+AxisTable glbm_narrow_table(const AxisTableHi &t)
+{
+    AxisTable o;
+    memset(&o, 0, sizeof(o));
+    o.N = t.N;
+    o.zv = t.zv;
+    const int M = GLBM_MAXN_2N1;
+    for (int i = 0; i < 2 * M + 2; ++i) {
+        o.W[i] = t.W[i];
+        o.WN[i] = t.WN[i];
+        o.Wf[i] = t.Wf[i];
+        o.WNf[i] = t.WNf[i];
+    }
+    for (int n = 0; n <= M; ++n) {
+        for (int i = 0; i <= M; ++i) {
+            o.Ce[n][i] = t.Ce[n][i];
+            o.Cef[n][i] = t.Cef[n][i];
+        }
+        for (int i = 0; i < M; ++i) {
+            o.Co[n][i] = t.Co[n][i];
+            o.Cof[n][i] = t.Cof[n][i];
+        }
+        o.Co1lo[n] = t.Co1lo[n];
+    }
+    return o;
 }

@@ -6,8 +6,12 @@
 #pragma once
 #include "glbm_internal.h"
 
+// Combinations without candidates (D2Q(2N+2)^2 above level 8) have none.
 template <int N, typename T, int KIND>
-struct TilesZv;
+struct TilesZv {
+    static constexpr TileShape shape[1] = {{1, 1, 1}};
+    static constexpr int count = 0;
+};
 
 #define GLBM_TILES_ZV(N_, T_, K_, ...)                                 \
     template <>                                                        \
@@ -27,6 +31,12 @@ GLBM_TILES_ZV(5, float, GLBM_ZVK_X1, {2, 2, 2}, {1, 2, 2}, {1, 4, 1}, {2, 2, 1},
 GLBM_TILES_ZV(6, float, GLBM_ZVK_X1, {2, 2, 2}, {1, 2, 2}, {1, 4, 1}, {2, 2, 1}, {1, 2, 1})
 GLBM_TILES_ZV(7, float, GLBM_ZVK_X1, {2, 2, 2}, {4, 1, 2}, {1, 4, 1}, {2, 2, 1}, {2, 4, 1})
 GLBM_TILES_ZV(8, float, GLBM_ZVK_X1, {2, 2, 2}, {3, 1, 2}, {2, 2, 1}, {1, 4, 1}, {3, 2, 1})
+// levels 9..13 (the paper's G-D1Q22 x D1Q3 .. G-D1Q28 x D1Q3, Sec. 5.4)
+GLBM_TILES_ZV(9, float, GLBM_ZVK_X1, {4, 1, 2}, {2, 2, 2}, {2, 2, 1}, {1, 4, 1})
+GLBM_TILES_ZV(10, float, GLBM_ZVK_X1, {2, 2, 2}, {2, 1, 2}, {2, 2, 1}, {1, 4, 1})
+GLBM_TILES_ZV(11, float, GLBM_ZVK_X1, {2, 2, 2}, {3, 1, 2}, {2, 2, 1}, {4, 1, 1})
+GLBM_TILES_ZV(12, float, GLBM_ZVK_X1, {2, 2, 2}, {2, 1, 2}, {2, 2, 1}, {1, 4, 1})
+GLBM_TILES_ZV(13, float, GLBM_ZVK_X1, {2, 2, 2}, {4, 1, 2}, {2, 2, 1}, {4, 1, 1})
 GLBM_TILES_ZV(1, double, GLBM_ZVK_X1, {1, 4, 1}, {1, 8, 1})
 GLBM_TILES_ZV(2, double, GLBM_ZVK_X1, {1, 4, 1}, {1, 8, 1})
 GLBM_TILES_ZV(3, double, GLBM_ZVK_X1, {1, 4, 1}, {2, 2, 1})
@@ -35,6 +45,11 @@ GLBM_TILES_ZV(5, double, GLBM_ZVK_X1, {1, 4, 1}, {2, 2, 1})
 GLBM_TILES_ZV(6, double, GLBM_ZVK_X1, {2, 2, 1}, {1, 4, 1})
 GLBM_TILES_ZV(7, double, GLBM_ZVK_X1, {2, 2, 1}, {1, 2, 1})
 GLBM_TILES_ZV(8, double, GLBM_ZVK_X1, {2, 2, 1}, {3, 2, 1})
+GLBM_TILES_ZV(9, double, GLBM_ZVK_X1, {1, 4, 1}, {2, 2, 1})
+GLBM_TILES_ZV(10, double, GLBM_ZVK_X1, {1, 4, 1}, {2, 2, 1})
+GLBM_TILES_ZV(11, double, GLBM_ZVK_X1, {2, 2, 1}, {4, 1, 1})
+GLBM_TILES_ZV(12, double, GLBM_ZVK_X1, {1, 4, 1}, {2, 2, 1})
+GLBM_TILES_ZV(13, double, GLBM_ZVK_X1, {2, 2, 1}, {4, 1, 1})
 GLBM_TILES_ZV(1, float, GLBM_ZVK_XY, {1, 16, 1}, {1, 8, 1}, {1, 4, 1})
 GLBM_TILES_ZV(2, float, GLBM_ZVK_XY, {1, 4, 1}, {2, 4, 1}, {1, 8, 1})
 GLBM_TILES_ZV(3, float, GLBM_ZVK_XY, {2, 4, 1}, {2, 2, 1}, {1, 4, 1})

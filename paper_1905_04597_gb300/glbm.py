@@ -106,7 +106,7 @@ def check(status):
     raise GlbmError(status, msg)
 
 
-LEVELS = 8      # levels k = 0..7
+LEVELS = 13     # levels k = 0..12 (k > 7: D1Q3 x D1Q(2k+4) only)
 MAX_TILES = 8   # candidate tile shapes per level and precision
 
 
@@ -300,7 +300,7 @@ class Lattice:
         return np.array(J[:]), np.array(dt[:]), np.array(dg[:])
 
     def tiles(self):
-        """Tile shape index in use for every level k = 0..7."""
+        """Tile shape index in use for every level k = 0..LEVELS-1."""
         t = (ctypes.c_int * LEVELS)()
         check(lib().glbm_get_tiles(self.h, t))
         return list(t)

@@ -40,7 +40,7 @@ def test_library_exports_every_declared_symbol():
     assert not missing, missing
 
 
-@pytest.mark.parametrize("k", range(0, 8))
+@pytest.mark.parametrize("k", range(0, 13))
 def test_coefficient_table_matches_oracle(k):
     """Row a1: the convolution-built polynomial table reproduces the factorial-sum
     equilibrium of the oracle at any velocity (Sec. 2, Eqs. maineq03-05)."""
@@ -55,7 +55,7 @@ def test_coefficient_table_matches_oracle(k):
 
 def test_table_rejects_bad_level():
     with pytest.raises(glbm.GlbmError):
-        glbm.eq_table(8)
+        glbm.eq_table(13)
 
 
 def test_invalid_config_is_rejected_before_any_device_call():
@@ -64,8 +64,15 @@ def test_invalid_config_is_rejected_before_any_device_call():
     st = glbm.lib().glbm_create(ctypes.byref(cfg), 1, None, ctypes.byref(h))
     assert st == glbm.E_INVAL and not h.value
     assert b"ny" in glbm.lib().glbm_last_error()
-    cfg = glbm.make_config(dims=2, nx=8, ny=8, k=9, tau=1.0)
+    cfg = glbm.make_config(dims=2, nx=8, ny=8, k=9, tau=1.0)  # k > 7: 2N+2 channels only
     assert glbm.lib().glbm_create(ctypes.byref(cfg), 1, None, ctypes.byref(h)) == glbm.E_UNSUPPORTED
+    cfg = glbm.make_config(dims=2, nx=8, ny=32, k=9, tau=1.0, x_level=1)
+    assert glbm.lib().glbm_create(ctypes.byref(cfg), 1, None, ctypes.byref(h)) == glbm.E_UNSUPPORTED
+    cfg = glbm.make_config(dims=2, nx=8, ny=32, k=13, tau=1.0, x_level=1, zv_axes=glbm.ZV_Y)
+    assert glbm.lib().glbm_create(ctypes.byref(cfg), 1, None, ctypes.byref(h)) == glbm.E_UNSUPPORTED
+    cfg = glbm.make_config(dims=2, nx=8, ny=20, k=9, tau=1.0, x_level=1, zv_axes=glbm.ZV_Y)
+    assert glbm.lib().glbm_create(ctypes.byref(cfg), 1, None, ctypes.byref(h)) == glbm.E_INVAL
+    assert b"ny >= 21" in glbm.lib().glbm_last_error()
     cfg = glbm.make_config(dims=2, nx=8, ny=8, k=1, tau=-1.0)
     assert glbm.lib().glbm_create(ctypes.byref(cfg), 1, None, ctypes.byref(h)) == glbm.E_INVAL
     cfg = glbm.make_config(dims=2, nx=8, ny=8, k=0, tau=1.0, u_wall_lo=0.9)  # > sqrt(2/3)
@@ -79,7 +86,7 @@ def test_anisotropic_configs_are_checked_before_any_device_call():
     create = glbm.lib().glbm_create
     cfg = glbm.make_config(dims=2, nx=8, ny=8, k=5, tau=1.0, x_level=3)
     assert create(ctypes.byref(cfg), 1, None, ctypes.byref(h)) == glbm.E_UNSUPPORTED
-    cfg = glbm.make_config(dims=2, nx=8, ny=8, k=5, tau=1.0, x_level=9)
+    cfg = glbm.make_config(dims=2, nx=8, ny=8, k=5, tau=1.0, x_level=14)
     assert create(ctypes.byref(cfg), 1, None, ctypes.byref(h)) == glbm.E_INVAL
     cfg = glbm.make_config(dims=1, nx=8, k=2, tau=1.0, x_level=1)
     assert create(ctypes.byref(cfg), 1, None, ctypes.byref(h)) == glbm.E_INVAL
@@ -130,7 +137,7 @@ def test_tile_shape_candidates():
     with 1 <= G <= 2k+3 warp groups, at most 512 threads per CTA and one or
     two nodes per thread (pairs in FP32 only); invalid levels have none."""
     for prec in (glbm.FP64, glbm.FP32_DEV):
-        for k in range(glbm.LEVELS):
+        for k in range(8):
             shapes = glbm.tile_shapes(k, prec)
             assert 1 <= len(shapes) <= glbm.MAX_TILES
             assert len(set(shapes)) == len(shapes)

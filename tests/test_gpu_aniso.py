@@ -86,7 +86,7 @@ def test_every_tile_shape_one_step(prec):
         times = base.autotune(reps=2)
         assert set(times) == {k} and len(times[k]) >= 2
         G, R, V = base.tile_shape(k)
-        assert G >= 1 and R >= 1 and V == 1
+        assert G >= 1 and R >= 1 and (V == 1 or prec == glbm.FP32_DEV)
         n_shapes = len(times[k])
         base.close()
         for idx in range(n_shapes):

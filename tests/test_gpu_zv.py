@@ -72,6 +72,15 @@ def test_one_step_all_populations(kind, k, bc, prec):
 
 
 @pytest.mark.parametrize("prec", [glbm.FP64, glbm.FP32_DEV])
+@pytest.mark.parametrize("bc", [glbm.BC_WALLS, glbm.BC_PERIODIC])
+@pytest.mark.parametrize("k", range(8, 13))
+def test_one_step_all_populations_channel_levels_9_to_13(k, bc, prec):
+    """Levels N = 9..13 exist for the channel models only (the paper's
+    G-D1Q22 x D1Q3 .. G-D1Q28 x D1Q3)."""
+    test_one_step_all_populations("x1", k, bc, prec)
+
+
+@pytest.mark.parametrize("prec", [glbm.FP64, glbm.FP32_DEV])
 @pytest.mark.parametrize("k", [1, 4, 7])
 @pytest.mark.parametrize("kind", sorted(KINDS))
 def test_moments_after_steps(kind, k, prec):
@@ -90,6 +99,34 @@ def test_moments_after_steps(kind, k, prec):
     want, F = oracle_moments(o, X)
     errs = rel_errors(lat.moments(0), want, F=F, q1x=_q1x(kind, k), zv=KINDS[kind])
     assert max(errs.values()) < TOL[prec], errs
+    lat.close()
+
+
+@pytest.mark.parametrize("prec", [glbm.FP64, glbm.FP32_DEV])
+def test_after_steps_level_13(prec):
+    """G-D1Q28 x D1Q3 (the paper's N = 13 channel model) after 60 steps: every
+    population (FP64 within 1e-12 of the oracle's), and the moments. At N = 13
+    the heat flux sums terms up to |xi|^3 = 27^3 times the populations, so two
+    FP64 summation orders differ by about 1e-15 of the terms' sum: its FP64
+    bound is 5e-12 against the metric's 1e-3 floor, the other fields keep 1e-12."""
+    k, N = 12, 13
+    nx, ny, steps = 48, 3 * N + 8, 60
+    kw = dict(kn=0.15, u_wall_lo=-0.05, u_wall_hi=0.05, g=1e-5)
+    fields = inputs.random_macro(933, nx, ny)
+    lat = glbm.Lattice(_cfg("x1", k, nx, ny, prec, **kw))
+    lat.set_equilibrium(0, *fields)
+    lat.step(steps)
+    lat.sync()
+    tau = orc.tau_from_kn(N, ny, 0.15, zv=1)
+    o = _oracle("x1", k, nx, ny, orc.BC_WALLS, tau, -0.05, 0.05, 1e-5)
+    X, _ = o.run(o.equilibrium(*fields), steps)
+    got = lat.get_populations(0)
+    assert np.abs(got - X).max() / np.abs(X).max() < (1e-12 if prec == glbm.FP64 else 1e-5)
+    want, F = oracle_moments(o, X)
+    errs = rel_errors(lat.moments(0), want, F=F, q1x=3, zv=glbm.ZV_Y)
+    for name, e in errs.items():
+        bound = 5e-12 if (prec == glbm.FP64 and name in ("qx", "qy")) else TOL[prec]
+        assert e < bound, (name, errs)
     lat.close()
 
 
@@ -115,7 +152,7 @@ def test_equilibrium_has_the_shifted_temperature(kind):
 @pytest.mark.parametrize("prec", [glbm.FP64, glbm.FP32_DEV])
 @pytest.mark.parametrize("kind", sorted(KINDS))
 def test_every_tile_shape_one_step(kind, prec):
-    for k in (2, 7):
+    for k in (2, 7) if kind == "xy" else (2, 7, 10, 12):
         N = k + 1
         nx, ny = 45, 2 * N + 3
         Q = _q1x(kind, k) * (2 * N + 2)
@@ -186,7 +223,7 @@ def test_conservation_checkpoint_and_unsupported_operations(tmp_path):
         x.close()
 
 
-@pytest.mark.parametrize("k", [0, 2, 5, 7])
+@pytest.mark.parametrize("k", [0, 2, 5, 7, 9, 12])
 def test_pair_tiles_bitwise_equal_one_node_tiles(k):
     """D1Q3 x D1Q(2N+2) in FP32: pair and one-node tiles of the same warp-group
     split give bit-identical populations (same operations, same order)."""

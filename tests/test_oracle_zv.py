@@ -81,7 +81,7 @@ def test_d1q4_rest_weights():
                                rtol=1e-15)
 
 
-@pytest.mark.parametrize("N", range(1, 9))
+@pytest.mark.parametrize("N", range(1, 14))
 @pytest.mark.parametrize("u", [0.0, 0.11, -0.54, 1.3])
 def test_moments_shifted_temperature_and_third(N, u):
     """Sec. 4: mass and momentum exact, second moment u^2 + (4N+3)/3; App. B: the
@@ -96,7 +96,7 @@ def test_moments_shifted_temperature_and_third(N, u):
     assert (v ** 3 * f).sum() == pytest.approx(8 * m3c, abs=2e-13)
 
 
-@pytest.mark.parametrize("N", [1, 2, 5, 8])
+@pytest.mark.parametrize("N", [1, 2, 5, 8, 13])
 def test_positive_on_the_positivity_domain(N):
     """Sec. 3 bounds |u/c| by sqrt(2/3) N; on the c/2 lattice that is twice as wide."""
     umax = 2 * np.sqrt(2.0 / 3.0) * N
