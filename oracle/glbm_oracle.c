@@ -36,6 +36,11 @@
  * axis (orc_cfg.zv): the paper's channel models G-D1Q6 x D1Q3 and
  * G-D1Q8 x D1Q3 take it along the wall normal y only, G-D2Q784 along both.
  *
+ * 3D lattices (Sec. 4: the product extends to any number of axes) take the
+ * product of three 1D levels, q = (iz Qy + iy) Qx + ix and f[q][z][y][x],
+ * periodic in x and z, walls (or periodicity) in y as in 2D; the wall
+ * re-emits rho_w(x, z) E^x(u_w) E^y(0) E^z(0).
+ *
  * Boundary readings (the paper cites its wall condition but states no
  * formula; Sec. 5.3-5.4):
  *   - walls sit halfway between nodes, at y = -1/2 and y = Ly - 1/2;
@@ -72,6 +77,8 @@ typedef struct {
     double g;     /* body force along x (lattice units), 2D only */
     int zv;       /* 2D axes that take the 2N+2 hierarchy without zero velocity:
                      bit 0 (ORC_ZV_X) x, bit 1 (ORC_ZV_Y) y; 0 = none */
+    int NZ;       /* level N along z (3D only) */
+    int Lz;       /* nodes along z (1 below 3D) */
 } orc_cfg;
 
 static double orc_factorial(int n)
@@ -236,6 +243,16 @@ double orc_tau_from_kn(int N, double H, double kn)
 static int orc_check(const orc_cfg *c)
 {
     if (c->zv < 0 || c->zv > 3 || (c->zv && c->dims != 2)) return -1;
+    if (c->dims == 3) {
+        if (c->NX < 1 || c->NX > ORC_MAX_N || c->NY < 1 || c->NY > ORC_MAX_N || c->NZ < 1 ||
+            c->NZ > ORC_MAX_N)
+            return -1;
+        if (c->Lx < 1 || c->Ly < 1 || c->Lz < 1) return -1;
+        if (c->bc == ORC_BC_WALLS && c->Ly < c->NY) return -1;
+        if (c->bc != ORC_BC_WALLS && c->bc != ORC_BC_PERIODIC) return -1;
+        return c->tau > 0.0 ? 0 : -1;
+    }
+    if (c->Lz != 1 && c->Lz != 0) return -1;
     if (c->dims == 1) {
         if (c->NX < 1 || c->NX > ORC_MAX_N || c->Lx < 1 || c->Ly != 1) return -1;
         if (c->bc == ORC_BC_BOUNCEBACK && c->Lx < c->NX) return -1;
@@ -253,12 +270,19 @@ static int orc_check(const orc_cfg *c)
 
 static int orc_nq(const orc_cfg *c)
 {
+    if (c->dims == 3) return (2 * c->NX + 1) * (2 * c->NY + 1) * (2 * c->NZ + 1);
     return c->dims == 1 ? 2 * c->NX + 1 : (2 * c->NX + 1 + ORC_ZVX(c)) * (2 * c->NY + 1 + ORC_ZVY(c));
 }
 
 /* ------------------------------------------------------------------------ */
 /* Streaming (push form)                                                     */
 /* ------------------------------------------------------------------------ */
+
+/* Nodes of the lattice (all axes). */
+static size_t orc_nodes(const orc_cfg *c)
+{
+    return (size_t)c->Lx * c->Ly * (c->dims == 3 ? c->Lz : 1);
+}
 
 static int orc_wrap(int i, int L)
 {
@@ -367,11 +391,87 @@ static void orc_stream2d(const orc_cfg *c, const double *X, double *F)
     free(Dhi);
 }
 
+/*
+ * 3D push streaming: periodic in x and z; in y as in 2D (periodic, or the
+ * diffuse walls with the absorbed mass of each (x, z) column re-emitted with
+ * the shape E^x(u_w) W^y W^z).
+ */
+static void orc_stream3d(const orc_cfg *c, const double *X, double *F)
+{
+    const int NX = c->NX, NY = c->NY, NZ = c->NZ, Lx = c->Lx, Ly = c->Ly, Lz = c->Lz;
+    const int Qx = 2 * NX + 1, Qy = 2 * NY + 1, Qz = 2 * NZ + 1;
+    const size_t plane = (size_t)Lx * Ly * Lz, col = (size_t)Lx * Lz;
+    double *Dlo = (double *)calloc(col, sizeof(double));
+    double *Dhi = (double *)calloc(col, sizeof(double));
+    for (int iz = 0; iz < Qz; ++iz)
+        for (int iy = 0; iy < Qy; ++iy)
+            for (int ix = 0; ix < Qx; ++ix) {
+                const int q = (iz * Qy + iy) * Qx + ix, nx = ix - NX, ny = iy - NY, nz = iz - NZ;
+                for (int z = 0; z < Lz; ++z)
+                    for (int y = 0; y < Ly; ++y)
+                        for (int x = 0; x < Lx; ++x) {
+                            const double v = X[q * plane + ((size_t)z * Ly + y) * Lx + x];
+                            const int xd = orc_wrap(x + nx, Lx), zd = orc_wrap(z + nz, Lz);
+                            const int yd = y + ny;
+                            if (c->bc == ORC_BC_PERIODIC)
+                                F[q * plane + ((size_t)zd * Ly + orc_wrap(yd, Ly)) * Lx + xd] = v;
+                            else if (yd < 0)
+                                Dlo[(size_t)zd * Lx + xd] += v;
+                            else if (yd >= Ly)
+                                Dhi[(size_t)zd * Lx + xd] += v;
+                            else
+                                F[q * plane + ((size_t)zd * Ly + yd) * Lx + xd] = v;
+                        }
+            }
+    if (c->bc == ORC_BC_WALLS) {
+        double Wy[2 * ORC_MAX_N + 1], Wz[2 * ORC_MAX_N + 1];
+        double Elo[2 * ORC_MAX_N + 1], Ehi[2 * ORC_MAX_N + 1];
+        orc_eq_lattice(NY, 0.0, Wy);
+        orc_eq_lattice(NZ, 0.0, Wz);
+        orc_eq_lattice(NX, c->uw_lo, Elo);
+        orc_eq_lattice(NX, c->uw_hi, Ehi);
+        /* emitted mass per unit rho_w: sum over velocities leaving the wall of
+           |xi_y| E^x W^y W^z */
+        double den = 0.0, den_hi = 0.0;
+        for (int iz = 0; iz < Qz; ++iz)
+            for (int iy = 0; iy < Qy; ++iy)
+                for (int ix = 0; ix < Qx; ++ix) {
+                    const int ny = iy - NY;
+                    if (ny > 0) den += ny * Elo[ix] * Wy[iy] * Wz[iz];
+                    if (ny < 0) den_hi += -ny * Ehi[ix] * Wy[iy] * Wz[iz];
+                }
+        for (int z = 0; z < Lz; ++z)
+            for (int x = 0; x < Lx; ++x) {
+                const double rlo = Dlo[(size_t)z * Lx + x] / den;
+                const double rhi = Dhi[(size_t)z * Lx + x] / den_hi;
+                for (int iz = 0; iz < Qz; ++iz)
+                    for (int iy = 0; iy < Qy; ++iy) {
+                        const int ny = iy - NY;
+                        for (int ix = 0; ix < Qx; ++ix) {
+                            const int q = (iz * Qy + iy) * Qx + ix;
+                            for (int k = 0; k < (ny > 0 ? ny : -ny); ++k) {
+                                if (ny > 0)
+                                    F[q * plane + ((size_t)z * Ly + k) * Lx + x] =
+                                        rlo * Elo[ix] * Wy[iy] * Wz[iz];
+                                else
+                                    F[q * plane + ((size_t)z * Ly + (Ly - 1 - k)) * Lx + x] =
+                                        rhi * Ehi[ix] * Wy[iy] * Wz[iz];
+                            }
+                        }
+                    }
+            }
+    }
+    free(Dlo);
+    free(Dhi);
+}
+
 int orc_stream(const orc_cfg *c, const double *X, double *F)
 {
     if (orc_check(c)) return -1;
     if (c->dims == 1)
         orc_stream1d(c, X, F);
+    else if (c->dims == 3)
+        orc_stream3d(c, X, F);
     else
         orc_stream2d(c, X, F);
     return 0;
@@ -409,6 +509,45 @@ int orc_collide(const orc_cfg *c, const double *F, double *X)
                 double f = F[(n + N) * L + x];
                 X[(n + N) * L + x] = f + omega * (rho * E[n + N] - f);
             }
+        }
+        return bad;
+    }
+    if (c->dims == 3) {
+        const int NX = c->NX, NY = c->NY, NZ = c->NZ;
+        const int Qx = 2 * NX + 1, Qy = 2 * NY + 1, Qz = 2 * NZ + 1;
+        const size_t plane = orc_nodes(c);
+        double Wx[2 * ORC_MAX_N + 1], Wy[2 * ORC_MAX_N + 1], Wz[2 * ORC_MAX_N + 1];
+        double Ex[2 * ORC_MAX_N + 1], Ey[2 * ORC_MAX_N + 1], Ez[2 * ORC_MAX_N + 1];
+        orc_eq_lattice(NX, 0.0, Wx);
+        orc_eq_lattice(NY, 0.0, Wy);
+        orc_eq_lattice(NZ, 0.0, Wz);
+        const double theta_x = NX / 3.0;
+        for (size_t node = 0; node < plane; ++node) {
+            double rho = 0.0, jx = 0.0, jy = 0.0, jz = 0.0;
+            for (int iz = 0; iz < Qz; ++iz)
+                for (int iy = 0; iy < Qy; ++iy)
+                    for (int ix = 0; ix < Qx; ++ix) {
+                        const double f = F[((iz * Qy + iy) * Qx + ix) * plane + node];
+                        rho += f;
+                        jx += (ix - NX) * f;
+                        jy += (iy - NY) * f;
+                        jz += (iz - NZ) * f;
+                    }
+            const double ux = jx / rho, uy = jy / rho, uz = jz / rho;
+            const double b = sqrt(2.0 / 3.0);
+            if (!(rho > 0.0) || fabs(ux) > b * NX || fabs(uy) > b * NY || fabs(uz) > b * NZ) ++bad;
+            orc_eq_lattice(NX, ux, Ex);
+            orc_eq_lattice(NY, uy, Ey);
+            orc_eq_lattice(NZ, uz, Ez);
+            for (int iz = 0; iz < Qz; ++iz)
+                for (int iy = 0; iy < Qy; ++iy)
+                    for (int ix = 0; ix < Qx; ++ix) {
+                        const size_t idx = ((iz * Qy + iy) * Qx + ix) * plane + node;
+                        const double f = F[idx];
+                        const double feq = rho * Ex[ix] * Ey[iy] * Ez[iz];
+                        const double force = Wx[ix] * Wy[iy] * Wz[iz] * (ix - NX) * c->g / theta_x;
+                        X[idx] = f + omega * (feq - f) + force;
+                    }
         }
         return bad;
     }
@@ -463,11 +602,47 @@ int orc_collide(const orc_cfg *c, const double *F, double *X)
  * temperature, heat flux and shear stress are the usual central moments):
  * 2D out[7][Ly][Lx] = rho, u_x, u_y, T = sum |xi-u|^2 f / (2 rho),
  *   q_x, q_y = (1/2) sum (xi-u)_a |xi-u|^2 f, sigma_xy = sum (xi-u)_x (xi-u)_y f;
- * 1D out[4][L] = rho, u, T = sum (xi-u)^2 f / rho, q = (1/2) sum (xi-u)^3 f.
+ * 1D out[4][L] = rho, u, T = sum (xi-u)^2 f / rho, q = (1/2) sum (xi-u)^3 f;
+ * 3D out[9][Lz][Ly][Lx] = rho, u_x, u_y, T = sum |xi-u|^2 f / (3 rho), q_x,
+ *   q_y, sigma_xy, u_z, q_z (the 2D fields first, then the z ones).
  */
 int orc_macro(const orc_cfg *c, const double *F, double *out)
 {
     if (orc_check(c)) return -1;
+    if (c->dims == 3) {
+        const int NX = c->NX, NY = c->NY, NZ = c->NZ;
+        const int Qx = 2 * NX + 1, Qy = 2 * NY + 1, Qz = 2 * NZ + 1;
+        const size_t plane = orc_nodes(c);
+        for (size_t node = 0; node < plane; ++node) {
+            double rho = 0.0, jx = 0.0, jy = 0.0, jz = 0.0;
+            for (int iz = 0; iz < Qz; ++iz)
+                for (int iy = 0; iy < Qy; ++iy)
+                    for (int ix = 0; ix < Qx; ++ix) {
+                        const double f = F[((iz * Qy + iy) * Qx + ix) * plane + node];
+                        rho += f;
+                        jx += (ix - NX) * f;
+                        jy += (iy - NY) * f;
+                        jz += (iz - NZ) * f;
+                    }
+            const double ux = jx / rho, uy = jy / rho, uz = jz / rho;
+            double e2 = 0.0, qx = 0.0, qy = 0.0, qz = 0.0, sxy = 0.0;
+            for (int iz = 0; iz < Qz; ++iz)
+                for (int iy = 0; iy < Qy; ++iy)
+                    for (int ix = 0; ix < Qx; ++ix) {
+                        const double f = F[((iz * Qy + iy) * Qx + ix) * plane + node];
+                        const double dx = ix - NX - ux, dy = iy - NY - uy, dz = iz - NZ - uz;
+                        const double d2 = dx * dx + dy * dy + dz * dz;
+                        e2 += d2 * f;
+                        qx += dx * d2 * f;
+                        qy += dy * d2 * f;
+                        qz += dz * d2 * f;
+                        sxy += dx * dy * f;
+                    }
+            const double m[9] = {rho, ux, uy, e2 / (3.0 * rho), 0.5 * qx, 0.5 * qy, sxy, uz, 0.5 * qz};
+            for (int k = 0; k < 9; ++k) out[k * plane + node] = m[k];
+        }
+        return 0;
+    }
     if (c->dims == 1) {
         int N = c->NX, L = c->Lx;
         for (int x = 0; x < L; ++x) {
@@ -533,7 +708,7 @@ int orc_macro(const orc_cfg *c, const double *F, double *out)
 int orc_equilibrium(const orc_cfg *c, const double *rho, const double *ux, const double *uy,
                     double *X)
 {
-    if (orc_check(c)) return -1;
+    if (orc_check(c) || c->dims == 3) return -1;
     if (c->dims == 1) {
         int N = c->NX, L = c->Lx;
         double E[2 * ORC_MAX_N + 1];
@@ -559,13 +734,36 @@ int orc_equilibrium(const orc_cfg *c, const double *rho, const double *ux, const
 }
 
 /*
+ * 3D local equilibrium X_0 = rho E^x(u_x) E^y(u_y) E^z(u_z) at every node.
+ */
+int orc_equilibrium3d(const orc_cfg *c, const double *rho, const double *ux, const double *uy,
+                      const double *uz, double *X)
+{
+    if (orc_check(c) || c->dims != 3) return -1;
+    const int NX = c->NX, NY = c->NY, NZ = c->NZ;
+    const int Qx = 2 * NX + 1, Qy = 2 * NY + 1, Qz = 2 * NZ + 1;
+    const size_t plane = orc_nodes(c);
+    double Ex[2 * ORC_MAX_N + 1], Ey[2 * ORC_MAX_N + 1], Ez[2 * ORC_MAX_N + 1];
+    for (size_t node = 0; node < plane; ++node) {
+        orc_eq_lattice(NX, ux[node], Ex);
+        orc_eq_lattice(NY, uy[node], Ey);
+        orc_eq_lattice(NZ, uz[node], Ez);
+        for (int iz = 0; iz < Qz; ++iz)
+            for (int iy = 0; iy < Qy; ++iy)
+                for (int ix = 0; ix < Qx; ++ix)
+                    X[((iz * Qy + iy) * Qx + ix) * plane + node] = rho[node] * Ex[ix] * Ey[iy] * Ez[iz];
+    }
+    return 0;
+}
+
+/*
  * Advance X in place by `steps` steps X <- C(S(X)). Returns the number of
  * collisions that left the positivity domain, or -1 on a bad configuration.
  */
 long orc_run(const orc_cfg *c, double *X, long steps)
 {
     if (orc_check(c)) return -1;
-    size_t n = (size_t)orc_nq(c) * c->Lx * c->Ly;
+    size_t n = (size_t)orc_nq(c) * orc_nodes(c);
     double *F = (double *)malloc(n * sizeof(double));
     long bad = 0;
     for (long t = 0; t < steps; ++t) {
@@ -580,7 +778,7 @@ long orc_run(const orc_cfg *c, double *X, long steps)
 int orc_observe(const orc_cfg *c, const double *X, double *out)
 {
     if (orc_check(c)) return -1;
-    size_t n = (size_t)orc_nq(c) * c->Lx * c->Ly;
+    size_t n = (size_t)orc_nq(c) * orc_nodes(c);
     double *F = (double *)malloc(n * sizeof(double));
     orc_stream(c, X, F);
     orc_macro(c, F, out);

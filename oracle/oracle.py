@@ -45,7 +45,8 @@ class Cfg(ctypes.Structure):
     _fields_ = [("dims", ctypes.c_int), ("NX", ctypes.c_int), ("NY", ctypes.c_int),
                 ("Lx", ctypes.c_int), ("Ly", ctypes.c_int), ("bc", ctypes.c_int),
                 ("tau", ctypes.c_double), ("uw_lo", ctypes.c_double),
-                ("uw_hi", ctypes.c_double), ("g", ctypes.c_double), ("zv", ctypes.c_int)]
+                ("uw_hi", ctypes.c_double), ("g", ctypes.c_double), ("zv", ctypes.c_int),
+                ("NZ", ctypes.c_int), ("Lz", ctypes.c_int)]
 
 
 _lib = None
@@ -73,6 +74,8 @@ def lib():
             getattr(_lib, name).restype = ctypes.c_int
         _lib.orc_equilibrium.argtypes = [cp, dp, dp, dp, dp]
         _lib.orc_equilibrium.restype = ctypes.c_int
+        _lib.orc_equilibrium3d.argtypes = [cp, dp, dp, dp, dp, dp]
+        _lib.orc_equilibrium3d.restype = ctypes.c_int
         _lib.orc_run.argtypes = [cp, dp, ctypes.c_long]
         _lib.orc_run.restype = ctypes.c_long
         _lib.orc_flowrate_grad.argtypes = [cp, dp, ctypes.c_long, dp]
@@ -92,26 +95,37 @@ class Lattice:
     ZV_X = 1 and/or ZV_Y = 2, the 2N+2 hierarchy's odd integers
     -(2N+1)..2N+1, 2D only)."""
 
-    def __init__(self, dims, NX, NY, Lx, Ly, bc, tau, uw_lo=0.0, uw_hi=0.0, g=0.0, zv=0):
-        self.cfg = Cfg(dims, NX, NY if dims == 2 else 0, Lx, Ly if dims == 2 else 1, bc,
-                       tau, uw_lo, uw_hi, g, zv)
+    def __init__(self, dims, NX, NY, Lx, Ly, bc, tau, uw_lo=0.0, uw_hi=0.0, g=0.0, zv=0,
+                 NZ=0, Lz=1):
+        self.cfg = Cfg(dims, NX, NY if dims >= 2 else 0, Lx, Ly if dims >= 2 else 1, bc,
+                       tau, uw_lo, uw_hi, g, zv, NZ if dims == 3 else 0, Lz if dims == 3 else 1)
         self.dims = dims
         qx = 2 * NX + (2 if zv & ZV_X else 1)
         qy = 2 * NY + (2 if zv & ZV_Y else 1)
-        self.Q = qx * (qy if dims == 2 else 1)
-        self.shape = (self.Q, self.cfg.Ly, Lx) if dims == 2 else (self.Q, Lx)
-        self.nfields = 7 if dims == 2 else 4
+        if dims == 3:
+            self.Q = qx * qy * (2 * NZ + 1)
+            self.shape = (self.Q, Lz, self.cfg.Ly, Lx)
+            self.nfields = 9
+        else:
+            self.Q = qx * (qy if dims == 2 else 1)
+            self.shape = (self.Q, self.cfg.Ly, Lx) if dims == 2 else (self.Q, Lx)
+            self.nfields = 7 if dims == 2 else 4
 
     def _chk(self, rc):
         if rc < 0:
             raise ValueError("oracle rejected the configuration")
         return rc
 
-    def equilibrium(self, rho, ux, uy=None):
+    def equilibrium(self, rho, ux, uy=None, uz=None):
         rho = np.ascontiguousarray(rho, dtype=np.float64)
         ux = np.ascontiguousarray(ux, dtype=np.float64)
         uy = np.zeros_like(ux) if uy is None else np.ascontiguousarray(uy, dtype=np.float64)
         X = np.empty(self.shape)
+        if self.dims == 3:
+            uz = np.zeros_like(ux) if uz is None else np.ascontiguousarray(uz, dtype=np.float64)
+            self._chk(lib().orc_equilibrium3d(ctypes.byref(self.cfg), _dp(rho), _dp(ux),
+                                              _dp(uy), _dp(uz), _dp(X)))
+            return X
         self._chk(lib().orc_equilibrium(ctypes.byref(self.cfg), _dp(rho), _dp(ux), _dp(uy),
                                         _dp(X)))
         return X

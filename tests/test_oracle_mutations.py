@@ -38,6 +38,10 @@ MUTATIONS = {
                              "return a->N / (a->zv ? 0.75 : 3.0);"),
     "2N+2 even velocities": ("a->v[j] = zv ? 2 * j - (2 * N + 1) : j - N;",
                              "a->v[j] = zv ? 2 * j - 2 * N : j - N;"),
+    "3D z stream sign": ("zd = orc_wrap(z + nz, Lz);", "zd = orc_wrap(z - nz, Lz);"),
+    "3D emission without W^z": ("rlo * Elo[ix] * Wy[iy] * Wz[iz];", "rlo * Elo[ix] * Wy[iy];"),
+    "3D x and z swapped in q": ("const double f = F[((iz * Qy + iy) * Qx + ix) * plane + node];\n                        rho += f;",
+                                "const double f = F[((ix * Qy + iy) * Qx + iz) * plane + node];\n                        rho += f;"),
 }
 
 
@@ -57,6 +61,7 @@ def test_pins_catch_planted_mistake(name, tmp_path):
                         os.path.join(ROOT, "tests", "test_oracle_dynamics.py"),
                         os.path.join(ROOT, "tests", "test_oracle_gradient.py"),
                         os.path.join(ROOT, "tests", "test_oracle_aniso.py"),
-                        os.path.join(ROOT, "tests", "test_oracle_zv.py")],
+                        os.path.join(ROOT, "tests", "test_oracle_zv.py"),
+                        os.path.join(ROOT, "tests", "test_oracle_3d.py")],
                        cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
     assert r.returncode != 0, f"pins did not catch mutation {name!r}"
