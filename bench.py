@@ -53,6 +53,11 @@ def workload(name):
                      zv_axes=c["zv_axes"], kn=kn, u_wall_lo=c["u_wall_lo"],
                      u_wall_hi=c["u_wall_hi"]) for kn in c["kn"]]
         label = c["label"]
+    elif name == "couette3d":
+        c = inputs.COUETTE_3D
+        cfgs = [dict(dims=3, nx=c["nx"], ny=c["ny"], nz=c["nz"], k=c["k"], kn=kn,
+                     u_wall_lo=c["u_wall_lo"], u_wall_hi=c["u_wall_hi"]) for kn in c["kn"]]
+        label = c["label"]
     elif name == "poiseuille":
         c = inputs.POISEUILLE
         cfgs = [dict(dims=2, nx=c["nx"], ny=c["ny"], k=c["k"], kn=kn, g=c["g"]) for kn in c["kn"]]
@@ -253,8 +258,8 @@ def run_ours(args):
     cfgs, label = workload(args.workload)
     dims = cfgs[0]["dims"]
     N, NX, Q1y, Q1x, ZV = lattice_axes(cfgs[0])
-    Q = Q1y * Q1x if dims == 2 else 2 * N + 1
-    nodes = cfgs[0]["nx"] * (cfgs[0]["ny"] if dims == 2 else 1)
+    Q = Q1y * Q1x if dims == 2 else ((2 * N + 1) ** 3 if dims == 3 else 2 * N + 1)
+    nodes = cfgs[0]["nx"] * (cfgs[0]["ny"] if dims >= 2 else 1) * (cfgs[0]["nz"] if dims == 3 else 1)
     n_inst = len(cfgs)
     pops_per_step = Q * nodes * n_inst
     stream = torch.cuda.current_stream()
@@ -263,6 +268,8 @@ def run_ours(args):
 
     def kernel_name(prec, lat):
         G, R, V = lat.tile_shape(N - 1)
+        if dims == 3:
+            return f"k_step3d<{N},{'float' if prec == glbm.FP32_DEV else 'double'},{G},{R}>"
         if V == 2:
             tail = ",1,1" if ZV else (",1" if NX != N else "")
             return f"k_step2d_pair<{N},{G},{R}{tail}>"
@@ -273,7 +280,7 @@ def run_ours(args):
 
     def timed(prec, steps, warmup):
         lat = glbm.Lattice([dict(c, prec=prec) for c in cfgs])
-        if dims == 2:
+        if dims >= 2:
             if args.tiles == "autotune":
                 lat.autotune(reps=10)
             tiles_used[prec] = kernel_name(prec, lat)
@@ -313,17 +320,18 @@ def run_ours(args):
     # end to end through the public API with pinned host buffers: upload the initial
     # fields, run a chunk of steps, read every moment back
     e2e = None
-    if dims == 2:
+    if dims >= 2:
         lb_per_call = 100
         lat = glbm.Lattice([dict(c, prec=glbm.FP32_DEV) for c in cfgs])
         if args.tiles == "autotune":
             lat.autotune(reps=10)
-        ny, nx = cfgs[0]["ny"], cfgs[0]["nx"]
+        shp = lat.shape(0)
+        nf = 9 if dims == 3 else 7
         pin = lambda a: torch.from_numpy(a).pin_memory()  # noqa: E731
-        rho = pin(np.ones((ny, nx)))
-        ux = pin(np.zeros((ny, nx)))
-        uy = pin(np.zeros((ny, nx)))
-        outs = [torch.empty((7, ny, nx), dtype=torch.float64).pin_memory() for _ in cfgs]
+        rho = pin(np.ones(shp))
+        ux = pin(np.zeros(shp))
+        uy = pin(np.zeros(shp))
+        outs = [torch.empty((nf,) + shp, dtype=torch.float64).pin_memory() for _ in cfgs]
         reps = max(2, min(20, steps // lb_per_call))
 
         def one():
@@ -343,11 +351,11 @@ def run_ours(args):
         lat.close()
         e2e = {"value": pops_per_step * lb_per_call * world / dt, "unit": UNIT,
                "h2d_bytes_per_step": 3 * 8 * nodes * n_inst,
-               "d2h_bytes_per_step": 7 * 8 * nodes * n_inst,
+               "d2h_bytes_per_step": nf * 8 * nodes * n_inst,
                "lb_steps_per_step": lb_per_call,
                "call": "glbm_set_equilibrium(host) x3 + glbm_step(100) + glbm_moments(host) x3"}
 
-    precision = precision_check(cfgs[0], min(steps, 2000)) if dims == 2 else None
+    precision = precision_check(cfgs[0], min(steps, 2000)) if dims >= 2 else None
     # FP64 is bound by the FP64 pipe: its instructions per launch come from the
     # committed ncu counters, the peak from the pipe's issue rate and the clock
     fp64_roof = None
@@ -415,13 +423,14 @@ def precision_check(cfg, steps):
         runs[prec] = (lat.moments(0), lat.get_populations(0) if prec == glbm.FP64 else None)
         lat.close()
     dims = cfg["dims"]
-    names = metrics.FIELDS_2D if dims == 2 else metrics.FIELDS_1D
+    names = (metrics.FIELDS_3D if dims == 3 else
+             (metrics.FIELDS_2D if dims == 2 else metrics.FIELDS_1D))
     want = np.stack([runs[glbm.FP64][0][n] for n in names])
     q1x, zv = (lattice_axes(cfg)[3], cfg.get("zv_axes", 0)) if dims == 2 else (None, 0)
     errs = metrics.rel_errors(runs[glbm.FP32_DEV][0], want, dims=dims, F=runs[glbm.FP64][1],
                               q1x=q1x, zv=zv)
     return {"steps": steps,
-            "instance": {k: cfg[k] for k in ("k", "x_level", "zv_axes", "nx", "ny", "kn")
+            "instance": {k: cfg[k] for k in ("k", "x_level", "zv_axes", "nx", "ny", "nz", "kn")
                          if k in cfg},
             "fp32_vs_fp64_max_rel_err": errs, "max": max(errs.values())}
 
@@ -494,6 +503,13 @@ def cpu_baseline(name, budget_s=15.0, steps=None):
         X = o.equilibrium(np.ones((c["ny"], c["nx"])), np.zeros((c["ny"], c["nx"])),
                           np.zeros((c["ny"], c["nx"])))
         pops = Q1y * Q1x * c["nx"] * c["ny"]
+    elif dims == 3:
+        o = orc.Lattice(3, N, N, c["nx"], c["ny"], orc.BC_WALLS, orc.tau_from_kn(N, c["ny"], c["kn"]),
+                        c.get("u_wall_lo", 0.0), c.get("u_wall_hi", 0.0), c.get("g", 0.0),
+                        NZ=N, Lz=c["nz"])
+        shp = (c["nz"], c["ny"], c["nx"])
+        X = o.equilibrium(np.ones(shp), np.zeros(shp), np.zeros(shp), np.zeros(shp))
+        pops = (2 * N + 1) ** 3 * c["nx"] * c["ny"] * c["nz"]
     else:
         o = orc.Lattice(1, N, 0, c["nx"], 1, orc.BC_BOUNCEBACK, orc.tau_from_kn(N, c["nx"], c["kn"]))
         X = o.equilibrium(np.ones(c["nx"]), np.zeros(c["nx"]))
@@ -541,6 +557,22 @@ def run_reference(args):
         X = o.equilibrium(np.ones((ny, cols)), np.zeros((ny, cols)), np.zeros((ny, cols)))
         pops = Q1y * Q1x * ny * cols
         sample = f"{label}: strip of {cols} of {c['nx']} columns x {ny} rows, one instance, FP64"
+    elif dims == 3:
+        ny, nz = c["ny"], c["nz"]
+        mk = lambda nx: orc.Lattice(3, N, N, nx, ny, orc.BC_WALLS,  # noqa: E731
+                                    orc.tau_from_kn(N, ny, c["kn"]), c.get("u_wall_lo", 0.0),
+                                    c.get("u_wall_hi", 0.0), c.get("g", 0.0), NZ=N, Lz=nz)
+        o = mk(1)
+        z1 = np.zeros((nz, ny, 1))
+        t0 = time.perf_counter()
+        o.run(o.equilibrium(z1 + 1, z1, z1, z1), 2)
+        per_col = (time.perf_counter() - t0) / 2
+        cols = int(max(1, min(c["nx"], budget / total_steps / max(per_col, 1e-9))))
+        o = mk(cols)
+        zc = np.zeros((nz, ny, cols))
+        X = o.equilibrium(zc + 1, zc, zc, zc)
+        pops = (2 * N + 1) ** 3 * ny * nz * cols
+        sample = f"{label}: slab of {cols} of {c['nx']} x-columns ({ny} x {nz} each), one instance, FP64"
     else:
         o = orc.Lattice(1, N, 0, c["nx"], 1, orc.BC_BOUNCEBACK, orc.tau_from_kn(N, c["nx"], c["kn"]))
         X = o.equilibrium(np.ones(c["nx"]), np.zeros(c["nx"]))
@@ -570,7 +602,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=200)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="couette",
-                    choices=["couette", "couette_aniso", "couette_zv", "couette_zv_xy",
+                    choices=["couette", "couette_aniso", "couette_zv", "couette_zv_xy", "couette3d",
                              "poiseuille", "sod", "batched"])
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")

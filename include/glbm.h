@@ -67,7 +67,7 @@ typedef enum {
 
 /*
  * One lattice instance.
- *   dims      1 or 2.
+ *   dims      1, 2 or 3.
  *   nx, ny    nodes (ny ignored when dims == 1). With walls ny >= k+1; with
  *             bounce-back nx >= k+1.
  *   k         summations of D1Q3 per axis (level N = k+1, 2N+1 velocities per
@@ -105,6 +105,12 @@ typedef enum {
  *             GLBM_E_UNSUPPORTED. Walls then need ny >= 2N+1. Velocity q of
  *             the layout is iy Q_x + ix with the velocity indices of the axes.
  *             Not for heterogeneous batches or the adjoint.
+ *   nz        nodes along z of a 3D lattice (dims 3): the product of the
+ *             level-(k+1) axis on x, y and z (Sec. 4), D3Q(2k+3)^3, k <= 2,
+ *             periodic in x and z, bc along y as in 2D; layout [q][z][y][x]
+ *             with q = (n_z + N) (2N+1)^2 + (n_y + N) (2N+1) + (n_x + N);
+ *             ny * nz <= 65535. Ignored below 3D. Not for heterogeneous
+ *             batches or the adjoint.
  */
 typedef struct {
     int dims;
@@ -118,6 +124,7 @@ typedef struct {
     double u_wall_lo, u_wall_hi;
     double g;
     int zv_axes;
+    int nz;
 } glbm_config;
 
 /*
@@ -152,6 +159,10 @@ glbm_status glbm_set_allocator(glbm_alloc_fn alloc, glbm_free_fn release, void *
  * else in host memory (copied in this call). Resets the step counter. */
 glbm_status glbm_set_equilibrium(glbm_ctx *ctx, int inst, const double *rho, const double *ux,
                                  const double *uy, int on_device);
+/* The same for a 3D context with the z velocity uz (NULL: u_z = 0); every
+ * field nz*ny*nx values [z][y][x]. GLBM_E_INVAL for other contexts. */
+glbm_status glbm_set_equilibrium_3d(glbm_ctx *ctx, int inst, const double *rho, const double *ux,
+                                    const double *uy, const double *uz, int on_device);
 
 /* Set / read the populations X of instance `inst` in the FP64 logical layout
  * described above (Q*ny*nx values). */
@@ -173,7 +184,9 @@ glbm_status glbm_sync(glbm_ctx *ctx);
  *   bit 0 rho, bit 1 u_x, bit 2 u_y, bit 3 T = sum |xi-u|^2 f / (D rho),
  *   bit 4 q_x, bit 5 q_y (q = (1/2) sum (xi-u) |xi-u|^2 f),
  *   bit 6 sigma_xy = sum (xi_x-u_x)(xi_y-u_y) f.
- * In 1D only bits 0, 1, 3, 4 apply. `out_len` is the capacity in doubles.
+ * In 1D only bits 0, 1, 3, 4 apply. 3D lattices (fields nz*ny*nx values
+ * [z][y][x]) add bit 7 u_z and bit 8 q_z, with T = sum |xi-u|^2 f / (3 rho).
+ * `out_len` is the capacity in doubles.
  * Synchronises the stream when out is host memory. */
 #define GLBM_M_RHO 0x01u
 #define GLBM_M_UX 0x02u
@@ -183,6 +196,9 @@ glbm_status glbm_sync(glbm_ctx *ctx);
 #define GLBM_M_QY 0x20u
 #define GLBM_M_SXY 0x40u
 #define GLBM_M_ALL 0x7Fu
+#define GLBM_M_UZ 0x80u
+#define GLBM_M_QZ 0x100u
+#define GLBM_M_ALL3 0x1FFu
 glbm_status glbm_moments(glbm_ctx *ctx, int inst, unsigned mask, double *out, size_t out_len,
                          int out_on_device);
 

@@ -90,9 +90,10 @@ static void dev_free(const DevAlloc &A, void *p, cudaStream_t s)
 struct Geo {
     int N, NX, Lx, Ly, pitch, Q;  // N: level along y (and x), NX: level along x
     int zv;           // axes on the 2N+2 hierarchy (GLBM_ZV_X | GLBM_ZV_Y)
+    int Lz;           // nodes along z (3D; 1 otherwise)
     long long plane;  // elements per velocity plane
     long long off;    // element offset of the instance in the pool
-    long long nodes() const { return (long long)Lx * Ly; }
+    long long nodes() const { return (long long)Lx * Ly * Lz; }
 };
 
 struct glbm_ctx {
@@ -115,7 +116,7 @@ struct glbm_ctx {
     InstParams *d_ip = nullptr;
     unsigned *d_status = nullptr;  // [0] status flags, [1] launch counter, [2] CTAs done
     unsigned *h_status = nullptr;  // pinned copy, refreshed after every glbm_step
-    double *d_mom = nullptr;       // 7 fields of one instance
+    double *d_mom = nullptr;       // 7 (2D) or 9 (3D) fields of one instance
     double *d_part = nullptr;      // block partials of the conservation sums
     double *d_sums = nullptr;      // 3 sums
     double *d_stage = nullptr;     // staging of host inputs
@@ -156,7 +157,7 @@ static void fill_inst(const glbm_ctx *c, const glbm_config &cfg, const Geo &g, I
     const AxisTableHi &tab = tab_y(c, g);
     const double theta_x = axis_theta(NX, (g.zv & GLBM_ZV_X) != 0);
     ip.omega = 1.0 / (tau + 0.5);
-    ip.g_theta = c->dims == 2 ? cfg.g / theta_x : 0.0;
+    ip.g_theta = c->dims >= 2 ? cfg.g / theta_x : 0.0;
     double den = 0.0;  // the wall's normaliser runs over the y velocities
     for (int i = 0; i < ax_q(tab); ++i)
         if (ax_vel(tab, i) > 0) den += ax_vel(tab, i) * tab.W[i];
@@ -212,7 +213,25 @@ static void fill_inst(const glbm_ctx *c, const glbm_config &cfg, const Geo &g, I
 
 static glbm_status validate(const glbm_config &c)
 {
-    if (c.dims != 1 && c.dims != 2) return fail(GLBM_E_INVAL, "dims must be 1 or 2 (got %d)", c.dims);
+    if (c.dims < 1 || c.dims > 3) return fail(GLBM_E_INVAL, "dims must be 1, 2 or 3 (got %d)", c.dims);
+    if (c.dims == 3) {
+        if (c.k < 0 || c.k > GLBM_MAXN_3D - 1)
+            return fail(GLBM_E_UNSUPPORTED, "3D lattices take k in 0..%d (got %d)", GLBM_MAXN_3D - 1, c.k);
+        if (c.x_level != 0 || c.zv_axes != 0)
+            return fail(GLBM_E_UNSUPPORTED, "3D lattices take the level of k on every axis");
+        if (c.nx < 1 || c.ny < 1 || c.nz < 1) return fail(GLBM_E_INVAL, "nx, ny, nz must be >= 1");
+        if ((long long)c.ny * c.nz > 65535)
+            return fail(GLBM_E_UNSUPPORTED, "3D lattices take ny * nz <= 65535");
+        if (c.bc != GLBM_BC_WALLS && c.bc != GLBM_BC_PERIODIC)
+            return fail(GLBM_E_INVAL, "3D lattices take GLBM_BC_WALLS or GLBM_BC_PERIODIC");
+        if (c.bc == GLBM_BC_WALLS && c.ny < c.k + 1) return fail(GLBM_E_INVAL, "walls need ny >= k+1");
+        if (c.prec != GLBM_FP64 && c.prec != GLBM_FP32_DEV) return fail(GLBM_E_INVAL, "bad precision %d", c.prec);
+        if (!(c.kn > 0.0) && !(c.tau > 0.0)) return fail(GLBM_E_INVAL, "tau must be > 0 (or kn > 0)");
+        const double umax = sqrt(2.0 / 3.0) * (c.k + 1);
+        if (!(fabs(c.u_wall_lo) < umax) || !(fabs(c.u_wall_hi) < umax) || !isfinite(c.g))
+            return fail(GLBM_E_INVAL, "wall speed outside the positivity domain or bad force");
+        return GLBM_OK;
+    }
     if (c.k < 0 || c.k > GLBM_MAXN - 1)
         return fail(GLBM_E_UNSUPPORTED, "k must be in 0..%d (got %d)", GLBM_MAXN - 1, c.k);
     const int N = c.k + 1;
@@ -264,7 +283,7 @@ static double tau_of(const glbm_config &c)
     if (c.kn > 0.0) {
         const int N = c.k + 1;
         const double theta = axis_theta(N, c.dims == 2 && (c.zv_axes & GLBM_ZV_Y));
-        const double H = c.dims == 2 ? c.ny : c.nx;
+        const double H = c.dims >= 2 ? c.ny : c.nx;
         return c.kn * H / sqrt(2.0 * theta);  // Eq. (kn), nu = theta tau
     }
     return c.tau;
@@ -276,12 +295,14 @@ static Geo make_geo(const glbm_config &c)
     g.N = c.k + 1;
     g.NX = c.dims == 2 && c.x_level > 0 ? c.x_level : g.N;
     g.Lx = c.nx;
-    g.Ly = c.dims == 2 ? c.ny : 1;
+    g.Ly = c.dims >= 2 ? c.ny : 1;
+    g.Lz = c.dims == 3 ? c.nz : 1;
     g.pitch = ((g.Lx + 31) / 32) * 32;
     g.zv = c.dims == 2 ? c.zv_axes : 0;
     const int Q1 = 2 * g.N + 1 + ((g.zv & GLBM_ZV_Y) ? 1 : 0);
     g.Q = c.dims == 2 ? Q1 * (2 * g.NX + 1 + ((g.zv & GLBM_ZV_X) ? 1 : 0)) : Q1;
-    g.plane = (long long)g.Ly * g.pitch;
+    if (c.dims == 3) g.Q = Q1 * Q1 * Q1;
+    g.plane = (long long)g.Lz * g.Ly * g.pitch;
     g.off = 0;
     return g;
 }
@@ -326,6 +347,7 @@ static AuxArgs aux_args(const glbm_ctx *c, int inst)
     a.NX = g.NX;
     a.plane = g.plane;
     a.inst_stride = 0;
+    a.Lz = g.Lz;
     return a;
 }
 
@@ -403,7 +425,8 @@ static glbm_status finish_create(glbm_ctx *c, const glbm_config *cfgs, int n, vo
     c->buf[1] = dev_alloc(c->A, bytes_state(c), c->stream);
     c->d_ip = (InstParams *)dev_alloc(c->A, sizeof(InstParams) * n, c->stream);
     c->d_status = (unsigned *)dev_alloc(c->A, 4 * sizeof(unsigned), c->stream);
-    c->d_mom = (double *)dev_alloc(c->A, 7 * (size_t)max_nodes * sizeof(double), c->stream);
+    c->d_mom = (double *)dev_alloc(c->A, (c->dims == 3 ? 9 : 7) * (size_t)max_nodes * sizeof(double),
+                                   c->stream);
     c->d_part = (double *)dev_alloc(c->A, 3 * (size_t)blocks * sizeof(double), c->stream);
     c->d_sums = (double *)dev_alloc(c->A, 3 * sizeof(double), c->stream);
     if (!c->buf[0] || !c->buf[1] || !c->d_ip || !c->d_status || !c->d_mom || !c->d_part || !c->d_sums)
@@ -414,16 +437,22 @@ static glbm_status finish_create(glbm_ctx *c, const glbm_config *cfgs, int n, vo
     CUDA_TRY(cudaMemsetAsync(c->buf[0], 0, bytes_state(c), c->stream));
     CUDA_TRY(cudaMemsetAsync(c->buf[1], 0, bytes_state(c), c->stream));
     // rest state X = W everywhere
-    glbm_status st = ensure_stage(c, 3 * (size_t)max_nodes);
+    glbm_status st = ensure_stage(c, 4 * (size_t)max_nodes);
     if (st != GLBM_OK) return st;
     std::vector<double> one(max_nodes, 1.0), zero(max_nodes, 0.0);
     CUDA_TRY(cudaMemcpy(c->d_stage, one.data(), max_nodes * 8, cudaMemcpyHostToDevice));
     CUDA_TRY(cudaMemcpy(c->d_stage + max_nodes, zero.data(), max_nodes * 8, cudaMemcpyHostToDevice));
     CUDA_TRY(cudaMemcpy(c->d_stage + 2 * max_nodes, zero.data(), max_nodes * 8, cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(c->d_stage + 3 * max_nodes, zero.data(), max_nodes * 8, cudaMemcpyHostToDevice));
     for (int i = 0; i < n; ++i) {
-        CUDA_TRY(glbm_launch_set_equilibrium(aux_args(c, i), inst_ptr(c, 0, i), 0, c->d_stage,
-                                             c->d_stage + max_nodes, c->d_stage + 2 * max_nodes,
-                                             c->stream));
+        if (c->dims == 3)
+            CUDA_TRY(glbm_launch_set_equilibrium3d(aux_args(c, i), inst_ptr(c, 0, i), 0, c->d_stage,
+                                                   c->d_stage + max_nodes, c->d_stage + 2 * max_nodes,
+                                                   c->d_stage + 3 * max_nodes, c->stream));
+        else
+            CUDA_TRY(glbm_launch_set_equilibrium(aux_args(c, i), inst_ptr(c, 0, i), 0, c->d_stage,
+                                                 c->d_stage + max_nodes, c->d_stage + 2 * max_nodes,
+                                                 c->stream));
         c->launches += 1;
     }
     CUDA_TRY(cudaStreamSynchronize(c->stream));
@@ -438,12 +467,15 @@ extern "C" glbm_status glbm_create(const glbm_config *cfgs, int n, void *stream,
         glbm_status st = validate(cfgs[i]);
         if (st != GLBM_OK) return st;
         const glbm_config &a = cfgs[0], &b = cfgs[i];
-        if (a.dims != b.dims || a.nx != b.nx || (a.dims == 2 && a.ny != b.ny) || a.k != b.k ||
+        if (a.dims != b.dims || a.nx != b.nx || (a.dims >= 2 && a.ny != b.ny) ||
+            (a.dims == 3 && a.nz != b.nz) || a.k != b.k ||
             a.bc != b.bc || a.prec != b.prec || make_geo(a).NX != make_geo(b).NX ||
             make_geo(a).zv != make_geo(b).zv)
             return fail(GLBM_E_UNSUPPORTED,
                         "instances differ in geometry; use glbm_batch_create for mixed batches");
     }
+    if (cfgs[0].dims == 3 && (long long)n * cfgs[0].nz > 65535)
+        return fail(GLBM_E_UNSUPPORTED, "3D contexts take instances * nz <= 65535");
     glbm_ctx *c = new (std::nothrow) glbm_ctx();
     if (!c) return fail(GLBM_E_NOMEM, "host allocation failed");
     glbm_status st = finish_create(c, cfgs, n, stream);
@@ -468,6 +500,7 @@ static int zv_kind(const glbm_ctx *c)
 // Candidate tile shapes of level N for this context's lattices.
 static int ctx_tile_shapes(const glbm_ctx *c, int N, TileShape *out)
 {
+    if (c->dims == 3) return glbm_tile_shapes_3d(N, c->prec, out);
     if (is_zv(c)) return glbm_tile_shapes_zv(N, zv_kind(c), c->prec, out);
     return is_x1(c) ? glbm_tile_shapes_x1(N, c->prec, out) : glbm_tile_shapes(N, c->prec, out);
 }
@@ -573,32 +606,61 @@ static glbm_status check_inst(const glbm_ctx *c, int inst)
     return GLBM_OK;
 }
 
-extern "C" glbm_status glbm_set_equilibrium(glbm_ctx *c, int inst, const double *rho,
-                                            const double *ux, const double *uy, int on_device)
+// Equilibrium of fields rho, ux, uy (2D, 3D) and uz (3D; NULL = 0).
+static glbm_status set_equilibrium_impl(glbm_ctx *c, int inst, const double *rho, const double *ux,
+                                        const double *uy, const double *uz, int on_device)
 {
     glbm_status st = check_inst(c, inst);
     if (st != GLBM_OK) return st;
-    if (!rho || !ux || (c->dims == 2 && !uy)) return fail(GLBM_E_INVAL, "null field");
+    if (!rho || !ux || (c->dims >= 2 && !uy)) return fail(GLBM_E_INVAL, "null field");
     const size_t nodes = (size_t)c->geo[inst].nodes();
-    const double *dr = rho, *du = ux, *dv = uy;
-    if (!on_device) {
-        st = ensure_stage(c, 3 * nodes);
+    const double *dr = rho, *du = ux, *dv = uy, *dw = uz;
+    if (!on_device || (c->dims == 3 && !uz)) {
+        st = ensure_stage(c, 4 * nodes);
         if (st != GLBM_OK) return st;
+    }
+    if (!on_device) {
         CUDA_TRY(cudaMemcpyAsync(c->d_stage, rho, nodes * 8, cudaMemcpyHostToDevice, c->stream));
         CUDA_TRY(cudaMemcpyAsync(c->d_stage + nodes, ux, nodes * 8, cudaMemcpyHostToDevice, c->stream));
-        if (c->dims == 2)
+        if (c->dims >= 2)
             CUDA_TRY(cudaMemcpyAsync(c->d_stage + 2 * nodes, uy, nodes * 8, cudaMemcpyHostToDevice, c->stream));
+        if (c->dims == 3 && uz)
+            CUDA_TRY(cudaMemcpyAsync(c->d_stage + 3 * nodes, uz, nodes * 8, cudaMemcpyHostToDevice, c->stream));
         dr = c->d_stage;
         du = c->d_stage + nodes;
-        dv = c->dims == 2 ? c->d_stage + 2 * nodes : c->d_stage;
+        dv = c->dims >= 2 ? c->d_stage + 2 * nodes : c->d_stage;
+        if (uz) dw = c->d_stage + 3 * nodes;
     }
     if (!dv) dv = du;
-    CUDA_TRY(glbm_launch_set_equilibrium(aux_args(c, inst), inst_ptr(c, c->cur, inst), 0, dr, du, dv,
-                                         c->stream));
+    if (c->dims == 3) {
+        if (!dw) {  // u_z = 0
+            CUDA_TRY(cudaMemsetAsync(c->d_stage + 3 * nodes, 0, nodes * 8, c->stream));
+            dw = c->d_stage + 3 * nodes;
+        }
+        CUDA_TRY(glbm_launch_set_equilibrium3d(aux_args(c, inst), inst_ptr(c, c->cur, inst), 0, dr, du,
+                                               dv, dw, c->stream));
+    } else {
+        CUDA_TRY(glbm_launch_set_equilibrium(aux_args(c, inst), inst_ptr(c, c->cur, inst), 0, dr, du,
+                                             dv, c->stream));
+    }
     c->launches += 1;
     CUDA_TRY(set_clock(c, 0));
     if (!on_device) CUDA_TRY(cudaStreamSynchronize(c->stream));  // host buffers reusable on return
     return GLBM_OK;
+}
+
+extern "C" glbm_status glbm_set_equilibrium(glbm_ctx *c, int inst, const double *rho,
+                                            const double *ux, const double *uy, int on_device)
+{
+    return set_equilibrium_impl(c, inst, rho, ux, uy, nullptr, on_device);
+}
+
+extern "C" glbm_status glbm_set_equilibrium_3d(glbm_ctx *c, int inst, const double *rho,
+                                               const double *ux, const double *uy, const double *uz,
+                                               int on_device)
+{
+    if (c && c->dims != 3) return fail(GLBM_E_INVAL, "glbm_set_equilibrium_3d takes 3D contexts");
+    return set_equilibrium_impl(c, inst, rho, ux, uy, uz, on_device);
 }
 
 extern "C" glbm_status glbm_set_populations(glbm_ctx *c, int inst, const double *f, int on_device)
@@ -676,6 +738,28 @@ static Step2DArgsT<TY> step_args_t(const glbm_ctx *c, int from)
 }
 static Step2DArgs step_args(const glbm_ctx *c, int from) { return step_args_t<AxisTable>(c, from); }
 
+static Step3DArgs step3d_args(const glbm_ctx *c, int from)
+{
+    const Geo &g = c->geo[0];
+    Step3DArgs a;
+    memset(&a, 0, sizeof(a));
+    a.tab = glbm_narrow_table(c->tabs[g.N]);
+    a.fin = c->buf[from];
+    a.fout = c->buf[1 - from];
+    a.ip = c->d_ip;
+    a.status = c->d_status;
+    a.step_ctr = c->d_status + 1;
+    a.done_ctr = c->d_status + 2;
+    a.Lx = g.Lx;
+    a.Ly = g.Ly;
+    a.Lz = g.Lz;
+    a.pitch = g.pitch;
+    a.bc = c->cfg[0].bc;
+    a.plane = g.plane;
+    a.inst_stride = c->n_inst > 1 ? c->geo[1].off : 0;
+    return a;
+}
+
 static BatchArgs batch_args(const glbm_ctx *c, int from)
 {
     BatchArgs b;
@@ -705,6 +789,7 @@ static cudaError_t launch_one_2d(const glbm_ctx *c, int from, cudaStream_t s)
 {
     if (c->hetero) return glbm_launch_batched_f32(batch_args(c, from), s);
     const int N = c->geo[0].N;
+    if (c->dims == 3) return glbm_launch_step3d(N, c->prec, c->tile[N], step3d_args(c, from), c->n_inst, s);
     if (N > GLBM_MAXN_2N1)
         return glbm_launch_step2d_zv_hi(N, c->prec, c->tile[N],
                                         step_args_t<AxisTableHi>(c, from), c->n_inst, s);
@@ -806,7 +891,10 @@ extern "C" glbm_status glbm_sync(glbm_ctx *c)
 // ---------------------------------------------------------------------------
 static glbm_status compute_moments(glbm_ctx *c, int inst)
 {
-    CUDA_TRY(glbm_launch_moments(aux_args(c, inst), inst_ptr(c, c->cur, inst), 0, c->d_mom, c->stream));
+    if (c->dims == 3)
+        CUDA_TRY(glbm_launch_moments3d(aux_args(c, inst), inst_ptr(c, c->cur, inst), 0, c->d_mom, c->stream));
+    else
+        CUDA_TRY(glbm_launch_moments(aux_args(c, inst), inst_ptr(c, c->cur, inst), 0, c->d_mom, c->stream));
     c->launches += 1;
     return GLBM_OK;
 }
@@ -818,13 +906,16 @@ extern "C" glbm_status glbm_moments(glbm_ctx *c, int inst, unsigned mask, double
     if (st != GLBM_OK) return st;
     if (!out) return fail(GLBM_E_INVAL, "null output");
     // field slot of each mask bit in the reducer's output
-    const int slot2d[7] = {0, 1, 2, 3, 4, 5, 6};
-    const int slot1d[7] = {0, 1, -1, 2, 3, -1, -1};
+    const int slot2d[9] = {0, 1, 2, 3, 4, 5, 6, -1, -1};
+    const int slot1d[9] = {0, 1, -1, 2, 3, -1, -1, -1, -1};
+    const int slot3d[9] = {0, 1, 2, 3, 4, 5, 6, 7, 8};
+    const int *slot = c->dims == 3 ? slot3d : (c->dims == 2 ? slot2d : slot1d);
     const size_t nodes = (size_t)c->geo[inst].nodes();
     size_t need = 0;
-    for (int b = 0; b < 7; ++b) {
+    if (mask >> 9) return fail(GLBM_E_INVAL, "unknown field bits in mask 0x%x", mask);
+    for (int b = 0; b < 9; ++b) {
         if (!(mask & (1u << b))) continue;
-        if (c->dims == 1 && slot1d[b] < 0) return fail(GLBM_E_INVAL, "field bit %d has no 1D meaning", b);
+        if (slot[b] < 0) return fail(GLBM_E_INVAL, "field bit %d has no %dD meaning", b, c->dims);
         need += nodes;
     }
     if (need == 0) return fail(GLBM_E_INVAL, "empty field mask");
@@ -832,10 +923,9 @@ extern "C" glbm_status glbm_moments(glbm_ctx *c, int inst, unsigned mask, double
     st = compute_moments(c, inst);
     if (st != GLBM_OK) return st;
     size_t o = 0;
-    for (int b = 0; b < 7; ++b) {
+    for (int b = 0; b < 9; ++b) {
         if (!(mask & (1u << b))) continue;
-        const int slot = c->dims == 2 ? slot2d[b] : slot1d[b];
-        CUDA_TRY(cudaMemcpyAsync(out + o, c->d_mom + (size_t)slot * nodes, nodes * 8,
+        CUDA_TRY(cudaMemcpyAsync(out + o, c->d_mom + (size_t)slot[b] * nodes, nodes * 8,
                                  out_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
                                  c->stream));
         o += nodes;
@@ -852,7 +942,7 @@ extern "C" glbm_status glbm_conservation(glbm_ctx *c, int inst, double *mass, do
     st = compute_moments(c, inst);
     if (st != GLBM_OK) return st;
     const long long nodes = c->geo[inst].nodes();
-    CUDA_TRY(glbm_launch_field_sums(c->d_mom, c->dims == 2 ? 3 : 2, nodes, c->d_part,
+    CUDA_TRY(glbm_launch_field_sums(c->d_mom, c->dims >= 2 ? 3 : 2, nodes, c->d_part,
                                     glbm_field_sum_blocks(nodes), c->d_sums, c->stream));
     c->launches += 2;
     double h[3];
@@ -860,7 +950,7 @@ extern "C" glbm_status glbm_conservation(glbm_ctx *c, int inst, double *mass, do
     CUDA_TRY(cudaStreamSynchronize(c->stream));
     if (mass) *mass = h[0];
     if (mom_x) *mom_x = h[1];
-    if (mom_y) *mom_y = c->dims == 2 ? h[2] : 0.0;
+    if (mom_y) *mom_y = c->dims >= 2 ? h[2] : 0.0;
     return GLBM_OK;
 }
 
@@ -904,6 +994,7 @@ static void fill_header(const glbm_ctx *c, CkptHeader &h)
         if (nx_level != g.k + 1) crc = crc32_update(crc, (const unsigned char *)&nx_level, sizeof(int));
         const int zv = make_geo(g).zv;  // and 2N+2 lattices their axes
         if (zv != 0) crc = crc32_update(crc, (const unsigned char *)&zv, sizeof(int));
+        if (g.dims == 3) crc = crc32_update(crc, (const unsigned char *)&g.nz, sizeof(int));
     }
     h.config_crc = crc;
 }
@@ -1168,7 +1259,7 @@ static cudaError_t launch_level_once(const glbm_ctx *c, int N)
 extern "C" glbm_status glbm_autotune(glbm_ctx *c, int reps, double *us)
 {
     if (!c) return fail(GLBM_E_INVAL, "null context");
-    if (c->dims != 2) return fail(GLBM_E_UNSUPPORTED, "tile shapes apply to 2D lattices");
+    if (c->dims < 2) return fail(GLBM_E_UNSUPPORTED, "tile shapes apply to 2D and 3D lattices");
     if (reps < 1 || reps > 1000) return fail(GLBM_E_INVAL, "reps must be in 1..1000");
     if (us)
         for (int i = 0; i < GLBM_LEVELS * GLBM_MAX_TILES; ++i) us[i] = -1.0;

@@ -37,10 +37,14 @@ __device__ __forceinline__ double load_full(const AuxArgs &a, const void *f, lon
     return (double)static_cast<const float *>(f)[idx];
 }
 
-// rest weight of flat velocity q (q = iy Qx + ix in 2D)
+// rest weight of flat velocity q (q = iy Qx + ix in 2D, (iz Q1 + iy) Q1 + ix in 3D)
 __device__ __forceinline__ double rest_weight(const AuxArgs &a, int q)
 {
     if (a.dims == 1) return a.tab.W[q];
+    if (a.dims == 3) {
+        const int Q1 = ax_q(a.tab);
+        return a.tab.W[q / (Q1 * Q1)] * a.tab.W[(q / Q1) % Q1] * a.tab.W[q % Q1];
+    }
     const int Qx = ax_q(a.tabx);
     return a.tab.W[q / Qx] * a.tabx.W[q % Qx];
 }
@@ -84,7 +88,8 @@ __global__ void k_set_populations(const __grid_constant__ AuxArgs a, void *f, in
     const int y = blockIdx.y;
     const int q = blockIdx.z;
     if (x >= a.Lx) return;
-    const double v = src[((long long)q * a.Ly + y) * a.Lx + x];
+    const long long rows = (long long)a.Ly * a.Lz;  // (z, y) rows of a velocity plane
+    const double v = src[((long long)q * rows + y) * a.Lx + x];
     const long long idx =
         (long long)inst * a.inst_stride + (long long)q * a.plane + (long long)y * a.pitch + x;
     if (a.prec == GLBM_FP64)
@@ -104,7 +109,7 @@ __global__ void k_get_populations(const __grid_constant__ AuxArgs a, const void 
         (long long)inst * a.inst_stride + (long long)q * a.plane + (long long)y * a.pitch + x;
     double v = load_full(a, f, idx, q);
     if (a.prec != GLBM_FP64) v += rest_weight(a, q);
-    dst[((long long)q * a.Ly + y) * a.Lx + x] = v;
+    dst[((long long)q * a.Ly * a.Lz + y) * a.Lx + x] = v;
 }
 
 // Population of velocity (ix, iy) arriving at node (x, y) by streaming X
@@ -407,7 +412,153 @@ cudaError_t launch_resident_t(const AuxArgs &a, void *fv, int inst, long long st
     }
 }
 
+// ---------------------------------------------------------------------------
+// 3D tensor products: level N on every axis, layout f[q][z][y][x] with
+// q = (iz Q1 + iy) Q1 + ix, periodic in x and z, walls or periodicity in y.
+// ---------------------------------------------------------------------------
+__global__ void k_set_equilibrium3d(const __grid_constant__ AuxArgs a, void *f, int inst,
+                                    const double *__restrict__ rho, const double *__restrict__ ux,
+                                    const double *__restrict__ uy, const double *__restrict__ uz)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int zy = blockIdx.y;  // z * Ly + y
+    if (x >= a.Lx) return;
+    const int Q1 = ax_q(a.tab);
+    const long long node = (long long)zy * a.Lx + x;
+    const double r = rho[node];
+    const long long base = (long long)inst * a.inst_stride + (long long)zy * a.pitch + x;
+    for (int iz = 0; iz < Q1; ++iz) {
+        const double wz = a.tab.W[iz], dz = eq_dev_rt(a.tab, uz[node], iz);
+        for (int iy = 0; iy < Q1; ++iy) {
+            const double wy = a.tab.W[iy], dy = eq_dev_rt(a.tab, uy[node], iy);
+            for (int ix = 0; ix < Q1; ++ix) {
+                const double wx = a.tab.W[ix], dx = eq_dev_rt(a.tab, ux[node], ix);
+                const long long idx = base + (long long)((iz * Q1 + iy) * Q1 + ix) * a.plane;
+                if (a.prec == GLBM_FP64) {
+                    static_cast<double *>(f)[idx] = r * (wx + dx) * (wy + dy) * (wz + dz);
+                } else {
+                    // rho E^x E^y E^z - W^x W^y W^z without cancellation
+                    const double eyz = (wy + dy) * (wz + dz), wyz = wy * wz;
+                    const double dyz = dy * (wz + dz) + wy * dz;  // e^y e^z - W^y W^z
+                    const double dev = (r - 1.0) * wx * wyz + r * (dx * eyz + wx * dyz);
+                    static_cast<float *>(f)[idx] = (float)dev;
+                }
+            }
+        }
+    }
+}
+
+// Population of velocity (ix, iy, iz) arriving at node (x, y, z) by streaming
+// X (full FP64 value), with the wall emission rho_w E^x(u_w) W^y W^z.
+__device__ double pulled3d(const AuxArgs &a, const InstParams &ip, const void *f, long long ibase,
+                           int x, int y, int z, int ix, int iy, int iz, double rw_lo, double rw_hi)
+{
+    const int N = a.N, Q1 = 2 * N + 1;
+    const int xs = wrap_index(x - (ix - N), a.Lx), zs = wrap_index(z - (iz - N), a.Lz);
+    int ys = y - (iy - N);
+    const double wyz = a.tab.W[iy] * a.tab.W[iz];
+    if (a.bc == GLBM_BC_WALLS) {
+        if (ys < 0) return rw_lo * ip.ew_lo[ix] * wyz;
+        if (ys >= a.Ly) return rw_hi * ip.ew_hi[ix] * wyz;
+    } else {
+        ys = wrap_index(ys, a.Ly);
+    }
+    const int q = (iz * Q1 + iy) * Q1 + ix;
+    double v = load_full(a, f, ibase + (long long)q * a.plane +
+                                   ((long long)zs * a.Ly + ys) * a.pitch + xs, q);
+    if (a.prec != GLBM_FP64) v += a.tab.W[ix] * wyz;
+    return v;
+}
+
+// Wall density of column (x, z): absorbed mass / sum_{n>0} n W_n.
+__device__ double wall_density3d(const AuxArgs &a, const InstParams &ip, const void *f,
+                                 long long ibase, int x, int z, bool lower)
+{
+    const int N = a.N, Q1 = 2 * N + 1;
+    double D = 0.0;
+    for (int aa = 1; aa <= N; ++aa)
+        for (int k = 0; k < aa; ++k)
+            for (int iz = 0; iz < Q1; ++iz) {
+                const int iy = lower ? N - aa : N + aa;
+                const int row = lower ? k : a.Ly - 1 - k;
+                const int zs = wrap_index(z - (iz - N), a.Lz);
+                for (int ix = 0; ix < Q1; ++ix) {
+                    const int xs = wrap_index(x - (ix - N), a.Lx);
+                    const int q = (iz * Q1 + iy) * Q1 + ix;
+                    double v = load_full(a, f, ibase + (long long)q * a.plane +
+                                                   ((long long)zs * a.Ly + row) * a.pitch + xs, q);
+                    if (a.prec != GLBM_FP64) v += a.tab.W[ix] * a.tab.W[iy] * a.tab.W[iz];
+                    D += v;
+                }
+            }
+    return D * ip.inv_den;
+}
+
+// out[9][Lz][Ly][Lx]: rho, u_x, u_y, T = sum |xi-u|^2 f / (3 rho), q_x, q_y,
+// sigma_xy, u_z, q_z of S(X).
+__global__ void k_moments3d(const __grid_constant__ AuxArgs a, const void *f, int inst,
+                            double *__restrict__ out)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int zy = blockIdx.y;
+    if (x >= a.Lx) return;
+    const int y = zy % a.Ly, z = zy / a.Ly;
+    const InstParams &ip = a.ip[inst];
+    const int N = a.N, Q1 = 2 * N + 1;
+    const long long ibase = (long long)inst * a.inst_stride;
+    double rw_lo = 0.0, rw_hi = 0.0;
+    if (a.bc == GLBM_BC_WALLS) {
+        if (y < N) rw_lo = wall_density3d(a, ip, f, ibase, x, z, true);
+        if (y >= a.Ly - N) rw_hi = wall_density3d(a, ip, f, ibase, x, z, false);
+    }
+    double rho = 0.0, jx = 0.0, jy = 0.0, jz = 0.0;
+    for (int iz = 0; iz < Q1; ++iz)
+        for (int iy = 0; iy < Q1; ++iy)
+            for (int ix = 0; ix < Q1; ++ix) {
+                const double v = pulled3d(a, ip, f, ibase, x, y, z, ix, iy, iz, rw_lo, rw_hi);
+                rho += v;
+                jx += (ix - N) * v;
+                jy += (iy - N) * v;
+                jz += (iz - N) * v;
+            }
+    const double ux = jx / rho, uy = jy / rho, uz = jz / rho;
+    double e2 = 0.0, qx = 0.0, qy = 0.0, qz = 0.0, sxy = 0.0;
+    for (int iz = 0; iz < Q1; ++iz)
+        for (int iy = 0; iy < Q1; ++iy)
+            for (int ix = 0; ix < Q1; ++ix) {
+                const double v = pulled3d(a, ip, f, ibase, x, y, z, ix, iy, iz, rw_lo, rw_hi);
+                const double dx = (ix - N) - ux, dy = (iy - N) - uy, dz = (iz - N) - uz;
+                const double d2 = dx * dx + dy * dy + dz * dz;
+                e2 += d2 * v;
+                qx += dx * d2 * v;
+                qy += dy * d2 * v;
+                qz += dz * d2 * v;
+                sxy += dx * dy * v;
+            }
+    const long long nodes = (long long)a.Lx * a.Ly * a.Lz;
+    const long long node = (long long)zy * a.Lx + x;
+    const double m[9] = {rho, ux, uy, e2 / (3.0 * rho), 0.5 * qx, 0.5 * qy, sxy, uz, 0.5 * qz};
+    for (int k = 0; k < 9; ++k) out[k * nodes + node] = m[k];
+}
+
 }  // namespace
+
+cudaError_t glbm_launch_set_equilibrium3d(const AuxArgs &a, void *f, int inst, const double *rho,
+                                          const double *ux, const double *uy, const double *uz,
+                                          cudaStream_t s)
+{
+    dim3 grid((a.Lx + 127) / 128, a.Ly * a.Lz);
+    k_set_equilibrium3d<<<grid, 128, 0, s>>>(a, f, inst, rho, ux, uy, uz);
+    return cudaGetLastError();
+}
+
+cudaError_t glbm_launch_moments3d(const AuxArgs &a, const void *f, int inst, double *out,
+                                  cudaStream_t s)
+{
+    dim3 grid((a.Lx + 63) / 64, a.Ly * a.Lz);
+    k_moments3d<<<grid, 64, 0, s>>>(a, f, inst, out);
+    return cudaGetLastError();
+}
 
 cudaError_t glbm_launch_set_equilibrium(const AuxArgs &a, void *f, int inst, const double *rho,
                                         const double *ux, const double *uy, cudaStream_t s)
@@ -420,7 +571,9 @@ cudaError_t glbm_launch_set_equilibrium(const AuxArgs &a, void *f, int inst, con
 cudaError_t glbm_launch_set_populations(const AuxArgs &a, void *f, int inst, const double *src,
                                         cudaStream_t s)
 {
-    dim3 grid((a.Lx + 127) / 128, a.Ly, a.dims == 2 ? ax_q(a.tab) * ax_q(a.tabx) : ax_q(a.tab));
+    dim3 grid((a.Lx + 127) / 128, a.Ly * a.Lz,
+              a.dims == 3 ? ax_q(a.tab) * ax_q(a.tab) * ax_q(a.tab)
+                          : (a.dims == 2 ? ax_q(a.tab) * ax_q(a.tabx) : ax_q(a.tab)));
     k_set_populations<<<grid, 128, 0, s>>>(a, f, inst, src);
     return cudaGetLastError();
 }
@@ -428,7 +581,9 @@ cudaError_t glbm_launch_set_populations(const AuxArgs &a, void *f, int inst, con
 cudaError_t glbm_launch_get_populations(const AuxArgs &a, const void *f, int inst, double *dst,
                                         cudaStream_t s)
 {
-    dim3 grid((a.Lx + 127) / 128, a.Ly, a.dims == 2 ? ax_q(a.tab) * ax_q(a.tabx) : ax_q(a.tab));
+    dim3 grid((a.Lx + 127) / 128, a.Ly * a.Lz,
+              a.dims == 3 ? ax_q(a.tab) * ax_q(a.tab) * ax_q(a.tab)
+                          : (a.dims == 2 ? ax_q(a.tab) * ax_q(a.tabx) : ax_q(a.tab)));
     k_get_populations<<<grid, 128, 0, s>>>(a, f, inst, dst);
     return cudaGetLastError();
 }

@@ -204,6 +204,23 @@ template <int N, typename T>
 cudaError_t glbm_step2d_zv_level(int kind, int shape, const Step2DArgsOf<N> &a, int n_inst,
                                  cudaStream_t s);
 
+// 3D tensor products (glbm_step3d.cu): levels 1..3, isotropic, periodic in x
+// and z, walls or periodicity in y.
+struct Step3DArgs {
+    AxisTable tab;         // level N (all three axes)
+    const void *fin;
+    void *fout;
+    const InstParams *ip;
+    unsigned *status, *step_ctr, *done_ctr;
+    int Lx, Ly, Lz, pitch, bc;
+    long long plane;       // elements per velocity plane (Lz * Ly * pitch)
+    long long inst_stride; // elements per instance
+};
+#define GLBM_MAXN_3D 3
+cudaError_t glbm_launch_step3d(int N, int prec, int shape, const Step3DArgs &a, int n_inst,
+                               cudaStream_t s);
+int glbm_tile_shapes_3d(int N, int prec, TileShape *out);
+
 // Auxiliary kernels (glbm_aux.cu).
 struct AuxArgs {
     AxisTableHi tab;      // level N along y (the only axis in 1D)
@@ -212,6 +229,7 @@ struct AuxArgs {
     int dims, prec;       // prec: 0 = FP64, 1 = FP32 deviations
     int Lx, Ly, pitch, bc, N, NX;
     long long plane, inst_stride;
+    int Lz;               // nodes along z (3D; 1 otherwise)
 };
 cudaError_t glbm_launch_set_equilibrium(const AuxArgs &a, void *f, int inst, const double *rho,
                                         const double *ux, const double *uy, cudaStream_t s);
@@ -221,6 +239,12 @@ cudaError_t glbm_launch_get_populations(const AuxArgs &a, const void *f, int ins
                                         cudaStream_t s);
 cudaError_t glbm_launch_moments(const AuxArgs &a, const void *f, int inst, double *out,
                                 cudaStream_t s);
+// 3D: initial equilibrium with u_z, and the nine moment fields.
+cudaError_t glbm_launch_set_equilibrium3d(const AuxArgs &a, void *f, int inst, const double *rho,
+                                          const double *ux, const double *uy, const double *uz,
+                                          cudaStream_t s);
+cudaError_t glbm_launch_moments3d(const AuxArgs &a, const void *f, int inst, double *out,
+                                  cudaStream_t s);
 cudaError_t glbm_launch_field_sums(const double *fields, int nfields, long long n, double *partials,
                                    int nblocks, double *out, cudaStream_t s);
 int glbm_field_sum_blocks(long long n);

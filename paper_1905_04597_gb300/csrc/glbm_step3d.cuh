@@ -1,0 +1,267 @@
+// Fused pull-stream + BGK collide for the 3D tensor-product lattices (Sec. 4:
+// the product of 1D levels on three axes, D3Q(2N+1)^3), with the diffuse
+// walls at y = -1/2 and y = Ly - 1/2 (periodic in x and z), the linearised
+// body force along x (Sec. 5.4) and the FP32-deviation or FP64 storage of the
+// 2D step.
+//
+// One CTA covers 32 columns x R rows of one z-slice of one instance. A node's
+// (2N+1)^3 populations form (2N+1)^2 velocity rows (n_z, n_y) of 2N+1
+// columns (n_x); the rows are dealt to G warps, so a thread keeps
+// ceil((2N+1)^2 / G) (2N+1) values in registers. Phases as in the 2D tile:
+//   phase 0 (CTAs touching a wall): the mass streaming into each wall per
+//           (x, z) column, turned into the wall density rho_w(x, z);
+//   phase 1: pull (periodic in x and z; sources inside a wall take the
+//           wall's emission rho_w E^x(u_w) W^y W^z), partial moments;
+//   phase 2: moments, E - W per axis, relaxation plus force, store.
+// The equilibrium deviation is built row by row:
+//   delta f^eq = d^x rho e^y e^z + W^x (rho e^y e^z - W^y W^z),
+//   rho e^y e^z - W^y W^z = d^y rho e^z + W^y (drho W^z + rho d^z),
+// with e = W + d per axis.
+#pragma once
+#include "glbm_step2d.cuh"
+
+template <int N, typename T, int G, int R>
+struct Step3D {
+    static constexpr int Q1 = 2 * N + 1;
+    static constexpr int NROW = Q1 * Q1;               // velocity rows (n_z, n_y)
+    static constexpr int RPG = (NROW + G - 1) / G;     // rows per warp group
+    static constexpr int NW = G * R;
+    static constexpr int NV = 4;                       // wall-flux accumulators
+    static constexpr bool DEV = sizeof(T) == 4;
+    using A = TabAcc<T>;
+
+    struct Smem {
+        T part[R][G][8][32];  // (s, c) of delta rho, j_x, j_y, j_z per row and group
+        T rw[2][32];          // wall density (FP64) or its deviation (FP32): lo, hi
+        T dsum[NV][2][32];
+    };
+
+    __device__ static void run(const AxisTable &tab, const InstParams &ip, int Lx, int Ly, int Lz,
+                               int pitch, int plane, int bc, const T *__restrict__ fin,
+                               T *__restrict__ fout, int x0, int y0, int z, Smem &sm,
+                               unsigned *status, unsigned seed)
+    {
+        const int lane = threadIdx.x & 31;
+        const int w = threadIdx.x >> 5;
+        const int g = w % G;
+        const int r = w / G;
+        const bool walls = bc == GLBM_BC_WALLS;
+        const int x = x0 + lane, y = y0 + r;
+        const bool active = (x < Lx) && (y < Ly);
+        const int xc = x < Lx ? x : Lx - 1;
+        const int yc = y < Ly ? y : Ly - 1;
+        const int slab = Ly * pitch;  // elements per z-slice of a velocity plane
+
+        int cofs[Q1];
+#pragma unroll
+        for (int ix = 0; ix < Q1; ++ix) cofs[ix] = ix * plane + wrap_shift(xc - (ix - N), Lx, Lx > N);
+
+        // ---- phase 0: wall densities of this tile's (x, z) columns ----------
+        const bool need_lo = walls && (y0 < N);
+        const bool need_hi = walls && (y0 + R > Ly - N);
+        if (need_lo || need_hi) {
+            // (n_y, row) pairs with row < |n_y| in order of |n_y|, each over
+            // every n_z, through NV fixed accumulators (order independent of
+            // the tile shape)
+#pragma unroll 1
+            for (int v = w; v < NV; v += NW) {
+                T slo = T(0), shi = T(0);
+#pragma unroll 1
+                for (int p = v; p < N * (N + 1) / 2 * Q1; p += NV) {
+                    const int iz = p % Q1;
+                    int aa = 1, k = p / Q1;
+                    while (k >= aa) {
+                        k -= aa;
+                        ++aa;
+                    }
+                    const int zs = wrap_shift(z - (iz - N), Lz, Lz > N);
+                    if (need_lo) {  // n_y = -aa leaving row k through y = -1/2
+                        const T *pl = fin + ((iz * Q1 + N - aa) * Q1 * plane + zs * slab + k * pitch);
+#pragma unroll
+                        for (int ix = 0; ix < Q1; ++ix) slo += __ldg(pl + cofs[ix]);
+                    }
+                    if (need_hi) {  // n_y = +aa leaving row Ly-1-k through y = Ly-1/2
+                        const T *ph =
+                            fin + ((iz * Q1 + N + aa) * Q1 * plane + zs * slab + (Ly - 1 - k) * pitch);
+#pragma unroll
+                        for (int ix = 0; ix < Q1; ++ix) shi += __ldg(ph + cofs[ix]);
+                    }
+                }
+                sm.dsum[v][0][lane] = slo;
+                sm.dsum[v][1][lane] = shi;
+            }
+            __syncthreads();
+            if (w == 0) {
+                T s0 = T(0), s1 = T(0);
+#pragma unroll
+                for (int j = 0; j < NV; ++j) {
+                    s0 += sm.dsum[j][0][lane];
+                    s1 += sm.dsum[j][1][lane];
+                }
+                const T inv_den = DEV ? (T)ip.inv_den_f : (T)ip.inv_den;
+                sm.rw[0][lane] = s0 * inv_den;
+                sm.rw[1][lane] = s1 * inv_den;
+            }
+            __syncthreads();
+        }
+
+        // ---- phase 1: pull and partial moments -----------------------------
+        T f[RPG][Q1];
+        T s_r = T(0), c_r = T(0), s_x = T(0), c_x = T(0), s_y = T(0), c_y = T(0), s_z = T(0),
+          c_z = T(0);
+#pragma unroll
+        for (int k = 0; k < RPG; ++k) {
+            const int row = g + k * G;
+            if (row < NROW) {
+                const int iz = row / Q1, iy = row % Q1;
+                int ys = yc - (iy - N);
+                ys = walls ? min(max(ys, 0), Ly - 1) : wrap_shift(ys, Ly, Ly > N);
+                const int zs = wrap_shift(z - (iz - N), Lz, Lz > N);
+                const T *rowp = fin + (row * Q1 * plane + zs * slab + ys * pitch);
+#pragma unroll
+                for (int ix = 0; ix < Q1; ++ix) f[k][ix] = __ldg(rowp + cofs[ix]);
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < RPG; ++k) {
+            const int row = g + k * G;
+            if (row < NROW) {
+                const int iz = row / Q1, iy = row % Q1;
+                const int ny = iy - N, nz = iz - N;
+                const int ys = yc - ny;
+                if (walls && (ys < 0 || ys >= Ly)) {  // uniform across the warp
+                    const bool lo = ys < 0;
+                    const T wyz = mul_rn(A::W(tab, iy), A::W(tab, iz));
+                    const T rw = sm.rw[lo ? 0 : 1][lane];
+#pragma unroll
+                    for (int ix = 0; ix < Q1; ++ix) {
+                        if (DEV) {
+                            const T dw = lo ? (T)ip.dw_lo_f[ix] : (T)ip.dw_hi_f[ix];
+                            f[k][ix] = mul_rn(wyz, fma(rw, A::W(tab, ix), (T(1) + rw) * dw));
+                        } else {
+                            const T ew = lo ? (T)ip.ew_lo[ix] : (T)ip.ew_hi[ix];
+                            f[k][ix] = mul_rn(rw * ew, wyz);
+                        }
+                    }
+                }
+                T rs = T(0);
+#pragma unroll
+                for (int ix = 0; ix < Q1; ++ix) rs += f[k][ix];
+                T jx = T(0);
+#pragma unroll
+                for (int n = 1; n <= N; ++n) jx = fma(T(n), f[k][N + n] - f[k][N - n], jx);
+                acc2(s_r, c_r, rs);
+                acc2(s_x, c_x, jx);
+                if (ny != 0) acc2(s_y, c_y, mul_rn(T(ny), rs));
+                if (nz != 0) acc2(s_z, c_z, mul_rn(T(nz), rs));
+            }
+        }
+        {
+            T *pp = &sm.part[r][g][0][lane];
+            pp[0 * 32] = s_r;
+            pp[1 * 32] = c_r;
+            pp[2 * 32] = s_x;
+            pp[3 * 32] = c_x;
+            pp[4 * 32] = s_y;
+            pp[5 * 32] = c_y;
+            pp[6 * 32] = s_z;
+            pp[7 * 32] = c_z;
+        }
+        __syncthreads();
+
+        // ---- phase 2: moments, equilibrium, relaxation, store --------------
+        T S_r = T(0), C_r = T(0), S_x = T(0), C_x = T(0), S_y = T(0), C_y = T(0), S_z = T(0),
+          C_z = T(0);
+#pragma unroll
+        for (int gi = 0; gi < G; ++gi) {
+            const T *pp = &sm.part[r][gi][0][lane];
+            acc2(S_r, C_r, pp[0 * 32]);
+            acc2(S_x, C_x, pp[2 * 32]);
+            acc2(S_y, C_y, pp[4 * 32]);
+            acc2(S_z, C_z, pp[6 * 32]);
+            if (DEV) {
+                C_r += pp[1 * 32];
+                C_x += pp[3 * 32];
+                C_y += pp[5 * 32];
+                C_z += pp[7 * 32];
+            }
+        }
+        const T m0 = S_r + C_r;
+        const T rho = DEV ? T(1) + m0 : m0;
+        const T drho = DEV ? m0 : m0 - T(1);
+        const T inv_rho = T(1) / rho;
+        const T ux = (S_x + C_x) * inv_rho;
+        const T uy = (S_y + C_y) * inv_rho;
+        const T uz = (S_z + C_z) * inv_rho;
+        if (active) {
+            const T umax = (T)(0.816496580927726 * N);  // sqrt(2/3) N (Sec. 3)
+            if (!(rho > T(0)) || !(fabs(ux) <= umax) || !(fabs(uy) <= umax) || !(fabs(uz) <= umax))
+                atomicOr(status, 1u);
+        }
+        T dx[Q1], dy[Q1], dz[Q1];
+        eq_dev_all<N, T>(tab, ux, dx);
+        eq_dev_all<N, T>(tab, uy, dy);
+        eq_dev_all<N, T>(tab, uz, dz);
+
+        const T om = DEV ? (T)ip.omega_f : (T)ip.omega;
+        const T gto = DEV ? (T)ip.g_theta_om_f : (T)ip.g_theta_om;  // g / (theta omega)
+        T *const obase = fout + (z * slab + y * pitch + x);
+        const unsigned hnode = DEV ? hash32((unsigned)((z * Ly + y) * Lx + x) ^ seed) : 0u;
+#pragma unroll
+        for (int k = 0; k < RPG; ++k) {
+            const int row = g + k * G;
+            if (row < NROW) {
+                const int iz = row / Q1, iy = row % Q1;
+                const T wy = A::W(tab, iy), wz = A::W(tab, iz);
+                // runtime row: the per-axis deviations by a select chain
+                T dyv = dy[0], dzv = dz[0];
+#pragma unroll
+                for (int i = 1; i < Q1; ++i) {
+                    if (iy == i) dyv = dy[i];
+                    if (iz == i) dzv = dz[i];
+                }
+                const T rez = rho * (wz + dzv);       // rho e^z
+                const T rez_y = rez * (wy + dyv);     // rho e^y e^z
+                const T wyz = mul_rn(wy, wz);
+                const T gr = mul_rn(gto, wyz);        // W^y W^z g / (theta omega)
+                // FP32: rho e^y e^z - W^y W^z
+                const T B = DEV ? fma(dyv, rez, wy * fma(drho, wz, rho * dzv)) : T(0);
+                T *const op = obase + row * Q1 * plane;
+                const unsigned hrow = hnode + (unsigned)row * 0x85EBCA6Bu;
+#pragma unroll
+                for (int ix = 0; ix < Q1; ++ix) {
+                    const int nx = ix - N;
+                    const T f0 = f[k][ix];
+                    T v;
+                    if (DEV) {
+                        const T Bn = nx != 0 ? fma(T(nx), gr, B) : B;
+                        const T eq = fma(dx[ix], rez_y, A::W(tab, ix) * Bn);
+                        const unsigned rnd = hrow * (0x9E3779B9u * (2u * ix + 1u)) + 0x7F4A7C15u * ix;
+                        const T inc = fma(om, eq - f0, (T)dither_ulp((float)f0, rnd));
+                        v = f0 + inc;
+                    } else {
+                        T eq = (A::W(tab, ix) + dx[ix]) * rez_y;
+                        if (nx != 0) eq = fma(A::WN(tab, ix), gr, eq);
+                        v = fma(om, eq - f0, f0);
+                    }
+                    if (active) op[ix * plane] = v;
+                }
+            }
+        }
+    }
+};
+
+template <int N, typename T, int G, int R>
+__global__ void __launch_bounds__(32 * G * R) k_step3d(const __grid_constant__ Step3DArgs a)
+{
+    using S = Step3D<N, T, G, R>;
+    __shared__ typename S::Smem sm;
+    const int inst = blockIdx.z / a.Lz;
+    const int z = blockIdx.z - inst * a.Lz;
+    const T *fin = static_cast<const T *>(a.fin) + (long long)inst * a.inst_stride;
+    T *fout = static_cast<T *>(a.fout) + (long long)inst * a.inst_stride;
+    const unsigned seed = S::DEV ? hash32(__ldcg(a.step_ctr) * 0x632BE5ABu + inst) : 0u;
+    S::run(a.tab, a.ip[inst], a.Lx, a.Ly, a.Lz, a.pitch, (int)a.plane, a.bc, fin, fout,
+           blockIdx.x * 32, blockIdx.y * R, z, sm, a.status, seed);
+    if (S::DEV) advance_launch_counter(a.step_ctr, a.done_ctr);
+}

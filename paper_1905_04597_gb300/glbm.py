@@ -22,7 +22,9 @@ BC_WALLS, BC_BOUNCEBACK, BC_PERIODIC = 0, 1, 2
 FP64, FP32_DEV = 0, 1
 ZV_X, ZV_Y = 1, 2  # axes on the 2N+2 hierarchy (Config.zv_axes)
 M_RHO, M_UX, M_UY, M_T, M_QX, M_QY, M_SXY, M_ALL = 1, 2, 4, 8, 16, 32, 64, 127
+M_UZ, M_QZ, M_ALL3 = 128, 256, 511
 FIELDS_2D = ("rho", "ux", "uy", "T", "qx", "qy", "sxy")
+FIELDS_3D = FIELDS_2D + ("uz", "qz")
 FIELDS_1D = ("rho", "ux", "T", "qx")
 
 
@@ -42,7 +44,7 @@ class Config(ctypes.Structure):
                 ("kn", ctypes.c_double),
                 ("bc", ctypes.c_int), ("prec", ctypes.c_int), ("u_wall_lo", ctypes.c_double),
                 ("u_wall_hi", ctypes.c_double), ("g", ctypes.c_double),
-                ("zv_axes", ctypes.c_int)]
+                ("zv_axes", ctypes.c_int), ("nz", ctypes.c_int)]
 
 
 _lib = None
@@ -67,6 +69,7 @@ def lib():
         "glbm_destroy": ([vp], None),
         "glbm_set_allocator": ([ALLOC_FN, FREE_FN, vp], i),
         "glbm_set_equilibrium": ([vp, i, vp, vp, vp, i], i),
+        "glbm_set_equilibrium_3d": ([vp, i, vp, vp, vp, vp, i], i),
         "glbm_set_populations": ([vp, i, vp, i], i),
         "glbm_get_populations": ([vp, i, vp, i], i),
         "glbm_step": ([vp, i64], i),
@@ -131,14 +134,14 @@ def eq_table(k: int) -> np.ndarray:
 
 
 def make_config(dims=2, nx=1, ny=1, k=0, tau=0.0, kn=0.0, bc=None, prec=FP64, u_wall_lo=0.0,
-                u_wall_hi=0.0, g=0.0, x_level=0, zv_axes=0) -> Config:
+                u_wall_hi=0.0, g=0.0, x_level=0, zv_axes=0, nz=1) -> Config:
     """One instance; x_level=1 makes the anisotropic product D1Q3 (x) times the
     level-(k+1) lattice (y); 0 keeps level k+1 on both axes. zv_axes (ZV_X,
     ZV_Y) puts axes on the 2N+2 hierarchy (odd velocities, half spacing)."""
     if bc is None:
-        bc = BC_WALLS if dims == 2 else BC_BOUNCEBACK
-    return Config(dims, nx, ny if dims == 2 else 1, k, x_level, tau, kn, bc, prec, u_wall_lo,
-                  u_wall_hi, g, zv_axes)
+        bc = BC_WALLS if dims >= 2 else BC_BOUNCEBACK
+    return Config(dims, nx, ny if dims >= 2 else 1, k, x_level, tau, kn, bc, prec, u_wall_lo,
+                  u_wall_hi, g, zv_axes, nz if dims == 3 else 1)
 
 
 _torch_alloc_refs = None
@@ -225,10 +228,12 @@ class Lattice:
 
     def nodes(self, inst=0):
         c = self.configs[inst]
-        return c.nx * (c.ny if c.dims == 2 else 1)
+        return c.nx * (c.ny if c.dims >= 2 else 1) * (c.nz if c.dims == 3 else 1)
 
     def nq(self, inst=0):
         c = self.configs[inst]
+        if c.dims == 3:
+            return (2 * c.k + 3) ** 3
         if c.dims != 2:
             return 2 * c.k + 3
         q1 = 2 * c.k + 3 + (1 if c.zv_axes & ZV_Y else 0)
@@ -237,12 +242,18 @@ class Lattice:
 
     def shape(self, inst=0):
         c = self.configs[inst]
+        if c.dims == 3:
+            return (c.nz, c.ny, c.nx)
         return (c.ny, c.nx) if c.dims == 2 else (c.nx,)
 
-    def set_equilibrium(self, inst, rho, ux, uy=None):
+    def set_equilibrium(self, inst, rho, ux, uy=None, uz=None):
         pr, dev = _ptr(rho)
         pu, _ = _ptr(ux)
         pv = _ptr(uy)[0] if uy is not None else ctypes.c_void_p()
+        if self.dims == 3:
+            pw = _ptr(uz)[0] if uz is not None else ctypes.c_void_p()
+            check(lib().glbm_set_equilibrium_3d(self.h, inst, pr, pu, pv, pw, dev))
+            return
         check(lib().glbm_set_equilibrium(self.h, inst, pr, pu, pv, dev))
 
     def set_populations(self, inst, f):
@@ -265,8 +276,14 @@ class Lattice:
     def moments(self, inst=0, mask=M_ALL, out=None):
         """Moments of S(X) at the current time; returns a dict of arrays (host) or
         fills `out` (numpy or torch, host or device) packed in field order."""
-        fields = FIELDS_2D if self.dims == 2 else FIELDS_1D
-        bits = [1, 2, 4, 8, 16, 32, 64] if self.dims == 2 else [1, 2, 8, 16]
+        if self.dims == 3:
+            fields, bits = FIELDS_3D, [1, 2, 4, 8, 16, 32, 64, 128, 256]
+            if mask == M_ALL:
+                mask = M_ALL3
+        elif self.dims == 2:
+            fields, bits = FIELDS_2D, [1, 2, 4, 8, 16, 32, 64]
+        else:
+            fields, bits = FIELDS_1D, [1, 2, 8, 16]
         names = [f for f, b in zip(fields, bits) if mask & b]
         if self.dims == 1:
             mask &= M_RHO | M_UX | M_T | M_QX

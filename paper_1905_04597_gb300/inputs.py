@@ -79,6 +79,10 @@ COUETTE_ANISO = dict(nx=1024, ny=200, k=7, x_level=1, kn=(0.01, 0.1, 1.0), u_wal
 COUETTE_ZV = dict(nx=4096, ny=200, k=2, x_level=1, zv_axes=2, kn=(0.01, 0.1, 1.0),
                   u_wall_lo=-0.05, u_wall_hi=0.05,
                   label="couette_zv_d1q3xd1q8_4096x200_kn{0.01,0.1,1}")
+# Couette channel on the 3D product D3Q125 (level 2 on every axis), periodic in
+# x and z (Sec. 4's product on three axes; the paper names 3D without a case)
+COUETTE_3D = dict(nx=256, ny=64, nz=64, k=1, kn=(0.01, 0.1, 1.0), u_wall_lo=-0.05,
+                  u_wall_hi=0.05, label="couette3d_d3q125_256x64x64_kn{0.01,0.1,1}")
 # and the fully symmetric 2N+2 lattice of the same level, D2Q64 (8 x 8)
 COUETTE_ZV_XY = dict(nx=512, ny=256, k=2, x_level=0, zv_axes=3, kn=(0.01, 0.1, 1.0),
                      u_wall_lo=-0.05, u_wall_hi=0.05,

@@ -12,6 +12,7 @@ import numpy as np
 
 FIELDS_2D = ("rho", "ux", "uy", "T", "qx", "qy", "sxy")
 FIELDS_1D = ("rho", "ux", "T", "qx")
+FIELDS_3D = FIELDS_2D + ("uz", "qz")
 
 
 def _axis_velocities(Q1, zv):
@@ -29,6 +30,21 @@ def term_scales(F, want, dims=2, q1x=None, zv=0):
     velocities of an anisotropic product (default: the square lattice); zv the
     mask of axes on the 2N+2 hierarchy (1: x, 2: y)."""
     Q = F.shape[0]
+    if dims == 3:
+        Q1 = int(round(Q ** (1.0 / 3.0)))
+        v = _axis_velocities(Q1, 0).astype(float)
+        ex = (slice(None), None, None, None)
+        cx = np.tile(v, Q1 * Q1)[ex]
+        cy = np.tile(np.repeat(v, Q1), Q1)[ex]
+        cz = np.repeat(v, Q1 * Q1)[ex]
+        rho, ux, uy, uz = want[0], want[1], want[2], want[7]
+        dx, dy, dz = cx - ux, cy - uy, cz - uz
+        d2 = dx * dx + dy * dy + dz * dz
+        su = max((np.abs(c) * F).sum(0).max() for c in (cx, cy, cz)) / rho.min()
+        sq = 0.5 * (np.sqrt(d2) ** 3 * F).sum(0).max()
+        return {"rho": F.sum(0).max(), "ux": su, "uy": su, "uz": su,
+                "T": (d2 * F).sum(0).max() / 3 / rho.min(), "qx": sq, "qy": sq, "qz": sq,
+                "sxy": (np.abs(dx * dy) * F).sum(0).max()}
     if dims == 2:
         Q1x = q1x or int(round(np.sqrt(Q)))
         Q1y = Q // Q1x
@@ -53,9 +69,12 @@ def rel_errors(got, want, dims=2, F=None, q1x=None, zv=0):
     """Per-field max |got - want| / max(max |want|, 1e-3 S); got maps field names
     to arrays, want is the stacked reference moments. F (populations of the
     reference) gives the term scales S; q1x and zv as in term_scales."""
-    names = FIELDS_2D if dims == 2 else FIELDS_1D
+    names = FIELDS_3D if dims == 3 else (FIELDS_2D if dims == 2 else FIELDS_1D)
     w = {n: want[i] for i, n in enumerate(names)}
     groups = {"ux": ("ux", "uy"), "uy": ("ux", "uy"), "qx": ("qx", "qy"), "qy": ("qx", "qy")}
+    if dims == 3:
+        groups = {k: ("ux", "uy", "uz") for k in ("ux", "uy", "uz")}
+        groups.update({k: ("qx", "qy", "qz") for k in ("qx", "qy", "qz")})
     S = term_scales(F, want, dims, q1x, zv) if F is not None else {}
     out = {}
     for n in names:

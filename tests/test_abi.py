@@ -132,6 +132,28 @@ def test_2n2_configs_are_checked_before_any_device_call():
     assert create(two, 2, None, ctypes.byref(h)) == glbm.E_UNSUPPORTED
 
 
+def test_3d_configs_are_checked_before_any_device_call():
+    """3D: levels k <= 2, the level of k on every axis, ny * nz <= 65535, no
+    heterogeneous batches; invalid configurations fail before any CUDA call."""
+    h = ctypes.c_void_p()
+    create = glbm.lib().glbm_create
+    for kw, st in [(dict(k=3, nx=8, ny=8, nz=8), glbm.E_UNSUPPORTED),
+                   (dict(k=1, nx=8, ny=8, nz=8, x_level=1), glbm.E_UNSUPPORTED),
+                   (dict(k=1, nx=8, ny=8, nz=8, zv_axes=glbm.ZV_Y), glbm.E_UNSUPPORTED),
+                   (dict(k=1, nx=8, ny=300, nz=300), glbm.E_UNSUPPORTED),
+                   (dict(k=2, nx=8, ny=2, nz=8), glbm.E_INVAL),
+                   (dict(k=1, nx=8, ny=8, nz=0), glbm.E_INVAL),
+                   (dict(k=0, nx=8, ny=8, nz=8, u_wall_lo=0.9), glbm.E_INVAL)]:
+        cfg = glbm.make_config(dims=3, tau=1.0, **kw)
+        assert create(ctypes.byref(cfg), 1, None, ctypes.byref(h)) == st, kw
+        assert not h.value
+    cfg = glbm.make_config(dims=3, nx=8, ny=8, nz=8, k=1, tau=1.0, prec=glbm.FP32_DEV)
+    assert glbm.lib().glbm_batch_create(ctypes.byref(cfg), 1, None,
+                                        ctypes.byref(h)) == glbm.E_UNSUPPORTED
+    cfg = glbm.make_config(dims=4, nx=8, ny=8, k=1, tau=1.0)
+    assert create(ctypes.byref(cfg), 1, None, ctypes.byref(h)) == glbm.E_INVAL
+
+
 def test_tile_shape_candidates():
     """Every level has 1..MAX_TILES candidate shapes in each precision, each
     with 1 <= G <= 2k+3 warp groups, at most 512 threads per CTA and one or
