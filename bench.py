@@ -278,11 +278,20 @@ def run_ours(args):
             ",1" if NX != N else "")
         return f"k_step2d<{N},{t},{G},{R}{tail}>"
 
+    def choose_tiles(lat, prec):
+        """Autotune, keep the defaults, or (idx:<i>) take candidate i of the
+        FP32 list for the workload's level (FP64 keeps its default)."""
+        if args.tiles == "autotune":
+            lat.autotune(reps=10)
+        elif args.tiles.startswith("idx:") and prec == glbm.FP32_DEV:
+            t = [-1] * glbm.LEVELS
+            t[N - 1] = int(args.tiles[4:])
+            lat.set_tiles(t)
+
     def timed(prec, steps, warmup):
         lat = glbm.Lattice([dict(c, prec=prec) for c in cfgs])
         if dims >= 2:
-            if args.tiles == "autotune":
-                lat.autotune(reps=10)
+            choose_tiles(lat, prec)
             tiles_used[prec] = kernel_name(prec, lat)
         lat.step(warmup)
         lat.sync()
@@ -323,8 +332,7 @@ def run_ours(args):
     if dims >= 2:
         lb_per_call = 100
         lat = glbm.Lattice([dict(c, prec=glbm.FP32_DEV) for c in cfgs])
-        if args.tiles == "autotune":
-            lat.autotune(reps=10)
+        choose_tiles(lat, glbm.FP32_DEV)
         shp = lat.shape(0)
         nf = 9 if dims == 3 else 7
         pin = lambda a: torch.from_numpy(a).pin_memory()  # noqa: E731
@@ -607,9 +615,13 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
-    ap.add_argument("--tiles", default="autotune", choices=["autotune", "default"],
-                    help="time every tile shape on the context first, or keep the defaults")
+    ap.add_argument("--tiles", default="autotune",
+                    help="autotune (time every tile shape on the context first), default "
+                         "(keep the defaults), or idx:<i> (FP32 candidate i of the level)")
     args = ap.parse_args()
+    if args.tiles not in ("autotune", "default") and not (
+            args.tiles.startswith("idx:") and args.tiles[4:].isdigit()):
+        ap.error("--tiles takes autotune, default or idx:<i>")
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
     if args.impl == "reference":
