@@ -29,6 +29,11 @@ struct Step3D {
     static constexpr int NV = 4;                       // wall-flux accumulators
     static constexpr bool DEV = sizeof(T) == 4;
     using A = TabAcc<T>;
+    // With G == 2N+1 warp groups, group g holds the rows (n_z = k - N, n_y = g - N):
+    // n_z is a compile-time index of the unrolled loop and n_y is fixed per thread.
+    static constexpr bool ZROW = G == Q1;
+    __device__ static int row_z(int row, int k) { return ZROW ? k : row / Q1; }
+    __device__ static int row_y(int row, int g) { return ZROW ? g : row % Q1; }
 
     struct Smem {
         T part[R][G][8][32];  // (s, c) of delta rho, j_x, j_y, j_z per row and group
@@ -113,7 +118,7 @@ struct Step3D {
         for (int k = 0; k < RPG; ++k) {
             const int row = g + k * G;
             if (row < NROW) {
-                const int iz = row / Q1, iy = row % Q1;
+                const int iz = row_z(row, k), iy = row_y(row, g);
                 int ys = yc - (iy - N);
                 ys = walls ? min(max(ys, 0), Ly - 1) : wrap_shift(ys, Ly, Ly > N);
                 const int zs = wrap_shift(z - (iz - N), Lz, Lz > N);
@@ -126,7 +131,7 @@ struct Step3D {
         for (int k = 0; k < RPG; ++k) {
             const int row = g + k * G;
             if (row < NROW) {
-                const int iz = row / Q1, iy = row % Q1;
+                const int iz = row_z(row, k), iy = row_y(row, g);
                 const int ny = iy - N, nz = iz - N;
                 const int ys = yc - ny;
                 if (walls && (ys < 0 || ys >= Ly)) {  // uniform across the warp
@@ -203,6 +208,13 @@ struct Step3D {
         eq_dev_all<N, T>(tab, uy, dy);
         eq_dev_all<N, T>(tab, uz, dz);
 
+        // ZROW: this thread's n_y deviation, selected once
+        T dy_g = dy[0];
+        if constexpr (ZROW) {
+#pragma unroll
+            for (int i = 1; i < Q1; ++i)
+                if (g == i) dy_g = dy[i];
+        }
         const T om = DEV ? (T)ip.omega_f : (T)ip.omega;
         const T gto = DEV ? (T)ip.g_theta_om_f : (T)ip.g_theta_om;  // g / (theta omega)
         T *const obase = fout + (z * slab + y * pitch + x);
@@ -211,14 +223,21 @@ struct Step3D {
         for (int k = 0; k < RPG; ++k) {
             const int row = g + k * G;
             if (row < NROW) {
-                const int iz = row / Q1, iy = row % Q1;
+                const int iz = row_z(row, k), iy = row_y(row, g);
                 const T wy = A::W(tab, iy), wz = A::W(tab, iz);
                 // runtime row: the per-axis deviations by a select chain
-                T dyv = dy[0], dzv = dz[0];
+                T dyv, dzv;
+                if constexpr (ZROW) {
+                    dzv = dz[k];
+                    dyv = dy_g;
+                } else {
+                    dyv = dy[0];
+                    dzv = dz[0];
 #pragma unroll
-                for (int i = 1; i < Q1; ++i) {
-                    if (iy == i) dyv = dy[i];
-                    if (iz == i) dzv = dz[i];
+                    for (int i = 1; i < Q1; ++i) {
+                        if (iy == i) dyv = dy[i];
+                        if (iz == i) dzv = dz[i];
+                    }
                 }
                 const T rez = rho * (wz + dzv);       // rho e^z
                 const T rez_y = rez * (wy + dyv);     // rho e^y e^z
