@@ -37,6 +37,13 @@ struct TabAcc<float> {
     static __device__ __forceinline__ float Co(const Tab &t, int n, int i) { return t.Cof[n][i]; }
 };
 
+// Programmatic dependent launch: the uniform step kernels are launched with
+// programmatic stream serialization (launch_serialized), so a launch's CTAs
+// are scheduled while the previous step's grid drains. This wait holds them
+// until that grid has completed and its writes are visible (a no-op for a
+// launch without a programmatic dependency); it precedes every global access.
+__device__ __forceinline__ void wait_prior_grid() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 // Product rounded on its own (never contracted into a following addition), so
 // that the one-node and the packed pair tiles round alike.
 __device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }

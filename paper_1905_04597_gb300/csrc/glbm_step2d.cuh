@@ -322,6 +322,7 @@ __global__ void __launch_bounds__(32 * G * R)
 {
     using S = Step2D<N, T, G, R, NXL, ZY, ZX>;
     __shared__ typename S::Smem sm;
+    wait_prior_grid();
     const int inst = blockIdx.z;
     const T *fin = static_cast<const T *>(a.fin) + (long long)inst * a.inst_stride;
     T *fout = static_cast<T *>(a.fout) + (long long)inst * a.inst_stride;

@@ -43,11 +43,10 @@ static cudaError_t launch_x1_shape(int shape, const Step2DArgs &a, int n_inst, c
             const dim3 grid((a.Lx + 32 * t.V - 1) / (32 * t.V), (a.Ly + t.R - 1) / t.R, n_inst);
             if constexpr (t.V == 2) {
                 static_assert(sizeof(T) == 4, "pair tiles store FP32 deviations");
-                k_step2d_pair<N, t.G, t.R, 1><<<grid, 32 * t.G * t.R, 0, s>>>(a);
+                return launch_serialized(k_step2d_pair<N, t.G, t.R, 1>, grid, dim3(32 * t.G * t.R), s, a);
             } else {
-                k_step2d<N, T, t.G, t.R, 1><<<grid, 32 * t.G * t.R, 0, s>>>(a);
+                return launch_serialized(k_step2d<N, T, t.G, t.R, 1>, grid, dim3(32 * t.G * t.R), s, a);
             }
-            return cudaGetLastError();
         }
         return launch_x1_shape<N, T, I + 1>(shape, a, n_inst, s);
     } else {

@@ -10,6 +10,7 @@ __global__ void __launch_bounds__(32 * G * R)
 {
     using S = Step2DPair<N, G, R, NXL, ZY>;
     __shared__ __align__(16) typename S::Smem sm;
+    wait_prior_grid();
     const int inst = blockIdx.z;
     const float *fin = static_cast<const float *>(a.fin) + (long long)inst * a.inst_stride;
     float *fout = static_cast<float *>(a.fout) + (long long)inst * a.inst_stride;
@@ -24,6 +25,24 @@ __global__ void __launch_bounds__(32 * G * R)
     advance_launch_counter(a.step_ctr, a.done_ctr);
 }
 
+// Launch with programmatic stream serialization (see wait_prior_grid).
+template <typename Args>
+inline cudaError_t launch_serialized(void (*kern)(Args), dim3 grid, dim3 block, cudaStream_t s,
+                                     const Args &a)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, a);
+}
+
 // Launch of tile shape number I of level N.
 template <int N, typename T, int I = 0>
 cudaError_t launch_step2d_shape(int shape, const Step2DArgs &a, int n_inst, cudaStream_t s)
@@ -35,11 +54,10 @@ cudaError_t launch_step2d_shape(int shape, const Step2DArgs &a, int n_inst, cuda
             const dim3 grid((a.Lx + TW - 1) / TW, (a.Ly + R - 1) / R, n_inst);
             if constexpr (t.V == 2) {
                 static_assert(sizeof(T) == 4, "pair tiles store FP32 deviations");
-                k_step2d_pair<N, G, R><<<grid, 32 * G * R, 0, s>>>(a);
+                return launch_serialized(k_step2d_pair<N, G, R>, grid, dim3(32 * G * R), s, a);
             } else {
-                k_step2d<N, T, G, R><<<grid, 32 * G * R, 0, s>>>(a);
+                return launch_serialized(k_step2d<N, T, G, R>, grid, dim3(32 * G * R), s, a);
             }
-            return cudaGetLastError();
         }
         return launch_step2d_shape<N, T, I + 1>(shape, a, n_inst, s);
     } else {

@@ -20,11 +20,12 @@ cudaError_t launch_zv_shape(int shape, const Step2DArgsOf<N> &a, int n_inst, cud
             if constexpr (t.V == 2) {
                 static_assert(sizeof(T) == 4 && KIND == GLBM_ZVK_X1,
                               "pair tiles: FP32 deviations with a 2N+1 x axis");
-                k_step2d_pair<N, t.G, t.R, 1, 1><<<grid, 32 * t.G * t.R, 0, s>>>(a);
+                return launch_serialized(k_step2d_pair<N, t.G, t.R, 1, 1>, grid,
+                                         dim3(32 * t.G * t.R), s, a);
             } else {
-                k_step2d<N, T, t.G, t.R, NXL, 1, ZX><<<grid, 32 * t.G * t.R, 0, s>>>(a);
+                return launch_serialized(k_step2d<N, T, t.G, t.R, NXL, 1, ZX>, grid,
+                                         dim3(32 * t.G * t.R), s, a);
             }
-            return cudaGetLastError();
         }
         return launch_zv_shape<N, T, KIND, I + 1>(shape, a, n_inst, s);
     } else {

@@ -1,5 +1,6 @@
 // Tile shapes and launches of the 3D step (glbm_step3d.cuh), levels 1..3
 // (D3Q27, D3Q125, D3Q343), FP32 deviations and FP64.
+#include "glbm_step2d_launch.cuh"
 #include "glbm_step3d.cuh"
 
 template <int N, typename T>
@@ -30,8 +31,7 @@ static cudaError_t launch_3d_shape(int shape, const Step3DArgs &a, int n_inst, c
         if (shape == I) {
             constexpr TileShape t = Tiles3D<N, T>::shape[I];
             const dim3 grid((a.Lx + 31) / 32, (a.Ly + t.R - 1) / t.R, a.Lz * n_inst);
-            k_step3d<N, T, t.G, t.R><<<grid, 32 * t.G * t.R, 0, s>>>(a);
-            return cudaGetLastError();
+            return launch_serialized(k_step3d<N, T, t.G, t.R>, grid, dim3(32 * t.G * t.R), s, a);
         }
         return launch_3d_shape<N, T, I + 1>(shape, a, n_inst, s);
     } else {

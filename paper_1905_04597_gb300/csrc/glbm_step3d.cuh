@@ -275,6 +275,7 @@ __global__ void __launch_bounds__(32 * G * R) k_step3d(const __grid_constant__ S
 {
     using S = Step3D<N, T, G, R>;
     __shared__ typename S::Smem sm;
+    wait_prior_grid();
     const int inst = blockIdx.z / a.Lz;
     const int z = blockIdx.z - inst * a.Lz;
     const T *fin = static_cast<const T *>(a.fin) + (long long)inst * a.inst_stride;
