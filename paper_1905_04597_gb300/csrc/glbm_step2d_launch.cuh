@@ -4,11 +4,11 @@
 #include "glbm_step2d_pair.cuh"
 #include "glbm_tiles.h"
 
-template <int N, int G, int R, int NXL = N, int ZY = 0>
+template <int N, int G, int R, int NXL = N, int ZY = 0, int ZX = 0>
 __global__ void __launch_bounds__(32 * G * R)
     k_step2d_pair(const __grid_constant__ Step2DArgsOf<N> a)
 {
-    using S = Step2DPair<N, G, R, NXL, ZY>;
+    using S = Step2DPair<N, G, R, NXL, ZY, ZX>;
     __shared__ __align__(16) typename S::Smem sm;
     wait_prior_grid();
     const int inst = blockIdx.z;
@@ -16,7 +16,7 @@ __global__ void __launch_bounds__(32 * G * R)
     float *fout = static_cast<float *>(a.fout) + (long long)inst * a.inst_stride;
     // launch counter (read before any CTA of this launch can advance it)
     const unsigned seed = hash32(__ldcg(a.step_ctr) * 0x632BE5ABu + inst);
-    if constexpr (NXL == N && !ZY)
+    if constexpr (NXL == N && ZX == ZY)
         S::run(a.tab, a.tab, a.ip[inst], a.Lx, a.Ly, a.pitch, (int)a.plane, a.bc, fin, fout,
                blockIdx.x * S::TW, blockIdx.y * R, sm, a.status, seed);
     else

@@ -19,9 +19,8 @@
 //            inside a wall take the wall's re-emitted value), partial moments
 //            per velocity row with compensated sums;
 //   phase 2: moments, equilibrium, relaxation plus force, dithered store.
-// ZY = 1 puts the y axis on the 2N+2 hierarchy (Sec. 4, zero velocity
-// removed: odd velocities on a half-spacing lattice); the x axis is always on
-// the 2N+1 hierarchy here.
+// ZY = 1 / ZX = 1 put the y / x axis on the 2N+2 hierarchy (Sec. 4, zero
+// velocity removed: odd velocities on a half-spacing lattice).
 #pragma once
 #include "glbm_step2d.cuh"
 
@@ -85,14 +84,15 @@ __device__ __forceinline__ void acc2x2(f32x2 &s, f32x2 &c, f32x2 x)
 // p mod NV of the (|n_y|, row) pairs) in the order of the one-node tile,
 // whatever the tile shape; the NW warps of the CTA share the accumulators.
 // Leaves rho_w - 1 of both walls in rw[2][64]. Every thread calls it.
-template <int N, int NX, int NV, int ZY = 0>
+template <int N, int NX, int NV, int ZY = 0, int ZX = 0>
 __device__ __forceinline__ void pair_wall_densities(const InstParams &ip, const float *__restrict__ fin,
                                                     int Ly, int pitch, int plane, const int *win,
                                                     bool need_lo, bool need_hi, int w, int NW,
                                                     int lane, float (*dsum)[2][64], float (*rw)[64])
 {
     using AY = AxisVel<N, ZY>;
-    constexpr int Q1 = 2 * NX + 1;  // velocity columns (N: level along y)
+    using AX = AxisVel<NX, ZX>;
+    constexpr int Q1 = AX::Q;  // velocity columns (N: level along y)
 #pragma unroll 1
     for (int v = w; v < NV; v += NW) {
         float slo0 = 0.f, slo1 = 0.f, shi0 = 0.f, shi1 = 0.f;
@@ -107,16 +107,16 @@ __device__ __forceinline__ void pair_wall_densities(const InstParams &ip, const 
                 const float *pl = fin + (AY::ineg(m) * Q1 * plane + k * pitch);
 #pragma unroll
                 for (int ix = 0; ix < Q1; ++ix) {
-                    slo0 += __ldg(pl + (ix * plane + win[2 * NX - ix]));
-                    slo1 += __ldg(pl + (ix * plane + win[2 * NX - ix + 1]));
+                    slo0 += __ldg(pl + (ix * plane + win[AX::VMAX - AX::vel(ix)]));
+                    slo1 += __ldg(pl + (ix * plane + win[AX::VMAX - AX::vel(ix) + 1]));
                 }
             }
             if (need_hi) {  // velocity ny = +|v_m| leaving row Ly-1-k through y = Ly-1/2
                 const float *ph = fin + (AY::ipos(m) * Q1 * plane + (Ly - 1 - k) * pitch);
 #pragma unroll
                 for (int ix = 0; ix < Q1; ++ix) {
-                    shi0 += __ldg(ph + (ix * plane + win[2 * NX - ix]));
-                    shi1 += __ldg(ph + (ix * plane + win[2 * NX - ix + 1]));
+                    shi0 += __ldg(ph + (ix * plane + win[AX::VMAX - AX::vel(ix)]));
+                    shi1 += __ldg(ph + (ix * plane + win[AX::VMAX - AX::vel(ix) + 1]));
                 }
             }
         }
@@ -146,18 +146,20 @@ __device__ __forceinline__ void pair_wall_densities(const InstParams &ip, const 
 }
 
 // Pull of one velocity row iy (source row ys) for a node pair: f[ix] holds
-// both nodes' populations of velocity (ix - N, iy - N_y); N is the x level.
-template <int N>
+// both nodes' populations of x velocity index ix; N is the x level (ZX: its
+// 2N+2 hierarchy). The window win[j] is column x - VMAX + j.
+template <int N, int ZX = 0>
 __device__ __forceinline__ void pair_load_row(const float *__restrict__ fin, int iy, int ys,
                                               int pitch, int plane, int x, bool inner,
-                                              const int *win, f32x2 (&f)[2 * N + 1])
+                                              const int *win, f32x2 (&f)[2 * N + 1 + ZX])
 {
-    constexpr int Q1 = 2 * N + 1;
+    using AX = AxisVel<N, ZX>;
+    constexpr int Q1 = AX::Q;
     const float *rowp = fin + (iy * Q1 * plane + ys * pitch);
     if (inner) {
 #pragma unroll
         for (int ix = 0; ix < Q1; ++ix) {
-            const int nx = ix - N;
+            const int nx = AX::vel(ix);
             const float *p = rowp + (ix * plane + (x - nx));
             if ((nx & 1) == 0)  // (x - nx) even: one aligned 8-byte load
                 f[ix] = __ldg(reinterpret_cast<const f32x2 *>(p));
@@ -168,22 +170,23 @@ __device__ __forceinline__ void pair_load_row(const float *__restrict__ fin, int
 #pragma unroll
         for (int ix = 0; ix < Q1; ++ix) {
             const float *p = rowp + ix * plane;
-            f[ix] = pk2(__ldg(p + win[2 * N - ix]), __ldg(p + win[2 * N - ix + 1]));
+            const int j = AX::VMAX - AX::vel(ix);
+            f[ix] = pk2(__ldg(p + win[j]), __ldg(p + win[j + 1]));
         }
     }
 }
 
 // The populations a wall re-emits into velocity row iy of a node pair
 // (sources inside the wall): W^y (drho_w W^x + rho_w (E^x(u_w) - W^x)).
-template <int N, class TY, class TX>
+template <int N, int ZX, class TY, class TX>
 __device__ __forceinline__ void pair_wall_row(const TY &tab, const TX &tabx,
                                               const InstParams &ip, int iy, bool lo, float rw0,
-                                              float rw1, f32x2 (&f)[2 * N + 1])
+                                              float rw1, f32x2 (&f)[2 * N + 1 + ZX])
 {
     using A = TabAcc<float>;
     const float wy = A::W(tab, iy);  // tab: y axis; tabx and N: x axis
 #pragma unroll
-    for (int ix = 0; ix < 2 * N + 1; ++ix) {
+    for (int ix = 0; ix < 2 * N + 1 + ZX; ++ix) {
         const float dw = lo ? ip.dw_lo_f[ix] : ip.dw_hi_f[ix];
         const float wx = A::W(tabx, ix);
         f[ix] = pk2(wy * fmaf(rw0, wx, (1.f + rw0) * dw), wy * fmaf(rw1, wx, (1.f + rw1) * dw));
@@ -197,11 +200,11 @@ __device__ __forceinline__ void pair_wall_row(const TY &tab, const TX &tabx,
 // the nodes' words h0, h1, the row and the column. E^x - W comes from the
 // registers dxr, or from shared memory at dxs (stride 32 pairs) when DXS.
 // N and tabx: the x axis.
-template <int N, bool DXS, class TX>
+template <int N, bool DXS, int ZX, class TX>
 __device__ __forceinline__ void pair_collide_row(const TX &tabx, int iy, float wy, f32x2 dy,
                                                  f32x2 rho, f32x2 drho, f32x2 om, float gto,
-                                                 const f32x2 (&f)[2 * N + 1],
-                                                 const f32x2 (&dxr)[2 * N + 1], const f32x2 *dxs,
+                                                 const f32x2 (&f)[2 * N + 1 + ZX],
+                                                 const f32x2 (&dxr)[2 * N + 1 + ZX], const f32x2 *dxs,
                                                  float *op, int plane, unsigned h0, unsigned h1,
                                                  bool act0, bool act1)
 {
@@ -215,8 +218,8 @@ __device__ __forceinline__ void pair_collide_row(const TX &tabx, int iy, float w
     const unsigned hr1 = h1 + (unsigned)iy * 0x85EBCA6Bu;
     const f32x2 two55 = pk2(0x1p-55f, 0x1p-55f);
 #pragma unroll
-    for (int ix = 0; ix < 2 * N + 1; ++ix) {
-        const int nx = ix - N;
+    for (int ix = 0; ix < 2 * N + 1 + ZX; ++ix) {
+        const int nx = AxisVel<N, ZX>::vel(ix);
         const f32x2 f0 = f[ix];
         const f32x2 Bn = nx != 0 ? fma2(pk2((float)nx, (float)nx), gr, B) : B;
         const float wx = A::W(tabx, ix);
@@ -240,15 +243,16 @@ __device__ __forceinline__ void pair_collide_row(const TX &tabx, int iy, float w
     }
 }
 
-template <int N, int G, int R, int NXL = N, int ZY = 0>
+template <int N, int G, int R, int NXL = N, int ZY = 0, int ZX = 0>
 struct Step2DPair {
     using AY = AxisVel<N, ZY>;
+    using AX = AxisVel<NXL, ZX>;
     static constexpr int Q1 = AY::Q;              // velocity rows (level N along y)
-    static constexpr int QX = 2 * NXL + 1;        // velocity columns (level NXL along x)
+    static constexpr int QX = AX::Q;              // velocity columns (level NXL along x)
     static constexpr int RPG = (Q1 + G - 1) / G;  // velocity rows per warp group
     static constexpr int NW = G * R;              // warps per CTA
     static constexpr int TW = 64;                 // tile width (columns)
-    static constexpr int NWIN = 2 * NXL + 2;      // source columns of a node pair
+    static constexpr int NWIN = 2 * AX::VMAX + 2; // source columns of a node pair
     static constexpr int NV = Step2D<N, float, G, R>::NV;  // wall-flux accumulators
     using A = TabAcc<float>;
 
@@ -281,22 +285,22 @@ struct Step2DPair {
         const bool act0 = yin && x < Lx, act1 = yin && x + 1 < Lx;
         const int xc = x < Lx ? x : Lx - 1;
         const int yc = yin ? y : Ly - 1;
-        // the tile pulls from columns x0-NXL .. x0+63+NXL without wrapping
-        const bool inner = x0 >= NXL && x0 + TW + NXL <= Lx;
+        // the tile pulls from columns x0-VMAX .. x0+63+VMAX without wrapping
+        const bool inner = x0 >= AX::VMAX && x0 + TW + AX::VMAX <= Lx;
 
         // source columns of the pair: node x pulls velocity n_x from column
-        // win[N - n_x], node x + 1 from win[N - n_x + 1]
+        // win[VMAX - n_x], node x + 1 from win[VMAX - n_x + 1]
         int win[NWIN];
-        const bool one_wrap = Lx > NXL + 1;
+        const bool one_wrap = Lx > AX::VMAX + 1;
 #pragma unroll
-        for (int j = 0; j < NWIN; ++j) win[j] = wrap_shift(xc - NXL + j, Lx, one_wrap);
+        for (int j = 0; j < NWIN; ++j) win[j] = wrap_shift(xc - AX::VMAX + j, Lx, one_wrap);
 
         // ---- phase 0: wall densities of this tile's columns ---------------
         const bool need_lo = walls && (y0 < AY::VMAX);
         const bool need_hi = walls && (y0 + R > Ly - AY::VMAX);
         if (need_lo || need_hi)
-            pair_wall_densities<N, NXL, NV, ZY>(ip, fin, Ly, pitch, plane, win, need_lo, need_hi, w,
-                                                NW, lane, sm.dsum, sm.rw);
+            pair_wall_densities<N, NXL, NV, ZY, ZX>(ip, fin, Ly, pitch, plane, win, need_lo, need_hi,
+                                                    w, NW, lane, sm.dsum, sm.rw);
 
         // ---- phase 1: pull and partial moments -----------------------------
         // rows iy = g + k G of this warp group; f[k][ix] holds both nodes
@@ -309,7 +313,7 @@ struct Step2DPair {
                 const int ny = AY::vel(iy);
                 int ys = yc - ny;
                 ys = walls ? min(max(ys, 0), Ly - 1) : wrap_shift(ys, Ly, Ly > AY::VMAX);
-                pair_load_row<NXL>(fin, iy, ys, pitch, plane, x, inner, win, f[k]);
+                pair_load_row<NXL, ZX>(fin, iy, ys, pitch, plane, x, inner, win, f[k]);
             }
         }
 #pragma unroll
@@ -320,7 +324,7 @@ struct Step2DPair {
                 const int ys = yc - ny;
                 if (walls && (ys < 0 || ys >= Ly)) {  // uniform across the warp
                     const bool lo = ys < 0;
-                    pair_wall_row<NXL>(tab, tabx, ip, iy, lo, sm.rw[lo ? 0 : 1][2 * lane],
+                    pair_wall_row<NXL, ZX>(tab, tabx, ip, iy, lo, sm.rw[lo ? 0 : 1][2 * lane],
                                      sm.rw[lo ? 0 : 1][2 * lane + 1], f[k]);
                 }
                 f32x2 rs = 0ull;
@@ -328,8 +332,9 @@ struct Step2DPair {
                 for (int ix = 0; ix < QX; ++ix) rs = add2(rs, f[k][ix]);
                 f32x2 jx = 0ull;
 #pragma unroll
-                for (int n = 1; n <= NXL; ++n)
-                    jx = fma2(pk2((float)n, (float)n), sub2(f[k][NXL + n], f[k][NXL - n]), jx);
+                for (int m = AX::M0; m <= NXL; ++m)
+                    jx = fma2(pk2((float)AX::vmag(m), (float)AX::vmag(m)),
+                              sub2(f[k][AX::ipos(m)], f[k][AX::ineg(m)]), jx);
                 acc2x2(s_r, c_r, rs);
                 acc2x2(s_x, c_x, jx);
                 if (ny != 0)  // products rounded per lane, as in the one-node tile
@@ -369,7 +374,7 @@ struct Step2DPair {
         {
             // sqrt(2/3) N per axis (Sec. 3), twice that on a 2N+2 axis
             const float umax = (float)(0.816496580927726 * (ZY ? 2 * N : N));
-            const float umaxx = (float)(0.816496580927726 * NXL);
+            const float umaxx = (float)(0.816496580927726 * (ZX ? 2 * NXL : NXL));
             const bool bad0 = act0 && (!(lo2(rho) > 0.f) || !(fabsf(lo2(ux)) <= umaxx) ||
                                        !(fabsf(lo2(uy)) <= umax));
             const bool bad1 = act1 && (!(hi2(rho) > 0.f) || !(fabsf(hi2(ux)) <= umaxx) ||
@@ -382,8 +387,8 @@ struct Step2DPair {
         float dy0all[G == 1 ? Q1 : 1], dy1all[G == 1 ? Q1 : 1];
         if constexpr (G == 1) {
             float d0[QX], d1[QX];
-            eq_dev_all<NXL, float>(tabx, lo2(ux), d0);
-            eq_dev_all<NXL, float>(tabx, hi2(ux), d1);
+            eq_dev_all<NXL, float, ZX>(tabx, lo2(ux), d0);
+            eq_dev_all<NXL, float, ZX>(tabx, hi2(ux), d1);
 #pragma unroll
             for (int ix = 0; ix < QX; ++ix) dx[ix] = pk2(d0[ix], d1[ix]);
             eq_dev_all<N, float, ZY>(tab, lo2(uy), dy0all);
@@ -402,17 +407,18 @@ struct Step2DPair {
                     if (c < 2 ? n > NXL : n > N) continue;  // x nodes: level NXL; y: N
                     float ae, bo;
                     if (c < 2)
-                        eq_parts<NXL, float>(tabx, n, u[c] * u[c], ae, bo);
+                        eq_parts<NXL, float, ZX>(tabx, n, u[c] * u[c], ae, bo);
                     else
                         eq_parts<N, float, ZY>(tab, n, u[c] * u[c], ae, bo);
-                    const bool single = n == 0 && (c < 2 || !ZY);  // the zero velocity
+                    const bool single = n == 0 && (c < 2 ? !ZX : !ZY);  // the zero velocity
                     plus[c] = single ? ae : fmaf(u[c], bo, ae);
                     minus[c] = single ? ae : fmaf(-u[c], bo, ae);
                 }
                 if (n <= NXL) {
-                    *reinterpret_cast<f32x2 *>(&sm.eqx[r][NXL + n][2 * lane]) = pk2(plus[0], plus[1]);
-                    if (n != 0)
-                        *reinterpret_cast<f32x2 *>(&sm.eqx[r][NXL - n][2 * lane]) =
+                    *reinterpret_cast<f32x2 *>(&sm.eqx[r][AX::ipos(n)][2 * lane]) =
+                        pk2(plus[0], plus[1]);
+                    if (n != 0 || ZX)
+                        *reinterpret_cast<f32x2 *>(&sm.eqx[r][AX::ineg(n)][2 * lane]) =
                             pk2(minus[0], minus[1]);
                 }
                 if (n <= N) {
@@ -443,7 +449,7 @@ struct Step2DPair {
                 else
                     dy = *reinterpret_cast<const f32x2 *>(&sm.eqy[r][iy][2 * lane]);
                 const f32x2 *dxs = reinterpret_cast<const f32x2 *>(&sm.eqx[G > 1 ? r : 0][0][2 * lane]);
-                pair_collide_row<NXL, (G > 1)>(tabx, iy, wy, dy, rho, drho, om, gto, f[k], dx, dxs,
+                pair_collide_row<NXL, (G > 1), ZX>(tabx, iy, wy, dy, rho, drho, om, gto, f[k], dx, dxs,
                                                obase + iy * QX * plane, plane, h0, h1, act0, act1);
             }
         }

@@ -18,9 +18,8 @@ cudaError_t launch_zv_shape(int shape, const Step2DArgsOf<N> &a, int n_inst, cud
             constexpr int ZX = KIND == GLBM_ZVK_X1 ? 0 : 1;
             const dim3 grid((a.Lx + 32 * t.V - 1) / (32 * t.V), (a.Ly + t.R - 1) / t.R, n_inst);
             if constexpr (t.V == 2) {
-                static_assert(sizeof(T) == 4 && KIND == GLBM_ZVK_X1,
-                              "pair tiles: FP32 deviations with a 2N+1 x axis");
-                return launch_serialized(k_step2d_pair<N, t.G, t.R, 1, 1>, grid,
+                static_assert(sizeof(T) == 4, "pair tiles store FP32 deviations");
+                return launch_serialized(k_step2d_pair<N, t.G, t.R, NXL, 1, ZX>, grid,
                                          dim3(32 * t.G * t.R), s, a);
             } else {
                 return launch_serialized(k_step2d<N, T, t.G, t.R, NXL, 1, ZX>, grid,

@@ -1,8 +1,7 @@
 // Candidate tile shapes of the fused 2D step on the 2N+2 hierarchy (Sec. 4:
 // the zero velocity removed), per level N, precision and kind: GLBM_ZVK_X1
 // (D1Q3 along x times the level-N 2N+2 axis along y) or GLBM_ZVK_XY (the 2N+2
-// axis on both). X1 lattices in FP32 also have packed pair tiles (V = 2, the
-// x axis being D1Q3); the others take one-node tiles (V = 1).
+// axis on both). In FP32 both kinds also have packed pair tiles (V = 2).
 #pragma once
 #include "glbm_internal.h"
 
@@ -50,14 +49,14 @@ GLBM_TILES_ZV(10, double, GLBM_ZVK_X1, {1, 4, 1}, {2, 2, 1})
 GLBM_TILES_ZV(11, double, GLBM_ZVK_X1, {2, 2, 1}, {4, 1, 1})
 GLBM_TILES_ZV(12, double, GLBM_ZVK_X1, {1, 4, 1}, {2, 2, 1})
 GLBM_TILES_ZV(13, double, GLBM_ZVK_X1, {2, 2, 1}, {4, 1, 1})
-GLBM_TILES_ZV(1, float, GLBM_ZVK_XY, {1, 16, 1}, {1, 8, 1}, {1, 4, 1})
-GLBM_TILES_ZV(2, float, GLBM_ZVK_XY, {1, 4, 1}, {2, 4, 1}, {1, 8, 1})
-GLBM_TILES_ZV(3, float, GLBM_ZVK_XY, {2, 4, 1}, {2, 2, 1}, {1, 4, 1})
-GLBM_TILES_ZV(4, float, GLBM_ZVK_XY, {2, 2, 1}, {5, 1, 1}, {2, 4, 1})
-GLBM_TILES_ZV(5, float, GLBM_ZVK_XY, {4, 1, 1}, {3, 1, 1}, {3, 2, 1})
-GLBM_TILES_ZV(6, float, GLBM_ZVK_XY, {7, 1, 1}, {2, 2, 1}, {4, 1, 1})
-GLBM_TILES_ZV(7, float, GLBM_ZVK_XY, {8, 1, 1}, {4, 1, 1}, {4, 2, 1})
-GLBM_TILES_ZV(8, float, GLBM_ZVK_XY, {6, 1, 1}, {9, 1, 1}, {3, 2, 1})
+GLBM_TILES_ZV(1, float, GLBM_ZVK_XY, {1, 8, 2}, {1, 4, 2}, {1, 16, 1}, {1, 8, 1}, {1, 4, 1})
+GLBM_TILES_ZV(2, float, GLBM_ZVK_XY, {1, 4, 2}, {2, 4, 2}, {1, 4, 1}, {2, 4, 1}, {1, 8, 1})
+GLBM_TILES_ZV(3, float, GLBM_ZVK_XY, {2, 2, 2}, {2, 4, 2}, {2, 4, 1}, {2, 2, 1}, {1, 4, 1})
+GLBM_TILES_ZV(4, float, GLBM_ZVK_XY, {2, 4, 1}, {2, 2, 1}, {5, 1, 1}, {2, 2, 2}, {5, 1, 2})
+GLBM_TILES_ZV(5, float, GLBM_ZVK_XY, {4, 1, 2}, {3, 1, 2}, {4, 1, 1}, {3, 1, 1}, {3, 2, 1})
+GLBM_TILES_ZV(6, float, GLBM_ZVK_XY, {2, 2, 1}, {7, 1, 1}, {4, 1, 1}, {7, 1, 2}, {2, 2, 2})
+GLBM_TILES_ZV(7, float, GLBM_ZVK_XY, {4, 1, 2}, {8, 1, 2}, {8, 1, 1}, {4, 1, 1}, {4, 2, 1})
+GLBM_TILES_ZV(8, float, GLBM_ZVK_XY, {6, 1, 1}, {9, 1, 1}, {3, 2, 1}, {9, 1, 2}, {6, 1, 2})
 GLBM_TILES_ZV(1, double, GLBM_ZVK_XY, {1, 4, 1}, {1, 8, 1})
 GLBM_TILES_ZV(2, double, GLBM_ZVK_XY, {1, 4, 1}, {2, 2, 1})
 GLBM_TILES_ZV(3, double, GLBM_ZVK_XY, {2, 2, 1}, {1, 4, 1})

@@ -169,7 +169,7 @@ def test_every_tile_shape_one_step(kind, prec):
             t = [-1] * glbm.LEVELS
             t[k] = idx
             lat.set_tiles(t)
-            assert lat.tile_shape(k)[2] == 1 or (kind == "x1" and prec == glbm.FP32_DEV)
+            assert lat.tile_shape(k)[2] == 1 or prec == glbm.FP32_DEV
             lat.set_populations(0, f0)
             lat.step(1)
             lat.sync()
@@ -223,13 +223,15 @@ def test_conservation_checkpoint_and_unsupported_operations(tmp_path):
         x.close()
 
 
-@pytest.mark.parametrize("k", [0, 2, 5, 7, 9, 12])
-def test_pair_tiles_bitwise_equal_one_node_tiles(k):
-    """D1Q3 x D1Q(2N+2) in FP32: pair and one-node tiles of the same warp-group
-    split give bit-identical populations (same operations, same order)."""
+@pytest.mark.parametrize("kind,k", [("x1", 0), ("x1", 2), ("x1", 5), ("x1", 7), ("x1", 9),
+                                    ("x1", 12), ("xy", 0), ("xy", 1), ("xy", 2), ("xy", 5)])
+def test_pair_tiles_bitwise_equal_one_node_tiles(kind, k):
+    """FP32 on the 2N+2 hierarchy: pair and one-node tiles of the same
+    warp-group split give bit-identical populations (same operations, same
+    order), with D1Q3 along x and with the 2N+2 axis along x too."""
     N = k + 1
     nx, ny = 100, 3 * N + 6
-    cfg = _cfg("x1", k, nx, ny, glbm.FP32_DEV, kn=0.2, u_wall_lo=-0.03, u_wall_hi=0.05, g=2e-5)
+    cfg = _cfg(kind, k, nx, ny, glbm.FP32_DEV, kn=0.2, u_wall_lo=-0.03, u_wall_hi=0.05, g=2e-5)
     fields = inputs.random_macro(960 + k, nx, ny)
     probe = glbm.Lattice(cfg)
     n = len(probe.autotune(reps=1)[k])
