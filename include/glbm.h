@@ -169,6 +169,22 @@ glbm_status glbm_set_equilibrium_3d(glbm_ctx *ctx, int inst, const double *rho, 
 glbm_status glbm_set_populations(glbm_ctx *ctx, int inst, const double *f, int on_device);
 glbm_status glbm_get_populations(glbm_ctx *ctx, int inst, double *f, int on_device);
 
+/* Halo columns of an x-slab decomposition (one lattice split along the
+ * periodic x axis over several contexts; the paper has no counterpart). Copy
+ * the x-columns [x0, x0 + ncols) of every velocity plane and (z, y) row of
+ * instance `inst`, exactly as stored (FP32 deviations or FP64, glbm_elem_size
+ * bytes per element, no conversion), from the current state X_t to a packed
+ * buffer laid out [q][z][y][ncols] (pack), or from such a buffer into the
+ * state (unpack). `on_device` selects device or host memory for the buffer;
+ * host copies synchronise. GLBM_E_INVAL for columns outside 0..nx. */
+glbm_status glbm_pack_columns(glbm_ctx *ctx, int inst, int x0, int ncols, void *dst,
+                              int on_device);
+glbm_status glbm_unpack_columns(glbm_ctx *ctx, int inst, int x0, int ncols, const void *src,
+                                int on_device);
+/* Bytes per stored population element (4 in FP32 deviations, 8 in FP64); 0
+ * for a null context. */
+size_t glbm_elem_size(const glbm_ctx *ctx);
+
 /* Advance every instance by n >= 0 steps (Eq. maineq01 with the boundary
  * rule), asynchronously. Repeated chunks are replayed from a CUDA graph.
  * Returns GLBM_E_UNSTABLE when an earlier, already-finished step flagged a

@@ -706,6 +706,45 @@ extern "C" glbm_status glbm_get_populations(glbm_ctx *c, int inst, double *f, in
     return GLBM_OK;
 }
 
+// Copy x-columns [x0, x0 + ncols) of every (velocity, z, y) row of instance
+// inst as stored, between the current buffer and a packed [q][z][y][ncols]
+// buffer (one strided 2D copy).
+static glbm_status copy_columns(glbm_ctx *c, int inst, int x0, int ncols, void *buf, int on_device,
+                                bool pack)
+{
+    glbm_status st = check_inst(c, inst);
+    if (st != GLBM_OK) return st;
+    const Geo &g = c->geo[inst];
+    if (!buf) return fail(GLBM_E_INVAL, "null buffer");
+    if (ncols < 1 || x0 < 0 || x0 + ncols > g.Lx)
+        return fail(GLBM_E_INVAL, "columns [%d, %d) outside 0..%d", x0, x0 + ncols, g.Lx);
+    const size_t e = c->elem;
+    char *base = (char *)inst_ptr(c, c->cur, inst) + (size_t)x0 * e;
+    const size_t rows = (size_t)g.Q * g.Ly * g.Lz, width = (size_t)ncols * e, spitch = (size_t)g.pitch * e;
+    cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice
+                                    : (pack ? cudaMemcpyDeviceToHost : cudaMemcpyHostToDevice);
+    if (pack)
+        CUDA_TRY(cudaMemcpy2DAsync(buf, width, base, spitch, width, rows, kind, c->stream));
+    else
+        CUDA_TRY(cudaMemcpy2DAsync(base, spitch, buf, width, width, rows, kind, c->stream));
+    if (!on_device) CUDA_TRY(cudaStreamSynchronize(c->stream));
+    return GLBM_OK;
+}
+
+extern "C" glbm_status glbm_pack_columns(glbm_ctx *c, int inst, int x0, int ncols, void *dst,
+                                         int on_device)
+{
+    return copy_columns(c, inst, x0, ncols, dst, on_device, true);
+}
+
+extern "C" glbm_status glbm_unpack_columns(glbm_ctx *c, int inst, int x0, int ncols,
+                                           const void *src, int on_device)
+{
+    return copy_columns(c, inst, x0, ncols, const_cast<void *>(src), on_device, false);
+}
+
+extern "C" size_t glbm_elem_size(const glbm_ctx *c) { return c ? c->elem : 0; }
+
 // ---------------------------------------------------------------------------
 // stepping
 // ---------------------------------------------------------------------------

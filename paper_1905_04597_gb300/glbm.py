@@ -70,6 +70,9 @@ def lib():
         "glbm_set_allocator": ([ALLOC_FN, FREE_FN, vp], i),
         "glbm_set_equilibrium": ([vp, i, vp, vp, vp, i], i),
         "glbm_set_equilibrium_3d": ([vp, i, vp, vp, vp, vp, i], i),
+        "glbm_pack_columns": ([vp, i, i, i, vp, i], i),
+        "glbm_unpack_columns": ([vp, i, i, i, vp, i], i),
+        "glbm_elem_size": ([vp], ctypes.c_size_t),
         "glbm_set_populations": ([vp, i, vp, i], i),
         "glbm_get_populations": ([vp, i, vp, i], i),
         "glbm_step": ([vp, i64], i),
@@ -192,6 +195,21 @@ def _ptr(a):
     raise TypeError(f"unsupported array type {type(a)}")
 
 
+def _raw_ptr(a, itemsize):
+    """(pointer, on_device) of a contiguous numpy array or torch tensor whose
+    element size is `itemsize` bytes (the stored population type)."""
+    if isinstance(a, np.ndarray):
+        if a.itemsize != itemsize or not a.flags["C_CONTIGUOUS"]:
+            raise TypeError(f"expected a C-contiguous array of {itemsize}-byte elements")
+        return ctypes.c_void_p(a.ctypes.data), 0
+    import torch
+    if isinstance(a, torch.Tensor):
+        if a.element_size() != itemsize or not a.is_contiguous():
+            raise TypeError(f"expected a contiguous tensor of {itemsize}-byte elements")
+        return ctypes.c_void_p(a.data_ptr()), 1 if a.is_cuda else 0
+    raise TypeError(f"unsupported array type {type(a)}")
+
+
 class Lattice:
     """One or more lattice instances stepped together by libglbm."""
 
@@ -266,6 +284,23 @@ class Lattice:
         p, dev = _ptr(out)
         check(lib().glbm_get_populations(self.h, inst, p, dev))
         return out
+
+    def pack_columns(self, inst, x0, ncols, out):
+        """Stored values of x-columns [x0, x0 + ncols) into `out` (numpy or torch,
+        host or device, packed [q][(z,)y][ncols], dtype float32 or float64 as
+        stored)."""
+        p, dev = _raw_ptr(out, self.elem_size)
+        check(lib().glbm_pack_columns(self.h, inst, x0, ncols, p, dev))
+        return out
+
+    def unpack_columns(self, inst, x0, ncols, src):
+        """The inverse of pack_columns: write stored values into the state."""
+        p, dev = _raw_ptr(src, self.elem_size)
+        check(lib().glbm_unpack_columns(self.h, inst, x0, ncols, p, dev))
+
+    @property
+    def elem_size(self):
+        return lib().glbm_elem_size(self.h)
 
     def step(self, n=1):
         check(lib().glbm_step(self.h, int(n)))

@@ -1,0 +1,97 @@
+"""The x-slab decomposition's exchange on CPU ranks (gloo, world sizes 2 and
+3) with the oracle as each rank's local stepper: the owned columns of the
+slabs, stepped with one halo exchange per step, equal the undivided
+lattice's run bit for bit (FP64), with walls, moving walls and the force."""
+import os
+import socket
+import sys
+
+import numpy as np
+import pytest
+import torch
+import torch.multiprocessing as mp
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+CASES = {
+    "d2q25_walls": dict(N=2, nx=24, ny=9, bc=0, tau=0.8, uw=(-0.04, 0.05), g=3e-5, steps=12),
+    "d2q49_periodic": dict(N=3, nx=18, ny=7, bc=2, tau=0.7, uw=(0.0, 0.0), g=0.0, steps=9),
+}
+
+
+class OracleSlab:
+    """A rank's slab stepped by the oracle (periodic over the padded width)."""
+
+    def __init__(self, c, X):
+        from oracle import oracle as orc
+        self.o = orc.Lattice(2, c["N"], c["N"], X.shape[-1], c["ny"], c["bc"], c["tau"],
+                             c["uw"][0], c["uw"][1], c["g"])
+        self.X = X
+
+    def step(self):
+        self.X, _ = self.o.run(self.X, 1)
+
+    def pack(self, x0, n):
+        return torch.from_numpy(np.ascontiguousarray(self.X[..., x0:x0 + n]))
+
+    def unpack(self, x0, n, buf):
+        self.X[..., x0:x0 + n] = buf.numpy()
+
+
+def _initial(c):
+    Q = (2 * c["N"] + 1) ** 2
+    rng = np.random.default_rng(7)
+    return rng.uniform(0.5, 1.5, size=(Q, c["ny"], c["nx"])) / Q
+
+
+def _rank_main(rank, world, port, name, out):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    sys.path.insert(0, ROOT)
+    import torch.distributed as dist
+    from paper_1905_04597_gb300 import slab
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    c = CASES[name]
+    Ls, H = c["nx"] // world, c["N"]
+    cols = [(rank * Ls + j - H) % c["nx"] for j in range(Ls + 2 * H)]
+    st = OracleSlab(c, np.ascontiguousarray(_initial(c)[..., cols]))
+    slab.step_slab(st, c["steps"], Ls, H, rank, world, slab.torch_sendrecv())
+    np.save(os.path.join(out, f"rank{rank}.npy"), st.X[..., H:H + Ls])
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("world", [2, 3])
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_slabs_equal_the_undivided_lattice(name, world, tmp_path):
+    sys.path.insert(0, ROOT)
+    from oracle import oracle as orc
+    orc.build()
+    c = CASES[name]
+    mp.spawn(_rank_main, args=(world, _free_port(), name, str(tmp_path)), nprocs=world, join=True)
+    got = np.concatenate([np.load(tmp_path / f"rank{r}.npy") for r in range(world)], axis=-1)
+    o = orc.Lattice(2, c["N"], c["N"], c["nx"], c["ny"], c["bc"], c["tau"], c["uw"][0],
+                    c["uw"][1], c["g"])
+    want, _ = o.run(_initial(c), c["steps"])
+    np.testing.assert_array_equal(got, want)
+
+
+def test_single_rank_exchange_wraps_onto_itself():
+    """world = 1: the halos are the slab's own opposite columns."""
+    sys.path.insert(0, ROOT)
+    from oracle import oracle as orc
+    from paper_1905_04597_gb300 import slab
+    c = CASES["d2q25_walls"]
+    H, nx = c["N"], c["nx"]
+    cols = [(j - H) % nx for j in range(nx + 2 * H)]
+    st = OracleSlab(c, np.ascontiguousarray(_initial(c)[..., cols]))
+    slab.step_slab(st, c["steps"], nx, H, 0, 1, None)
+    o = orc.Lattice(2, c["N"], c["N"], nx, c["ny"], c["bc"], c["tau"], c["uw"][0], c["uw"][1], c["g"])
+    want, _ = o.run(_initial(c), c["steps"])
+    np.testing.assert_array_equal(st.X[..., H:H + nx], want)
