@@ -267,16 +267,16 @@ def run_ours(args):
     tiles_used = {}
 
     def kernel_name(prec, lat):
+        """Name of the step kernel the context runs, with every template
+        argument (the form profiles/traffic.json records)."""
         G, R, V = lat.tile_shape(N - 1)
-        if dims == 3:
-            return f"k_step3d<{N},{'float' if prec == glbm.FP32_DEV else 'double'},{G},{R}>"
-        if V == 2:
-            tail = ",1,1" if ZV else (",1" if NX != N else "")
-            return f"k_step2d_pair<{N},{G},{R}{tail}>"
         t = "float" if prec == glbm.FP32_DEV else "double"
-        tail = f",{NX},{1 if ZV & 2 else 0},{1 if ZV & 1 else 0}" if ZV else (
-            ",1" if NX != N else "")
-        return f"k_step2d<{N},{t},{G},{R}{tail}>"
+        if dims == 3:
+            return f"k_step3d<{N},{t},{G},{R}>"
+        zy, zx = (1 if ZV & 2 else 0), (1 if ZV & 1 else 0)
+        if V == 2:
+            return f"k_step2d_pair<{N},{G},{R},{NX},{zy},{zx}>"
+        return f"k_step2d<{N},{t},{G},{R},{NX},{zy},{zx}>"
 
     def choose_tiles(lat, prec):
         """Autotune, keep the defaults, or (idx:<i>) take candidate i of the
