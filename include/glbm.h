@@ -294,8 +294,10 @@ glbm_status glbm_adjoint_flowrate(glbm_ctx *ctx, int64_t steps, int64_t ckpt_eve
  *
  * glbm_autotune times every candidate of every level the context steps: reps
  * launches each (1..1000) from the current state into the spare buffer, with
- * CUDA events on the context's stream, and keeps the fastest. The state, the
- * step clock and the dither sequence are unchanged. If us is non-NULL it
+ * CUDA events on the context's stream, and keeps the fastest; with walls it
+ * then times both ways of summing the wall densities (glbm_set_wall_launch)
+ * with the chosen shapes and keeps the faster. The state, the step clock and
+ * the dither sequence are unchanged. If us is non-NULL it
  * receives the microseconds per launch, us[k * GLBM_MAX_TILES + idx], -1 for
  * pairs not timed (GLBM_LEVELS * GLBM_MAX_TILES doubles, host memory). R and
  * V change only which CTA and thread update a node; G also groups the
@@ -312,6 +314,23 @@ glbm_status glbm_get_tiles(const glbm_ctx *ctx, int *tiles);
 glbm_status glbm_get_tile_shape(const glbm_ctx *ctx, int k, int *G, int *R, int *V);
 glbm_status glbm_set_tiles(glbm_ctx *ctx, const int *tiles);
 glbm_status glbm_autotune(glbm_ctx *ctx, int reps, double *us);
+
+/* Wall densities (GLBM_BC_WALLS). Every step turns the mass that streams
+ * into each diffuse wall into the wall's density rho_w(x), which sets the
+ * populations the wall re-emits (diffuse reflection, Sec. 5.3). Either every
+ * tile within reach of a wall sums that mass for its own columns before its
+ * update (mode 0), or one launch before the stream-collide kernel sums it once
+ * per column and wall into a small device buffer (mode 1, one more launch per
+ * step). The sums are the same, in the same order: both modes give identical
+ * results. A new context takes mode 1 where the tiles near the walls would
+ * repeat the sums for more than a tenth of a step's own loads (high levels,
+ * narrow channels), else mode 0. glbm_set_wall_launch sets the mode (0 or 1;
+ * -1 restores that default; GLBM_E_INVAL otherwise, GLBM_E_UNSUPPORTED for a
+ * context without walls, a batch of mixed levels or a 3D context;
+ * synchronises). glbm_get_wall_launch returns the mode, -1 where none applies.
+ */
+glbm_status glbm_set_wall_launch(glbm_ctx *ctx, int mode);
+int glbm_get_wall_launch(const glbm_ctx *ctx);
 
 /* Checkpoint of every instance's state (header, raw device image, CRC-32).
  * glbm_load requires a context created with the same configuration. */

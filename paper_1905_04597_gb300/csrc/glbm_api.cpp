@@ -121,6 +121,8 @@ struct glbm_ctx {
     double *d_sums = nullptr;      // 3 sums
     double *d_stage = nullptr;     // staging of host inputs
     size_t stage_len = 0;
+    void *d_rw = nullptr;          // wall densities of the current step (k_wall_rho)
+    bool wall_launch = false;      // whether k_wall_rho computes them (else each wall tile)
     int4 *d_items = nullptr;       // heterogeneous work list, sorted by level
     int n_items = 0;
     int group[GLBM_MAXN + 2] = {0};  // first item of each level
@@ -323,6 +325,7 @@ static void destroy_resources(glbm_ctx *c)
     dev_free(c->A, c->d_sums, c->stream);
     dev_free(c->A, c->d_stage, c->stream);
     dev_free(c->A, c->d_items, c->stream);
+    dev_free(c->A, c->d_rw, c->stream);
     if (c->h_status) cudaFreeHost(c->h_status);
     if (c->cap) cudaStreamDestroy(c->cap);
 }
@@ -377,6 +380,38 @@ static glbm_status ensure_stage(glbm_ctx *c, size_t n)
 }
 
 // Allocation and initial state shared by both kinds of context.
+// Whether the wall densities of a step get a launch of their own (k_wall_rho,
+// once per column and wall) instead of the prologue of every tile within reach
+// of a wall: when those tiles, at one node row each, would repeat the wall sums
+// for more than a tenth of the step's own loads. Uniform 2D lattices with walls.
+static bool wall_rho_pays(int N, int NX, int zv, int Ly)
+{
+    const bool zy = (zv & GLBM_ZV_Y) != 0, zx = (zv & GLBM_ZV_X) != 0;
+    // largest y speed and number of (velocity, row) pairs of one wall: the 2N+1
+    // speeds 1..N, or the 2N+2 odd speeds 1, 3, .., 2N+1
+    const long long vmax = zy ? 2 * N + 1 : N;
+    const long long npair = zy ? (long long)(N + 1) * (N + 1) : (long long)N * (N + 1) / 2;
+    const long long qx = zx ? 2 * NX + 2 : 2 * NX + 1, qy = zy ? 2 * N + 2 : 2 * N + 1;
+    const long long repeated = 2 * std::min<long long>(vmax, Ly) * npair * qx;
+    return 10 * repeated > (long long)Ly * qx * qy;
+}
+
+static bool wall_rho_possible(const glbm_ctx *c)
+{
+    return c->dims == 2 && !c->hetero && c->cfg[0].bc == GLBM_BC_WALLS;
+}
+static bool wall_rho_launch(const glbm_ctx *c)
+{
+    const Geo &g = c->geo[0];
+    return wall_rho_possible(c) && wall_rho_pays(g.N, g.NX, g.zv, g.Ly);
+}
+static glbm_status alloc_wall_rho(glbm_ctx *c)
+{
+    if (c->d_rw) return GLBM_OK;
+    c->d_rw = dev_alloc(c->A, (size_t)c->n_inst * 2 * c->geo[0].pitch * c->elem, c->stream);
+    return c->d_rw ? GLBM_OK : fail(GLBM_E_NOMEM, "device allocation of the wall densities failed");
+}
+
 static glbm_status finish_create(glbm_ctx *c, const glbm_config *cfgs, int n, void *stream)
 {
     c->n_inst = n;
@@ -429,6 +464,11 @@ static glbm_status finish_create(glbm_ctx *c, const glbm_config *cfgs, int n, vo
                                    c->stream);
     c->d_part = (double *)dev_alloc(c->A, 3 * (size_t)blocks * sizeof(double), c->stream);
     c->d_sums = (double *)dev_alloc(c->A, 3 * sizeof(double), c->stream);
+    if (wall_rho_launch(c)) {
+        glbm_status ws = alloc_wall_rho(c);
+        if (ws != GLBM_OK) return ws;
+        c->wall_launch = true;
+    }
     if (!c->buf[0] || !c->buf[1] || !c->d_ip || !c->d_status || !c->d_mom || !c->d_part || !c->d_sums)
         return fail(GLBM_E_NOMEM, "device allocation of %.1f MB failed", 2.0 * bytes_state(c) / 1e6);
     CUDA_TRY(cudaMemcpyAsync(c->d_ip, c->h_ip.data(), sizeof(InstParams) * n, cudaMemcpyHostToDevice,
@@ -767,6 +807,7 @@ static Step2DArgsT<TY> step_args_t(const glbm_ctx *c, int from)
     a.status = c->d_status;
     a.step_ctr = c->d_status + 1;
     a.done_ctr = c->d_status + 2;
+    a.rw = c->wall_launch ? c->d_rw : nullptr;
     a.Lx = g.Lx;
     a.Ly = g.Ly;
     a.pitch = g.pitch;
@@ -820,7 +861,7 @@ static BatchArgs batch_args(const glbm_ctx *c, int from)
 // Kernel launches of one 2D step.
 static int launches_per_step(const glbm_ctx *c)
 {
-    return c->hetero ? glbm_batched_launches(batch_args(c, 0)) : 1;
+    return c->hetero ? glbm_batched_launches(batch_args(c, 0)) : (c->wall_launch ? 2 : 1);
 }
 
 // One 2D step of every instance from buffer `from` into the other, on stream s.
@@ -1191,7 +1232,7 @@ extern "C" glbm_status glbm_adjoint_flowrate(glbm_ctx *c, int64_t steps, int64_t
             CUDA_TRY(set_clock(c, t_start + t0));
             for (int64_t r = 0; r + 1 < len; ++r) {
                 CUDA_TRY(launch_2d_between(c, seg + pool * r, seg + pool * (r + 1), c->stream));
-                c->launches += 1;
+                c->launches += launches_per_step(c);
             }
             for (int64_t r = len - 1; r >= 0; --r) {
                 a.X = seg + pool * r + (size_t)c->geo[i].off * c->elem;
@@ -1266,6 +1307,27 @@ static glbm_status tiles_changed(glbm_ctx *c)
     return c->hetero ? build_items(c) : GLBM_OK;
 }
 
+extern "C" glbm_status glbm_set_wall_launch(glbm_ctx *c, int mode)
+{
+    if (!c) return fail(GLBM_E_INVAL, "null context");
+    if (mode < -1 || mode > 1) return fail(GLBM_E_INVAL, "wall launch mode %d (-1, 0 or 1)", mode);
+    if (!wall_rho_possible(c))
+        return fail(GLBM_E_UNSUPPORTED, "wall densities apply to uniform 2D contexts with walls");
+    const bool on = mode < 0 ? wall_rho_launch(c) : mode == 1;
+    if (on) {
+        glbm_status st = alloc_wall_rho(c);
+        if (st != GLBM_OK) return st;
+    }
+    c->wall_launch = on;
+    return tiles_changed(c);  // the captured step graphs name the old launches
+}
+
+extern "C" int glbm_get_wall_launch(const glbm_ctx *c)
+{
+    if (!c || !wall_rho_possible(c)) return -1;
+    return c->wall_launch ? 1 : 0;
+}
+
 extern "C" glbm_status glbm_set_tiles(glbm_ctx *c, const int *tiles)
 {
     if (!c || !tiles) return fail(GLBM_E_INVAL, "null argument");
@@ -1333,6 +1395,24 @@ extern "C" glbm_status glbm_autotune(glbm_ctx *c, int reps, double *us)
             }
         }
         c->tile[N] = best;
+    }
+    // then the way the wall densities are summed, with the chosen shapes: the
+    // faster of the two modes (identical results)
+    if (st == GLBM_OK && wall_rho_possible(c)) st = alloc_wall_rho(c);
+    if (st == GLBM_OK && wall_rho_possible(c)) {
+        const int N = c->geo[0].N;
+        float ms_mode[2] = {0.f, 0.f};
+        for (int m = 0; m < 2 && st == GLBM_OK; ++m) {
+            c->wall_launch = m == 1;
+            cudaError_t e = launch_level_once(c, N);  // warm-up
+            if (e == cudaSuccess) e = cudaEventRecord(e0, c->stream);
+            for (int r = 0; r < reps && e == cudaSuccess; ++r) e = launch_level_once(c, N);
+            if (e == cudaSuccess) e = cudaEventRecord(e1, c->stream);
+            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms_mode[m], e0, e1);
+            if (e != cudaSuccess) st = fail(GLBM_E_CUDA, "autotune launch: %s", cudaGetErrorString(e));
+        }
+        c->wall_launch = ms_mode[1] < ms_mode[0];
     }
     if (e1) cudaEventDestroy(e1);
     cudaEventDestroy(e0);

@@ -141,17 +141,38 @@ __device__ __forceinline__ unsigned hash32(unsigned x)
     return x;
 }
 
-// Dither for the FP32 store of `ref + inc`: uniform in [-1/2, 1/2) units in the
-// last place of `ref`, from the random word r. Adding it to the increment
-// before the final rounding makes the rounding error zero-mean, so a steady
-// state does not repeat the same rounding error at every step (whose effect on
-// slowly relaxing moments would grow like 1/omega).
-__device__ __forceinline__ float dither_ulp(float ref, unsigned r)
+// Dither for the FP32 store of `ref + inc`: u times the power of two of ref's
+// exponent (0 for zero and subnormal ref), with u uniform in [-2^-24, 2^-24),
+// i.e. uniform in [-1/2, 1/2) units in the last place of `ref`. Adding it to
+// the increment before the final rounding makes the rounding error zero-mean,
+// so a steady state does not repeat the same rounding error at every step
+// (whose effect on slowly relaxing moments would grow like 1/omega).
+__device__ __forceinline__ float dither_ulp(float ref, float u)
 {
-    // the signed word times 2^-55 lies in [-2^-24, 2^-24); times the power of
-    // two of ref's exponent (0 for zero and subnormal ref) that is half an ulp
-    const float p2 = __int_as_float(__float_as_int(ref) & 0x7F800000);
-    return ((float)(int)r * 0x1p-55f) * p2;
+    return u * __int_as_float(__float_as_int(ref) & 0x7F800000);
+}
+
+// A draw u in [-2^-24, 2^-24) from the random word r (the signed word times
+// 2^-55). Each (launch, node, velocity row) draws two, a and b; the row's
+// velocity columns take a, b, -a, -b in turn, so every population's dither is
+// uniform and fresh at every launch while the draw costs nothing per population.
+__device__ __forceinline__ float dither_unit(unsigned r)
+{
+    return (float)(int)r * 0x1p-55f;
+}
+__device__ __forceinline__ unsigned dither_word_b(unsigned hrow)
+{
+    return hrow * 0x9E3779B9u;
+}
+template <class U>
+__device__ __forceinline__ U dither_pick(int ix, U a, U b, U na, U nb)
+{
+    switch (ix & 3) {
+    case 0: return a;
+    case 1: return b;
+    case 2: return na;
+    default: return nb;
+    }
 }
 
 __device__ __forceinline__ int wrap_index(int i, int L)

@@ -139,6 +139,8 @@ struct Step2DArgsT {
     unsigned *status;     // bit 0: non-positive density / positivity domain left
     unsigned *step_ctr;   // launches so far: seeds the FP32 dithered rounding
     unsigned *done_ctr;   // CTAs finished in the current launch
+    void *rw;             // wall densities, 2 x pitch per instance (k_wall_rho), or null:
+                          // then every tile near a wall sums them itself
     int Lx, Ly, pitch, bc;
     long long plane;      // elements per velocity plane
     long long inst_stride;// elements per instance

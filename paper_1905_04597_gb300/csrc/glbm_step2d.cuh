@@ -47,15 +47,73 @@ struct Step2D {
         T eqy[G > 1 ? R : 1][G > 1 ? Q1 : 1][32];
     };
 
+    // Wall densities of the columns of cofs (phase 0): for each wall flagged,
+    // the mass streaming into it, summed over the pairs (velocity, row) with
+    // row < |ny| from the previous post-collision state fin, becomes rho_w(x)
+    // (FP64) or rho_w(x) - 1 (FP32) in rw[0] (y = -1/2) or rw[1] (y = Ly - 1/2).
+    // The pairs are enumerated in order of |ny| and summed by NV fixed
+    // accumulators (pair number mod NV) that the nw warps share round robin, so
+    // the order of the additions depends neither on the tile shape nor on the
+    // launch. The loops stay rolled (few tiles run it; the code must not grow).
+    // Every thread of the CTA calls it.
+    __device__ static void wall_densities(const InstParams &ip, const T *__restrict__ fin, int Ly,
+                                          int pitch, int plane, const int (&cofs)[QX], bool need_lo,
+                                          bool need_hi, int w, int nw, int lane,
+                                          T (&dsum)[NV][2][32], T (&rw)[2][32])
+    {
+#pragma unroll 1
+        for (int v = w; v < NV; v += nw) {
+            T slo = T(0), shi = T(0);
+#pragma unroll 1
+            for (int p = v; p < AY::NPAIR; p += NV) {
+                int m = AY::M0, k = p;
+                while (k >= AY::vmag(m)) {
+                    k -= AY::vmag(m);
+                    ++m;
+                }
+                if (need_lo) {  // velocity ny = -|v_m| leaving row k through y = -1/2
+                    const T *pl = fin + (AY::ineg(m) * QX * plane + k * pitch);
+#pragma unroll
+                    for (int ix = 0; ix < QX; ++ix) slo += __ldg(pl + cofs[ix]);
+                }
+                if (need_hi) {  // velocity ny = +|v_m| leaving row Ly-1-k through y = Ly-1/2
+                    const T *ph = fin + (AY::ipos(m) * QX * plane + (Ly - 1 - k) * pitch);
+#pragma unroll
+                    for (int ix = 0; ix < QX; ++ix) shi += __ldg(ph + cofs[ix]);
+                }
+            }
+            dsum[v][0][lane] = slo;
+            dsum[v][1][lane] = shi;
+        }
+        __syncthreads();
+        if (w == 0) {
+            T s0 = T(0), s1 = T(0);
+#pragma unroll
+            for (int j = 0; j < NV; ++j) {
+                s0 += dsum[j][0][lane];
+                s1 += dsum[j][1][lane];
+            }
+            const T inv_den = DEV ? (T)ip.inv_den_f : (T)ip.inv_den;
+            // FP64: rho_w = D / den.  FP32: rho_w - 1 = (D - den) / den, and
+            // D - den is the sum of the absorbed deviations.
+            rw[0][lane] = s0 * inv_den;
+            rw[1][lane] = s1 * inv_den;
+        }
+        __syncthreads();
+    }
+
     // One tile: columns x0..x0+31, rows y0..y0+R-1 of one instance whose
     // populations start at fin / fout; tab is the y axis's table, tabx the x
-    // axis's (the same table for isotropic lattices). Every thread calls it.
+    // axis's (the same table for isotropic lattices). rwg, when set, holds the
+    // instance's wall densities (rwg[x] at y = -1/2, rwg[pitch + x] at
+    // y = Ly - 1/2) from k_wall_rho, and phase 0 is skipped. Every thread
+    // calls it.
     template <class TY, class TX>
     __device__ static void run(const TY &tab, const TX &tabx, const InstParams &ip,
                                int Lx, int Ly,
                                int pitch, int plane, int bc, const T *__restrict__ fin,
                                T *__restrict__ fout, int x0, int y0, Smem &sm, unsigned *status,
-                               unsigned seed)
+                               unsigned seed, const T *__restrict__ rwg = nullptr)
     {
         const int lane = threadIdx.x & 31;
         const int w = threadIdx.x >> 5;
@@ -75,54 +133,12 @@ struct Step2D {
             cofs[ix] = ix * plane + wrap_shift(xc - AX::vel(ix), Lx, Lx > AX::VMAX);
 
         // ---- phase 0: wall densities of this tile's columns ---------------
+        // (read from rwg instead when a separate launch computed them)
         const bool need_lo = walls && (y0 < AY::VMAX);
         const bool need_hi = walls && (y0 + R > Ly - AY::VMAX);
-        if (need_lo || need_hi) {
-            // pairs (velocity, row) with row < |ny|, enumerated in order of |ny|,
-            // summed by NV fixed accumulators (p mod NV) that the warps share
-            // round robin, so the order of the additions does not depend on the
-            // tile shape; the loops stay rolled (the wall prologue runs on few
-            // tiles and must not grow the code)
-#pragma unroll 1
-            for (int v = w; v < NV; v += NW) {
-                T slo = T(0), shi = T(0);
-#pragma unroll 1
-                for (int p = v; p < AY::NPAIR; p += NV) {
-                    int m = AY::M0, k = p;
-                    while (k >= AY::vmag(m)) {
-                        k -= AY::vmag(m);
-                        ++m;
-                    }
-                    if (need_lo) {  // velocity ny = -|v_m| leaving row k through y = -1/2
-                        const T *pl = fin + (AY::ineg(m) * QX * plane + k * pitch);
-#pragma unroll
-                        for (int ix = 0; ix < QX; ++ix) slo += __ldg(pl + cofs[ix]);
-                    }
-                    if (need_hi) {  // velocity ny = +|v_m| leaving row Ly-1-k through y = Ly-1/2
-                        const T *ph = fin + (AY::ipos(m) * QX * plane + (Ly - 1 - k) * pitch);
-#pragma unroll
-                        for (int ix = 0; ix < QX; ++ix) shi += __ldg(ph + cofs[ix]);
-                    }
-                }
-                sm.dsum[v][0][lane] = slo;
-                sm.dsum[v][1][lane] = shi;
-            }
-            __syncthreads();
-            if (w == 0) {
-                T s0 = T(0), s1 = T(0);
-#pragma unroll
-                for (int j = 0; j < NV; ++j) {
-                    s0 += sm.dsum[j][0][lane];
-                    s1 += sm.dsum[j][1][lane];
-                }
-                const T inv_den = DEV ? (T)ip.inv_den_f : (T)ip.inv_den;
-                // FP64: rho_w = D / den.  FP32: rho_w - 1 = (D - den) / den, and
-                // D - den is the sum of the absorbed deviations.
-                sm.rw[0][lane] = s0 * inv_den;
-                sm.rw[1][lane] = s1 * inv_den;
-            }
-            __syncthreads();
-        }
+        if ((need_lo || need_hi) && !rwg)
+            wall_densities(ip, fin, Ly, pitch, plane, cofs, need_lo, need_hi, w, NW, lane, sm.dsum,
+                           sm.rw);
 
         // ---- phase 1: pull and partial moments -----------------------------
         // This warp's velocity rows are iy = g + k G (k = 0..RPG-1): the row is a
@@ -153,7 +169,7 @@ struct Step2D {
                 if (walls && (ys < 0 || ys >= Ly)) {  // uniform across the warp
                     const bool lo = ys < 0;
                     const T wy = A::W(tab, iy);
-                    const T rw = sm.rw[lo ? 0 : 1][lane];
+                    const T rw = rwg ? __ldg(rwg + (lo ? xc : pitch + xc)) : sm.rw[lo ? 0 : 1][lane];
 #pragma unroll
                     for (int ix = 0; ix < QX; ++ix) {
                         if (DEV) {
@@ -274,8 +290,11 @@ struct Step2D {
                 // FP32: delta f^eq = d^x rho e^y + W^x (drho W^y + rho d^y)
                 const T B = DEV ? fma(drho, wy, rho * dy) : T(0);
                 T *const op = obase + iy * QX * plane;
-                // random word of this row: node word plus a multiple of the row
+                // random word of this row: node word plus a multiple of the row;
+                // the row's two dither draws
                 const unsigned hrow = hnode + (unsigned)iy * 0x85EBCA6Bu;
+                const float ua = DEV ? dither_unit(hrow) : 0.0f;
+                const float ub = DEV ? dither_unit(dither_word_b(hrow)) : 0.0f;
 #pragma unroll
                 for (int ix = 0; ix < QX; ++ix) {
                     const int nx = AX::vel(ix);
@@ -287,8 +306,8 @@ struct Step2D {
                         const T dxv = DX_SHARED ? sm.eqx[r][ix][lane] : dx[ix];
                         const T eq = fma(dxv, rey, A::W(tabx, ix) * Bn);
                         // increment plus dither, then one rounding of the store
-                        const unsigned rnd = hrow * (0x9E3779B9u * (2u * ix + 1u)) + 0x7F4A7C15u * ix;
-                        const T inc = fma(om, eq - f0, (T)dither_ulp((float)f0, rnd));
+                        const float u = dither_pick(ix, ua, ub, -ua, -ub);
+                        const T inc = fma(om, eq - f0, (T)dither_ulp((float)f0, u));
                         v = f0 + inc;
                     } else {
                         T eq = ex[ix] * rey;
@@ -328,11 +347,43 @@ __global__ void __launch_bounds__(32 * G * R)
     T *fout = static_cast<T *>(a.fout) + (long long)inst * a.inst_stride;
     // launch counter (read before any CTA of this launch can advance it)
     const unsigned seed = S::DEV ? hash32(__ldcg(a.step_ctr) * 0x632BE5ABu + inst) : 0u;
+    const T *rwg = a.rw ? static_cast<const T *>(a.rw) + (long long)inst * 2 * a.pitch : nullptr;
     if constexpr (NXL == N && ZX == ZY)
         S::run(a.tab, a.tab, a.ip[inst], a.Lx, a.Ly, a.pitch, (int)a.plane, a.bc, fin, fout,
-               blockIdx.x * 32, blockIdx.y * R, sm, a.status, seed);
+               blockIdx.x * 32, blockIdx.y * R, sm, a.status, seed, rwg);
     else
         S::run(a.tab, a.tabx, a.ip[inst], a.Lx, a.Ly, a.pitch, (int)a.plane, a.bc, fin, fout,
-               blockIdx.x * 32, blockIdx.y * R, sm, a.status, seed);
+               blockIdx.x * 32, blockIdx.y * R, sm, a.status, seed, rwg);
     if (S::DEV) advance_launch_counter(a.step_ctr, a.done_ctr);
+}
+
+// Wall densities of one step computed once per column and wall, for lattices
+// whose tiles within reach of a wall would otherwise each repeat the sums of
+// phase 0 (the step launched next reads them through Step2DArgs::rw). Grid
+// (ceil(Lx / 32), instances, 2 walls) of NV warps; writes rho_w (FP64) or
+// rho_w - 1 (FP32) of column x and wall h (0: y = -1/2, 1: y = Ly - 1/2) at
+// rw[(inst * 2 + h) * pitch + x]. The sums are those of phase 0, in the same
+// order, so the step's result does not depend on which of the two ran.
+template <int N, typename T, int NXL, int ZY, int ZX>
+__global__ void __launch_bounds__(32 * Step2D<N, T, 1, 1, NXL, ZY, ZX>::NV)
+    k_wall_rho(const __grid_constant__ Step2DArgsOf<N> a)
+{
+    using S = Step2D<N, T, 1, 1, NXL, ZY, ZX>;
+    using AX = typename S::AX;
+    __shared__ T dsum[S::NV][2][32];
+    __shared__ T rw[2][32];
+    wait_prior_grid();
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int inst = blockIdx.y, h = blockIdx.z;
+    const int x = blockIdx.x * 32 + lane;
+    const int xc = x < a.Lx ? x : a.Lx - 1;
+    const T *fin = static_cast<const T *>(a.fin) + (long long)inst * a.inst_stride;
+    int cofs[S::QX];
+#pragma unroll
+    for (int ix = 0; ix < S::QX; ++ix)
+        cofs[ix] = ix * (int)a.plane + wrap_shift(xc - AX::vel(ix), a.Lx, a.Lx > AX::VMAX);
+    S::wall_densities(a.ip[inst], fin, a.Ly, a.pitch, (int)a.plane, cofs, h == 0, h == 1, w, S::NV,
+                      lane, dsum, rw);
+    if (w == 0 && x < a.Lx)
+        static_cast<T *>(a.rw)[((long long)inst * 2 + h) * a.pitch + x] = rw[h][lane];
 }

@@ -41,6 +41,8 @@ static cudaError_t launch_x1_shape(int shape, const Step2DArgs &a, int n_inst, c
         if (shape == I) {
             constexpr TileShape t = TilesX1<N, T>::shape[I];
             const dim3 grid((a.Lx + 32 * t.V - 1) / (32 * t.V), (a.Ly + t.R - 1) / t.R, n_inst);
+            const cudaError_t e = launch_wall_rho<N, T, 1, 0, 0>(a, n_inst, s);
+            if (e != cudaSuccess) return e;
             if constexpr (t.V == 2) {
                 static_assert(sizeof(T) == 4, "pair tiles store FP32 deviations");
                 return launch_serialized(k_step2d_pair<N, t.G, t.R, 1>, grid, dim3(32 * t.G * t.R), s, a);

@@ -16,12 +16,14 @@ __global__ void __launch_bounds__(32 * G * R)
     float *fout = static_cast<float *>(a.fout) + (long long)inst * a.inst_stride;
     // launch counter (read before any CTA of this launch can advance it)
     const unsigned seed = hash32(__ldcg(a.step_ctr) * 0x632BE5ABu + inst);
+    const float *rwg =
+        a.rw ? static_cast<const float *>(a.rw) + (long long)inst * 2 * a.pitch : nullptr;
     if constexpr (NXL == N && ZX == ZY)
         S::run(a.tab, a.tab, a.ip[inst], a.Lx, a.Ly, a.pitch, (int)a.plane, a.bc, fin, fout,
-               blockIdx.x * S::TW, blockIdx.y * R, sm, a.status, seed);
+               blockIdx.x * S::TW, blockIdx.y * R, sm, a.status, seed, rwg);
     else
         S::run(a.tab, a.tabx, a.ip[inst], a.Lx, a.Ly, a.pitch, (int)a.plane, a.bc, fin, fout,
-               blockIdx.x * S::TW, blockIdx.y * R, sm, a.status, seed);
+               blockIdx.x * S::TW, blockIdx.y * R, sm, a.status, seed, rwg);
     advance_launch_counter(a.step_ctr, a.done_ctr);
 }
 
@@ -43,6 +45,17 @@ inline cudaError_t launch_serialized(void (*kern)(Args), dim3 grid, dim3 block, 
     return cudaLaunchKernelEx(&cfg, kern, a);
 }
 
+// The wall-density launch that precedes a step whose arguments carry a
+// wall-density buffer (Step2DArgs::rw); nothing otherwise.
+template <int N, typename T, int NXL, int ZY, int ZX, class Args>
+inline cudaError_t launch_wall_rho(const Args &a, int n_inst, cudaStream_t s)
+{
+    if (!a.rw || a.bc != GLBM_BC_WALLS) return cudaSuccess;
+    constexpr int NV = Step2D<N, T, 1, 1, NXL, ZY, ZX>::NV;
+    return launch_serialized(k_wall_rho<N, T, NXL, ZY, ZX>, dim3((a.Lx + 31) / 32, n_inst, 2),
+                             dim3(32 * NV), s, a);
+}
+
 // Launch of tile shape number I of level N.
 template <int N, typename T, int I = 0>
 cudaError_t launch_step2d_shape(int shape, const Step2DArgs &a, int n_inst, cudaStream_t s)
@@ -52,6 +65,8 @@ cudaError_t launch_step2d_shape(int shape, const Step2DArgs &a, int n_inst, cuda
             constexpr TileShape t = Tiles<N, T>::shape[I];
             constexpr int G = t.G, R = t.R, TW = 32 * t.V;
             const dim3 grid((a.Lx + TW - 1) / TW, (a.Ly + R - 1) / R, n_inst);
+            const cudaError_t e = launch_wall_rho<N, T, N, 0, 0>(a, n_inst, s);
+            if (e != cudaSuccess) return e;
             if constexpr (t.V == 2) {
                 static_assert(sizeof(T) == 4, "pair tiles store FP32 deviations");
                 return launch_serialized(k_step2d_pair<N, G, R>, grid, dim3(32 * G * R), s, a);

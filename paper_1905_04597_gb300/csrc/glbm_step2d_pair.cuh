@@ -196,8 +196,9 @@ __device__ __forceinline__ void pair_wall_row(const TY &tab, const TX &tabx,
 // Relaxation plus force and the dithered FP32 store of velocity row iy of a
 // node pair: f* = f + omega (f^eq + F/omega - f) with
 // delta f^eq = d^x rho e^y + W^x (drho W^y + rho d^y), the force through the
-// row factor gr = W^y g / (theta omega), and a dither of half an ulp drawn from
-// the nodes' words h0, h1, the row and the column. E^x - W comes from the
+// row factor gr = W^y g / (theta omega), and a dither of half an ulp from the
+// two draws of each node's row word (h0, h1 and the row), taken in turn with
+// alternating signs along the row. E^x - W comes from the
 // registers dxr, or from shared memory at dxs (stride 32 pairs) when DXS.
 // N and tabx: the x axis.
 template <int N, bool DXS, int ZX, class TX>
@@ -216,7 +217,10 @@ __device__ __forceinline__ void pair_collide_row(const TX &tabx, int iy, float w
     const f32x2 B = fma2(drho, wy2, mul2(rho, dy));
     const unsigned hr0 = h0 + (unsigned)iy * 0x85EBCA6Bu;  // row words
     const unsigned hr1 = h1 + (unsigned)iy * 0x85EBCA6Bu;
-    const f32x2 two55 = pk2(0x1p-55f, 0x1p-55f);
+    // the row's two dither draws of each node and their negatives
+    const float a0 = dither_unit(hr0), a1 = dither_unit(hr1);
+    const float b0 = dither_unit(dither_word_b(hr0)), b1 = dither_unit(dither_word_b(hr1));
+    const f32x2 ua = pk2(a0, a1), ub = pk2(b0, b1), na = pk2(-a0, -a1), nb = pk2(-b0, -b1);
 #pragma unroll
     for (int ix = 0; ix < 2 * N + 1 + ZX; ++ix) {
         const int nx = AxisVel<N, ZX>::vel(ix);
@@ -226,11 +230,9 @@ __device__ __forceinline__ void pair_collide_row(const TX &tabx, int iy, float w
         const f32x2 dxv = DXS ? dxs[ix * 32] : dxr[ix];
         const f32x2 eq = fma2(dxv, rey, mul2(pk2(wx, wx), Bn));
         // increment plus dither, then one rounding of the store
-        const unsigned a = 0x9E3779B9u * (2u * ix + 1u), b = 0x7F4A7C15u * ix;
-        const unsigned r0 = hr0 * a + b, r1 = hr1 * a + b;
         const float p0 = __int_as_float(__float_as_int(lo2(f0)) & 0x7F800000);
         const float p1 = __int_as_float(__float_as_int(hi2(f0)) & 0x7F800000);
-        const f32x2 dith = mul2(mul2(pk2((float)(int)r0, (float)(int)r1), two55), pk2(p0, p1));
+        const f32x2 dith = mul2(dither_pick(ix, ua, ub, na, nb), pk2(p0, p1));
         const f32x2 inc = fma2(om, sub2(eq, f0), dith);
         const f32x2 v = add2(f0, inc);
         float *const o = op + ix * plane;
@@ -268,12 +270,15 @@ struct Step2DPair {
     // One tile: columns x0..x0+63 (x0 a multiple of 64), rows y0..y0+R-1 of one
     // instance whose populations start at fin / fout (8-byte aligned planes);
     // tab is the y axis's table, tabx the x axis's (the same when isotropic).
+    // rwg, when set, holds the instance's wall densities from k_wall_rho
+    // (rwg[x] at y = -1/2, rwg[pitch + x] at y = Ly - 1/2).
     template <class TY, class TX>
     __device__ static void run(const TY &tab, const TX &tabx, const InstParams &ip,
                                int Lx, int Ly,
                                int pitch, int plane, int bc, const float *__restrict__ fin,
                                float *__restrict__ fout, int x0, int y0, Smem &sm,
-                               unsigned *status, unsigned seed)
+                               unsigned *status, unsigned seed,
+                               const float *__restrict__ rwg = nullptr)
     {
         const int lane = threadIdx.x & 31;
         const int w = threadIdx.x >> 5;
@@ -298,7 +303,7 @@ struct Step2DPair {
         // ---- phase 0: wall densities of this tile's columns ---------------
         const bool need_lo = walls && (y0 < AY::VMAX);
         const bool need_hi = walls && (y0 + R > Ly - AY::VMAX);
-        if (need_lo || need_hi)
+        if ((need_lo || need_hi) && !rwg)  // else computed by k_wall_rho
             pair_wall_densities<N, NXL, NV, ZY, ZX>(ip, fin, Ly, pitch, plane, win, need_lo, need_hi,
                                                     w, NW, lane, sm.dsum, sm.rw);
 
@@ -324,8 +329,16 @@ struct Step2DPair {
                 const int ys = yc - ny;
                 if (walls && (ys < 0 || ys >= Ly)) {  // uniform across the warp
                     const bool lo = ys < 0;
-                    pair_wall_row<NXL, ZX>(tab, tabx, ip, iy, lo, sm.rw[lo ? 0 : 1][2 * lane],
-                                     sm.rw[lo ? 0 : 1][2 * lane + 1], f[k]);
+                    float rw0, rw1;
+                    if (rwg) {
+                        const float *rl = rwg + (lo ? 0 : pitch);
+                        rw0 = __ldg(rl + xc);
+                        rw1 = __ldg(rl + (x + 1 < Lx ? x + 1 : xc));
+                    } else {
+                        rw0 = sm.rw[lo ? 0 : 1][2 * lane];
+                        rw1 = sm.rw[lo ? 0 : 1][2 * lane + 1];
+                    }
+                    pair_wall_row<NXL, ZX>(tab, tabx, ip, iy, lo, rw0, rw1, f[k]);
                 }
                 f32x2 rs = 0ull;
 #pragma unroll

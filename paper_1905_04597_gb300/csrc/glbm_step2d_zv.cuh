@@ -17,6 +17,8 @@ cudaError_t launch_zv_shape(int shape, const Step2DArgsOf<N> &a, int n_inst, cud
             constexpr int NXL = KIND == GLBM_ZVK_X1 ? 1 : N;
             constexpr int ZX = KIND == GLBM_ZVK_X1 ? 0 : 1;
             const dim3 grid((a.Lx + 32 * t.V - 1) / (32 * t.V), (a.Ly + t.R - 1) / t.R, n_inst);
+            const cudaError_t e = launch_wall_rho<N, T, NXL, 1, ZX>(a, n_inst, s);
+            if (e != cudaSuccess) return e;
             if constexpr (t.V == 2) {
                 static_assert(sizeof(T) == 4, "pair tiles store FP32 deviations");
                 return launch_serialized(k_step2d_pair<N, t.G, t.R, NXL, 1, ZX>, grid,

@@ -247,6 +247,8 @@ struct Step3D {
                 const T B = DEV ? fma(dyv, rez, wy * fma(drho, wz, rho * dzv)) : T(0);
                 T *const op = obase + row * Q1 * plane;
                 const unsigned hrow = hnode + (unsigned)row * 0x85EBCA6Bu;
+                const float ua = DEV ? dither_unit(hrow) : 0.0f;  // the row's dither draws
+                const float ub = DEV ? dither_unit(dither_word_b(hrow)) : 0.0f;
 #pragma unroll
                 for (int ix = 0; ix < Q1; ++ix) {
                     const int nx = ix - N;
@@ -255,8 +257,8 @@ struct Step3D {
                     if (DEV) {
                         const T Bn = nx != 0 ? fma(T(nx), gr, B) : B;
                         const T eq = fma(dx[ix], rez_y, A::W(tab, ix) * Bn);
-                        const unsigned rnd = hrow * (0x9E3779B9u * (2u * ix + 1u)) + 0x7F4A7C15u * ix;
-                        const T inc = fma(om, eq - f0, (T)dither_ulp((float)f0, rnd));
+                        const float u = dither_pick(ix, ua, ub, -ua, -ub);
+                        const T inc = fma(om, eq - f0, (T)dither_ulp((float)f0, u));
                         v = f0 + inc;
                     } else {
                         T eq = (A::W(tab, ix) + dx[ix]) * rez_y;

@@ -93,6 +93,8 @@ def lib():
         "glbm_set_tiles": ([vp, ctypes.POINTER(i)], i),
         "glbm_get_tile_shape": ([vp, i] + [ctypes.POINTER(i)] * 3, i),
         "glbm_autotune": ([vp, i, dp], i),
+        "glbm_set_wall_launch": ([vp, i], i),
+        "glbm_get_wall_launch": ([vp], i),
         "glbm_last_error": ([], ctypes.c_char_p),
     }
     for name, (args, res) in sig.items():
@@ -379,6 +381,17 @@ class Lattice:
             if any(v >= 0 for v in row):
                 out[k] = [v for v in row if v >= 0]
         return out
+
+    @property
+    def wall_launch(self):
+        """1: the wall densities get a launch of their own each step; 0: every
+        tile near a wall sums them itself; -1: no walls (or a mixed batch, 3D)."""
+        return lib().glbm_get_wall_launch(self.h)
+
+    def set_wall_launch(self, mode):
+        """Choose how the wall densities are computed (0, 1, or -1 for the
+        context's default); the results are identical either way."""
+        check(lib().glbm_set_wall_launch(self.h, int(mode)))
 
     @property
     def time(self):
