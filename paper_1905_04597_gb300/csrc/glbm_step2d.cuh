@@ -54,8 +54,11 @@ struct Step2D {
     // The pairs are enumerated in order of |ny| and summed by NV fixed
     // accumulators (pair number mod NV) that the nw warps share round robin, so
     // the order of the additions depends neither on the tile shape nor on the
-    // launch. The loops stay rolled (few tiles run it; the code must not grow).
-    // Every thread of the CTA calls it.
+    // launch. U pairs of an accumulator are loaded before they are added (more
+    // loads in flight, same order of additions): the tiles' prologue keeps
+    // U = 1 and its loops rolled (the code must not grow), k_wall_rho takes
+    // more. Every thread of the CTA calls it.
+    template <int U = 1>
     __device__ static void wall_densities(const InstParams &ip, const T *__restrict__ fin, int Ly,
                                           int pitch, int plane, const int (&cofs)[QX], bool need_lo,
                                           bool need_hi, int w, int nw, int lane,
@@ -65,21 +68,38 @@ struct Step2D {
         for (int v = w; v < NV; v += nw) {
             T slo = T(0), shi = T(0);
 #pragma unroll 1
-            for (int p = v; p < AY::NPAIR; p += NV) {
-                int m = AY::M0, k = p;
-                while (k >= AY::vmag(m)) {
-                    k -= AY::vmag(m);
-                    ++m;
-                }
-                if (need_lo) {  // velocity ny = -|v_m| leaving row k through y = -1/2
-                    const T *pl = fin + (AY::ineg(m) * QX * plane + k * pitch);
+            for (int p0 = v; p0 < AY::NPAIR; p0 += U * NV) {
+                T vlo[U][QX], vhi[U][QX];
 #pragma unroll
-                    for (int ix = 0; ix < QX; ++ix) slo += __ldg(pl + cofs[ix]);
-                }
-                if (need_hi) {  // velocity ny = +|v_m| leaving row Ly-1-k through y = Ly-1/2
-                    const T *ph = fin + (AY::ipos(m) * QX * plane + (Ly - 1 - k) * pitch);
+                for (int u = 0; u < U; ++u) {
+                    const int p = p0 + u * NV;
+                    if (p < AY::NPAIR) {
+                        int m = AY::M0, k = p;
+                        while (k >= AY::vmag(m)) {
+                            k -= AY::vmag(m);
+                            ++m;
+                        }
+                        if (need_lo) {  // velocity ny = -|v_m| leaving row k through y = -1/2
+                            const T *pl = fin + (AY::ineg(m) * QX * plane + k * pitch);
 #pragma unroll
-                    for (int ix = 0; ix < QX; ++ix) shi += __ldg(ph + cofs[ix]);
+                            for (int ix = 0; ix < QX; ++ix) vlo[u][ix] = __ldg(pl + cofs[ix]);
+                        }
+                        if (need_hi) {  // velocity ny = +|v_m| leaving row Ly-1-k through y = Ly-1/2
+                            const T *ph = fin + (AY::ipos(m) * QX * plane + (Ly - 1 - k) * pitch);
+#pragma unroll
+                            for (int ix = 0; ix < QX; ++ix) vhi[u][ix] = __ldg(ph + cofs[ix]);
+                        }
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    if (p0 + u * NV < AY::NPAIR) {
+#pragma unroll
+                        for (int ix = 0; ix < QX; ++ix) {
+                            if (need_lo) slo += vlo[u][ix];
+                            if (need_hi) shi += vhi[u][ix];
+                        }
+                    }
                 }
             }
             dsum[v][0][lane] = slo;
@@ -382,8 +402,11 @@ __global__ void __launch_bounds__(32 * Step2D<N, T, 1, 1, NXL, ZY, ZX>::NV)
 #pragma unroll
     for (int ix = 0; ix < S::QX; ++ix)
         cofs[ix] = ix * (int)a.plane + wrap_shift(xc - AX::vel(ix), a.Lx, a.Lx > AX::VMAX);
-    S::wall_densities(a.ip[inst], fin, a.Ly, a.pitch, (int)a.plane, cofs, h == 0, h == 1, w, S::NV,
-                      lane, dsum, rw);
+    // up to 192 bytes of loads (U pairs) in flight per thread
+    constexpr int LMAX = 192 / (int)sizeof(T);
+    constexpr int U = S::QX >= LMAX ? 1 : LMAX / S::QX;
+    S::template wall_densities<U>(a.ip[inst], fin, a.Ly, a.pitch, (int)a.plane, cofs, h == 0, h == 1,
+                                  w, S::NV, lane, dsum, rw);
     if (w == 0 && x < a.Lx)
         static_cast<T *>(a.rw)[((long long)inst * 2 + h) * a.pitch + x] = rw[h][lane];
 }
