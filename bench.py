@@ -288,11 +288,14 @@ def run_ours(args):
             t[N - 1] = int(args.tiles[4:])
             lat.set_tiles(t)
 
+    wall_mode = {}
+
     def timed(prec, steps, warmup):
         lat = glbm.Lattice([dict(c, prec=prec) for c in cfgs])
         if dims >= 2:
             choose_tiles(lat, prec)
             tiles_used[prec] = kernel_name(prec, lat)
+            wall_mode[prec] = lat.wall_launch if dims == 2 else -1
         lat.step(warmup)
         lat.sync()
         l0 = lat.kernel_launches
@@ -389,7 +392,9 @@ def run_ours(args):
                    "nodes": nodes, "instances": n_inst, "storage": "fp32 deviations",
                    "l2": f"populations {2 * bytes32 / 2 / 1e6:.0f} MB per buffer set x2 > 129 MB L2; no flush",
                    "parallelism": f"instances batched per launch; {world} rank(s), independent copies",
-                   "tiles": args.tiles},
+                   "tiles": args.tiles,
+                   "wall_densities": {1: "own launch", 0: "in the tiles"}.get(
+                       wall_mode.get(glbm.FP32_DEV, -1), "no walls")},
         "mlups": nodes * n_inst * steps * world / (ms32 / 1e3) / 1e6,
         "hbm_gbs_algorithmic": gbs32,
         "fp64": {"value": value64, "unit": UNIT, "ms_per_step": ms64 / steps64, "steps": steps64,
@@ -400,7 +405,11 @@ def run_ours(args):
                      "frac": gbs32 / peak,
                      "traffic": measured_traffic(tiles_used.get(glbm.FP32_DEV), label),
                      "kernel": tiles_used.get(glbm.FP32_DEV, "k_step1d"),
-                     "bytes_per_launch": bytes32, "peak_source": peak_kind},
+                     "bytes_per_launch": bytes32, "peak_source": peak_kind,
+                     "launches_per_step": launches / steps,
+                     "timing": "CUDA events over the timed steps; a step's every launch (the "
+                               "wall-density launch too, where the step has one) is counted "
+                               "against the step kernel"},
         "gpu_launches": launches,
         "clocks": clocks,
         "e2e": e2e,
