@@ -169,3 +169,11 @@ def test_tile_shape_candidates():
         assert glbm.tile_shapes(8, prec) == [] and glbm.tile_shapes(-1, prec) == []
     with pytest.raises(glbm.GlbmError):
         glbm.check(glbm.lib().glbm_tile_shape(0, glbm.FP64, 99, None, None, None))
+
+
+def test_wall_launch_mode_rejects_null_context():
+    """The wall-density mode calls check their arguments before touching a
+    device: a null context is GLBM_E_INVAL (set) or -1 (get)."""
+    assert glbm.lib().glbm_set_wall_launch(None, 0) == glbm.E_INVAL
+    assert glbm.lib().glbm_set_wall_launch(None, 1) == glbm.E_INVAL
+    assert glbm.lib().glbm_get_wall_launch(None) == -1
