@@ -1,7 +1,9 @@
 """The x-slab decomposition's exchange on CPU ranks (gloo, world sizes 2 and
 3) with the oracle as each rank's local stepper: the owned columns of the
 slabs, stepped with one halo exchange per step, equal the undivided
-lattice's run bit for bit (FP64), with walls, moving walls and the force."""
+lattice's run bit for bit (FP64), with walls, moving walls and the force, on
+the isotropic, anisotropic, 2N+2 and 3D lattices (halo width H = the largest
+x speed: N_x, or 2N_x + 1 with the 2N+2 hierarchy along x)."""
 import os
 import socket
 import sys
@@ -23,16 +25,36 @@ def _free_port():
 CASES = {
     "d2q25_walls": dict(N=2, nx=24, ny=9, bc=0, tau=0.8, uw=(-0.04, 0.05), g=3e-5, steps=12),
     "d2q49_periodic": dict(N=3, nx=18, ny=7, bc=2, tau=0.7, uw=(0.0, 0.0), g=0.0, steps=9),
+    # D1Q3 along x, D1Q9 along y: H = 1
+    "d1q3xd1q9_walls": dict(N=4, NX=1, nx=24, ny=11, bc=0, tau=0.9, uw=(-0.03, 0.04), g=2e-5,
+                            steps=10),
+    # the 2N+2 hierarchy on both axes (D2Q36): odd x speeds up to 5, H = 5
+    "d2q36_zv_walls": dict(N=2, zv=3, nx=30, ny=7, bc=0, tau=0.75, uw=(-0.05, 0.03), g=1e-5,
+                           steps=8),
+    # D3Q27 channel, 4 z-slices: H = 1
+    "d3q27_walls": dict(N=1, dims=3, Lz=4, nx=18, ny=5, bc=0, tau=0.8, uw=(-0.04, 0.04), g=2e-5,
+                        steps=8),
 }
+
+
+def _oracle(c, nx):
+    from oracle import oracle as orc
+    dims = c.get("dims", 2)
+    return orc.Lattice(dims, c.get("NX", c["N"]), c["N"], nx, c["ny"], c["bc"], c["tau"],
+                       c["uw"][0], c["uw"][1], c["g"], zv=c.get("zv", 0),
+                       NZ=c["N"] if dims == 3 else 0, Lz=c.get("Lz", 1))
+
+
+def _halo(c):
+    NX = c.get("NX", c["N"])
+    return 2 * NX + 1 if c.get("zv", 0) & 1 else NX
 
 
 class OracleSlab:
     """A rank's slab stepped by the oracle (periodic over the padded width)."""
 
     def __init__(self, c, X):
-        from oracle import oracle as orc
-        self.o = orc.Lattice(2, c["N"], c["N"], X.shape[-1], c["ny"], c["bc"], c["tau"],
-                             c["uw"][0], c["uw"][1], c["g"])
+        self.o = _oracle(c, X.shape[-1])
         self.X = X
 
     def step(self):
@@ -46,9 +68,9 @@ class OracleSlab:
 
 
 def _initial(c):
-    Q = (2 * c["N"] + 1) ** 2
+    shape = _oracle(c, c["nx"]).shape
     rng = np.random.default_rng(7)
-    return rng.uniform(0.5, 1.5, size=(Q, c["ny"], c["nx"])) / Q
+    return rng.uniform(0.5, 1.5, size=shape) / shape[0]
 
 
 def _rank_main(rank, world, port, name, out):
@@ -58,7 +80,7 @@ def _rank_main(rank, world, port, name, out):
     from paper_1905_04597_gb300 import slab
     dist.init_process_group("gloo", rank=rank, world_size=world)
     c = CASES[name]
-    Ls, H = c["nx"] // world, c["N"]
+    Ls, H = c["nx"] // world, _halo(c)
     cols = [(rank * Ls + j - H) % c["nx"] for j in range(Ls + 2 * H)]
     st = OracleSlab(c, np.ascontiguousarray(_initial(c)[..., cols]))
     slab.step_slab(st, c["steps"], Ls, H, rank, world, slab.torch_sendrecv())
@@ -76,9 +98,7 @@ def test_slabs_equal_the_undivided_lattice(name, world, tmp_path):
     c = CASES[name]
     mp.spawn(_rank_main, args=(world, _free_port(), name, str(tmp_path)), nprocs=world, join=True)
     got = np.concatenate([np.load(tmp_path / f"rank{r}.npy") for r in range(world)], axis=-1)
-    o = orc.Lattice(2, c["N"], c["N"], c["nx"], c["ny"], c["bc"], c["tau"], c["uw"][0],
-                    c["uw"][1], c["g"])
-    want, _ = o.run(_initial(c), c["steps"])
+    want, _ = _oracle(c, c["nx"]).run(_initial(c), c["steps"])
     np.testing.assert_array_equal(got, want)
 
 
@@ -88,10 +108,9 @@ def test_single_rank_exchange_wraps_onto_itself():
     from oracle import oracle as orc
     from paper_1905_04597_gb300 import slab
     c = CASES["d2q25_walls"]
-    H, nx = c["N"], c["nx"]
+    H, nx = _halo(c), c["nx"]
     cols = [(j - H) % nx for j in range(nx + 2 * H)]
     st = OracleSlab(c, np.ascontiguousarray(_initial(c)[..., cols]))
     slab.step_slab(st, c["steps"], nx, H, 0, 1, None)
-    o = orc.Lattice(2, c["N"], c["N"], nx, c["ny"], c["bc"], c["tau"], c["uw"][0], c["uw"][1], c["g"])
-    want, _ = o.run(_initial(c), c["steps"])
+    want, _ = _oracle(c, nx).run(_initial(c), c["steps"])
     np.testing.assert_array_equal(st.X[..., H:H + nx], want)
