@@ -63,6 +63,20 @@ def test_equilibrium_moments_per_axis(N):
     np.testing.assert_allclose(m(nx * nz), rho * ux * uz, rtol=1e-11, atol=1e-16)
 
 
+@pytest.mark.parametrize("N", [1, 2, 3])
+def test_equilibrium_moment_fields(N):
+    """The reducer's fields of a local equilibrium: T = N/3, no shear stress,
+    and q_a = half the third central moment of axis a, -rho u_a^3 / N^2 (the
+    third moment of Sec. 3); field order rho, ux, uy, T, qx, qy, sxy, uz, qz."""
+    rho, ux, uy, uz = _fields3(60 + N, 3, 4, 2)
+    lat = _lat3(N, 3, 4, 2, bc=orc.BC_PERIODIC)
+    M = lat.macro(lat.equilibrium(rho, ux, uy, uz))
+    np.testing.assert_allclose(M[3], N / 3.0, rtol=1e-13)
+    np.testing.assert_allclose(M[6], 0.0, rtol=0, atol=1e-14)
+    for i, u in ((4, ux), (5, uy), (8, uz)):
+        np.testing.assert_allclose(M[i], -rho * u ** 3 / (2 * N ** 2), rtol=1e-8, atol=1e-14)
+
+
 @pytest.mark.parametrize("N", [1, 2])
 def test_collision_conserves_mass_and_momenta(N):
     lat = _lat3(N, 5, 4, 3, tau=0.63)

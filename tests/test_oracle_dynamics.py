@@ -4,7 +4,8 @@ Checks against invariants and closed forms: conservation of mass and momentum
 by the BGK collision (Sec. 2: the equilibrium reproduces rho and rho u at every
 level), equilibrium as a fixed point, periodic streaming as an exact shift
 (numpy.roll), mass conservation of the diffuse walls and bounce-back ends,
-the rest state as a fixed point of the wall rule, linear Couette and parabolic
+the rest state as a fixed point of the wall rule, the heat flux and shear
+stress of a local equilibrium (closed forms), linear Couette and parabolic
 Poiseuille profiles at small Knudsen number (Secs. 5.3-5.4, viscosity
 nu = theta tau), growth of the wall slip with Kn, the D2Q9 weights of the
 N = 1 tensor product (Sec. 4), and x-uniform flows staying x-uniform.
@@ -68,6 +69,22 @@ def test_equilibrium_is_fixed_point_of_collision(N):
     np.testing.assert_allclose(M[2], uy, atol=1e-15)
     # temperature of the local equilibrium is the lattice temperature N/3
     np.testing.assert_allclose(M[3], N / 3.0, rtol=1e-13)
+
+
+@pytest.mark.parametrize("N", [1, 2, 4, 8])
+def test_equilibrium_heat_flux_and_shear_stress(N):
+    """At a local equilibrium the shear stress vanishes (the product form makes
+    the central cross moment the product of two zero central first moments)
+    and the heat flux q_x is half the third central moment of the x axis,
+    -rho u_x^3 / N^2 (from the third moment u^3 + 3 u theta - u^3 / N^2 of
+    Sec. 3 with theta = N/3)."""
+    rho, ux, uy = inputs.random_macro(4, 8, 6)
+    lat = _lat2(N, N, 8, 6, bc=orc.BC_PERIODIC)
+    M = lat.macro(lat.equilibrium(rho, ux, uy))
+    assert np.abs(ux).max() > 0.01 and np.abs(uy).max() > 0.01
+    np.testing.assert_allclose(M[6], 0.0, rtol=0, atol=1e-14)
+    np.testing.assert_allclose(M[4], -rho * ux ** 3 / (2 * N ** 2), rtol=1e-8, atol=1e-14)
+    np.testing.assert_allclose(M[5], -rho * uy ** 3 / (2 * N ** 2), rtol=1e-8, atol=1e-14)
 
 
 @pytest.mark.parametrize("N", [1, 2])
@@ -137,6 +154,19 @@ def test_bounceback_conserves_mass_1d():
     X1, bad = lat.run(X0, 300)
     assert bad == 0
     assert X1.sum() == pytest.approx(X0.sum(), rel=1e-13)
+
+
+@pytest.mark.parametrize("N", [1, 3, 8])
+def test_equilibrium_moment_fields_1d(N):
+    """1D reducer on a local equilibrium: T = N/3 and q = half the third central
+    moment, -rho u^3 / N^2 (field order rho, u, T, q)."""
+    L = 12
+    rng = np.random.default_rng(70 + N)
+    rho, u = 1.0 + 0.05 * rng.uniform(-1, 1, L), 0.2 * rng.uniform(-1, 1, L)
+    lat = orc.Lattice(1, N, 0, L, 1, orc.BC_PERIODIC, tau=0.7)
+    M = lat.macro(lat.equilibrium(rho, u))
+    np.testing.assert_allclose(M[2], N / 3.0, rtol=1e-13)
+    np.testing.assert_allclose(M[3], -rho * u ** 3 / (2 * N ** 2), rtol=1e-9, atol=1e-15)
 
 
 def test_d2q9_weights():

@@ -40,6 +40,15 @@ MUTATIONS = {
                              "a->v[j] = zv ? 2 * j - 2 * N : j - N;"),
     "3D z stream sign": ("zd = orc_wrap(z + nz, Lz);", "zd = orc_wrap(z - nz, Lz);"),
     "3D emission without W^z": ("rlo * Elo[ix] * Wy[iy] * Wz[iz];", "rlo * Elo[ix] * Wy[iy];"),
+    "heat flux without 1/2": ("out[4 * plane + node] = 0.5 * qx;", "out[4 * plane + node] = qx;"),
+    "shear stress about zero": ("                sxy += dx * dy * f;\n            }\n        }\n        out[0 * plane",
+                                "                sxy += ax.v[ix] * ay.v[iy] * f;\n            }\n        }\n        out[0 * plane"),
+    "wall denominator without |ny|": ("if (ay.v[iy] > 0) den += ay.v[iy] * Elo[ix] * Wy[iy];",
+                                      "if (ay.v[iy] > 0) den += Elo[ix] * Wy[iy];"),
+    "Kn with theta for 2 theta": ("    double theta = N / 3.0;\n    return kn * H / sqrt(2.0 * theta);",
+                                  "    double theta = N / 3.0;\n    return kn * H / sqrt(theta);"),
+    "3D heat flux without 1/2": ("e2 / (3.0 * rho), 0.5 * qx, 0.5 * qy", "e2 / (3.0 * rho), qx, 0.5 * qy"),
+    "1D heat flux without 1/2": ("out[3 * L + x] = 0.5 * e3;", "out[3 * L + x] = e3;"),
     "3D x and z swapped in q": ("const double f = F[((iz * Qy + iy) * Qx + ix) * plane + node];\n                        rho += f;",
                                 "const double f = F[((ix * Qy + iy) * Qx + iz) * plane + node];\n                        rho += f;"),
 }
