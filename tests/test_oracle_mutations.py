@@ -49,6 +49,12 @@ MUTATIONS = {
                                   "    double theta = N / 3.0;\n    return kn * H / sqrt(theta);"),
     "3D heat flux without 1/2": ("e2 / (3.0 * rho), 0.5 * qx, 0.5 * qy", "e2 / (3.0 * rho), qx, 0.5 * qy"),
     "1D heat flux without 1/2": ("out[3 * L + x] = 0.5 * e3;", "out[3 * L + x] = e3;"),
+    "3D force sign": ("* (ix - NX) * c->g / theta_x", "* (NX - ix) * c->g / theta_x"),
+    "3D force theta": ("        const double theta_x = NX / 3.0;\n", "        const double theta_x = NX;\n"),
+    "tangent of g without theta": ("const double wxg = Wx[nx + NX] * Wy[ny + NY] * nx / theta_x;",
+                                   "const double wxg = Wx[nx + NX] * Wy[ny + NY] * nx;"),
+    "stream y sign": ("                    int yd = y + ny;", "                    int yd = y - ny;"),
+    "3D stream y sign": ("const int yd = y + ny;", "const int yd = y - ny;"),
     "3D x and z swapped in q": ("const double f = F[((iz * Qy + iy) * Qx + ix) * plane + node];\n                        rho += f;",
                                 "const double f = F[((ix * Qy + iy) * Qx + iz) * plane + node];\n                        rho += f;"),
 }
