@@ -55,6 +55,14 @@ MUTATIONS = {
                                    "const double wxg = Wx[nx + NX] * Wy[ny + NY] * nx;"),
     "stream y sign": ("                    int yd = y + ny;", "                    int yd = y - ny;"),
     "3D stream y sign": ("const int yd = y + ny;", "const int yd = y - ny;"),
+    "tangent of rho dropped": ("const double dfeq = rho[d] * Ex[nx + NX] * Ey[ny + NY] +\n                                        rho[0] *",
+                               "const double dfeq = 0.0 * rho[d] * Ex[nx + NX] * Ey[ny + NY] +\n                                        rho[0] *"),
+    "tangent of u without rho term": ("dux[d] = (jx[d] - ux * rho[d]) / rho[0];", "dux[d] = jx[d] / rho[0];"),
+    "tangents not streamed": ("        for (int d = 0; d < 3; ++d) orc_stream2d(c, X + d * n, F + d * n);\n        orc_collide_dual",
+                              "        for (int d = 0; d < 1; ++d) orc_stream2d(c, X + d * n, F + d * n);\n        orc_collide_dual"),
+    "force theta of the y axis": ("double theta_x = orc_axis_theta(&ax);", "double theta_x = orc_axis_theta(&ay);"),
+    "collision x axis with the y flag": ("    orc_axis_make(c->NX, ORC_ZVX(c), &ax);\n    orc_axis_make(c->NY, ORC_ZVY(c), &ay);\n    int Lx = c->Lx, Ly = c->Ly;\n    size_t plane = (size_t)Lx * Ly;\n    double Wx[",
+                                         "    orc_axis_make(c->NX, ORC_ZVY(c), &ax);\n    orc_axis_make(c->NY, ORC_ZVY(c), &ay);\n    int Lx = c->Lx, Ly = c->Ly;\n    size_t plane = (size_t)Lx * Ly;\n    double Wx["),
     "3D x and z swapped in q": ("const double f = F[((iz * Qy + iy) * Qx + ix) * plane + node];\n                        rho += f;",
                                 "const double f = F[((ix * Qy + iy) * Qx + iz) * plane + node];\n                        rho += f;"),
 }
