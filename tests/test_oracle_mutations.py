@@ -63,6 +63,9 @@ MUTATIONS = {
     "force theta of the y axis": ("double theta_x = orc_axis_theta(&ax);", "double theta_x = orc_axis_theta(&ay);"),
     "collision x axis with the y flag": ("    orc_axis_make(c->NX, ORC_ZVX(c), &ax);\n    orc_axis_make(c->NY, ORC_ZVY(c), &ay);\n    int Lx = c->Lx, Ly = c->Ly;\n    size_t plane = (size_t)Lx * Ly;\n    double Wx[",
                                          "    orc_axis_make(c->NX, ORC_ZVY(c), &ax);\n    orc_axis_make(c->NY, ORC_ZVY(c), &ay);\n    int Lx = c->Lx, Ly = c->Ly;\n    size_t plane = (size_t)Lx * Ly;\n    double Wx["),
+    "m sum one term short": ("for (int m = 0; m <= (N - n) / 2; ++m) {", "for (int m = 0; m < (N - n) / 2; ++m) {"),
+    "P0 power": ("pow(P0, N - n - 2 * m);", "pow(P0, N - n - m);"),
+    "P0 closure sign": ("*P0 = 1.0 - *Pp - *Pm;", "*P0 = 1.0 - *Pp + *Pm;"),
     "3D x and z swapped in q": ("const double f = F[((iz * Qy + iy) * Qx + ix) * plane + node];\n                        rho += f;",
                                 "const double f = F[((ix * Qy + iy) * Qx + iz) * plane + node];\n                        rho += f;"),
 }
