@@ -307,7 +307,11 @@ __device__ __forceinline__ void node1d(const AuxArgs &a, const InstParams &ip, c
     const T m0 = s + c;
     const T rho = DEV ? T(1) + m0 : m0;
     const T drho = DEV ? m0 : m0 - T(1);
-    const T u = (sj + cj) / rho;
+    const T j = sj + cj;
+    T u = j / rho;
+    // FP32: u = j / (1 + delta rho) from the unrounded density, by one
+    // correction with the residual (j - u) - u delta rho (j - u is exact)
+    if (DEV) u += fma(-u, drho, j - u) / rho;
     const T umax = (T)(0.816496580927726 * N);
     if (!(rho > T(0)) || !(fabs(u) <= umax)) atomicOr(status, 1u);
     T d[Q1];
@@ -316,8 +320,9 @@ __device__ __forceinline__ void node1d(const AuxArgs &a, const InstParams &ip, c
 #pragma unroll
     for (int ix = 0; ix < Q1; ++ix) {
         const T w = Acc::W(a.tab, ix);
-        // FP32: delta f^eq = drho W + rho d ; FP64: f^eq = rho (W + d)
-        const T eq = DEV ? fma(drho, w, rho * d[ix]) : rho * (w + d[ix]);
+        // FP32: delta f^eq = d + drho (W + d), the momentum-carrying d unscaled
+        // by a rounded rho; FP64: f^eq = rho (W + d)
+        const T eq = DEV ? fma(drho, w + d[ix], d[ix]) : rho * (w + d[ix]);
         fout[(long long)ix * plane + x] = fma(om, eq - f[ix], f[ix]);  // f + omega (f^eq - f)
     }
 }

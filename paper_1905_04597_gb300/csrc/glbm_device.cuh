@@ -49,86 +49,6 @@ __device__ __forceinline__ void wait_prior_grid() { asm volatile("griddepcontrol
 __device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
 __device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
 
-// Deviation of the level-N equilibrium from the rest weights, for one |n|:
-// Ae_n(v) (even powers >= 2) and Bo_n(v) (odd powers / u), v = u^2, so that
-// E_{+n}(u) - W_n = Ae + u Bo and E_{-n}(u) - W_n = Ae - u Bo. On the 2N+2
-// hierarchy (Z = 1) n is the magnitude index m of the velocities +-(2m+1).
-template <int N, typename T, int Z = 0, class Tab>
-__device__ __forceinline__ void eq_parts(const Tab &t, int n, T v, T &ae, T &bo)
-{
-    using A = TabAcc<T>;
-    T a = A::Ce(t, n, N);
-#pragma unroll
-    for (int i = N - 1; i >= 1; --i) a = fma(a, v, A::Ce(t, n, i));
-    ae = mul_rn(a, v);
-    if (n == 0 && !Z) {
-        bo = T(0);  // E_0 is even in u
-    } else if (A::HILO) {
-        // linear coefficient as hi + lo: the low part joins before the high part
-        T b = A::Co(t, n, N - 1);
-        if (N >= 2) {
-#pragma unroll
-            for (int i = N - 2; i >= 1; --i) b = fma(b, v, A::Co(t, n, i));
-            b = fma(b, v, A::C1lo(t, n));
-        } else {
-            b = A::C1lo(t, n);
-        }
-        bo = b + A::Co(t, n, 0);
-    } else {
-        T b = A::Co(t, n, N - 1);
-#pragma unroll
-        for (int i = N - 2; i >= 0; --i) b = fma(b, v, A::Co(t, n, i));
-        bo = b;
-    }
-}
-
-// d[i] = E_i(u) - W_i for every velocity index i of the axis (i = n + N on
-// the 2N+1 hierarchy).
-template <int N, typename T, int Z = 0, class Tab>
-__device__ __forceinline__ void eq_dev_all(const Tab &t, T u, T (&d)[2 * N + 1 + Z])
-{
-    using AV = AxisVel<N, Z>;
-    const T v = u * u;
-#pragma unroll
-    for (int n = 0; n <= N; ++n) {
-        T ae, bo;
-        eq_parts<N, T, Z>(t, n, v, ae, bo);
-        if (n == 0 && !Z) {
-            d[N] = ae;
-        } else {
-            d[AV::ipos(n)] = fma(u, bo, ae);
-            d[AV::ineg(n)] = fma(-u, bo, ae);
-        }
-    }
-}
-
-// E_n(u) - W_n for a single n (compile-time after unrolling).
-template <int N, typename T, class Tab>
-__device__ __forceinline__ T eq_dev_one(const Tab &t, T u, int n)
-{
-    const int an = n < 0 ? -n : n;
-    T ae, bo;
-    eq_parts<N, T>(t, an, u * u, ae, bo);
-    if (an == 0) return ae;
-    return n > 0 ? fma(u, bo, ae) : fma(-u, bo, ae);
-}
-
-// Knuth's two-sum: s + x is added to (s, c) with the rounding error of the
-// addition carried in c (compensated summation of the FP32 moments).
-__device__ __forceinline__ void acc2(float &s, float &c, float x)
-{
-    const float t = s + x;
-    const float bp = t - s;
-    const float err = (s - (t - bp)) + (x - bp);
-    s = t;
-    c += err;
-}
-__device__ __forceinline__ void acc2(double &s, double &c, double x)
-{
-    (void)c;
-    s += x;
-}
-
 // 32-bit integer hash (xorshift-multiply), used to draw the dither of the
 // FP32 stores from (launch, instance, node).
 __device__ __forceinline__ unsigned hash32(unsigned x)
@@ -164,6 +84,17 @@ __device__ __forceinline__ unsigned dither_word_b(unsigned hrow)
 {
     return hrow * 0x9E3779B9u;
 }
+// Second and third random words of a node word, for the stochastic rounding
+// of its velocity components (decorrelated from the row words).
+__device__ __forceinline__ unsigned dither_word_ux(unsigned hnode) { return hnode * 0x27D4EB2Du; }
+__device__ __forceinline__ unsigned dither_word_uy(unsigned hnode) { return hnode * 0x165667B1u; }
+__device__ __forceinline__ unsigned dither_word_uz(unsigned hnode) { return hnode * 0xD3A2646Du; }
+// Words of the stochastic rounding of a node's equilibrium polynomials, one
+// per axis, and a draw in [-2^-23, 2^-23) (two ulps at dither_ulp's scale).
+__device__ __forceinline__ unsigned dither_word_ex(unsigned hnode) { return hnode * 0x4CF5AD43u; }
+__device__ __forceinline__ unsigned dither_word_ey(unsigned hnode) { return hnode * 0x2545F491u; }
+__device__ __forceinline__ unsigned dither_word_ez(unsigned hnode) { return hnode * 0x6A09E667u; }
+__device__ __forceinline__ float dither_unit2(unsigned r) { return (float)(int)r * 0x1p-54f; }
 template <class U>
 __device__ __forceinline__ U dither_pick(int ix, U a, U b, U na, U nb)
 {
@@ -173,6 +104,153 @@ __device__ __forceinline__ U dither_pick(int ix, U a, U b, U na, U nb)
     case 2: return na;
     default: return nb;
     }
+}
+
+// Deviation of the level-N equilibrium from the rest weights, for one |n|:
+// Ae_n(v) (even powers >= 2) and Bo_n(v) (odd powers / u), v = u^2, so that
+// E_{+n}(u) - W_n = Ae + u Bo and E_{-n}(u) - W_n = Ae - u Bo. On the 2N+2
+// hierarchy (Z = 1) n is the magnitude index m of the velocities +-(2m+1).
+// FP32 keeps Bo in two parts, bo + b0 with b0 the constant (linear)
+// coefficient's high part: eq_pm adds u b0 inside the final fused rounding,
+// so each value E_{+-n} - W_n is rounded once (a rounded Bo would give a
+// fixed relative error of the momentum at each u). FP64: bo = Bo, b0 = 0.
+template <int N, typename T, int Z = 0, class Tab>
+__device__ __forceinline__ void eq_parts(const Tab &t, int n, T v, T &ae, T &bo, T &b0)
+{
+    using A = TabAcc<T>;
+    T a = A::Ce(t, n, N);
+#pragma unroll
+    for (int i = N - 1; i >= 1; --i) a = fma(a, v, A::Ce(t, n, i));
+    ae = mul_rn(a, v);
+    b0 = T(0);
+    if (n == 0 && !Z) {
+        bo = T(0);  // E_0 is even in u
+    } else if (A::HILO) {
+        // linear coefficient as hi + lo: the low part joins the higher powers
+        T b = A::Co(t, n, N - 1);
+        if (N >= 2) {
+#pragma unroll
+            for (int i = N - 2; i >= 1; --i) b = fma(b, v, A::Co(t, n, i));
+            b = fma(b, v, A::C1lo(t, n));
+        } else {
+            b = A::C1lo(t, n);
+        }
+        bo = b;
+        b0 = A::Co(t, n, 0);
+    } else {
+        T b = A::Co(t, n, N - 1);
+#pragma unroll
+        for (int i = N - 2; i >= 0; --i) b = fma(b, v, A::Co(t, n, i));
+        bo = b;
+    }
+}
+
+// E_{+n}(u) - W_n and E_{-n}(u) - W_n from the parts of eq_parts.
+template <typename T>
+__device__ __forceinline__ void eq_pm(T u, T ae, T bo, T b0, T &plus, T &minus)
+{
+    if (TabAcc<T>::HILO) {
+        plus = fma(u, b0, fma(u, bo, ae));
+        minus = fma(-u, b0, fma(-u, bo, ae));
+    } else {
+        plus = fma(u, bo, ae);
+        minus = fma(-u, bo, ae);
+    }
+}
+
+// FP32 E_{+n}(u) - W_n and E_{-n}(u) - W_n (or E_{+-(2m+1)} on the 2N+2
+// hierarchy, n = m) with a stochastic final rounding. Each value is
+// a v + (+-u bo) + (+-u b0) with a the even Horner value (Ae = a v) and bo,
+// b0 the odd parts of eq_parts; it is rounded once, after a dither that spans
+// two ulps of |a v| + |u b0| (a bound of both values up to one binade, so the
+// dither covers a power-of-two number of their ulps and the rounding is
+// zero-mean). r is a draw in [-2^-23, 2^-23) shared by every n of the axis,
+// taken with opposite signs for +n and -n. Deterministic roundings of E - W
+// would repeat at every step of a steady flow and act as fixed sources of
+// mass and momentum; with the dither they are noise. single: the zero velocity
+// of a 2N+1 axis (plus = minus = Ae).
+template <int N, int Z = 0, class Tab>
+__device__ __forceinline__ void eq_pm_sr(const Tab &t, int n, float u, float v, float r,
+                                         float &plus, float &minus)
+{
+    using A = TabAcc<float>;
+    float a = A::Ce(t, n, N);
+#pragma unroll
+    for (int i = N - 1; i >= 1; --i) a = fmaf(a, v, A::Ce(t, n, i));
+    const float av = a * v;
+    if (n == 0 && !Z) {  // E_0 is even in u
+        plus = minus = fmaf(a, v, dither_ulp(av, r));
+        return;
+    }
+    float b = A::Co(t, n, N - 1);  // odd part without the linear coefficient's high part
+    if (N >= 2) {
+#pragma unroll
+        for (int i = N - 2; i >= 1; --i) b = fmaf(b, v, A::Co(t, n, i));
+        b = fmaf(b, v, A::C1lo(t, n));
+    } else {
+        b = A::C1lo(t, n);
+    }
+    const float b0 = A::Co(t, n, 0);
+    const float del = dither_ulp(fabsf(av) + fabsf(u * b0), r);
+    const float sd = fmaf(u, b, del);
+    plus = fmaf(u, b0, fmaf(a, v, sd));
+    minus = fmaf(-u, b0, fmaf(a, v, -sd));
+}
+
+// d[i] = E_i(u) - W_i of every velocity index of the axis in FP32, rounded
+// stochastically (eq_pm_sr) with the axis draw r.
+template <int N, int Z = 0, class Tab>
+__device__ __forceinline__ void eq_dev_all_sr(const Tab &t, float u, float r,
+                                              float (&d)[2 * N + 1 + Z])
+{
+    using AV = AxisVel<N, Z>;
+    const float v = u * u;
+#pragma unroll
+    for (int n = 0; n <= N; ++n) {
+        float dp, dm;
+        eq_pm_sr<N, Z>(t, n, u, v, r, dp, dm);
+        if (n == 0 && !Z) {
+            d[N] = dp;
+        } else {
+            d[AV::ipos(n)] = dp;
+            d[AV::ineg(n)] = dm;
+        }
+    }
+}
+
+// d[i] = E_i(u) - W_i for every velocity index i of the axis (i = n + N on
+// the 2N+1 hierarchy).
+template <int N, typename T, int Z = 0, class Tab>
+__device__ __forceinline__ void eq_dev_all(const Tab &t, T u, T (&d)[2 * N + 1 + Z])
+{
+    using AV = AxisVel<N, Z>;
+    const T v = u * u;
+#pragma unroll
+    for (int n = 0; n <= N; ++n) {
+        T ae, bo, b0;
+        eq_parts<N, T, Z>(t, n, v, ae, bo, b0);
+        if (n == 0 && !Z) {
+            d[N] = ae;
+        } else {
+            eq_pm(u, ae, bo, b0, d[AV::ipos(n)], d[AV::ineg(n)]);
+        }
+    }
+}
+
+// Knuth's two-sum: s + x is added to (s, c) with the rounding error of the
+// addition carried in c (compensated summation of the FP32 moments).
+__device__ __forceinline__ void acc2(float &s, float &c, float x)
+{
+    const float t = s + x;
+    const float bp = t - s;
+    const float err = (s - (t - bp)) + (x - bp);
+    s = t;
+    c += err;
+}
+__device__ __forceinline__ void acc2(double &s, double &c, double x)
+{
+    (void)c;
+    s += x;
 }
 
 __device__ __forceinline__ int wrap_index(int i, int L)

@@ -194,8 +194,9 @@ struct Step2D {
                     for (int ix = 0; ix < QX; ++ix) {
                         if (DEV) {
                             const T dw = lo ? (T)ip.dw_lo_f[ix] : (T)ip.dw_hi_f[ix];
-                            // W^y (drho_w W^x + rho_w (E^x(u_w) - W^x))
-                            f[k][ix] = mul_rn(wy, fma(rw, A::W(tabx, ix), (T(1) + rw) * dw));
+                            // W^y (drho_w W^x + (E^x(u_w) - W^x) + drho_w (E^x(u_w) - W^x)):
+                            // no rounded 1 + drho_w scales the emitted momentum
+                            f[k][ix] = mul_rn(wy, fma(rw, A::W(tabx, ix), fma(rw, dw, dw)));
                         } else {
                             const T ew = lo ? (T)ip.ew_lo[ix] : (T)ip.ew_hi[ix];
                             f[k][ix] = mul_rn(rw * ew, wy);
@@ -239,8 +240,24 @@ struct Step2D {
         const T rho = DEV ? T(1) + m0 : m0;
         const T drho = DEV ? m0 : m0 - T(1);
         const T inv_rho = T(1) / rho;
-        const T ux = (S_x + C_x) * inv_rho;
-        const T uy = (S_y + C_y) * inv_rho;
+        const T jx = S_x + C_x, jy = S_y + C_y;
+        T ux = jx * inv_rho, uy = jy * inv_rho;
+        // random word of this node and launch for the dithered FP32 roundings
+        const unsigned hnode = DEV ? hash32((unsigned)(y * Lx + x) ^ seed) : 0u;
+        if constexpr (DEV) {
+            // u = j / (1 + delta rho) from the unrounded density, rounded
+            // stochastically: one correction by the residual (j - u) - u delta rho
+            // (S - u is exact) plus a dither of half an ulp of u, so that the
+            // rounding error of u (and of the equilibrium's momentum rho u) is
+            // zero-mean instead of repeating at every step of a steady flow. j
+            // times the rounded reciprocal alone misses by up to 2^-24 of u, with
+            // a fixed sign where rho lies just below 1.
+            const T dux = dither_ulp(ux, dither_unit(dither_word_ux(hnode)));
+            const T duy = dither_ulp(uy, dither_unit(dither_word_uy(hnode)));
+            // (the residual takes the compensated sum S + C unrounded)
+            ux = fma(fma(-ux, drho, (S_x - ux) + C_x) + dux, inv_rho, ux);
+            uy = fma(fma(-uy, drho, (S_y - uy) + C_y) + duy, inv_rho, uy);
+        }
         if (active) {
             // sqrt(2/3) N per axis: positivity bound (Sec. 3), twice that in
             // the half-spacing units of a 2N+2 axis
@@ -251,9 +268,18 @@ struct Step2D {
 
         T dx[QX];
         T dyall[G == 1 ? Q1 : 1];  // one warp group: E^y - W for every row at once
+        // FP32: the polynomial values are rounded stochastically, one draw per
+        // node and axis (eq_pm_sr)
+        const float rex = DEV ? dither_unit2(dither_word_ex(hnode)) : 0.0f;
+        const float rey_ = DEV ? dither_unit2(dither_word_ey(hnode)) : 0.0f;
         if constexpr (G == 1) {
-            eq_dev_all<NXL, T, ZX>(tabx, ux, dx);
-            eq_dev_all<N, T, ZY>(tab, uy, dyall);
+            if constexpr (DEV) {
+                eq_dev_all_sr<NXL, ZX>(tabx, ux, rex, dx);
+                eq_dev_all_sr<N, ZY>(tab, uy, rey_, dyall);
+            } else {
+                eq_dev_all<NXL, T, ZX>(tabx, ux, dx);
+                eq_dev_all<N, T, ZY>(tab, uy, dyall);
+            }
         } else {
             // the G warp groups of a node row share the polynomial work: group g
             // evaluates E^x - W and E^y - W for |n| = g, g + G, ..., and the
@@ -262,18 +288,30 @@ struct Step2D {
 #pragma unroll
             for (int n = 0; n <= (N > NXL ? N : NXL); ++n) {
                 if (n % G != g) continue;
-                T ae, bo;
+                T ae, bo, b0, dp, dm;
                 if (n <= NXL) {
-                    eq_parts<NXL, T, ZX>(tabx, n, vx, ae, bo);
                     const bool single = n == 0 && !ZX;  // the zero velocity
-                    sm.eqx[r][AX::ipos(n)][lane] = single ? ae : fma(ux, bo, ae);
-                    if (!single) sm.eqx[r][AX::ineg(n)][lane] = fma(-ux, bo, ae);
+                    if constexpr (DEV) {
+                        eq_pm_sr<NXL, ZX>(tabx, n, ux, vx, rex, dp, dm);
+                    } else {
+                        eq_parts<NXL, T, ZX>(tabx, n, vx, ae, bo, b0);
+                        eq_pm(ux, ae, bo, b0, dp, dm);
+                        if (single) dp = ae;
+                    }
+                    sm.eqx[r][AX::ipos(n)][lane] = dp;
+                    if (!single) sm.eqx[r][AX::ineg(n)][lane] = dm;
                 }
                 if (n <= N) {
-                    eq_parts<N, T, ZY>(tab, n, vy, ae, bo);
                     const bool single = n == 0 && !ZY;
-                    sm.eqy[r][AY::ipos(n)][lane] = single ? ae : fma(uy, bo, ae);
-                    if (!single) sm.eqy[r][AY::ineg(n)][lane] = fma(-uy, bo, ae);
+                    if constexpr (DEV) {
+                        eq_pm_sr<N, ZY>(tab, n, uy, vy, rey_, dp, dm);
+                    } else {
+                        eq_parts<N, T, ZY>(tab, n, vy, ae, bo, b0);
+                        eq_pm(uy, ae, bo, b0, dp, dm);
+                        if (single) dp = ae;
+                    }
+                    sm.eqy[r][AY::ipos(n)][lane] = dp;
+                    if (!single) sm.eqy[r][AY::ineg(n)][lane] = dm;
                 }
             }
             __syncthreads();
@@ -288,8 +326,8 @@ struct Step2D {
         const T om = DEV ? (T)ip.omega_f : (T)ip.omega;
         const T gto = DEV ? (T)ip.g_theta_om_f : (T)ip.g_theta_om;  // g / (theta omega)
         T *const obase = fout + (y * pitch + x);
-        // random word of this node and launch for the dithered FP32 stores
-        const unsigned hnode = DEV ? hash32((unsigned)(y * Lx + x) ^ seed) : 0u;
+        // the store's dither enters the equilibrium divided by omega (below)
+        const float iom = DEV ? 1.0f / ip.omega_f : 0.0f;
 
         // f* = f + omega (f^eq + F/omega - f): the relaxation is written as a
         // correction to f (no rounded (1 - omega) factor biases mass or momentum)
@@ -307,14 +345,16 @@ struct Step2D {
                     dy = sm.eqy[r][iy][lane];
                 const T rey = rho * (wy + dy);  // rho e^y
                 const T gr = mul_rn(gto, wy);
-                // FP32: delta f^eq = d^x rho e^y + W^x (drho W^y + rho d^y)
-                const T B = DEV ? fma(drho, wy, rho * dy) : T(0);
+                // FP32: delta f^eq = d^x W^y + E^x B with B = rho e^y - W^y =
+                // drho W^y + d^y + drho d^y: the y momentum's carrier d^y is not
+                // scaled by a rounded rho
+                const T B = DEV ? fma(drho, wy, fma(drho, dy, dy)) : T(0);
                 T *const op = obase + iy * QX * plane;
                 // random word of this row: node word plus a multiple of the row;
-                // the row's two dither draws
+                // the row's two dither draws, divided by omega
                 const unsigned hrow = hnode + (unsigned)iy * 0x85EBCA6Bu;
-                const float ua = DEV ? dither_unit(hrow) : 0.0f;
-                const float ub = DEV ? dither_unit(dither_word_b(hrow)) : 0.0f;
+                const float ua = DEV ? mul_rn(dither_unit(hrow), iom) : 0.0f;
+                const float ub = DEV ? mul_rn(dither_unit(dither_word_b(hrow)), iom) : 0.0f;
 #pragma unroll
                 for (int ix = 0; ix < QX; ++ix) {
                     const int nx = AX::vel(ix);
@@ -324,11 +364,18 @@ struct Step2D {
                         const T Bn = nx != 0 ? fma(T(nx), gr, B) : B;
                         // split FP32 tiles read E^x - W where it is used (fewer registers)
                         const T dxv = DX_SHARED ? sm.eqx[r][ix][lane] : dx[ix];
-                        const T eq = fma(dxv, rey, A::W(tabx, ix) * Bn);
-                        // increment plus dither, then one rounding of the store
+                        // delta f^eq = d^x W^y + E^x B + F/omega: the momentum-
+                        // carrying d^x meets only the float weight W^y (whose row
+                        // sum is exactly 1), in the final fused rounding; a rounded
+                        // rho e^y there would scale the momentum by a fixed
+                        // 1 + O(2^-24) at every step of a steady flow. The dither
+                        // (half an ulp of f0, over omega) joins at the innermost
+                        // product, so the rounding of f^eq and the one rounding of
+                        // the store f0 + omega (f^eq - f0) are both zero-mean.
                         const float u = dither_pick(ix, ua, ub, -ua, -ub);
-                        const T inc = fma(om, eq - f0, (T)dither_ulp((float)f0, u));
-                        v = f0 + inc;
+                        const T dith = (T)dither_ulp((float)f0, u);
+                        const T eq = fma(dxv, wy, fma(dxv, B, fma(A::W(tabx, ix), Bn, dith)));
+                        v = fma(om, eq - f0, f0);
                     } else {
                         T eq = ex[ix] * rey;
                         if (nx != 0) eq = fma(A::WN(tabx, ix), gr, eq);

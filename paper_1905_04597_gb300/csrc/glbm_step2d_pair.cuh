@@ -189,13 +189,15 @@ __device__ __forceinline__ void pair_wall_row(const TY &tab, const TX &tabx,
     for (int ix = 0; ix < 2 * N + 1 + ZX; ++ix) {
         const float dw = lo ? ip.dw_lo_f[ix] : ip.dw_hi_f[ix];
         const float wx = A::W(tabx, ix);
-        f[ix] = pk2(wy * fmaf(rw0, wx, (1.f + rw0) * dw), wy * fmaf(rw1, wx, (1.f + rw1) * dw));
+        // no rounded 1 + drho_w scales the emitted momentum (as in the one-node tile)
+        f[ix] = pk2(mul_rn(wy, fmaf(rw0, wx, fmaf(rw0, dw, dw))),
+                    mul_rn(wy, fmaf(rw1, wx, fmaf(rw1, dw, dw))));
     }
 }
 
 // Relaxation plus force and the dithered FP32 store of velocity row iy of a
 // node pair: f* = f + omega (f^eq + F/omega - f) with
-// delta f^eq = d^x rho e^y + W^x (drho W^y + rho d^y), the force through the
+// delta f^eq = d^x W^y + E^x B, B = drho W^y + d^y + drho d^y, the force through the
 // row factor gr = W^y g / (theta omega), and a dither of half an ulp from the
 // two draws of each node's row word (h0, h1 and the row), taken in turn with
 // alternating signs along the row. E^x - W comes from the
@@ -203,7 +205,7 @@ __device__ __forceinline__ void pair_wall_row(const TY &tab, const TX &tabx,
 // N and tabx: the x axis.
 template <int N, bool DXS, int ZX, class TX>
 __device__ __forceinline__ void pair_collide_row(const TX &tabx, int iy, float wy, f32x2 dy,
-                                                 f32x2 rho, f32x2 drho, f32x2 om, float gto,
+                                                 f32x2 drho, f32x2 om, float iom, float gto,
                                                  const f32x2 (&f)[2 * N + 1 + ZX],
                                                  const f32x2 (&dxr)[2 * N + 1 + ZX], const f32x2 *dxs,
                                                  float *op, int plane, unsigned h0, unsigned h1,
@@ -211,15 +213,15 @@ __device__ __forceinline__ void pair_collide_row(const TX &tabx, int iy, float w
 {
     using A = TabAcc<float>;
     const f32x2 wy2 = pk2(wy, wy);
-    const f32x2 rey = mul2(rho, add2(wy2, dy));  // rho e^y
     const float grs = mul_rn(gto, wy);
     const f32x2 gr = pk2(grs, grs);
-    const f32x2 B = fma2(drho, wy2, mul2(rho, dy));
+    const f32x2 B = fma2(drho, wy2, fma2(drho, dy, dy));  // rho e^y - W^y
     const unsigned hr0 = h0 + (unsigned)iy * 0x85EBCA6Bu;  // row words
     const unsigned hr1 = h1 + (unsigned)iy * 0x85EBCA6Bu;
-    // the row's two dither draws of each node and their negatives
-    const float a0 = dither_unit(hr0), a1 = dither_unit(hr1);
-    const float b0 = dither_unit(dither_word_b(hr0)), b1 = dither_unit(dither_word_b(hr1));
+    // the row's two dither draws of each node (divided by omega) and their negatives
+    const float a0 = mul_rn(dither_unit(hr0), iom), a1 = mul_rn(dither_unit(hr1), iom);
+    const float b0 = mul_rn(dither_unit(dither_word_b(hr0)), iom);
+    const float b1 = mul_rn(dither_unit(dither_word_b(hr1)), iom);
     const f32x2 ua = pk2(a0, a1), ub = pk2(b0, b1), na = pk2(-a0, -a1), nb = pk2(-b0, -b1);
 #pragma unroll
     for (int ix = 0; ix < 2 * N + 1 + ZX; ++ix) {
@@ -228,13 +230,14 @@ __device__ __forceinline__ void pair_collide_row(const TX &tabx, int iy, float w
         const f32x2 Bn = nx != 0 ? fma2(pk2((float)nx, (float)nx), gr, B) : B;
         const float wx = A::W(tabx, ix);
         const f32x2 dxv = DXS ? dxs[ix * 32] : dxr[ix];
-        const f32x2 eq = fma2(dxv, rey, mul2(pk2(wx, wx), Bn));
-        // increment plus dither, then one rounding of the store
+        // the dither (half an ulp of f0, over omega) joins at the innermost
+        // product and d^x meets only the float weight W^y, in the final fused
+        // rounding (the one-node tile's order); one rounding of the store
         const float p0 = __int_as_float(__float_as_int(lo2(f0)) & 0x7F800000);
         const float p1 = __int_as_float(__float_as_int(hi2(f0)) & 0x7F800000);
         const f32x2 dith = mul2(dither_pick(ix, ua, ub, na, nb), pk2(p0, p1));
-        const f32x2 inc = fma2(om, sub2(eq, f0), dith);
-        const f32x2 v = add2(f0, inc);
+        const f32x2 eq = fma2(dxv, wy2, fma2(dxv, B, fma2(pk2(wx, wx), Bn, dith)));
+        const f32x2 v = fma2(om, sub2(eq, f0), f0);
         float *const o = op + ix * plane;
         if (act0 && act1) {
             *reinterpret_cast<f32x2 *>(o) = v;
@@ -382,8 +385,22 @@ struct Step2DPair {
         const f32x2 drho = add2(S_r, C_r);  // delta rho of both nodes
         const f32x2 rho = add2(pk2(1.f, 1.f), drho);
         const f32x2 inv_rho = pk2(1.f / lo2(rho), 1.f / hi2(rho));
-        const f32x2 ux = mul2(add2(S_x, C_x), inv_rho);
-        const f32x2 uy = mul2(add2(S_y, C_y), inv_rho);
+        const f32x2 jx = add2(S_x, C_x), jy = add2(S_y, C_y);
+        f32x2 ux = mul2(jx, inv_rho), uy = mul2(jy, inv_rho);
+        // random words of the two nodes and this launch (dithered roundings)
+        const unsigned h0 = hash32((unsigned)(y * Lx + x) ^ seed);
+        const unsigned h1 = hash32((unsigned)(y * Lx + x + 1) ^ seed);
+        {
+            // u = j / (1 + delta rho), rounded stochastically (the one-node
+            // tile's correction and dither, lane by lane)
+            constexpr f32x2 SIGN2 = 0x8000000080000000ull;
+            const f32x2 dux = pk2(dither_ulp(lo2(ux), dither_unit(dither_word_ux(h0))),
+                                  dither_ulp(hi2(ux), dither_unit(dither_word_ux(h1))));
+            const f32x2 duy = pk2(dither_ulp(lo2(uy), dither_unit(dither_word_uy(h0))),
+                                  dither_ulp(hi2(uy), dither_unit(dither_word_uy(h1))));
+            ux = fma2(add2(fma2(ux ^ SIGN2, drho, add2(sub2(S_x, ux), C_x)), dux), inv_rho, ux);
+            uy = fma2(add2(fma2(uy ^ SIGN2, drho, add2(sub2(S_y, uy), C_y)), duy), inv_rho, uy);
+        }
         {
             // sqrt(2/3) N per axis (Sec. 3), twice that on a 2N+2 axis
             const float umax = (float)(0.816496580927726 * (ZY ? 2 * N : N));
@@ -398,19 +415,23 @@ struct Step2DPair {
         // E^x - W and E^y - W for both nodes
         f32x2 dx[QX];
         float dy0all[G == 1 ? Q1 : 1], dy1all[G == 1 ? Q1 : 1];
+        // polynomial values rounded stochastically: one draw per node and axis
+        const float rx0 = dither_unit2(dither_word_ex(h0)), rx1 = dither_unit2(dither_word_ex(h1));
+        const float ry0 = dither_unit2(dither_word_ey(h0)), ry1 = dither_unit2(dither_word_ey(h1));
         if constexpr (G == 1) {
             float d0[QX], d1[QX];
-            eq_dev_all<NXL, float, ZX>(tabx, lo2(ux), d0);
-            eq_dev_all<NXL, float, ZX>(tabx, hi2(ux), d1);
+            eq_dev_all_sr<NXL, ZX>(tabx, lo2(ux), rx0, d0);
+            eq_dev_all_sr<NXL, ZX>(tabx, hi2(ux), rx1, d1);
 #pragma unroll
             for (int ix = 0; ix < QX; ++ix) dx[ix] = pk2(d0[ix], d1[ix]);
-            eq_dev_all<N, float, ZY>(tab, lo2(uy), dy0all);
-            eq_dev_all<N, float, ZY>(tab, hi2(uy), dy1all);
+            eq_dev_all_sr<N, ZY>(tab, lo2(uy), ry0, dy0all);
+            eq_dev_all_sr<N, ZY>(tab, hi2(uy), ry1, dy1all);
         } else {
             // the G warp groups share the polynomial work: group g evaluates
             // |n| = g, g + G, ... for both nodes and both axes, and the values
             // meet in shared memory
             const float u[4] = {lo2(ux), hi2(ux), lo2(uy), hi2(uy)};
+            const float rr[4] = {rx0, rx1, ry0, ry1};
 #pragma unroll
             for (int n = 0; n <= (N > NXL ? N : NXL); ++n) {
                 if (n % G != g) continue;
@@ -418,14 +439,10 @@ struct Step2DPair {
 #pragma unroll
                 for (int c = 0; c < 4; ++c) {
                     if (c < 2 ? n > NXL : n > N) continue;  // x nodes: level NXL; y: N
-                    float ae, bo;
                     if (c < 2)
-                        eq_parts<NXL, float, ZX>(tabx, n, u[c] * u[c], ae, bo);
+                        eq_pm_sr<NXL, ZX>(tabx, n, u[c], u[c] * u[c], rr[c], plus[c], minus[c]);
                     else
-                        eq_parts<N, float, ZY>(tab, n, u[c] * u[c], ae, bo);
-                    const bool single = n == 0 && (c < 2 ? !ZX : !ZY);  // the zero velocity
-                    plus[c] = single ? ae : fmaf(u[c], bo, ae);
-                    minus[c] = single ? ae : fmaf(-u[c], bo, ae);
+                        eq_pm_sr<N, ZY>(tab, n, u[c], u[c] * u[c], rr[c], plus[c], minus[c]);
                 }
                 if (n <= NXL) {
                     *reinterpret_cast<f32x2 *>(&sm.eqx[r][AX::ipos(n)][2 * lane]) =
@@ -445,11 +462,9 @@ struct Step2DPair {
             __syncthreads();  // E^x - W is read from shared memory where it is used
         }
         const f32x2 om = pk2(ip.omega_f, ip.omega_f);
+        const float iom = 1.0f / ip.omega_f;
         const float gto = ip.g_theta_om_f;  // g / (theta omega)
         float *const obase = fout + (y * pitch + x);
-        // random words of the two nodes and this launch (dithered stores)
-        const unsigned h0 = hash32((unsigned)(y * Lx + x) ^ seed);
-        const unsigned h1 = hash32((unsigned)(y * Lx + x + 1) ^ seed);
 
 #pragma unroll
         for (int k = 0; k < RPG; ++k) {
@@ -462,7 +477,7 @@ struct Step2DPair {
                 else
                     dy = *reinterpret_cast<const f32x2 *>(&sm.eqy[r][iy][2 * lane]);
                 const f32x2 *dxs = reinterpret_cast<const f32x2 *>(&sm.eqx[G > 1 ? r : 0][0][2 * lane]);
-                pair_collide_row<NXL, (G > 1), ZX>(tabx, iy, wy, dy, rho, drho, om, gto, f[k], dx, dxs,
+                pair_collide_row<NXL, (G > 1), ZX>(tabx, iy, wy, dy, drho, om, iom, gto, f[k], dx, dxs,
                                                obase + iy * QX * plane, plane, h0, h1, act0, act1);
             }
         }

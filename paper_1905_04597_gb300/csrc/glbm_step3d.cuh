@@ -142,7 +142,8 @@ struct Step3D {
                     for (int ix = 0; ix < Q1; ++ix) {
                         if (DEV) {
                             const T dw = lo ? (T)ip.dw_lo_f[ix] : (T)ip.dw_hi_f[ix];
-                            f[k][ix] = mul_rn(wyz, fma(rw, A::W(tab, ix), (T(1) + rw) * dw));
+                            // no rounded 1 + drho_w scales the emitted momentum
+                            f[k][ix] = mul_rn(wyz, fma(rw, A::W(tab, ix), fma(rw, dw, dw)));
                         } else {
                             const T ew = lo ? (T)ip.ew_lo[ix] : (T)ip.ew_hi[ix];
                             f[k][ix] = mul_rn(rw * ew, wyz);
@@ -195,18 +196,36 @@ struct Step3D {
         const T rho = DEV ? T(1) + m0 : m0;
         const T drho = DEV ? m0 : m0 - T(1);
         const T inv_rho = T(1) / rho;
-        const T ux = (S_x + C_x) * inv_rho;
-        const T uy = (S_y + C_y) * inv_rho;
-        const T uz = (S_z + C_z) * inv_rho;
+        const T jx = S_x + C_x, jy = S_y + C_y, jz = S_z + C_z;
+        T ux = jx * inv_rho, uy = jy * inv_rho, uz = jz * inv_rho;
+        const unsigned hnode = DEV ? hash32((unsigned)((z * Ly + y) * Lx + x) ^ seed) : 0u;
+        if constexpr (DEV) {
+            // u = j / (1 + delta rho), rounded stochastically (as in the 2D tile):
+            // j times the rounded reciprocal alone carries a fixed relative bias
+            // of up to 2^-24 where rho lies just below 1
+            const T dux = dither_ulp(ux, dither_unit(dither_word_ux(hnode)));
+            const T duy = dither_ulp(uy, dither_unit(dither_word_uy(hnode)));
+            const T duz = dither_ulp(uz, dither_unit(dither_word_uz(hnode)));
+            ux = fma(fma(-ux, drho, (S_x - ux) + C_x) + dux, inv_rho, ux);
+            uy = fma(fma(-uy, drho, (S_y - uy) + C_y) + duy, inv_rho, uy);
+            uz = fma(fma(-uz, drho, (S_z - uz) + C_z) + duz, inv_rho, uz);
+        }
         if (active) {
             const T umax = (T)(0.816496580927726 * N);  // sqrt(2/3) N (Sec. 3)
             if (!(rho > T(0)) || !(fabs(ux) <= umax) || !(fabs(uy) <= umax) || !(fabs(uz) <= umax))
                 atomicOr(status, 1u);
         }
         T dx[Q1], dy[Q1], dz[Q1];
-        eq_dev_all<N, T>(tab, ux, dx);
-        eq_dev_all<N, T>(tab, uy, dy);
-        eq_dev_all<N, T>(tab, uz, dz);
+        if constexpr (DEV) {
+            // polynomial values rounded stochastically, one draw per node and axis
+            eq_dev_all_sr<N>(tab, ux, dither_unit2(dither_word_ex(hnode)), dx);
+            eq_dev_all_sr<N>(tab, uy, dither_unit2(dither_word_ey(hnode)), dy);
+            eq_dev_all_sr<N>(tab, uz, dither_unit2(dither_word_ez(hnode)), dz);
+        } else {
+            eq_dev_all<N, T>(tab, ux, dx);
+            eq_dev_all<N, T>(tab, uy, dy);
+            eq_dev_all<N, T>(tab, uz, dz);
+        }
 
         // ZROW: this thread's n_y deviation, selected once
         T dy_g = dy[0];
@@ -218,7 +237,7 @@ struct Step3D {
         const T om = DEV ? (T)ip.omega_f : (T)ip.omega;
         const T gto = DEV ? (T)ip.g_theta_om_f : (T)ip.g_theta_om;  // g / (theta omega)
         T *const obase = fout + (z * slab + y * pitch + x);
-        const unsigned hnode = DEV ? hash32((unsigned)((z * Ly + y) * Lx + x) ^ seed) : 0u;
+        const float iom = DEV ? 1.0f / ip.omega_f : 0.0f;  // the dither enters f^eq over omega
 #pragma unroll
         for (int k = 0; k < RPG; ++k) {
             const int row = g + k * G;
@@ -243,12 +262,16 @@ struct Step3D {
                 const T rez_y = rez * (wy + dyv);     // rho e^y e^z
                 const T wyz = mul_rn(wy, wz);
                 const T gr = mul_rn(gto, wyz);        // W^y W^z g / (theta omega)
-                // FP32: rho e^y e^z - W^y W^z
-                const T B = DEV ? fma(dyv, rez, wy * fma(drho, wz, rho * dzv)) : T(0);
+                // FP32: B = rho e^y e^z - W^y W^z = d^y W^z + (W^y + d^y) Bz with
+                // Bz = rho e^z - W^z = drho W^z + d^z + drho d^z: no momentum
+                // carrier (d^y, d^z) is scaled by a rounded rho or e^y
+                const T Bz = DEV ? fma(drho, wz, fma(drho, dzv, dzv)) : T(0);
+                const T B = DEV ? fma(dyv, wz, fma(dyv, Bz, mul_rn(wy, Bz))) : T(0);
                 T *const op = obase + row * Q1 * plane;
                 const unsigned hrow = hnode + (unsigned)row * 0x85EBCA6Bu;
-                const float ua = DEV ? dither_unit(hrow) : 0.0f;  // the row's dither draws
-                const float ub = DEV ? dither_unit(dither_word_b(hrow)) : 0.0f;
+                // the row's dither draws, divided by omega
+                const float ua = DEV ? mul_rn(dither_unit(hrow), iom) : 0.0f;
+                const float ub = DEV ? mul_rn(dither_unit(dither_word_b(hrow)), iom) : 0.0f;
 #pragma unroll
                 for (int ix = 0; ix < Q1; ++ix) {
                     const int nx = ix - N;
@@ -256,10 +279,18 @@ struct Step3D {
                     T v;
                     if (DEV) {
                         const T Bn = nx != 0 ? fma(T(nx), gr, B) : B;
-                        const T eq = fma(dx[ix], rez_y, A::W(tab, ix) * Bn);
+                        // delta f^eq = d^x W^y W^z + E^x B + F/omega: the
+                        // momentum-carrying d^x is rounded with W^y, then meets W^z
+                        // in the final fused rounding (no rounded rho or W^y W^z
+                        // factor, whose fixed error would scale the momentum at
+                        // every step); the dither (half an ulp of f0, over omega)
+                        // joins at the innermost product, and the store
+                        // f0 + omega (f^eq - f0) is one rounding (as in 2D)
                         const float u = dither_pick(ix, ua, ub, -ua, -ub);
-                        const T inc = fma(om, eq - f0, (T)dither_ulp((float)f0, u));
-                        v = f0 + inc;
+                        const T dith = (T)dither_ulp((float)f0, u);
+                        const T eq = fma(mul_rn(dx[ix], wy), wz,
+                                         fma(dx[ix], B, fma(A::W(tab, ix), Bn, dith)));
+                        v = fma(om, eq - f0, f0);
                     } else {
                         T eq = (A::W(tab, ix) + dx[ix]) * rez_y;
                         if (nx != 0) eq = fma(A::WN(tab, ix), gr, eq);
