@@ -82,3 +82,16 @@ def rel_errors(got, want, dims=2, F=None, q1x=None, zv=0):
         scale = max(scale, 1e-3 * S.get(n, 0.0))
         out[n] = float(np.abs(got[n] - w[n]).max() / max(scale, 1e-300))
     return out
+
+
+def plain_errors(got, want, dims=2):
+    """Per-field max |got - want| / max |want| (the plain field max-norm, no
+    floor); a field whose reference is zero everywhere reports None unless it
+    is matched exactly (0.0)."""
+    names = FIELDS_3D if dims == 3 else (FIELDS_2D if dims == 2 else FIELDS_1D)
+    out = {}
+    for i, n in enumerate(names):
+        d = float(np.abs(got[n] - want[i]).max())
+        m = float(np.abs(want[i]).max())
+        out[n] = d / m if m > 0 else (0.0 if d == 0 else None)
+    return out
