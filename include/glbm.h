@@ -186,9 +186,20 @@ glbm_status glbm_unpack_columns(glbm_ctx *ctx, int inst, int x0, int ncols, cons
 size_t glbm_elem_size(const glbm_ctx *ctx);
 
 /* Advance every instance by n >= 0 steps (Eq. maineq01 with the boundary
- * rule), asynchronously. Repeated chunks are replayed from a CUDA graph.
- * Returns GLBM_E_UNSTABLE when an earlier, already-finished step flagged a
- * node outside the positivity domain (the flag is read without waiting). */
+ * rule). The steps are enqueued on the context's stream (repeated chunks of
+ * 64 are replayed from a CUDA graph); the call then waits for them and
+ * returns.
+ * Failure: a step in which any node leaves the positivity domain of Sec. 3
+ * (|u| > sqrt(2/3) N per axis, twice that on a 2N+2 axis, or rho <= 0)
+ * completes, and the device then skips every later step of the call: the
+ * state is X_{t0+k} after the k completed steps, glbm_time() returns t0 + k,
+ * and the call returns GLBM_E_UNSTABLE with "k of n steps completed" in
+ * glbm_last_error(). Further glbm_step calls complete no step (k = 0) until a
+ * new state is set (glbm_set_equilibrium, glbm_set_populations, glbm_load).
+ * 1D contexts step their instances one after another, each stopping at its
+ * own failing step; there glbm_time() advances by the fewest steps any
+ * instance completed. GLBM_E_CUDA: a launch failed (the state is then
+ * undefined). */
 glbm_status glbm_step(glbm_ctx *ctx, int64_t n);
 
 /* Wait for the context's stream; GLBM_E_UNSTABLE if any step flagged a node. */
@@ -222,6 +233,38 @@ glbm_status glbm_moments(glbm_ctx *ctx, int inst, unsigned mask, double *out, si
  * instance `inst` (fixed-order block reduction, deterministic). Synchronises. */
 glbm_status glbm_conservation(glbm_ctx *ctx, int inst, double *mass, double *mom_x,
                               double *mom_y);
+
+/*
+ * Channel diagnostics of instance `inst` (2D, or 3D averaged over z) at the
+ * current time, from the moments of S(X) (FP64, lattice units, every sum in a
+ * fixed order on the device, so repeated calls agree bit for bit):
+ *   profile[y] = <u_x>(y) = (1/(nx nz)) sum_{x,z} u_x        (ny values)
+ *   stats[GLBM_CH_FLOW_RATE]  J = sum_y (1/(nx nz)) sum_{x,z} rho u_x, the
+ *       flow rate (momentum per unit width), as in glbm_adjoint_flowrate;
+ *   stats[GLBM_CH_VOLUMETRIC] Q = (1/Kn) sum_y <u_x>(y) / (4 U0 H), the
+ *       volumetric flow of Sec. 5.4 with H = ny, U0 = g H^2 / (8 nu),
+ *       nu = theta_y tau, Kn = sqrt(2/theta_y) nu / H (Eq. kn); NaN if g = 0;
+ *   stats[GLBM_CH_U_LO], stats[GLBM_CH_U_HI] the gas velocity at the wall
+ *       planes y = -1/2 and y = ny - 1/2: <u_x> extrapolated linearly from
+ *       the two nearest rows, (3 <u_x>(0) - <u_x>(1)) / 2 and its mirror;
+ *   stats[GLBM_CH_SLIP_LO] = (u(-1/2) - u_wall_lo) / (u_wall_hi - u_wall_lo),
+ *   stats[GLBM_CH_SLIP_HI] = (u_wall_hi - u(ny-1/2)) / (u_wall_hi - u_wall_lo):
+ *       the Couette slip of Sec. 5.3, u(0)/(2 U_w) in the frame of each wall
+ *       (NaN when the walls have equal speeds).
+ * The four wall entries are NaN without walls. `profile` (ny doubles) and
+ * `stats` (GLBM_CH_COUNT doubles) may each be NULL; both are host or both
+ * device memory (on_device). Synchronises when they are host memory.
+ * GLBM_E_UNSUPPORTED for 1D contexts.
+ */
+#define GLBM_CH_FLOW_RATE 0
+#define GLBM_CH_VOLUMETRIC 1
+#define GLBM_CH_U_LO 2
+#define GLBM_CH_U_HI 3
+#define GLBM_CH_SLIP_LO 4
+#define GLBM_CH_SLIP_HI 5
+#define GLBM_CH_COUNT 6
+glbm_status glbm_channel_diagnostics(glbm_ctx *ctx, int inst, double *profile, double *stats,
+                                     int on_device);
 
 /*
  * Conservation sums without allocation. The paper has no counterpart: this is

@@ -114,11 +114,13 @@ struct glbm_ctx {
     void *buf[2] = {nullptr, nullptr};
     int cur = 0;                 // buffer holding X_t
     InstParams *d_ip = nullptr;
-    unsigned *d_status = nullptr;  // [0] status flags, [1] launch counter, [2] CTAs done
-    unsigned *h_status = nullptr;  // pinned copy, refreshed after every glbm_step
+    unsigned *d_status = nullptr;  // ST_WORDS status words (ST_FLAGS .. ST_HALT, glbm_internal.h)
+    unsigned *h_status = nullptr;  // pinned copy of them, read after every glbm_step
     double *d_mom = nullptr;       // 7 (2D) or 9 (3D) fields of one instance
     double *d_part = nullptr;      // block partials of the conservation sums
     double *d_sums = nullptr;      // 3 sums
+    double *d_diag = nullptr;      // channel diagnostics: row means and scalars
+    size_t diag_len = 0;
     double *d_stage = nullptr;     // staging of host inputs
     size_t stage_len = 0;
     void *d_rw = nullptr;          // wall densities of the current step (k_wall_rho)
@@ -321,6 +323,7 @@ static void destroy_resources(glbm_ctx *c)
     dev_free(c->A, c->d_ip, c->stream);
     dev_free(c->A, c->d_status, c->stream);
     dev_free(c->A, c->d_mom, c->stream);
+    dev_free(c->A, c->d_diag, c->stream);
     dev_free(c->A, c->d_part, c->stream);
     dev_free(c->A, c->d_sums, c->stream);
     dev_free(c->A, c->d_stage, c->stream);
@@ -365,8 +368,17 @@ static cudaError_t set_clock(glbm_ctx *c, int64_t t)
 {
     c->t = t;
     c->clock_word = (unsigned)t;
-    return cudaMemcpyAsync(c->d_status + 1, &c->clock_word, sizeof(unsigned), cudaMemcpyHostToDevice,
+    return cudaMemcpyAsync(c->d_status + ST_CLOCK, &c->clock_word, sizeof(unsigned), cudaMemcpyHostToDevice,
                            c->stream);
+}
+
+// A new state (set_equilibrium, set_populations, load): clear the positivity
+// flags and the halt word, so that stepping resumes.
+static cudaError_t clear_unstable(glbm_ctx *c)
+{
+    cudaError_t e = cudaMemsetAsync(c->d_status + ST_FLAGS, 0, sizeof(unsigned), c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->d_status + ST_HALT, 0, sizeof(unsigned), c->stream);
+    return e;
 }
 
 static glbm_status ensure_stage(glbm_ctx *c, size_t n)
@@ -452,14 +464,15 @@ static glbm_status finish_create(glbm_ctx *c, const glbm_config *cfgs, int n, vo
 
     cudaError_t e = cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking);
     if (e != cudaSuccess) return fail(GLBM_E_CUDA, "stream creation failed: %s", cudaGetErrorString(e));
-    if (cudaHostAlloc((void **)&c->h_status, sizeof(unsigned), cudaHostAllocDefault) != cudaSuccess)
+    if (cudaHostAlloc((void **)&c->h_status, ST_WORDS * sizeof(unsigned), cudaHostAllocDefault) !=
+        cudaSuccess)
         return fail(GLBM_E_NOMEM, "pinned status allocation failed");
-    *c->h_status = 0;
+    memset(c->h_status, 0, ST_WORDS * sizeof(unsigned));
     const int blocks = glbm_field_sum_blocks(max_nodes);
     c->buf[0] = dev_alloc(c->A, bytes_state(c), c->stream);
     c->buf[1] = dev_alloc(c->A, bytes_state(c), c->stream);
     c->d_ip = (InstParams *)dev_alloc(c->A, sizeof(InstParams) * n, c->stream);
-    c->d_status = (unsigned *)dev_alloc(c->A, 4 * sizeof(unsigned), c->stream);
+    c->d_status = (unsigned *)dev_alloc(c->A, ST_WORDS * sizeof(unsigned), c->stream);
     c->d_mom = (double *)dev_alloc(c->A, (c->dims == 3 ? 9 : 7) * (size_t)max_nodes * sizeof(double),
                                    c->stream);
     c->d_part = (double *)dev_alloc(c->A, 3 * (size_t)blocks * sizeof(double), c->stream);
@@ -473,7 +486,7 @@ static glbm_status finish_create(glbm_ctx *c, const glbm_config *cfgs, int n, vo
         return fail(GLBM_E_NOMEM, "device allocation of %.1f MB failed", 2.0 * bytes_state(c) / 1e6);
     CUDA_TRY(cudaMemcpyAsync(c->d_ip, c->h_ip.data(), sizeof(InstParams) * n, cudaMemcpyHostToDevice,
                              c->stream));
-    CUDA_TRY(cudaMemsetAsync(c->d_status, 0, 4 * sizeof(unsigned), c->stream));
+    CUDA_TRY(cudaMemsetAsync(c->d_status, 0, ST_WORDS * sizeof(unsigned), c->stream));
     CUDA_TRY(cudaMemsetAsync(c->buf[0], 0, bytes_state(c), c->stream));
     CUDA_TRY(cudaMemsetAsync(c->buf[1], 0, bytes_state(c), c->stream));
     // rest state X = W everywhere
@@ -685,6 +698,7 @@ static glbm_status set_equilibrium_impl(glbm_ctx *c, int inst, const double *rho
     }
     c->launches += 1;
     CUDA_TRY(set_clock(c, 0));
+    CUDA_TRY(clear_unstable(c));
     if (!on_device) CUDA_TRY(cudaStreamSynchronize(c->stream));  // host buffers reusable on return
     return GLBM_OK;
 }
@@ -720,6 +734,7 @@ extern "C" glbm_status glbm_set_populations(glbm_ctx *c, int inst, const double 
                                          c->stream));
     c->launches += 1;
     CUDA_TRY(set_clock(c, 0));
+    CUDA_TRY(clear_unstable(c));
     if (!on_device) CUDA_TRY(cudaStreamSynchronize(c->stream));
     return GLBM_OK;
 }
@@ -805,8 +820,8 @@ static Step2DArgsT<TY> step_args_t(const glbm_ctx *c, int from)
     a.fout = c->buf[1 - from];
     a.ip = c->d_ip;
     a.status = c->d_status;
-    a.step_ctr = c->d_status + 1;
-    a.done_ctr = c->d_status + 2;
+    a.step_ctr = c->d_status + ST_CLOCK;
+    a.done_ctr = c->d_status + ST_DONE;
     a.rw = c->wall_launch ? c->d_rw : nullptr;
     a.Lx = g.Lx;
     a.Ly = g.Ly;
@@ -828,8 +843,8 @@ static Step3DArgs step3d_args(const glbm_ctx *c, int from)
     a.fout = c->buf[1 - from];
     a.ip = c->d_ip;
     a.status = c->d_status;
-    a.step_ctr = c->d_status + 1;
-    a.done_ctr = c->d_status + 2;
+    a.step_ctr = c->d_status + ST_CLOCK;
+    a.done_ctr = c->d_status + ST_DONE;
     a.Lx = g.Lx;
     a.Ly = g.Ly;
     a.Lz = g.Lz;
@@ -853,8 +868,8 @@ static BatchArgs batch_args(const glbm_ctx *c, int from)
     for (int N = 0; N <= GLBM_MAXN + 1; ++N) b.group[N] = c->group[N];
     for (int N = 0; N <= GLBM_MAXN; ++N) b.shape[N] = c->tile[N];
     b.status = c->d_status;
-    b.step_ctr = c->d_status + 1;
-    b.done_ctr = c->d_status + 2;
+    b.step_ctr = c->d_status + ST_CLOCK;
+    b.done_ctr = c->d_status + ST_DONE;
     return b;
 }
 
@@ -902,67 +917,125 @@ static glbm_status capture_chunk(glbm_ctx *c, int from)
     return GLBM_OK;
 }
 
+// The status words after the work enqueued so far (waits for it).
+static glbm_status read_status(glbm_ctx *c)
+{
+    CUDA_TRY(cudaMemcpyAsync(c->h_status, c->d_status, ST_WORDS * sizeof(unsigned),
+                             cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
+    return GLBM_OK;
+}
+
+// Steps of one 1D instance (all in one resident launch where the lattice fits
+// one CTA's shared memory, else one launch per step); returns the steps
+// completed, which stop after a step that left the positivity domain.
+static glbm_status step_1d_instance(glbm_ctx *c, int i, int64_t n, int64_t *completed)
+{
+    const AuxArgs a = aux_args(c, i);
+    CUDA_TRY(cudaMemsetAsync(c->d_status + ST_STEPS, 0, sizeof(unsigned), c->stream));
+    int ok = 0;
+    CUDA_TRY(glbm_launch_run1d_resident(a, inst_ptr(c, c->cur, i), 0, n, c->d_status, c->stream,
+                                        &ok));
+    int b = c->cur;
+    if (ok) {
+        c->launches += 1;
+    } else {
+        // too large for one CTA: one launch per step through both buffers
+        for (int64_t s = 0; s < n; ++s) {
+            CUDA_TRY(glbm_launch_step1d(a, inst_ptr(c, b, i), inst_ptr(c, 1 - b, i), 0, c->d_status,
+                                        c->stream));
+            b = 1 - b;
+        }
+        c->launches += n;
+    }
+    glbm_status st = read_status(c);
+    if (st != GLBM_OK) return st;
+    *completed = c->h_status[ST_STEPS];
+    if (!ok && (*completed & 1)) {  // the last completed step wrote the other buffer
+        const size_t bytes = (size_t)c->geo[i].Q * c->geo[i].plane * c->elem;
+        CUDA_TRY(cudaMemcpyAsync(inst_ptr(c, c->cur, i), inst_ptr(c, 1 - c->cur, i), bytes,
+                                 cudaMemcpyDeviceToDevice, c->stream));
+    }
+    return GLBM_OK;
+}
+
+// Enqueue n (< 2^31) 2D or 3D steps of every instance; returns the steps
+// completed (each step's last launch counts itself, and once a step has left
+// the positivity domain the launches of later steps do nothing).
+static glbm_status step_nd(glbm_ctx *c, int64_t n, int64_t *completed)
+{
+    const int cur0 = c->cur;
+    CUDA_TRY(cudaMemsetAsync(c->d_status + ST_STEPS, 0, sizeof(unsigned), c->stream));
+    int64_t left = n;
+    while (left >= kGraphChunk) {
+        if (!c->graph[c->cur]) {
+            glbm_status st = capture_chunk(c, c->cur);
+            if (st != GLBM_OK) return st;
+        }
+        CUDA_TRY(cudaGraphLaunch(c->graph[c->cur], c->stream));
+        c->launches += kGraphChunk * launches_per_step(c);
+        left -= kGraphChunk;  // even chunk: c->cur unchanged
+    }
+    for (; left > 0; --left) {
+        CUDA_TRY(launch_one_2d(c, c->cur, c->stream));
+        c->cur = 1 - c->cur;
+        c->launches += launches_per_step(c);
+    }
+    glbm_status st = read_status(c);
+    if (st != GLBM_OK) return st;
+    *completed = c->h_status[ST_STEPS];
+    c->cur = (int)((cur0 + *completed) & 1);  // X_{t + completed} is in this buffer
+    return GLBM_OK;
+}
+
 extern "C" glbm_status glbm_step(glbm_ctx *c, int64_t n)
 {
     if (!c) return fail(GLBM_E_INVAL, "null context");
     if (n < 0) return fail(GLBM_E_INVAL, "negative step count");
-    const unsigned prior = *c->h_status;  // flags of steps already finished
-    if (n == 0) return prior ? fail(GLBM_E_UNSTABLE, "a node left the positivity domain") : GLBM_OK;
+    const int64_t t0 = c->t;
+    int64_t done = 0;  // steps of every instance completed by this call
+    bool bad = false;
     if (c->dims == 1) {
+        // instances one after another; each stops at its own failing step
+        done = n;
         for (int i = 0; i < c->n_inst; ++i) {
-            const AuxArgs a = aux_args(c, i);
-            int ok = 0;
-            CUDA_TRY(glbm_launch_run1d_resident(a, inst_ptr(c, c->cur, i), 0, n, c->d_status,
-                                                c->stream, &ok));
-            if (ok) {
-                c->launches += 1;
-                continue;
-            }
-            // too large for one CTA: one launch per step, ping-pong through both buffers
-            int b = c->cur;
-            for (int64_t s = 0; s < n; ++s) {
-                CUDA_TRY(glbm_launch_step1d(a, inst_ptr(c, b, i), inst_ptr(c, 1 - b, i), 0,
-                                            c->d_status, c->stream));
-                b = 1 - b;
-            }
-            if (b != c->cur) {
-                const size_t bytes = (size_t)c->geo[i].Q * c->geo[i].plane * c->elem;
-                CUDA_TRY(cudaMemcpyAsync(inst_ptr(c, c->cur, i), inst_ptr(c, b, i), bytes,
-                                         cudaMemcpyDeviceToDevice, c->stream));
-            }
-            c->launches += n;
+            int64_t k = 0;
+            glbm_status st = step_1d_instance(c, i, n, &k);
+            if (st != GLBM_OK) return st;
+            if (k < n || (c->h_status[ST_FLAGS] & 1u)) bad = true;
+            done = std::min(done, k);
         }
     } else {
-        int64_t left = n;
-        while (left >= kGraphChunk) {
-            if (!c->graph[c->cur]) {
-                glbm_status st = capture_chunk(c, c->cur);
-                if (st != GLBM_OK) return st;
-            }
-            CUDA_TRY(cudaGraphLaunch(c->graph[c->cur], c->stream));
-            c->launches += kGraphChunk * launches_per_step(c);
-            left -= kGraphChunk;  // even chunk: c->cur unchanged
+        for (int64_t left = n; left > 0 && !bad;) {
+            const int64_t m = std::min<int64_t>(left, (int64_t)1 << 30);
+            int64_t k = 0;
+            glbm_status st = step_nd(c, m, &k);
+            if (st != GLBM_OK) return st;
+            done += k;
+            left -= m;
+            bad = (c->h_status[ST_FLAGS] & 1u) != 0u;
         }
-        for (; left > 0; --left) {
-            CUDA_TRY(launch_one_2d(c, c->cur, c->stream));
-            c->cur = 1 - c->cur;
-            c->launches += launches_per_step(c);
+        if (n == 0) {
+            glbm_status st = read_status(c);
+            if (st != GLBM_OK) return st;
+            bad = (c->h_status[ST_FLAGS] & 1u) != 0u;
         }
     }
-    c->t += n;
-    CUDA_TRY(cudaMemcpyAsync(c->h_status, c->d_status, sizeof(unsigned), cudaMemcpyDeviceToHost,
-                             c->stream));
-    if (prior) return fail(GLBM_E_UNSTABLE, "a node left the positivity domain");
+    c->t = t0 + done;
+    if (bad)
+        return fail(GLBM_E_UNSTABLE,
+                    "a node left the positivity domain (|u| > sqrt(2/3) N per axis, or rho <= 0); "
+                    "%lld of %lld steps completed, the state is that of time %lld",
+                    (long long)done, (long long)n, (long long)c->t);
     return GLBM_OK;
 }
 
 extern "C" glbm_status glbm_sync(glbm_ctx *c)
 {
     if (!c) return fail(GLBM_E_INVAL, "null context");
-    CUDA_TRY(cudaMemcpyAsync(c->h_status, c->d_status, sizeof(unsigned), cudaMemcpyDeviceToHost,
-                             c->stream));
-    CUDA_TRY(cudaStreamSynchronize(c->stream));
-    if (*c->h_status) return fail(GLBM_E_UNSTABLE, "a node left the positivity domain");
+    glbm_status st = read_status(c);
+    if (st != GLBM_OK) return st;
+    if (c->h_status[ST_FLAGS] & 1u) return fail(GLBM_E_UNSTABLE, "a node left the positivity domain");
     return GLBM_OK;
 }
 
@@ -976,6 +1049,43 @@ static glbm_status compute_moments(glbm_ctx *c, int inst)
     else
         CUDA_TRY(glbm_launch_moments(aux_args(c, inst), inst_ptr(c, c->cur, inst), 0, c->d_mom, c->stream));
     c->launches += 1;
+    return GLBM_OK;
+}
+
+extern "C" glbm_status glbm_channel_diagnostics(glbm_ctx *c, int inst, double *profile,
+                                                double *stats, int on_device)
+{
+    glbm_status st = check_inst(c, inst);
+    if (st != GLBM_OK) return st;
+    if (c->dims < 2) return fail(GLBM_E_UNSUPPORTED, "channel diagnostics need a 2D or 3D lattice");
+    const Geo &g = c->geo[inst];
+    const size_t need = 2 * (size_t)g.Ly + GLBM_CH_COUNT;
+    if (c->diag_len < need) {
+        dev_free(c->A, c->d_diag, c->stream);
+        c->d_diag = (double *)dev_alloc(c->A, need * sizeof(double), c->stream);
+        c->diag_len = c->d_diag ? need : 0;
+        if (!c->d_diag) return fail(GLBM_E_NOMEM, "diagnostics buffer of %zu doubles", need);
+    }
+    st = compute_moments(c, inst);
+    if (st != GLBM_OK) return st;
+    const glbm_config &cf = c->cfg[inst];
+    ChannelParams p;
+    p.theta_y = axis_theta(g.N, c->dims == 2 && (g.zv & GLBM_ZV_Y));
+    p.tau = c->tau[inst];
+    p.g = cf.g;
+    p.u_lo = cf.u_wall_lo;
+    p.u_hi = cf.u_wall_hi;
+    p.walls = cf.bc == GLBM_BC_WALLS;
+    double *d_prof = c->d_diag, *d_stats = c->d_diag + 2 * (size_t)g.Ly;
+    CUDA_TRY(glbm_launch_channel_diagnostics(c->d_mom, g.Lx, g.Ly, g.Lz, p, d_prof, d_stats,
+                                             c->stream));
+    c->launches += 2;
+    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    if (profile)
+        CUDA_TRY(cudaMemcpyAsync(profile, d_prof, (size_t)g.Ly * sizeof(double), kind, c->stream));
+    if (stats)
+        CUDA_TRY(cudaMemcpyAsync(stats, d_stats, GLBM_CH_COUNT * sizeof(double), kind, c->stream));
+    if (!on_device) CUDA_TRY(cudaStreamSynchronize(c->stream));
     return GLBM_OK;
 }
 
@@ -1124,6 +1234,7 @@ extern "C" glbm_status glbm_load(glbm_ctx *c, const char *path)
     if (crc != crc_file) return fail(GLBM_E_IO, "checkpoint %s fails its CRC-32 check", path);
     CUDA_TRY(cudaMemcpyAsync(c->buf[c->cur], img.data(), img.size(), cudaMemcpyHostToDevice, c->stream));
     CUDA_TRY(set_clock(c, h.t));
+    CUDA_TRY(clear_unstable(c));
     CUDA_TRY(cudaStreamSynchronize(c->stream));
     return GLBM_OK;
 }
@@ -1364,6 +1475,15 @@ extern "C" glbm_status glbm_autotune(glbm_ctx *c, int reps, double *us)
     if (reps < 1 || reps > 1000) return fail(GLBM_E_INVAL, "reps must be in 1..1000");
     if (us)
         for (int i = 0; i < GLBM_LEVELS * GLBM_MAX_TILES; ++i) us[i] = -1.0;
+    // the trial launches must neither be skipped by an earlier failure nor leave
+    // flags of their own: keep the status words and put them back afterwards
+    unsigned saved[ST_WORDS];
+    {
+        glbm_status rs = read_status(c);
+        if (rs != GLBM_OK) return rs;
+        memcpy(saved, c->h_status, sizeof(saved));
+        CUDA_TRY(clear_unstable(c));
+    }
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     CUDA_TRY(cudaEventCreate(&e0));
     cudaError_t ce = cudaEventCreate(&e1);
@@ -1419,7 +1539,9 @@ extern "C" glbm_status glbm_autotune(glbm_ctx *c, int reps, double *us)
     if (st != GLBM_OK) return st;
     st = tiles_changed(c);
     if (st != GLBM_OK) return st;
-    // the uniform FP32 launches advanced the dither counter: put it back
+    // the trial launches advanced the dither counter and may have set flags:
+    // restore the status words, then the clock
+    CUDA_TRY(cudaMemcpyAsync(c->d_status, saved, sizeof(saved), cudaMemcpyHostToDevice, c->stream));
     CUDA_TRY(set_clock(c, c->t));
     CUDA_TRY(cudaStreamSynchronize(c->stream));
     return GLBM_OK;

@@ -273,6 +273,85 @@ __global__ void k_field_final(const double *__restrict__ partials, int nblocks, 
 }
 
 // ---------------------------------------------------------------------------
+// Channel diagnostics (Sec. 5.3, 5.4) from the moment fields of one instance
+// (rho at field 0, u_x at field 1, each [z][y][x]): the row means over x (and
+// z) of u_x and rho u_x, then the flow rate, the volumetric flow and the slip
+// ratios. FP64, every sum in a fixed order (deterministic).
+// ---------------------------------------------------------------------------
+constexpr int ROW_THREADS = 256;
+
+// Fixed tree over ROW_THREADS shared values (two arrays at once).
+__device__ __forceinline__ void tree2(double *a, double *b)
+{
+    __syncthreads();
+    for (int stride = ROW_THREADS / 2; stride > 0; stride >>= 1) {
+        if ((int)threadIdx.x < stride) {
+            a[threadIdx.x] += a[threadIdx.x + stride];
+            b[threadIdx.x] += b[threadIdx.x + stride];
+        }
+        __syncthreads();
+    }
+}
+
+// Block y: prof[y] = mean over (z, x) of u_x, prof[Ly + y] = mean of rho u_x.
+__global__ void k_row_means(const double *__restrict__ mom, int Lx, int Ly, int Lz,
+                            double *__restrict__ prof)
+{
+    __shared__ double su[ROW_THREADS], sj[ROW_THREADS];
+    const int y = blockIdx.x;
+    const long long plane = (long long)Lx * Ly * Lz;
+    double a = 0.0, b = 0.0;
+    for (int z = 0; z < Lz; ++z)
+        for (int x = threadIdx.x; x < Lx; x += ROW_THREADS) {
+            const long long node = ((long long)z * Ly + y) * Lx + x;
+            const double u = mom[plane + node];
+            a += u;
+            b += mom[node] * u;
+        }
+    su[threadIdx.x] = a;
+    sj[threadIdx.x] = b;
+    tree2(su, sj);
+    if (threadIdx.x == 0) {
+        const double n = (double)Lx * (double)Lz;
+        prof[y] = su[0] / n;
+        prof[Ly + y] = sj[0] / n;
+    }
+}
+
+// One block: stats[GLBM_CH_*] from the row means (see glbm_channel_diagnostics).
+__global__ void k_channel_stats(const double *__restrict__ prof, int Ly, ChannelParams p,
+                                double *__restrict__ stats)
+{
+    __shared__ double su[ROW_THREADS], sj[ROW_THREADS];
+    double a = 0.0, b = 0.0;
+    for (int y = threadIdx.x; y < Ly; y += ROW_THREADS) {
+        a += prof[y];
+        b += prof[Ly + y];
+    }
+    su[threadIdx.x] = a;
+    sj[threadIdx.x] = b;
+    tree2(su, sj);
+    if (threadIdx.x == 0) {
+        const double nan = __longlong_as_double(0x7FF8000000000000LL);
+        const double H = (double)Ly;
+        // volumetric flow Q = (1/Kn) int_0^H u dy / (4 U0 H), U0 = g H^2 / (8 nu)
+        const double nu = p.theta_y * p.tau;
+        const double U0 = p.g * H * H / (8.0 * nu);
+        const double kn = p.tau * sqrt(2.0 * p.theta_y) / H;  // Eq. (kn) with nu = theta tau
+        stats[GLBM_CH_FLOW_RATE] = sj[0];
+        stats[GLBM_CH_VOLUMETRIC] = p.g != 0.0 ? su[0] / (kn * 4.0 * U0 * H) : nan;
+        // the row means extrapolated linearly to the wall planes y = -1/2, Ly - 1/2
+        const double ulo = Ly > 1 ? 1.5 * prof[0] - 0.5 * prof[1] : prof[0];
+        const double uhi = Ly > 1 ? 1.5 * prof[Ly - 1] - 0.5 * prof[Ly - 2] : prof[Ly - 1];
+        const double du = p.u_hi - p.u_lo;
+        stats[GLBM_CH_U_LO] = p.walls ? ulo : nan;
+        stats[GLBM_CH_U_HI] = p.walls ? uhi : nan;
+        stats[GLBM_CH_SLIP_LO] = p.walls && du != 0.0 ? (ulo - p.u_lo) / du : nan;
+        stats[GLBM_CH_SLIP_HI] = p.walls && du != 0.0 ? (p.u_hi - uhi) / du : nan;
+    }
+}
+
+// ---------------------------------------------------------------------------
 // 1D step (Sec. 5.1): pull with halfway bounce-back or periodic ends, moments,
 // equilibrium, relaxation. One thread per node.
 // ---------------------------------------------------------------------------
@@ -313,7 +392,7 @@ __device__ __forceinline__ void node1d(const AuxArgs &a, const InstParams &ip, c
     // correction with the residual (j - u) - u delta rho (j - u is exact)
     if (DEV) u += fma(-u, drho, j - u) / rho;
     const T umax = (T)(0.816496580927726 * N);
-    if (!(rho > T(0)) || !(fabs(u) <= umax)) atomicOr(status, 1u);
+    if (!(rho > T(0)) || !(fabs(u) <= umax)) flag_unstable(status);
     T d[Q1];
     eq_dev_all<N, T>(a.tab, u, d);
     const T om = DEV ? (T)ip.omega_f : (T)ip.omega;
@@ -331,9 +410,10 @@ template <int N, typename T>
 __global__ void k_step1d(const __grid_constant__ AuxArgs a, const T *__restrict__ fin,
                          T *__restrict__ fout, int inst, unsigned *status)
 {
+    if (step_halted(status)) return;
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    if (x >= a.Lx) return;
-    node1d<N, T>(a, a.ip[inst], fin, fout, x, a.Lx, a.plane, status);
+    if (x < a.Lx) node1d<N, T>(a, a.ip[inst], fin, fout, x, a.Lx, a.plane, status);
+    finish_step(status);
 }
 
 // Many steps of one small 1D lattice inside one CTA: both population copies
@@ -344,7 +424,9 @@ __global__ void k_run1d_resident(const __grid_constant__ AuxArgs a, T *__restric
                                  int inst, long long steps, unsigned *status)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ unsigned bad;
     constexpr int Q1 = 2 * N + 1;
+    if (step_halted(status)) return;  // an earlier step left the positivity domain
     const int L = a.Lx;
     T *A = reinterpret_cast<T *>(smem_raw);
     T *B = A + (long long)Q1 * L;
@@ -352,18 +434,30 @@ __global__ void k_run1d_resident(const __grid_constant__ AuxArgs a, T *__restric
         const int q = i / L, x = i % L;
         A[i] = f[(long long)q * a.plane + x];
     }
+    if (threadIdx.x == 0) bad = 0u;
     __syncthreads();
-    for (long long t = 0; t < steps; ++t) {
+    long long done = 0;
+    while (done < steps) {
         for (int x = threadIdx.x; x < L; x += blockDim.x)
             node1d<N, T>(a, a.ip[inst], A, B, x, L, L, status);
-        __syncthreads();
+        __syncthreads();  // the step's flags (global atomics of this block) are visible
         T *tmp = A;
         A = B;
         B = tmp;
+        ++done;
+        // stop after a step that left the positivity domain: one read,
+        // broadcast, so that every thread leaves the loop at the same step
+        if (threadIdx.x == 0) bad = __ldcg(status + ST_FLAGS) & 1u;
+        __syncthreads();
+        if (bad) break;
     }
     for (int i = threadIdx.x; i < Q1 * L; i += blockDim.x) {
         const int q = i / L, x = i % L;
         f[(long long)q * a.plane + x] = A[i];
+    }
+    if (threadIdx.x == 0) {
+        atomicAdd(status + ST_STEPS, (unsigned)done);
+        if (bad) atomicExch(status + ST_HALT, 1u);
     }
 }
 
@@ -682,4 +776,13 @@ extern "C" glbm_status glbm_conservation_noalloc(const double *fields, int dims,
                                nblocks, sums, static_cast<cudaStream_t>(stream));
     if (e != cudaSuccess) return glbm_set_error(GLBM_E_CUDA, "launch: %s", cudaGetErrorString(e));
     return GLBM_OK;
+}
+
+cudaError_t glbm_launch_channel_diagnostics(const double *mom, int Lx, int Ly, int Lz,
+                                            const ChannelParams &p, double *prof, double *stats,
+                                            cudaStream_t s)
+{
+    k_row_means<<<Ly, ROW_THREADS, 0, s>>>(mom, Lx, Ly, Lz, prof);
+    k_channel_stats<<<1, ROW_THREADS, 0, s>>>(prof, Ly, p, stats);
+    return cudaGetLastError();
 }

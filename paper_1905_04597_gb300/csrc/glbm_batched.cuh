@@ -15,14 +15,15 @@ __global__ void __launch_bounds__(32 * G * R)
 {
     using S = Step2D<N, float, G, R>;
     __shared__ typename S::Smem sm;
+    const bool live = !step_halted(a.status);  // needed only at the stores
     const int4 it = a.items[first + blockIdx.x];  // (instance, x0, y0, N)
     const InstParams &ip = a.ip[it.x];
     const float *fin = static_cast<const float *>(a.fin) + ip.off;
     float *fout = static_cast<float *>(a.fout) + ip.off;
     const unsigned seed = hash32(__ldcg(a.step_ctr) * 0x632BE5ABu + (unsigned)it.x);
     S::run(a.tab[N - 1], a.tab[N - 1], ip, ip.Lx, ip.Ly, ip.pitch, (int)ip.plane, ip.bc, fin, fout,
-           it.y, it.z, sm, a.status, seed);
-    if (advance) advance_launch_counter(a.step_ctr, a.done_ctr);
+           it.y, it.z, sm, a.status, seed, nullptr, live);
+    if (advance && live) finish_step(a.status);
 }
 
 template <int N, int G, int R>
@@ -31,14 +32,15 @@ __global__ void __launch_bounds__(32 * G * R)
 {
     using S = Step2DPair<N, G, R>;
     __shared__ __align__(16) typename S::Smem sm;
+    const bool live = !step_halted(a.status);  // needed only at the stores
     const int4 it = a.items[first + blockIdx.x];  // (instance, x0, y0, N)
     const InstParams &ip = a.ip[it.x];
     const float *fin = static_cast<const float *>(a.fin) + ip.off;
     float *fout = static_cast<float *>(a.fout) + ip.off;
     const unsigned seed = hash32(__ldcg(a.step_ctr) * 0x632BE5ABu + (unsigned)it.x);
     S::run(a.tab[N - 1], a.tab[N - 1], ip, ip.Lx, ip.Ly, ip.pitch, (int)ip.plane, ip.bc, fin, fout,
-           it.y, it.z, sm, a.status, seed);
-    if (advance) advance_launch_counter(a.step_ctr, a.done_ctr);
+           it.y, it.z, sm, a.status, seed, nullptr, live);
+    if (advance && live) finish_step(a.status);
 }
 
 template <int N, int I = 0>

@@ -44,6 +44,44 @@ struct TabAcc<float> {
 // launch without a programmatic dependency); it precedes every global access.
 __device__ __forceinline__ void wait_prior_grid() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 
+// Whether an earlier step left the positivity domain (status word ST_HALT):
+// then the launches of later steps store nothing and do not count, so the
+// state stays at the end of the failing step. Read after wait_prior_grid;
+// uniform over the grid. The step kernels read it at entry but use it only at
+// their stores, so that it delays none of their loads.
+__device__ __forceinline__ bool step_halted(const unsigned *status)
+{
+    return __ldcg(status + ST_HALT) != 0u;
+}
+
+// Called by every CTA of a step's last launch: the last CTA to finish advances
+// the launch counter that seeds the FP32 dither of the next step (every CTA
+// read it before finishing) and the count of completed steps, and sets the
+// halt word when a node of this or an earlier step left the positivity
+// domain (flag_unstable fences each flag before its CTA reaches the count).
+__device__ __forceinline__ void finish_step(unsigned *status)
+{
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const unsigned total = gridDim.x * gridDim.y * gridDim.z;
+        if (atomicAdd(status + ST_DONE, 1u) == total - 1u) {
+            status[ST_DONE] = 0u;
+            atomicAdd(status + ST_CLOCK, 1u);
+            atomicAdd(status + ST_STEPS, 1u);
+            if (atomicOr(status + ST_FLAGS, 0u) & 1u) atomicExch(status + ST_HALT, 1u);
+        }
+    }
+}
+
+// A node left the positivity domain: set the status flag, visible device-wide
+// before this thread goes on (so before its CTA's finish_step count), the
+// only path that pays for a fence.
+__device__ __forceinline__ void flag_unstable(unsigned *status)
+{
+    atomicOr(status + ST_FLAGS, 1u);
+    __threadfence();
+}
+
 // Product rounded on its own (never contracted into a following addition), so
 // that the one-node and the packed pair tiles round alike.
 __device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }

@@ -106,6 +106,17 @@ double glbm_eq_dev_host(const AxisTableHi &t, double u, int i);
 // Host: the same table in the small layout (level N <= 8).
 AxisTable glbm_narrow_table(const AxisTableHi &t);
 
+// Words of a context's device status array: ST_FLAGS bit 0 is set by any node
+// that leaves the positivity domain; ST_CLOCK counts the steps launched (it
+// seeds the FP32 dither and follows the step clock); ST_DONE counts the CTAs
+// finished in the current launch; ST_STEPS counts the steps completed since the
+// host last cleared it; ST_HALT is set at the end of a step whose flags are
+// set, after which the launches of later steps do nothing. Every CTA reads
+// ST_CLOCK and ST_HALT when it starts and adds to ST_DONE when it ends: the
+// counter has a 128-byte line of its own, so that those reads do not queue
+// behind its atomics at L2.
+enum { ST_FLAGS = 0, ST_CLOCK = 32, ST_HALT = 33, ST_DONE = 64, ST_STEPS = 65, ST_WORDS = 96 };
+
 // Per-instance constants read by the step kernels (one per lattice instance).
 struct InstParams {
     double omega;      // 1 / (tau + 1/2)                         (Eq. maineq01)
@@ -247,6 +258,17 @@ cudaError_t glbm_launch_set_equilibrium3d(const AuxArgs &a, void *f, int inst, c
                                           cudaStream_t s);
 cudaError_t glbm_launch_moments3d(const AuxArgs &a, const void *f, int inst, double *out,
                                   cudaStream_t s);
+// Channel diagnostics (Sec. 5.3, 5.4) of one instance from its moment fields
+// (glbm_launch_moments / glbm_launch_moments3d output): prof[0..Ly) the row
+// means of u_x, prof[Ly..2Ly) of rho u_x, stats[GLBM_CH_*] the scalars.
+struct ChannelParams {
+    double theta_y, tau, g;  // lattice temperature of the y axis, relaxation time, force
+    double u_lo, u_hi;       // wall speeds (x direction)
+    int walls;               // diffuse walls along y (else the wall entries are NaN)
+};
+cudaError_t glbm_launch_channel_diagnostics(const double *mom, int Lx, int Ly, int Lz,
+                                            const ChannelParams &p, double *prof, double *stats,
+                                            cudaStream_t s);
 cudaError_t glbm_launch_field_sums(const double *fields, int nfields, long long n, double *partials,
                                    int nblocks, double *out, cudaStream_t s);
 int glbm_field_sum_blocks(long long n);

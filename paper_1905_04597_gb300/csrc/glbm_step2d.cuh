@@ -133,7 +133,8 @@ struct Step2D {
                                int Lx, int Ly,
                                int pitch, int plane, int bc, const T *__restrict__ fin,
                                T *__restrict__ fout, int x0, int y0, Smem &sm, unsigned *status,
-                               unsigned seed, const T *__restrict__ rwg = nullptr)
+                               unsigned seed, const T *__restrict__ rwg = nullptr,
+                               bool live = true)
     {
         const int lane = threadIdx.x & 31;
         const int w = threadIdx.x >> 5;
@@ -142,7 +143,8 @@ struct Step2D {
         // plane < 2^31 / Q: instance offsets fit 31 bits (checked at creation)
         const bool walls = bc == GLBM_BC_WALLS;
         const int x = x0 + lane, y = y0 + r;
-        const bool active = (x < Lx) && (y < Ly);
+        // live: no earlier step halted the run (else nothing is stored)
+        const bool active = (x < Lx) && (y < Ly) && live;
         const int xc = x < Lx ? x : Lx - 1;
         const int yc = y < Ly ? y : Ly - 1;
 
@@ -263,7 +265,7 @@ struct Step2D {
             // the half-spacing units of a 2N+2 axis
             const T umax = (T)(0.816496580927726 * (ZY ? 2 * N : N));
             const T umaxx = (T)(0.816496580927726 * (ZX ? 2 * NXL : NXL));
-            if (!(rho > T(0)) || !(fabs(ux) <= umaxx) || !(fabs(uy) <= umax)) atomicOr(status, 1u);
+            if (!(rho > T(0)) || !(fabs(ux) <= umaxx) || !(fabs(uy) <= umax)) flag_unstable(status);
         }
 
         T dx[QX];
@@ -337,7 +339,7 @@ struct Step2D {
         for (int k = 0; k < RPG; ++k) {
             const int iy = g + k * G;
             if (iy < Q1) {
-                const T wy = A::W(tab, iy);
+                const T wy = A::W(tab, iy), nwy = -wy;
                 T dy;
                 if constexpr (G == 1)
                     dy = dyall[k];
@@ -366,16 +368,19 @@ struct Step2D {
                         const T dxv = DX_SHARED ? sm.eqx[r][ix][lane] : dx[ix];
                         // delta f^eq = d^x W^y + E^x B + F/omega: the momentum-
                         // carrying d^x meets only the float weight W^y (whose row
-                        // sum is exactly 1), in the final fused rounding; a rounded
-                        // rho e^y there would scale the momentum by a fixed
-                        // 1 + O(2^-24) at every step of a steady flow. The dither
-                        // (half an ulp of f0, over omega) joins at the innermost
-                        // product, so the rounding of f^eq and the one rounding of
-                        // the store f0 + omega (f^eq - f0) are both zero-mean.
+                        // sum is exactly 1); a rounded rho e^y there would scale
+                        // the momentum by a fixed 1 + O(2^-24) at every step of a
+                        // steady flow. f^eq is never rounded at the scale of f:
+                        // r = f0 - d^x W^y cancels (one fused rounding, of a small
+                        // value when the flow runs along x), t1 holds the rest of
+                        // f^eq plus the dither (half an ulp of f0, over omega),
+                        // and the store f0 + omega (t1 - r) is one rounding that
+                        // sees the whole dither: zero-mean.
                         const float u = dither_pick(ix, ua, ub, -ua, -ub);
                         const T dith = (T)dither_ulp((float)f0, u);
-                        const T eq = fma(dxv, wy, fma(dxv, B, fma(A::W(tabx, ix), Bn, dith)));
-                        v = fma(om, eq - f0, f0);
+                        const T t1 = fma(dxv, B, fma(A::W(tabx, ix), Bn, dith));
+                        const T r = fma(dxv, nwy, f0);
+                        v = fma(om, t1 - r, f0);
                     } else {
                         T eq = ex[ix] * rey;
                         if (nx != 0) eq = fma(A::WN(tabx, ix), gr, eq);
@@ -388,20 +393,6 @@ struct Step2D {
     }
 };
 
-// The last CTA of a launch to finish advances the launch counter that seeds the
-// dithered stores of the next launch (every CTA read it before finishing).
-__device__ __forceinline__ void advance_launch_counter(unsigned *step_ctr, unsigned *done_ctr)
-{
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        const unsigned total = gridDim.x * gridDim.y * gridDim.z;
-        if (atomicAdd(done_ctr, 1u) == total - 1u) {
-            *done_ctr = 0u;
-            atomicAdd(step_ctr, 1u);
-        }
-    }
-}
-
 template <int N, typename T, int G, int R, int NXL = N, int ZY = 0, int ZX = 0>
 __global__ void __launch_bounds__(32 * G * R)
     k_step2d(const __grid_constant__ Step2DArgsOf<N> a)
@@ -409,6 +400,8 @@ __global__ void __launch_bounds__(32 * G * R)
     using S = Step2D<N, T, G, R, NXL, ZY, ZX>;
     __shared__ typename S::Smem sm;
     wait_prior_grid();
+    // read here, needed only at the stores: no CTA waits for it before its loads
+    const bool live = !step_halted(a.status);
     const int inst = blockIdx.z;
     const T *fin = static_cast<const T *>(a.fin) + (long long)inst * a.inst_stride;
     T *fout = static_cast<T *>(a.fout) + (long long)inst * a.inst_stride;
@@ -417,11 +410,11 @@ __global__ void __launch_bounds__(32 * G * R)
     const T *rwg = a.rw ? static_cast<const T *>(a.rw) + (long long)inst * 2 * a.pitch : nullptr;
     if constexpr (NXL == N && ZX == ZY)
         S::run(a.tab, a.tab, a.ip[inst], a.Lx, a.Ly, a.pitch, (int)a.plane, a.bc, fin, fout,
-               blockIdx.x * 32, blockIdx.y * R, sm, a.status, seed, rwg);
+               blockIdx.x * 32, blockIdx.y * R, sm, a.status, seed, rwg, live);
     else
         S::run(a.tab, a.tabx, a.ip[inst], a.Lx, a.Ly, a.pitch, (int)a.plane, a.bc, fin, fout,
-               blockIdx.x * 32, blockIdx.y * R, sm, a.status, seed, rwg);
-    if (S::DEV) advance_launch_counter(a.step_ctr, a.done_ctr);
+               blockIdx.x * 32, blockIdx.y * R, sm, a.status, seed, rwg, live);
+    if (live) finish_step(a.status);
 }
 
 // Wall densities of one step computed once per column and wall, for lattices
@@ -440,6 +433,7 @@ __global__ void __launch_bounds__(32 * Step2D<N, T, 1, 1, NXL, ZY, ZX>::NV)
     __shared__ T dsum[S::NV][2][32];
     __shared__ T rw[2][32];
     wait_prior_grid();
+    const bool live = !step_halted(a.status);  // needed only at the store
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int inst = blockIdx.y, h = blockIdx.z;
     const int x = blockIdx.x * 32 + lane;
@@ -454,6 +448,6 @@ __global__ void __launch_bounds__(32 * Step2D<N, T, 1, 1, NXL, ZY, ZX>::NV)
     constexpr int U = S::QX >= LMAX ? 1 : LMAX / S::QX;
     S::template wall_densities<U>(a.ip[inst], fin, a.Ly, a.pitch, (int)a.plane, cofs, h == 0, h == 1,
                                   w, S::NV, lane, dsum, rw);
-    if (w == 0 && x < a.Lx)
+    if (w == 0 && x < a.Lx && live)
         static_cast<T *>(a.rw)[((long long)inst * 2 + h) * a.pitch + x] = rw[h][lane];
 }

@@ -11,6 +11,7 @@ __global__ void __launch_bounds__(32 * G * R)
     using S = Step2DPair<N, G, R, NXL, ZY, ZX>;
     __shared__ __align__(16) typename S::Smem sm;
     wait_prior_grid();
+    const bool live = !step_halted(a.status);  // needed only at the stores
     const int inst = blockIdx.z;
     const float *fin = static_cast<const float *>(a.fin) + (long long)inst * a.inst_stride;
     float *fout = static_cast<float *>(a.fout) + (long long)inst * a.inst_stride;
@@ -20,11 +21,11 @@ __global__ void __launch_bounds__(32 * G * R)
         a.rw ? static_cast<const float *>(a.rw) + (long long)inst * 2 * a.pitch : nullptr;
     if constexpr (NXL == N && ZX == ZY)
         S::run(a.tab, a.tab, a.ip[inst], a.Lx, a.Ly, a.pitch, (int)a.plane, a.bc, fin, fout,
-               blockIdx.x * S::TW, blockIdx.y * R, sm, a.status, seed, rwg);
+               blockIdx.x * S::TW, blockIdx.y * R, sm, a.status, seed, rwg, live);
     else
         S::run(a.tab, a.tabx, a.ip[inst], a.Lx, a.Ly, a.pitch, (int)a.plane, a.bc, fin, fout,
-               blockIdx.x * S::TW, blockIdx.y * R, sm, a.status, seed, rwg);
-    advance_launch_counter(a.step_ctr, a.done_ctr);
+               blockIdx.x * S::TW, blockIdx.y * R, sm, a.status, seed, rwg, live);
+    if (live) finish_step(a.status);
 }
 
 // Launch with programmatic stream serialization (see wait_prior_grid).

@@ -212,7 +212,7 @@ __device__ __forceinline__ void pair_collide_row(const TX &tabx, int iy, float w
                                                  bool act0, bool act1)
 {
     using A = TabAcc<float>;
-    const f32x2 wy2 = pk2(wy, wy);
+    const f32x2 wy2 = pk2(wy, wy), nwy2 = pk2(-wy, -wy);
     const float grs = mul_rn(gto, wy);
     const f32x2 gr = pk2(grs, grs);
     const f32x2 B = fma2(drho, wy2, fma2(drho, dy, dy));  // rho e^y - W^y
@@ -230,14 +230,14 @@ __device__ __forceinline__ void pair_collide_row(const TX &tabx, int iy, float w
         const f32x2 Bn = nx != 0 ? fma2(pk2((float)nx, (float)nx), gr, B) : B;
         const float wx = A::W(tabx, ix);
         const f32x2 dxv = DXS ? dxs[ix * 32] : dxr[ix];
-        // the dither (half an ulp of f0, over omega) joins at the innermost
-        // product and d^x meets only the float weight W^y, in the final fused
-        // rounding (the one-node tile's order); one rounding of the store
+        // the one-node tile's order: t1 = d^x B + W^x Bn + dither / omega,
+        // r = f0 - d^x W^y, one rounding of the store f0 + omega (t1 - r)
         const float p0 = __int_as_float(__float_as_int(lo2(f0)) & 0x7F800000);
         const float p1 = __int_as_float(__float_as_int(hi2(f0)) & 0x7F800000);
         const f32x2 dith = mul2(dither_pick(ix, ua, ub, na, nb), pk2(p0, p1));
-        const f32x2 eq = fma2(dxv, wy2, fma2(dxv, B, fma2(pk2(wx, wx), Bn, dith)));
-        const f32x2 v = fma2(om, sub2(eq, f0), f0);
+        const f32x2 t1 = fma2(dxv, B, fma2(pk2(wx, wx), Bn, dith));
+        const f32x2 r = fma2(dxv, nwy2, f0);
+        const f32x2 v = fma2(om, sub2(t1, r), f0);
         float *const o = op + ix * plane;
         if (act0 && act1) {
             *reinterpret_cast<f32x2 *>(o) = v;
@@ -281,7 +281,7 @@ struct Step2DPair {
                                int pitch, int plane, int bc, const float *__restrict__ fin,
                                float *__restrict__ fout, int x0, int y0, Smem &sm,
                                unsigned *status, unsigned seed,
-                               const float *__restrict__ rwg = nullptr)
+                               const float *__restrict__ rwg = nullptr, bool live = true)
     {
         const int lane = threadIdx.x & 31;
         const int w = threadIdx.x >> 5;
@@ -290,7 +290,8 @@ struct Step2DPair {
         const bool walls = bc == GLBM_BC_WALLS;
         const int x = x0 + 2 * lane, y = y0 + r;
         const bool yin = y < Ly;
-        const bool act0 = yin && x < Lx, act1 = yin && x + 1 < Lx;
+        // live: no earlier step halted the run (else nothing is stored)
+        const bool act0 = yin && x < Lx && live, act1 = yin && x + 1 < Lx && live;
         const int xc = x < Lx ? x : Lx - 1;
         const int yc = yin ? y : Ly - 1;
         // the tile pulls from columns x0-VMAX .. x0+63+VMAX without wrapping
@@ -409,7 +410,7 @@ struct Step2DPair {
                                        !(fabsf(lo2(uy)) <= umax));
             const bool bad1 = act1 && (!(hi2(rho) > 0.f) || !(fabsf(hi2(ux)) <= umaxx) ||
                                        !(fabsf(hi2(uy)) <= umax));
-            if (bad0 || bad1) atomicOr(status, 1u);
+            if (bad0 || bad1) flag_unstable(status);
         }
 
         // E^x - W and E^y - W for both nodes

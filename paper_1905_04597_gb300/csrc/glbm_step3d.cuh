@@ -44,7 +44,7 @@ struct Step3D {
     __device__ static void run(const AxisTable &tab, const InstParams &ip, int Lx, int Ly, int Lz,
                                int pitch, int plane, int bc, const T *__restrict__ fin,
                                T *__restrict__ fout, int x0, int y0, int z, Smem &sm,
-                               unsigned *status, unsigned seed)
+                               unsigned *status, unsigned seed, bool live = true)
     {
         const int lane = threadIdx.x & 31;
         const int w = threadIdx.x >> 5;
@@ -52,7 +52,8 @@ struct Step3D {
         const int r = w / G;
         const bool walls = bc == GLBM_BC_WALLS;
         const int x = x0 + lane, y = y0 + r;
-        const bool active = (x < Lx) && (y < Ly);
+        // live: no earlier step halted the run (else nothing is stored)
+        const bool active = (x < Lx) && (y < Ly) && live;
         const int xc = x < Lx ? x : Lx - 1;
         const int yc = y < Ly ? y : Ly - 1;
         const int slab = Ly * pitch;  // elements per z-slice of a velocity plane
@@ -213,7 +214,7 @@ struct Step3D {
         if (active) {
             const T umax = (T)(0.816496580927726 * N);  // sqrt(2/3) N (Sec. 3)
             if (!(rho > T(0)) || !(fabs(ux) <= umax) || !(fabs(uy) <= umax) || !(fabs(uz) <= umax))
-                atomicOr(status, 1u);
+                flag_unstable(status);
         }
         T dx[Q1], dy[Q1], dz[Q1];
         if constexpr (DEV) {
@@ -281,16 +282,16 @@ struct Step3D {
                         const T Bn = nx != 0 ? fma(T(nx), gr, B) : B;
                         // delta f^eq = d^x W^y W^z + E^x B + F/omega: the
                         // momentum-carrying d^x is rounded with W^y, then meets W^z
-                        // in the final fused rounding (no rounded rho or W^y W^z
-                        // factor, whose fixed error would scale the momentum at
-                        // every step); the dither (half an ulp of f0, over omega)
-                        // joins at the innermost product, and the store
-                        // f0 + omega (f^eq - f0) is one rounding (as in 2D)
+                        // in a fused rounding (no rounded rho or W^y W^z factor,
+                        // whose fixed error would scale the momentum at every
+                        // step); as in 2D, r = f0 - d^x W^y W^z, t1 holds the rest
+                        // plus the dither (half an ulp of f0, over omega), and the
+                        // store f0 + omega (t1 - r) is one rounding
                         const float u = dither_pick(ix, ua, ub, -ua, -ub);
                         const T dith = (T)dither_ulp((float)f0, u);
-                        const T eq = fma(mul_rn(dx[ix], wy), wz,
-                                         fma(dx[ix], B, fma(A::W(tab, ix), Bn, dith)));
-                        v = fma(om, eq - f0, f0);
+                        const T t1 = fma(dx[ix], B, fma(A::W(tab, ix), Bn, dith));
+                        const T r = fma(-mul_rn(dx[ix], wy), wz, f0);  // f0 - d^x W^y W^z
+                        v = fma(om, t1 - r, f0);
                     } else {
                         T eq = (A::W(tab, ix) + dx[ix]) * rez_y;
                         if (nx != 0) eq = fma(A::WN(tab, ix), gr, eq);
@@ -309,12 +310,13 @@ __global__ void __launch_bounds__(32 * G * R) k_step3d(const __grid_constant__ S
     using S = Step3D<N, T, G, R>;
     __shared__ typename S::Smem sm;
     wait_prior_grid();
+    const bool live = !step_halted(a.status);  // needed only at the stores
     const int inst = blockIdx.z / a.Lz;
     const int z = blockIdx.z - inst * a.Lz;
     const T *fin = static_cast<const T *>(a.fin) + (long long)inst * a.inst_stride;
     T *fout = static_cast<T *>(a.fout) + (long long)inst * a.inst_stride;
     const unsigned seed = S::DEV ? hash32(__ldcg(a.step_ctr) * 0x632BE5ABu + inst) : 0u;
     S::run(a.tab, a.ip[inst], a.Lx, a.Ly, a.Lz, a.pitch, (int)a.plane, a.bc, fin, fout,
-           blockIdx.x * 32, blockIdx.y * R, z, sm, a.status, seed);
-    if (S::DEV) advance_launch_counter(a.step_ctr, a.done_ctr);
+           blockIdx.x * 32, blockIdx.y * R, z, sm, a.status, seed, live);
+    if (live) finish_step(a.status);
 }

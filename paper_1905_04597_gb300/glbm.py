@@ -26,6 +26,9 @@ M_UZ, M_QZ, M_ALL3 = 128, 256, 511
 FIELDS_2D = ("rho", "ux", "uy", "T", "qx", "qy", "sxy")
 FIELDS_3D = FIELDS_2D + ("uz", "qz")
 FIELDS_1D = ("rho", "ux", "T", "qx")
+# entries of glbm_channel_diagnostics' stats (GLBM_CH_* in glbm.h)
+CHANNEL_STATS = ("flow_rate", "volumetric_flow", "u_wall_lo_gas", "u_wall_hi_gas", "slip_lo",
+                 "slip_hi")
 
 
 class GlbmError(RuntimeError):
@@ -79,6 +82,7 @@ def lib():
         "glbm_sync": ([vp], i),
         "glbm_moments": ([vp, i, ctypes.c_uint, vp, sz, i], i),
         "glbm_conservation": ([vp, i, dp, dp, dp], i),
+        "glbm_channel_diagnostics": ([vp, i, vp, vp, i], i),
         "glbm_save": ([vp, ctypes.c_char_p], i),
         "glbm_load": ([vp, ctypes.c_char_p], i),
         "glbm_time": ([vp], i64),
@@ -338,6 +342,26 @@ class Lattice:
         check(lib().glbm_conservation(self.h, inst, ctypes.byref(m), ctypes.byref(jx),
                                       ctypes.byref(jy)))
         return m.value, jx.value, jy.value
+
+    def channel_diagnostics(self, inst=0, profile=None, stats=None):
+        """Channel diagnostics of Sec. 5.3-5.4 at the current time (glbm.h,
+        glbm_channel_diagnostics): returns (profile <u_x>(y), dict of the flow
+        rate, volumetric flow, wall-plane velocities and slip ratios). With
+        torch tensors `profile` and `stats` (float64, device or host), fills
+        them and returns them."""
+        c = self.configs[inst]
+        if profile is None and stats is None:
+            prof, st = np.empty(c.ny), np.empty(len(CHANNEL_STATS))
+            check(lib().glbm_channel_diagnostics(self.h, inst, ctypes.c_void_p(prof.ctypes.data),
+                                                 ctypes.c_void_p(st.ctypes.data), 0))
+            return prof, dict(zip(CHANNEL_STATS, st.tolist()))
+        pp, dev = _ptr(profile) if profile is not None else (ctypes.c_void_p(), None)
+        sp, dev2 = _ptr(stats) if stats is not None else (ctypes.c_void_p(), None)
+        on_dev = dev if dev is not None else dev2
+        if dev is not None and dev2 is not None and dev != dev2:
+            raise TypeError("profile and stats must both be host or both device memory")
+        check(lib().glbm_channel_diagnostics(self.h, inst, pp, sp, on_dev))
+        return profile, stats
 
     def save(self, path):
         check(lib().glbm_save(self.h, str(path).encode()))

@@ -335,12 +335,16 @@ def test_column_invariance_nx1_vs_nx64():
 
 
 def test_instability_flag_is_reported():
-    """A state outside the positivity domain (|u| > sqrt(2/3) N, Sec. 3) raises on sync."""
+    """A state outside the positivity domain (|u| > sqrt(2/3) N, Sec. 3): the
+    first step flags it, glbm_step reports one completed step, and the flag
+    stays visible to glbm_sync."""
     k, nx, ny = 0, 32, 8
     lat = glbm.Lattice(dict(dims=2, nx=nx, ny=ny, k=k, tau=0.8, bc=glbm.BC_PERIODIC))
     ux = np.full((ny, nx), 1.2 * np.sqrt(2 / 3))
     lat.set_equilibrium(0, np.ones((ny, nx)), ux, np.zeros((ny, nx)))
-    lat.step(2)
+    with pytest.raises(glbm.UnstableError, match="1 of 2 steps completed"):
+        lat.step(2)
+    assert lat.time == 1
     with pytest.raises(glbm.UnstableError):
         lat.sync()
     lat.close()
