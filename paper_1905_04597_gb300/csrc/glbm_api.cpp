@@ -301,12 +301,16 @@ static Geo make_geo(const glbm_config &c)
     g.Lx = c.nx;
     g.Ly = c.dims >= 2 ? c.ny : 1;
     g.Lz = c.dims == 3 ? c.nz : 1;
-    g.pitch = ((g.Lx + 31) / 32) * 32;
+    // rows padded to 64 elements and, in 2D, one spare row per velocity plane
+    // (y = Ly): the step tiles store every thread's result unconditionally, the
+    // columns past Lx of a ragged tile into the padding and the rows past Ly
+    // into the spare row; no pull, reducer or copy reads either
+    g.pitch = ((g.Lx + 63) / 64) * 64;
     g.zv = c.dims == 2 ? c.zv_axes : 0;
     const int Q1 = 2 * g.N + 1 + ((g.zv & GLBM_ZV_Y) ? 1 : 0);
     g.Q = c.dims == 2 ? Q1 * (2 * g.NX + 1 + ((g.zv & GLBM_ZV_X) ? 1 : 0)) : Q1;
     if (c.dims == 3) g.Q = Q1 * Q1 * Q1;
-    g.plane = (long long)g.Lz * g.Ly * g.pitch;
+    g.plane = (long long)g.Lz * (c.dims == 2 ? g.Ly + 1 : g.Ly) * g.pitch;
     g.off = 0;
     return g;
 }
@@ -775,13 +779,19 @@ static glbm_status copy_columns(glbm_ctx *c, int inst, int x0, int ncols, void *
         return fail(GLBM_E_INVAL, "columns [%d, %d) outside 0..%d", x0, x0 + ncols, g.Lx);
     const size_t e = c->elem;
     char *base = (char *)inst_ptr(c, c->cur, inst) + (size_t)x0 * e;
-    const size_t rows = (size_t)g.Q * g.Ly * g.Lz, width = (size_t)ncols * e, spitch = (size_t)g.pitch * e;
-    cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice
-                                    : (pack ? cudaMemcpyDeviceToHost : cudaMemcpyHostToDevice);
-    if (pack)
-        CUDA_TRY(cudaMemcpy2DAsync(buf, width, base, spitch, width, rows, kind, c->stream));
-    else
-        CUDA_TRY(cudaMemcpy2DAsync(base, spitch, buf, width, width, rows, kind, c->stream));
+    // the (z, y) rows of each velocity plane, planes g.plane elements apart
+    // (2D planes hold a spare row after the Ly rows of data)
+    const size_t rows = (size_t)g.Ly * g.Lz, width = (size_t)ncols * e, spitch = (size_t)g.pitch * e;
+    const size_t plane_rows = (size_t)(g.plane / g.pitch);
+    cudaMemcpy3DParms p = {};
+    cudaPitchedPtr state = make_cudaPitchedPtr(base, spitch, width, plane_rows);
+    cudaPitchedPtr packed = make_cudaPitchedPtr(buf, width, width, rows);
+    p.srcPtr = pack ? state : packed;
+    p.dstPtr = pack ? packed : state;
+    p.extent = make_cudaExtent(width, rows, (size_t)g.Q);
+    p.kind = on_device ? cudaMemcpyDeviceToDevice
+                       : (pack ? cudaMemcpyDeviceToHost : cudaMemcpyHostToDevice);
+    CUDA_TRY(cudaMemcpy3DAsync(&p, c->stream));
     if (!on_device) CUDA_TRY(cudaStreamSynchronize(c->stream));
     return GLBM_OK;
 }

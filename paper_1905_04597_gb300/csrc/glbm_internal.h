@@ -131,7 +131,7 @@ struct InstParams {
     // geometry of the instance (heterogeneous batches keep their own)
     int N;            // level along y (along both axes unless NX differs)
     int Lx, Ly;       // nodes
-    int pitch;        // row pitch in elements (multiple of 32)
+    int pitch;        // row pitch in elements (multiple of 64)
     int bc;           // GLBM_BC_*
     int NX;           // level along x
     long long off;    // element offset of this instance in the population buffers

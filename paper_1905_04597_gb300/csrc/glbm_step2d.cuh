@@ -327,7 +327,11 @@ struct Step2D {
         for (int ix = 0; ix < QX; ++ix) ex[ix] = DEV ? T(0) : A::W(tabx, ix) + dx[ix];
         const T om = DEV ? (T)ip.omega_f : (T)ip.omega;
         const T gto = DEV ? (T)ip.g_theta_om_f : (T)ip.g_theta_om;  // g / (theta omega)
-        T *const obase = fout + (y * pitch + x);
+        if (!live) return;  // an earlier step halted the run: store nothing
+        // rows past Ly store into the plane's spare row y = Ly, columns past
+        // Lx into the row padding (pitch is a multiple of 64): no store needs a
+        // per-node condition, and nothing ever reads those places
+        T *const obase = fout + ((y < Ly ? y : Ly) * pitch + x);
         // the store's dither enters the equilibrium divided by omega (below)
         const float iom = DEV ? 1.0f / ip.omega_f : 0.0f;
 
@@ -386,7 +390,7 @@ struct Step2D {
                         if (nx != 0) eq = fma(A::WN(tabx, ix), gr, eq);
                         v = fma(om, eq - f0, f0);
                     }
-                    if (active) op[ix * plane] = v;
+                    op[ix * plane] = v;
                 }
             }
         }

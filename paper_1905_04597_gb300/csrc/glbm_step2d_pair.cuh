@@ -208,8 +208,7 @@ __device__ __forceinline__ void pair_collide_row(const TX &tabx, int iy, float w
                                                  f32x2 drho, f32x2 om, float iom, float gto,
                                                  const f32x2 (&f)[2 * N + 1 + ZX],
                                                  const f32x2 (&dxr)[2 * N + 1 + ZX], const f32x2 *dxs,
-                                                 float *op, int plane, unsigned h0, unsigned h1,
-                                                 bool act0, bool act1)
+                                                 float *op, int plane, unsigned h0, unsigned h1)
 {
     using A = TabAcc<float>;
     const f32x2 wy2 = pk2(wy, wy), nwy2 = pk2(-wy, -wy);
@@ -238,13 +237,9 @@ __device__ __forceinline__ void pair_collide_row(const TX &tabx, int iy, float w
         const f32x2 t1 = fma2(dxv, B, fma2(pk2(wx, wx), Bn, dith));
         const f32x2 r = fma2(dxv, nwy2, f0);
         const f32x2 v = fma2(om, sub2(t1, r), f0);
-        float *const o = op + ix * plane;
-        if (act0 && act1) {
-            *reinterpret_cast<f32x2 *>(o) = v;
-        } else {
-            if (act0) o[0] = lo2(v);
-            if (act1) o[1] = hi2(v);
-        }
+        // every thread stores both nodes: columns past Lx land in the row
+        // padding, rows past Ly in the plane's spare row (the caller's op)
+        *reinterpret_cast<f32x2 *>(op + ix * plane) = v;
     }
 }
 
@@ -465,7 +460,11 @@ struct Step2DPair {
         const f32x2 om = pk2(ip.omega_f, ip.omega_f);
         const float iom = 1.0f / ip.omega_f;
         const float gto = ip.g_theta_om_f;  // g / (theta omega)
-        float *const obase = fout + (y * pitch + x);
+        if (!live) return;  // an earlier step halted the run: store nothing
+        // rows past Ly store into the plane's spare row y = Ly, columns past
+        // Lx into the row padding (pitch is a multiple of 64): no store needs a
+        // per-node condition, and nothing ever reads those places
+        float *const obase = fout + ((yin ? y : Ly) * pitch + x);
 
 #pragma unroll
         for (int k = 0; k < RPG; ++k) {
@@ -479,7 +478,7 @@ struct Step2DPair {
                     dy = *reinterpret_cast<const f32x2 *>(&sm.eqy[r][iy][2 * lane]);
                 const f32x2 *dxs = reinterpret_cast<const f32x2 *>(&sm.eqx[G > 1 ? r : 0][0][2 * lane]);
                 pair_collide_row<NXL, (G > 1), ZX>(tabx, iy, wy, dy, drho, om, iom, gto, f[k], dx, dxs,
-                                               obase + iy * QX * plane, plane, h0, h1, act0, act1);
+                                               obase + iy * QX * plane, plane, h0, h1);
             }
         }
     }
