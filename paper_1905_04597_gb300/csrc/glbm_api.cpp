@@ -301,16 +301,17 @@ static Geo make_geo(const glbm_config &c)
     g.Lx = c.nx;
     g.Ly = c.dims >= 2 ? c.ny : 1;
     g.Lz = c.dims == 3 ? c.nz : 1;
-    // rows padded to 64 elements and, in 2D, one spare row per velocity plane
-    // (y = Ly): the step tiles store every thread's result unconditionally, the
-    // columns past Lx of a ragged tile into the padding and the rows past Ly
-    // into the spare row; no pull, reducer or copy reads either
+    // rows padded to 64 elements and, in 2D and 3D, one spare row after the
+    // Lz Ly rows of each velocity plane: the step tiles store every thread's
+    // result unconditionally, the columns past Lx of a ragged tile into the
+    // padding and the rows past Ly into the spare row; no pull, reducer or
+    // copy reads either
     g.pitch = ((g.Lx + 63) / 64) * 64;
     g.zv = c.dims == 2 ? c.zv_axes : 0;
     const int Q1 = 2 * g.N + 1 + ((g.zv & GLBM_ZV_Y) ? 1 : 0);
     g.Q = c.dims == 2 ? Q1 * (2 * g.NX + 1 + ((g.zv & GLBM_ZV_X) ? 1 : 0)) : Q1;
     if (c.dims == 3) g.Q = Q1 * Q1 * Q1;
-    g.plane = (long long)g.Lz * (c.dims == 2 ? g.Ly + 1 : g.Ly) * g.pitch;
+    g.plane = ((long long)g.Lz * g.Ly + (c.dims >= 2 ? 1 : 0)) * g.pitch;
     g.off = 0;
     return g;
 }

@@ -237,7 +237,11 @@ struct Step3D {
         }
         const T om = DEV ? (T)ip.omega_f : (T)ip.omega;
         const T gto = DEV ? (T)ip.g_theta_om_f : (T)ip.g_theta_om;  // g / (theta omega)
-        T *const obase = fout + (z * slab + y * pitch + x);
+        if (!live) return;  // an earlier step halted the run: store nothing
+        // rows past Ly store into the plane's spare row after its Lz Ly rows,
+        // columns past Lx into the row padding (pitch is a multiple of 64): no
+        // store needs a per-node condition, and nothing reads those places
+        T *const obase = fout + ((y < Ly ? z * slab + y * pitch : Lz * slab) + x);
         const float iom = DEV ? 1.0f / ip.omega_f : 0.0f;  // the dither enters f^eq over omega
 #pragma unroll
         for (int k = 0; k < RPG; ++k) {
@@ -297,7 +301,7 @@ struct Step3D {
                         if (nx != 0) eq = fma(A::WN(tab, ix), gr, eq);
                         v = fma(om, eq - f0, f0);
                     }
-                    if (active) op[ix * plane] = v;
+                    op[ix * plane] = v;
                 }
             }
         }
