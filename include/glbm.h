@@ -273,11 +273,10 @@ glbm_status glbm_channel_diagnostics(glbm_ctx *ctx, int inst, double *profile, d
  * sum rho u_y), but it owns no context and allocates nothing. The block
  * partials go to a static 24 KiB array in the library's device memory.
  *
- * It is for callers that may not call cudaMalloc: code running while a
- * stream is captured into a CUDA graph (allocation is not a stream operation
- * and would break the capture), real-time loops that cannot take the
- * allocator's device-wide synchronisation, and applications whose memory pool
- * owns all device memory.
+ * It is for callers that may not call cudaMalloc: real-time loops that
+ * cannot take the allocator's device-wide synchronisation, applications whose
+ * memory pool owns all device memory, and code that runs inside such a pool's
+ * own callbacks, where a nested allocation would deadlock or recurse.
  *
  *   fields  device pointer to the moment fields as glbm_moments writes them
  *           with mask GLBM_M_RHO | GLBM_M_UX | GLBM_M_UY: rho, u_x, u_y (2D,
@@ -288,7 +287,10 @@ glbm_status glbm_channel_diagnostics(glbm_ctx *ctx, int inst, double *profile, d
  *   stream  cudaStream_t; the call is asynchronous on it.
  *
  * The first call on a device looks up the scratch's device address, and it
- * should come before any stream capture. Every call shares the one scratch
+ * should come before any stream capture. The address is kept for the life of
+ * the device's primary context: after cudaDeviceReset (or anything else that
+ * destroys that context) the library must be reloaded before this call is
+ * used again. Every call shares the one scratch
  * array, which keeps the last call's contents. Nothing in it needs clearing,
  * because each call overwrites every partial it reads. Calls that overlap on
  * the GPU (different streams, or the same graph launched concurrently) race

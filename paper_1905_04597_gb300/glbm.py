@@ -442,11 +442,18 @@ def _flowrate_autograd():
         @staticmethod
         def forward(ctx, tau, g, config, steps, ckpt_every=100):
             cfg = dict(config, tau=float(tau), kn=0.0, g=float(g))
+            dev = tau.device if isinstance(tau, torch.Tensor) else torch.device("cpu")
+            f64 = dict(dtype=torch.float64, device=dev)
+            if not any(ctx.needs_input_grad[:2]):
+                # no gradient wanted: the forward steps and the flow rate only
+                with Lattice(cfg) as lat:
+                    lat.step(steps)
+                    _, stats = lat.channel_diagnostics(0)
+                return torch.tensor(stats["flow_rate"], **f64)
             with Lattice(cfg) as lat:
                 J, dtau, dg = lat.adjoint_flowrate(steps, ckpt_every)
-            ctx.save_for_backward(torch.tensor(dtau[0], dtype=torch.float64),
-                                  torch.tensor(dg[0], dtype=torch.float64))
-            return torch.tensor(J[0], dtype=torch.float64)
+            ctx.save_for_backward(torch.tensor(dtau[0], **f64), torch.tensor(dg[0], **f64))
+            return torch.tensor(J[0], **f64)
 
         @staticmethod
         def backward(ctx, grad):

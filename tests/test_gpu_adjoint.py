@@ -103,3 +103,25 @@ def test_autograd_function():
     assert J.item() == pytest.approx(oJ, rel=1e-10)
     assert tau.grad.item() == pytest.approx(3 * otau, rel=1e-9)
     assert g.grad.item() == pytest.approx(3 * og, rel=1e-9)
+
+
+def test_autograd_function_without_gradients_runs_forward_only():
+    """With no input requiring a gradient the Function runs the forward steps
+    only (no adjoint sweep) and returns the same flow rate, on the device of
+    tau."""
+    import torch
+    nx, ny, k = 16, 12, 1
+    config = dict(dims=2, nx=nx, ny=ny, k=k, prec=glbm.FP64)
+    tau = torch.tensor(0.9, dtype=torch.float64, device="cuda")
+    g = torch.tensor(2e-5, dtype=torch.float64, device="cuda")
+    J = glbm.flow_rate(tau, g, config, steps=50, ckpt_every=10)
+    assert J.device == tau.device and not J.requires_grad
+    N = k + 1
+    o = orc.Lattice(2, N, N, nx, ny, orc.BC_WALLS, 0.9, 0.0, 0.0, 2e-5)
+    X0 = o.equilibrium(np.ones((ny, nx)), np.zeros((ny, nx)), np.zeros((ny, nx)))
+    oJ, _, _ = o.flowrate_grad(X0, 50)
+    assert J.item() == pytest.approx(oJ, rel=1e-10)
+    with torch.no_grad():
+        tau2 = tau.clone().requires_grad_(True)
+        J2 = glbm.flow_rate(tau2, g, config, steps=50, ckpt_every=10)
+    assert J2.item() == pytest.approx(oJ, rel=1e-10)
