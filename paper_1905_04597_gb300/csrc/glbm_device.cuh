@@ -275,6 +275,65 @@ __device__ __forceinline__ void eq_dev_all(const Tab &t, T u, T (&d)[2 * N + 1 +
     }
 }
 
+// Two FP32 lanes in one 64-bit register pair, with the two-lane instructions
+// of sm_100 and later (add/sub/mul/fma .f32x2): each lane rounds exactly like
+// the scalar instruction. The pair tile packs two nodes per thread, the
+// one-node tile two velocity columns of one node.
+typedef unsigned long long f32x2;  // two FP32 lanes; low word: node x, or the lower column
+
+__device__ __forceinline__ f32x2 pk2(float a, float b)
+{
+    f32x2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ float lo2(f32x2 v)
+{
+    float a;
+    asm("{ .reg .f32 t; mov.b64 {%0, t}, %1; }" : "=f"(a) : "l"(v));
+    return a;
+}
+__device__ __forceinline__ float hi2(f32x2 v)
+{
+    float b;
+    asm("{ .reg .f32 t; mov.b64 {t, %0}, %1; }" : "=f"(b) : "l"(v));
+    return b;
+}
+__device__ __forceinline__ f32x2 add2(f32x2 a, f32x2 b)
+{
+    f32x2 d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f32x2 sub2(f32x2 a, f32x2 b)
+{
+    f32x2 d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f32x2 mul2(f32x2 a, f32x2 b)
+{
+    f32x2 d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f32x2 fma2(f32x2 a, f32x2 b, f32x2 c)
+{
+    f32x2 d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+
+// Knuth's two-sum on both lanes (the packed form of acc2).
+__device__ __forceinline__ void acc2x2(f32x2 &s, f32x2 &c, f32x2 x)
+{
+    const f32x2 t = add2(s, x);
+    const f32x2 bp = sub2(t, s);
+    const f32x2 err = add2(sub2(s, sub2(t, bp)), sub2(x, bp));
+    s = t;
+    c = add2(c, err);
+}
+
 // Knuth's two-sum: s + x is added to (s, c) with the rounding error of the
 // addition carried in c (compensated summation of the FP32 moments).
 __device__ __forceinline__ void acc2(float &s, float &c, float x)

@@ -361,8 +361,34 @@ struct Step2D {
                 const unsigned hrow = hnode + (unsigned)iy * 0x85EBCA6Bu;
                 const float ua = DEV ? mul_rn(dither_unit(hrow), iom) : 0.0f;
                 const float ub = DEV ? mul_rn(dither_unit(dither_word_b(hrow)), iom) : 0.0f;
+                if constexpr (DEV) {
+                    // velocity columns in pairs (ix, ix + 1) on the two-lane FP32
+                    // instructions: each lane does exactly the scalar operations
+                    // below, in the same order, so the results are those of the
+                    // scalar loop bit for bit; the last column of an odd count
+                    // takes the scalar loop
+                    const f32x2 B2 = pk2(B, B), nwy2 = pk2(nwy, nwy), om2 = pk2(om, om),
+                                gr2 = pk2(gr, gr);
 #pragma unroll
-                for (int ix = 0; ix < QX; ++ix) {
+                    for (int ix = 0; ix + 1 < QX; ix += 2) {
+                        const f32x2 f0 = pk2(f[k][ix], f[k][ix + 1]);
+                        const f32x2 Bn = fma2(pk2(T(AX::vel(ix)), T(AX::vel(ix + 1))), gr2, B2);
+                        const f32x2 dxv = DX_SHARED ? pk2(sm.eqx[r][ix][lane], sm.eqx[r][ix + 1][lane])
+                                                    : pk2(dx[ix], dx[ix + 1]);
+                        const float p0 = __int_as_float(__float_as_int(lo2(f0)) & 0x7F800000);
+                        const float p1 = __int_as_float(__float_as_int(hi2(f0)) & 0x7F800000);
+                        const f32x2 dith = mul2(pk2(dither_pick(ix, ua, ub, -ua, -ub),
+                                                    dither_pick(ix + 1, ua, ub, -ua, -ub)),
+                                                pk2(p0, p1));
+                        const f32x2 t1 = fma2(dxv, B2, fma2(pk2(A::W(tabx, ix), A::W(tabx, ix + 1)), Bn, dith));
+                        const f32x2 rr = fma2(dxv, nwy2, f0);
+                        const f32x2 v2 = fma2(om2, sub2(t1, rr), f0);
+                        op[ix * plane] = lo2(v2);
+                        op[(ix + 1) * plane] = hi2(v2);
+                    }
+                }
+#pragma unroll
+                for (int ix = (DEV ? QX - (QX & 1) : 0); ix < QX; ++ix) {
                     const int nx = AX::vel(ix);
                     const T f0 = f[k][ix];
                     T v;

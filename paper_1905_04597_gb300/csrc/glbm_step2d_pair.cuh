@@ -24,61 +24,6 @@
 #pragma once
 #include "glbm_step2d.cuh"
 
-typedef unsigned long long f32x2;  // two FP32 lanes, low word = node x
-
-__device__ __forceinline__ f32x2 pk2(float a, float b)
-{
-    f32x2 r;
-    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
-    return r;
-}
-__device__ __forceinline__ float lo2(f32x2 v)
-{
-    float a;
-    asm("{ .reg .f32 t; mov.b64 {%0, t}, %1; }" : "=f"(a) : "l"(v));
-    return a;
-}
-__device__ __forceinline__ float hi2(f32x2 v)
-{
-    float b;
-    asm("{ .reg .f32 t; mov.b64 {t, %0}, %1; }" : "=f"(b) : "l"(v));
-    return b;
-}
-__device__ __forceinline__ f32x2 add2(f32x2 a, f32x2 b)
-{
-    f32x2 d;
-    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-    return d;
-}
-__device__ __forceinline__ f32x2 sub2(f32x2 a, f32x2 b)
-{
-    f32x2 d;
-    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-    return d;
-}
-__device__ __forceinline__ f32x2 mul2(f32x2 a, f32x2 b)
-{
-    f32x2 d;
-    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-    return d;
-}
-__device__ __forceinline__ f32x2 fma2(f32x2 a, f32x2 b, f32x2 c)
-{
-    f32x2 d;
-    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
-    return d;
-}
-
-// Knuth's two-sum on both lanes (the packed form of acc2).
-__device__ __forceinline__ void acc2x2(f32x2 &s, f32x2 &c, f32x2 x)
-{
-    const f32x2 t = add2(s, x);
-    const f32x2 bp = sub2(t, s);
-    const f32x2 err = add2(sub2(s, sub2(t, bp)), sub2(x, bp));
-    s = t;
-    c = add2(c, err);
-}
-
 // Wall densities of a pair tile's 64 columns (row a2 of the fused step): the
 // mass streaming into each wall, summed through NV fixed accumulators (pair
 // p mod NV of the (|n_y|, row) pairs) in the order of the one-node tile,
