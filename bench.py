@@ -42,6 +42,12 @@ def workload(name):
         cfgs = [dict(dims=2, nx=c["nx"], ny=c["ny"], k=c["k"], kn=kn, u_wall_lo=c["u_wall_lo"],
                      u_wall_hi=c["u_wall_hi"]) for kn in c["kn"]]
         label = "couette_d2q81_512x256_kn{0.01,0.1,1}"
+    elif name == "couette_4096":
+        # the Couette workload on 4096 x 256: 2.0 GB per step, 16 times L2
+        c = inputs.COUETTE
+        cfgs = [dict(dims=2, nx=4096, ny=c["ny"], k=c["k"], kn=kn, u_wall_lo=c["u_wall_lo"],
+                     u_wall_hi=c["u_wall_hi"]) for kn in c["kn"]]
+        label = "couette_d2q81_4096x256_kn{0.01,0.1,1}"
     elif name == "couette_aniso":
         c = inputs.COUETTE_ANISO
         cfgs = [dict(dims=2, nx=c["nx"], ny=c["ny"], k=c["k"], x_level=c["x_level"], kn=kn,
@@ -254,6 +260,17 @@ def run_ours(args):
                               "data": "synthetic",
                               "config": {"workload": "batched_256_channels_k1-7_ny32-512_nx64"},
                               "batched": res, "gpu_launches": int(args.steps)}), flush=True)
+        return
+    if args.workload == "adjoint":
+        res = measure_adjoint(reps=max(1, args.steps // 4000), warmup_steps=args.warmup)
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "value": res["pop_steps_per_s"], "unit": UNIT,
+                              "n_gpus": world, "steps": res["steps"], "warmup": args.warmup,
+                              "ms_per_step": res["ms_per_step"], "higher_is_better": True,
+                              "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                              "data": "synthetic", "config": {"workload": res["label"]},
+                              "roofline": res["roofline"], "adjoint": res,
+                              "gpu_launches": res["launches"]}), flush=True)
         return
     cfgs, label = workload(args.workload)
     dims = cfgs[0]["dims"]
@@ -478,6 +495,49 @@ def precision_check(cfgs, steps):
             "seconds": time.perf_counter() - t0}
 
 
+ADJ_BYTES_PER_POP = 36  # per population and time step: see measure_adjoint
+
+
+def measure_adjoint(reps=1, warmup_steps=200):
+    """Throughput of the flow-rate gradient (glbm_adjoint_flowrate) on the adjoint
+    workload (D2Q121 256 x 128, Kn 0.1, g 1e-6, FP32 forward, 4000 steps,
+    checkpoints every 100). Per population and time step the algorithmic
+    traffic is 36 bytes: the forward step reads and writes the FP32 state
+    (8 B), the segment recomputed from its checkpoint does it again (8 B), and
+    the adjoint step reads the forward state (4 B) and the FP64 adjoint state
+    of the next step (8 B) and writes the adjoint state (8 B)."""
+    import torch
+    from paper_1905_04597_gb300 import glbm, inputs
+    c = inputs.ADJOINT
+    cfg = dict(dims=2, nx=c["nx"], ny=c["ny"], k=c["k"], kn=c["kn"], g=c["g"], prec=glbm.FP32_DEV)
+    Q = (2 * c["k"] + 3) ** 2
+    pops = Q * c["nx"] * c["ny"]
+    lat = glbm.Lattice(cfg)
+    lat.adjoint_flowrate(warmup_steps, c["ckpt_every"])  # warm-up (graphs, buffers)
+    torch.cuda.synchronize()
+    l0 = lat.kernel_launches
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            J, dtau, dg = lat.adjoint_flowrate(c["steps"], c["ckpt_every"])
+        dt = time.perf_counter() - t0
+    launches = lat.kernel_launches - l0
+    lat.close()
+    steps = c["steps"] * reps
+    peak, peak_kind = peaks()
+    gbs = ADJ_BYTES_PER_POP * pops * steps / dt / 1e9
+    return {"label": f"adjoint_d2q{Q}_{c['nx']}x{c['ny']}_kn{c['kn']}_{c['steps']}steps_ckpt{c['ckpt_every']}",
+            "steps": steps, "ms_per_step": dt / steps * 1e3, "pop_steps_per_s": pops * steps / dt,
+            "solves_per_s": reps / dt, "J": float(J[0]), "dJ_dtau": float(dtau[0]),
+            "dJ_dg": float(dg[0]), "launches": int(launches),
+            "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s",
+                         "frac": gbs / peak, "traffic": None, "peak_source": peak_kind,
+                         "bytes_per_pop_step": ADJ_BYTES_PER_POP,
+                         "timing": "host wall clock around the synchronous call (forward, "
+                                   "checkpoints, recomputed segments and adjoint sweep)"},
+            "clocks": clk.summary()}
+
+
 def measure_batched(steps32=256, steps64=64, warmup=8, autotune=True):
     """Solves/s of the 256-instance heterogeneous batch in FP32 (one persistent
     launch per step) against the same instances in FP64, one context (and one
@@ -529,10 +589,31 @@ def measure_batched(steps32=256, steps64=64, warmup=8, autotune=True):
             "speedup": sps32 / sps64, "steps_per_solve": STEPS_PER_SOLVE}
 
 
-def cpu_baseline(name, budget_s=15.0, steps=None):
-    """The FP64 oracle, as it stands, on this host's cores (single thread) over a
-    bounded sample of the workload: the full lattice of one instance for as many
-    steps as fit the budget (at least one)."""
+def _omp_threads():
+    """Threads an -fopenmp oracle uses here (OMP_NUM_THREADS, else every core)."""
+    try:
+        return max(1, int(os.environ.get("OMP_NUM_THREADS", "")))
+    except ValueError:
+        return os.cpu_count() or 1
+
+
+def _host_cpu():
+    """This host's CPU model and logical core count (lscpu when present)."""
+    model = ""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.lower().startswith("model name"):
+                model = ln.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    return {"model": model or "unknown", "nproc": os.cpu_count()}
+
+
+def _oracle_sample(name, openmp):
+    """(oracle lattice, initial state, populations per step, label, first instance)
+    for one instance of the workload, on the single-thread or the -fopenmp build."""
     from oracle import oracle as orc
     cfgs, label = workload(name)
     c = cfgs[0]
@@ -542,41 +623,61 @@ def cpu_baseline(name, budget_s=15.0, steps=None):
         _, NX, Q1y, Q1x, zv = lattice_axes(c)
         o = orc.Lattice(2, NX, N, c["nx"], c["ny"], orc.BC_WALLS,
                         orc.tau_from_kn(N, c["ny"], c["kn"], zv=zv & 2), c.get("u_wall_lo", 0.0),
-                        c.get("u_wall_hi", 0.0), c.get("g", 0.0), zv=zv)
+                        c.get("u_wall_hi", 0.0), c.get("g", 0.0), zv=zv, openmp=openmp)
         X = o.equilibrium(np.ones((c["ny"], c["nx"])), np.zeros((c["ny"], c["nx"])),
                           np.zeros((c["ny"], c["nx"])))
         pops = Q1y * Q1x * c["nx"] * c["ny"]
     elif dims == 3:
         o = orc.Lattice(3, N, N, c["nx"], c["ny"], orc.BC_WALLS, orc.tau_from_kn(N, c["ny"], c["kn"]),
                         c.get("u_wall_lo", 0.0), c.get("u_wall_hi", 0.0), c.get("g", 0.0),
-                        NZ=N, Lz=c["nz"])
+                        NZ=N, Lz=c["nz"], openmp=openmp)
         shp = (c["nz"], c["ny"], c["nx"])
         X = o.equilibrium(np.ones(shp), np.zeros(shp), np.zeros(shp), np.zeros(shp))
         pops = (2 * N + 1) ** 3 * c["nx"] * c["ny"] * c["nz"]
     else:
-        o = orc.Lattice(1, N, 0, c["nx"], 1, orc.BC_BOUNCEBACK, orc.tau_from_kn(N, c["nx"], c["kn"]))
+        o = orc.Lattice(1, N, 0, c["nx"], 1, orc.BC_BOUNCEBACK,
+                        orc.tau_from_kn(N, c["nx"], c["kn"]), openmp=openmp)
         X = o.equilibrium(np.ones(c["nx"]), np.zeros(c["nx"]))
         pops = (2 * N + 1) * c["nx"]
-    t0 = time.perf_counter()
-    X, _ = o.run(X, 1)
-    one = time.perf_counter() - t0
-    n = steps or max(1, int(budget_s / max(one, 1e-6)) - 1)
-    t0 = time.perf_counter()
-    X, _ = o.run(X, n)
-    dt = time.perf_counter() - t0
-    return {"value": pops * n / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+    return o, X, pops, label, c
+
+
+def cpu_baseline(name, budget_s=15.0, steps=None):
+    """The FP64 oracle, as it stands, on this host's cores over a bounded sample
+    of the workload (the full lattice of one instance for as many steps as fit
+    half the budget, at least one): once on all cores (its -fopenmp build,
+    whose collision runs over rows in parallel with identical results; this is
+    the reported value) and once single-threaded."""
+    out = {}
+    for openmp in (True, False):
+        o, X, pops, label, c = _oracle_sample(name, openmp)
+        t0 = time.perf_counter()
+        X, _ = o.run(X, 1)
+        one = time.perf_counter() - t0
+        n = steps or max(1, int(0.5 * budget_s / max(one, 1e-6)) - 1)
+        t0 = time.perf_counter()
+        X, _ = o.run(X, n)
+        dt = time.perf_counter() - t0
+        out[openmp] = (pops * n / dt, n, dt, label, c)
+    v, n, dt, label, c = out[True]
+    v1, n1, dt1 = out[False][:3]
+    cores = _omp_threads()
+    return {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "host": _host_cpu(),
             "sample": f"{label}: one instance (Kn {c['kn']}), full lattice, {n} steps, FP64, "
-                      f"single thread, {dt:.1f} s"}
+                      f"{cores} threads (collision over rows), {dt:.1f} s",
+            "single_thread": {"value": v1, "unit": UNIT, "cores": 1,
+                              "sample": f"the same lattice, {n1} steps, {dt1:.1f} s"}}
 
 
 def run_reference(args):
-    """The oracle timed as the reference arm: each step one oracle time step of a
-    bounded slab of the workload (a column strip of the lattice)."""
+    """The oracle timed as the reference arm, on all cores (its -fopenmp build):
+    each step one oracle time step of a bounded slab of the workload (a column
+    strip of the lattice)."""
     world, rank, _ = dist_setup()
     if rank != 0:
         return
     from oracle import oracle as orc
-    orc.build()
+    orc.build_openmp()
     cfgs, label = workload(args.workload)
     c = cfgs[0]
     N = c["k"] + 1
@@ -589,7 +690,7 @@ def run_reference(args):
         mk = lambda nx: orc.Lattice(2, NX, N, nx, ny, orc.BC_WALLS,  # noqa: E731
                                     orc.tau_from_kn(N, ny, c["kn"], zv=zv & 2),
                                     c.get("u_wall_lo", 0.0), c.get("u_wall_hi", 0.0),
-                                    c.get("g", 0.0), zv=zv)
+                                    c.get("g", 0.0), zv=zv, openmp=True)
         o = mk(1)
         X = o.equilibrium(np.ones((ny, 1)), np.zeros((ny, 1)), np.zeros((ny, 1)))
         t0 = time.perf_counter()
@@ -604,7 +705,8 @@ def run_reference(args):
         ny, nz = c["ny"], c["nz"]
         mk = lambda nx: orc.Lattice(3, N, N, nx, ny, orc.BC_WALLS,  # noqa: E731
                                     orc.tau_from_kn(N, ny, c["kn"]), c.get("u_wall_lo", 0.0),
-                                    c.get("u_wall_hi", 0.0), c.get("g", 0.0), NZ=N, Lz=nz)
+                                    c.get("u_wall_hi", 0.0), c.get("g", 0.0), NZ=N, Lz=nz,
+                                    openmp=True)
         o = mk(1)
         z1 = np.zeros((nz, ny, 1))
         t0 = time.perf_counter()
@@ -617,7 +719,8 @@ def run_reference(args):
         pops = (2 * N + 1) ** 3 * ny * nz * cols
         sample = f"{label}: slab of {cols} of {c['nx']} x-columns ({ny} x {nz} each), one instance, FP64"
     else:
-        o = orc.Lattice(1, N, 0, c["nx"], 1, orc.BC_BOUNCEBACK, orc.tau_from_kn(N, c["nx"], c["kn"]))
+        o = orc.Lattice(1, N, 0, c["nx"], 1, orc.BC_BOUNCEBACK, orc.tau_from_kn(N, c["nx"], c["kn"]),
+                        openmp=True)
         X = o.equilibrium(np.ones(c["nx"]), np.zeros(c["nx"]))
         pops = (2 * N + 1) * c["nx"]
         sample = f"{label}: full lattice, FP64"
@@ -632,8 +735,9 @@ def run_reference(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
             "config": {"workload": label, "reference": "FP64 CPU oracle (oracle/glbm_oracle.c)"},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": _omp_threads(), "kind": "oracle",
+                             "sample": sample + f", {_omp_threads()} threads (collision over rows)",
+                             "host": _host_cpu()},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -645,8 +749,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=200)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="couette",
-                    choices=["couette", "couette_aniso", "couette_zv", "couette_zv_xy", "couette3d",
-                             "poiseuille", "sod", "batched"])
+                    choices=["couette", "couette_4096", "couette_aniso", "couette_zv",
+                             "couette_zv_xy", "couette3d", "poiseuille", "sod", "batched",
+                             "adjoint"])
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")

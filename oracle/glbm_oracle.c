@@ -558,11 +558,15 @@ int orc_collide(const orc_cfg *c, const double *F, double *X)
     int Lx = c->Lx, Ly = c->Ly;
     size_t plane = (size_t)Lx * Ly;
     double Wx[2 * ORC_MAX_N + 2], Wy[2 * ORC_MAX_N + 2];
-    double Ex[2 * ORC_MAX_N + 2], Ey[2 * ORC_MAX_N + 2];
     orc_axis_eq(&ax, 0.0, Wx);
     orc_axis_eq(&ay, 0.0, Wy);
     double theta_x = orc_axis_theta(&ax);
+    /* every node collides on its own: rows may run on several threads (an
+       -fopenmp build, used only to time the oracle on all cores) with results
+       identical to the serial loop */
+#pragma omp parallel for reduction(+ : bad)
     for (int y = 0; y < Ly; ++y) {
+        double Ex[2 * ORC_MAX_N + 2], Ey[2 * ORC_MAX_N + 2];
         for (int x = 0; x < Lx; ++x) {
             size_t node = (size_t)y * Lx + x;
             double rho = 0.0, jx = 0.0, jy = 0.0;

@@ -41,6 +41,22 @@ def build(force: bool = False) -> str:
     return LIB
 
 
+LIB_OMP = os.path.join(HERE, "liboracle_omp.so")
+
+
+def build_openmp(force: bool = False) -> str:
+    """The same source compiled with -fopenmp: its collision loops over rows run
+    on all cores with results identical to the serial build. Used only to time
+    the oracle as a CPU baseline on every core of a host."""
+    if force or not os.path.exists(LIB_OMP) or os.path.getmtime(LIB_OMP) < os.path.getmtime(SRC):
+        tmp = LIB_OMP + f".tmp{os.getpid()}"
+        subprocess.check_call(
+            ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fopenmp", "-fPIC", "-shared",
+             "-o", tmp, SRC, "-lm"])
+        os.replace(tmp, LIB_OMP)
+    return LIB_OMP
+
+
 class Cfg(ctypes.Structure):
     _fields_ = [("dims", ctypes.c_int), ("NX", ctypes.c_int), ("NY", ctypes.c_int),
                 ("Lx", ctypes.c_int), ("Ly", ctypes.c_int), ("bc", ctypes.c_int),
@@ -52,35 +68,50 @@ class Cfg(ctypes.Structure):
 _lib = None
 
 
+_lib_omp = None
+
+
+def lib_openmp():
+    """The -fopenmp build of the oracle (build_openmp), loaded on first use."""
+    global _lib_omp
+    if _lib_omp is None:
+        _lib_omp = _declare(ctypes.CDLL(build_openmp()))
+    return _lib_omp
+
+
 def lib():
     global _lib
     if _lib is None:
-        _lib = ctypes.CDLL(build())
-        dp = ctypes.POINTER(ctypes.c_double)
-        cp = ctypes.POINTER(Cfg)
-        _lib.orc_prob.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double,
-                                  ctypes.c_double, dp]
-        _lib.orc_prob.restype = ctypes.c_int
-        _lib.orc_eq1d.argtypes = [ctypes.c_int, ctypes.c_double, dp]
-        _lib.orc_weights.argtypes = [ctypes.c_int, dp]
-        _lib.orc_tau_from_kn.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double]
-        _lib.orc_tau_from_kn.restype = ctypes.c_double
-        _lib.orc_eq_axis.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, dp]
-        _lib.orc_tau_from_kn_axis.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double,
-                                              ctypes.c_double]
-        _lib.orc_tau_from_kn_axis.restype = ctypes.c_double
-        for name in ("orc_stream", "orc_collide", "orc_macro", "orc_observe"):
-            getattr(_lib, name).argtypes = [cp, dp, dp]
-            getattr(_lib, name).restype = ctypes.c_int
-        _lib.orc_equilibrium.argtypes = [cp, dp, dp, dp, dp]
-        _lib.orc_equilibrium.restype = ctypes.c_int
-        _lib.orc_equilibrium3d.argtypes = [cp, dp, dp, dp, dp, dp]
-        _lib.orc_equilibrium3d.restype = ctypes.c_int
-        _lib.orc_run.argtypes = [cp, dp, ctypes.c_long]
-        _lib.orc_run.restype = ctypes.c_long
-        _lib.orc_flowrate_grad.argtypes = [cp, dp, ctypes.c_long, dp]
-        _lib.orc_flowrate_grad.restype = ctypes.c_int
+        _lib = _declare(ctypes.CDLL(build()))
     return _lib
+
+
+def _declare(L):
+    """Argument and result types of the oracle's C functions on handle L."""
+    dp = ctypes.POINTER(ctypes.c_double)
+    cp = ctypes.POINTER(Cfg)
+    L.orc_prob.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double, dp]
+    L.orc_prob.restype = ctypes.c_int
+    L.orc_eq1d.argtypes = [ctypes.c_int, ctypes.c_double, dp]
+    L.orc_weights.argtypes = [ctypes.c_int, dp]
+    L.orc_tau_from_kn.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double]
+    L.orc_tau_from_kn.restype = ctypes.c_double
+    L.orc_eq_axis.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, dp]
+    L.orc_tau_from_kn_axis.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                       ctypes.c_double]
+    L.orc_tau_from_kn_axis.restype = ctypes.c_double
+    for name in ("orc_stream", "orc_collide", "orc_macro", "orc_observe"):
+        getattr(L, name).argtypes = [cp, dp, dp]
+        getattr(L, name).restype = ctypes.c_int
+    L.orc_equilibrium.argtypes = [cp, dp, dp, dp, dp]
+    L.orc_equilibrium.restype = ctypes.c_int
+    L.orc_equilibrium3d.argtypes = [cp, dp, dp, dp, dp, dp]
+    L.orc_equilibrium3d.restype = ctypes.c_int
+    L.orc_run.argtypes = [cp, dp, ctypes.c_long]
+    L.orc_run.restype = ctypes.c_long
+    L.orc_flowrate_grad.argtypes = [cp, dp, ctypes.c_long, dp]
+    L.orc_flowrate_grad.restype = ctypes.c_int
+    return L
 
 
 def _dp(a: np.ndarray):
@@ -96,10 +127,12 @@ class Lattice:
     -(2N+1)..2N+1, 2D only)."""
 
     def __init__(self, dims, NX, NY, Lx, Ly, bc, tau, uw_lo=0.0, uw_hi=0.0, g=0.0, zv=0,
-                 NZ=0, Lz=1):
+                 NZ=0, Lz=1, openmp=False):
         self.cfg = Cfg(dims, NX, NY if dims >= 2 else 0, Lx, Ly if dims >= 2 else 1, bc,
                        tau, uw_lo, uw_hi, g, zv, NZ if dims == 3 else 0, Lz if dims == 3 else 1)
         self.dims = dims
+        # openmp: run on the -fopenmp build (same results, all cores; timing only)
+        self._L = lib_openmp() if openmp else lib()
         qx = 2 * NX + (2 if zv & ZV_X else 1)
         qy = 2 * NY + (2 if zv & ZV_Y else 1)
         if dims == 3:
@@ -123,36 +156,36 @@ class Lattice:
         X = np.empty(self.shape)
         if self.dims == 3:
             uz = np.zeros_like(ux) if uz is None else np.ascontiguousarray(uz, dtype=np.float64)
-            self._chk(lib().orc_equilibrium3d(ctypes.byref(self.cfg), _dp(rho), _dp(ux),
+            self._chk(self._L.orc_equilibrium3d(ctypes.byref(self.cfg), _dp(rho), _dp(ux),
                                               _dp(uy), _dp(uz), _dp(X)))
             return X
-        self._chk(lib().orc_equilibrium(ctypes.byref(self.cfg), _dp(rho), _dp(ux), _dp(uy),
+        self._chk(self._L.orc_equilibrium(ctypes.byref(self.cfg), _dp(rho), _dp(ux), _dp(uy),
                                         _dp(X)))
         return X
 
     def stream(self, X):
         X = np.ascontiguousarray(X, dtype=np.float64)
         F = np.empty(self.shape)
-        self._chk(lib().orc_stream(ctypes.byref(self.cfg), _dp(X), _dp(F)))
+        self._chk(self._L.orc_stream(ctypes.byref(self.cfg), _dp(X), _dp(F)))
         return F
 
     def collide(self, F):
         F = np.ascontiguousarray(F, dtype=np.float64)
         X = np.empty(self.shape)
-        bad = self._chk(lib().orc_collide(ctypes.byref(self.cfg), _dp(F), _dp(X)))
+        bad = self._chk(self._L.orc_collide(ctypes.byref(self.cfg), _dp(F), _dp(X)))
         return X, bad
 
     def macro(self, F):
         F = np.ascontiguousarray(F, dtype=np.float64)
         out = np.empty((self.nfields,) + self.shape[1:])
-        self._chk(lib().orc_macro(ctypes.byref(self.cfg), _dp(F), _dp(out)))
+        self._chk(self._L.orc_macro(ctypes.byref(self.cfg), _dp(F), _dp(out)))
         return out
 
     def observe(self, X):
         """Moments at the current time: moments of the streamed state S(X)."""
         X = np.ascontiguousarray(X, dtype=np.float64)
         out = np.empty((self.nfields,) + self.shape[1:])
-        self._chk(lib().orc_observe(ctypes.byref(self.cfg), _dp(X), _dp(out)))
+        self._chk(self._L.orc_observe(ctypes.byref(self.cfg), _dp(X), _dp(out)))
         return out
 
     def flowrate_grad(self, X, steps):
@@ -160,7 +193,7 @@ class Lattice:
         (dJ/dtau, dJ/dg) by forward-mode dual numbers."""
         X = np.ascontiguousarray(X, dtype=np.float64)
         out = np.empty(3)
-        self._chk(lib().orc_flowrate_grad(ctypes.byref(self.cfg), _dp(X), int(steps), _dp(out)))
+        self._chk(self._L.orc_flowrate_grad(ctypes.byref(self.cfg), _dp(X), int(steps), _dp(out)))
         return out[0], out[1], out[2]
 
     def flowrate(self, X, steps):
@@ -173,7 +206,7 @@ class Lattice:
     def run(self, X, steps):
         """Advance a copy of X by `steps` steps; returns (X, unstable_count)."""
         X = np.array(X, dtype=np.float64, order="C", copy=True)
-        bad = self._chk(lib().orc_run(ctypes.byref(self.cfg), _dp(X), int(steps)))
+        bad = self._chk(self._L.orc_run(ctypes.byref(self.cfg), _dp(X), int(steps)))
         return X, bad
 
 
