@@ -52,7 +52,16 @@
  *   - 1D ends use halfway bounce-back;
  *   - the body force is F_i = W_i * xi_{x,i} * g / theta_x added after the
  *     relaxation (the linearised force of Sec. 5.4 written for the lattice
- *     used along the flow).
+ *     used along the flow);
+ *   - or, when orc_cfg.guo is set, the force of Guo, Zheng and Shi (Phys.
+ *     Rev. E 65, 046308, 2002), which the paper does not use: the
+ *     equilibrium and the reported velocity take u = (j + g/2) / rho, and
+ *     F_i = (1 - omega/2) W_i [(xi_i - u).G + (xi_i.U)(xi_i.G)] with
+ *     G_a = g_a / theta_a and U_a = u_a / theta_a per axis (Guo's second-order
+ *     Hermite form, c_s^2 replaced by each axis's temperature). g is a force
+ *     density in both forms: each injects exactly g of x momentum per node and
+ *     step (here omega g/2 through the relaxation towards the shifted u and
+ *     (1 - omega/2) g through F).
  */
 #include <math.h>
 #include <stdlib.h>
@@ -79,6 +88,7 @@ typedef struct {
                      bit 0 (ORC_ZV_X) x, bit 1 (ORC_ZV_Y) y; 0 = none */
     int NZ;       /* level N along z (3D only) */
     int Lz;       /* nodes along z (1 below 3D) */
+    int guo;      /* 1: Guo's force and half-force velocity shift; 0: linearised */
 } orc_cfg;
 
 static double orc_factorial(int n)
@@ -243,6 +253,7 @@ double orc_tau_from_kn(int N, double H, double kn)
 static int orc_check(const orc_cfg *c)
 {
     if (c->zv < 0 || c->zv > 3 || (c->zv && c->dims != 2)) return -1;
+    if (c->guo != 0 && (c->guo != 1 || c->dims == 1)) return -1;
     if (c->dims == 3) {
         if (c->NX < 1 || c->NX > ORC_MAX_N || c->NY < 1 || c->NY > ORC_MAX_N || c->NZ < 1 ||
             c->NZ > ORC_MAX_N)
@@ -482,6 +493,32 @@ int orc_stream(const orc_cfg *c, const double *X, double *F)
 /* ------------------------------------------------------------------------ */
 
 /*
+ * Velocity that the equilibrium and the reported fields use: j / rho, or
+ * (j_x + g/2) / rho along x in Guo's form.
+ */
+static double orc_ux(const orc_cfg *c, double jx, double rho)
+{
+    return (c->guo ? jx + 0.5 * c->g : jx) / rho;
+}
+
+/*
+ * Body force on the population of velocity (vx, vy, vz) at a node of velocity
+ * (ux, uy, uz), W the product of its rest weights, thx, thy, thz the axis
+ * temperatures: linearised W vx g / theta_x (Sec. 5.4), or Guo's
+ * (1 - omega/2) W [(xi - u).G + (xi.U)(xi.G)] with G = (g/theta_x, 0, 0) and
+ * U_a = u_a / theta_a.
+ */
+static double orc_force(const orc_cfg *c, double omega, double W, double vx, double vy,
+                        double vz, double ux, double uy, double uz, double thx, double thy,
+                        double thz)
+{
+    const double Gx = c->g / thx;
+    if (!c->guo) return W * vx * Gx;
+    const double xiU = vx * ux / thx + vy * uy / thy + vz * uz / thz;
+    return (1.0 - 0.5 * omega) * W * ((vx - ux) * Gx + xiU * vx * Gx);
+}
+
+/*
  * BGK relaxation at every node: f* = f + omega (f^eq - f) + F_i with
  * omega = 1/(tau + 1/2), f^eq = rho E^x(u_x) E^y(u_y) (product form, Sec. 4)
  * and rho, rho u the zeroth and first moments of f. Returns the number of
@@ -533,7 +570,7 @@ int orc_collide(const orc_cfg *c, const double *F, double *X)
                         jy += (iy - NY) * f;
                         jz += (iz - NZ) * f;
                     }
-            const double ux = jx / rho, uy = jy / rho, uz = jz / rho;
+            const double ux = orc_ux(c, jx, rho), uy = jy / rho, uz = jz / rho;
             const double b = sqrt(2.0 / 3.0);
             if (!(rho > 0.0) || fabs(ux) > b * NX || fabs(uy) > b * NY || fabs(uz) > b * NZ) ++bad;
             orc_eq_lattice(NX, ux, Ex);
@@ -545,7 +582,9 @@ int orc_collide(const orc_cfg *c, const double *F, double *X)
                         const size_t idx = ((iz * Qy + iy) * Qx + ix) * plane + node;
                         const double f = F[idx];
                         const double feq = rho * Ex[ix] * Ey[iy] * Ez[iz];
-                        const double force = Wx[ix] * Wy[iy] * Wz[iz] * (ix - NX) * c->g / theta_x;
+                        const double force =
+                            orc_force(c, omega, Wx[ix] * Wy[iy] * Wz[iz], ix - NX, iy - NY, iz - NZ,
+                                      ux, uy, uz, theta_x, NY / 3.0, NZ / 3.0);
                         X[idx] = f + omega * (feq - f) + force;
                     }
         }
@@ -560,7 +599,7 @@ int orc_collide(const orc_cfg *c, const double *F, double *X)
     double Wx[2 * ORC_MAX_N + 2], Wy[2 * ORC_MAX_N + 2];
     orc_axis_eq(&ax, 0.0, Wx);
     orc_axis_eq(&ay, 0.0, Wy);
-    double theta_x = orc_axis_theta(&ax);
+    double theta_x = orc_axis_theta(&ax), theta_y = orc_axis_theta(&ay);
     /* every node collides on its own: rows may run on several threads (an
        -fopenmp build, used only to time the oracle on all cores) with results
        identical to the serial loop */
@@ -578,7 +617,7 @@ int orc_collide(const orc_cfg *c, const double *F, double *X)
                     jy += ay.v[iy] * f;
                 }
             }
-            double ux = jx / rho, uy = jy / rho;
+            double ux = orc_ux(c, jx, rho), uy = jy / rho;
             if (!(rho > 0.0) || fabs(ux) > orc_axis_umax(&ax) || fabs(uy) > orc_axis_umax(&ay))
                 ++bad;
             orc_axis_eq(&ax, ux, Ex);
@@ -588,7 +627,8 @@ int orc_collide(const orc_cfg *c, const double *F, double *X)
                     size_t idx = (iy * ax.Q + ix) * plane + node;
                     double f = F[idx];
                     double feq = rho * Ex[ix] * Ey[iy];
-                    double force = Wx[ix] * Wy[iy] * ax.v[ix] * c->g / theta_x;
+                    double force = orc_force(c, omega, Wx[ix] * Wy[iy], ax.v[ix], ay.v[iy], 0.0,
+                                             ux, uy, 0.0, theta_x, theta_y, 1.0);
                     X[idx] = f + omega * (feq - f) + force;
                 }
             }
@@ -603,7 +643,8 @@ int orc_collide(const orc_cfg *c, const double *F, double *X)
 
 /*
  * Moments of populations F at every node (Sec. 2 for rho, rho u; the
- * temperature, heat flux and shear stress are the usual central moments):
+ * temperature, heat flux and shear stress are the usual central moments,
+ * taken about u; u_x = (j_x + g/2) / rho in Guo's form):
  * 2D out[7][Ly][Lx] = rho, u_x, u_y, T = sum |xi-u|^2 f / (2 rho),
  *   q_x, q_y = (1/2) sum (xi-u)_a |xi-u|^2 f, sigma_xy = sum (xi-u)_x (xi-u)_y f;
  * 1D out[4][L] = rho, u, T = sum (xi-u)^2 f / rho, q = (1/2) sum (xi-u)^3 f;
@@ -628,7 +669,7 @@ int orc_macro(const orc_cfg *c, const double *F, double *out)
                         jy += (iy - NY) * f;
                         jz += (iz - NZ) * f;
                     }
-            const double ux = jx / rho, uy = jy / rho, uz = jz / rho;
+            const double ux = orc_ux(c, jx, rho), uy = jy / rho, uz = jz / rho;
             double e2 = 0.0, qx = 0.0, qy = 0.0, qz = 0.0, sxy = 0.0;
             for (int iz = 0; iz < Qz; ++iz)
                 for (int iy = 0; iy < Qy; ++iy)
@@ -682,7 +723,7 @@ int orc_macro(const orc_cfg *c, const double *F, double *out)
                 jy += ay.v[iy] * f;
             }
         }
-        double ux = jx / rho, uy = jy / rho;
+        double ux = orc_ux(c, jx, rho), uy = jy / rho;
         double e2 = 0.0, qx = 0.0, qy = 0.0, sxy = 0.0;
         for (int iy = 0; iy < ay.Q; ++iy) {
             for (int ix = 0; ix < ax.Q; ++ix) {
@@ -905,7 +946,7 @@ static void orc_collide_dual(const orc_cfg *c, const double *F, double *X)
  */
 int orc_flowrate_grad(const orc_cfg *c, const double *X0, long steps, double *out)
 {
-    if (orc_check(c) || c->dims != 2 || c->zv) return -1;  /* the 2N+1 hierarchy only */
+    if (orc_check(c) || c->dims != 2 || c->zv || c->guo) return -1;  /* 2N+1, linearised force */
     const size_t plane = (size_t)c->Lx * c->Ly;
     const size_t n = (size_t)orc_nq(c) * plane;
     double *X = (double *)calloc(3 * n, sizeof(double));

@@ -62,7 +62,7 @@ class Cfg(ctypes.Structure):
                 ("Lx", ctypes.c_int), ("Ly", ctypes.c_int), ("bc", ctypes.c_int),
                 ("tau", ctypes.c_double), ("uw_lo", ctypes.c_double),
                 ("uw_hi", ctypes.c_double), ("g", ctypes.c_double), ("zv", ctypes.c_int),
-                ("NZ", ctypes.c_int), ("Lz", ctypes.c_int)]
+                ("NZ", ctypes.c_int), ("Lz", ctypes.c_int), ("guo", ctypes.c_int)]
 
 
 _lib = None
@@ -124,12 +124,15 @@ class Lattice:
     boundary kind, relaxation time, wall speeds and body force, all in lattice
     units (velocities are the integers -N..N; on an axis that zv selects,
     ZV_X = 1 and/or ZV_Y = 2, the 2N+2 hierarchy's odd integers
-    -(2N+1)..2N+1, 2D only)."""
+    -(2N+1)..2N+1, 2D only). guo=1 takes the force of Guo, Zheng and Shi
+    (2002) with the half-force velocity shift instead of the paper's
+    linearised force (2D and 3D)."""
 
     def __init__(self, dims, NX, NY, Lx, Ly, bc, tau, uw_lo=0.0, uw_hi=0.0, g=0.0, zv=0,
-                 NZ=0, Lz=1, openmp=False):
+                 NZ=0, Lz=1, openmp=False, guo=0):
         self.cfg = Cfg(dims, NX, NY if dims >= 2 else 0, Lx, Ly if dims >= 2 else 1, bc,
-                       tau, uw_lo, uw_hi, g, zv, NZ if dims == 3 else 0, Lz if dims == 3 else 1)
+                       tau, uw_lo, uw_hi, g, zv, NZ if dims == 3 else 0, Lz if dims == 3 else 1,
+                       int(guo))
         self.dims = dims
         # openmp: run on the -fopenmp build (same results, all cores; timing only)
         self._L = lib_openmp() if openmp else lib()

@@ -20,8 +20,8 @@ MUTATIONS = {
                         "orc_factorial(n) * orc_factorial(m)"),
     "mirror not swapped": ("        Pp = Pm;\n        Pm = t;\n", "        (void)t;\n"),
     "omega without 1/2": ("double omega = 1.0 / (c->tau + 0.5);", "double omega = 1.0 / c->tau;"),
-    "force sign": ("* ax.v[ix] * c->g / theta_x", "* (-ax.v[ix]) * c->g / theta_x"),
-    "force theta": ("* ax.v[ix] * c->g / theta_x", "* ax.v[ix] * c->g"),
+    "force sign": ("if (!c->guo) return W * vx * Gx;", "if (!c->guo) return -W * vx * Gx;"),
+    "force theta": ("const double Gx = c->g / thx;", "const double Gx = c->g;"),
     "stream x sign": ("int xd = orc_wrap(x + nx, Lx);", "int xd = orc_wrap(x - nx, Lx);"),
     "wall speeds swapped": ("orc_axis_eq(&ax, c->uw_lo, Elo);", "orc_axis_eq(&ax, c->uw_hi, Elo);"),
     "emission rows": ("for (int k = 0; k < (ny > 0 ? ny : -ny); ++k) {",
@@ -49,7 +49,7 @@ MUTATIONS = {
                                   "    double theta = N / 3.0;\n    return kn * H / sqrt(theta);"),
     "3D heat flux without 1/2": ("e2 / (3.0 * rho), 0.5 * qx, 0.5 * qy", "e2 / (3.0 * rho), qx, 0.5 * qy"),
     "1D heat flux without 1/2": ("out[3 * L + x] = 0.5 * e3;", "out[3 * L + x] = e3;"),
-    "3D force sign": ("* (ix - NX) * c->g / theta_x", "* (NX - ix) * c->g / theta_x"),
+    "3D force sign": ("Wx[ix] * Wy[iy] * Wz[iz], ix - NX, iy - NY", "Wx[ix] * Wy[iy] * Wz[iz], NX - ix, iy - NY"),
     "3D force theta": ("        const double theta_x = NX / 3.0;\n", "        const double theta_x = NX;\n"),
     "tangent of g without theta": ("const double wxg = Wx[nx + NX] * Wy[ny + NY] * nx / theta_x;",
                                    "const double wxg = Wx[nx + NX] * Wy[ny + NY] * nx;"),
@@ -60,12 +60,25 @@ MUTATIONS = {
     "tangent of u without rho term": ("dux[d] = (jx[d] - ux * rho[d]) / rho[0];", "dux[d] = jx[d] / rho[0];"),
     "tangents not streamed": ("        for (int d = 0; d < 3; ++d) orc_stream2d(c, X + d * n, F + d * n);\n        orc_collide_dual",
                               "        for (int d = 0; d < 1; ++d) orc_stream2d(c, X + d * n, F + d * n);\n        orc_collide_dual"),
-    "force theta of the y axis": ("double theta_x = orc_axis_theta(&ax);", "double theta_x = orc_axis_theta(&ay);"),
+    "force theta of the y axis": ("double theta_x = orc_axis_theta(&ax), theta_y", "double theta_x = orc_axis_theta(&ay), theta_y"),
     "collision x axis with the y flag": ("    orc_axis_make(c->NX, ORC_ZVX(c), &ax);\n    orc_axis_make(c->NY, ORC_ZVY(c), &ay);\n    int Lx = c->Lx, Ly = c->Ly;\n    size_t plane = (size_t)Lx * Ly;\n    double Wx[",
                                          "    orc_axis_make(c->NX, ORC_ZVY(c), &ax);\n    orc_axis_make(c->NY, ORC_ZVY(c), &ay);\n    int Lx = c->Lx, Ly = c->Ly;\n    size_t plane = (size_t)Lx * Ly;\n    double Wx["),
     "m sum one term short": ("for (int m = 0; m <= (N - n) / 2; ++m) {", "for (int m = 0; m < (N - n) / 2; ++m) {"),
     "P0 power": ("pow(P0, N - n - 2 * m);", "pow(P0, N - n - m);"),
     "P0 closure sign": ("*P0 = 1.0 - *Pp - *Pm;", "*P0 = 1.0 - *Pp + *Pm;"),
+    "Guo without (1 - omega/2)": ("return (1.0 - 0.5 * omega) * W * ((vx - ux) * Gx + xiU * vx * Gx);",
+                                  "return W * ((vx - ux) * Gx + xiU * vx * Gx);"),
+    "Guo without the half-force shift": ("return (c->guo ? jx + 0.5 * c->g : jx) / rho;",
+                                         "return jx / rho;"),
+    "Guo shift of a whole g": ("return (c->guo ? jx + 0.5 * c->g : jx) / rho;",
+                               "return (c->guo ? jx + c->g : jx) / rho;"),
+    "Guo without the -u term": ("((vx - ux) * Gx + xiU * vx * Gx)", "(vx * Gx + xiU * vx * Gx)"),
+    "Guo xi.U without y": ("const double xiU = vx * ux / thx + vy * uy / thy + vz * uz / thz;",
+                           "const double xiU = vx * ux / thx + vz * uz / thz;"),
+    "Guo xi.U with theta_x on y": ("const double xiU = vx * ux / thx + vy * uy / thy + vz * uz / thz;",
+                                   "const double xiU = vx * ux / thx + vy * uy / thx + vz * uz / thz;"),
+    "Guo moments without the shift": ("        double ux = orc_ux(c, jx, rho), uy = jy / rho;\n        double e2",
+                                      "        double ux = jx / rho, uy = jy / rho;\n        double e2"),
     "3D x and z swapped in q": ("const double f = F[((iz * Qy + iy) * Qx + ix) * plane + node];\n                        rho += f;",
                                 "const double f = F[((ix * Qy + iy) * Qx + iz) * plane + node];\n                        rho += f;"),
 }
@@ -88,6 +101,7 @@ def test_pins_catch_planted_mistake(name, tmp_path):
                         os.path.join(ROOT, "tests", "test_oracle_gradient.py"),
                         os.path.join(ROOT, "tests", "test_oracle_aniso.py"),
                         os.path.join(ROOT, "tests", "test_oracle_zv.py"),
-                        os.path.join(ROOT, "tests", "test_oracle_3d.py")],
+                        os.path.join(ROOT, "tests", "test_oracle_3d.py"),
+                        os.path.join(ROOT, "tests", "test_oracle_guo.py")],
                        cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
     assert r.returncode != 0, f"pins did not catch mutation {name!r}"
