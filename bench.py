@@ -249,28 +249,40 @@ def run_ours(args):
     from paper_1905_04597_gb300 import glbm
 
     if args.workload == "batched":
-        res = measure_batched(steps32=args.steps, steps64=max(args.steps // 8, 8),
-                              warmup=args.warmup, autotune=args.tiles == "autotune")
+        with ClockSampler(local) as clk:
+            res = measure_batched(steps32=args.steps, steps64=max(args.steps // 8, 8),
+                                  warmup=args.warmup, autotune=args.tiles == "autotune",
+                                  rank=rank, world=world)
         if rank == 0:
             b = res["fp32_batched"]
+            cpu = cpu_baseline_batched() if not args.no_cpu_baseline and world == 1 else None
             print(json.dumps({"metric": METRIC, "value": b["pop_updates_per_s"], "unit": UNIT,
                               "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
                               "ms_per_step": b["ms_per_step"], "higher_is_better": True,
-                              "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                              "scaling": "strong", "vs_baseline": None, "dtype": "f32",
                               "data": "synthetic",
-                              "config": {"workload": "batched_256_channels_k1-7_ny32-512_nx64"},
-                              "batched": res, "gpu_launches": int(args.steps)}), flush=True)
+                              "config": {"workload": "batched_256_channels_k1-7_ny32-512_nx64",
+                                         "parallelism": f"the 256 instances split by population "
+                                                        f"bytes over {world} rank(s), no "
+                                                        f"data-path collective",
+                                         "l2": "2.6 GB of populations per buffer set; no flush"},
+                              "batched": res, "clocks": clk.summary(), "cpu_baseline": cpu,
+                              "gpu_launches": int(round(b["launches_per_step"] * args.steps))}),
+                  flush=True)
         return
     if args.workload == "adjoint":
-        res = measure_adjoint(reps=max(1, args.steps // 4000), warmup_steps=args.warmup)
+        with ClockSampler(local) as clk:
+            res = measure_adjoint(reps=max(1, args.steps // 4000), warmup_steps=args.warmup)
         if rank == 0:
+            cpu = (cpu_baseline_adjoint(args.cpu_seconds)
+                   if not args.no_cpu_baseline and world == 1 else None)
             print(json.dumps({"metric": METRIC, "value": res["pop_steps_per_s"], "unit": UNIT,
                               "n_gpus": world, "steps": res["steps"], "warmup": args.warmup,
                               "ms_per_step": res["ms_per_step"], "higher_is_better": True,
                               "scaling": "weak", "vs_baseline": None, "dtype": "f32",
                               "data": "synthetic", "config": {"workload": res["label"]},
-                              "roofline": res["roofline"], "adjoint": res,
-                              "gpu_launches": res["launches"]}), flush=True)
+                              "roofline": res["roofline"], "adjoint": res, "clocks": clk.summary(),
+                              "cpu_baseline": cpu, "gpu_launches": res["launches"]}), flush=True)
         return
     cfgs, label = workload(args.workload)
     dims = cfgs[0]["dims"]
@@ -395,7 +407,7 @@ def run_ours(args):
         fp64_roof = {"bound": "alu", "achieved": ach, "peak": pk, "unit": "G FP64 inst/s",
                      "frac": ach / pk, "hbm_frac": gbs64 / peak,
                      "dp_flops_per_pop": rec["dp_flops_per_launch"] / pops_per_step}
-    batched = (measure_batched(autotune=args.tiles == "autotune")
+    batched = (measure_batched(autotune=args.tiles == "autotune", rank=rank, world=world)
                if (args.workload == "couette" and not args.no_batched) else None)
 
     cpu = None
@@ -538,16 +550,43 @@ def measure_adjoint(reps=1, warmup_steps=200):
             "clocks": clk.summary()}
 
 
-def measure_batched(steps32=256, steps64=64, warmup=8, autotune=True):
-    """Solves/s of the 256-instance heterogeneous batch in FP32 (one persistent
-    launch per step) against the same instances in FP64, one context (and one
-    launch per step) per instance."""
-    import torch
-    from paper_1905_04597_gb300 import glbm, inputs
+def batch_share(rank, world):
+    """This rank's instances of the 256-channel batch: the batch split across
+    the ranks by population bytes (shard.partition_by_bytes), with the split's
+    balance."""
+    from paper_1905_04597_gb300 import inputs, shard
     recipe = inputs.batched_instances(seed=0)
-    pops = sum((2 * r["k"] + 3) ** 2 * r["nx"] * r["ny"] for r in recipe)
+    sizes = [shard.instance_bytes(r) for r in recipe]
+    parts = shard.partition_by_bytes(sizes, world)
+    loads = [sum(sizes[i] for i in p) for p in parts]
+    return ([recipe[i] for i in parts[rank]], recipe,
+            {"instances": len(parts[rank]), "bytes": loads[rank],
+             "max_share_over_mean": max(loads) * world / sum(loads)})
+
+
+def measure_batched(steps32=256, steps64=64, warmup=8, autotune=True, rank=0, world=1):
+    """Solves/s of the 256-instance heterogeneous batch in FP32 (one launch per
+    level present per step) against the same instances in FP64, one context
+    (and one launch per step) per instance. With several ranks each steps its
+    byte-balanced share of the batch (no data-path collective), and the batch's
+    time is the slowest rank's (strong scaling: the batch is fixed)."""
+    import torch
+    from paper_1905_04597_gb300 import glbm
+    recipe, recipe_all, share = batch_share(rank, world)
+
+    def pops_of(rs):
+        return sum((2 * r["k"] + 3) ** 2 * r["nx"] * r["ny"] for r in rs)
+
+    pops = pops_of(recipe_all)
     stream = torch.cuda.current_stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def barrier():
+        import torch.distributed as dist
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
     lat = glbm.Lattice([dict(dims=2, prec=glbm.FP32_DEV, **r) for r in recipe], hetero=True)
     if autotune:
         lat.autotune(reps=5)
@@ -555,37 +594,37 @@ def measure_batched(steps32=256, steps64=64, warmup=8, autotune=True):
     lat.step(warmup)
     lat.sync()
     l0 = lat.kernel_launches
-    torch.cuda.synchronize()
+    barrier()
     e0.record(stream)
     lat.step(steps32)
     e1.record(stream)
-    torch.cuda.synchronize()
-    ms32 = e0.elapsed_time(e1)
+    barrier()
+    ms32 = max_over_ranks(e0.elapsed_time(e1))
     launches32 = lat.kernel_launches - l0
     lat.close()
     singles = [glbm.Lattice(dict(dims=2, prec=glbm.FP64, **r)) for r in recipe]
     for x in singles:
         x.step(2)
-    torch.cuda.synchronize()
+    barrier()
     e0.record(stream)
     for x in singles:
         x.step(steps64)
     e1.record(stream)
-    torch.cuda.synchronize()
-    ms64 = e0.elapsed_time(e1)
+    barrier()
+    ms64 = max_over_ranks(e0.elapsed_time(e1))
     for x in singles:
         x.close()
-    sps32 = steps32 / (ms32 / 1e3)          # steps/s of all 256 instances
+    sps32 = steps32 / (ms32 / 1e3)          # steps/s of the whole batch
     sps64 = steps64 / (ms64 / 1e3)
-    n = len(recipe)
-    return {"instances": n, "pop_updates_per_step": pops,
+    n = len(recipe_all)
+    return {"instances": n, "pop_updates_per_step": pops, "ranks": world, "rank0_share": share,
             "fp32_batched": {"solves_per_s": n * sps32 / STEPS_PER_SOLVE, "tiles": tiles,
                              "pop_updates_per_s": pops * sps32, "ms_per_step": ms32 / steps32,
                              "launches_per_step": launches32 / steps32},
             "fp64_one_instance_per_launch": {"solves_per_s": n * sps64 / STEPS_PER_SOLVE,
                                              "pop_updates_per_s": pops * sps64,
                                              "ms_per_step": ms64 / steps64,
-                                             "launches_per_step": n},
+                                             "launches_per_step": len(recipe)},
             "speedup": sps32 / sps64, "steps_per_solve": STEPS_PER_SOLVE}
 
 
@@ -667,6 +706,64 @@ def cpu_baseline(name, budget_s=15.0, steps=None):
                       f"{cores} threads (collision over rows), {dt:.1f} s",
             "single_thread": {"value": v1, "unit": UNIT, "cores": 1,
                               "sample": f"the same lattice, {n1} steps, {dt1:.1f} s"}}
+
+
+def cpu_baseline_batched():
+    """The FP64 oracle over one step of every instance of the 256-channel batch
+    (about 0.65 G population updates), on all cores and single-threaded: a
+    sample with the batch's own mix of levels, sizes and boundary kinds."""
+    from oracle import oracle as orc
+    cfgs, label = workload("batched")
+    out = {}
+    for openmp in (True, False):
+        pops, dt = 0, 0.0
+        for c in cfgs:
+            N = c["k"] + 1
+            o = orc.Lattice(2, N, N, c["nx"], c["ny"], orc.BC_WALLS,
+                            orc.tau_from_kn(N, c["ny"], c["kn"]), c["u_wall_lo"], c["u_wall_hi"],
+                            c["g"], openmp=openmp)
+            shp = (c["ny"], c["nx"])
+            X = o.equilibrium(np.ones(shp), np.zeros(shp), np.zeros(shp))
+            t0 = time.perf_counter()
+            o.run(X, 1)
+            dt += time.perf_counter() - t0
+            pops += (2 * N + 1) ** 2 * c["nx"] * c["ny"]
+        out[openmp] = (pops / dt, dt)
+    cores = _omp_threads()
+    return {"value": out[True][0], "unit": UNIT, "cores": cores, "kind": "oracle",
+            "host": _host_cpu(),
+            "sample": f"{label}: one step of each of the {len(cfgs)} instances, FP64, {cores} "
+                      f"threads (collision over rows), {out[True][1]:.1f} s",
+            "single_thread": {"value": out[False][0], "unit": UNIT, "cores": 1,
+                              "sample": f"the same, {out[False][1]:.1f} s"}}
+
+
+def cpu_baseline_adjoint(budget_s=15.0):
+    """The oracle's gradient of the flow rate (forward-mode dual numbers: the
+    state and its tau and g tangents in one pass, single-threaded) on the
+    adjoint workload's lattice, for as many steps from rest as fit about the
+    budget; per population and time step, as the GPU figure counts."""
+    from oracle import oracle as orc
+    from paper_1905_04597_gb300 import inputs
+    c = inputs.ADJOINT
+    N = c["k"] + 1
+    o = orc.Lattice(2, N, N, c["nx"], c["ny"], orc.BC_WALLS, orc.tau_from_kn(N, c["ny"], c["kn"]),
+                    0.0, 0.0, c["g"])
+    shp = (c["ny"], c["nx"])
+    X = o.equilibrium(np.ones(shp), np.zeros(shp), np.zeros(shp))
+    t0 = time.perf_counter()
+    o.flowrate_grad(X, 1)
+    one = time.perf_counter() - t0
+    n = max(1, int(budget_s / max(one, 1e-6)))
+    t0 = time.perf_counter()
+    o.flowrate_grad(X, n)
+    dt = time.perf_counter() - t0
+    pops = (2 * N + 1) ** 2 * c["nx"] * c["ny"]
+    return {"value": pops * n / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "host": _host_cpu(),
+            "sample": f"D2Q{(2 * N + 1) ** 2} {c['nx']}x{c['ny']}, Kn {c['kn']}: J and its tau "
+                      f"and g derivatives by dual numbers over {n} steps, FP64, one thread, "
+                      f"{dt:.1f} s"}
 
 
 def run_reference(args):

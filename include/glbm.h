@@ -65,6 +65,11 @@ typedef enum {
     GLBM_ZV_Y = 2            /* y axis on the 2N+2 hierarchy */
 } glbm_zv;
 
+typedef enum {
+    GLBM_FORCE_LINEAR = 0,   /* F_i = W_i xi_x g / theta_x, the linearised force of Sec. 5.4 */
+    GLBM_FORCE_GUO = 1       /* Guo, Zheng and Shi (2002); not used by the paper */
+} glbm_force;
+
 /*
  * One lattice instance.
  *   dims      1, 2 or 3.
@@ -89,7 +94,9 @@ typedef enum {
  *   bc, prec  glbm_bc, glbm_prec.
  *   u_wall_lo, u_wall_hi  x-velocities of the walls (GLBM_BC_WALLS).
  *   g         body force along x (2D), added after relaxation as
- *             F_i = W_i xi_x g / theta_x (the linearised force of Sec. 5.4).
+ *             F_i = W_i xi_x g / theta_x (the linearised force of Sec. 5.4),
+ *             or in Guo's form (see force). Either way g is a force density:
+ *             every node gains exactly g of x momentum per step.
  *   zv_axes   axes of a 2D lattice on the 2N+2 hierarchy of Sec. 4 (the zero
  *             velocity removed, Eqs. maineq01_noball - maineq04_noball), a
  *             mask of glbm_zv; 0 keeps the 2N+1 hierarchy. Such an axis has
@@ -111,6 +118,18 @@ typedef enum {
  *             with q = (n_z + N) (2N+1)^2 + (n_y + N) (2N+1) + (n_x + N);
  *             ny * nz <= 65535. Ignored below 3D. Not for heterogeneous
  *             batches or the adjoint.
+ *   force     glbm_force. GLBM_FORCE_GUO takes the force of Guo, Zheng and
+ *             Shi (Phys. Rev. E 65, 046308, 2002) instead of the paper's: the
+ *             equilibrium and the reported velocity use u = (j + g/2) / rho,
+ *             j = sum xi f, and F_i = (1 - omega/2) W_i [(xi_i - u).G +
+ *             (xi_i.U)(xi_i.G)] with G = (g / theta_x, 0) and U_a = u_a /
+ *             theta_a (Guo's second-order term, each axis's temperature in
+ *             place of c_s^2). 2D lattices with k <= 7, isotropic, D1Q3 x
+ *             level k+1 (x_level 1) or D1Q3 x the 2N+2 axis (zv_axes
+ *             GLBM_ZV_Y); one tile shape per level (glbm_tune has nothing to
+ *             choose); not for heterogeneous batches or the adjoint
+ *             (GLBM_E_UNSUPPORTED). Every instance of a context takes the
+ *             same form.
  */
 typedef struct {
     int dims;
@@ -125,6 +144,7 @@ typedef struct {
     double g;
     int zv_axes;
     int nz;
+    int force;
 } glbm_config;
 
 /*
@@ -230,7 +250,9 @@ glbm_status glbm_moments(glbm_ctx *ctx, int inst, unsigned mask, double *out, si
                          int out_on_device);
 
 /* Global FP64 sums at the current time: total mass, x- and y-momentum of
- * instance `inst` (fixed-order block reduction, deterministic). Synchronises. */
+ * instance `inst` (fixed-order block reduction, deterministic): sum rho,
+ * sum rho u_x, sum rho u_y over the moments of S(X), so with Guo's force the
+ * x-momentum is that of the shifted velocity, sum (j_x + g/2). Synchronises. */
 glbm_status glbm_conservation(glbm_ctx *ctx, int inst, double *mass, double *mom_x,
                               double *mom_y);
 

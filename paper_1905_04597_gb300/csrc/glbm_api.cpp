@@ -201,6 +201,13 @@ static void fill_inst(const glbm_ctx *c, const glbm_config &cfg, const Geo &g, I
         ip.dw_hi_f[n] = (float)(dhi * cfg.u_wall_hi);
     }
     ip.g_theta_om = ip.g_theta / ip.omega;
+    if (cfg.force == GLBM_FORCE_GUO) {
+        // Guo's form: F_i carries (1 - omega/2) g, the relaxation towards the
+        // half-force-shifted u the other omega g/2
+        ip.g_theta_om *= 1.0 - 0.5 * ip.omega;
+        ip.g_half = 0.5 * cfg.g;
+    }
+    ip.g_half_f = (float)ip.g_half;
     ip.omega_f = (float)ip.omega;
     ip.g_theta_f = (float)ip.g_theta;
     ip.g_theta_om_f = (float)ip.g_theta_om;
@@ -218,6 +225,16 @@ static void fill_inst(const glbm_ctx *c, const glbm_config &cfg, const Geo &g, I
 static glbm_status validate(const glbm_config &c)
 {
     if (c.dims < 1 || c.dims > 3) return fail(GLBM_E_INVAL, "dims must be 1, 2 or 3 (got %d)", c.dims);
+    if (c.force != GLBM_FORCE_LINEAR && c.force != GLBM_FORCE_GUO)
+        return fail(GLBM_E_INVAL, "force must be GLBM_FORCE_LINEAR or GLBM_FORCE_GUO (got %d)", c.force);
+    if (c.force == GLBM_FORCE_GUO) {
+        if (c.dims != 2) return fail(GLBM_E_UNSUPPORTED, "Guo's force is compiled for 2D lattices");
+        if (c.k > GLBM_MAXN_2N1 - 1)
+            return fail(GLBM_E_UNSUPPORTED, "Guo's force is compiled for k <= %d", GLBM_MAXN_2N1 - 1);
+        if (c.zv_axes == (GLBM_ZV_X | GLBM_ZV_Y))
+            return fail(GLBM_E_UNSUPPORTED,
+                        "Guo's force is compiled for the 2N+2 hierarchy along y only");
+    }
     if (c.dims == 3) {
         if (c.k < 0 || c.k > GLBM_MAXN_3D - 1)
             return fail(GLBM_E_UNSUPPORTED, "3D lattices take k in 0..%d (got %d)", GLBM_MAXN_3D - 1, c.k);
@@ -531,6 +548,7 @@ extern "C" glbm_status glbm_create(const glbm_config *cfgs, int n, void *stream,
             make_geo(a).zv != make_geo(b).zv)
             return fail(GLBM_E_UNSUPPORTED,
                         "instances differ in geometry; use glbm_batch_create for mixed batches");
+        if (a.force != b.force) return fail(GLBM_E_UNSUPPORTED, "instances differ in the force form");
     }
     if (cfgs[0].dims == 3 && (long long)n * cfgs[0].nz > 65535)
         return fail(GLBM_E_UNSUPPORTED, "3D contexts take instances * nz <= 65535");
@@ -555,9 +573,17 @@ static int zv_kind(const glbm_ctx *c)
     return c->geo[0].zv == GLBM_ZV_Y ? GLBM_ZVK_X1 : GLBM_ZVK_XY;
 }
 
+// Whether the context steps with Guo's force, and its lattice kind.
+static bool is_guo(const glbm_ctx *c) { return !c->hetero && c->cfg[0].force == GLBM_FORCE_GUO; }
+static int guo_kind(const glbm_ctx *c)
+{
+    return is_zv(c) ? GLBM_GUOK_ZV : is_x1(c) ? GLBM_GUOK_X1 : GLBM_GUOK_ISO;
+}
+
 // Candidate tile shapes of level N for this context's lattices.
 static int ctx_tile_shapes(const glbm_ctx *c, int N, TileShape *out)
 {
+    if (is_guo(c)) return glbm_tile_shape_guo(N, guo_kind(c), c->prec, out);
     if (c->dims == 3) return glbm_tile_shapes_3d(N, c->prec, out);
     if (is_zv(c)) return glbm_tile_shapes_zv(N, zv_kind(c), c->prec, out);
     return is_x1(c) ? glbm_tile_shapes_x1(N, c->prec, out) : glbm_tile_shapes(N, c->prec, out);
@@ -614,6 +640,8 @@ extern "C" glbm_status glbm_batch_create(const glbm_config *cfgs, int n, void *s
             return fail(GLBM_E_UNSUPPORTED,
                         "heterogeneous batches store FP32 deviations (FP64 instances go through "
                         "glbm_create)");
+        if (cfgs[i].force != GLBM_FORCE_LINEAR)
+            return fail(GLBM_E_UNSUPPORTED, "heterogeneous batches take the linearised force");
     }
     glbm_ctx *c = new (std::nothrow) glbm_ctx();
     if (!c) return fail(GLBM_E_NOMEM, "host allocation failed");
@@ -900,6 +928,7 @@ static cudaError_t launch_one_2d(const glbm_ctx *c, int from, cudaStream_t s)
         return glbm_launch_step2d_zv_hi(N, c->prec, c->tile[N],
                                         step_args_t<AxisTableHi>(c, from), c->n_inst, s);
     const Step2DArgs a = step_args(c, from);
+    if (is_guo(c)) return glbm_launch_step2d_guo(N, guo_kind(c), c->prec, a, c->n_inst, s);
     if (is_zv(c)) return glbm_launch_step2d_zv(N, zv_kind(c), c->prec, c->tile[N], a, c->n_inst, s);
     if (is_x1(c)) return glbm_launch_step2d_x1(N, c->prec, c->tile[N], a, c->n_inst, s);
     return c->prec == GLBM_FP64 ? glbm_launch_step2d_f64(N, c->tile[N], a, c->n_inst, s)
@@ -1261,6 +1290,7 @@ static cudaError_t launch_2d_between(const glbm_ctx *c, const void *fin, void *f
     Step2DArgs a = step_args(c, 0);
     a.fin = fin;
     a.fout = fout;
+    if (is_guo(c)) return glbm_launch_step2d_guo(N, guo_kind(c), c->prec, a, c->n_inst, s);
     if (is_zv(c)) return glbm_launch_step2d_zv(N, zv_kind(c), c->prec, c->tile[N], a, c->n_inst, s);
     if (is_x1(c)) return glbm_launch_step2d_x1(N, c->prec, c->tile[N], a, c->n_inst, s);
     return c->prec == GLBM_FP64 ? glbm_launch_step2d_f64(N, c->tile[N], a, c->n_inst, s)
@@ -1293,6 +1323,7 @@ extern "C" glbm_status glbm_adjoint_flowrate(glbm_ctx *c, int64_t steps, int64_t
         return fail(GLBM_E_UNSUPPORTED, "the adjoint takes 2D uniform contexts");
     if (is_x1(c) || is_zv(c))
         return fail(GLBM_E_UNSUPPORTED, "the adjoint takes isotropic lattices of the 2N+1 hierarchy");
+    if (is_guo(c)) return fail(GLBM_E_UNSUPPORTED, "the adjoint takes the linearised force");
     if (steps < 1 || ckpt_every < 1) return fail(GLBM_E_INVAL, "steps and ckpt_every must be >= 1");
     const int64_t K = ckpt_every < steps ? ckpt_every : steps;
     const int64_t nseg = (steps + K - 1) / K;

@@ -201,7 +201,8 @@ __global__ void k_moments(const __grid_constant__ AuxArgs a, const void *f, int 
             jx += ax_vel(tx, ix) * v;
             jy += (a.dims == 2 ? ax_vel(a.tab, iy) : 0) * v;
         }
-    const double ux = jx / rho, uy = jy / rho;
+    // u_x = (j_x + g/2) / rho with Guo's force (g_half = 0 otherwise)
+    const double ux = (jx + ip.g_half) / rho, uy = jy / rho;
     double e2 = 0.0, qx = 0.0, qy = 0.0, sxy = 0.0;
     for (int iy = 0; iy < Qy; ++iy)
         for (int ix = 0; ix < Q1x; ++ix) {

@@ -73,6 +73,11 @@ struct AxisVel {
     __host__ __device__ static constexpr int vmag(int m) { return Z ? 2 * m + 1 : m; }
     __host__ __device__ static constexpr int ipos(int m) { return Z ? N + 1 + m : N + m; }
     __host__ __device__ static constexpr int ineg(int m) { return N - m; }
+    // lattice temperature of the axis: N/3, or (4N+3)/3 in the half-spacing
+    // units of the 2N+2 hierarchy (Eq. temp_2N2)
+    static constexpr double THETA = Z ? (4.0 * N + 3.0) / 3.0 : N / 3.0;
+    // v_i^2 / theta - 1: the coefficient of u_x in Guo's force term
+    __host__ __device__ static constexpr double ck(int i) { return (double)vel(i) * vel(i) / THETA - 1.0; }
 };
 
 // The same at run time from a table.
@@ -123,6 +128,7 @@ struct InstParams {
     double g_theta;    // g / theta_x: force F_i = W_i xi_x g/theta_x   (Sec. 5.4)
     double inv_den;    // 1 / sum_{n>0} n W^y_n: wall emission normaliser
     double g_theta_om; // g / (theta_x omega): force folded into the equilibrium
+                       // ((1 - omega/2) g / (theta_x omega) in Guo's form)
     double ew_lo[GLBM_MAXQA];  // E^x_i(u_wall_lo) by x velocity index
     double ew_hi[GLBM_MAXQA];  // E^x_i(u_wall_hi)
     float omega_f, g_theta_f, inv_den_f, g_theta_om_f;
@@ -136,6 +142,8 @@ struct InstParams {
     int NX;           // level along x
     long long off;    // element offset of this instance in the population buffers
     long long plane;  // elements per velocity plane (Ly * pitch)
+    double g_half;    // g / 2: Guo's half-force velocity shift (0 otherwise)
+    float g_half_f;
 };
 
 // Arguments of one uniform (same geometry for every instance) 2D step; TY is
@@ -207,6 +215,16 @@ int glbm_tile_shapes_x1(int N, int prec, TileShape *out);
 // Lattices on the 2N+2 hierarchy: kind GLBM_ZVK_X1 is D1Q3 along x times the
 // level-N 2N+2 axis along y; GLBM_ZVK_XY has the level-N 2N+2 axis on both.
 enum { GLBM_ZVK_X1 = 0, GLBM_ZVK_XY = 1 };
+// Lattice kinds of the 2D step with Guo's force (glbm_step2d_guo.cuh): the
+// level-N lattice on both axes, D1Q3 x level N, D1Q3 x the level-N 2N+2 axis.
+enum { GLBM_GUOK_ISO = 0, GLBM_GUOK_X1 = 1, GLBM_GUOK_ZV = 2 };
+template <int N, typename T, int KIND>
+cudaError_t glbm_step2d_guo_level(const Step2DArgs &a, int n_inst, cudaStream_t s);
+// Step with Guo's force of level N (1..8), kind GLBM_GUOK_*, precision prec,
+// in its one tile shape (glbm_tile_shape_guo).
+cudaError_t glbm_launch_step2d_guo(int N, int kind, int prec, const Step2DArgs &a, int n_inst,
+                                   cudaStream_t s);
+int glbm_tile_shape_guo(int N, int kind, int prec, TileShape *out);
 cudaError_t glbm_launch_step2d_zv(int N, int kind, int prec, int shape, const Step2DArgs &a,
                                   int n_inst, cudaStream_t s);
 // Levels 9..13 (kind GLBM_ZVK_X1 only).

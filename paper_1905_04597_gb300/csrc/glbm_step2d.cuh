@@ -21,10 +21,14 @@
 // ZY / ZX select the 2N+2 hierarchy (Sec. 4, zero velocity removed) along y /
 // x: that axis has 2N+2 velocity indices i with the odd velocities
 // v = 2i - (2N+1) on a lattice of half the spacing (AxisVel).
+// GUO replaces the linearised force by the force of Guo, Zheng and Shi (Phys.
+// Rev. E 65, 046308, 2002), which the paper does not use: u = (j + g/2) / rho
+// in the equilibrium and F_i = (1 - omega/2) W_i [(xi_i - u).G + (xi_i.U)
+// (xi_i.G)] with G = (g / theta_x, 0), U_a = u_a / theta_a.
 #pragma once
 #include "glbm_device.cuh"
 
-template <int N, typename T, int G, int R, int NXL = N, int ZY = 0, int ZX = 0>
+template <int N, typename T, int G, int R, int NXL = N, int ZY = 0, int ZX = 0, bool GUO = false>
 struct Step2D {
     using AY = AxisVel<N, ZY>;
     using AX = AxisVel<NXL, ZX>;
@@ -242,7 +246,11 @@ struct Step2D {
         const T rho = DEV ? T(1) + m0 : m0;
         const T drho = DEV ? m0 : m0 - T(1);
         const T inv_rho = T(1) / rho;
-        const T jx = S_x + C_x, jy = S_y + C_y;
+        T jx = S_x + C_x;
+        const T jy = S_y + C_y;
+        // Guo's form: the equilibrium takes u = (j + g/2) / rho
+        const T gh = GUO ? (DEV ? (T)ip.g_half_f : (T)ip.g_half) : T(0);
+        if constexpr (GUO) jx += gh;
         T ux = jx * inv_rho, uy = jy * inv_rho;
         // random word of this node and launch for the dithered FP32 roundings
         const unsigned hnode = DEV ? hash32((unsigned)(y * Lx + x) ^ seed) : 0u;
@@ -257,7 +265,9 @@ struct Step2D {
             const T dux = dither_ulp(ux, dither_unit(dither_word_ux(hnode)));
             const T duy = dither_ulp(uy, dither_unit(dither_word_uy(hnode)));
             // (the residual takes the compensated sum S + C unrounded)
-            ux = fma(fma(-ux, drho, (S_x - ux) + C_x) + dux, inv_rho, ux);
+            T rx = (S_x - ux) + C_x;
+            if constexpr (GUO) rx += gh;
+            ux = fma(fma(-ux, drho, rx) + dux, inv_rho, ux);
             uy = fma(fma(-uy, drho, (S_y - uy) + C_y) + duy, inv_rho, uy);
         }
         if (active) {
@@ -327,6 +337,7 @@ struct Step2D {
         for (int ix = 0; ix < QX; ++ix) ex[ix] = DEV ? T(0) : A::W(tabx, ix) + dx[ix];
         const T om = DEV ? (T)ip.omega_f : (T)ip.omega;
         const T gto = DEV ? (T)ip.g_theta_om_f : (T)ip.g_theta_om;  // g / (theta omega)
+        const T cyv = GUO ? uy * T(1.0 / AY::THETA) : T(0);        // Guo: U_y = u_y / theta_y
         if (!live) return;  // an earlier step halted the run: store nothing
         // rows past Ly store into the plane's spare row y = Ly, columns past
         // Lx into the row padding (pitch is a multiple of 64): no store needs a
@@ -351,6 +362,13 @@ struct Step2D {
                     dy = sm.eqy[r][iy][lane];
                 const T rey = rho * (wy + dy);  // rho e^y
                 const T gr = mul_rn(gto, wy);
+                // Guo's form: F_i / omega = W^x_i (v_x grA + ck_i grB) with
+                // grA = gr (1 + v_y U_y), grB = gr u_x, ck_i = v_x^2 / theta_x - 1
+                T grA = gr, grB = T(0);
+                if constexpr (GUO) {
+                    grA = fma(gr, T(AY::vel(iy)) * cyv, gr);
+                    grB = gr * ux;
+                }
                 // FP32: delta f^eq = d^x W^y + E^x B with B = rho e^y - W^y =
                 // drho W^y + d^y + drho d^y: the y momentum's carrier d^y is not
                 // scaled by a rounded rho
@@ -368,11 +386,14 @@ struct Step2D {
                     // scalar loop bit for bit; the last column of an odd count
                     // takes the scalar loop
                     const f32x2 B2 = pk2(B, B), nwy2 = pk2(nwy, nwy), om2 = pk2(om, om),
-                                gr2 = pk2(gr, gr);
+                                gr2 = pk2(grA, grA), grB2 = pk2(grB, grB);
 #pragma unroll
                     for (int ix = 0; ix + 1 < QX; ix += 2) {
                         const f32x2 f0 = pk2(f[k][ix], f[k][ix + 1]);
-                        const f32x2 Bn = fma2(pk2(T(AX::vel(ix)), T(AX::vel(ix + 1))), gr2, B2);
+                        const f32x2 Bn =
+                            GUO ? fma2(pk2(T(AX::vel(ix)), T(AX::vel(ix + 1))), gr2,
+                                       fma2(pk2(T(AX::ck(ix)), T(AX::ck(ix + 1))), grB2, B2))
+                                : fma2(pk2(T(AX::vel(ix)), T(AX::vel(ix + 1))), gr2, B2);
                         const f32x2 dxv = DX_SHARED ? pk2(sm.eqx[r][ix][lane], sm.eqx[r][ix + 1][lane])
                                                     : pk2(dx[ix], dx[ix + 1]);
                         const float p0 = __int_as_float(__float_as_int(lo2(f0)) & 0x7F800000);
@@ -393,7 +414,8 @@ struct Step2D {
                     const T f0 = f[k][ix];
                     T v;
                     if (DEV) {
-                        const T Bn = nx != 0 ? fma(T(nx), gr, B) : B;
+                        const T Bn = GUO ? fma(T(nx), grA, fma(T(AX::ck(ix)), grB, B))
+                                         : (nx != 0 ? fma(T(nx), gr, B) : B);
                         // split FP32 tiles read E^x - W where it is used (fewer registers)
                         const T dxv = DX_SHARED ? sm.eqx[r][ix][lane] : dx[ix];
                         // delta f^eq = d^x W^y + E^x B + F/omega: the momentum-
@@ -413,7 +435,10 @@ struct Step2D {
                         v = fma(om, t1 - r, f0);
                     } else {
                         T eq = ex[ix] * rey;
-                        if (nx != 0) eq = fma(A::WN(tabx, ix), gr, eq);
+                        if constexpr (GUO)
+                            eq = fma(A::W(tabx, ix), fma(T(nx), grA, T(AX::ck(ix)) * grB), eq);
+                        else if (nx != 0)
+                            eq = fma(A::WN(tabx, ix), gr, eq);
                         v = fma(om, eq - f0, f0);
                     }
                     op[ix * plane] = v;
@@ -423,11 +448,11 @@ struct Step2D {
     }
 };
 
-template <int N, typename T, int G, int R, int NXL = N, int ZY = 0, int ZX = 0>
+template <int N, typename T, int G, int R, int NXL = N, int ZY = 0, int ZX = 0, bool GUO = false>
 __global__ void __launch_bounds__(32 * G * R)
     k_step2d(const __grid_constant__ Step2DArgsOf<N> a)
 {
-    using S = Step2D<N, T, G, R, NXL, ZY, ZX>;
+    using S = Step2D<N, T, G, R, NXL, ZY, ZX, GUO>;
     __shared__ typename S::Smem sm;
     wait_prior_grid();
     // read here, needed only at the stores: no CTA waits for it before its loads

@@ -48,3 +48,33 @@ GLBM_TILES(7, double, {4, 1, 1}, {5, 1, 1}, {6, 1, 1})
 GLBM_TILES(8, double, {6, 1, 1}, {5, 1, 1}, {9, 1, 1})
 
 #undef GLBM_TILES
+
+// Anisotropic products D1Q3 (x) times level N (y), the channel lattices of Sec. 5.
+template <int N, typename T>
+struct TilesX1;
+
+#define GLBM_TILES_X1(N_, T_, ...)                                     \
+    template <>                                                        \
+    struct TilesX1<N_, T_> {                                           \
+        static constexpr TileShape shape[] = {__VA_ARGS__};            \
+        static constexpr int count = sizeof(shape) / sizeof(shape[0]); \
+    };
+// {G, R, V}: 3 (2N+1) populations per node, a few rows per CTA; V = 2 pairs.
+// Entry 0 of each level is the fastest measured on GB300 (1024 x 200, walls).
+GLBM_TILES_X1(1, float, {1, 8, 2}, {1, 4, 2}, {1, 8, 1}, {1, 4, 1}, {1, 16, 1})
+GLBM_TILES_X1(2, float, {1, 8, 2}, {1, 4, 2}, {1, 8, 1}, {1, 4, 1}, {1, 16, 1})
+GLBM_TILES_X1(3, float, {1, 4, 2}, {1, 2, 2}, {1, 8, 1}, {1, 4, 1}, {1, 16, 1})
+GLBM_TILES_X1(4, float, {1, 4, 2}, {1, 2, 2}, {2, 2, 2}, {1, 8, 1}, {1, 4, 1}, {1, 2, 1})
+GLBM_TILES_X1(5, float, {2, 2, 2}, {1, 2, 2}, {2, 1, 2}, {1, 4, 1}, {1, 8, 1}, {1, 2, 1})
+GLBM_TILES_X1(6, float, {2, 2, 2}, {1, 2, 2}, {2, 1, 2}, {1, 4, 1}, {1, 8, 1}, {1, 2, 1})
+GLBM_TILES_X1(7, float, {2, 2, 2}, {2, 1, 2}, {3, 1, 2}, {1, 4, 1}, {1, 2, 1}, {2, 4, 1})
+GLBM_TILES_X1(8, float, {2, 2, 2}, {2, 1, 2}, {3, 1, 2}, {1, 4, 1}, {1, 2, 1}, {2, 4, 1})
+GLBM_TILES_X1(1, double, {1, 8, 1}, {1, 4, 1})
+GLBM_TILES_X1(2, double, {1, 8, 1}, {1, 4, 1})
+GLBM_TILES_X1(3, double, {1, 4, 1}, {1, 8, 1})
+GLBM_TILES_X1(4, double, {1, 4, 1}, {1, 2, 1})
+GLBM_TILES_X1(5, double, {1, 4, 1}, {1, 2, 1})
+GLBM_TILES_X1(6, double, {1, 4, 1}, {2, 2, 1})
+GLBM_TILES_X1(7, double, {1, 4, 1}, {2, 2, 1})
+GLBM_TILES_X1(8, double, {1, 2, 1}, {2, 2, 1})
+#undef GLBM_TILES_X1

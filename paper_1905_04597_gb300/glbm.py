@@ -21,6 +21,7 @@ OK, E_INVAL, E_NOMEM, E_CUDA, E_UNSTABLE, E_TIMEOUT, E_IO, E_UNSUPPORTED = 0, -1
 BC_WALLS, BC_BOUNCEBACK, BC_PERIODIC = 0, 1, 2
 FP64, FP32_DEV = 0, 1
 ZV_X, ZV_Y = 1, 2  # axes on the 2N+2 hierarchy (Config.zv_axes)
+FORCE_LINEAR, FORCE_GUO = 0, 1  # Config.force: the paper's linearised force, or Guo's
 M_RHO, M_UX, M_UY, M_T, M_QX, M_QY, M_SXY, M_ALL = 1, 2, 4, 8, 16, 32, 64, 127
 M_UZ, M_QZ, M_ALL3 = 128, 256, 511
 FIELDS_2D = ("rho", "ux", "uy", "T", "qx", "qy", "sxy")
@@ -47,7 +48,7 @@ class Config(ctypes.Structure):
                 ("kn", ctypes.c_double),
                 ("bc", ctypes.c_int), ("prec", ctypes.c_int), ("u_wall_lo", ctypes.c_double),
                 ("u_wall_hi", ctypes.c_double), ("g", ctypes.c_double),
-                ("zv_axes", ctypes.c_int), ("nz", ctypes.c_int)]
+                ("zv_axes", ctypes.c_int), ("nz", ctypes.c_int), ("force", ctypes.c_int)]
 
 
 _lib = None
@@ -143,14 +144,15 @@ def eq_table(k: int) -> np.ndarray:
 
 
 def make_config(dims=2, nx=1, ny=1, k=0, tau=0.0, kn=0.0, bc=None, prec=FP64, u_wall_lo=0.0,
-                u_wall_hi=0.0, g=0.0, x_level=0, zv_axes=0, nz=1) -> Config:
+                u_wall_hi=0.0, g=0.0, x_level=0, zv_axes=0, nz=1, force=FORCE_LINEAR) -> Config:
     """One instance; x_level=1 makes the anisotropic product D1Q3 (x) times the
     level-(k+1) lattice (y); 0 keeps level k+1 on both axes. zv_axes (ZV_X,
-    ZV_Y) puts axes on the 2N+2 hierarchy (odd velocities, half spacing)."""
+    ZV_Y) puts axes on the 2N+2 hierarchy (odd velocities, half spacing).
+    force=FORCE_GUO takes Guo's force with the half-force velocity shift."""
     if bc is None:
         bc = BC_WALLS if dims >= 2 else BC_BOUNCEBACK
     return Config(dims, nx, ny if dims >= 2 else 1, k, x_level, tau, kn, bc, prec, u_wall_lo,
-                  u_wall_hi, g, zv_axes, nz if dims == 3 else 1)
+                  u_wall_hi, g, zv_axes, nz if dims == 3 else 1, force)
 
 
 _torch_alloc_refs = None

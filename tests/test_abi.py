@@ -132,6 +132,32 @@ def test_2n2_configs_are_checked_before_any_device_call():
     assert create(two, 2, None, ctypes.byref(h)) == glbm.E_UNSUPPORTED
 
 
+def test_guo_configs_are_checked_before_any_device_call():
+    """force: GLBM_FORCE_LINEAR or GLBM_FORCE_GUO; Guo's form is compiled for 2D
+    lattices with k <= 7 (isotropic, D1Q3 x level N, D1Q3 x the 2N+2 axis), not
+    for heterogeneous batches, and every instance of a context takes one form."""
+    h = ctypes.c_void_p()
+    create = glbm.lib().glbm_create
+    G = glbm.FORCE_GUO
+    zy, zxy = glbm.ZV_Y, glbm.ZV_X | glbm.ZV_Y
+    for kw, st in [(dict(dims=2, nx=8, ny=16, k=2, force=2), glbm.E_INVAL),
+                   (dict(dims=2, nx=8, ny=16, k=2, force=-1), glbm.E_INVAL),
+                   (dict(dims=1, nx=8, k=2, force=G), glbm.E_UNSUPPORTED),
+                   (dict(dims=3, nx=8, ny=8, nz=8, k=1, force=G), glbm.E_UNSUPPORTED),
+                   (dict(dims=2, nx=8, ny=32, k=8, x_level=1, zv_axes=zy, force=G),
+                    glbm.E_UNSUPPORTED),
+                   (dict(dims=2, nx=8, ny=16, k=2, zv_axes=zxy, force=G), glbm.E_UNSUPPORTED)]:
+        cfg = glbm.make_config(tau=1.0, **kw)
+        assert create(ctypes.byref(cfg), 1, None, ctypes.byref(h)) == st, kw
+        assert not h.value
+    cfg = glbm.make_config(dims=2, nx=8, ny=16, k=2, tau=1.0, prec=glbm.FP32_DEV, force=G)
+    assert glbm.lib().glbm_batch_create(ctypes.byref(cfg), 1, None,
+                                        ctypes.byref(h)) == glbm.E_UNSUPPORTED
+    two = (glbm.Config * 2)(glbm.make_config(dims=2, nx=8, ny=16, k=2, tau=1.0),
+                            glbm.make_config(dims=2, nx=8, ny=16, k=2, tau=1.0, force=G))
+    assert create(two, 2, None, ctypes.byref(h)) == glbm.E_UNSUPPORTED
+
+
 def test_3d_configs_are_checked_before_any_device_call():
     """3D: levels k <= 2, the level of k on every axis, ny * nz <= 65535, no
     heterogeneous batches; invalid configurations fail before any CUDA call."""
