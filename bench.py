@@ -345,6 +345,24 @@ def run_ours(args):
         return ms, launches, clk.summary()
 
     steps, warmup = args.steps, args.warmup
+    if args.only:
+        # one precision's timed steps alone (what a profiler capture needs)
+        prec = glbm.FP32_DEV if args.only == "fp32" else glbm.FP64
+        ms, launches, clk = timed(prec, steps, warmup)
+        if rank == 0:
+            s = 4 if prec == glbm.FP32_DEV else 8
+            print(json.dumps({"metric": METRIC, "value": job_throughput(pops_per_step * steps,
+                                                                        world, ms),
+                              "unit": UNIT, "n_gpus": world, "steps": steps, "warmup": warmup,
+                              "ms_per_step": ms / steps, "higher_is_better": True,
+                              "scaling": "weak", "vs_baseline": None,
+                              "dtype": "f32" if s == 4 else "f64", "data": "synthetic",
+                              "config": {"workload": label, "only": args.only,
+                                         "tiles": args.tiles},
+                              "kernel": tiles_used.get(prec),
+                              "hbm_gbs_algorithmic": 2 * s * pops_per_step / (ms / steps / 1e3) / 1e9,
+                              "clocks": clk, "gpu_launches": launches}), flush=True)
+        return
     ms32, launches, clocks = timed(glbm.FP32_DEV, steps, warmup)
     ms64, _, clocks64 = timed(glbm.FP64, max(steps // 4, 4), warmup)
     steps64 = max(steps // 4, 4)
@@ -560,7 +578,7 @@ def batch_share(rank, world):
     parts = shard.partition_by_bytes(sizes, world)
     loads = [sum(sizes[i] for i in p) for p in parts]
     return ([recipe[i] for i in parts[rank]], recipe,
-            {"instances": len(parts[rank]), "bytes": loads[rank],
+            {"instances": len(parts[rank]), "bytes": loads[rank], "index": parts[rank],
              "max_share_over_mean": max(loads) * world / sum(loads)})
 
 
@@ -601,6 +619,16 @@ def measure_batched(steps32=256, steps64=64, warmup=8, autotune=True, rank=0, wo
     barrier()
     ms32 = max_over_ranks(e0.elapsed_time(e1))
     launches32 = lat.kernel_launches - l0
+    # the final gather: every instance's flow rate J (channel diagnostics), in
+    # batch order on every rank (outside the timed region)
+    mine = {idx: lat.channel_diagnostics(k)[1]["flow_rate"] for k, idx in enumerate(share["index"])}
+    if world > 1:
+        import torch.distributed as dist
+        parts = [None] * world
+        dist.all_gather_object(parts, mine)
+        for p in parts:
+            mine.update(p)
+    flow = [mine[i] for i in range(len(recipe_all))]
     lat.close()
     singles = [glbm.Lattice(dict(dims=2, prec=glbm.FP64, **r)) for r in recipe]
     for x in singles:
@@ -617,7 +645,10 @@ def measure_batched(steps32=256, steps64=64, warmup=8, autotune=True, rank=0, wo
     sps32 = steps32 / (ms32 / 1e3)          # steps/s of the whole batch
     sps64 = steps64 / (ms64 / 1e3)
     n = len(recipe_all)
+    share = {k: v for k, v in share.items() if k != "index"}
     return {"instances": n, "pop_updates_per_step": pops, "ranks": world, "rank0_share": share,
+            "gathered_flow_rates": {"instances": len(flow), "sum": float(np.sum(flow)),
+                                    "finite": bool(np.all(np.isfinite(flow)))},
             "fp32_batched": {"solves_per_s": n * sps32 / STEPS_PER_SOLVE, "tiles": tiles,
                              "pop_updates_per_s": pops * sps32, "ms_per_step": ms32 / steps32,
                              "launches_per_step": launches32 / steps32},
@@ -853,6 +884,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-precision", action="store_true")
+    ap.add_argument("--only", choices=["fp32", "fp64"], default=None,
+                    help="time one precision's steps alone and print a reduced line (no "
+                         "e2e, precision, batched or CPU baseline): for profiler captures")
     ap.add_argument("--tiles", default="autotune",
                     help="autotune (time every tile shape on the context first), default "
                          "(keep the defaults), or idx:<i> (FP32 candidate i of the level)")

@@ -63,12 +63,14 @@ __global__ void k_set_equilibrium(const __grid_constant__ AuxArgs a, void *f, in
     const double r = rho[node], u = ux[node], v = a.dims == 2 ? uy[node] : 0.0;
     const long long base = (long long)inst * a.inst_stride + (long long)y * a.pitch + x;
     const int Qy = a.dims == 2 ? ax_q(a.tab) : 1;
+    double dxs[GLBM_MAXQA];  // E^x - W^x of the node, evaluated once
+    for (int ix = 0; ix < Q1x; ++ix) dxs[ix] = eq_dev_rt(tx, u, ix);
     for (int iy = 0; iy < Qy; ++iy) {
         const double wy = a.dims == 2 ? a.tab.W[iy] : 1.0;
         const double dy = a.dims == 2 ? eq_dev_rt(a.tab, v, iy) : 0.0;
         for (int ix = 0; ix < Q1x; ++ix) {
             const double wx = tx.W[ix];
-            const double dx = eq_dev_rt(tx, u, ix);
+            const double dx = dxs[ix];
             const long long idx = base + (long long)(iy * Q1x + ix) * a.plane;
             if (a.prec == GLBM_FP64) {
                 static_cast<double *>(f)[idx] = r * (wx + dx) * (wy + dy);
@@ -193,28 +195,43 @@ __global__ void k_moments(const __grid_constant__ AuxArgs a, const void *f, int 
         if (y < vmax) rw_lo = wall_density(a, ip, f, ibase, x, true);
         if (y >= a.Ly - vmax) rw_hi = wall_density(a, ip, f, ibase, x, false);
     }
-    double rho = 0.0, jx = 0.0, jy = 0.0;
-    for (int iy = 0; iy < Qy; ++iy)
+    // one pass of raw moments, row by row: R_p = sum_ix xi_x^p v for p = 0..3,
+    // then the central moments about u from them (expanded in FP64)
+    double M0 = 0.0, jx = 0.0, jy = 0.0, Pxx = 0.0, Pyy = 0.0, Pxy = 0.0, Mx = 0.0, My = 0.0;
+    for (int iy = 0; iy < Qy; ++iy) {
+        double R0 = 0.0, R1 = 0.0, R2 = 0.0, R3 = 0.0;
         for (int ix = 0; ix < Q1x; ++ix) {
             const double v = pulled(a, ip, f, ibase, x, y, ix, iy, rw_lo, rw_hi);
-            rho += v;
-            jx += ax_vel(tx, ix) * v;
-            jy += (a.dims == 2 ? ax_vel(a.tab, iy) : 0) * v;
+            const double c = ax_vel(tx, ix);
+            R0 += v;
+            R1 = fma(c, v, R1);
+            R2 = fma(c * c, v, R2);
+            R3 = fma(c * c * c, v, R3);
         }
+        const double cy = a.dims == 2 ? ax_vel(a.tab, iy) : 0.0;
+        M0 += R0;
+        jx += R1;
+        jy = fma(cy, R0, jy);
+        Pxx += R2;
+        Pyy = fma(cy * cy, R0, Pyy);
+        Pxy = fma(cy, R1, Pxy);
+        Mx += fma(cy * cy, R1, R3);             // sum xi_x |xi|^2 v
+        My += cy * fma(cy * cy, R0, R2);        // sum xi_y |xi|^2 v
+    }
+    const double rho = M0;
     // u_x = (j_x + g/2) / rho with Guo's force (g_half = 0 otherwise)
     const double ux = (jx + ip.g_half) / rho, uy = jy / rho;
-    double e2 = 0.0, qx = 0.0, qy = 0.0, sxy = 0.0;
-    for (int iy = 0; iy < Qy; ++iy)
-        for (int ix = 0; ix < Q1x; ++ix) {
-            const double v = pulled(a, ip, f, ibase, x, y, ix, iy, rw_lo, rw_hi);
-            const double dx = ax_vel(tx, ix) - ux;
-            const double dy = a.dims == 2 ? ax_vel(a.tab, iy) - uy : 0.0;
-            const double d2 = dx * dx + dy * dy;
-            e2 += d2 * v;
-            qx += dx * d2 * v;
-            qy += dy * d2 * v;
-            sxy += dx * dy * v;
-        }
+    // central second moments: P_ab - u_a j_b - j_a u_b + rho u_a u_b
+    const double cxx = Pxx - 2.0 * ux * jx + rho * ux * ux;
+    const double cyy = Pyy - 2.0 * uy * jy + rho * uy * uy;
+    const double sxy = Pxy - ux * jy - jx * uy + rho * ux * uy;
+    // sum c_a |c|^2 v, c = xi - u: M3_a - u_a tr P - 2 u.P_a + 2 u_a u.j + |u|^2 j_a - u_a |u|^2 rho
+    const double trP = Pxx + Pyy, uj = ux * jx + uy * jy, u2 = ux * ux + uy * uy;
+    const double qx = Mx - ux * trP - 2.0 * (ux * Pxx + uy * Pxy) + 2.0 * ux * uj + u2 * jx -
+                      ux * u2 * rho;
+    const double qy = My - uy * trP - 2.0 * (ux * Pxy + uy * Pyy) + 2.0 * uy * uj + u2 * jy -
+                      uy * u2 * rho;
+    const double e2 = cxx + cyy;
     const long long plane = (long long)a.Lx * a.Ly;
     const long long node = (long long)y * a.Lx + x;
     if (a.dims == 2) {
@@ -527,12 +544,17 @@ __global__ void k_set_equilibrium3d(const __grid_constant__ AuxArgs a, void *f, 
     const long long node = (long long)zy * a.Lx + x;
     const double r = rho[node];
     const long long base = (long long)inst * a.inst_stride + (long long)zy * a.pitch + x;
+    double dxs[GLBM_MAXQA], dys[GLBM_MAXQA];  // E - W of the node per axis, evaluated once
+    for (int i = 0; i < Q1; ++i) {
+        dxs[i] = eq_dev_rt(a.tab, ux[node], i);
+        dys[i] = eq_dev_rt(a.tab, uy[node], i);
+    }
     for (int iz = 0; iz < Q1; ++iz) {
         const double wz = a.tab.W[iz], dz = eq_dev_rt(a.tab, uz[node], iz);
         for (int iy = 0; iy < Q1; ++iy) {
-            const double wy = a.tab.W[iy], dy = eq_dev_rt(a.tab, uy[node], iy);
+            const double wy = a.tab.W[iy], dy = dys[iy];
             for (int ix = 0; ix < Q1; ++ix) {
-                const double wx = a.tab.W[ix], dx = eq_dev_rt(a.tab, ux[node], ix);
+                const double wx = a.tab.W[ix], dx = dxs[ix];
                 const long long idx = base + (long long)((iz * Q1 + iy) * Q1 + ix) * a.plane;
                 if (a.prec == GLBM_FP64) {
                     static_cast<double *>(f)[idx] = r * (wx + dx) * (wy + dy) * (wz + dz);
@@ -611,30 +633,47 @@ __global__ void k_moments3d(const __grid_constant__ AuxArgs a, const void *f, in
         if (y < N) rw_lo = wall_density3d(a, ip, f, ibase, x, z, true);
         if (y >= a.Ly - N) rw_hi = wall_density3d(a, ip, f, ibase, x, z, false);
     }
+    // one pass of raw moments, row by row (R_p = sum_ix xi_x^p v), then the
+    // central moments about u from them (expanded in FP64)
     double rho = 0.0, jx = 0.0, jy = 0.0, jz = 0.0;
+    double Pxx = 0.0, Pyy = 0.0, Pzz = 0.0, Pxy = 0.0, Pxz = 0.0, Pyz = 0.0;
+    double Mx = 0.0, My = 0.0, Mz = 0.0;  // sum xi_a |xi|^2 v
     for (int iz = 0; iz < Q1; ++iz)
-        for (int iy = 0; iy < Q1; ++iy)
+        for (int iy = 0; iy < Q1; ++iy) {
+            double R0 = 0.0, R1 = 0.0, R2 = 0.0, R3 = 0.0;
             for (int ix = 0; ix < Q1; ++ix) {
                 const double v = pulled3d(a, ip, f, ibase, x, y, z, ix, iy, iz, rw_lo, rw_hi);
-                rho += v;
-                jx += (ix - N) * v;
-                jy += (iy - N) * v;
-                jz += (iz - N) * v;
+                const double c = ix - N;
+                R0 += v;
+                R1 = fma(c, v, R1);
+                R2 = fma(c * c, v, R2);
+                R3 = fma(c * c * c, v, R3);
             }
+            const double cy = iy - N, cz = iz - N, s2 = cy * cy + cz * cz;
+            rho += R0;
+            jx += R1;
+            jy = fma(cy, R0, jy);
+            jz = fma(cz, R0, jz);
+            Pxx += R2;
+            Pyy = fma(cy * cy, R0, Pyy);
+            Pzz = fma(cz * cz, R0, Pzz);
+            Pxy = fma(cy, R1, Pxy);
+            Pxz = fma(cz, R1, Pxz);
+            Pyz = fma(cy * cz, R0, Pyz);
+            Mx += fma(s2, R1, R3);
+            My += cy * fma(s2, R0, R2);
+            Mz += cz * fma(s2, R0, R2);
+        }
     const double ux = jx / rho, uy = jy / rho, uz = jz / rho;
-    double e2 = 0.0, qx = 0.0, qy = 0.0, qz = 0.0, sxy = 0.0;
-    for (int iz = 0; iz < Q1; ++iz)
-        for (int iy = 0; iy < Q1; ++iy)
-            for (int ix = 0; ix < Q1; ++ix) {
-                const double v = pulled3d(a, ip, f, ibase, x, y, z, ix, iy, iz, rw_lo, rw_hi);
-                const double dx = (ix - N) - ux, dy = (iy - N) - uy, dz = (iz - N) - uz;
-                const double d2 = dx * dx + dy * dy + dz * dz;
-                e2 += d2 * v;
-                qx += dx * d2 * v;
-                qy += dy * d2 * v;
-                qz += dz * d2 * v;
-                sxy += dx * dy * v;
-            }
+    const double trP = Pxx + Pyy + Pzz, uj = ux * jx + uy * jy + uz * jz;
+    const double u2 = ux * ux + uy * uy + uz * uz;
+    const double e2 = trP - 2.0 * uj + rho * u2;
+    const double sxy = Pxy - ux * jy - jx * uy + rho * ux * uy;
+    const double uPx = ux * Pxx + uy * Pxy + uz * Pxz, uPy = ux * Pxy + uy * Pyy + uz * Pyz,
+                 uPz = ux * Pxz + uy * Pyz + uz * Pzz;
+    const double qx = Mx - ux * trP - 2.0 * uPx + 2.0 * ux * uj + u2 * jx - ux * u2 * rho;
+    const double qy = My - uy * trP - 2.0 * uPy + 2.0 * uy * uj + u2 * jy - uy * u2 * rho;
+    const double qz = Mz - uz * trP - 2.0 * uPz + 2.0 * uz * uj + u2 * jz - uz * u2 * rho;
     const long long nodes = (long long)a.Lx * a.Ly * a.Lz;
     const long long node = (long long)zy * a.Lx + x;
     const double m[9] = {rho, ux, uy, e2 / (3.0 * rho), 0.5 * qx, 0.5 * qy, sxy, uz, 0.5 * qz};

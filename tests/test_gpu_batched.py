@@ -103,6 +103,41 @@ def test_batched_workload_sample_matches_oracle():
     assert not failures, failures
 
 
+def test_every_instance_of_the_256_batch_equals_its_own_context():
+    """Every instance of the 256-instance batch, from its own random state, after 6
+    steps against the same instance stepped alone in a uniform context: a tile or
+    work-list boundary that mixed instances would show as an O(1) error somewhere.
+    The two runs differ only in the dither seed (the instance index enters it), so
+    they agree to FP32 rounding, not bit for bit (a batch of one is bitwise equal,
+    above)."""
+    recipe = inputs.batched_instances(seed=0)
+    cfgs = [dict(dims=2, prec=glbm.FP32_DEV, **r) for r in recipe]
+    lat = glbm.Lattice(cfgs, hetero=True)
+    fields = []
+    for i, r in enumerate(recipe):
+        f = inputs.random_macro(1000 + i, r["nx"], r["ny"])
+        lat.set_equilibrium(i, *f)
+        fields.append(f)
+    steps = 6
+    lat.step(steps)
+    lat.sync()
+    worst = (0.0, None)
+    for i, r in enumerate(recipe):
+        one = glbm.Lattice(cfgs[i])
+        one.set_equilibrium(0, *fields[i])
+        one.step(steps)
+        m = one.moments(0)
+        want = np.stack([m[n] for n in glbm.FIELDS_2D])
+        F = one.get_populations(0)  # term scales of the metric (post-collision state)
+        one.close()
+        errs = rel_errors(lat.moments(i), want, F=F)
+        n = max(errs, key=errs.get)
+        if errs[n] > worst[0]:
+            worst = (errs[n], (i, n))
+    lat.close()
+    assert worst[0] < 1e-5, worst
+
+
 def test_batched_rejects_fp64_and_1d():
     with pytest.raises(glbm.GlbmError):
         glbm.Lattice([dict(dims=2, nx=32, ny=8, k=1, tau=1.0, prec=glbm.FP64)], hetero=True)
