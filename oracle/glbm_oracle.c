@@ -874,14 +874,20 @@ static void orc_eq_lattice_du(int N, double u, double *E, double *dE)
     }
 }
 
+/* States of the dual numbers: the value and its derivatives by tau, g and the
+   two wall speeds. */
+#define ORC_NT 5
+
 /*
- * Collision of a dual state: X = C(F) for the values and, for each of the two
- * parameters p in (tau, g), dX/dp = dC/dF . dF/dp + dC/dp, with
+ * Collision of a dual state: X = C(F) for the values and, for each parameter p
+ * in (tau, g, u_wall_lo, u_wall_hi), dX/dp = dC/dF . dF/dp + dC/dp, with
  *   f* = f + omega (f^eq - f) + F_i,  omega = 1/(tau + 1/2),
  *   d omega / d tau = -omega^2,  dF_i/dg = W_i xi_x / theta_x,
  *   d f^eq_i = E_i d rho + rho (dE^x_i/du_x du_x E^y_i + E^x_i dE^y_i/du_y du_y),
- *   du = (dj - u d rho) / rho.
- * F, dF arrays hold [value | d/dtau | d/dg] each of n populations.
+ *   du = (dj - u d rho) / rho;
+ * the collision has no explicit dependence on the wall speeds (they enter
+ * through the streaming, orc_emission_du). F, X hold ORC_NT arrays of n
+ * populations: [value | d/dtau | d/dg | d/du_wall_lo | d/du_wall_hi].
  */
 static void orc_collide_dual(const orc_cfg *c, const double *F, double *X)
 {
@@ -897,11 +903,11 @@ static void orc_collide_dual(const orc_cfg *c, const double *F, double *X)
     orc_eq_lattice(NX, 0.0, Wx);
     orc_eq_lattice(NY, 0.0, Wy);
     for (size_t node = 0; node < plane; ++node) {
-        double rho[3] = {0, 0, 0}, jx[3] = {0, 0, 0}, jy[3] = {0, 0, 0};
+        double rho[ORC_NT] = {0}, jx[ORC_NT] = {0}, jy[ORC_NT] = {0};
         for (int ny = -NY; ny <= NY; ++ny)
             for (int nx = -NX; nx <= NX; ++nx) {
                 const size_t idx = ((ny + NY) * Q1x + (nx + NX)) * plane + node;
-                for (int d = 0; d < 3; ++d) {
+                for (int d = 0; d < ORC_NT; ++d) {
                     const double f = F[d * n + idx];
                     rho[d] += f;
                     jx[d] += nx * f;
@@ -909,8 +915,8 @@ static void orc_collide_dual(const orc_cfg *c, const double *F, double *X)
                 }
             }
         const double ux = jx[0] / rho[0], uy = jy[0] / rho[0];
-        double dux[3], duy[3];
-        for (int d = 1; d < 3; ++d) {
+        double dux[ORC_NT], duy[ORC_NT];
+        for (int d = 1; d < ORC_NT; ++d) {
             dux[d] = (jx[d] - ux * rho[d]) / rho[0];
             duy[d] = (jy[d] - uy * rho[d]) / rho[0];
         }
@@ -923,7 +929,7 @@ static void orc_collide_dual(const orc_cfg *c, const double *F, double *X)
                 const double feq = rho[0] * Ex[nx + NX] * Ey[ny + NY];
                 const double wxg = Wx[nx + NX] * Wy[ny + NY] * nx / theta_x;
                 X[idx] = f + omega * (feq - f) + wxg * c->g;
-                for (int d = 1; d < 3; ++d) {
+                for (int d = 1; d < ORC_NT; ++d) {
                     const double df = F[d * n + idx];
                     const double dfeq = rho[d] * Ex[nx + NX] * Ey[ny + NY] +
                                         rho[0] * (dEx[nx + NX] * dux[d] * Ey[ny + NY] +
@@ -938,27 +944,83 @@ static void orc_collide_dual(const orc_cfg *c, const double *F, double *X)
 }
 
 /*
+ * Derivative by the speed of one wall (upper = 0: y = -1/2, 1: y = Ly - 1/2) of
+ * streaming the value state X, added to dF: the wall re-emits
+ * rho_w(x) E^x_i(u_w) W^y_i (reading R5), where rho_w balances the mass X
+ * sends into the wall and so does not depend on u_w (the emitted mass per unit
+ * rho_w, sum_{n>0} n W^y_n sum_i E^x_i(u_w), is the same at every u_w because
+ * sum_i E^x_i = 1); the derivative is rho_w(x) dE^x_i/du(u_w) W^y_i at every
+ * emitted (node, velocity) of that wall. Isotropic 2N+1 lattices.
+ */
+static void orc_emission_du(const orc_cfg *c, const double *X, int upper, double *dF)
+{
+    const int NX = c->NX, NY = c->NY, Q1x = 2 * NX + 1;
+    const int Lx = c->Lx, Ly = c->Ly;
+    const size_t plane = (size_t)Lx * Ly;
+    const double uw = upper ? c->uw_hi : c->uw_lo;
+    double Wy[2 * ORC_MAX_N + 1], E[2 * ORC_MAX_N + 1], dE[2 * ORC_MAX_N + 1];
+    orc_eq_lattice(NY, 0.0, Wy);
+    orc_eq_lattice_du(NX, uw, E, dE);
+    double den = 0.0;
+    for (int ny = 1; ny <= NY; ++ny)
+        for (int ix = 0; ix < Q1x; ++ix) den += ny * E[ix] * Wy[ny + NY];
+    double *D = (double *)calloc((size_t)Lx, sizeof(double));
+    /* the mass that streams into the wall, booked under the column it reaches */
+    for (int ny = -NY; ny <= NY; ++ny) {
+        if ((upper && ny <= 0) || (!upper && ny >= 0)) continue;
+        for (int nx = -NX; nx <= NX; ++nx) {
+            const int q = (ny + NY) * Q1x + (nx + NX);
+            for (int y = 0; y < Ly; ++y) {
+                const int yd = y + ny;
+                if ((upper && yd < Ly) || (!upper && yd >= 0)) continue;
+                for (int x = 0; x < Lx; ++x)
+                    D[orc_wrap(x + nx, Lx)] += X[q * plane + (size_t)y * Lx + x];
+            }
+        }
+    }
+    for (int x = 0; x < Lx; ++x) {
+        const double rw = D[x] / den;
+        for (int a = 1; a <= NY; ++a) {
+            const int ny = upper ? -a : a;  /* velocities leaving the wall */
+            for (int nx = -NX; nx <= NX; ++nx) {
+                const int q = (ny + NY) * Q1x + (nx + NX);
+                for (int k = 0; k < a; ++k) {
+                    const int y = upper ? Ly - 1 - k : k;
+                    dF[q * plane + (size_t)y * Lx + x] += rw * dE[nx + NX] * Wy[ny + NY];
+                }
+            }
+        }
+    }
+    free(D);
+}
+
+/*
  * Flow rate J = (1/Lx) sum over nodes of the x-momentum of S(X_T) after `steps`
- * steps from X (2D), and dJ/dtau, dJ/dg by forward-mode differentiation of every
- * step (streaming is linear, so the tangents stream like the values).
- * X holds the initial populations (independent of tau and g); out = {J, dJ/dtau,
- * dJ/dg}. Returns -1 on a bad configuration.
+ * steps from X (2D), and its derivatives by tau, g, u_wall_lo and u_wall_hi by
+ * forward-mode differentiation of every step (streaming is linear in the
+ * populations, so the tangents stream like the values, plus the wall speeds'
+ * own term of the emission). X holds the initial populations (independent of
+ * the parameters); out = {J, dJ/dtau, dJ/dg, dJ/du_wall_lo, dJ/du_wall_hi}.
+ * Returns -1 on a bad configuration.
  */
 int orc_flowrate_grad(const orc_cfg *c, const double *X0, long steps, double *out)
 {
     if (orc_check(c) || c->dims != 2 || c->zv || c->guo) return -1;  /* 2N+1, linearised force */
     const size_t plane = (size_t)c->Lx * c->Ly;
     const size_t n = (size_t)orc_nq(c) * plane;
-    double *X = (double *)calloc(3 * n, sizeof(double));
-    double *F = (double *)malloc(3 * n * sizeof(double));
+    double *X = (double *)calloc(ORC_NT * n, sizeof(double));
+    double *F = (double *)malloc(ORC_NT * n * sizeof(double));
     memcpy(X, X0, n * sizeof(double));
-    for (long t = 0; t < steps; ++t) {
-        for (int d = 0; d < 3; ++d) orc_stream2d(c, X + d * n, F + d * n);
-        orc_collide_dual(c, F, X);
+    for (long t = 0; t <= steps; ++t) {
+        for (int d = 0; d < ORC_NT; ++d) orc_stream2d(c, X + d * n, F + d * n);
+        if (c->bc == ORC_BC_WALLS) {
+            orc_emission_du(c, X, 0, F + 3 * n);
+            orc_emission_du(c, X, 1, F + 4 * n);
+        }
+        if (t < steps) orc_collide_dual(c, F, X);
     }
-    for (int d = 0; d < 3; ++d) orc_stream2d(c, X + d * n, F + d * n);
     const int NX = c->NX, NY = c->NY, Q1x = 2 * NX + 1;
-    for (int d = 0; d < 3; ++d) {
+    for (int d = 0; d < ORC_NT; ++d) {
         double s = 0.0;
         for (int ny = -NY; ny <= NY; ++ny)
             for (int nx = -NX; nx <= NX; ++nx)

@@ -191,13 +191,14 @@ class Lattice:
         self._chk(self._L.orc_observe(ctypes.byref(self.cfg), _dp(X), _dp(out)))
         return out
 
-    def flowrate_grad(self, X, steps):
+    def flowrate_grad(self, X, steps, walls=False):
         """J = x-momentum of S(X_T) per column after `steps` steps from X, and
-        (dJ/dtau, dJ/dg) by forward-mode dual numbers."""
+        (dJ/dtau, dJ/dg) by forward-mode dual numbers; with walls=True also
+        (dJ/du_wall_lo, dJ/du_wall_hi)."""
         X = np.ascontiguousarray(X, dtype=np.float64)
-        out = np.empty(3)
+        out = np.empty(5)
         self._chk(self._L.orc_flowrate_grad(ctypes.byref(self.cfg), _dp(X), int(steps), _dp(out)))
-        return out[0], out[1], out[2]
+        return tuple(out) if walls else (out[0], out[1], out[2])
 
     def flowrate(self, X, steps):
         """J alone from a plain run (no tangents)."""

@@ -79,6 +79,12 @@ MUTATIONS = {
                                    "const double xiU = vx * ux / thx + vy * uy / thx + vz * uz / thz;"),
     "Guo moments without the shift": ("        double ux = orc_ux(c, jx, rho), uy = jy / rho;\n        double e2",
                                       "        double ux = jx / rho, uy = jy / rho;\n        double e2"),
+    "wall-speed tangent without rho_w": ("dF[q * plane + (size_t)y * Lx + x] += rw * dE[nx + NX] * Wy[ny + NY];",
+                                         "dF[q * plane + (size_t)y * Lx + x] += dE[nx + NX] * Wy[ny + NY];"),
+    "wall-speed tangent with E for dE/du": ("dF[q * plane + (size_t)y * Lx + x] += rw * dE[nx + NX] * Wy[ny + NY];",
+                                           "dF[q * plane + (size_t)y * Lx + x] += rw * E[nx + NX] * Wy[ny + NY];"),
+    "wall-speed tangent into the far rows": ("const int y = upper ? Ly - 1 - k : k;",
+                                             "const int y = upper ? k : Ly - 1 - k;"),
     "3D x and z swapped in q": ("const double f = F[((iz * Qy + iy) * Qx + ix) * plane + node];\n                        rho += f;",
                                 "const double f = F[((ix * Qy + iy) * Qx + iz) * plane + node];\n                        rho += f;"),
 }
