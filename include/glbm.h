@@ -323,6 +323,36 @@ glbm_status glbm_conservation_noalloc(const double *fields, int dims, int64_t no
                                       void *stream);
 
 /*
+ * Dataflow stepping (an engineering choice; the paper has no counterpart).
+ * With it (the default), glbm_step runs uniform 2D contexts of levels k <= 7
+ * whose wall densities come from the step tiles (glbm_get_wall_launch 0, or
+ * no walls) in chunks of 64 steps whose launches overlap: a tile of step t+1
+ * starts as soon as the rows of step t it reads and overwrites are done,
+ * instead of after the whole of step t. The results are identical to
+ * launching the steps one after another (same arithmetic, same dither), and so
+ * is the failure contract: glbm_step keeps the state at its start in a copy
+ * (one state's memory, allocated on first use) and, if a node leaves the
+ * positivity domain, restores it and replays the call one step after
+ * another, which stops after the failing step. A wait that takes longer than
+ * 0.5 s (none should) restores the state at the call's start and returns
+ * GLBM_E_TIMEOUT. on = 0 launches the steps one after another.
+ * glbm_get_dataflow returns 1 when the context's steps take this path.
+ */
+glbm_status glbm_set_dataflow(glbm_ctx *ctx, int on);
+int glbm_get_dataflow(const glbm_ctx *ctx);
+
+/*
+ * Measured FP64 FMA throughput of the current device (a measurement aid for
+ * the FP64 roofline; the paper has no counterpart): a probe kernel in which
+ * every thread runs 8 independent FMA chains, 8 CTAs of 256 threads per SM,
+ * timed with CUDA events on `stream` (a cudaStream_t; NULL = legacy default),
+ * best of two runs after a warm-up. *fma_per_s receives FP64 FMA thread
+ * instructions per second. Allocates 2 KB for the duration of the call;
+ * synchronises the stream.
+ */
+glbm_status glbm_measure_fp64_rate(void *stream, double *fma_per_s);
+
+/*
  * Gradient of the flow rate by the discrete adjoint. From the current state
  * X_t0 the context advances `steps` steps (the state afterwards is X_t0+steps,
  * as after glbm_step) keeping a checkpoint every `ckpt_every` steps. It then
@@ -333,14 +363,19 @@ glbm_status glbm_conservation_noalloc(const double *fields, int dims, int64_t no
  *   J        = (1/nx) sum over nodes of the x-momentum of S(X_T) (the
  *              volumetric flow rate per unit width, Sec. 5.4),
  *   dJ_dtau  = dJ/dtau  (omega = 1/(tau + 1/2)),
- *   dJ_dg    = dJ/dg    (body force along x).
- * Each output is an array of n_inst doubles in host memory. 2D uniform
- * contexts only. The adjoint state and the gradient sums are FP64. The call
- * allocates steps/ckpt_every + ckpt_every state copies for the duration of
- * the call. Synchronises.
+ *   dJ_dg    = dJ/dg    (body force along x),
+ *   dJ_du_lo, dJ_du_hi = dJ/du_wall_lo, dJ/du_wall_hi (the wall speeds of
+ *              Sec. 5.3; a wall speed enters only through E^x(u_w) of the
+ *              populations the wall re-emits; 0 without walls).
+ * Each output is an array of n_inst doubles in host memory; dJ_du_lo and
+ * dJ_du_hi may be NULL. 2D uniform contexts of isotropic 2N+1 lattices with
+ * the linearised force only (else GLBM_E_UNSUPPORTED). The adjoint state and
+ * the gradient sums are FP64. The call allocates steps/ckpt_every +
+ * ckpt_every state copies for the duration of the call. Synchronises.
  */
 glbm_status glbm_adjoint_flowrate(glbm_ctx *ctx, int64_t steps, int64_t ckpt_every, double *J,
-                                  double *dJ_dtau, double *dJ_dg);
+                                  double *dJ_dtau, double *dJ_dg, double *dJ_du_lo,
+                                  double *dJ_du_hi);
 
 /*
  * Tile shapes of the fused 2D step (an engineering choice; the paper has no
@@ -363,8 +398,12 @@ glbm_status glbm_adjoint_flowrate(glbm_ctx *ctx, int64_t steps, int64_t ckpt_eve
  * launches each (1..1000) from the current state into the spare buffer, with
  * CUDA events on the context's stream, and keeps the fastest; with walls it
  * then times both ways of summing the wall densities (glbm_set_wall_launch)
- * with the chosen shapes and keeps the faster. The state, the step clock and
- * the dither sequence are unchanged. If us is non-NULL it
+ * with the chosen shapes and keeps the faster. A uniform 2D context of level
+ * k <= 7 then steps 128 steps from its state (put back afterwards) with that
+ * choice, and with every tile shape in dataflow chunks (glbm_set_dataflow,
+ * wall densities from the tiles), and keeps the fastest of all, dataflow on
+ * or off. The state, the step clock and the dither sequence are unchanged;
+ * the first call allocates the dataflow copy of the state. If us is non-NULL it
  * receives the microseconds per launch, us[k * GLBM_MAX_TILES + idx], -1 for
  * pairs not timed (GLBM_LEVELS * GLBM_MAX_TILES doubles, host memory). R and
  * V change only which CTA and thread update a node; G also groups the

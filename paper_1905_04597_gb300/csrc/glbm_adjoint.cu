@@ -1,7 +1,7 @@
 // Discrete adjoint of the 2D stream-collide step, for the gradient of the flow
 // rate J = (1/Lx) sum_nodes sum_i xi_x,i F_i(T) (F = S(X): the streamed
 // populations, Sec. 5.4 volumetric flow) with respect to the relaxation time
-// tau and the body force g.
+// tau, the body force g and the two wall speeds (Sec. 5.3).
 //
 // Forward: X_{t+1} = C(F_t), F_t = S(X_t). With mu_t = dJ/dF_t:
 //   mu_T = xi_x / Lx,
@@ -19,6 +19,12 @@
 // rho_w of the column it would reach by 1/den, and rho_w scales every emitted
 // ghost rho_w E^x_i(u_w) W^y_i; so lambda of an absorbed population is
 //   G(x_d) / den,  G(x) = sum_{emitted (i, y) of that wall} mu_i(x, y) E^x_i(u_w) W^y_i.
+// A wall speed enters F_t only through E^x(u_w) of its emitted ghosts (rho_w
+// balances the absorbed mass), so
+//   dJ/du_w = sum_t sum_{emitted (x, y, i) of that wall} mu_t,i(x, y) rho_w,t(x)
+//             dE^x_i/du(u_w) W^y_i,
+// with rho_w,t from X_t: the step of time t adds its term at the wall rows,
+// k_adj_final_walls the term of F_T.
 #include "glbm_device.cuh"
 
 namespace {
@@ -154,7 +160,7 @@ template <int N, typename TF>
 __global__ void __launch_bounds__(ADJ_THREADS) k_adj_step(const __grid_constant__ AdjArgs a)
 {
     constexpr int Q1 = 2 * N + 1;
-    __shared__ double red[2][ADJ_THREADS];
+    __shared__ double red[GLBM_ADJ_NG][ADJ_THREADS];
     const int x = blockIdx.x * ADJ_THREADS + threadIdx.x;
     const int y = blockIdx.y;
     const bool active = x < a.Lx;
@@ -197,6 +203,9 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_adj_step(const __grid_constant_
         }
     // mu_t = (dC/dF)^T lambda at this node (the density cancels: d f^eq_i / d f_j =
     // E_i + sum_a dE_i/du_a (xi_j,a - u_a))
+    // and the wall speeds' term of F_t: mu_t of every ghost this node pulls
+    // from a wall, times rho_w dE^x/du(u_w) W^y
+    double glo = 0.0, ghi = 0.0;
     if (active) {
         for (int iy = 0; iy < Q1; ++iy)
             for (int ix = 0; ix < Q1; ++ix) {
@@ -204,11 +213,60 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_adj_step(const __grid_constant_
                 const double m = (1.0 - om) * lam +
                                  om * (a0 + ax * ((ix - N) - ux) + ay * ((iy - N) - uy));
                 a.mu_out[(long long)(iy * Q1 + ix) * a.plane + (long long)y * a.pitch + x] = m;
+                if (a.bc == GLBM_BC_WALLS) {
+                    const int ys = y - (iy - N);
+                    if (ys < 0) glo = fma(m * rw_lo * ip.dew_lo[ix], a.tab.W[iy], glo);
+                    if (ys >= a.Ly) ghi = fma(m * rw_hi * ip.dew_hi[ix], a.tab.W[iy], ghi);
+                }
             }
     }
     // gradient partials of this block, summed in a fixed order
     red[0][threadIdx.x] = active ? -om * om * gt : 0.0;
     red[1][threadIdx.x] = active ? gg / theta : 0.0;
+    red[2][threadIdx.x] = glo;
+    red[3][threadIdx.x] = ghi;
+    __syncthreads();
+    for (int s = ADJ_THREADS / 2; s > 0; s >>= 1) {
+        if ((int)threadIdx.x < s) {
+#pragma unroll
+            for (int k = 0; k < GLBM_ADJ_NG; ++k) red[k][threadIdx.x] += red[k][threadIdx.x + s];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const long long b = (long long)blockIdx.y * gridDim.x + blockIdx.x;
+#pragma unroll
+        for (int k = 0; k < GLBM_ADJ_NG; ++k) a.gpart[GLBM_ADJ_NG * b + k] += red[k][0];
+    }
+}
+
+// The wall speeds' term of F_T = S(X_T): mu_T = xi_x / Lx (the seed) at every
+// ghost a wall emits, times rho_w(X_T) dE^x/du(u_w) W^y, one thread per column,
+// added to the partials of the blocks of row 0 (the grid of k_adj_step's first
+// row), in a fixed order.
+template <int N, typename TF>
+__global__ void __launch_bounds__(ADJ_THREADS) k_adj_final_walls(const __grid_constant__ AdjArgs a)
+{
+    constexpr int Q1 = 2 * N + 1;
+    __shared__ double red[2][ADJ_THREADS];
+    const int x = blockIdx.x * ADJ_THREADS + threadIdx.x;
+    const InstParams &ip = *a.ip;
+    double glo = 0.0, ghi = 0.0;
+    if (x < a.Lx) {
+        const double rlo = fwd_wall_density<N, TF>(a, x, true);
+        const double rhi = fwd_wall_density<N, TF>(a, x, false);
+        for (int ny = 1; ny <= N; ++ny) {
+            const double wy = a.tab.W[N + ny];
+            for (int k = 0; k < ny; ++k)  // rows 0..ny-1 (lower), Ly-ny..Ly-1 (upper)
+                for (int ix = 0; ix < Q1; ++ix) {
+                    const double mu = (double)(ix - N) / a.Lx;
+                    glo = fma(mu * rlo * ip.dew_lo[ix], wy, glo);
+                    ghi = fma(mu * rhi * ip.dew_hi[ix], wy, ghi);
+                }
+        }
+    }
+    red[0][threadIdx.x] = glo;
+    red[1][threadIdx.x] = ghi;
     __syncthreads();
     for (int s = ADJ_THREADS / 2; s > 0; s >>= 1) {
         if ((int)threadIdx.x < s) {
@@ -218,9 +276,8 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_adj_step(const __grid_constant_
         __syncthreads();
     }
     if (threadIdx.x == 0) {
-        const long long b = (long long)blockIdx.y * gridDim.x + blockIdx.x;
-        a.gpart[2 * b] += red[0][0];
-        a.gpart[2 * b + 1] += red[1][0];
+        a.gpart[GLBM_ADJ_NG * blockIdx.x + 2] += red[0][0];
+        a.gpart[GLBM_ADJ_NG * blockIdx.x + 3] += red[1][0];
     }
 }
 
@@ -239,9 +296,9 @@ __global__ void k_adj_seed(const __grid_constant__ AdjArgs a)
 
 __global__ void k_adj_sum(const double *gpart, long long nblocks, double *out)
 {
-    if (threadIdx.x < 2) {
+    if (threadIdx.x < GLBM_ADJ_NG) {
         double s = 0.0;
-        for (long long b = 0; b < nblocks; ++b) s += gpart[2 * b + threadIdx.x];
+        for (long long b = 0; b < nblocks; ++b) s += gpart[GLBM_ADJ_NG * b + threadIdx.x];
         out[threadIdx.x] = s;
     }
 }
@@ -255,6 +312,18 @@ cudaError_t adj_step_n(const AdjArgs &a, cudaStream_t s)
         k_adj_step<N, double><<<grid, ADJ_THREADS, 0, s>>>(a);
     else
         k_adj_step<N, float><<<grid, ADJ_THREADS, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+template <int N>
+cudaError_t adj_final_walls_n(const AdjArgs &a, cudaStream_t s)
+{
+    if (a.bc != GLBM_BC_WALLS) return cudaSuccess;
+    const int blocks = (a.Lx + ADJ_THREADS - 1) / ADJ_THREADS;
+    if (a.prec == GLBM_FP64)
+        k_adj_final_walls<N, double><<<blocks, ADJ_THREADS, 0, s>>>(a);
+    else
+        k_adj_final_walls<N, float><<<blocks, ADJ_THREADS, 0, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -278,6 +347,18 @@ cudaError_t glbm_launch_adj_seed(const AdjArgs &a, cudaStream_t s)
     switch (a.N) {
 #define GLBM_CASE(NN) \
     case NN: return adj_seed_n<NN>(a, s);
+        GLBM_CASE(1) GLBM_CASE(2) GLBM_CASE(3) GLBM_CASE(4)
+        GLBM_CASE(5) GLBM_CASE(6) GLBM_CASE(7) GLBM_CASE(8)
+#undef GLBM_CASE
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t glbm_launch_adj_final_walls(const AdjArgs &a, cudaStream_t s)
+{
+    switch (a.N) {
+#define GLBM_CASE(NN) \
+    case NN: return adj_final_walls_n<NN>(a, s);
         GLBM_CASE(1) GLBM_CASE(2) GLBM_CASE(3) GLBM_CASE(4)
         GLBM_CASE(5) GLBM_CASE(6) GLBM_CASE(7) GLBM_CASE(8)
 #undef GLBM_CASE

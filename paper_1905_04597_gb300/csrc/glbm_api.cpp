@@ -130,6 +130,12 @@ struct glbm_ctx {
     int group[GLBM_MAXN + 2] = {0};  // first item of each level
     int tile[GLBM_MAXN + 1] = {0};   // tile shape index per level (glbm_tiles.h)
     cudaGraphExec_t graph[2] = {nullptr, nullptr};  // chunk graphs by starting buffer
+    cudaGraphExec_t graph_df[2] = {nullptr, nullptr};  // the same in dataflow form
+    int dataflow = 1;              // 1: dataflow chunks where the context allows them
+    unsigned *d_df = nullptr;      // per-step CTA counts of a chunk, then the band counts
+    long long df_words = 0;
+    void *snap = nullptr;          // state at the start of a dataflow glbm_step (replay)
+    bool halted = false;           // a glbm_step stopped at a failing step (until a new state)
     int64_t t = 0;
     int64_t launches = 0;
     unsigned clock_word = 0;  // host copy uploaded by set_clock (lives as long as the context)
@@ -199,6 +205,14 @@ static void fill_inst(const glbm_ctx *c, const glbm_config &cfg, const Geo &g, I
         }
         ip.dw_lo_f[n] = (float)(dlo * cfg.u_wall_lo);
         ip.dw_hi_f[n] = (float)(dhi * cfg.u_wall_hi);
+        // dE^x_n/du at the wall speeds (the adjoint's wall-speed term)
+        double slo = 0.0, shi = 0.0;
+        for (int j = Q1 - 1; j >= 1; --j) {
+            slo = slo * cfg.u_wall_lo + j * full[n * Q1 + j];
+            shi = shi * cfg.u_wall_hi + j * full[n * Q1 + j];
+        }
+        ip.dew_lo[n] = slo;
+        ip.dew_hi[n] = shi;
     }
     ip.g_theta_om = ip.g_theta / ip.omega;
     if (cfg.force == GLBM_FORCE_GUO) {
@@ -333,13 +347,21 @@ static Geo make_geo(const glbm_config &c)
     return g;
 }
 
-static void destroy_resources(glbm_ctx *c)
+static void drop_graphs(glbm_ctx *c)
 {
     for (int i = 0; i < 2; ++i) {
         if (c->graph[i]) cudaGraphExecDestroy(c->graph[i]);
-        c->graph[i] = nullptr;
+        if (c->graph_df[i]) cudaGraphExecDestroy(c->graph_df[i]);
+        c->graph[i] = c->graph_df[i] = nullptr;
     }
+}
+
+static void destroy_resources(glbm_ctx *c)
+{
+    drop_graphs(c);
     cudaStreamSynchronize(c->stream);
+    dev_free(c->A, c->d_df, c->stream);
+    dev_free(c->A, c->snap, c->stream);
     dev_free(c->A, c->buf[0], c->stream);
     dev_free(c->A, c->buf[1], c->stream);
     dev_free(c->A, c->d_ip, c->stream);
@@ -398,6 +420,7 @@ static cudaError_t set_clock(glbm_ctx *c, int64_t t)
 // flags and the halt word, so that stepping resumes.
 static cudaError_t clear_unstable(glbm_ctx *c)
 {
+    c->halted = false;
     cudaError_t e = cudaMemsetAsync(c->d_status + ST_FLAGS, 0, sizeof(unsigned), c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->d_status + ST_HALT, 0, sizeof(unsigned), c->stream);
     return e;
@@ -918,8 +941,18 @@ static int launches_per_step(const glbm_ctx *c)
     return c->hetero ? glbm_batched_launches(batch_args(c, 0)) : (c->wall_launch ? 2 : 1);
 }
 
-// One 2D step of every instance from buffer `from` into the other, on stream s.
-static cudaError_t launch_one_2d(const glbm_ctx *c, int from, cudaStream_t s)
+// Dataflow chunks (glbm_internal.h): uniform 2D contexts of levels up to 8
+// whose wall densities come from the tiles themselves (a separate wall launch
+// would be a second grid per step to order).
+static bool df_eligible(const glbm_ctx *c)
+{
+    return c->dataflow && !c->hetero && c->dims == 2 && c->geo[0].N <= GLBM_MAXN_2N1 &&
+           !c->wall_launch;
+}
+
+// One 2D step of every instance from buffer `from` into the other, on stream s;
+// node >= 0 makes it step `node` of a dataflow chunk.
+static cudaError_t launch_one_2d(const glbm_ctx *c, int from, cudaStream_t s, int node = -1)
 {
     if (c->hetero) return glbm_launch_batched_f32(batch_args(c, from), s);
     const int N = c->geo[0].N;
@@ -927,7 +960,12 @@ static cudaError_t launch_one_2d(const glbm_ctx *c, int from, cudaStream_t s)
     if (N > GLBM_MAXN_2N1)
         return glbm_launch_step2d_zv_hi(N, c->prec, c->tile[N],
                                         step_args_t<AxisTableHi>(c, from), c->n_inst, s);
-    const Step2DArgs a = step_args(c, from);
+    Step2DArgs a = step_args(c, from);
+    if (node >= 0) {
+        a.node_done = c->d_df;
+        a.bands = c->d_df + GLBM_DF_CHUNK;
+        a.node = node;
+    }
     if (is_guo(c)) return glbm_launch_step2d_guo(N, guo_kind(c), c->prec, a, c->n_inst, s);
     if (is_zv(c)) return glbm_launch_step2d_zv(N, zv_kind(c), c->prec, c->tile[N], a, c->n_inst, s);
     if (is_x1(c)) return glbm_launch_step2d_x1(N, c->prec, c->tile[N], a, c->n_inst, s);
@@ -935,15 +973,45 @@ static cudaError_t launch_one_2d(const glbm_ctx *c, int from, cudaStream_t s)
                                 : glbm_launch_step2d_f32(N, c->tile[N], a, c->n_inst, s);
 }
 
-static glbm_status capture_chunk(glbm_ctx *c, int from)
+// The counting words of dataflow chunks: GLBM_DF_CHUNK per-step CTA counts,
+// then one band count per (instance, row) (bands of R rows use the first
+// ceil(Ly / R) of an instance's Ly words).
+static glbm_status df_words_ready(glbm_ctx *c)
+{
+    const long long n = GLBM_DF_CHUNK + (long long)c->n_inst * c->geo[0].Ly;
+    if (c->d_df && c->df_words >= n) return GLBM_OK;
+    dev_free(c->A, c->d_df, c->stream);
+    c->d_df = (unsigned *)dev_alloc(c->A, n * sizeof(unsigned), c->stream);
+    if (!c->d_df) return fail(GLBM_E_NOMEM, "dataflow counters");
+    c->df_words = n;
+    return GLBM_OK;
+}
+
+// Enqueue steps 0..count-1 of a dataflow chunk from buffer `from` on stream s.
+static cudaError_t launch_df_chunk(glbm_ctx *c, int from, int count, cudaStream_t s)
+{
+    cudaError_t e = glbm_launch_df_start(c->d_status, c->d_df, c->df_words, s);
+    int b = from;
+    for (int i = 0; i < count && e == cudaSuccess; ++i) {
+        e = launch_one_2d(c, b, s, i);
+        b = 1 - b;
+    }
+    return e;
+}
+
+static glbm_status capture_chunk(glbm_ctx *c, int from, bool df = false)
 {
     cudaGraph_t g = nullptr;
     CUDA_TRY(cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal));
     cudaError_t e = cudaSuccess;
-    int b = from;
-    for (int i = 0; i < kGraphChunk && e == cudaSuccess; ++i) {
-        e = launch_one_2d(c, b, c->cap);
-        b = 1 - b;
+    if (df) {
+        e = launch_df_chunk(c, from, kGraphChunk, c->cap);
+    } else {
+        int b = from;
+        for (int i = 0; i < kGraphChunk && e == cudaSuccess; ++i) {
+            e = launch_one_2d(c, b, c->cap);
+            b = 1 - b;
+        }
     }
     cudaError_t e2 = cudaStreamEndCapture(c->cap, &g);
     if (e != cudaSuccess || e2 != cudaSuccess) {
@@ -951,7 +1019,7 @@ static glbm_status capture_chunk(glbm_ctx *c, int from)
         return fail(GLBM_E_CUDA, "graph capture failed: %s",
                     cudaGetErrorString(e != cudaSuccess ? e : e2));
     }
-    e = cudaGraphInstantiate(&c->graph[from], g, 0);
+    e = cudaGraphInstantiate(df ? &c->graph_df[from] : &c->graph[from], g, 0);
     cudaGraphDestroy(g);
     if (e != cudaSuccess) return fail(GLBM_E_CUDA, "graph instantiate failed: %s", cudaGetErrorString(e));
     return GLBM_OK;
@@ -1002,19 +1070,26 @@ static glbm_status step_1d_instance(glbm_ctx *c, int i, int64_t n, int64_t *comp
 // Enqueue n (< 2^31) 2D or 3D steps of every instance; returns the steps
 // completed (each step's last launch counts itself, and once a step has left
 // the positivity domain the launches of later steps do nothing).
-static glbm_status step_nd(glbm_ctx *c, int64_t n, int64_t *completed)
+static glbm_status step_nd(glbm_ctx *c, int64_t n, int64_t *completed, bool df = false)
 {
     const int cur0 = c->cur;
     CUDA_TRY(cudaMemsetAsync(c->d_status + ST_STEPS, 0, sizeof(unsigned), c->stream));
     int64_t left = n;
+    cudaGraphExec_t *graphs = df ? c->graph_df : c->graph;
     while (left >= kGraphChunk) {
-        if (!c->graph[c->cur]) {
-            glbm_status st = capture_chunk(c, c->cur);
+        if (!graphs[c->cur]) {
+            glbm_status st = capture_chunk(c, c->cur, df);
             if (st != GLBM_OK) return st;
         }
-        CUDA_TRY(cudaGraphLaunch(c->graph[c->cur], c->stream));
-        c->launches += kGraphChunk * launches_per_step(c);
+        CUDA_TRY(cudaGraphLaunch(graphs[c->cur], c->stream));
+        c->launches += kGraphChunk * launches_per_step(c) + (df ? 1 : 0);  // + k_df_start
         left -= kGraphChunk;  // even chunk: c->cur unchanged
+    }
+    if (df && left > 0) {
+        CUDA_TRY(launch_df_chunk(c, c->cur, (int)left, c->stream));
+        c->launches += left * launches_per_step(c) + 1;
+        if (left & 1) c->cur = 1 - c->cur;
+        left = 0;
     }
     for (; left > 0; --left) {
         CUDA_TRY(launch_one_2d(c, c->cur, c->stream));
@@ -1046,7 +1121,51 @@ extern "C" glbm_status glbm_step(glbm_ctx *c, int64_t n)
             done = std::min(done, k);
         }
     } else {
-        for (int64_t left = n; left > 0 && !bad;) {
+        bool strict = true;
+        if (n > 0 && df_eligible(c) && !c->halted) {
+            // dataflow chunks: the steps of a chunk overlap, so a failing step
+            // is not where the run stops; the state at the call's start is kept
+            // and, if a node leaves the positivity domain (or a wait runs out of
+            // time), restored and the call replayed one step after another,
+            // which stops exactly after the failing step (same arithmetic, same
+            // dither: the results are identical)
+            glbm_status st = df_words_ready(c);
+            if (st != GLBM_OK) return st;
+            const size_t bytes = bytes_state(c);
+            if (!c->snap) {
+                c->snap = dev_alloc(c->A, bytes, c->stream);
+                if (!c->snap) return fail(GLBM_E_NOMEM, "dataflow snapshot of %.1f MB", bytes / 1e6);
+            }
+            const int cur0 = c->cur;
+            CUDA_TRY(cudaMemcpyAsync(c->snap, c->buf[cur0], bytes, cudaMemcpyDeviceToDevice,
+                                     c->stream));
+            unsigned flags = 0u;
+            for (int64_t left = n; left > 0 && !flags;) {
+                const int64_t m = std::min<int64_t>(left, (int64_t)1 << 30);
+                int64_t k = 0;
+                st = step_nd(c, m, &k, true);
+                if (st != GLBM_OK) return st;
+                done += k;
+                left -= m;
+                flags = c->h_status[ST_FLAGS] & (ST_UNSTABLE | ST_TIMEOUT);
+            }
+            strict = flags != 0u;
+            if (strict) {
+                CUDA_TRY(cudaMemcpyAsync(c->buf[cur0], c->snap, bytes, cudaMemcpyDeviceToDevice,
+                                         c->stream));
+                c->cur = cur0;
+                CUDA_TRY(set_clock(c, t0));
+                CUDA_TRY(clear_unstable(c));
+                done = 0;
+                if (flags & ST_TIMEOUT) {
+                    CUDA_TRY(cudaStreamSynchronize(c->stream));
+                    return fail(GLBM_E_TIMEOUT,
+                                "a dataflow step waited more than 0.5 s for its rows; the state is "
+                                "that of time %lld again (no step applied)", (long long)t0);
+                }
+            }
+        }
+        for (int64_t left = strict ? n : 0; left > 0 && !bad;) {
             const int64_t m = std::min<int64_t>(left, (int64_t)1 << 30);
             int64_t k = 0;
             glbm_status st = step_nd(c, m, &k);
@@ -1062,6 +1181,7 @@ extern "C" glbm_status glbm_step(glbm_ctx *c, int64_t n)
         }
     }
     c->t = t0 + done;
+    if (bad) c->halted = true;
     if (bad)
         return fail(GLBM_E_UNSTABLE,
                     "a node left the positivity domain (|u| > sqrt(2/3) N per axis, or rho <= 0); "
@@ -1316,7 +1436,8 @@ struct Scratch {
 };
 
 extern "C" glbm_status glbm_adjoint_flowrate(glbm_ctx *c, int64_t steps, int64_t ckpt_every,
-                                             double *J, double *dJ_dtau, double *dJ_dg)
+                                             double *J, double *dJ_dtau, double *dJ_dg,
+                                             double *dJ_du_lo, double *dJ_du_hi)
 {
     if (!c || !J || !dJ_dtau || !dJ_dg) return fail(GLBM_E_INVAL, "null argument");
     if (c->dims != 2 || c->hetero)
@@ -1336,8 +1457,8 @@ extern "C" glbm_status glbm_adjoint_flowrate(glbm_ctx *c, int64_t steps, int64_t
     char *seg = (char *)S.get(pool * K);
     double *mu0 = (double *)S.get(mu_bytes), *mu1 = (double *)S.get(mu_bytes);
     double *G = (double *)S.get(2 * (size_t)g.Lx * sizeof(double));
-    double *gpart = (double *)S.get(2 * (size_t)nblk * sizeof(double));
-    double *gsum = (double *)S.get(2 * sizeof(double));
+    double *gpart = (double *)S.get(GLBM_ADJ_NG * (size_t)nblk * sizeof(double));
+    double *gsum = (double *)S.get(GLBM_ADJ_NG * sizeof(double));
     if (!ck || !seg || !mu0 || !mu1 || !G || !gpart || !gsum)
         return fail(GLBM_E_NOMEM, "adjoint scratch of %.1f MB failed",
                     (pool * (nseg + K) + 2.0 * mu_bytes) / 1e6);
@@ -1377,7 +1498,10 @@ extern "C" glbm_status glbm_adjoint_flowrate(glbm_ctx *c, int64_t steps, int64_t
         double *mu_cur = mu0, *mu_nxt = mu1;
         a.mu_out = mu_cur;
         CUDA_TRY(glbm_launch_adj_seed(a, c->stream));
-        CUDA_TRY(cudaMemsetAsync(gpart, 0, 2 * (size_t)nblk * sizeof(double), c->stream));
+        CUDA_TRY(cudaMemsetAsync(gpart, 0, GLBM_ADJ_NG * (size_t)nblk * sizeof(double), c->stream));
+        // the wall speeds' term of F_T, from X_T (the state after the forward run)
+        a.X = (const char *)c->buf[c->cur] + (size_t)c->geo[i].off * c->elem;
+        CUDA_TRY(glbm_launch_adj_final_walls(a, c->stream));
         for (int64_t s = nseg - 1; s >= 0; --s) {
             const int64_t t0 = s * K, len = std::min<int64_t>(K, steps - t0);
             // recompute X_t0 .. X_t0+len-1 with the dither counter of the forward pass
@@ -1397,11 +1521,13 @@ extern "C" glbm_status glbm_adjoint_flowrate(glbm_ctx *c, int64_t steps, int64_t
             }
         }
         CUDA_TRY(glbm_launch_adj_sum(gpart, nblk, gsum, c->stream));
-        double h[2];
+        double h[GLBM_ADJ_NG];
         CUDA_TRY(cudaMemcpyAsync(h, gsum, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
         CUDA_TRY(cudaStreamSynchronize(c->stream));
         dJ_dtau[i] = h[0];
         dJ_dg[i] = h[1];
+        if (dJ_du_lo) dJ_du_lo[i] = h[2];
+        if (dJ_du_hi) dJ_du_hi[i] = h[3];
     }
     CUDA_TRY(set_clock(c, t_end));
     CUDA_TRY(cudaStreamSynchronize(c->stream));
@@ -1453,11 +1579,21 @@ extern "C" glbm_status glbm_get_tile_shape(const glbm_ctx *c, int k, int *G, int
 static glbm_status tiles_changed(glbm_ctx *c)
 {
     CUDA_TRY(cudaStreamSynchronize(c->stream));
-    for (int i = 0; i < 2; ++i) {
-        if (c->graph[i]) cudaGraphExecDestroy(c->graph[i]);
-        c->graph[i] = nullptr;
-    }
+    drop_graphs(c);
     return c->hetero ? build_items(c) : GLBM_OK;
+}
+
+extern "C" glbm_status glbm_set_dataflow(glbm_ctx *c, int on)
+{
+    if (!c) return fail(GLBM_E_INVAL, "null context");
+    if (on != 0 && on != 1) return fail(GLBM_E_INVAL, "dataflow mode %d (0 or 1)", on);
+    c->dataflow = on;
+    return GLBM_OK;
+}
+
+extern "C" int glbm_get_dataflow(const glbm_ctx *c)
+{
+    return c && df_eligible(c) ? 1 : 0;
 }
 
 extern "C" glbm_status glbm_set_wall_launch(glbm_ctx *c, int mode)
@@ -1508,6 +1644,75 @@ static cudaError_t launch_level_once(const glbm_ctx *c, int N)
 {
     if (c->hetero) return glbm_launch_batched_level(N, batch_args(c, c->cur), false, c->stream);
     return launch_one_2d(c, c->cur, c->stream);
+}
+
+// Time `steps` steps of the context from its current state, with the step
+// path as configured; the state, buffer parity and clock are put back from the
+// copy in c->snap (which the caller made).
+static glbm_status time_steps(glbm_ctx *c, int64_t steps, bool df, cudaEvent_t e0, cudaEvent_t e1,
+                              float *ms)
+{
+    const int cur0 = c->cur;
+    const int64_t t0 = c->t;
+    const size_t bytes = bytes_state(c);
+    int64_t k = 0;
+    for (int rep = 0; rep < 2; ++rep) {  // the first run captures the chunk graphs
+        CUDA_TRY(cudaEventRecord(e0, c->stream));
+        glbm_status st = step_nd(c, steps, &k, df);
+        if (st != GLBM_OK) return st;
+        CUDA_TRY(cudaEventRecord(e1, c->stream));
+        CUDA_TRY(cudaEventSynchronize(e1));
+        CUDA_TRY(cudaEventElapsedTime(ms, e0, e1));
+        CUDA_TRY(cudaMemcpyAsync(c->buf[cur0], c->snap, bytes, cudaMemcpyDeviceToDevice, c->stream));
+        c->cur = cur0;
+        CUDA_TRY(set_clock(c, t0));
+        CUDA_TRY(clear_unstable(c));
+    }
+    return GLBM_OK;
+}
+
+// The last stage of glbm_autotune for contexts whose steps can take dataflow
+// chunks: 128 steps with the choice made so far (launch after launch), then
+// 128 steps in dataflow chunks with every tile shape of the level (wall
+// densities from the tiles); the fastest of all is kept, dataflow on or off.
+static glbm_status autotune_dataflow(glbm_ctx *c, cudaEvent_t e0, cudaEvent_t e1)
+{
+    const int N = c->geo[0].N;
+    glbm_status st = df_words_ready(c);
+    if (st != GLBM_OK) return st;
+    const size_t bytes = bytes_state(c);
+    if (!c->snap) {
+        c->snap = dev_alloc(c->A, bytes, c->stream);
+        if (!c->snap) return fail(GLBM_E_NOMEM, "dataflow snapshot of %.1f MB", bytes / 1e6);
+    }
+    CUDA_TRY(cudaMemcpyAsync(c->snap, c->buf[c->cur], bytes, cudaMemcpyDeviceToDevice, c->stream));
+    const int64_t steps = 2 * kGraphChunk;
+    const int tile0 = c->tile[N];
+    const bool wall0 = c->wall_launch;
+    float best = 0.f;
+    st = tiles_changed(c);
+    if (st == GLBM_OK) st = time_steps(c, steps, false, e0, e1, &best);
+    int best_tile = tile0;
+    bool best_wall = wall0, best_df = false;
+    TileShape sh[GLBM_MAX_TILES];
+    const int n = ctx_tile_shapes(c, N, sh);
+    for (int idx = 0; idx < n && st == GLBM_OK; ++idx) {
+        c->tile[N] = idx;
+        c->wall_launch = false;
+        st = tiles_changed(c);
+        float ms = 0.f;
+        if (st == GLBM_OK) st = time_steps(c, steps, true, e0, e1, &ms);
+        if (st == GLBM_OK && ms < best) {
+            best = ms;
+            best_tile = idx;
+            best_wall = false;
+            best_df = true;
+        }
+    }
+    c->tile[N] = best_tile;
+    c->wall_launch = best_wall;
+    c->dataflow = best_df ? 1 : 0;
+    return st;
 }
 
 extern "C" glbm_status glbm_autotune(glbm_ctx *c, int reps, double *us)
@@ -1575,6 +1780,12 @@ extern "C" glbm_status glbm_autotune(glbm_ctx *c, int reps, double *us)
             if (e != cudaSuccess) st = fail(GLBM_E_CUDA, "autotune launch: %s", cudaGetErrorString(e));
         }
         c->wall_launch = ms_mode[1] < ms_mode[0];
+    }
+    // and last, for contexts that can step in dataflow chunks, whole chunks of
+    // steps both ways (a launch timed alone cannot show the overlap)
+    if (st == GLBM_OK && !c->hetero && c->dims == 2 && c->geo[0].N <= GLBM_MAXN_2N1) {
+        c->dataflow = 1;
+        st = autotune_dataflow(c, e0, e1);
     }
     if (e1) cudaEventDestroy(e1);
     cudaEventDestroy(e0);

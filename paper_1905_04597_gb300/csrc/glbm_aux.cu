@@ -4,6 +4,7 @@
 // stress as central moments), deterministic global sums, and the 1D step
 // (Sec. 5.1 shock tube, halfway bounce-back) both per launch and resident in
 // one CTA for many steps.
+#include <algorithm>
 #include <mutex>
 
 #include "glbm_device.cuh"
@@ -824,5 +825,81 @@ cudaError_t glbm_launch_channel_diagnostics(const double *mom, int Lx, int Ly, i
 {
     k_row_means<<<Ly, ROW_THREADS, 0, s>>>(mom, Lx, Ly, Lz, prof);
     k_channel_stats<<<1, ROW_THREADS, 0, s>>>(prof, Ly, p, stats);
+    return cudaGetLastError();
+}
+
+// FP64 FMA throughput probe (glbm_measure_fp64_rate): a measurement aid for the
+// FP64 roofline, not part of the method. Every thread runs 8 independent FMA
+// chains (enough independent work per warp to keep the FP64 pipe busy), and
+// the sum goes to a sink only when it takes a value it never takes, so the
+// chains are not removed.
+namespace {
+constexpr int PROBE_CHAINS = 8;
+
+__global__ void k_fp64_rate(double *sink, int iters, double a, double b)
+{
+    double x[PROBE_CHAINS];
+#pragma unroll
+    for (int c = 0; c < PROBE_CHAINS; ++c) x[c] = 1e-3 * (threadIdx.x + c);
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int c = 0; c < PROBE_CHAINS; ++c) x[c] = fma(x[c], a, b);
+    }
+    double s = 0.0;
+#pragma unroll
+    for (int c = 0; c < PROBE_CHAINS; ++c) s += x[c];
+    if (s == -1.0) sink[threadIdx.x] = s;
+}
+}  // namespace
+
+extern "C" glbm_status glbm_measure_fp64_rate(void *stream, double *fma_per_s)
+{
+    if (!fma_per_s) return glbm_set_error(GLBM_E_INVAL, "null argument");
+    const cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    double *sink = nullptr;
+    if (e == cudaSuccess) e = cudaMalloc(&sink, 256 * sizeof(double));
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    const int threads = 256, blocks = sms * 8, iters = 4096;
+    double best = 0.0;
+    for (int rep = 0; rep < 3 && e == cudaSuccess; ++rep) {
+        cudaEventRecord(e0, s);
+        k_fp64_rate<<<blocks, threads, 0, s>>>(sink, iters, 0.9999999, 1e-7);
+        cudaEventRecord(e1, s);
+        e = cudaEventSynchronize(e1);
+        float ms = 0.0f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        const double rate = (double)blocks * threads * iters * PROBE_CHAINS / (ms * 1e-3);
+        if (e == cudaSuccess && rep > 0 && rate > best) best = rate;  // the first run warms up
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (sink) cudaFree(sink);
+    if (e != cudaSuccess) return glbm_set_error(GLBM_E_CUDA, "FP64 probe: %s", cudaGetErrorString(e));
+    *fma_per_s = best;
+    return GLBM_OK;
+}
+
+// Start of a dataflow chunk (glbm_internal.h): the band counts and the
+// per-step CTA counts go back to zero, and ST_BASE takes the step clock that
+// the chunk's first step starts from.
+namespace {
+__global__ void k_df_start(unsigned *status, unsigned *words, long long n)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+        words[i] = 0u;
+    if (blockIdx.x == 0 && threadIdx.x == 0) status[ST_BASE] = status[ST_CLOCK];
+}
+}  // namespace
+
+cudaError_t glbm_launch_df_start(unsigned *status, unsigned *words, long long n, cudaStream_t s)
+{
+    const int blocks = (int)std::min<long long>((n + 255) / 256, 1024);
+    k_df_start<<<blocks > 0 ? blocks : 1, 256, 0, s>>>(status, words, n);
     return cudaGetLastError();
 }

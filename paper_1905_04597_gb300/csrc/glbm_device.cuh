@@ -73,6 +73,110 @@ __device__ __forceinline__ void finish_step(unsigned *status)
     }
 }
 
+// Load of a population by the step tiles: through L2 (ld.global.cg), not the
+// read-only path, because in a dataflow chunk (below) another grid may still
+// have been writing the input when this one started; the band counts' acquire
+// orders those writes before the load. (Measured on GB300: within 2 % of the
+// read-only path when the steps do not overlap.)
+template <typename T>
+__device__ __forceinline__ T ld_pop(const T *p)
+{
+    return __ldcg(p);
+}
+
+// ---- dataflow stepping (GLBM_DF_CHUNK, glbm_internal.h) -------------------
+
+// Let the next launch of the stream start its CTAs now (their waits below
+// keep them off data that is not ready).
+__device__ __forceinline__ void df_launch_next() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+__device__ __forceinline__ unsigned ld_acquire(const unsigned *p)
+{
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Wait (bounded) until every band of rows [r0, r1] of instance `inst` counts at
+// least `need` finished tiles. Rows outside 0..Ly-1 wrap (periodic along y) or
+// clamp (walls). Warp 0 polls, one row per lane per pass; after half a second
+// a lane gives up, sets ST_TIMEOUT and ST_HALT (so no later step stores, and
+// the host reports the timeout), and the CTA goes on. Every thread of the CTA
+// calls it; the barrier at the end orders the acquire before every thread's
+// loads.
+__device__ __forceinline__ void df_wait_rows(const unsigned *bands, unsigned *status, int inst,
+                                             int r0, int r1, int Ly, int R, bool periodic,
+                                             unsigned need)
+{
+    if (threadIdx.x < 32) {
+        const int nb = gridDim.y;
+        for (int r = r0 + (int)threadIdx.x; r <= r1; r += 32) {
+            int row = r;
+            if (periodic) {
+                row %= Ly;
+                if (row < 0) row += Ly;
+            } else {
+                row = row < 0 ? 0 : (row >= Ly ? Ly - 1 : row);
+            }
+            const unsigned *c = bands + (long long)inst * nb + row / R;
+            if (ld_acquire(c) >= need) continue;
+            const unsigned long long t0 = global_ns();
+            bool gave_up = false;
+            while (ld_acquire(c) < need) {
+                // a halted run stores nothing more: stop waiting
+                if (ld_acquire(status + ST_HALT) != 0u) {
+                    gave_up = true;
+                    break;
+                }
+                __nanosleep(256);
+                if (global_ns() - t0 > 500000000ull) {  // 0.5 s
+                    atomicOr(status + ST_FLAGS, (unsigned)ST_TIMEOUT);
+                    atomicExch(status + ST_HALT, 1u);
+                    gave_up = true;
+                    break;
+                }
+            }
+            if (gave_up) break;
+        }
+    }
+    __syncthreads();
+}
+
+// This CTA's tile of band blockIdx.y of instance `inst` has finished its step:
+// after the barrier, one thread's fence releases every thread's stores of the
+// CTA (the barrier orders them before it), then the band count goes up by one.
+// A fence by every thread would hold each warp until its stores land.
+__device__ __forceinline__ void df_tile_done(unsigned *bands, int inst)
+{
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        atomicAdd(bands + (long long)inst * gridDim.y + blockIdx.y, 1u);
+    }
+}
+
+// finish_step of a dataflow launch: its CTAs count in their own word of the
+// chunk (launches overlap), the last one advances the clocks.
+__device__ __forceinline__ void finish_step_df(unsigned *status, unsigned *done)
+{
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const unsigned total = gridDim.x * gridDim.y * gridDim.z;
+        if (atomicAdd(done, 1u) == total - 1u) {
+            atomicAdd(status + ST_CLOCK, 1u);
+            atomicAdd(status + ST_STEPS, 1u);
+            if (atomicOr(status + ST_FLAGS, 0u) & ST_UNSTABLE) atomicExch(status + ST_HALT, 1u);
+        }
+    }
+}
+
 // A node left the positivity domain: set the status flag, visible device-wide
 // before this thread goes on (so before its CTA's finish_step count), the
 // only path that pays for a fence.

@@ -119,8 +119,28 @@ AxisTable glbm_narrow_table(const AxisTableHi &t);
 // set, after which the launches of later steps do nothing. Every CTA reads
 // ST_CLOCK and ST_HALT when it starts and adds to ST_DONE when it ends: the
 // counter has a 128-byte line of its own, so that those reads do not queue
-// behind its atomics at L2.
-enum { ST_FLAGS = 0, ST_CLOCK = 32, ST_HALT = 33, ST_DONE = 64, ST_STEPS = 65, ST_WORDS = 96 };
+// behind its atomics at L2. ST_BASE is the step clock at the start of a
+// dataflow chunk (below); ST_FLAGS bit 1 records a dataflow wait that ran out
+// of time.
+enum {
+    ST_FLAGS = 0, ST_CLOCK = 32, ST_HALT = 33, ST_BASE = 34, ST_DONE = 64, ST_STEPS = 65,
+    ST_WORDS = 96
+};
+enum { ST_UNSTABLE = 1u, ST_TIMEOUT = 2u };  // bits of ST_FLAGS
+
+// Dataflow stepping of uniform 2D contexts: the launches of a chunk of steps
+// overlap. Every CTA lets the next step's grid launch as soon as it starts
+// (griddepcontrol.launch_dependents), and instead of waiting for the whole
+// previous grid it waits only for the row bands its pulls read and its stores
+// overwrite: a CTA covering rows [y0, y0 + R) of step k waits until every
+// tile of the bands holding rows [y0 - V, y0 + R - 1 + V] (V the largest y
+// speed) has finished step k - 1. Finished tiles are counted per (instance,
+// band) in `bands`, reset at the start of each chunk, so step k of the chunk
+// waits for k times the tiles of a band. A chunk's first step and a launch
+// that follows anything else wait for the whole previous work as usual.
+constexpr int GLBM_DF_CHUNK = 64;  // steps per dataflow chunk (the graph chunk)
+// Zero the n counting words of a chunk and set ST_BASE from ST_CLOCK.
+cudaError_t glbm_launch_df_start(unsigned *status, unsigned *words, long long n, cudaStream_t s);
 
 // Per-instance constants read by the step kernels (one per lattice instance).
 struct InstParams {
@@ -144,6 +164,8 @@ struct InstParams {
     long long plane;  // elements per velocity plane (Ly * pitch)
     double g_half;    // g / 2: Guo's half-force velocity shift (0 otherwise)
     float g_half_f;
+    double dew_lo[GLBM_MAXQA];  // dE^x_i/du at u_wall_lo (2N+1 x axis; the adjoint)
+    double dew_hi[GLBM_MAXQA];  // dE^x_i/du at u_wall_hi
 };
 
 // Arguments of one uniform (same geometry for every instance) 2D step; TY is
@@ -160,6 +182,9 @@ struct Step2DArgsT {
     unsigned *done_ctr;   // CTAs finished in the current launch
     void *rw;             // wall densities, 2 x pitch per instance (k_wall_rho), or null:
                           // then every tile near a wall sums them itself
+    unsigned *bands;      // dataflow: finished tiles per (instance, row band), or null
+    unsigned *node_done;  // dataflow: CTAs finished per step of the chunk
+    int node;             // dataflow: this step's index in its chunk
     int Lx, Ly, pitch, bc;
     long long plane;      // elements per velocity plane
     long long inst_stride;// elements per instance
@@ -304,11 +329,15 @@ struct AdjArgs {
     double *mu_out;        // mu_t
     const double *G;       // [2][Lx] wall sums of mu_in (lower, upper)
     double *Gw;            // the same array, written by the wall kernel
-    double *gpart;         // [blocks][2] partials of dJ/dtau, dJ/dg, summed over steps
+    double *gpart;         // [blocks][GLBM_ADJ_NG] partials of dJ/dtau, dJ/dg, dJ/du_lo,
+                           // dJ/du_hi, summed over steps
     int Lx, Ly, pitch, bc, N, prec;
     long long plane;
 };
+enum { GLBM_ADJ_NG = 4 };  // gradient components of the adjoint
 long long glbm_adj_blocks(int Lx, int Ly);
 cudaError_t glbm_launch_adj_seed(const AdjArgs &a, cudaStream_t s);
+// the wall speeds' term of F_T = S(X_T) (a.X = X_T, mu_T the seed), into gpart
+cudaError_t glbm_launch_adj_final_walls(const AdjArgs &a, cudaStream_t s);
 cudaError_t glbm_launch_adj_step(const AdjArgs &a, cudaStream_t s);
 cudaError_t glbm_launch_adj_sum(const double *gpart, long long nblocks, double *out, cudaStream_t s);

@@ -86,12 +86,12 @@ struct Step2D {
                         if (need_lo) {  // velocity ny = -|v_m| leaving row k through y = -1/2
                             const T *pl = fin + (AY::ineg(m) * QX * plane + k * pitch);
 #pragma unroll
-                            for (int ix = 0; ix < QX; ++ix) vlo[u][ix] = __ldg(pl + cofs[ix]);
+                            for (int ix = 0; ix < QX; ++ix) vlo[u][ix] = ld_pop(pl + cofs[ix]);
                         }
                         if (need_hi) {  // velocity ny = +|v_m| leaving row Ly-1-k through y = Ly-1/2
                             const T *ph = fin + (AY::ipos(m) * QX * plane + (Ly - 1 - k) * pitch);
 #pragma unroll
-                            for (int ix = 0; ix < QX; ++ix) vhi[u][ix] = __ldg(ph + cofs[ix]);
+                            for (int ix = 0; ix < QX; ++ix) vhi[u][ix] = ld_pop(ph + cofs[ix]);
                         }
                     }
                 }
@@ -124,6 +124,27 @@ struct Step2D {
             rw[1][lane] = s1 * inv_den;
         }
         __syncthreads();
+    }
+
+    // Loads of this warp group's velocity rows iy = g + k G of the pull, all
+    // independent (rows beyond a wall clamp to the edge row; their values are
+    // replaced by the wall's emission afterwards).
+    __device__ static void pull_rows(const T *__restrict__ fin, int g, int yc, int Ly, int pitch,
+                                     int plane, bool walls, const int (&cofs)[QX],
+                                     T (&f)[RPG][QX])
+    {
+#pragma unroll
+        for (int k = 0; k < RPG; ++k) {
+            const int iy = g + k * G;
+            if (iy < Q1) {
+                const int ny = AY::vel(iy);
+                int ys = yc - ny;
+                ys = walls ? min(max(ys, 0), Ly - 1) : wrap_shift(ys, Ly, Ly > AY::VMAX);
+                const T *rowp = fin + (iy * QX * plane + ys * pitch);
+#pragma unroll
+                for (int ix = 0; ix < QX; ++ix) f[k][ix] = ld_pop(rowp + cofs[ix]);
+            }
+        }
     }
 
     // One tile: columns x0..x0+31, rows y0..y0+R-1 of one instance whose
@@ -173,18 +194,7 @@ struct Step2D {
         T f[RPG][QX];
         T s_r = T(0), c_r = T(0), s_x = T(0), c_x = T(0), s_y = T(0), c_y = T(0);
         // loads first, all independent
-#pragma unroll
-        for (int k = 0; k < RPG; ++k) {
-            const int iy = g + k * G;
-            if (iy < Q1) {
-                const int ny = AY::vel(iy);
-                int ys = yc - ny;
-                ys = walls ? min(max(ys, 0), Ly - 1) : wrap_shift(ys, Ly, Ly > AY::VMAX);
-                const T *rowp = fin + (iy * QX * plane + ys * pitch);
-#pragma unroll
-                for (int ix = 0; ix < QX; ++ix) f[k][ix] = __ldg(rowp + cofs[ix]);
-            }
-        }
+        pull_rows(fin, g, yc, Ly, pitch, plane, walls, cofs, f);
         // wall re-emission and row sums
 #pragma unroll
         for (int k = 0; k < RPG; ++k) {
@@ -454,14 +464,27 @@ __global__ void __launch_bounds__(32 * G * R)
 {
     using S = Step2D<N, T, G, R, NXL, ZY, ZX, GUO>;
     __shared__ typename S::Smem sm;
-    wait_prior_grid();
+    const int inst = blockIdx.z;
+    const bool df = a.bands != nullptr;  // dataflow chunk (glbm_internal.h)
+    if (df) {
+        df_launch_next();
+        if (a.node > 0) {
+            constexpr int V = S::AY::VMAX;
+            const int y0 = blockIdx.y * R;
+            df_wait_rows(a.bands, a.status, inst, y0 - V, y0 + R - 1 + V, a.Ly, R,
+                         a.bc != GLBM_BC_WALLS, (unsigned)a.node * gridDim.x);
+        }
+    } else {
+        wait_prior_grid();
+    }
     // read here, needed only at the stores: no CTA waits for it before its loads
     const bool live = !step_halted(a.status);
-    const int inst = blockIdx.z;
     const T *fin = static_cast<const T *>(a.fin) + (long long)inst * a.inst_stride;
     T *fout = static_cast<T *>(a.fout) + (long long)inst * a.inst_stride;
-    // launch counter (read before any CTA of this launch can advance it)
-    const unsigned seed = S::DEV ? hash32(__ldcg(a.step_ctr) * 0x632BE5ABu + inst) : 0u;
+    // the step clock: the launch counter (read before any CTA of this launch
+    // can advance it), or the chunk's base plus this step's index
+    const unsigned clk = df ? __ldcg(a.status + ST_BASE) + (unsigned)a.node : __ldcg(a.step_ctr);
+    const unsigned seed = S::DEV ? hash32(clk * 0x632BE5ABu + inst) : 0u;
     const T *rwg = a.rw ? static_cast<const T *>(a.rw) + (long long)inst * 2 * a.pitch : nullptr;
     if constexpr (NXL == N && ZX == ZY)
         S::run(a.tab, a.tab, a.ip[inst], a.Lx, a.Ly, a.pitch, (int)a.plane, a.bc, fin, fout,
@@ -469,7 +492,12 @@ __global__ void __launch_bounds__(32 * G * R)
     else
         S::run(a.tab, a.tabx, a.ip[inst], a.Lx, a.Ly, a.pitch, (int)a.plane, a.bc, fin, fout,
                blockIdx.x * 32, blockIdx.y * R, sm, a.status, seed, rwg, live);
-    if (live) finish_step(a.status);
+    if (df) {
+        df_tile_done(a.bands, inst);
+        if (live) finish_step_df(a.status, a.node_done + a.node);
+    } else if (live) {
+        finish_step(a.status);
+    }
 }
 
 // Wall densities of one step computed once per column and wall, for lattices

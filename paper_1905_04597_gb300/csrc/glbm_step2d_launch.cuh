@@ -10,13 +10,26 @@ __global__ void __launch_bounds__(32 * G * R)
 {
     using S = Step2DPair<N, G, R, NXL, ZY, ZX>;
     __shared__ __align__(16) typename S::Smem sm;
-    wait_prior_grid();
-    const bool live = !step_halted(a.status);  // needed only at the stores
     const int inst = blockIdx.z;
+    const bool df = a.bands != nullptr;  // dataflow chunk (glbm_internal.h)
+    if (df) {
+        df_launch_next();
+        if (a.node > 0) {
+            constexpr int V = AxisVel<N, ZY>::VMAX;
+            const int y0 = blockIdx.y * R;
+            df_wait_rows(a.bands, a.status, inst, y0 - V, y0 + R - 1 + V, a.Ly, R,
+                         a.bc != GLBM_BC_WALLS, (unsigned)a.node * gridDim.x);
+        }
+    } else {
+        wait_prior_grid();
+    }
+    const bool live = !step_halted(a.status);  // needed only at the stores
     const float *fin = static_cast<const float *>(a.fin) + (long long)inst * a.inst_stride;
     float *fout = static_cast<float *>(a.fout) + (long long)inst * a.inst_stride;
-    // launch counter (read before any CTA of this launch can advance it)
-    const unsigned seed = hash32(__ldcg(a.step_ctr) * 0x632BE5ABu + inst);
+    // the step clock: the launch counter (read before any CTA of this launch
+    // can advance it), or the chunk's base plus this step's index
+    const unsigned clk = df ? __ldcg(a.status + ST_BASE) + (unsigned)a.node : __ldcg(a.step_ctr);
+    const unsigned seed = hash32(clk * 0x632BE5ABu + inst);
     const float *rwg =
         a.rw ? static_cast<const float *>(a.rw) + (long long)inst * 2 * a.pitch : nullptr;
     if constexpr (NXL == N && ZX == ZY)
@@ -25,10 +38,27 @@ __global__ void __launch_bounds__(32 * G * R)
     else
         S::run(a.tab, a.tabx, a.ip[inst], a.Lx, a.Ly, a.pitch, (int)a.plane, a.bc, fin, fout,
                blockIdx.x * S::TW, blockIdx.y * R, sm, a.status, seed, rwg, live);
-    if (live) finish_step(a.status);
+    if (df) {
+        df_tile_done(a.bands, inst);
+        if (live) finish_step_df(a.status, a.node_done + a.node);
+    } else if (live) {
+        finish_step(a.status);
+    }
 }
 
-// Launch with programmatic stream serialization (see wait_prior_grid).
+// Launch with programmatic stream serialization (see wait_prior_grid), except
+// the first step of a dataflow chunk, which waits for all work before it.
+template <class TY>
+inline bool programmatic(const Step2DArgsT<TY> &a)
+{
+    return !(a.bands && a.node == 0);
+}
+template <typename Args>
+inline bool programmatic(const Args &)
+{
+    return true;
+}
+
 template <typename Args>
 inline cudaError_t launch_serialized(void (*kern)(Args), dim3 grid, dim3 block, cudaStream_t s,
                                      const Args &a)
@@ -42,7 +72,7 @@ inline cudaError_t launch_serialized(void (*kern)(Args), dim3 grid, dim3 block, 
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
-    cfg.numAttrs = 1;
+    cfg.numAttrs = programmatic(a) ? 1 : 0;
     return cudaLaunchKernelEx(&cfg, kern, a);
 }
 

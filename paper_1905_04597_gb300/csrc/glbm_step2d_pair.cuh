@@ -52,16 +52,16 @@ __device__ __forceinline__ void pair_wall_densities(const InstParams &ip, const 
                 const float *pl = fin + (AY::ineg(m) * Q1 * plane + k * pitch);
 #pragma unroll
                 for (int ix = 0; ix < Q1; ++ix) {
-                    slo0 += __ldg(pl + (ix * plane + win[AX::VMAX - AX::vel(ix)]));
-                    slo1 += __ldg(pl + (ix * plane + win[AX::VMAX - AX::vel(ix) + 1]));
+                    slo0 += ld_pop(pl + (ix * plane + win[AX::VMAX - AX::vel(ix)]));
+                    slo1 += ld_pop(pl + (ix * plane + win[AX::VMAX - AX::vel(ix) + 1]));
                 }
             }
             if (need_hi) {  // velocity ny = +|v_m| leaving row Ly-1-k through y = Ly-1/2
                 const float *ph = fin + (AY::ipos(m) * Q1 * plane + (Ly - 1 - k) * pitch);
 #pragma unroll
                 for (int ix = 0; ix < Q1; ++ix) {
-                    shi0 += __ldg(ph + (ix * plane + win[AX::VMAX - AX::vel(ix)]));
-                    shi1 += __ldg(ph + (ix * plane + win[AX::VMAX - AX::vel(ix) + 1]));
+                    shi0 += ld_pop(ph + (ix * plane + win[AX::VMAX - AX::vel(ix)]));
+                    shi1 += ld_pop(ph + (ix * plane + win[AX::VMAX - AX::vel(ix) + 1]));
                 }
             }
         }
@@ -107,16 +107,16 @@ __device__ __forceinline__ void pair_load_row(const float *__restrict__ fin, int
             const int nx = AX::vel(ix);
             const float *p = rowp + (ix * plane + (x - nx));
             if ((nx & 1) == 0)  // (x - nx) even: one aligned 8-byte load
-                f[ix] = __ldg(reinterpret_cast<const f32x2 *>(p));
+                f[ix] = ld_pop(reinterpret_cast<const f32x2 *>(p));
             else
-                f[ix] = pk2(__ldg(p), __ldg(p + 1));
+                f[ix] = pk2(ld_pop(p), ld_pop(p + 1));
         }
     } else {
 #pragma unroll
         for (int ix = 0; ix < Q1; ++ix) {
             const float *p = rowp + ix * plane;
             const int j = AX::VMAX - AX::vel(ix);
-            f[ix] = pk2(__ldg(p + win[j]), __ldg(p + win[j + 1]));
+            f[ix] = pk2(ld_pop(p + win[j]), ld_pop(p + win[j + 1]));
         }
     }
 }

@@ -91,7 +91,10 @@ def lib():
         "glbm_tau": ([vp, i], ctypes.c_double),
         "glbm_eq_table": ([i, dp, sz], i),
         "glbm_conservation_noalloc": ([vp, i, i64, vp, vp], i),
-        "glbm_adjoint_flowrate": ([vp, i64, i64, dp, dp, dp], i),
+        "glbm_measure_fp64_rate": ([vp, dp], i),
+        "glbm_set_dataflow": ([vp, i], i),
+        "glbm_get_dataflow": ([vp], i),
+        "glbm_adjoint_flowrate": ([vp, i64, i64, dp, dp, dp, dp, dp], i),
         "glbm_tile_count": ([i, i], i),
         "glbm_tile_shape": ([i, i, i, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i)], i),
         "glbm_get_tiles": ([vp, ctypes.POINTER(i)], i),
@@ -371,13 +374,15 @@ class Lattice:
     def load(self, path):
         check(lib().glbm_load(self.h, str(path).encode()))
 
-    def adjoint_flowrate(self, steps, ckpt_every=100):
+    def adjoint_flowrate(self, steps, ckpt_every=100, walls=False):
         """Advance `steps` steps and return per instance (J, dJ/dtau, dJ/dg) of the flow
-        rate J = (1/nx) sum of the x-momentum of S(X_T), by the discrete adjoint."""
+        rate J = (1/nx) sum of the x-momentum of S(X_T), by the discrete adjoint;
+        with walls=True also (dJ/du_wall_lo, dJ/du_wall_hi)."""
         n = self.n
-        J, dt, dg = (ctypes.c_double * n)(), (ctypes.c_double * n)(), (ctypes.c_double * n)()
-        check(lib().glbm_adjoint_flowrate(self.h, int(steps), int(ckpt_every), J, dt, dg))
-        return np.array(J[:]), np.array(dt[:]), np.array(dg[:])
+        out = [(ctypes.c_double * n)() for _ in range(5)]
+        check(lib().glbm_adjoint_flowrate(self.h, int(steps), int(ckpt_every), *out))
+        res = tuple(np.array(o[:]) for o in out)
+        return res if walls else res[:3]
 
     def tiles(self):
         """Tile shape index in use for every level k = 0..LEVELS-1."""
@@ -414,6 +419,16 @@ class Lattice:
         tile near a wall sums them itself; -1: no walls (or a mixed batch, 3D)."""
         return lib().glbm_get_wall_launch(self.h)
 
+    @property
+    def dataflow(self):
+        """1 when glbm_step runs this context's steps in overlapping dataflow chunks."""
+        return lib().glbm_get_dataflow(self.h)
+
+    def set_dataflow(self, on):
+        """Overlapping dataflow chunks (1, the default where the context allows
+        them) or one launch after another (0); the results are identical."""
+        check(lib().glbm_set_dataflow(self.h, int(on)))
+
     def set_wall_launch(self, mode):
         """Choose how the wall densities are computed (0, 1, or -1 for the
         context's default); the results are identical either way."""
@@ -431,40 +446,58 @@ class Lattice:
         return lib().glbm_tau(self.h, inst)
 
 
+def measure_fp64_rate(stream=None):
+    """FP64 FMA thread instructions per second of the current device, measured
+    by the library's probe kernel (glbm_measure_fp64_rate)."""
+    out = ctypes.c_double()
+    s = stream if stream is not None else _current_stream()
+    check(lib().glbm_measure_fp64_rate(s, ctypes.byref(out)))
+    return out.value
+
+
 def _flowrate_autograd():
     import torch
 
     class FlowRate(torch.autograd.Function):
-        """J(tau, g): flow rate of a force-driven (or wall-driven) channel after
-        `steps` steps from rest, with gradients from the hand-written adjoint.
+        """J(tau, g, u_wall_lo, u_wall_hi): flow rate of a force-driven (or
+        wall-driven) channel after `steps` steps from rest, with gradients from
+        the hand-written adjoint.
 
-        config: glbm lattice configuration without tau/g (dims, nx, ny, k, bc,
-        prec, u_wall_lo, u_wall_hi); tau and g are 0-d float64 tensors."""
+        config: glbm lattice configuration without tau, g and the wall speeds
+        (dims, nx, ny, k, bc, prec); the four parameters are 0-d float64
+        tensors or numbers."""
 
         @staticmethod
-        def forward(ctx, tau, g, config, steps, ckpt_every=100):
-            cfg = dict(config, tau=float(tau), kn=0.0, g=float(g))
+        def forward(ctx, tau, g, u_lo, u_hi, config, steps, ckpt_every=100):
+            cfg = dict(config, tau=float(tau), kn=0.0, g=float(g), u_wall_lo=float(u_lo),
+                       u_wall_hi=float(u_hi))
             dev = tau.device if isinstance(tau, torch.Tensor) else torch.device("cpu")
             f64 = dict(dtype=torch.float64, device=dev)
-            if not any(ctx.needs_input_grad[:2]):
+            if not any(ctx.needs_input_grad[:4]):
                 # no gradient wanted: the forward steps and the flow rate only
                 with Lattice(cfg) as lat:
                     lat.step(steps)
                     _, stats = lat.channel_diagnostics(0)
                 return torch.tensor(stats["flow_rate"], **f64)
             with Lattice(cfg) as lat:
-                J, dtau, dg = lat.adjoint_flowrate(steps, ckpt_every)
-            ctx.save_for_backward(torch.tensor(dtau[0], **f64), torch.tensor(dg[0], **f64))
+                J, dtau, dg, dlo, dhi = lat.adjoint_flowrate(steps, ckpt_every, walls=True)
+            ctx.save_for_backward(*[torch.tensor(v[0], **f64) for v in (dtau, dg, dlo, dhi)])
             return torch.tensor(J[0], **f64)
 
         @staticmethod
         def backward(ctx, grad):
-            dtau, dg = ctx.saved_tensors
-            return grad * dtau, grad * dg, None, None, None
+            d = ctx.saved_tensors  # dJ/dtau, dJ/dg, dJ/du_wall_lo, dJ/du_wall_hi
+            return tuple(grad * d[i] if ctx.needs_input_grad[i] else None
+                         for i in range(4)) + (None, None, None)
 
     return FlowRate
 
 
-def flow_rate(tau, g, config, steps, ckpt_every=100):
-    """Differentiable flow rate (torch.autograd) through libglbm's adjoint."""
-    return _flowrate_autograd().apply(tau, g, config, steps, ckpt_every)
+def flow_rate(tau, g, config, steps, ckpt_every=100, u_wall_lo=None, u_wall_hi=None):
+    """Differentiable flow rate (torch.autograd) through libglbm's adjoint: by
+    tau, g and, when given as tensors, the wall speeds (default: those of
+    config, else 0)."""
+    ulo = config.get("u_wall_lo", 0.0) if u_wall_lo is None else u_wall_lo
+    uhi = config.get("u_wall_hi", 0.0) if u_wall_hi is None else u_wall_hi
+    base = {k: v for k, v in config.items() if k not in ("u_wall_lo", "u_wall_hi")}
+    return _flowrate_autograd().apply(tau, g, ulo, uhi, base, steps, ckpt_every)

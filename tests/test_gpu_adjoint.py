@@ -1,6 +1,6 @@
-"""Gradient of the flow rate by the hand-written adjoint (glbm_adjoint_flowrate)
-against the oracle's forward-mode dual numbers and against central finite
-differences of GPU forward runs."""
+"""Gradient of the flow rate by the hand-written adjoint (glbm_adjoint_flowrate):
+by tau, g and both wall speeds, against the oracle's forward-mode dual numbers
+and against central finite differences of GPU forward runs."""
 import numpy as np
 import pytest
 
@@ -23,15 +23,20 @@ def _compare(cfg, steps, ckpt, fields, rtol):
     N = cfg["k"] + 1
     lat = glbm.Lattice(cfg)
     lat.set_equilibrium(0, *fields)
-    J, dtau, dg = lat.adjoint_flowrate(steps, ckpt)
+    J, dtau, dg, dlo, dhi = lat.adjoint_flowrate(steps, ckpt, walls=True)
     assert lat.time == steps
     lat.close()
     o = orc.Lattice(2, N, N, cfg["nx"], cfg["ny"], cfg.get("bc", orc.BC_WALLS), cfg["tau"],
                     cfg.get("u_wall_lo", 0.0), cfg.get("u_wall_hi", 0.0), cfg.get("g", 0.0))
-    oJ, otau, og = o.flowrate_grad(o.equilibrium(*fields), steps)
+    oJ, otau, og, olo, ohi = o.flowrate_grad(o.equilibrium(*fields), steps, walls=True)
     assert J[0] == pytest.approx(oJ, rel=rtol, abs=1e-300)
     assert dtau[0] == pytest.approx(otau, rel=rtol)
     assert dg[0] == pytest.approx(og, rel=rtol)
+    if cfg.get("bc", orc.BC_WALLS) == orc.BC_WALLS:
+        assert dlo[0] == pytest.approx(olo, rel=rtol)
+        assert dhi[0] == pytest.approx(ohi, rel=rtol)
+    else:
+        assert dlo[0] == 0.0 and dhi[0] == 0.0 and olo == 0.0 and ohi == 0.0
     return J[0], dtau[0], dg[0]
 
 
@@ -86,6 +91,57 @@ def test_adjoint_config_poiseuille_d2q121():
     fd_g = (J64(tau, c["g"] * (1 + h)) - J64(tau, c["g"] * (1 - h))) / (2 * h * c["g"])
     assert dtau[0] == pytest.approx(fd_tau, rel=1e-4)
     assert dg[0] == pytest.approx(fd_g, rel=1e-4)
+
+
+@pytest.mark.parametrize("prec,rtol", [(glbm.FP64, 1e-9), (glbm.FP32_DEV, 1e-4)])
+def test_adjoint_wall_speeds_couette(prec, rtol):
+    """Couette channel D2Q81 (k = 3), walls at -0.03 and +0.05, Kn 0.1, from a
+    sheared random state, 200 steps with checkpoints every 64: every derivative
+    against the oracle's dual numbers, and the wall speeds' against central
+    differences of FP64 GPU forward runs."""
+    nx, ny, k = 24, 20, 3
+    N = k + 1
+    tau = orc.tau_from_kn(N, ny, 0.1)
+    cfg = dict(dims=2, nx=nx, ny=ny, k=k, tau=tau, prec=prec, u_wall_lo=-0.03, u_wall_hi=0.05)
+    fields = inputs.random_macro(95, nx, ny)
+    steps = 200
+    _compare(cfg, steps, 64, fields, rtol)
+    if prec != glbm.FP64:
+        return
+    with glbm.Lattice(cfg) as lat:
+        lat.set_equilibrium(0, *fields)
+        _, _, _, dlo, dhi = lat.adjoint_flowrate(steps, 64, walls=True)
+
+    def J64(ulo, uhi):
+        with glbm.Lattice(dict(cfg, u_wall_lo=ulo, u_wall_hi=uhi)) as L:
+            L.set_equilibrium(0, *fields)
+            L.step(steps)
+            return L.conservation(0)[1] / nx
+    h = 1e-5
+    fd_lo = (J64(-0.03 + h, 0.05) - J64(-0.03 - h, 0.05)) / (2 * h)
+    fd_hi = (J64(-0.03, 0.05 + h) - J64(-0.03, 0.05 - h)) / (2 * h)
+    assert dlo[0] == pytest.approx(fd_lo, rel=1e-6)
+    assert dhi[0] == pytest.approx(fd_hi, rel=1e-6)
+
+
+def test_autograd_function_wall_speeds():
+    import torch
+    nx, ny, k = 16, 12, 1
+    config = dict(dims=2, nx=nx, ny=ny, k=k, prec=glbm.FP64)
+    tau = torch.tensor(0.9, dtype=torch.float64, requires_grad=True)
+    g = torch.tensor(0.0, dtype=torch.float64)
+    ulo = torch.tensor(-0.02, dtype=torch.float64, requires_grad=True)
+    uhi = torch.tensor(0.04, dtype=torch.float64, requires_grad=True)
+    J = glbm.flow_rate(tau, g, config, steps=60, ckpt_every=20, u_wall_lo=ulo, u_wall_hi=uhi)
+    J.backward()
+    N = k + 1
+    o = orc.Lattice(2, N, N, nx, ny, orc.BC_WALLS, 0.9, -0.02, 0.04, 0.0)
+    X0 = o.equilibrium(np.ones((ny, nx)), np.zeros((ny, nx)), np.zeros((ny, nx)))
+    oJ, otau, _, olo, ohi = o.flowrate_grad(X0, 60, walls=True)
+    assert J.item() == pytest.approx(oJ, rel=1e-10)
+    assert tau.grad.item() == pytest.approx(otau, rel=1e-9)
+    assert ulo.grad.item() == pytest.approx(olo, rel=1e-9)
+    assert uhi.grad.item() == pytest.approx(ohi, rel=1e-9)
 
 
 def test_autograd_function():

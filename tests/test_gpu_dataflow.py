@@ -1,0 +1,128 @@
+"""Dataflow stepping (overlapping launches within a chunk of steps, glbm.h
+glbm_set_dataflow) against stepping one launch after another: the same
+arithmetic and the same dither, so the populations must agree bit for bit,
+for every tile kind, both precisions, walls and periodic boundaries, several
+instances, and step counts that leave a partial chunk. Also the failure
+contract: a node leaving the positivity domain partway through a dataflow call
+stops the run exactly where the one-after-another run stops."""
+import numpy as np
+import pytest
+
+from paper_1905_04597_gb300 import glbm, inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+def _pair(cfgs, tiles=None, seed=0):
+    """Two contexts of the same instances from the same random state, one in
+    dataflow mode and one stepping launch after launch."""
+    out = []
+    for df in (1, 0):
+        lat = glbm.Lattice(cfgs)
+        if tiles is not None:
+            lat.set_tiles(tiles)
+        if cfgs[0].get("bc", glbm.BC_WALLS) == glbm.BC_WALLS:
+            lat.set_wall_launch(0)  # the wall densities from the tiles
+        lat.set_dataflow(df)
+        for i, c in enumerate(cfgs):
+            lat.set_equilibrium(i, *inputs.random_macro(seed + i, c["nx"], c["ny"]))
+        out.append(lat)
+    assert out[0].dataflow == 1 and out[1].dataflow == 0
+    return out
+
+
+def _same(a, b, n):
+    for i in range(n):
+        np.testing.assert_array_equal(a.get_populations(i), b.get_populations(i))
+
+
+CASES = [
+    # (k, x_level, zv, prec, bc, nx, ny, instances)
+    (3, 0, 0, glbm.FP32_DEV, glbm.BC_WALLS, 200, 70, 3),
+    (3, 0, 0, glbm.FP64, glbm.BC_WALLS, 96, 40, 2),
+    (0, 0, 0, glbm.FP32_DEV, glbm.BC_PERIODIC, 130, 33, 2),
+    (7, 0, 0, glbm.FP32_DEV, glbm.BC_WALLS, 70, 50, 1),
+    (4, 1, 0, glbm.FP32_DEV, glbm.BC_WALLS, 150, 45, 2),
+    (2, 1, glbm.ZV_Y, glbm.FP32_DEV, glbm.BC_WALLS, 100, 30, 2),
+    (1, 0, glbm.ZV_X | glbm.ZV_Y, glbm.FP32_DEV, glbm.BC_PERIODIC, 64, 20, 1),
+]
+
+
+@pytest.mark.parametrize("k,x_level,zv,prec,bc,nx,ny,n", CASES)
+def test_dataflow_equals_launch_after_launch(k, x_level, zv, prec, bc, nx, ny, n):
+    cfgs = [dict(dims=2, nx=nx, ny=ny, k=k, x_level=x_level, zv_axes=zv, kn=0.05 * (i + 1),
+                 prec=prec, bc=bc, u_wall_lo=-0.03, u_wall_hi=0.04, g=2e-5) for i in range(n)]
+    a, b = _pair(cfgs, seed=10 * k + n)
+    for steps in (64, 37, 130):  # whole chunks, a partial one, both
+        a.step(steps)
+        b.step(steps)
+        assert a.time == b.time
+        _same(a, b, n)
+    a.close()
+    b.close()
+
+
+@pytest.mark.parametrize("idx", range(3))
+def test_dataflow_every_couette_tile_shape(idx):
+    """The first three candidate tile shapes of Couette D2Q81 (pair and one-node
+    tiles of several row counts)."""
+    cfgs = [dict(dims=2, nx=160, ny=48, k=3, kn=kn, prec=glbm.FP32_DEV, u_wall_lo=-0.05,
+                 u_wall_hi=0.05) for kn in (0.01, 0.1, 1.0)]
+    tiles = [-1] * glbm.LEVELS
+    tiles[3] = idx
+    a, b = _pair(cfgs, tiles=tiles, seed=40 + idx)
+    a.step(200)
+    b.step(200)
+    _same(a, b, 3)
+    a.close()
+    b.close()
+
+
+def test_dataflow_guo_force():
+    cfgs = [dict(dims=2, nx=90, ny=36, k=5, kn=0.1, prec=glbm.FP32_DEV, g=3e-5,
+                 force=glbm.FORCE_GUO)]
+    a, b = _pair(cfgs, seed=77)
+    a.step(100)
+    b.step(100)
+    _same(a, b, 1)
+    a.close()
+    b.close()
+
+
+def test_dataflow_failure_stops_at_the_failing_step():
+    """A uniform periodic flow driven from rest by g = 0.01 on D2Q9 leaves the
+    positivity domain at step 82 (u = g t), inside the second chunk of a
+    200-step call: the dataflow context reports the same error, the same 83
+    completed steps and the same state as the launch-after-launch one (it
+    replays the call from its start)."""
+    nx, ny = 32, 8
+    cfg = dict(dims=2, nx=nx, ny=ny, k=0, tau=0.8, prec=glbm.FP32_DEV, bc=glbm.BC_PERIODIC,
+               g=0.01)
+    res = []
+    for df in (1, 0):
+        lat = glbm.Lattice(cfg)
+        lat.set_dataflow(df)
+        assert lat.dataflow == df
+        err = None
+        try:
+            lat.step(200)
+        except glbm.GlbmError as e:
+            err = str(e)
+        res.append((err, lat.time, lat.get_populations(0)))
+        # the context stays stopped, in either mode
+        with pytest.raises(glbm.UnstableError, match="0 of 10 steps completed"):
+            lat.step(10)
+        lat.close()
+    (e1, t1, f1), (e0, t0, f0) = res
+    assert e0 is not None and "83 of 200 steps completed" in e0
+    assert e1 == e0 and t1 == t0 == 83
+    np.testing.assert_array_equal(f1, f0)

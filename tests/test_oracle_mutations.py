@@ -58,8 +58,8 @@ MUTATIONS = {
     "tangent of rho dropped": ("const double dfeq = rho[d] * Ex[nx + NX] * Ey[ny + NY] +\n                                        rho[0] *",
                                "const double dfeq = 0.0 * rho[d] * Ex[nx + NX] * Ey[ny + NY] +\n                                        rho[0] *"),
     "tangent of u without rho term": ("dux[d] = (jx[d] - ux * rho[d]) / rho[0];", "dux[d] = jx[d] / rho[0];"),
-    "tangents not streamed": ("        for (int d = 0; d < 3; ++d) orc_stream2d(c, X + d * n, F + d * n);\n        orc_collide_dual",
-                              "        for (int d = 0; d < 1; ++d) orc_stream2d(c, X + d * n, F + d * n);\n        orc_collide_dual"),
+    "tangents not streamed": ("for (int d = 0; d < ORC_NT; ++d) orc_stream2d(c, X + d * n, F + d * n);",
+                              "for (int d = 0; d < 1; ++d) orc_stream2d(c, X + d * n, F + d * n);"),
     "force theta of the y axis": ("double theta_x = orc_axis_theta(&ax), theta_y", "double theta_x = orc_axis_theta(&ay), theta_y"),
     "collision x axis with the y flag": ("    orc_axis_make(c->NX, ORC_ZVX(c), &ax);\n    orc_axis_make(c->NY, ORC_ZVY(c), &ay);\n    int Lx = c->Lx, Ly = c->Ly;\n    size_t plane = (size_t)Lx * Ly;\n    double Wx[",
                                          "    orc_axis_make(c->NX, ORC_ZVY(c), &ax);\n    orc_axis_make(c->NY, ORC_ZVY(c), &ay);\n    int Lx = c->Lx, Ly = c->Ly;\n    size_t plane = (size_t)Lx * Ly;\n    double Wx["),
