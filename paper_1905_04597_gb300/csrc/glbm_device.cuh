@@ -73,15 +73,15 @@ __device__ __forceinline__ void finish_step(unsigned *status)
     }
 }
 
-// Load of a population by the step tiles: through L2 (ld.global.cg), not the
-// read-only path, because in a dataflow chunk (below) another grid may still
-// have been writing the input when this one started; the band counts' acquire
-// orders those writes before the load. (Measured on GB300: within 2 % of the
-// read-only path when the steps do not overlap.)
+// Load of a population by the step tiles: an ordinary (weak, L1-cached) load,
+// not the read-only path, because in a dataflow chunk (below) another grid may
+// still have been writing the input when this one started; the band counts'
+// acquire orders those writes before the load. (Measured on GB300: within 1 %
+// of the read-only path when the steps do not overlap.)
 template <typename T>
 __device__ __forceinline__ T ld_pop(const T *p)
 {
-    return __ldcg(p);
+    return __ldca(p);
 }
 
 // ---- dataflow stepping (GLBM_DF_CHUNK, glbm_internal.h) -------------------
@@ -150,15 +150,16 @@ __device__ __forceinline__ void df_wait_rows(const unsigned *bands, unsigned *st
 }
 
 // This CTA's tile of band blockIdx.y of instance `inst` has finished its step:
-// after the barrier, one thread's fence releases every thread's stores of the
-// CTA (the barrier orders them before it), then the band count goes up by one.
-// A fence by every thread would hold each warp until its stores land.
+// after the barrier, one thread adds one to the band count with release
+// semantics, which publishes every thread's stores of the CTA (the barrier
+// orders them before the release). A fence by every thread would hold each
+// warp until its stores land.
 __device__ __forceinline__ void df_tile_done(unsigned *bands, int inst)
 {
     __syncthreads();
     if (threadIdx.x == 0) {
-        __threadfence();
-        atomicAdd(bands + (long long)inst * gridDim.y + blockIdx.y, 1u);
+        unsigned *c = bands + (long long)inst * gridDim.y + blockIdx.y;
+        asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(c) : "memory");
     }
 }
 
