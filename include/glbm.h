@@ -218,7 +218,11 @@ size_t glbm_elem_size(const glbm_ctx *ctx);
  * new state is set (glbm_set_equilibrium, glbm_set_populations, glbm_load).
  * 1D contexts step their instances one after another, each stopping at its
  * own failing step; there glbm_time() advances by the fewest steps any
- * instance completed. GLBM_E_CUDA: a launch failed (the state is then
+ * instance completed. In dataflow mode (glbm_set_dataflow) the chunks'
+ * launches overlap; the contract is the same (the call replays itself launch
+ * after launch from a copy of its starting state when a node fails), and
+ * GLBM_E_TIMEOUT reports a dataflow wait that ran out, with the state that of
+ * the call's start. GLBM_E_CUDA: a launch failed (the state is then
  * undefined). */
 glbm_status glbm_step(glbm_ctx *ctx, int64_t n);
 
