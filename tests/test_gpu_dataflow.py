@@ -126,3 +126,37 @@ def test_dataflow_failure_stops_at_the_failing_step():
     assert e0 is not None and "83 of 200 steps completed" in e0
     assert e1 == e0 and t1 == t0 == 83
     np.testing.assert_array_equal(f1, f0)
+
+
+def test_dataflow_wait_that_runs_out_reports_a_timeout():
+    """Test mode 2 makes every wait of a chunk's later steps unsatisfiable: the
+    first wait gives up after 0.5 s and sets the timeout flag, no later wait
+    goes on (the halt word), and glbm_step returns GLBM_E_TIMEOUT with the state
+    and the clock of the call's start. The context then steps normally."""
+    import time
+    nx, ny = 96, 32
+    cfg = dict(dims=2, nx=nx, ny=ny, k=2, kn=0.1, prec=glbm.FP32_DEV, u_wall_lo=-0.05,
+               u_wall_hi=0.05)
+    lat = glbm.Lattice(cfg)
+    lat.set_wall_launch(0)
+    lat.set_equilibrium(0, *inputs.random_macro(5, nx, ny))
+    lat.step(3)
+    before = lat.get_populations(0)
+    lat.set_dataflow(2)
+    t0 = time.perf_counter()
+    with pytest.raises(glbm.GlbmError) as err:
+        lat.step(64)
+    assert err.value.status == glbm.E_TIMEOUT
+    assert time.perf_counter() - t0 < 30.0
+    assert lat.time == 3
+    np.testing.assert_array_equal(lat.get_populations(0), before)
+    lat.set_dataflow(1)
+    lat.step(64)
+    ref = glbm.Lattice(cfg)
+    ref.set_wall_launch(0)
+    ref.set_dataflow(0)
+    ref.set_equilibrium(0, *inputs.random_macro(5, nx, ny))
+    ref.step(67)
+    np.testing.assert_array_equal(lat.get_populations(0), ref.get_populations(0))
+    lat.close()
+    ref.close()
