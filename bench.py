@@ -259,7 +259,8 @@ def run_ours(args):
                               "data": "synthetic",
                               "config": {"workload": res["label"],
                                          "parallelism": f"x slabs over {world} rank(s), halo "
-                                                        f"exchange after every step",
+                                                        f"exchange every {res['steps_per_exchange']} "
+                                                        f"steps",
                                          "l2": "2.0 GB of populations per buffer set; no flush"},
                               "slab": res, "clocks": clk.summary(),
                               "gpu_launches": res["launches"]}), flush=True)
@@ -590,11 +591,12 @@ def measure_adjoint(reps=1, warmup_steps=200):
 
 def measure_slab(steps, warmup, rank=0, world=1):
     """One Couette D2Q81 lattice of 4096 x 256 (Kn 0.1, walls at -+0.05, FP32)
-    split into x slabs over the ranks (slab.SlabLattice): each rank steps its
-    Ls = 4096 / world owned columns plus H = 4 halo columns per side, and the
-    halos are exchanged after every step (NCCL between GPUs; one rank copies
-    its own columns across). The value counts the undivided lattice's
-    population updates over the slowest rank's time (strong scaling)."""
+    split into x slabs over the ranks (slab.SlabLattice, autotuned): each rank
+    steps its Ls = 4096 / world owned columns plus H = m x 4 halo columns per
+    side, and the halos are exchanged once every m steps (deep halos, m from
+    slab.default_depth; NCCL between GPUs, one rank copies its own columns
+    across). The value counts the undivided lattice's population updates over
+    the slowest rank's time (strong scaling)."""
     import torch
     from paper_1905_04597_gb300 import glbm, slab
     cfg = dict(dims=2, nx=4096, ny=256, k=3, kn=0.1, u_wall_lo=-0.05, u_wall_hi=0.05,
@@ -602,6 +604,7 @@ def measure_slab(steps, warmup, rank=0, world=1):
     s = slab.SlabLattice(cfg, rank, world)
     shp = (cfg["ny"], cfg["nx"])
     s.set_equilibrium_global(np.ones(shp), np.zeros(shp), np.zeros(shp))
+    s.lat.autotune(reps=5)
     s.advance(warmup)
     l0 = s.lat.kernel_launches
     if world > 1:
@@ -617,11 +620,14 @@ def measure_slab(steps, warmup, rank=0, world=1):
     ms = max_over_ranks(e0.elapsed_time(e1))
     launches = s.lat.kernel_launches - l0
     pops = 81 * cfg["nx"] * cfg["ny"]
-    halo = 2 * 81 * cfg["ny"] * s.H * 4  # bytes each rank sends per step (both sides)
+    halo = 2 * 81 * cfg["ny"] * s.H * 4  # bytes each rank sends per exchange (both sides)
     out = {"label": "couette_slab_d2q81_4096x256_kn0.1", "ranks": world, "owned_columns": s.Ls,
-           "halo_columns_per_side": s.H, "halo_bytes_sent_per_rank_step": halo,
+           "halo_columns_per_side": s.H, "steps_per_exchange": s.depth,
+           "halo_bytes_sent_per_rank_exchange": halo,
+           "halo_bytes_sent_per_rank_step": halo / s.depth,
            "step_bytes_per_rank": 8 * 81 * cfg["ny"] * (s.Ls + 2 * s.H),
            "redundant_fraction": 2 * s.H / s.Ls,
+           "tiles": s.lat.tiles()[3], "dataflow": s.lat.dataflow,
            "ms_per_step": ms / steps, "pop_updates_per_s": pops * steps / (ms / 1e3),
            "launches": launches}
     s.lat.close()

@@ -218,12 +218,13 @@ size_t glbm_elem_size(const glbm_ctx *ctx);
  * new state is set (glbm_set_equilibrium, glbm_set_populations, glbm_load).
  * 1D contexts step their instances one after another, each stopping at its
  * own failing step; there glbm_time() advances by the fewest steps any
- * instance completed. In dataflow mode (glbm_set_dataflow) the chunks'
- * launches overlap; the contract is the same (the call replays itself launch
- * after launch from a copy of its starting state when a node fails), and
- * GLBM_E_TIMEOUT reports a dataflow wait that ran out, with the state that of
- * the call's start. GLBM_E_CUDA: a launch failed (the state is then
- * undefined). */
+ * instance completed. In dataflow mode (glbm_set_dataflow; calls of 2 or more
+ * steps) the chunks' launches overlap; the contract is the same: the call
+ * writes only the other two of three state buffers (the third is allocated on
+ * the first such call), so its starting state survives, and when a node fails
+ * the call replays itself launch after launch from it. GLBM_E_TIMEOUT reports
+ * a dataflow wait that ran out, with the state that of the call's start.
+ * GLBM_E_CUDA: a launch failed (the state is then undefined). */
 glbm_status glbm_step(glbm_ctx *ctx, int64_t n);
 
 /* Wait for the context's stream; GLBM_E_UNSTABLE if any step flagged a node. */
@@ -334,12 +335,14 @@ glbm_status glbm_conservation_noalloc(const double *fields, int dims, int64_t no
  * starts as soon as the rows of step t it reads and overwrites are done,
  * instead of after the whole of step t. The results are identical to
  * launching the steps one after another (same arithmetic, same dither), and so
- * is the failure contract: glbm_step keeps the state at its start in a copy
- * (one state's memory, allocated on first use) and, if a node leaves the
- * positivity domain, restores it and replays the call one step after
- * another, which stops after the failing step. A wait that takes longer than
- * 0.5 s (none should) restores the state at the call's start and returns
- * GLBM_E_TIMEOUT. on = 0 launches the steps one after another. on = 2 is a
+ * is the failure contract: a glbm_step call of n >= 2 steps leaves the buffer
+ * of its starting state unwritten (its first step reads it into a second
+ * buffer, and the later steps alternate between that one and a third, one
+ * state's memory allocated on first use; the three rotate from call to call,
+ * no state is copied) and, if a node leaves the positivity domain, takes that
+ * state back and replays the call one step after another, which stops after
+ * the failing step. A wait that takes longer than 0.5 s (none should) returns
+ * GLBM_E_TIMEOUT with the state of the call's start. on = 0 launches the steps one after another. on = 2 is a
  * test of that path: every wait of a chunk's later steps asks for more tiles
  * than a band has, so the first call of glbm_step waits 0.5 s and returns
  * GLBM_E_TIMEOUT with the state unchanged.
@@ -410,7 +413,8 @@ glbm_status glbm_adjoint_flowrate(glbm_ctx *ctx, int64_t steps, int64_t ckpt_eve
  * choice, and with every tile shape in dataflow chunks (glbm_set_dataflow,
  * wall densities from the tiles), and keeps the fastest of all, dataflow on
  * or off. The state, the step clock and the dither sequence are unchanged;
- * the first call allocates the dataflow copy of the state. If us is non-NULL it
+ * the first call allocates the third state buffer of dataflow calls (the
+ * timed steps run through it and leave the state's buffer unwritten). If us is non-NULL it
  * receives the microseconds per launch, us[k * GLBM_MAX_TILES + idx], -1 for
  * pairs not timed (GLBM_LEVELS * GLBM_MAX_TILES doubles, host memory). R and
  * V change only which CTA and thread update a node; G also groups the

@@ -96,6 +96,15 @@ struct Geo {
     long long nodes() const { return (long long)Lx * Ly * Lz; }
 };
 
+// A captured chunk of kGraphChunk steps: step 0 reads p0 and writes pa, then the
+// steps alternate pa -> pb, pb -> pa (a chunk from buffer b into b' is
+// (b, b', b)); df marks the dataflow form.
+struct ChunkGraph {
+    const void *p0, *pa, *pb;
+    bool df;
+    cudaGraphExec_t exec;
+};
+
 struct glbm_ctx {
     int n_inst = 0;
     int dims = 2, prec = 0;
@@ -129,19 +138,18 @@ struct glbm_ctx {
     int n_items = 0;
     int group[GLBM_MAXN + 2] = {0};  // first item of each level
     int tile[GLBM_MAXN + 1] = {0};   // tile shape index per level (glbm_tiles.h)
-    cudaGraphExec_t graph[2] = {nullptr, nullptr};  // chunk graphs by starting buffer
-    cudaGraphExec_t graph_df[2] = {nullptr, nullptr};  // the same in dataflow form
+    std::vector<ChunkGraph> graphs;  // captured chunks, by their buffers and form
     int dataflow = 1;              // 1: dataflow chunks where the context allows them
     unsigned *d_df = nullptr;      // per-step CTA counts of a chunk, then the band counts
     long long df_words = 0;
-    void *snap = nullptr;          // state at the start of a dataflow glbm_step (replay)
+    void *spare = nullptr;         // third state buffer of dataflow calls (allocated on first use)
     bool halted = false;           // a glbm_step stopped at a failing step (until a new state)
     int64_t t = 0;
     int64_t launches = 0;
     unsigned clock_word = 0;  // host copy uploaded by set_clock (lives as long as the context)
 };
 
-static const int kGraphChunk = 64;  // steps per captured graph (even: keeps buffer parity)
+static const int kGraphChunk = 64;  // steps per captured graph (even: a chunk from b ends in b)
 
 static size_t bytes_state(const glbm_ctx *c) { return (size_t)c->pool_elems * c->elem; }
 
@@ -349,11 +357,8 @@ static Geo make_geo(const glbm_config &c)
 
 static void drop_graphs(glbm_ctx *c)
 {
-    for (int i = 0; i < 2; ++i) {
-        if (c->graph[i]) cudaGraphExecDestroy(c->graph[i]);
-        if (c->graph_df[i]) cudaGraphExecDestroy(c->graph_df[i]);
-        c->graph[i] = c->graph_df[i] = nullptr;
-    }
+    for (ChunkGraph &g : c->graphs) cudaGraphExecDestroy(g.exec);
+    c->graphs.clear();
 }
 
 static void destroy_resources(glbm_ctx *c)
@@ -361,7 +366,7 @@ static void destroy_resources(glbm_ctx *c)
     drop_graphs(c);
     cudaStreamSynchronize(c->stream);
     dev_free(c->A, c->d_df, c->stream);
-    dev_free(c->A, c->snap, c->stream);
+    dev_free(c->A, c->spare, c->stream);
     dev_free(c->A, c->buf[0], c->stream);
     dev_free(c->A, c->buf[1], c->stream);
     dev_free(c->A, c->d_ip, c->stream);
@@ -865,10 +870,10 @@ extern "C" size_t glbm_elem_size(const glbm_ctx *c) { return c ? c->elem : 0; }
 // ---------------------------------------------------------------------------
 // stepping
 // ---------------------------------------------------------------------------
-// Arguments of the uniform step; TY is AxisTable for levels up to 8 and
-// AxisTableHi above.
+// Arguments of the uniform step from fin into fout; TY is AxisTable for levels
+// up to 8 and AxisTableHi above.
 template <class TY>
-static Step2DArgsT<TY> step_args_t(const glbm_ctx *c, int from)
+static Step2DArgsT<TY> step_args_t(const glbm_ctx *c, const void *fin, void *fout)
 {
     const Geo &g = c->geo[0];
     Step2DArgsT<TY> a;
@@ -878,8 +883,8 @@ static Step2DArgsT<TY> step_args_t(const glbm_ctx *c, int from)
     else
         a.tab = glbm_narrow_table(tab_y(c, g));
     a.tabx = glbm_narrow_table(tab_x(c, g));
-    a.fin = c->buf[from];
-    a.fout = c->buf[1 - from];
+    a.fin = fin;
+    a.fout = fout;
     a.ip = c->d_ip;
     a.status = c->d_status;
     a.step_ctr = c->d_status + ST_CLOCK;
@@ -893,16 +898,19 @@ static Step2DArgsT<TY> step_args_t(const glbm_ctx *c, int from)
     a.inst_stride = c->n_inst > 1 ? c->geo[1].off : 0;
     return a;
 }
-static Step2DArgs step_args(const glbm_ctx *c, int from) { return step_args_t<AxisTable>(c, from); }
+static Step2DArgs step_args(const glbm_ctx *c, int from)
+{
+    return step_args_t<AxisTable>(c, c->buf[from], c->buf[1 - from]);
+}
 
-static Step3DArgs step3d_args(const glbm_ctx *c, int from)
+static Step3DArgs step3d_args(const glbm_ctx *c, const void *fin, void *fout)
 {
     const Geo &g = c->geo[0];
     Step3DArgs a;
     memset(&a, 0, sizeof(a));
     a.tab = glbm_narrow_table(c->tabs[g.N]);
-    a.fin = c->buf[from];
-    a.fout = c->buf[1 - from];
+    a.fin = fin;
+    a.fout = fout;
     a.ip = c->d_ip;
     a.status = c->d_status;
     a.step_ctr = c->d_status + ST_CLOCK;
@@ -917,13 +925,13 @@ static Step3DArgs step3d_args(const glbm_ctx *c, int from)
     return a;
 }
 
-static BatchArgs batch_args(const glbm_ctx *c, int from)
+static BatchArgs batch_args(const glbm_ctx *c, const void *fin, void *fout)
 {
     BatchArgs b;
     memset(&b, 0, sizeof(b));
     for (int N = 1; N <= GLBM_MAXN_2N1; ++N) b.tab[N - 1] = glbm_narrow_table(c->tabs[N]);
-    b.fin = c->buf[from];
-    b.fout = c->buf[1 - from];
+    b.fin = fin;
+    b.fout = fout;
     b.ip = c->d_ip;
     b.items = c->d_items;
     b.n_items = c->n_items;
@@ -933,6 +941,10 @@ static BatchArgs batch_args(const glbm_ctx *c, int from)
     b.step_ctr = c->d_status + ST_CLOCK;
     b.done_ctr = c->d_status + ST_DONE;
     return b;
+}
+static BatchArgs batch_args(const glbm_ctx *c, int from)
+{
+    return batch_args(c, c->buf[from], c->buf[1 - from]);
 }
 
 // Kernel launches of one 2D step.
@@ -950,17 +962,19 @@ static bool df_eligible(const glbm_ctx *c)
            !c->wall_launch;
 }
 
-// One 2D step of every instance from buffer `from` into the other, on stream s;
-// node >= 0 makes it step `node` of a dataflow chunk.
-static cudaError_t launch_one_2d(const glbm_ctx *c, int from, cudaStream_t s, int node = -1)
+// One 2D (or 3D) step of every instance from state buffer fin into fout, on
+// stream s; node >= 0 makes it step `node` of a dataflow chunk.
+static cudaError_t launch_step(const glbm_ctx *c, const void *fin, void *fout, cudaStream_t s,
+                               int node = -1)
 {
-    if (c->hetero) return glbm_launch_batched_f32(batch_args(c, from), s);
+    if (c->hetero) return glbm_launch_batched_f32(batch_args(c, fin, fout), s);
     const int N = c->geo[0].N;
-    if (c->dims == 3) return glbm_launch_step3d(N, c->prec, c->tile[N], step3d_args(c, from), c->n_inst, s);
+    if (c->dims == 3)
+        return glbm_launch_step3d(N, c->prec, c->tile[N], step3d_args(c, fin, fout), c->n_inst, s);
     if (N > GLBM_MAXN_2N1)
         return glbm_launch_step2d_zv_hi(N, c->prec, c->tile[N],
-                                        step_args_t<AxisTableHi>(c, from), c->n_inst, s);
-    Step2DArgs a = step_args(c, from);
+                                        step_args_t<AxisTableHi>(c, fin, fout), c->n_inst, s);
+    Step2DArgs a = step_args_t<AxisTable>(c, fin, fout);
     if (node >= 0) {
         a.node_done = c->d_df;
         a.bands = c->d_df + GLBM_DF_CHUNK;
@@ -980,6 +994,12 @@ static cudaError_t launch_one_2d(const glbm_ctx *c, int from, cudaStream_t s, in
                                 : glbm_launch_step2d_f32(N, c->tile[N], a, c->n_inst, s);
 }
 
+// One step from buffer `from` into the other.
+static cudaError_t launch_one_2d(const glbm_ctx *c, int from, cudaStream_t s)
+{
+    return launch_step(c, c->buf[from], c->buf[1 - from], s);
+}
+
 // The counting words of dataflow chunks: GLBM_DF_CHUNK per-step CTA counts,
 // then one band count per (instance, row) (bands of R rows use the first
 // ceil(Ly / R) of an instance's Ly words).
@@ -994,41 +1014,74 @@ static glbm_status df_words_ready(glbm_ctx *c)
     return GLBM_OK;
 }
 
-// Enqueue steps 0..count-1 of a dataflow chunk from buffer `from` on stream s.
-static cudaError_t launch_df_chunk(glbm_ctx *c, int from, int count, cudaStream_t s)
+// Enqueue `count` steps on stream s: step 0 from p0 into pa, then pa -> pb,
+// pb -> pa, ... (ChunkGraph); df: as a dataflow chunk (its counting words reset
+// first, the steps numbered 0..count-1).
+static cudaError_t launch_chunk(glbm_ctx *c, const void *p0, void *pa, void *pb, int count,
+                                cudaStream_t s, bool df)
 {
-    cudaError_t e = glbm_launch_df_start(c->d_status, c->d_df, c->df_words, s);
-    int b = from;
+    cudaError_t e = df ? glbm_launch_df_start(c->d_status, c->d_df, c->df_words, s) : cudaSuccess;
     for (int i = 0; i < count && e == cudaSuccess; ++i) {
-        e = launch_one_2d(c, b, s, i);
-        b = 1 - b;
+        const void *fin = i == 0 ? p0 : ((i & 1) ? pa : pb);
+        void *fout = (i & 1) ? pb : pa;
+        e = launch_step(c, fin, fout, s, df ? i : -1);
     }
     return e;
 }
 
-static glbm_status capture_chunk(glbm_ctx *c, int from, bool df = false)
+// The graph of a full chunk (p0, pa, pb) in the given form, captured on first
+// use (three state buffers give at most 12 per form).
+static glbm_status chunk_graph(glbm_ctx *c, const void *p0, void *pa, void *pb, bool df,
+                               cudaGraphExec_t *out)
 {
+    for (const ChunkGraph &g : c->graphs)
+        if (g.p0 == p0 && g.pa == pa && g.pb == pb && g.df == df) {
+            *out = g.exec;
+            return GLBM_OK;
+        }
     cudaGraph_t g = nullptr;
     CUDA_TRY(cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal));
-    cudaError_t e = cudaSuccess;
-    if (df) {
-        e = launch_df_chunk(c, from, kGraphChunk, c->cap);
-    } else {
-        int b = from;
-        for (int i = 0; i < kGraphChunk && e == cudaSuccess; ++i) {
-            e = launch_one_2d(c, b, c->cap);
-            b = 1 - b;
-        }
-    }
+    cudaError_t e = launch_chunk(c, p0, pa, pb, kGraphChunk, c->cap, df);
     cudaError_t e2 = cudaStreamEndCapture(c->cap, &g);
     if (e != cudaSuccess || e2 != cudaSuccess) {
         if (g) cudaGraphDestroy(g);
         return fail(GLBM_E_CUDA, "graph capture failed: %s",
                     cudaGetErrorString(e != cudaSuccess ? e : e2));
     }
-    e = cudaGraphInstantiate(df ? &c->graph_df[from] : &c->graph[from], g, 0);
+    cudaGraphExec_t exec = nullptr;
+    e = cudaGraphInstantiate(&exec, g, 0);
     cudaGraphDestroy(g);
     if (e != cudaSuccess) return fail(GLBM_E_CUDA, "graph instantiate failed: %s", cudaGetErrorString(e));
+    c->graphs.push_back(ChunkGraph{p0, pa, pb, df, exec});
+    *out = exec;
+    return GLBM_OK;
+}
+
+// Enqueue n steps as chunks whose first step reads p0 and writes pa, the steps
+// then alternating between pa and pb; full chunks replay graphs. Returns the
+// buffer that holds the state after the n steps (pa for odd n, else pb).
+static glbm_status enqueue_steps(glbm_ctx *c, int64_t n, const void *p0, void *pa, void *pb,
+                                 bool df, void **last)
+{
+    *last = const_cast<void *>(p0);
+    for (int64_t left = n; left > 0;) {
+        const int m = (int)std::min<int64_t>(left, kGraphChunk);
+        if (m == kGraphChunk) {
+            cudaGraphExec_t g = nullptr;
+            glbm_status st = chunk_graph(c, p0, pa, pb, df, &g);
+            if (st != GLBM_OK) return st;
+            CUDA_TRY(cudaGraphLaunch(g, c->stream));
+        } else {
+            CUDA_TRY(launch_chunk(c, p0, pa, pb, m, c->stream, df));
+        }
+        c->launches += (int64_t)m * launches_per_step(c) + (df ? 1 : 0);  // + k_df_start
+        void *now = (m & 1) ? pa : pb, *other = (m & 1) ? pb : pa;
+        p0 = now;  // the next chunk continues the alternation
+        pa = other;
+        pb = now;
+        *last = now;
+        left -= m;
+    }
     return GLBM_OK;
 }
 
@@ -1077,36 +1130,65 @@ static glbm_status step_1d_instance(glbm_ctx *c, int i, int64_t n, int64_t *comp
 // Enqueue n (< 2^31) 2D or 3D steps of every instance; returns the steps
 // completed (each step's last launch counts itself, and once a step has left
 // the positivity domain the launches of later steps do nothing).
-static glbm_status step_nd(glbm_ctx *c, int64_t n, int64_t *completed, bool df = false)
+static glbm_status step_nd(glbm_ctx *c, int64_t n, int64_t *completed)
 {
     const int cur0 = c->cur;
     CUDA_TRY(cudaMemsetAsync(c->d_status + ST_STEPS, 0, sizeof(unsigned), c->stream));
-    int64_t left = n;
-    cudaGraphExec_t *graphs = df ? c->graph_df : c->graph;
-    while (left >= kGraphChunk) {
-        if (!graphs[c->cur]) {
-            glbm_status st = capture_chunk(c, c->cur, df);
-            if (st != GLBM_OK) return st;
-        }
-        CUDA_TRY(cudaGraphLaunch(graphs[c->cur], c->stream));
-        c->launches += kGraphChunk * launches_per_step(c) + (df ? 1 : 0);  // + k_df_start
-        left -= kGraphChunk;  // even chunk: c->cur unchanged
-    }
-    if (df && left > 0) {
-        CUDA_TRY(launch_df_chunk(c, c->cur, (int)left, c->stream));
-        c->launches += left * launches_per_step(c) + 1;
-        if (left & 1) c->cur = 1 - c->cur;
-        left = 0;
-    }
-    for (; left > 0; --left) {
-        CUDA_TRY(launch_one_2d(c, c->cur, c->stream));
-        c->cur = 1 - c->cur;
-        c->launches += launches_per_step(c);
-    }
-    glbm_status st = read_status(c);
+    void *last = nullptr;
+    glbm_status st = enqueue_steps(c, n, c->buf[cur0], c->buf[1 - cur0], c->buf[cur0], false, &last);
+    if (st != GLBM_OK) return st;
+    st = read_status(c);
     if (st != GLBM_OK) return st;
     *completed = c->h_status[ST_STEPS];
     c->cur = (int)((cur0 + *completed) & 1);  // X_{t + completed} is in this buffer
+    return GLBM_OK;
+}
+
+// The third state buffer of dataflow calls (zeroed like the other two).
+static glbm_status spare_ready(glbm_ctx *c)
+{
+    if (c->spare) return GLBM_OK;
+    const size_t bytes = bytes_state(c);
+    c->spare = dev_alloc(c->A, bytes, c->stream);
+    if (!c->spare) return fail(GLBM_E_NOMEM, "third state buffer of %.1f MB", bytes / 1e6);
+    CUDA_TRY(cudaMemsetAsync(c->spare, 0, bytes, c->stream));
+    return GLBM_OK;
+}
+
+// Which buffers hold the state, the other step operand and the spare.
+struct Binding {
+    void *buf0, *buf1, *spare;
+    int cur;
+};
+static Binding binding(const glbm_ctx *c) { return Binding{c->buf[0], c->buf[1], c->spare, c->cur}; }
+static void rebind(glbm_ctx *c, const Binding &b)
+{
+    c->buf[0] = b.buf0;
+    c->buf[1] = b.buf1;
+    c->spare = b.spare;
+    c->cur = b.cur;
+}
+
+// Enqueue n (1 <= n < 2^31) steps in dataflow chunks without writing the
+// buffer S that holds X_t: the first step reads S into the second buffer X and
+// the steps then alternate between X and the spare Y. On return buf[cur] holds
+// the last state written, S is the spare, and the steps completed are returned:
+// n, unless a node left the positivity domain or a wait ran out of time, when
+// the caller binds S again (binding(), rebind()) and nothing is lost.
+static glbm_status step_df(glbm_ctx *c, int64_t n, int64_t *completed)
+{
+    void *S = c->buf[c->cur], *X = c->buf[1 - c->cur], *Y = c->spare;
+    CUDA_TRY(cudaMemsetAsync(c->d_status + ST_STEPS, 0, sizeof(unsigned), c->stream));
+    void *last = nullptr;
+    glbm_status st = enqueue_steps(c, n, S, X, Y, true, &last);
+    if (st != GLBM_OK) return st;
+    st = read_status(c);
+    if (st != GLBM_OK) return st;
+    *completed = c->h_status[ST_STEPS];
+    c->buf[0] = last;
+    c->buf[1] = last == X ? Y : X;
+    c->cur = 0;
+    c->spare = S;
     return GLBM_OK;
 }
 
@@ -1129,47 +1211,34 @@ extern "C" glbm_status glbm_step(glbm_ctx *c, int64_t n)
         }
     } else {
         bool strict = true;
-        if (n > 0 && df_eligible(c) && !c->halted) {
+        if (n >= 2 && n <= ((int64_t)1 << 30) && df_eligible(c) && !c->halted) {
             // dataflow chunks: the steps of a chunk overlap, so a failing step
-            // is not where the run stops; the state at the call's start is kept
-            // and, if a node leaves the positivity domain (or a wait runs out of
-            // time), restored and the call replayed one step after another,
-            // which stops exactly after the failing step (same arithmetic, same
-            // dither: the results are identical)
+            // is not where the run stops. The buffer of X_{t0} is not written
+            // (step_df); if a node leaves the positivity domain (or a wait runs
+            // out of time) it is bound again and the call replayed one step
+            // after another, which stops exactly after the failing step (same
+            // arithmetic, same dither: the results are identical)
             glbm_status st = df_words_ready(c);
+            if (st == GLBM_OK) st = spare_ready(c);
             if (st != GLBM_OK) return st;
-            const size_t bytes = bytes_state(c);
-            if (!c->snap) {
-                c->snap = dev_alloc(c->A, bytes, c->stream);
-                if (!c->snap) return fail(GLBM_E_NOMEM, "dataflow snapshot of %.1f MB", bytes / 1e6);
-            }
-            const int cur0 = c->cur;
-            CUDA_TRY(cudaMemcpyAsync(c->snap, c->buf[cur0], bytes, cudaMemcpyDeviceToDevice,
-                                     c->stream));
-            unsigned flags = 0u;
-            for (int64_t left = n; left > 0 && !flags;) {
-                const int64_t m = std::min<int64_t>(left, (int64_t)1 << 30);
-                int64_t k = 0;
-                st = step_nd(c, m, &k, true);
-                if (st != GLBM_OK) return st;
-                done += k;
-                left -= m;
-                flags = c->h_status[ST_FLAGS] & (ST_UNSTABLE | ST_TIMEOUT);
-            }
+            const Binding start = binding(c);
+            int64_t k = 0;
+            st = step_df(c, n, &k);
+            if (st != GLBM_OK) return st;
+            const unsigned flags = c->h_status[ST_FLAGS] & (ST_UNSTABLE | ST_TIMEOUT);
             strict = flags != 0u;
             if (strict) {
-                CUDA_TRY(cudaMemcpyAsync(c->buf[cur0], c->snap, bytes, cudaMemcpyDeviceToDevice,
-                                         c->stream));
-                c->cur = cur0;
+                rebind(c, start);
                 CUDA_TRY(set_clock(c, t0));
                 CUDA_TRY(clear_unstable(c));
-                done = 0;
                 if (flags & ST_TIMEOUT) {
                     CUDA_TRY(cudaStreamSynchronize(c->stream));
                     return fail(GLBM_E_TIMEOUT,
                                 "a dataflow step waited more than 0.5 s for its rows; the state is "
                                 "that of time %lld again (no step applied)", (long long)t0);
                 }
+            } else {
+                done = k;
             }
         }
         for (int64_t left = strict ? n : 0; left > 0 && !bad;) {
@@ -1654,25 +1723,25 @@ static cudaError_t launch_level_once(const glbm_ctx *c, int N)
     return launch_one_2d(c, c->cur, c->stream);
 }
 
-// Time `steps` steps of the context from its current state, with the step
-// path as configured; the state, buffer parity and clock are put back from the
-// copy in c->snap (which the caller made).
+// Time `steps` steps of the context from its current state, launch after
+// launch or in dataflow chunks, through the three state buffers so that the
+// current state's buffer is not written; the binding, the clock and the status
+// are put back after each of the two runs (the first captures the graphs).
 static glbm_status time_steps(glbm_ctx *c, int64_t steps, bool df, cudaEvent_t e0, cudaEvent_t e1,
                               float *ms)
 {
-    const int cur0 = c->cur;
+    const Binding start = binding(c);
     const int64_t t0 = c->t;
-    const size_t bytes = bytes_state(c);
-    int64_t k = 0;
-    for (int rep = 0; rep < 2; ++rep) {  // the first run captures the chunk graphs
+    for (int rep = 0; rep < 2; ++rep) {
         CUDA_TRY(cudaEventRecord(e0, c->stream));
-        glbm_status st = step_nd(c, steps, &k, df);
+        void *last = nullptr;
+        glbm_status st = enqueue_steps(c, steps, c->buf[c->cur], c->buf[1 - c->cur], c->spare, df,
+                                       &last);
         if (st != GLBM_OK) return st;
         CUDA_TRY(cudaEventRecord(e1, c->stream));
         CUDA_TRY(cudaEventSynchronize(e1));
         CUDA_TRY(cudaEventElapsedTime(ms, e0, e1));
-        CUDA_TRY(cudaMemcpyAsync(c->buf[cur0], c->snap, bytes, cudaMemcpyDeviceToDevice, c->stream));
-        c->cur = cur0;
+        rebind(c, start);
         CUDA_TRY(set_clock(c, t0));
         CUDA_TRY(clear_unstable(c));
     }
@@ -1687,13 +1756,8 @@ static glbm_status autotune_dataflow(glbm_ctx *c, cudaEvent_t e0, cudaEvent_t e1
 {
     const int N = c->geo[0].N;
     glbm_status st = df_words_ready(c);
+    if (st == GLBM_OK) st = spare_ready(c);
     if (st != GLBM_OK) return st;
-    const size_t bytes = bytes_state(c);
-    if (!c->snap) {
-        c->snap = dev_alloc(c->A, bytes, c->stream);
-        if (!c->snap) return fail(GLBM_E_NOMEM, "dataflow snapshot of %.1f MB", bytes / 1e6);
-    }
-    CUDA_TRY(cudaMemcpyAsync(c->snap, c->buf[c->cur], bytes, cudaMemcpyDeviceToDevice, c->stream));
     const int64_t steps = 2 * kGraphChunk;
     const int tile0 = c->tile[N];
     const bool wall0 = c->wall_launch;

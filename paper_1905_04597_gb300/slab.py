@@ -2,16 +2,21 @@
 
 The lattice is periodic along x, so it can be cut into slabs of consecutive
 columns. Rank r of W owns the global columns [r Ls, (r+1) Ls) and stores them
-with H halo columns on each side (local width Ls + 2H, H >= the largest x
-speed N): local column H + i is global column r Ls + i. A step of the fused
-kernel pulls each population from at most H columns away, so after every step
-the left halo [0, H) is refilled from the left neighbour's last H owned
-columns and the right halo [Ls + H, Ls + 2H) from the right neighbour's first
-H owned columns. Nodes in the halo are stepped too (their pulls wrap around
-the local array) but are overwritten by the next exchange; the owned nodes
-see exactly the populations the undivided lattice would give them, so in
-FP64 the slabs reproduce the undivided run bit for bit. The walls are along
-y and stay local; the wall density is per column.
+with H halo columns on each side (local width Ls + 2H): local column H + i is
+global column r Ls + i. A step of the fused kernel pulls each population from
+at most `reach` columns away (the largest x speed: N_x, or 2 N_x + 1 on a 2N+2
+x axis), so a column whose neighbourhood within `reach` held exact values
+before a step holds an exact value after it. With H = m reach, m steps after
+an exchange the exact columns have shrunk from [0, Ls + 2H) to exactly the
+owned ones [H, Ls + H): the halos are refilled once every m steps (deep halos:
+m times fewer, m times larger messages, at 2H / Ls redundant work), the left
+halo [0, H) from the left neighbour's last H owned columns and the right halo
+[Ls + H, Ls + 2H) from the right neighbour's first H owned columns. Halo nodes
+are stepped too (their pulls wrap around the local array) but are overwritten
+by the next exchange; the owned nodes see exactly the populations the
+undivided lattice would give them, so in FP64 the slabs reproduce the
+undivided run bit for bit. The walls are along y and stay local; the wall
+density is per column.
 
 The exchange works on any local stepper with step(), pack(x0, n) and
 unpack(x0, n, buf) and any pair of send/recv callables, so the same code runs
@@ -40,11 +45,25 @@ def exchange_halos(stepper, Ls: int, H: int, rank: int, world: int, sendrecv):
     stepper.unpack(0, H, from_left)
 
 
-def step_slab(stepper, steps: int, Ls: int, H: int, rank: int, world: int, sendrecv):
-    """Advance a slab by `steps` steps, exchanging the halos after each."""
-    for _ in range(steps):
-        stepper.step()
+def step_slab(stepper, steps: int, Ls: int, H: int, rank: int, world: int, sendrecv,
+              per: int = 1):
+    """Advance a slab by `steps` steps, exchanging the halos (H >= per x the
+    reach of a step) after every `per` steps and after the last."""
+    left = steps
+    while left > 0:
+        n = min(per, left)
+        stepper.step(n)
         exchange_halos(stepper, Ls, H, rank, world, sendrecv)
+        left -= n
+
+
+def default_depth(Ls: int, reach: int) -> int:
+    """Steps per exchange: the largest m <= 16 whose redundant halo work
+    2 m reach / Ls stays within 1/32 of the owned columns' (at least 1)."""
+    m = 16
+    while m > 1 and 2 * m * reach * 32 > Ls:
+        m -= 1
+    return m
 
 
 def torch_sendrecv(group=None):
@@ -66,10 +85,12 @@ def torch_sendrecv(group=None):
 
 class SlabLattice:
     """The slab of one rank on the GPU library: a glbm.Lattice of Ls + 2H
-    columns (H = the level N along x) whose halos are exchanged after every
-    step. cfg is the undivided lattice's configuration with nx = W Ls."""
+    columns, H = depth x reach, whose halos are exchanged after every `depth`
+    steps (default_depth unless given). cfg is the undivided lattice's
+    configuration with nx = W Ls."""
 
-    def __init__(self, cfg: dict, rank: int = 0, world: int = 1, sendrecv=None):
+    def __init__(self, cfg: dict, rank: int = 0, world: int = 1, sendrecv=None,
+                 depth: int | None = None):
         import torch
         from . import glbm
         nx = cfg["nx"]
@@ -80,9 +101,13 @@ class SlabLattice:
         self.Ls = nx // world
         NX = cfg.get("x_level") or (cfg["k"] + 1)
         # the largest x speed: N_x, or 2 N_x + 1 on a 2N+2 x axis
-        self.H = 2 * NX + 1 if cfg.get("zv_axes", 0) & 1 else NX
+        self.reach = 2 * NX + 1 if cfg.get("zv_axes", 0) & 1 else NX
+        self.depth = default_depth(self.Ls, self.reach) if depth is None else int(depth)
+        if self.depth < 1:
+            raise ValueError("depth must be at least 1")
+        self.H = self.depth * self.reach
         if self.Ls < self.H:
-            raise ValueError("each slab needs at least H owned columns")
+            raise ValueError("each slab needs at least H = depth x reach owned columns")
         self.rank, self.world = rank, world
         self.lat = glbm.Lattice(dict(cfg, nx=self.Ls + 2 * self.H))
         self.sendrecv = sendrecv or torch_sendrecv()
@@ -104,10 +129,9 @@ class SlabLattice:
         exchange_halos(self, self.Ls, self.H, self.rank, self.world, self.sendrecv)
 
     def advance(self, steps):
-        """steps steps of the undivided lattice (one halo exchange per step)."""
-        for _ in range(steps):
-            self.lat.step(1)
-            self.exchange()
+        """steps steps of the undivided lattice (one halo exchange per `depth`
+        steps and one after the last)."""
+        step_slab(self, steps, self.Ls, self.H, self.rank, self.world, self.sendrecv, self.depth)
 
     def local_columns(self):
         """Global column of every local column (halos wrap around)."""

@@ -98,12 +98,40 @@ def test_dataflow_guo_force():
     b.close()
 
 
-def test_dataflow_failure_stops_at_the_failing_step():
+def test_dataflow_calls_of_every_length():
+    """Calls of 1 to 130 steps one after another: a dataflow call leaves the
+    buffer of its starting state unwritten and rotates three state buffers, so
+    its chunks replay graphs captured for several bindings of them. Populations
+    and moments stay equal to launch-after-launch stepping after every call,
+    also across a state set in between."""
+    cfgs = [dict(dims=2, nx=120, ny=40, k=3, kn=kn, prec=glbm.FP32_DEV, u_wall_lo=-0.05,
+                 u_wall_hi=0.05, g=1e-5) for kn in (0.05, 0.5)]
+    a, b = _pair(cfgs, seed=91)
+    for j, n in enumerate((1, 2, 3, 64, 65, 1, 128, 7, 64, 64, 129, 2)):
+        a.step(n)
+        b.step(n)
+        assert a.time == b.time
+        _same(a, b, 2)
+        for i in range(2):
+            ma, mb = a.moments(i), b.moments(i)
+            for key in ma:
+                np.testing.assert_array_equal(ma[key], mb[key])
+        if j == 5:
+            f = a.get_populations(1)
+            for lat in (a, b):
+                lat.set_populations(1, f)
+    a.close()
+    b.close()
+
+
+@pytest.mark.parametrize("before", [0, 40])
+def test_dataflow_failure_stops_at_the_failing_step(before):
     """A uniform periodic flow driven from rest by g = 0.01 on D2Q9 leaves the
     positivity domain at step 82 (u = g t), inside the second chunk of a
-    200-step call: the dataflow context reports the same error, the same 83
-    completed steps and the same state as the launch-after-launch one (it
-    replays the call from its start)."""
+    200-step call (started at rest, or after a successful 40-step call that
+    rotated the state buffers): the dataflow context reports the same error,
+    the same completed steps and the same state as the launch-after-launch one
+    (it binds the call's starting buffer again and replays the call)."""
     nx, ny = 32, 8
     cfg = dict(dims=2, nx=nx, ny=ny, k=0, tau=0.8, prec=glbm.FP32_DEV, bc=glbm.BC_PERIODIC,
                g=0.01)
@@ -112,6 +140,8 @@ def test_dataflow_failure_stops_at_the_failing_step():
         lat = glbm.Lattice(cfg)
         lat.set_dataflow(df)
         assert lat.dataflow == df
+        if before:
+            lat.step(before)
         err = None
         try:
             lat.step(200)
@@ -123,7 +153,7 @@ def test_dataflow_failure_stops_at_the_failing_step():
             lat.step(10)
         lat.close()
     (e1, t1, f1), (e0, t0, f0) = res
-    assert e0 is not None and "83 of 200 steps completed" in e0
+    assert e0 is not None and f"{83 - before} of 200 steps completed" in e0
     assert e1 == e0 and t1 == t0 == 83
     np.testing.assert_array_equal(f1, f0)
 

@@ -1,5 +1,6 @@
 """The x-slab decomposition on the GPU library: slabs of Ls + 2H columns with
-their halos refilled after every step reproduce the undivided lattice on
+their halos refilled after every step, or H = m x reach refilled after every
+m steps, reproduce the undivided lattice on
 their owned columns (FP64 bit for bit; FP32 within the dithered rounding,
 whose random words follow the local node index). Every call of this run has
 one GPU, so the multi-slab case runs its slabs as separate contexts on that
@@ -65,6 +66,41 @@ def test_slabs_reproduce_the_undivided_lattice(world, prec):
             slabs[0].exchange()
         else:
             _exchange_in_process(slabs)
+    got = np.concatenate([s.owned_populations() for s in slabs], axis=-1)
+    if prec == glbm.FP64:
+        np.testing.assert_array_equal(got, want)
+    else:
+        assert np.abs(got - want).max() / np.abs(want).max() < 1e-6
+    for s in slabs:
+        s.lat.close()
+
+
+@pytest.mark.parametrize("prec", [glbm.FP64, glbm.FP32_DEV])
+@pytest.mark.parametrize("world,depth", [(1, 4), (2, 5), (3, 3)])
+def test_deep_halos_reproduce_the_undivided_lattice(world, depth, prec):
+    """Halos of depth x reach columns refilled once every `depth` steps (13
+    steps: a ragged last block); the slabs' steps of several steps per call
+    run in dataflow chunks."""
+    cfg = _cfg(prec)
+    Q = (2 * cfg["k"] + 3) ** 2
+    f0 = inputs.random_populations(1200 + depth, Q, cfg["ny"], cfg["nx"])
+    steps = 13
+    want = _reference(cfg, f0, steps)
+    slabs = [slab.SlabLattice(cfg, r, world, sendrecv=lambda *a: None, depth=depth)
+             for r in range(world)]
+    assert all(s.H == depth * 3 for s in slabs)
+    for s in slabs:
+        s.set_populations_global(f0)
+    if world == 1:
+        slabs[0].advance(steps)
+    else:
+        left = steps
+        while left > 0:
+            n = min(depth, left)
+            for s in slabs:
+                s.step(n)
+            _exchange_in_process(slabs)
+            left -= n
     got = np.concatenate([s.owned_populations() for s in slabs], axis=-1)
     if prec == glbm.FP64:
         np.testing.assert_array_equal(got, want)

@@ -3,7 +3,9 @@
 slabs, stepped with one halo exchange per step, equal the undivided
 lattice's run bit for bit (FP64), with walls, moving walls and the force, on
 the isotropic, anisotropic, 2N+2 and 3D lattices (halo width H = the largest
-x speed: N_x, or 2N_x + 1 with the 2N+2 hierarchy along x)."""
+x speed: N_x, or 2N_x + 1 with the 2N+2 hierarchy along x). Deep halos
+(H = m x that reach, one exchange per m steps, a ragged last block) give the
+same bits."""
 import os
 import socket
 import sys
@@ -57,8 +59,8 @@ class OracleSlab:
         self.o = _oracle(c, X.shape[-1])
         self.X = X
 
-    def step(self):
-        self.X, _ = self.o.run(self.X, 1)
+    def step(self, n=1):
+        self.X, _ = self.o.run(self.X, n)
 
     def pack(self, x0, n):
         return torch.from_numpy(np.ascontiguousarray(self.X[..., x0:x0 + n]))
@@ -73,17 +75,17 @@ def _initial(c):
     return rng.uniform(0.5, 1.5, size=shape) / shape[0]
 
 
-def _rank_main(rank, world, port, name, out):
+def _rank_main(rank, world, port, name, out, depth=1):
     os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
     sys.path.insert(0, ROOT)
     import torch.distributed as dist
     from paper_1905_04597_gb300 import slab
     dist.init_process_group("gloo", rank=rank, world_size=world)
     c = CASES[name]
-    Ls, H = c["nx"] // world, _halo(c)
+    Ls, H = c["nx"] // world, depth * _halo(c)
     cols = [(rank * Ls + j - H) % c["nx"] for j in range(Ls + 2 * H)]
     st = OracleSlab(c, np.ascontiguousarray(_initial(c)[..., cols]))
-    slab.step_slab(st, c["steps"], Ls, H, rank, world, slab.torch_sendrecv())
+    slab.step_slab(st, c["steps"], Ls, H, rank, world, slab.torch_sendrecv(), per=depth)
     np.save(os.path.join(out, f"rank{rank}.npy"), st.X[..., H:H + Ls])
     dist.barrier()
     dist.destroy_process_group()
@@ -100,6 +102,37 @@ def test_slabs_equal_the_undivided_lattice(name, world, tmp_path):
     got = np.concatenate([np.load(tmp_path / f"rank{r}.npy") for r in range(world)], axis=-1)
     want, _ = _oracle(c, c["nx"]).run(_initial(c), c["steps"])
     np.testing.assert_array_equal(got, want)
+
+
+# (case, world, steps per exchange): H = depth x reach fits the owned columns
+DEEP = [("d2q25_walls", 2, 5), ("d1q3xd1q9_walls", 2, 4), ("d2q36_zv_walls", 2, 3),
+        ("d3q27_walls", 3, 3)]
+
+
+@pytest.mark.parametrize("name,world,depth", DEEP)
+def test_deep_halos_equal_the_undivided_lattice(name, world, depth, tmp_path):
+    sys.path.insert(0, ROOT)
+    from oracle import oracle as orc
+    orc.build()
+    c = CASES[name]
+    assert c["steps"] % depth != 0  # a ragged last block
+    assert depth * _halo(c) <= c["nx"] // world
+    mp.spawn(_rank_main, args=(world, _free_port(), name, str(tmp_path), depth), nprocs=world,
+             join=True)
+    got = np.concatenate([np.load(tmp_path / f"rank{r}.npy") for r in range(world)], axis=-1)
+    want, _ = _oracle(c, c["nx"]).run(_initial(c), c["steps"])
+    np.testing.assert_array_equal(got, want)
+
+
+def test_default_depth():
+    from paper_1905_04597_gb300 import slab
+    assert slab.default_depth(4096, 4) == 16   # 2 * 16 * 4 = 128 = 4096 / 32
+    assert slab.default_depth(512, 4) == 2     # 16 <= 16
+    assert slab.default_depth(96, 3) == 1
+    for Ls, reach in ((4096, 4), (512, 4), (2048, 9), (100, 1)):
+        m = slab.default_depth(Ls, reach)
+        assert m == 1 or 2 * m * reach * 32 <= Ls
+        assert m == 16 or 2 * (m + 1) * reach * 32 > Ls
 
 
 def test_single_rank_exchange_wraps_onto_itself():
