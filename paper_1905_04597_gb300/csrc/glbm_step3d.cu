@@ -18,7 +18,7 @@ struct Tiles3D;
 // GB300 (256 x 64 x 32, walls, about 400 MB per step).
 GLBM_TILES_3D(1, float, {1, 8, 1}, {1, 4, 1}, {3, 2, 1}, {3, 4, 1})
 GLBM_TILES_3D(2, float, {5, 1, 1}, {5, 2, 1}, {5, 4, 1}, {3, 2, 1})
-GLBM_TILES_3D(3, float, {5, 1, 1}, {7, 1, 1}, {7, 2, 1})
+GLBM_TILES_3D(3, float, {7, 1, 1}, {5, 1, 1}, {7, 2, 1})
 GLBM_TILES_3D(1, double, {1, 4, 1}, {3, 2, 1})
 GLBM_TILES_3D(2, double, {5, 1, 1}, {5, 2, 1})
 GLBM_TILES_3D(3, double, {7, 1, 1}, {10, 1, 1})

@@ -277,8 +277,33 @@ struct Step3D {
                 // the row's dither draws, divided by omega
                 const float ua = DEV ? mul_rn(dither_unit(hrow), iom) : 0.0f;
                 const float ub = DEV ? mul_rn(dither_unit(dither_word_b(hrow)), iom) : 0.0f;
+                if constexpr (DEV) {
+                    // velocity columns in pairs (ix, ix + 1) on the two-lane FP32
+                    // instructions, each lane doing exactly the scalar loop's
+                    // operations in its order (bit-identical results); the last
+                    // of the odd 2N+1 columns takes the scalar loop
+                    const f32x2 B2 = pk2(B, B), gr2 = pk2(gr, gr), om2 = pk2(om, om),
+                                nwy2 = pk2(-wy, -wy), wz2 = pk2(wz, wz);
 #pragma unroll
-                for (int ix = 0; ix < Q1; ++ix) {
+                    for (int ix = 0; ix + 1 < Q1; ix += 2) {
+                        const f32x2 f0 = pk2(f[k][ix], f[k][ix + 1]);
+                        const f32x2 Bn = fma2(pk2(T(ix - N), T(ix + 1 - N)), gr2, B2);
+                        const f32x2 dxv = pk2(dx[ix], dx[ix + 1]);
+                        const float p0 = __int_as_float(__float_as_int(lo2(f0)) & 0x7F800000);
+                        const float p1 = __int_as_float(__float_as_int(hi2(f0)) & 0x7F800000);
+                        const f32x2 dith = mul2(pk2(dither_pick(ix, ua, ub, -ua, -ub),
+                                                    dither_pick(ix + 1, ua, ub, -ua, -ub)),
+                                                pk2(p0, p1));
+                        const f32x2 t1 =
+                            fma2(dxv, B2, fma2(pk2(A::W(tab, ix), A::W(tab, ix + 1)), Bn, dith));
+                        const f32x2 rr = fma2(mul2(dxv, nwy2), wz2, f0);
+                        const f32x2 v2 = fma2(om2, sub2(t1, rr), f0);
+                        op[ix * plane] = lo2(v2);
+                        op[(ix + 1) * plane] = hi2(v2);
+                    }
+                }
+#pragma unroll
+                for (int ix = (DEV ? Q1 - 1 : 0); ix < Q1; ++ix) {
                     const int nx = ix - N;
                     const T f0 = f[k][ix];
                     T v;
