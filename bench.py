@@ -89,15 +89,38 @@ def lattice_axes(cfg):
     return N, NX, 2 * N + 1 + (1 if zv & 2 else 0), 2 * NX + 1 + (1 if zv & 1 else 0), zv
 
 
+def workload_config(name, args, world):
+    """The `config` object of both arms' lines for a workload of workload():
+    what the workload is and how it is laid out and timed, nothing that
+    depends on the arm (the arm's storage and kernel choices are reported
+    beside it)."""
+    cfgs, label = workload(name)
+    c = cfgs[0]
+    dims = c["dims"]
+    N, NX, Q1y, Q1x, _ = lattice_axes(c)
+    Q = Q1y * Q1x if dims == 2 else ((2 * N + 1) ** 3 if dims == 3 else 2 * N + 1)
+    nodes = c["nx"] * (c["ny"] if dims >= 2 else 1) * (c["nz"] if dims == 3 else 1)
+    pops = Q * nodes * len(cfgs)
+    return {"workload": label, "lattice": f"D{dims}Q{Q}", "k": N - 1, "nodes": nodes,
+            "instances": len(cfgs),
+            "l2": (f"FP32 populations {4 * pops / 1e6:.0f} MB per buffer, two buffers "
+                   f"{8 * pops / 1e6:.0f} MB " + ("> 129 MB L2" if 8 * pops > 129e6 else
+                                                   "(fit in the 129 MB L2)") + "; no flush"),
+            "parallelism": f"instances batched per launch; {world} rank(s), independent copies",
+            "tiles": args.tiles}
+
+
 KERNEL_SOURCES = ("glbm_device.cuh", "glbm_step2d.cuh", "glbm_step2d_pair.cuh",
                   "glbm_step2d_launch.cuh", "glbm_tiles.h", "glbm_internal.h")
+KERNEL_SOURCES_3D = KERNEL_SOURCES + ("glbm_step3d.cuh", "glbm_step3d.cu")
 
 
-def kernel_source_hash():
-    """SHA-256 (first 16 hex digits) of the sources of the fused 2D step."""
+def kernel_source_hash(kernel=""):
+    """SHA-256 (first 16 hex digits) of the sources of the fused 2D step, and
+    of the 3D step's own sources too for a k_step3d kernel."""
     import hashlib
     h = hashlib.sha256()
-    for f in KERNEL_SOURCES:
+    for f in (KERNEL_SOURCES_3D if kernel.startswith("k_step3d") else KERNEL_SOURCES):
         with open(os.path.join(ROOT, "paper_1905_04597_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -114,7 +137,7 @@ def measured_traffic(kernel, workload):
         rec = json.load(fh)
     for r in rec.get("captures", []):
         if (r.get("kernel") == kernel and r.get("workload") == workload
-                and r.get("source_hash") == kernel_source_hash()):
+                and r.get("source_hash") == kernel_source_hash(kernel)):
             return r["dram_bytes_per_launch"]
     return None
 
@@ -457,13 +480,10 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": steps,
         "warmup": warmup, "ms_per_step": ms32 / steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": label, "lattice": f"D{dims}Q{Q}", "k": N - 1,
-                   "nodes": nodes, "instances": n_inst, "storage": "fp32 deviations",
-                   "l2": f"populations {2 * bytes32 / 2 / 1e6:.0f} MB per buffer set x2 > 129 MB L2; no flush",
-                   "parallelism": f"instances batched per launch; {world} rank(s), independent copies",
-                   "tiles": args.tiles,
-                   "wall_densities": {1: "own launch", 0: "in the tiles"}.get(
-                       wall_mode.get(glbm.FP32_DEV, -1), "no walls")},
+        "config": workload_config(args.workload, args, world),
+        "storage": "fp32 deviations",
+        "wall_densities": {1: "own launch", 0: "in the tiles"}.get(
+            wall_mode.get(glbm.FP32_DEV, -1), "no walls"),
         "mlups": nodes * n_inst * steps * world / (ms32 / 1e3) / 1e6,
         "hbm_gbs_algorithmic": gbs32,
         "fp64": {"value": value64, "unit": UNIT, "ms_per_step": ms64 / steps64, "steps": steps64,
@@ -928,7 +948,8 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": label, "reference": "FP64 CPU oracle (oracle/glbm_oracle.c)"},
+            "config": workload_config(args.workload, args, world),
+            "reference": "FP64 CPU oracle (oracle/glbm_oracle.c)",
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": _omp_threads(), "kind": "oracle",
                              "sample": sample + f", {_omp_threads()} threads (collision over rows)",
                              "host": _host_cpu()},
