@@ -444,12 +444,15 @@ struct Step2D {
                         const T r = fma(dxv, nwy, f0);
                         v = fma(om, t1 - r, f0);
                     } else {
-                        T eq = ex[ix] * rey;
+                        // f^eq - f0 in one fused rounding, then the force term,
+                        // then f0 + omega (f^eq + F/omega - f0): three FP64
+                        // instructions (two without a force term)
+                        T d = fma(ex[ix], rey, -f0);
                         if constexpr (GUO)
-                            eq = fma(A::W(tabx, ix), fma(T(nx), grA, T(AX::ck(ix)) * grB), eq);
+                            d = fma(A::W(tabx, ix), fma(T(nx), grA, T(AX::ck(ix)) * grB), d);
                         else if (nx != 0)
-                            eq = fma(A::WN(tabx, ix), gr, eq);
-                        v = fma(om, eq - f0, f0);
+                            d = fma(A::WN(tabx, ix), gr, d);
+                        v = fma(om, d, f0);
                     }
                     op[ix * plane] = v;
                 }

@@ -226,6 +226,8 @@ struct Step3D {
             eq_dev_all<N, T>(tab, ux, dx);
             eq_dev_all<N, T>(tab, uy, dy);
             eq_dev_all<N, T>(tab, uz, dz);
+#pragma unroll
+            for (int ix = 0; ix < Q1; ++ix) dx[ix] += A::W(tab, ix);  // E^x, once per node
         }
 
         // ZROW: this thread's n_y deviation, selected once
@@ -322,9 +324,11 @@ struct Step3D {
                         const T r = fma(-mul_rn(dx[ix], wy), wz, f0);  // f0 - d^x W^y W^z
                         v = fma(om, t1 - r, f0);
                     } else {
-                        T eq = (A::W(tab, ix) + dx[ix]) * rez_y;
-                        if (nx != 0) eq = fma(A::WN(tab, ix), gr, eq);
-                        v = fma(om, eq - f0, f0);
+                        // dx holds E^x itself in FP64 mode; f^eq - f0 in one
+                        // fused rounding, the force term, f0 + omega (...)
+                        T d = fma(dx[ix], rez_y, -f0);
+                        if (nx != 0) d = fma(A::WN(tab, ix), gr, d);
+                        v = fma(om, d, f0);
                     }
                     op[ix * plane] = v;
                 }
