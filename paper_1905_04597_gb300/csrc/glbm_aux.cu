@@ -64,22 +64,29 @@ __global__ void k_set_equilibrium(const __grid_constant__ AuxArgs a, void *f, in
     const double r = rho[node], u = ux[node], v = a.dims == 2 ? uy[node] : 0.0;
     const long long base = (long long)inst * a.inst_stride + (long long)y * a.pitch + x;
     const int Qy = a.dims == 2 ? ax_q(a.tab) : 1;
-    double dxs[GLBM_MAXQA];  // E^x - W^x of the node, evaluated once
-    for (int ix = 0; ix < Q1x; ++ix) dxs[ix] = eq_dev_rt(tx, u, ix);
+    const bool f64 = a.prec == GLBM_FP64;
+    double exs[GLBM_MAXQA];  // per node: E^x (FP64 storage) or E^x - W^x (FP32 deviations)
+    for (int ix = 0; ix < Q1x; ++ix) {
+        const double dx = eq_dev_rt(tx, u, ix);
+        exs[ix] = f64 ? tx.W[ix] + dx : dx;
+    }
     for (int iy = 0; iy < Qy; ++iy) {
         const double wy = a.dims == 2 ? a.tab.W[iy] : 1.0;
         const double dy = a.dims == 2 ? eq_dev_rt(a.tab, v, iy) : 0.0;
-        for (int ix = 0; ix < Q1x; ++ix) {
-            const double wx = tx.W[ix];
-            const double dx = dxs[ix];
-            const long long idx = base + (long long)(iy * Q1x + ix) * a.plane;
-            if (a.prec == GLBM_FP64) {
-                static_cast<double *>(f)[idx] = r * (wx + dx) * (wy + dy);
-            } else {
-                // rho E^x E^y - W^x W^y without cancellation
-                const double dev = (r - 1.0) * wx * wy + r * (dx * (wy + dy) + wx * dy);
-                static_cast<float *>(f)[idx] = (float)dev;
-            }
+        // per row: A = rho E^y and B = rho E^y - W^y = (rho - 1) W^y + rho d^y
+        // (no cancellation); then rho E^x E^y = E^x A and, in deviations,
+        // rho E^x E^y - W^x W^y = W^x B + d^x A: one or two FP64 operations
+        // per population
+        const double A = r * (wy + dy);
+        const double B = fma(r - 1.0, wy, r * dy);
+        const long long row = base + (long long)(iy * Q1x) * a.plane;
+        if (f64) {
+            double *out = static_cast<double *>(f) + row;
+            for (int ix = 0; ix < Q1x; ++ix) out[(long long)ix * a.plane] = exs[ix] * A;
+        } else {
+            float *out = static_cast<float *>(f) + row;
+            for (int ix = 0; ix < Q1x; ++ix)
+                out[(long long)ix * a.plane] = (float)fma(exs[ix], A, tx.W[ix] * B);
         }
     }
 }
@@ -121,7 +128,7 @@ __global__ void k_get_populations(const __grid_constant__ AuxArgs a, const void 
 __device__ double pulled(const AuxArgs &a, const InstParams &ip, const void *f, long long ibase,
                          int x, int y, int ix, int iy, double rw_lo, double rw_hi)
 {
-    const int N = a.N, Q1 = 2 * N + 1;
+    const int N = a.N;
     if (a.dims == 1) {
         const int n = ix - N;
         int xs = x - n;
@@ -199,15 +206,63 @@ __global__ void k_moments(const __grid_constant__ AuxArgs a, const void *f, int 
     // one pass of raw moments, row by row: R_p = sum_ix xi_x^p v for p = 0..3,
     // then the central moments about u from them (expanded in FP64)
     double M0 = 0.0, jx = 0.0, jy = 0.0, Pxx = 0.0, Pyy = 0.0, Pxy = 0.0, Mx = 0.0, My = 0.0;
+    const bool f64 = a.prec == GLBM_FP64;
+    const int cmax = ax_vel(tx, Q1x - 1);  // the largest x speed
+    const bool one_wrap = a.Lx > cmax;
+    // FP32 deviations: the rest weights' part of a row's R_p is W^y sum_ix W^x
+    // xi_x^p, added once per row
+    double m0 = 0.0, m1 = 0.0, m2 = 0.0, m3 = 0.0;
+    if (!f64 && a.dims == 2) {
+        for (int ix = 0; ix < Q1x; ++ix) {
+            const double w = tx.W[ix], c = ax_vel(tx, ix);
+            m0 += w;
+            m1 = fma(c, w, m1);
+            m2 = fma(c * c, w, m2);
+            m3 = fma(c * c * c, w, m3);
+        }
+    }
     for (int iy = 0; iy < Qy; ++iy) {
         double R0 = 0.0, R1 = 0.0, R2 = 0.0, R3 = 0.0;
-        for (int ix = 0; ix < Q1x; ++ix) {
-            const double v = pulled(a, ip, f, ibase, x, y, ix, iy, rw_lo, rw_hi);
-            const double c = ax_vel(tx, ix);
-            R0 += v;
-            R1 = fma(c, v, R1);
-            R2 = fma(c * c, v, R2);
-            R3 = fma(c * c * c, v, R3);
+        const int ny = a.dims == 2 ? ax_vel(a.tab, iy) : 0;
+        int ys = y - ny;
+        if (a.dims == 1 || (a.bc == GLBM_BC_WALLS && (ys < 0 || ys >= a.Ly))) {
+            // 1D (bounce-back ends) and rows emitted by a wall: value by value
+            for (int ix = 0; ix < Q1x; ++ix) {
+                const double v = pulled(a, ip, f, ibase, x, y, ix, iy, rw_lo, rw_hi);
+                const double c = ax_vel(tx, ix);
+                R0 += v;
+                R1 = fma(c, v, R1);
+                R2 = fma(c * c, v, R2);
+                R3 = fma(c * c * c, v, R3);
+            }
+        } else {
+            // a pulled row: the velocity columns in mirror pairs (+c, -c), so
+            // that the odd powers take the pair's difference and the even ones
+            // its sum; stored values (FP32: deviations) are summed and the rest
+            // weights' part is added once
+            if (a.bc != GLBM_BC_WALLS) ys = wrap_index(ys, a.Ly);
+            const long long row = ibase + (long long)(iy * Q1x) * a.plane + (long long)ys * a.pitch;
+            for (int p = 0; p < Q1x / 2; ++p) {
+                const int ipos = Q1x - 1 - p;
+                const int cv = ax_vel(tx, ipos);  // > 0; column p moves at -cv
+                const long long ap = row + (long long)ipos * a.plane + wrap_shift(x - cv, a.Lx, one_wrap);
+                const long long am = row + (long long)p * a.plane + wrap_shift(x + cv, a.Lx, one_wrap);
+                const double vp = load_full(a, f, ap, 0), vm = load_full(a, f, am, 0);
+                const double sp = vp + vm, dm = vp - vm;
+                const double c = cv, c2 = c * c;
+                R0 += sp;
+                R1 = fma(c, dm, R1);
+                R2 = fma(c2, sp, R2);
+                R3 = fma(c2 * c, dm, R3);
+            }
+            if (Q1x & 1) R0 += load_full(a, f, row + (long long)(Q1x / 2) * a.plane + x, 0);
+            if (!f64) {
+                const double wy = a.tab.W[iy];
+                R0 = fma(wy, m0, R0);
+                R1 = fma(wy, m1, R1);
+                R2 = fma(wy, m2, R2);
+                R3 = fma(wy, m3, R3);
+            }
         }
         const double cy = a.dims == 2 ? ax_vel(a.tab, iy) : 0.0;
         M0 += R0;
@@ -545,27 +600,31 @@ __global__ void k_set_equilibrium3d(const __grid_constant__ AuxArgs a, void *f, 
     const long long node = (long long)zy * a.Lx + x;
     const double r = rho[node];
     const long long base = (long long)inst * a.inst_stride + (long long)zy * a.pitch + x;
-    double dxs[GLBM_MAXQA], dys[GLBM_MAXQA];  // E - W of the node per axis, evaluated once
+    const bool f64 = a.prec == GLBM_FP64;
+    // per node: E^x (FP64 storage) or E^x - W^x (FP32 deviations), and E^y - W^y
+    double exs[GLBM_MAXQA], dys[GLBM_MAXQA];
     for (int i = 0; i < Q1; ++i) {
-        dxs[i] = eq_dev_rt(a.tab, ux[node], i);
+        const double dx = eq_dev_rt(a.tab, ux[node], i);
+        exs[i] = f64 ? a.tab.W[i] + dx : dx;
         dys[i] = eq_dev_rt(a.tab, uy[node], i);
     }
     for (int iz = 0; iz < Q1; ++iz) {
         const double wz = a.tab.W[iz], dz = eq_dev_rt(a.tab, uz[node], iz);
         for (int iy = 0; iy < Q1; ++iy) {
             const double wy = a.tab.W[iy], dy = dys[iy];
-            for (int ix = 0; ix < Q1; ++ix) {
-                const double wx = a.tab.W[ix], dx = dxs[ix];
-                const long long idx = base + (long long)((iz * Q1 + iy) * Q1 + ix) * a.plane;
-                if (a.prec == GLBM_FP64) {
-                    static_cast<double *>(f)[idx] = r * (wx + dx) * (wy + dy) * (wz + dz);
-                } else {
-                    // rho E^x E^y E^z - W^x W^y W^z without cancellation
-                    const double eyz = (wy + dy) * (wz + dz), wyz = wy * wz;
-                    const double dyz = dy * (wz + dz) + wy * dz;  // e^y e^z - W^y W^z
-                    const double dev = (r - 1.0) * wx * wyz + r * (dx * eyz + wx * dyz);
-                    static_cast<float *>(f)[idx] = (float)dev;
-                }
+            // per row: A = rho E^y E^z and B = rho E^y E^z - W^y W^z =
+            // (rho - 1) W^y W^z + rho (d^y E^z + W^y d^z) (no cancellation);
+            // then rho E^x E^y E^z = E^x A, and in deviations W^x B + d^x A
+            const double A = r * ((wy + dy) * (wz + dz));
+            const double B = fma(r - 1.0, wy * wz, r * fma(dy, wz + dz, wy * dz));
+            const long long row = base + (long long)((iz * Q1 + iy) * Q1) * a.plane;
+            if (f64) {
+                double *out = static_cast<double *>(f) + row;
+                for (int ix = 0; ix < Q1; ++ix) out[(long long)ix * a.plane] = exs[ix] * A;
+            } else {
+                float *out = static_cast<float *>(f) + row;
+                for (int ix = 0; ix < Q1; ++ix)
+                    out[(long long)ix * a.plane] = (float)fma(exs[ix], A, a.tab.W[ix] * B);
             }
         }
     }
@@ -639,16 +698,62 @@ __global__ void k_moments3d(const __grid_constant__ AuxArgs a, const void *f, in
     double rho = 0.0, jx = 0.0, jy = 0.0, jz = 0.0;
     double Pxx = 0.0, Pyy = 0.0, Pzz = 0.0, Pxy = 0.0, Pxz = 0.0, Pyz = 0.0;
     double Mx = 0.0, My = 0.0, Mz = 0.0;  // sum xi_a |xi|^2 v
+    const bool f64 = a.prec == GLBM_FP64;
+    const bool one_wrap = a.Lx > N;
+    // FP32 deviations: the rest weights' part of a row's R_p is W^y W^z sum_ix
+    // W^x xi_x^p, added once per row
+    double m0 = 0.0, m1 = 0.0, m2 = 0.0, m3 = 0.0;
+    if (!f64) {
+        for (int ix = 0; ix < Q1; ++ix) {
+            const double w = a.tab.W[ix], c = ix - N;
+            m0 += w;
+            m1 = fma(c, w, m1);
+            m2 = fma(c * c, w, m2);
+            m3 = fma(c * c * c, w, m3);
+        }
+    }
     for (int iz = 0; iz < Q1; ++iz)
         for (int iy = 0; iy < Q1; ++iy) {
             double R0 = 0.0, R1 = 0.0, R2 = 0.0, R3 = 0.0;
-            for (int ix = 0; ix < Q1; ++ix) {
-                const double v = pulled3d(a, ip, f, ibase, x, y, z, ix, iy, iz, rw_lo, rw_hi);
-                const double c = ix - N;
-                R0 += v;
-                R1 = fma(c, v, R1);
-                R2 = fma(c * c, v, R2);
-                R3 = fma(c * c * c, v, R3);
+            int ys = y - (iy - N);
+            if (a.bc == GLBM_BC_WALLS && (ys < 0 || ys >= a.Ly)) {
+                // a row emitted by a wall: value by value
+                for (int ix = 0; ix < Q1; ++ix) {
+                    const double v = pulled3d(a, ip, f, ibase, x, y, z, ix, iy, iz, rw_lo, rw_hi);
+                    const double c = ix - N;
+                    R0 += v;
+                    R1 = fma(c, v, R1);
+                    R2 = fma(c * c, v, R2);
+                    R3 = fma(c * c * c, v, R3);
+                }
+            } else {
+                // a pulled row: mirror pairs (+c, -c), odd powers on the pair's
+                // difference, even ones on its sum; FP32 stores deviations, whose
+                // rest weights' part is added once per row
+                if (a.bc != GLBM_BC_WALLS) ys = wrap_index(ys, a.Ly);
+                const int zs = wrap_index(z - (iz - N), a.Lz);
+                const long long row = ibase + (long long)((iz * Q1 + iy) * Q1) * a.plane +
+                                      ((long long)zs * a.Ly + ys) * a.pitch;
+                for (int n = 1; n <= N; ++n) {
+                    const double vp = load_full(a, f, row + (long long)(N + n) * a.plane +
+                                                          wrap_shift(x - n, a.Lx, one_wrap), 0);
+                    const double vm = load_full(a, f, row + (long long)(N - n) * a.plane +
+                                                          wrap_shift(x + n, a.Lx, one_wrap), 0);
+                    const double sp = vp + vm, dm = vp - vm;
+                    const double c = n, c2 = c * c;
+                    R0 += sp;
+                    R1 = fma(c, dm, R1);
+                    R2 = fma(c2, sp, R2);
+                    R3 = fma(c2 * c, dm, R3);
+                }
+                R0 += load_full(a, f, row + (long long)N * a.plane + x, 0);
+                if (!f64) {
+                    const double wyz = a.tab.W[iy] * a.tab.W[iz];
+                    R0 = fma(wyz, m0, R0);
+                    R1 = fma(wyz, m1, R1);
+                    R2 = fma(wyz, m2, R2);
+                    R3 = fma(wyz, m3, R3);
+                }
             }
             const double cy = iy - N, cz = iz - N, s2 = cy * cy + cz * cz;
             rho += R0;
