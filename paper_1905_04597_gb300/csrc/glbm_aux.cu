@@ -31,6 +31,27 @@ __device__ double eq_dev_rt(const AxisTableHi &t, double u, int i)
     return n >= 0 ? fma(u, bo, ae) : fma(-u, bo, ae);
 }
 
+// E_i(u) - W_i of every velocity index of a runtime level, the mirror pairs
+// (i, Q - 1 - i), whose velocities are opposite, from one evaluation of the
+// even and odd parts each: the same operations as eq_dev_rt per index.
+__device__ void eq_dev_all_rt(const AxisTableHi &t, double u, double *out)
+{
+    const int N = t.N, Q = ax_q(t);
+    const double v = u * u;
+    for (int p = 0; p < Q / 2; ++p) {
+        const int an = ax_vel(t, Q - 1 - p);  // > 0
+        const int m = t.zv ? (an - 1) / 2 : an;
+        double ae = t.Ce[m][N];
+        for (int k = N - 1; k >= 1; --k) ae = fma(ae, v, t.Ce[m][k]);
+        ae *= v;
+        double bo = t.Co[m][N - 1];
+        for (int k = N - 2; k >= 0; --k) bo = fma(bo, v, t.Co[m][k]);
+        out[Q - 1 - p] = fma(u, bo, ae);
+        out[p] = fma(-u, bo, ae);
+    }
+    if (Q & 1) out[Q / 2] = eq_dev_rt(t, u, Q / 2);
+}
+
 __device__ __forceinline__ double load_full(const AuxArgs &a, const void *f, long long idx, int q)
 {
     (void)q;
@@ -66,13 +87,14 @@ __global__ void k_set_equilibrium(const __grid_constant__ AuxArgs a, void *f, in
     const int Qy = a.dims == 2 ? ax_q(a.tab) : 1;
     const bool f64 = a.prec == GLBM_FP64;
     double exs[GLBM_MAXQA];  // per node: E^x (FP64 storage) or E^x - W^x (FP32 deviations)
-    for (int ix = 0; ix < Q1x; ++ix) {
-        const double dx = eq_dev_rt(tx, u, ix);
-        exs[ix] = f64 ? tx.W[ix] + dx : dx;
-    }
+    double dys[GLBM_MAXQA];  // E^y - W^y
+    eq_dev_all_rt(tx, u, exs);
+    if (f64)
+        for (int ix = 0; ix < Q1x; ++ix) exs[ix] += tx.W[ix];
+    if (a.dims == 2) eq_dev_all_rt(a.tab, v, dys);
     for (int iy = 0; iy < Qy; ++iy) {
         const double wy = a.dims == 2 ? a.tab.W[iy] : 1.0;
-        const double dy = a.dims == 2 ? eq_dev_rt(a.tab, v, iy) : 0.0;
+        const double dy = a.dims == 2 ? dys[iy] : 0.0;
         // per row: A = rho E^y and B = rho E^y - W^y = (rho - 1) W^y + rho d^y
         // (no cancellation); then rho E^x E^y = E^x A and, in deviations,
         // rho E^x E^y - W^x W^y = W^x B + d^x A: one or two FP64 operations
@@ -242,6 +264,7 @@ __global__ void k_moments(const __grid_constant__ AuxArgs a, const void *f, int 
             // weights' part is added once
             if (a.bc != GLBM_BC_WALLS) ys = wrap_index(ys, a.Ly);
             const long long row = ibase + (long long)(iy * Q1x) * a.plane + (long long)ys * a.pitch;
+#pragma unroll 4
             for (int p = 0; p < Q1x / 2; ++p) {
                 const int ipos = Q1x - 1 - p;
                 const int cv = ax_vel(tx, ipos);  // > 0; column p moves at -cv
@@ -602,14 +625,14 @@ __global__ void k_set_equilibrium3d(const __grid_constant__ AuxArgs a, void *f, 
     const long long base = (long long)inst * a.inst_stride + (long long)zy * a.pitch + x;
     const bool f64 = a.prec == GLBM_FP64;
     // per node: E^x (FP64 storage) or E^x - W^x (FP32 deviations), and E^y - W^y
-    double exs[GLBM_MAXQA], dys[GLBM_MAXQA];
-    for (int i = 0; i < Q1; ++i) {
-        const double dx = eq_dev_rt(a.tab, ux[node], i);
-        exs[i] = f64 ? a.tab.W[i] + dx : dx;
-        dys[i] = eq_dev_rt(a.tab, uy[node], i);
-    }
+    double exs[GLBM_MAXQA], dys[GLBM_MAXQA], dzs[GLBM_MAXQA];
+    eq_dev_all_rt(a.tab, ux[node], exs);
+    eq_dev_all_rt(a.tab, uy[node], dys);
+    eq_dev_all_rt(a.tab, uz[node], dzs);
+    if (f64)
+        for (int i = 0; i < Q1; ++i) exs[i] += a.tab.W[i];
     for (int iz = 0; iz < Q1; ++iz) {
-        const double wz = a.tab.W[iz], dz = eq_dev_rt(a.tab, uz[node], iz);
+        const double wz = a.tab.W[iz], dz = dzs[iz];
         for (int iy = 0; iy < Q1; ++iy) {
             const double wy = a.tab.W[iy], dy = dys[iy];
             // per row: A = rho E^y E^z and B = rho E^y E^z - W^y W^z =
@@ -734,6 +757,7 @@ __global__ void k_moments3d(const __grid_constant__ AuxArgs a, const void *f, in
                 const int zs = wrap_index(z - (iz - N), a.Lz);
                 const long long row = ibase + (long long)((iz * Q1 + iy) * Q1) * a.plane +
                                       ((long long)zs * a.Ly + ys) * a.pitch;
+#pragma unroll 3
                 for (int n = 1; n <= N; ++n) {
                     const double vp = load_full(a, f, row + (long long)(N + n) * a.plane +
                                                           wrap_shift(x - n, a.Lx, one_wrap), 0);
