@@ -211,12 +211,41 @@ __device__ double wall_density(const AuxArgs &a, const InstParams &ip, const voi
 __global__ void k_moments(const __grid_constant__ AuxArgs a, const void *f, int inst,
                           double *__restrict__ out)
 {
+    const AxisTableHi &tx = a.dims == 2 ? a.tabx : a.tab;
+    const int Q1x = ax_q(tx);
+    const bool f64 = a.prec == GLBM_FP64;
+    // per block, from the x axis: (c, c^2, c^3) of every mirror pair's positive
+    // velocity and, for FP32 deviations, m_p = sum_ix W^x xi_x^p (the rest
+    // weights' part of a row's R_p is W^y m_p, added once per row)
+    __shared__ double cpow[GLBM_MAXQA / 2][3];
+    __shared__ double wmom[4];
+    if ((int)threadIdx.x < Q1x / 2) {
+        const double c = ax_vel(tx, Q1x - 1 - threadIdx.x), c2 = c * c;
+        cpow[threadIdx.x][0] = c;
+        cpow[threadIdx.x][1] = c2;
+        cpow[threadIdx.x][2] = c2 * c;
+    }
+    if (threadIdx.x == 32) {
+        double m0 = 0.0, m1 = 0.0, m2 = 0.0, m3 = 0.0;
+        if (!f64 && a.dims == 2) {
+            for (int ix = 0; ix < Q1x; ++ix) {
+                const double w = tx.W[ix], c = ax_vel(tx, ix);
+                m0 += w;
+                m1 = fma(c, w, m1);
+                m2 = fma(c * c, w, m2);
+                m3 = fma(c * c * c, w, m3);
+            }
+        }
+        wmom[0] = m0;
+        wmom[1] = m1;
+        wmom[2] = m2;
+        wmom[3] = m3;
+    }
+    __syncthreads();
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y;
     if (x >= a.Lx) return;
     const InstParams &ip = a.ip[inst];
-    const AxisTableHi &tx = a.dims == 2 ? a.tabx : a.tab;
-    const int Q1x = ax_q(tx);
     const int Qy = a.dims == 2 ? ax_q(a.tab) : 1;
     const int vmax = a.tab.zv ? 2 * a.N + 1 : a.N;  // fastest y velocity
     const long long ibase = (long long)inst * a.inst_stride;
@@ -228,21 +257,9 @@ __global__ void k_moments(const __grid_constant__ AuxArgs a, const void *f, int 
     // one pass of raw moments, row by row: R_p = sum_ix xi_x^p v for p = 0..3,
     // then the central moments about u from them (expanded in FP64)
     double M0 = 0.0, jx = 0.0, jy = 0.0, Pxx = 0.0, Pyy = 0.0, Pxy = 0.0, Mx = 0.0, My = 0.0;
-    const bool f64 = a.prec == GLBM_FP64;
     const int cmax = ax_vel(tx, Q1x - 1);  // the largest x speed
     const bool one_wrap = a.Lx > cmax;
-    // FP32 deviations: the rest weights' part of a row's R_p is W^y sum_ix W^x
-    // xi_x^p, added once per row
-    double m0 = 0.0, m1 = 0.0, m2 = 0.0, m3 = 0.0;
-    if (!f64 && a.dims == 2) {
-        for (int ix = 0; ix < Q1x; ++ix) {
-            const double w = tx.W[ix], c = ax_vel(tx, ix);
-            m0 += w;
-            m1 = fma(c, w, m1);
-            m2 = fma(c * c, w, m2);
-            m3 = fma(c * c * c, w, m3);
-        }
-    }
+    const double m0 = wmom[0], m1 = wmom[1], m2 = wmom[2], m3 = wmom[3];
     for (int iy = 0; iy < Qy; ++iy) {
         double R0 = 0.0, R1 = 0.0, R2 = 0.0, R3 = 0.0;
         const int ny = a.dims == 2 ? ax_vel(a.tab, iy) : 0;
@@ -272,11 +289,10 @@ __global__ void k_moments(const __grid_constant__ AuxArgs a, const void *f, int 
                 const long long am = row + (long long)p * a.plane + wrap_shift(x + cv, a.Lx, one_wrap);
                 const double vp = load_full(a, f, ap, 0), vm = load_full(a, f, am, 0);
                 const double sp = vp + vm, dm = vp - vm;
-                const double c = cv, c2 = c * c;
                 R0 += sp;
-                R1 = fma(c, dm, R1);
-                R2 = fma(c2, sp, R2);
-                R3 = fma(c2 * c, dm, R3);
+                R1 = fma(cpow[p][0], dm, R1);
+                R2 = fma(cpow[p][1], sp, R2);
+                R3 = fma(cpow[p][2], dm, R3);
             }
             if (Q1x & 1) R0 += load_full(a, f, row + (long long)(Q1x / 2) * a.plane + x, 0);
             if (!f64) {
