@@ -1220,6 +1220,12 @@ extern "C" glbm_status glbm_step(glbm_ctx *c, int64_t n)
             // arithmetic, same dither: the results are identical)
             glbm_status st = df_words_ready(c);
             if (st == GLBM_OK) st = spare_ready(c);
+            if (st == GLBM_E_NOMEM) {
+                // no memory for the counters or the third state buffer: this
+                // context steps launch after launch from now on (same results)
+                c->dataflow = 0;
+                return glbm_step(c, n);
+            }
             if (st != GLBM_OK) return st;
             const Binding start = binding(c);
             int64_t k = 0;
@@ -1757,6 +1763,10 @@ static glbm_status autotune_dataflow(glbm_ctx *c, cudaEvent_t e0, cudaEvent_t e1
     const int N = c->geo[0].N;
     glbm_status st = df_words_ready(c);
     if (st == GLBM_OK) st = spare_ready(c);
+    if (st == GLBM_E_NOMEM) {  // no room for dataflow chunks: keep stepping launch after launch
+        c->dataflow = 0;
+        return tiles_changed(c);
+    }
     if (st != GLBM_OK) return st;
     const int64_t steps = 2 * kGraphChunk;
     const int tile0 = c->tile[N];

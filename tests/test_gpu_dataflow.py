@@ -218,3 +218,53 @@ def test_checkpoint_and_adjoint_after_rotated_buffers(tmp_path):
     np.testing.assert_array_equal(np.asarray(ja), np.asarray(jb))
     for lat in (a, b, c):
         lat.close()
+
+
+def test_dataflow_falls_back_when_its_buffers_cannot_be_allocated():
+    """An allocator that refuses the third state buffer (and the dataflow
+    counters): glbm_step runs the call launch after launch, switches the
+    context's dataflow off, and the results are those of stepping launch after
+    launch from the start."""
+    import torch
+    refuse = {"on": False}
+
+    def _alloc(nbytes, stream, user):
+        if refuse["on"]:
+            return None
+        return torch.cuda.caching_allocator_alloc(int(nbytes), torch.cuda.current_device(),
+                                                  stream or 0)
+
+    def _free(ptr, stream, user):
+        torch.cuda.caching_allocator_delete(ptr)
+
+    hooks = (glbm.ALLOC_FN(_alloc), glbm.FREE_FN(_free))
+    had_torch = glbm._torch_alloc_refs is not None
+    glbm.check(glbm.lib().glbm_set_allocator(hooks[0], hooks[1], None))
+    nx, ny = 96, 32
+    cfg = dict(dims=2, nx=nx, ny=ny, k=2, kn=0.1, prec=glbm.FP32_DEV, u_wall_lo=-0.05,
+               u_wall_hi=0.05)
+    fields = inputs.random_macro(8, nx, ny)
+    try:
+        lat = glbm.Lattice(cfg)
+        lat.set_wall_launch(0)
+        lat.set_equilibrium(0, *fields)
+        assert lat.dataflow == 1
+        refuse["on"] = True
+        lat.step(40)
+        refuse["on"] = False
+        assert lat.dataflow == 0 and lat.time == 40
+        got = lat.get_populations(0)
+        lat.close()
+    finally:
+        refuse["on"] = False
+        if had_torch:
+            glbm.install_torch_allocator()
+        else:
+            glbm.uninstall_allocator()
+    ref = glbm.Lattice(cfg)
+    ref.set_wall_launch(0)
+    ref.set_dataflow(0)
+    ref.set_equilibrium(0, *fields)
+    ref.step(40)
+    np.testing.assert_array_equal(got, ref.get_populations(0))
+    ref.close()
