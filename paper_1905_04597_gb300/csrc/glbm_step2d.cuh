@@ -231,25 +231,38 @@ struct Step2D {
                 if (ny != 0) acc2(s_y, c_y, mul_rn(T(ny), rs));
             }
         }
-        sm.part[r][g][0][lane] = s_r;
-        sm.part[r][g][1][lane] = c_r;
-        sm.part[r][g][2][lane] = s_x;
-        sm.part[r][g][3][lane] = c_x;
-        sm.part[r][g][4][lane] = s_y;
-        sm.part[r][g][5][lane] = c_y;
-        __syncthreads();
-
         // ---- phase 2: moments, equilibrium, relaxation, store --------------
         T S_r = T(0), C_r = T(0), S_x = T(0), C_x = T(0), S_y = T(0), C_y = T(0);
-#pragma unroll
-        for (int gi = 0; gi < G; ++gi) {
-            acc2(S_r, C_r, sm.part[r][gi][0][lane]);
-            acc2(S_x, C_x, sm.part[r][gi][2][lane]);
-            acc2(S_y, C_y, sm.part[r][gi][4][lane]);
+        if constexpr (G == 1) {
+            // one warp group holds a node's every row: its own sums are the
+            // node's (adding them to zero as below changes nothing), so no
+            // exchange and no barrier
+            S_r = s_r;
+            S_x = s_x;
+            S_y = s_y;
             if (DEV) {
-                C_r += sm.part[r][gi][1][lane];
-                C_x += sm.part[r][gi][3][lane];
-                C_y += sm.part[r][gi][5][lane];
+                C_r = c_r;
+                C_x = c_x;
+                C_y = c_y;
+            }
+        } else {
+            sm.part[r][g][0][lane] = s_r;
+            sm.part[r][g][1][lane] = c_r;
+            sm.part[r][g][2][lane] = s_x;
+            sm.part[r][g][3][lane] = c_x;
+            sm.part[r][g][4][lane] = s_y;
+            sm.part[r][g][5][lane] = c_y;
+            __syncthreads();
+#pragma unroll
+            for (int gi = 0; gi < G; ++gi) {
+                acc2(S_r, C_r, sm.part[r][gi][0][lane]);
+                acc2(S_x, C_x, sm.part[r][gi][2][lane]);
+                acc2(S_y, C_y, sm.part[r][gi][4][lane]);
+                if (DEV) {
+                    C_r += sm.part[r][gi][1][lane];
+                    C_x += sm.part[r][gi][3][lane];
+                    C_y += sm.part[r][gi][5][lane];
+                }
             }
         }
         const T m0 = S_r + C_r;            // FP32: delta rho; FP64: rho
