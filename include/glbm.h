@@ -342,12 +342,12 @@ glbm_status glbm_conservation_noalloc(const double *fields, int dims, int64_t no
  * no state is copied) and, if a node leaves the positivity domain, takes that
  * state back and replays the call one step after another, which stops after
  * the failing step. A wait that takes longer than 0.5 s (none should) returns
- * GLBM_E_TIMEOUT with the state of the call's start. on = 0 launches the steps one after another. on = 2 is a
- * test of that path: every wait of a chunk's later steps asks for more tiles
- * than a band has, so the first call of glbm_step waits 0.5 s and returns
- * GLBM_E_TIMEOUT with the state unchanged.
- * If the counters or the third state buffer cannot be allocated, the context
- * steps launch after launch from then on (glbm_get_dataflow returns 0).
+ * GLBM_E_TIMEOUT with the state of the call's start.
+ * on = 0 launches the steps one after another. on = 2 is a test of the timeout
+ * path: every wait of a chunk's later steps asks for more tiles than a band
+ * has, so the first call of glbm_step waits 0.5 s and returns GLBM_E_TIMEOUT
+ * with the state unchanged. If the counters or the third state buffer cannot
+ * be allocated, the context steps launch after launch from then on.
  * glbm_get_dataflow returns 1 when the context's steps take this path.
  */
 glbm_status glbm_set_dataflow(glbm_ctx *ctx, int on);
